@@ -1,0 +1,919 @@
+/*
+ * CPU oracle for light field display point rendering (LFDPR).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or call
+ * this file: only the tests, the package's smoke check and the benchmark's CPU
+ * baseline do. It shares no code, header, table or constant generator with
+ * the CUDA library; the two meet only through the seeded inputs.
+ *
+ * What it computes, step by step in the paper's order (Sec. 3 and Sec. 4):
+ *   1. per-frame model transform (the scenes rotate every frame, Sec. 5.1);
+ *   2. vertex visibility against every LFD view (Sec. 3, pipeline overview);
+ *   3. the triangle's sampling frame aligned with the views' horizontal and
+ *      vertical axes (Sec. 3.1, T_align);
+ *   4. LFD-biased horizontal and vertical sample spacings from pixel edges
+ *      reverse-projected at the closest point of the triangle (Sec. 3.1, Fig. 4);
+ *   5. texture-based sampling, Eq. 1-3 (Sec. 3.1);
+ *   6. multiview-mipmap setup, Eq. 4-7 (Sec. 3.3);
+ *   7. one point per sampling-lattice cell overlapping the triangle;
+ *   8. tv_min / tv_max fetched from the mip chain at LOD_min / LOD_max (Sec. 3.3);
+ *   9. EPR splatting of every point into every view: the point's cell is
+ *      projected and only pixels inside both the cell and the triangle are
+ *      written, with a 64-bit depth|id minimum per view pixel (Sec. 3.2, Sec. 5.1);
+ *  10. per-view, per-splat texture interpolation, Eq. 8-9 (Sec. 3.3);
+ *  11. angular supersampling, reconstruction, crosstalk (Sec. 4);
+ *  12. lenticular interleave into the elemental image array (Sec. 4).
+ *
+ * Floating point: IEEE binary32 throughout, every fused multiply-add written
+ * as fmaf(), compiled with -ffp-contract=off so no other contraction happens.
+ * Where the paper leaves a choice open, the reading taken is stated at the
+ * step. The splat bounding box is computed in double with a one-pixel pad; it
+ * only limits which pixels are tested and never decides one.
+ *
+ * Parity pins (tests, not this file): closed-form point counts, brute-force
+ * ray casting (orc_raycast below, double precision), constant and
+ * checkerboard textures, log2 against the C library, interleave histograms.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* -------------------------------------------------------------------------- */
+/* Types                                                                       */
+/* -------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t n_views, view_w, view_h;
+    float cone_deg, view_dist, focal_w, focal_h, near_z, far_z, bias_h, bias_v;
+    int32_t panel_w, panel_h;
+    float lens_pitch_px, slant, phase_offset;
+    int32_t recon;
+    float crosstalk;
+} orc_display;
+
+/* Per-triangle record, written by orc_setup as ORC_TRI_FLOATS floats. */
+enum {
+    T_LIVE = 0,            /* 1 if the triangle emits points */
+    T_P0 = 1,              /* 3: transformed first vertex */
+    T_N = 4,               /* 3: unit normal */
+    T_EU = 7,              /* 3: horizontal sampling axis u-hat */
+    T_EV = 10,             /* 3: vertical sampling axis v-hat */
+    T_UMIN = 13, T_VMIN = 14,
+    T_A1 = 15, T_B1 = 16, T_A2 = 17, T_B2 = 18,   /* unshifted 2-D coords of v1, v2 */
+    T_U = 19,              /* 3: shifted 2-D u of v0, v1, v2 */
+    T_V = 22,              /* 3: shifted 2-D v */
+    T_AWS = 25, T_ATS = 26, T_NTEX = 27, T_SIZE_UV = 28,
+    T_DMIN = 29, T_DMAX = 30, T_SU = 31, T_SV = 32,
+    T_VPUV_MIN = 33, T_VPUV_MAX = 34, T_SPL_UV = 35,
+    T_LOD_MIN = 36, T_LOD_MAX = 37,
+    T_S0 = 38, T_SGU = 39, T_SGV = 40, T_T0 = 41, T_TGU = 42, T_TGV = 43,
+    T_TEX = 44, T_UMAX = 45, T_VMAX = 46,
+    ORC_TRI_FLOATS = 48
+};
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EOVERFLOW = 4 };
+
+/* Largest lattice index along either axis (cells are stored as u16 pairs). */
+#define ORC_MAX_CELL 65535
+
+/* -------------------------------------------------------------------------- */
+/* Small float helpers (each is the plain formula with its rounding spelled out) */
+/* -------------------------------------------------------------------------- */
+
+static float dot3(const float *a, const float *b) {
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+static void cross3(const float *a, const float *b, float *o) {
+    o[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
+    o[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
+    o[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
+}
+
+/* Signed doubled area of (p, r, q): the 2-D edge function of edge p->r at q. */
+static float edge2(float px, float py, float rx, float ry, float qx, float qy) {
+    return fmaf(rx - px, qy - py, -((ry - py) * (qx - px)));
+}
+
+/* Squared distance from q to segment p-r. */
+static float segd2(float px, float py, float rx, float ry, float qx, float qy) {
+    float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+    float ee = fmaf(ex, ex, ey * ey);
+    float t = ee > 0.0f ? fmaf(wx, ex, wy * ey) / ee : 0.0f;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    float dx = fmaf(-t, ex, wx), dy = fmaf(-t, ey, wy);
+    return fmaf(dx, dx, dy * dy);
+}
+
+static int inside3(float w0, float w1, float w2) {
+    return (w0 >= 0.0f && w1 >= 0.0f && w2 >= 0.0f) ||
+           (w0 <= 0.0f && w1 <= 0.0f && w2 <= 0.0f);
+}
+
+static uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static float bitsf(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+/*
+ * log2 for Eq. 6-7. Neither side has a correctly rounded library log2, so both
+ * write this one method: split x = m * 2^e from the bits, fold m into
+ * [sqrt(1/2), sqrt(2)], and take ln m = 2 atanh(z), z = (m-1)/(m+1), from the
+ * Taylor series of atanh truncated after z^9/9 (|z| < 0.172 so the first
+ * dropped term is below 2^-28); log2 x = e + ln m / ln 2.
+ */
+float orc_log2f(float x) {
+    if (isnan(x)) return x;
+    if (x <= 0.0f) return -INFINITY;
+    if (isinf(x)) return INFINITY;
+    int e;
+    uint32_t b = fbits(x);
+    if ((b >> 23) == 0) {               /* subnormal: scale into the normal range */
+        b = fbits(x * 16777216.0f);
+        e = (int)(b >> 23) - 127 - 24;
+    } else {
+        e = (int)(b >> 23) - 127;
+    }
+    float m = bitsf((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) { m = m * 0.5f; e += 1; }
+    float z = (m - 1.0f) / (m + 1.0f);
+    float z2 = z * z;
+    float p = fmaf(z2, (float)(1.0 / 9.0), (float)(1.0 / 7.0));
+    p = fmaf(z2, p, (float)(1.0 / 5.0));
+    p = fmaf(z2, p, (float)(1.0 / 3.0));
+    p = fmaf(z2, p, 1.0f);
+    float ln_m = (2.0f * z) * p;
+    return fmaf(ln_m, (float)(1.0 / 0.69314718055994530942), (float)e);
+}
+
+/* -------------------------------------------------------------------------- */
+/* Views (Sec. 3: views defined by the LFD; Sec. 4: angular supersampling)      */
+/* -------------------------------------------------------------------------- */
+
+int orc_n_render_views(const orc_display *d) {
+    return d->recon == 1 ? 2 * d->n_views : d->n_views;
+}
+
+/*
+ * Eye x positions. The N display views sit at the centres of N equal angular
+ * intervals of the viewing cone, on the line y = 0, z = D. Sec. 4 projects
+ * the splats into twice as many views placed randomly inside the view
+ * intervals; the reading taken here is deterministic: 2N views at
+ * half-interval steps, the even ones on the N display-view centres.
+ */
+void orc_eyes(const orc_display *d, float *ex) {
+    int nr = orc_n_render_views(d);
+    double cone = d->cone_deg, D = d->view_dist;
+    for (int k = 0; k < nr; k++) {
+        double deg = d->recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * d->n_views)
+                                   : -cone / 2.0 + cone * (k + 0.5) / d->n_views;
+        ex[k] = (float)(D * tan(deg * M_PI / 180.0));
+    }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Mip chain (Sec. 3.3 relies on the hardware mipmap; here: 2x2 box, rounded)   */
+/* -------------------------------------------------------------------------- */
+
+static int ilog2u(uint32_t v) { int l = 0; while ((1u << l) < v) l++; return l; }
+
+int orc_mip_levels(uint32_t w, uint32_t h) {
+    return ilog2u(w > h ? w : h) + 1;
+}
+
+size_t orc_mip_bytes(uint32_t w, uint32_t h) {
+    size_t n = 0;
+    int L = orc_mip_levels(w, h);
+    for (int l = 0; l < L; l++) {
+        uint32_t lw = w >> l ? w >> l : 1, lh = h >> l ? h >> l : 1;
+        n += (size_t)lw * lh * 4;
+    }
+    return n;
+}
+
+/* chain = level 0 followed by every coarser level, each row-major RGBA8.
+ * Texel (x, y) of level l+1 is the rounded mean (a+b+c+d+2)>>2 of texels
+ * (2x..2x+1, 2y..2y+1) of level l, indices clamped to the level. */
+void orc_build_mips(const uint8_t *level0, uint32_t w, uint32_t h, uint8_t *chain) {
+    memcpy(chain, level0, (size_t)w * h * 4);
+    int L = orc_mip_levels(w, h);
+    const uint8_t *src = chain;
+    uint32_t sw = w, sh = h;
+    uint8_t *dst = chain + (size_t)w * h * 4;
+    for (int l = 1; l < L; l++) {
+        uint32_t dw = sw > 1 ? sw / 2 : 1, dh = sh > 1 ? sh / 2 : 1;
+        for (uint32_t y = 0; y < dh; y++) {
+            uint32_t y0 = 2 * y < sh ? 2 * y : sh - 1, y1 = 2 * y + 1 < sh ? 2 * y + 1 : sh - 1;
+            for (uint32_t x = 0; x < dw; x++) {
+                uint32_t x0 = 2 * x < sw ? 2 * x : sw - 1, x1 = 2 * x + 1 < sw ? 2 * x + 1 : sw - 1;
+                for (int c = 0; c < 4; c++) {
+                    unsigned s = src[((size_t)y0 * sw + x0) * 4 + c] + src[((size_t)y0 * sw + x1) * 4 + c] +
+                                 src[((size_t)y1 * sw + x0) * 4 + c] + src[((size_t)y1 * sw + x1) * 4 + c];
+                    dst[((size_t)y * dw + x) * 4 + c] = (uint8_t)((s + 2) >> 2);
+                }
+            }
+        }
+        src = dst;
+        dst += (size_t)dw * dh * 4;
+        sw = dw;
+        sh = dh;
+    }
+}
+
+/* Bilinear sample of one level with wrap addressing; texel centres at (k+1/2)/w. */
+static void bilinear(const uint8_t *lvl, uint32_t w, uint32_t h, float s, float t, float out[4]) {
+    if (!isfinite(s)) s = 0.0f;
+    if (!isfinite(t)) t = 0.0f;
+    float fs = s - floorf(s), ft = t - floorf(t);
+    float x = fmaf(fs, (float)w, -0.5f), y = fmaf(ft, (float)h, -0.5f);
+    float xf = floorf(x), yf = floorf(y);
+    float fx = x - xf, fy = y - yf;
+    uint32_t ix0 = (uint32_t)(int)xf & (w - 1), iy0 = (uint32_t)(int)yf & (h - 1);
+    uint32_t ix1 = (ix0 + 1) & (w - 1), iy1 = (iy0 + 1) & (h - 1);
+    const uint8_t *t00 = lvl + ((size_t)iy0 * w + ix0) * 4, *t10 = lvl + ((size_t)iy0 * w + ix1) * 4;
+    const uint8_t *t01 = lvl + ((size_t)iy1 * w + ix0) * 4, *t11 = lvl + ((size_t)iy1 * w + ix1) * 4;
+    for (int c = 0; c < 4; c++) {
+        float a = t00[c], b = t10[c], cc = t01[c], dd = t11[c];
+        float top = fmaf(fx, b - a, a);
+        float bot = fmaf(fx, dd - cc, cc);
+        out[c] = fmaf(fy, bot - top, top);
+    }
+}
+
+static uint8_t to_u8(float v) {
+    float r = rintf(v);
+    if (!(r >= 0.0f)) r = 0.0f;
+    if (r > 255.0f) r = 255.0f;
+    return (uint8_t)r;
+}
+
+/* Trilinear fetch at a level of detail (Sec. 3.3, the tv_min / tv_max fetch):
+ * LOD clamped to [0, L_max], level floor(LOD), blended to the next level by
+ * the fraction, FP32 weights, then rounded half-to-even to RGBA8. */
+void orc_trilinear(const uint8_t *chain, uint32_t w, uint32_t h, float s, float t,
+                   float lod, uint8_t out[4]) {
+    int L = orc_mip_levels(w, h) - 1;
+    lod = fminf(fmaxf(lod, 0.0f), (float)L);
+    int l = (int)floorf(lod);
+    float f = lod - (float)l;
+    const uint8_t *p = chain;
+    for (int k = 0; k < l; k++) {
+        uint32_t lw = w >> k ? w >> k : 1, lh = h >> k ? h >> k : 1;
+        p += (size_t)lw * lh * 4;
+    }
+    uint32_t lw = w >> l ? w >> l : 1, lh = h >> l ? h >> l : 1;
+    float c0[4], c1[4];
+    bilinear(p, lw, lh, s, t, c0);
+    if (f > 0.0f && l < L) {
+        const uint8_t *q = p + (size_t)lw * lh * 4;
+        uint32_t nw = lw > 1 ? lw / 2 : 1, nh = lh > 1 ? lh / 2 : 1;
+        bilinear(q, nw, nh, s, t, c1);
+        for (int c = 0; c < 4; c++) out[c] = to_u8(fmaf(f, c1[c] - c0[c], c0[c]));
+    } else {
+        for (int c = 0; c < 4; c++) out[c] = to_u8(c0[c]);
+    }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Per-frame model transform                                                    */
+/* -------------------------------------------------------------------------- */
+
+void orc_transform(const float *m, const float *p, float *o) {
+    o[0] = fmaf(m[0], p[0], fmaf(m[1], p[1], fmaf(m[2], p[2], m[3])));
+    o[1] = fmaf(m[4], p[0], fmaf(m[5], p[1], fmaf(m[6], p[2], m[7])));
+    o[2] = fmaf(m[8], p[0], fmaf(m[9], p[1], fmaf(m[10], p[2], m[11])));
+}
+
+/* -------------------------------------------------------------------------- */
+/* Triangle setup: visibility, T_align frame, spacings, Eq. 1-7, point count    */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * Vertex visibility (Sec. 3): a triangle is dropped when, for every view, all
+ * three vertices lie outside one common plane of that view's frustum. The
+ * frustum of view k has apex E_k = (Ex_k, 0, D) and passes through the focal
+ * rectangle [-fw/2, fw/2] x [-fh/2, fh/2] at z = 0; near and far bound the
+ * depth D - z. Each plane is the linear form below, negative outside.
+ */
+static int culled(const orc_display *d, const float *ex, int nr, float P[3][3]) {
+    float D = d->view_dist, fw2 = 0.5f * d->focal_w, fh2 = 0.5f * d->focal_h;
+    int out_t = 1, out_b = 1, out_n = 1, out_f = 1;
+    for (int k = 0; k < 3; k++) {
+        float dep = D - P[k][2];
+        float top = fmaf(fh2, dep, -(P[k][1] * D));
+        float bot = fmaf(P[k][1], D, fh2 * dep);
+        out_t &= top < 0.0f;
+        out_b &= bot < 0.0f;
+        out_n &= dep - d->near_z < 0.0f;
+        out_f &= d->far_z - dep < 0.0f;
+    }
+    if (out_t || out_b || out_n || out_f) return 1;
+    for (int v = 0; v < nr; v++) {
+        float lx = -fw2 - ex[v], rx = fw2 - ex[v];
+        int out_l = 1, out_r = 1;
+        for (int k = 0; k < 3; k++) {
+            float dep = D - P[k][2];
+            float l = fmaf(P[k][0] - ex[v], D, -(lx * dep));
+            float r = fmaf(rx, dep, -((P[k][0] - ex[v]) * D));
+            out_l &= l < 0.0f;
+            out_r &= r < 0.0f;
+        }
+        if (!(out_l || out_r)) return 0;   /* visible in view v */
+    }
+    return 1;
+}
+
+/*
+ * Rows of lattice column i: the cells [i s_u, (i+1) s_u) x [j s_v, (j+1) s_v)
+ * of the triangle's shifted 2-D frame whose open interior overlaps the open
+ * triangle (reading of iVIR's rasterisation of the aligned triangle: the
+ * conservative rule, which makes the splat union hole-free). The triangle's v
+ * range over the column slab comes from the vertices inside the slab and the
+ * edges' crossings of its two borders.
+ */
+static int column_rows(const float *T, int i, int *j0, int *j1) {
+    float su = T[T_SU], sv = T[T_SV];
+    const float *U = T + T_U, *V = T + T_V;
+    float a = (float)i * su;
+    float b = fminf((float)(i + 1) * su, T[T_UMAX]);
+    float lo = INFINITY, hi = -INFINITY;
+    for (int k = 0; k < 3; k++) {
+        if (U[k] >= a && U[k] <= b) { lo = fminf(lo, V[k]); hi = fmaxf(hi, V[k]); }
+    }
+    static const int E[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    for (int e = 0; e < 3; e++) {
+        int p = E[e][0], r = E[e][1];
+        if (U[p] == U[r]) continue;
+        float xs[2] = {a, b};
+        for (int q = 0; q < 2; q++) {
+            float x = xs[q];
+            if (x >= fminf(U[p], U[r]) && x <= fmaxf(U[p], U[r])) {
+                float tt = (x - U[p]) / (U[r] - U[p]);
+                float vx = fmaf(tt, V[r] - V[p], V[p]);
+                lo = fminf(lo, vx);
+                hi = fmaxf(hi, vx);
+            }
+        }
+    }
+    if (lo > hi) { *j0 = 0; *j1 = 0; return 0; }
+    *j0 = (int)floorf(lo / sv);
+    *j1 = (int)ceilf(hi / sv);
+    if (*j1 < *j0) *j1 = *j0;
+    return *j1 - *j0;
+}
+
+static int n_columns(const float *T) {
+    return (int)ceilf(T[T_UMAX] / T[T_SU]);
+}
+
+/*
+ * orc_setup: steps 1-7 for every triangle. tri_out receives ORC_TRI_FLOATS
+ * floats per triangle, counts the number of points it emits. Returns ORC_OK,
+ * or ORC_EOVERFLOW if some triangle needs more than ORC_MAX_CELL lattice
+ * columns or rows (its count is then 0).
+ */
+int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
+              const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_tris,
+              const uint32_t *tex_wh, uint32_t n_tex, const float *model,
+              float *tri_out, uint32_t *counts) {
+    int nr = orc_n_render_views(d);
+    float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
+    orc_eyes(d, ex);
+    float D = d->view_dist;
+    /* pixel footprint per unit distance, horizontal and vertical */
+    float px = (float)((double)d->focal_w / ((double)d->view_dist * d->view_w));
+    float py = (float)((double)d->focal_h / ((double)d->view_dist * d->view_h));
+    int status = ORC_OK;
+    for (uint32_t t = 0; t < n_tris; t++) {
+        float *T = tri_out + (size_t)t * ORC_TRI_FLOATS;
+        memset(T, 0, sizeof(float) * ORC_TRI_FLOATS);
+        counts[t] = 0;
+        float P[3][3], Q[3][2];
+        for (int k = 0; k < 3; k++) {
+            uint32_t vi = idx[3 * (size_t)t + k];
+            orc_transform(model, xyz + 3 * (size_t)vi, P[k]);
+            Q[k][0] = uvs[2 * (size_t)vi];
+            Q[k][1] = uvs[2 * (size_t)vi + 1];
+        }
+        uint32_t tex = tri_tex[t] < n_tex ? tri_tex[t] : 0;
+        T[T_TEX] = (float)tex;
+        memcpy(T + T_P0, P[0], sizeof(float) * 3);
+        if (culled(d, ex, nr, P)) continue;
+
+        /* world-space area and unit normal */
+        float e1[3], e2[3], cr[3];
+        for (int c = 0; c < 3; c++) { e1[c] = P[1][c] - P[0][c]; e2[c] = P[2][c] - P[0][c]; }
+        cross3(e1, e2, cr);
+        float len = sqrtf(dot3(cr, cr));
+        if (!(len > 0.0f) || !isfinite(len)) continue;  /* zero-area: no points */
+        float n[3] = {cr[0] / len, cr[1] / len, cr[2] / len};
+        float A_ws = 0.5f * len;
+
+        /* T_align (Sec. 3.1): v-hat is world up projected into the plane (the
+         * views' shared vertical), u-hat = v-hat x n the horizontal. When the
+         * plane is nearly horizontal, world x projected gives u-hat instead. */
+        float eu[3], ev[3];
+        float vv[3] = {-(n[1] * n[0]), fmaf(-n[1], n[1], 1.0f), -(n[1] * n[2])};
+        float l2 = dot3(vv, vv);
+        if (l2 >= 1e-6f) {
+            float l = sqrtf(l2);
+            for (int c = 0; c < 3; c++) ev[c] = vv[c] / l;
+            cross3(ev, n, eu);
+        } else {
+            float uu[3] = {fmaf(-n[0], n[0], 1.0f), -(n[0] * n[1]), -(n[0] * n[2])};
+            float l = sqrtf(dot3(uu, uu));
+            for (int c = 0; c < 3; c++) eu[c] = uu[c] / l;
+            cross3(n, eu, ev);
+        }
+        memcpy(T + T_N, n, sizeof n);
+        memcpy(T + T_EU, eu, sizeof eu);
+        memcpy(T + T_EV, ev, sizeof ev);
+
+        /* 2-D vertex coordinates relative to P0, then shifted to the bbox min */
+        float a1 = dot3(e1, eu), b1 = dot3(e1, ev), a2 = dot3(e2, eu), b2 = dot3(e2, ev);
+        float umin = fminf(fminf(0.0f, a1), a2), vmin = fminf(fminf(0.0f, b1), b2);
+        float U[3] = {0.0f - umin, a1 - umin, a2 - umin};
+        float V[3] = {0.0f - vmin, b1 - vmin, b2 - vmin};
+        T[T_UMIN] = umin; T[T_VMIN] = vmin;
+        T[T_A1] = a1; T[T_B1] = b1; T[T_A2] = a2; T[T_B2] = b2;
+        memcpy(T + T_U, U, sizeof U);
+        memcpy(T + T_V, V, sizeof V);
+        T[T_UMAX] = fmaxf(fmaxf(U[0], U[1]), U[2]);
+        T[T_VMAX] = fmaxf(fmaxf(V[0], V[1]), V[2]);
+
+        /* closest and farthest eye over all views (Fig. 4: pixel edges are
+         * reverse-projected around the point of the triangle closest to the
+         * eye). The eye's distance to the triangle: its height over the plane
+         * and its in-plane distance to the 2-D triangle. */
+        float d2min = INFINITY, d2max = -INFINITY;
+        for (int v = 0; v < nr; v++) {
+            float q[3] = {ex[v] - P[0][0], 0.0f - P[0][1], D - P[0][2]};
+            float qu = dot3(q, eu), qv = dot3(q, ev), h = dot3(q, n);
+            float w0 = edge2(a1, b1, a2, b2, qu, qv);
+            float w1 = edge2(a2, b2, 0.0f, 0.0f, qu, qv);
+            float w2 = edge2(0.0f, 0.0f, a1, b1, qu, qv);
+            float d2 = 0.0f;
+            if (!inside3(w0, w1, w2))
+                d2 = fminf(fminf(segd2(0.0f, 0.0f, a1, b1, qu, qv), segd2(a1, b1, a2, b2, qu, qv)),
+                           segd2(a2, b2, 0.0f, 0.0f, qu, qv));
+            float dd = fmaf(h, h, d2);
+            d2min = fminf(d2min, dd);
+            d2max = fmaxf(d2max, dd);
+        }
+        /* the footprint is never taken closer than the near plane */
+        float dmin = fmaxf(sqrtf(d2min), d->near_z), dmax = fmaxf(sqrtf(d2max), d->near_z);
+        T[T_DMIN] = dmin; T[T_DMAX] = dmax;
+
+        /* LFD-biased spacings (Sec. 3.1): horizontal and vertical pixel edges
+         * reverse-projected at distance dmin, times the sampling bias. */
+        float su0 = (d->bias_h * dmin) * px, sv0 = (d->bias_v * dmin) * py;
+        float size_xy = su0 * sv0;
+
+        /* Eq. 1-2: texels spanned and world area per texel */
+        uint32_t X = tex_wh[2 * tex], Y = tex_wh[2 * tex + 1];
+        float ds1 = Q[1][0] - Q[0][0], dt1 = Q[1][1] - Q[0][1];
+        float ds2 = Q[2][0] - Q[0][0], dt2 = Q[2][1] - Q[0][1];
+        float A_ts = 0.5f * fabsf(fmaf(ds1, dt2, -(dt1 * ds2)));
+        float n_tex = (A_ts * (float)X) * (float)Y;
+        if (n_tex < 1.0f) n_tex = 1.0f;   /* a triangle spans at least one texel */
+        float size_uv = A_ws / n_tex;
+
+        /* Eq. 3: sampling density lowered to the texel density (S_ortho is a
+         * density, so spacings grow by sqrt(size_uv / size_xy)) */
+        float su = su0, sv = sv0;
+        if (size_uv > size_xy) {
+            float f = sqrtf(size_uv / size_xy);
+            su = su0 * f;
+            sv = sv0 * f;
+        }
+        T[T_AWS] = A_ws; T[T_ATS] = A_ts; T[T_NTEX] = n_tex; T[T_SIZE_UV] = size_uv;
+        T[T_SU] = su; T[T_SV] = sv;
+
+        /* Eq. 4-5: pixel area in texture space, min and max over views; the
+         * per-view pixel area is the reverse-projected (biased) pixel at d_v,
+         * monotone in d_v, so the extremes sit at dmin and dmax. */
+        float r = A_ts / A_ws;
+        float size_xy_max = ((d->bias_h * dmax) * px) * ((d->bias_v * dmax) * py);
+        float vpuv_min = size_xy * r, vpuv_max = size_xy_max * r;
+        T[T_VPUV_MIN] = vpuv_min; T[T_VPUV_MAX] = vpuv_max;
+        T[T_SPL_UV] = (su * sv) * r;   /* the splat's area in texture space (Eq. 8) */
+
+        /* Eq. 6-7 */
+        T[T_LOD_MIN] = 0.5f * orc_log2f((vpuv_min * (float)X) * (float)Y);
+        T[T_LOD_MAX] = 0.5f * orc_log2f((vpuv_max * (float)X) * (float)Y);
+
+        /* affine map from the shifted 2-D frame to texture coordinates */
+        float det = fmaf(a1, b2, -(a2 * b1));
+        float gsu = 0.0f, gsv = 0.0f, gtu = 0.0f, gtv = 0.0f;
+        if (det != 0.0f) {
+            gsu = fmaf(ds1, b2, -(ds2 * b1)) / det;
+            gsv = fmaf(ds2, a1, -(ds1 * a2)) / det;
+            gtu = fmaf(dt1, b2, -(dt2 * b1)) / det;
+            gtv = fmaf(dt2, a1, -(dt1 * a2)) / det;
+        }
+        T[T_SGU] = gsu; T[T_SGV] = gsv; T[T_TGU] = gtu; T[T_TGV] = gtv;
+        T[T_S0] = fmaf(gsu, umin, fmaf(gsv, vmin, Q[0][0]));
+        T[T_T0] = fmaf(gtu, umin, fmaf(gtv, vmin, Q[0][1]));
+
+        /* point count: one point per overlapped lattice cell */
+        float ncol = ceilf(T[T_UMAX] / su);
+        if (!(ncol <= (float)ORC_MAX_CELL)) { status = ORC_EOVERFLOW; continue; }
+        T[T_LIVE] = 1.0f;
+        int cols = (int)ncol;
+        uint32_t cnt = 0;
+        for (int i = 0; i < cols; i++) {
+            int j0, j1;
+            int rows = column_rows(T, i, &j0, &j1);
+            if (j1 > ORC_MAX_CELL + 1) { status = ORC_EOVERFLOW; cnt = 0; T[T_LIVE] = 0.0f; break; }
+            cnt += (uint32_t)rows;
+        }
+        counts[t] = cnt;
+    }
+    free(ex);
+    return status;
+}
+
+/*
+ * orc_emit: the point buffer. Points are numbered by triangle (exclusive
+ * prefix sum of counts), then column i, then row j. Each point is four u32:
+ * triangle id, i | j << 16, tv_min RGBA8, tv_max RGBA8 (the last two are
+ * filled by orc_fetch). Returns the number of points, or -1 if it exceeds cap.
+ */
+int64_t orc_emit(const float *tri, const uint32_t *counts, uint32_t n_tris,
+                 uint32_t *points, int64_t cap) {
+    int64_t total = 0;
+    for (uint32_t t = 0; t < n_tris; t++) total += counts[t];
+    if (total > cap) return -1;
+    int64_t p = 0;
+    for (uint32_t t = 0; t < n_tris; t++) {
+        if (counts[t] == 0) continue;
+        const float *T = tri + (size_t)t * ORC_TRI_FLOATS;
+        int cols = n_columns(T);
+        for (int i = 0; i < cols; i++) {
+            int j0, j1;
+            column_rows(T, i, &j0, &j1);
+            for (int j = j0; j < j1; j++) {
+                uint32_t *o = points + 4 * p;
+                o[0] = t;
+                o[1] = (uint32_t)i | ((uint32_t)j << 16);
+                o[2] = 0;
+                o[3] = 0;
+                p++;
+            }
+        }
+    }
+    return p;
+}
+
+/*
+ * orc_fetch: tv_min and tv_max of every point (Sec. 3.3): the texture
+ * coordinate of the cell centre, trilinear at LOD_min and at LOD_max.
+ */
+void orc_fetch(const float *tri, uint32_t *points, int64_t n_points,
+               const uint8_t *const *chains, const uint32_t *tex_wh) {
+    for (int64_t p = 0; p < n_points; p++) {
+        uint32_t *o = points + 4 * p;
+        const float *T = tri + (size_t)o[0] * ORC_TRI_FLOATS;
+        uint32_t i = o[1] & 0xffffu, j = o[1] >> 16;
+        float uc = ((float)i + 0.5f) * T[T_SU];
+        float vc = ((float)j + 0.5f) * T[T_SV];
+        float s = fmaf(T[T_SGU], uc, fmaf(T[T_SGV], vc, T[T_S0]));
+        float t = fmaf(T[T_TGU], uc, fmaf(T[T_TGV], vc, T[T_T0]));
+        uint32_t tex = (uint32_t)T[T_TEX];
+        uint32_t w = tex_wh[2 * tex], h = tex_wh[2 * tex + 1];
+        uint8_t a[4], b[4];
+        orc_trilinear(chains[tex], w, h, s, t, T[T_LOD_MIN], a);
+        orc_trilinear(chains[tex], w, h, s, t, T[T_LOD_MAX], b);
+        memcpy(&o[2], a, 4);
+        memcpy(&o[3], b, 4);
+    }
+}
+
+/* -------------------------------------------------------------------------- */
+/* Splatting (Sec. 3.2) and the per-view depth test (64-bit buffers, Sec. 5.1)  */
+/* -------------------------------------------------------------------------- */
+
+/* World position of lattice corner (a s_u, b s_v) of the triangle's frame. */
+static void cell_corner(const float *T, int a, int b, float o[3]) {
+    float cu = (float)a * T[T_SU] + T[T_UMIN];
+    float cv = (float)b * T[T_SV] + T[T_VMIN];
+    for (int c = 0; c < 3; c++)
+        o[c] = fmaf(cu, T[T_EU + c], fmaf(cv, T[T_EV + c], T[T_P0 + c]));
+}
+
+/*
+ * orc_splat: for every point and every listed view, each pixel whose centre
+ * ray hits the triangle's plane inside the point's cell and inside the
+ * triangle (EPR's inside-triangle test), at a depth within [near, far], gets
+ * key = float_bits(t) << 32 | point id, keeping the minimum. t is the ray
+ * parameter from the eye through the pixel centre on the focal plane, so on
+ * one pixel it orders hits like depth (= t D). keys holds n_list views of
+ * view_h x view_w u64, initialised here to all ones (empty).
+ */
+void orc_splat(const orc_display *d, const float *tri, const uint32_t *points,
+               int64_t n_points, const int32_t *views, int n_list, uint64_t *keys) {
+    int nr = orc_n_render_views(d);
+    float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
+    orc_eyes(d, ex);
+    int W = d->view_w, H = d->view_h;
+    float D = d->view_dist;
+    float pw = (float)((double)d->focal_w / W), ph = (float)((double)d->focal_h / H);
+    float x0 = -0.5f * d->focal_w, y0 = 0.5f * d->focal_h;
+    size_t npix = (size_t)W * H;
+    for (size_t k = 0; k < npix * (size_t)n_list; k++) keys[k] = ~0ull;
+    for (int64_t p = 0; p < n_points; p++) {
+        const uint32_t *pt = points + 4 * p;
+        const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
+        int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
+        float C[4][3];
+        cell_corner(T, i, j, C[0]);
+        cell_corner(T, i + 1, j, C[1]);
+        cell_corner(T, i + 1, j + 1, C[2]);
+        cell_corner(T, i, j + 1, C[3]);
+        const float *n = T + T_N, *eu = T + T_EU, *ev = T + T_EV, *P0 = T + T_P0;
+        float su = T[T_SU], sv = T[T_SV];
+        float ulo = (float)i * su, uhi = (float)(i + 1) * su;
+        float vlo = (float)j * sv, vhi = (float)(j + 1) * sv;
+        float a1 = T[T_A1], b1 = T[T_B1], a2 = T[T_A2], b2 = T[T_B2];
+        for (int li = 0; li < n_list; li++) {
+            int v = views[li];
+            float E[3] = {ex[v], 0.0f, D};
+            /* conservative pixel box of the projected cell, in double */
+            int bx0 = 0, bx1 = W - 1, by0 = 0, by1 = H - 1;
+            int behind = 0;
+            double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+            for (int c = 0; c < 4; c++) {
+                double dep = (double)D - C[c][2];
+                if (!(dep > 1e-9)) { behind = 1; break; }
+                double sx = E[0] + (C[c][0] - (double)E[0]) * D / dep;
+                double sy = C[c][1] * (double)D / dep;
+                double qx = (sx + 0.5 * d->focal_w) * W / d->focal_w;
+                double qy = (0.5 * d->focal_h - sy) * H / d->focal_h;
+                mnx = fmin(mnx, qx); mxx = fmax(mxx, qx);
+                mny = fmin(mny, qy); mxy = fmax(mxy, qy);
+            }
+            if (!behind) {
+                double fx0 = floor(mnx - 0.5) - 1, fx1 = ceil(mxx - 0.5) + 1;
+                double fy0 = floor(mny - 0.5) - 1, fy1 = ceil(mxy - 0.5) + 1;
+                if (fx1 < 0 || fy1 < 0 || fx0 > W - 1 || fy0 > H - 1) continue;
+                bx0 = fx0 < 0 ? 0 : (int)fx0;
+                bx1 = fx1 > W - 1 ? W - 1 : (int)fx1;
+                by0 = fy0 < 0 ? 0 : (int)fy0;
+                by1 = fy1 > H - 1 ? H - 1 : (int)fy1;
+            }
+            float qE[3] = {E[0] - P0[0], E[1] - P0[1], E[2] - P0[2]};
+            float num = -dot3(n, qE);
+            uint64_t *kv = keys + (size_t)li * npix;
+            for (int y = by0; y <= by1; y++) {
+                float Fy = fmaf((float)y + 0.5f, -ph, y0);
+                for (int x = bx0; x <= bx1; x++) {
+                    float Fx = fmaf((float)x + 0.5f, pw, x0);
+                    float dir[3] = {Fx - E[0], Fy - E[1], -D};
+                    float den = dot3(n, dir);
+                    if (den == 0.0f) continue;
+                    float t = num / den;
+                    float depth = t * D;
+                    if (!(depth >= d->near_z && depth <= d->far_z)) continue;
+                    float h[3] = {fmaf(t, dir[0], qE[0]), fmaf(t, dir[1], qE[1]), fmaf(t, dir[2], qE[2])};
+                    float uq = dot3(h, eu), vq = dot3(h, ev);
+                    float u = uq - T[T_UMIN], vv = vq - T[T_VMIN];
+                    if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) continue;
+                    float w0 = edge2(a1, b1, a2, b2, uq, vq);
+                    float w1 = edge2(a2, b2, 0.0f, 0.0f, uq, vq);
+                    float w2 = edge2(0.0f, 0.0f, a1, b1, uq, vq);
+                    if (!inside3(w0, w1, w2)) continue;
+                    uint64_t key = ((uint64_t)fbits(t) << 32) | (uint64_t)(uint32_t)p;
+                    size_t o = (size_t)y * W + x;
+                    if (key < kv[o]) kv[o] = key;
+                }
+            }
+        }
+    }
+    free(ex);
+}
+
+/*
+ * orc_splat_hits: how many (point) splats pass every test at each pixel of the
+ * listed views, without the depth minimum. On a single-triangle scene this is
+ * 1 on the triangle's pixels and 0 elsewhere when the lattice cells tile the
+ * triangle exactly once (the half-open cells of the conservative rule).
+ */
+void orc_splat_hits(const orc_display *d, const float *tri, const uint32_t *points,
+                    int64_t n_points, const int32_t *views, int n_list, uint32_t *hits) {
+    int W = d->view_w, H = d->view_h;
+    size_t npix = (size_t)W * H;
+    uint64_t *one = (uint64_t *)malloc(sizeof(uint64_t) * npix);
+    for (size_t k = 0; k < npix * (size_t)n_list; k++) hits[k] = 0;
+    for (int64_t p = 0; p < n_points; p++) {
+        for (int li = 0; li < n_list; li++) {
+            orc_splat(d, tri, points + 4 * p, 1, views + li, 1, one);
+            for (size_t o = 0; o < npix; o++) hits[(size_t)li * npix + o] += one[o] != ~0ull;
+        }
+    }
+    free(one);
+}
+
+/* -------------------------------------------------------------------------- */
+/* Per-view texture interpolation, Eq. 8-9, and shading (unlit: colour = tv)    */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * orc_resolve: per listed view and pixel, the winning point's colour. The
+ * splat's pixel area is the shoelace area of its cell's four corners
+ * projected into the view (= size_ndc * 0.25 * X_v * Y_v of Eq. 8). Eq. 8
+ * grows the splat's texture area when it covers less than a pixel and clamps
+ * it to [size_vpuv_min, size_vpuv_max]; Eq. 9 interpolates tv between tv_min
+ * and tv_max per channel. Empty pixels are (0, 0, 0, 0).
+ */
+void orc_resolve(const orc_display *d, const float *tri, const uint32_t *points,
+                 const uint64_t *keys, const int32_t *views, int n_list, uint8_t *rgba) {
+    int nr = orc_n_render_views(d);
+    float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
+    orc_eyes(d, ex);
+    int W = d->view_w, H = d->view_h;
+    float D = d->view_dist;
+    float pw = (float)((double)d->focal_w / W), ph = (float)((double)d->focal_h / H);
+    float ipw = (float)((double)W / d->focal_w), iph = (float)((double)H / d->focal_h);
+    float x0 = -0.5f * d->focal_w, y0 = 0.5f * d->focal_h;
+    (void)pw; (void)ph;
+    size_t npix = (size_t)W * H;
+    for (int li = 0; li < n_list; li++) {
+        float Ex = ex[views[li]];
+        for (size_t o = 0; o < npix; o++) {
+            uint64_t key = keys[(size_t)li * npix + o];
+            uint8_t *out = rgba + ((size_t)li * npix + o) * 4;
+            if (key == ~0ull) { out[0] = out[1] = out[2] = out[3] = 0; continue; }
+            const uint32_t *pt = points + 4 * (size_t)(uint32_t)key;
+            const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
+            int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
+            float C[4][3], X[4], Y[4];
+            cell_corner(T, i, j, C[0]);
+            cell_corner(T, i + 1, j, C[1]);
+            cell_corner(T, i + 1, j + 1, C[2]);
+            cell_corner(T, i, j + 1, C[3]);
+            for (int c = 0; c < 4; c++) {
+                float s = D / (D - C[c][2]);
+                float sx = fmaf(C[c][0] - Ex, s, Ex);
+                float sy = C[c][1] * s;
+                X[c] = (sx - x0) * ipw;
+                Y[c] = (y0 - sy) * iph;
+            }
+            float acc = 0.0f;
+            for (int c = 0; c < 4; c++) {
+                int c1 = (c + 1) & 3;
+                acc = acc + fmaf(X[c], Y[c1], -(X[c1] * Y[c]));
+            }
+            float area_px = 0.5f * fabsf(acc);
+            float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
+            float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
+            float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
+            float w = vmax > vmin ? (size_vs - vmin) / (vmax - vmin) : 0.0f;
+            const uint8_t *tmin = (const uint8_t *)&pt[2], *tmax = (const uint8_t *)&pt[3];
+            for (int c = 0; c < 4; c++) {
+                float a = tmin[c], b = tmax[c];
+                out[c] = to_u8(fmaf(w, b - a, a));
+            }
+        }
+    }
+    free(ex);
+}
+
+/* -------------------------------------------------------------------------- */
+/* Reconstruction, crosstalk and interleave (Sec. 4)                           */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * orc_display_views: the N views the panel shows, as floats (RGBA, 0..255).
+ * With angular supersampling (recon = 1) view k is the [1/4, 1/2, 1/4] tent
+ * over rendered views 2k-1, 2k, 2k+1, renormalised over the taps that exist.
+ * With crosstalk x > 0 each view then becomes (1-2x) own + x each neighbour,
+ * neighbour indices wrapping (the lens phase is cyclic).
+ */
+void orc_display_views(const orc_display *d, const uint8_t *rendered, float *out) {
+    int N = d->n_views, nr = orc_n_render_views(d);
+    size_t npix = (size_t)d->view_w * d->view_h;
+    size_t nval = npix * 4;
+    float *o = (float *)malloc(sizeof(float) * nval * (size_t)N);
+    for (int k = 0; k < N; k++) {
+        for (size_t e = 0; e < nval; e++) {
+            if (d->recon == 1) {
+                static const float w[3] = {0.25f, 0.5f, 0.25f};
+                float acc = 0.0f, ws = 0.0f;
+                for (int q = 0; q < 3; q++) {
+                    int m = 2 * k - 1 + q;
+                    if (m < 0 || m >= nr) continue;
+                    acc = fmaf(w[q], (float)rendered[(size_t)m * nval + e], acc);
+                    ws += w[q];
+                }
+                o[(size_t)k * nval + e] = acc / ws;
+            } else {
+                o[(size_t)k * nval + e] = (float)rendered[(size_t)k * nval + e];
+            }
+        }
+    }
+    if (d->crosstalk > 0.0f) {
+        float x = d->crosstalk, c0 = (float)(1.0 - 2.0 * (double)d->crosstalk);
+        for (int k = 0; k < N; k++) {
+            int km = (k + N - 1) % N, kp = (k + 1) % N;
+            for (size_t e = 0; e < nval; e++) {
+                float acc = o[(size_t)k * nval + e] * c0;
+                acc = fmaf(x, o[(size_t)km * nval + e], acc);
+                acc = fmaf(x, o[(size_t)kp * nval + e], acc);
+                out[(size_t)k * nval + e] = acc;
+            }
+        }
+    } else {
+        memcpy(out, o, sizeof(float) * nval * (size_t)N);
+    }
+    free(o);
+}
+
+/* Subpixel phase -> view index under the slanted lenticular lens (reading of
+ * the interleave of Sec. 4: a van Berkel-style slanted-lens phase taken at the
+ * subpixel's centre, x + (c + 1/2)/3 for colour channel c of pixel x). */
+int orc_view_of_subpixel(const orc_display *d, int x, int y, int c) {
+    static const float third[3] = {(float)(1.0 / 6.0), 0.5f, (float)(5.0 / 6.0)};
+    float inv_pitch = (float)(1.0 / (double)d->lens_pitch_px);
+    float cx = (float)x + third[c];
+    float a = fmaf(d->slant, (float)y, cx);
+    float ph = fmaf(a, inv_pitch, d->phase_offset);
+    float fr = ph - floorf(ph);
+    int k = (int)(fr * (float)d->n_views);
+    if (k >= d->n_views) k = d->n_views - 1;
+    if (k < 0) k = 0;
+    return k;
+}
+
+/*
+ * orc_interleave: the elemental image array. Panel subpixel (x, y, c) shows
+ * channel c of display view orc_view_of_subpixel(x, y, c) at the nearest view
+ * texel (floor((x+1/2) W / W_p), floor((y+1/2) H / H_p)); alpha is 255.
+ */
+void orc_interleave(const orc_display *d, const uint8_t *rendered, uint8_t *panel) {
+    int N = d->n_views, W = d->view_w, H = d->view_h, Wp = d->panel_w, Hp = d->panel_h;
+    size_t npix = (size_t)W * H;
+    float *dv = (float *)malloc(sizeof(float) * npix * 4 * (size_t)N);
+    orc_display_views(d, rendered, dv);
+    for (int y = 0; y < Hp; y++) {
+        int sy = (int)(((int64_t)(2 * y + 1) * H) / (2 * (int64_t)Hp));
+        for (int x = 0; x < Wp; x++) {
+            int sx = (int)(((int64_t)(2 * x + 1) * W) / (2 * (int64_t)Wp));
+            uint8_t *o = panel + ((size_t)y * Wp + x) * 4;
+            for (int c = 0; c < 3; c++) {
+                int k = orc_view_of_subpixel(d, x, y, c);
+                o[c] = to_u8(dv[((size_t)k * npix + (size_t)sy * W + sx) * 4 + c]);
+            }
+            o[3] = 255;
+        }
+    }
+    free(dv);
+}
+
+/* -------------------------------------------------------------------------- */
+/* Brute-force ray caster (double precision): the pin for the splat step      */
+/* -------------------------------------------------------------------------- */
+
+/*
+ * orc_raycast: the triangle nearest along the centre ray of pixel (x, y) of
+ * rendered view v, over all triangles (transformed vertices txyz, 9 floats per
+ * triangle), within [near, far] depth; Moller-Trumbore in double. Returns the
+ * triangle id or -1, and the ray parameter in *t_out.
+ */
+int32_t orc_raycast(const orc_display *d, const float *txyz, uint32_t n_tris,
+                    int v, int x, int y, double *t_out) {
+    int nr = orc_n_render_views(d);
+    float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
+    orc_eyes(d, ex);
+    double D = d->view_dist;
+    double E[3] = {ex[v], 0.0, D};
+    free(ex);
+    double Fx = -0.5 * d->focal_w + (x + 0.5) * d->focal_w / d->view_w;
+    double Fy = 0.5 * d->focal_h - (y + 0.5) * d->focal_h / d->view_h;
+    double dir[3] = {Fx - E[0], Fy - E[1], -D};
+    double best = INFINITY;
+    int32_t hit = -1;
+    for (uint32_t t = 0; t < n_tris; t++) {
+        const float *p = txyz + 9 * (size_t)t;
+        double a[3] = {p[0], p[1], p[2]}, e1[3], e2[3], s[3], pv[3], qv[3];
+        for (int c = 0; c < 3; c++) { e1[c] = p[3 + c] - a[c]; e2[c] = p[6 + c] - a[c]; s[c] = E[c] - a[c]; }
+        pv[0] = dir[1] * e2[2] - dir[2] * e2[1];
+        pv[1] = dir[2] * e2[0] - dir[0] * e2[2];
+        pv[2] = dir[0] * e2[1] - dir[1] * e2[0];
+        double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+        if (fabs(det) < 1e-30) continue;
+        double inv = 1.0 / det;
+        double bu = (s[0] * pv[0] + s[1] * pv[1] + s[2] * pv[2]) * inv;
+        if (bu < 0.0 || bu > 1.0) continue;
+        qv[0] = s[1] * e1[2] - s[2] * e1[1];
+        qv[1] = s[2] * e1[0] - s[0] * e1[2];
+        qv[2] = s[0] * e1[1] - s[1] * e1[0];
+        double bv = (dir[0] * qv[0] + dir[1] * qv[1] + dir[2] * qv[2]) * inv;
+        if (bv < 0.0 || bu + bv > 1.0) continue;
+        double tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+        double depth = tt * D;
+        if (depth < d->near_z || depth > d->far_z) continue;
+        if (tt < best) { best = tt; hit = (int32_t)t; }
+    }
+    *t_out = best;
+    return hit;
+}

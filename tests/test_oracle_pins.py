@@ -1,0 +1,584 @@
+"""Pins of the CPU oracle against facts fixed outside it: closed-form point
+counts, a double-precision brute-force ray caster, textbook special cases of
+the mip/filtering and interleave steps, and the invariants the paper's method
+implies. A plausible slip anywhere in the oracle (a dropped term, a wrong sign,
+a transposed operand) fails at least one of these."""
+import math
+import os
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_19901_gb300 import scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def unit_display(**kw) -> S.Display:
+    """One eye at (0, 0, 4) over a 2 x 2 focal rectangle, 128 x 128 pixels:
+    a pixel reverse-projects to exactly 2^-6 at distance 4."""
+    base = dict(n_views=1, view_w=128, view_h=128, cone_deg=30.0, view_dist=4.0,
+                focal_w=2.0, focal_h=2.0, near_z=0.1, far_z=100.0, bias_h=1.0,
+                bias_v=1.0, panel_w=64, panel_h=64, lens_pitch_px=8.0, slant=0.0)
+    base.update(kw)
+    return S.Display(**base)
+
+
+def tri_scene(tris, uvs=None, tex=None) -> S.Scene:
+    tris = np.asarray(tris, np.float32).reshape(-1, 3, 3)
+    n = len(tris)
+    uv = np.tile(np.array([[0, 0], [1, 0], [0, 1]], np.float32), (n, 1)) if uvs is None \
+        else np.asarray(uvs, np.float32).reshape(-1, 2)
+    textures = [tex if tex is not None else np.full((4, 4, 4), 200, np.uint8)]
+    return S.Scene(xyz=tris.reshape(-1, 3), uv=uv,
+                   idx=np.arange(3 * n, dtype=np.uint32).reshape(n, 3),
+                   tri_tex=np.zeros(n, np.uint32), textures=textures)
+
+
+I4 = np.eye(4, dtype=np.float32)
+
+
+# ---------------------------------------------------------------------------
+# log2 (Eq. 6-7)
+# ---------------------------------------------------------------------------
+
+def test_log2_powers_of_two_exact():
+    for e in range(-149, 128):
+        assert O.log2f(math.ldexp(1.0, e)) == float(e)
+
+
+def test_log2_error_bound_against_exact():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.uniform(0.5, 2.0, 4000), 10.0 ** rng.uniform(-44, 38, 4000)]).astype(np.float32)
+    worst = 0.0
+    for x in xs:
+        got = O.log2f(float(x))
+        exact = math.log2(float(x))
+        ulp = np.spacing(np.float32(abs(exact))) if exact != 0 else np.float32(2 ** -149)
+        worst = max(worst, abs(got - exact) / float(ulp))
+    assert worst <= 4.0, worst
+
+
+def test_log2_monotone_on_a_sweep():
+    xs = np.float32(1.0) * np.arange(1, 20001, dtype=np.float32) / np.float32(997.0)
+    ys = [O.log2f(float(x)) for x in xs]
+    assert all(b >= a for a, b in zip(ys, ys[1:]))
+
+
+def test_log2_special_values():
+    assert O.log2f(0.0) == -math.inf
+    assert O.log2f(math.inf) == math.inf
+    assert math.isnan(O.log2f(math.nan))
+
+
+# ---------------------------------------------------------------------------
+# Views
+# ---------------------------------------------------------------------------
+
+def test_single_view_on_axis_and_views_symmetric():
+    assert O.eyes(unit_display())[0] == 0.0
+    ex = O.eyes(S.display_paper())
+    assert np.allclose(ex, -ex[::-1], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("d", [S.display_tiny(), S.display_paper(), S.display_angular_ss()])
+def test_view_angles_evenly_spaced(d):
+    ex = O.eyes(d).astype(np.float64)
+    ang = np.degrees(np.arctan(ex / d.view_dist))
+    step = d.cone_deg / d.n_render_views
+    assert np.allclose(np.diff(ang), step, atol=1e-4)
+    if d.recon == 1:   # even supersampled views sit on the display-view centres
+        centres = -d.cone_deg / 2 + d.cone_deg * (np.arange(d.n_views) + 0.5) / d.n_views
+        assert np.allclose(ang[0::2], centres, atol=1e-4)
+    else:
+        assert abs(ang[0] + d.cone_deg / 2 - step / 2) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Sampling: closed-form point counts (Sec. 3.1, Eq. 1-3)
+# ---------------------------------------------------------------------------
+
+def _golden_counts():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "point_counts.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        f = line.split()
+        rows.append(([float(v) for v in f[:6]], float(f[6]), float(f[7]), int(f[8]), int(f[9]), int(f[10])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_counts())
+def test_closed_form_point_counts(row):
+    verts2, bh, bv, tw, th, expected = row
+    s = 2.0 ** -6
+    tri = [[verts2[0] * s, verts2[1] * s, 0], [verts2[2] * s, verts2[3] * s, 0],
+           [verts2[4] * s, verts2[5] * s, 0]]
+    d = unit_display(bias_h=bh, bias_v=bv)
+    st, rec, counts = O.setup(d, tri_scene(tri), I4, tex_wh=[tw, th])
+    assert st == 0
+    assert rec[0, O.F["d_min"]] == 4.0
+    assert int(counts[0]) == expected
+
+
+def test_point_set_of_right_triangle_is_the_staircase():
+    s = 2.0 ** -6
+    m = 8
+    d = unit_display()
+    st, rec, counts = O.setup(d, tri_scene([[0, 0, 0], [m * s, 0, 0], [0, m * s, 0]]), I4, tex_wh=[4096, 4096])
+    pts = O.emit(rec, counts)
+    got = [(int(p[1]) & 0xFFFF, int(p[1]) >> 16) for p in pts]
+    want = [(i, j) for i in range(m) for j in range(m - i)]
+    assert got == want                           # order: column, then row
+    assert rec[0, O.F["s_u"]] == s and rec[0, O.F["s_v"]] == s
+
+
+def test_square_two_triangles_share_only_the_diagonal():
+    s = 2.0 ** -6
+    m = 8
+    d = unit_display()
+    a = [[0, 0, 0], [m * s, 0, 0], [m * s, m * s, 0]]
+    b = [[0, 0, 0], [m * s, m * s, 0], [0, m * s, 0]]
+    st, rec, counts = O.setup(d, tri_scene(a + b), I4, tex_wh=[4096, 4096])
+    pts = O.emit(rec, counts)
+    cells = [set(), set()]
+    for p in pts:
+        cells[int(p[0])].add((int(p[1]) & 0xFFFF, int(p[1]) >> 16))
+    assert len(cells[0] | cells[1]) == m * m
+    assert cells[0] & cells[1] == {(i, i) for i in range(m)}
+
+
+def test_texture_limit_never_adds_points_and_matches_texel_area():
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    m = S.model_matrix(0)
+    _, rec_big, c_big = O.setup(d, sc, m, tex_wh=[1 << 14, 1 << 14])
+    _, rec_tex, c_tex = O.setup(d, sc, m, tex_wh=[16, 16])
+    assert c_tex.sum() < c_big.sum()
+    limited = rec_tex[:, O.F["size_uv"]] > rec_tex[:, O.F["s_u"]] * 0 + rec_big[:, O.F["s_u"]] * rec_big[:, O.F["s_v"]]
+    assert limited.any()
+    # Eq. 3: where the texture limits, the cell area equals the world area per texel
+    area = rec_tex[limited, O.F["s_u"]].astype(np.float64) * rec_tex[limited, O.F["s_v"]]
+    assert np.allclose(area, rec_tex[limited, O.F["size_uv"]], rtol=1e-5)
+    # horizontal:vertical spacing ratio stays the LFD bias
+    ratio = rec_tex[:, O.F["s_u"]] / rec_tex[:, O.F["s_v"]]
+    live = rec_tex[:, O.F["live"]] == 1
+    assert np.allclose(ratio[live], d.bias_h / d.bias_v, rtol=1e-5)
+
+
+def test_every_live_triangle_emits_and_counts_sum_to_points():
+    d = S.display_tiny()
+    fr = O.render(d, S.scene_tiny(), S.model_matrix(5), splat=False)
+    live = fr.tri[:, O.F["live"]] == 1
+    assert np.all(fr.counts[live] >= 1) and np.all(fr.counts[~live] == 0)
+    assert len(fr.points) == int(fr.counts.sum())
+    # points are grouped by triangle in ascending order
+    assert np.all(np.diff(fr.points[:, 0].astype(np.int64)) >= 0)
+
+
+def test_dmin_is_distance_to_closest_point_double_check():
+    """d_min against a dense double-precision sampling of the triangle."""
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    m = S.model_matrix(2)
+    _, rec, _ = O.setup(d, sc, m)
+    tx = O.transformed_tris(sc, m).astype(np.float64).reshape(-1, 3, 3)
+    ex = O.eyes(d).astype(np.float64)
+    E = np.stack([ex, np.zeros_like(ex), np.full_like(ex, d.view_dist)], 1)
+    g = np.linspace(0, 1, 61)
+    a, b = np.meshgrid(g, g)
+    keep = a + b <= 1
+    a, b = a[keep], b[keep]
+    for t in range(0, sc.n_tris, 97):
+        P = tx[t]
+        pts = P[0] + a[:, None] * (P[1] - P[0]) + b[:, None] * (P[2] - P[0])
+        dist = np.sqrt(((pts[None, :, :] - E[:, None, :]) ** 2).sum(-1)).min()
+        got = float(rec[t, O.F["d_min"]])
+        edge = max(np.linalg.norm(P[1] - P[0]), np.linalg.norm(P[2] - P[0]))
+        assert got <= dist + 1e-5
+        assert got >= dist - edge / 60 - 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Visibility (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def test_culling_cases():
+    d = S.display_tiny()
+    left = [[-50, 0, 0], [-49, 0, 0], [-50, 1, 0]]
+    behind = [[0, 0, 10], [1, 0, 10], [0, 1, 10]]
+    centre = [[0, 0, 0], [0.1, 0, 0], [0, 0.1, 0]]
+    # right of every frustum at z = 0 except the rightmost view's
+    ex = O.eyes(d)
+    fw2 = d.focal_w / 2
+    z = -2.0
+    x_edge_last = ex[-1] + (fw2 - ex[-1]) * (d.view_dist - z) / d.view_dist
+    x_edge_prev = ex[-2] + (fw2 - ex[-2]) * (d.view_dist - z) / d.view_dist
+    xm = 0.5 * (x_edge_last + x_edge_prev)
+    only_last = [[xm, 0, z], [xm + 0.001, 0, z], [xm, 0.001, z]]
+    _, rec, counts = O.setup(d, tri_scene(left + behind + centre + only_last), I4)
+    assert list(rec[:, O.F["live"]]) == [0, 0, 1, 1]
+
+
+# ---------------------------------------------------------------------------
+# Splatting (Sec. 3.2) against brute-force ray casting
+# ---------------------------------------------------------------------------
+
+def _boundary(ids):
+    b = np.zeros(ids.shape, bool)
+    b[1:, :] |= ids[1:, :] != ids[:-1, :]
+    b[:-1, :] |= ids[1:, :] != ids[:-1, :]
+    b[:, 1:] |= ids[:, 1:] != ids[:, :-1]
+    b[:, :-1] |= ids[:, 1:] != ids[:, :-1]
+    return b
+
+
+def test_splat_winner_is_raycast_nearest_triangle():
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    m = S.model_matrix(7)
+    views = [0, 7]
+    fr = O.render(d, sc, m, views=views, panel=False)
+    tx = O.transformed_tris(sc, m)
+    total = agree = 0
+    for li, v in enumerate(views):
+        rc = np.full((d.view_h, d.view_w), -1, np.int64)
+        for y in range(d.view_h):
+            for x in range(d.view_w):
+                rc[y, x] = O.raycast(d, tx, v, x, y)[0]
+        k = fr.keys[li]
+        win = np.where(k == EMPTY, -1, fr.points[(k & np.uint64(0xFFFFFFFF)).astype(np.int64) % max(len(fr.points), 1), 0].astype(np.int64))
+        win[k == EMPTY] = -1
+        same = win == rc
+        total += same.size
+        agree += same.sum()
+        # every disagreement sits on a triangle boundary of the ray-cast image
+        assert np.all(_boundary(rc)[~same])
+    assert agree / total >= 0.999
+
+
+def test_single_triangle_each_pixel_filled_exactly_once():
+    """Cells are half-open and tile the triangle: on the triangle's pixels
+    exactly one of its points passes the tests, elsewhere none (up to pixel
+    centres on the triangle's own outline)."""
+    d = replace(S.display_tiny(), view_w=64, view_h=64)
+    tri = [[-0.6, -0.5, 0.3], [0.7, -0.3, -0.4], [-0.1, 0.6, 0.1]]
+    sc = tri_scene(tri, uvs=[[0, 0], [3, 0], [0, 3]], tex=np.full((64, 64, 4), 9, np.uint8))
+    m = S.model_matrix(0)
+    st, rec, counts = O.setup(d, sc, m)
+    pts = O.emit(rec, counts)
+    assert len(pts) > 50
+    views = [0, 3, 7]
+    hits = O.splat_hits(d, rec, pts, views)
+    tx = O.transformed_tris(sc, m)
+    assert hits.max() == 1
+    for li, v in enumerate(views):
+        cov = np.array([[O.raycast(d, tx, v, x, y)[0] >= 0 for x in range(d.view_w)] for y in range(d.view_h)])
+        diff = (hits[li] == 1) != cov
+        assert np.all(_boundary(cov.astype(np.int64))[diff])
+        assert diff.sum() <= 2
+
+
+def test_screen_parallel_square_is_an_exact_raster():
+    d = unit_display(view_w=64, view_h=64)
+    px = 2.0 / 64
+    x0, x1, y0, y1 = -1 + 10 * px, -1 + 30 * px, 1 - 40 * px, 1 - 22 * px
+    a = [[x0, y0, 0], [x1, y0, 0], [x1, y1, 0]]
+    b = [[x0, y0, 0], [x1, y1, 0], [x0, y1, 0]]
+    fr = O.render(d, tri_scene(a + b), I4, panel=False)
+    cov = fr.keys[0] != EMPTY
+    want = np.zeros_like(cov)
+    want[22:40, 10:30] = True            # rows from the top: y in (1 - 40px, 1 - 22px)
+    assert np.array_equal(cov, want)
+    # the depth is the focal plane: t = 1 exactly
+    t = (fr.keys[0][cov] >> np.uint64(32)).astype(np.uint32).view(np.float32)
+    assert np.all(t == 1.0)
+
+
+def test_nearest_surface_invariant_two_layers():
+    """Two parallel squares: the nearer one wins every pixel it covers."""
+    d = replace(S.display_tiny(), view_w=48, view_h=48)
+    far_sq = [[[-0.5, -0.5, -0.5], [0.5, -0.5, -0.5], [0.5, 0.5, -0.5]], [[-0.5, -0.5, -0.5], [0.5, 0.5, -0.5], [-0.5, 0.5, -0.5]]]
+    near_sq = [[[-0.2, -0.2, 0.5], [0.2, -0.2, 0.5], [0.2, 0.2, 0.5]], [[-0.2, -0.2, 0.5], [0.2, 0.2, 0.5], [-0.2, 0.2, 0.5]]]
+    sc = tri_scene(far_sq + near_sq)
+    fr = O.render(d, sc, I4, panel=False)
+    tx = O.transformed_tris(sc, I4)
+    for li in range(d.n_views):
+        k = fr.keys[li]
+        win = np.where(k == EMPTY, -1, fr.points[(k & np.uint64(0xFFFFFFFF)).astype(np.int64) % len(fr.points), 0].astype(np.int64))
+        for y in range(0, d.view_h, 3):
+            for x in range(0, d.view_w, 3):
+                tri, t = O.raycast(d, tx, li, x, y)
+                if tri >= 2 and not _boundary(win)[y, x]:
+                    assert win[y, x] in (2, 3)
+
+
+# ---------------------------------------------------------------------------
+# Mip chain and filtered fetch (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def test_mip_chain_sizes():
+    assert O.lib().orc_mip_bytes(256, 256) == 4 * 87381
+    assert O.lib().orc_mip_levels(8, 2) == 4
+    assert O.lib().orc_mip_bytes(8, 2) == 4 * (16 + 4 + 2 + 1)
+
+
+def test_checkerboard_mips_to_exact_mid_grey():
+    t = np.zeros((8, 8, 4), np.uint8)
+    t[(np.add.outer(np.arange(8), np.arange(8)) % 2) == 1] = 255
+    lv = O.mip_levels(O.mip_chain(t), 8, 8)
+    for l in lv[1:]:
+        assert np.all(l == 128)     # (0 + 255 + 0 + 255 + 2) >> 2
+
+
+def test_constant_texture_fetches_constant_everywhere():
+    t = np.empty((32, 16, 4), np.uint8)
+    t[:] = (17, 99, 201, 255)
+    ch = O.mip_chain(t)
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        s, tt = rng.uniform(-5, 5, 2)
+        lod = rng.uniform(-2, 9)
+        assert list(O.trilinear(ch, 16, 32, s, tt, lod)) == [17, 99, 201, 255]
+
+
+def test_bilinear_texel_centres_midpoints_and_wrap():
+    rng = np.random.default_rng(2)
+    t = rng.integers(0, 256, (8, 8, 4), dtype=np.uint8)
+    ch = O.mip_chain(t)
+    for y in range(8):
+        for x in range(8):
+            assert np.array_equal(O.trilinear(ch, 8, 8, (x + 0.5) / 8, (y + 0.5) / 8, 0.0), t[y, x])
+            assert np.array_equal(O.trilinear(ch, 8, 8, (x + 0.5) / 8 + 3, (y + 0.5) / 8 - 2, 0.0), t[y, x])
+    # halfway between texels (x-1, y) and (x, y): mean, rounded half to even
+    for y in range(8):
+        for x in range(8):
+            a = t[y, x - 1].astype(np.float64)
+            b = t[y, x].astype(np.float64)
+            want = np.round((a + b) / 2)            # numpy rounds half to even
+            got = O.trilinear(ch, 8, 8, x / 8, (y + 0.5) / 8, 0.0)
+            assert np.array_equal(got, want.astype(np.uint8))
+
+
+def test_lod_blend_between_levels():
+    t = np.zeros((2, 2, 4), np.uint8)
+    t[0, 1] = t[1, 0] = 255
+    ch = O.mip_chain(t)                 # level 1 = 128
+    assert O.trilinear(ch, 2, 2, 0.25, 0.25, 0.5)[0] == 64    # lerp(0, 128, 0.5)
+    assert O.trilinear(ch, 2, 2, 0.75, 0.25, 0.5)[0] == 192   # lerp(255, 128, 0.5) = 191.5 -> even
+    assert O.trilinear(ch, 2, 2, 0.25, 0.25, 1.0)[0] == 128
+    assert O.trilinear(ch, 2, 2, 0.25, 0.25, 7.0)[0] == 128   # clamped to the last level
+
+
+# ---------------------------------------------------------------------------
+# Multiview mipmapping (Eq. 4-9) invariants on a whole frame
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny_frame():
+    d = S.display_tiny()
+    return d, O.render(d, S.scene_tiny(), S.model_matrix(11))
+
+
+def test_lod_min_not_above_lod_max(tiny_frame):
+    _, fr = tiny_frame
+    live = fr.tri[:, O.F["live"]] == 1
+    assert np.all(fr.tri[live, O.F["lod_min"]] <= fr.tri[live, O.F["lod_max"]])
+    assert np.all(fr.tri[live, O.F["vpuv_min"]] <= fr.tri[live, O.F["vpuv_max"]])
+
+
+def test_resolved_colour_between_tv_min_and_tv_max(tiny_frame):
+    _, fr = tiny_frame
+    k = fr.keys
+    cov = k != EMPTY
+    pid = (k[cov] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    tmin = fr.points[pid, 2:3].copy().view(np.uint8).reshape(-1, 4)
+    tmax = fr.points[pid, 3:4].copy().view(np.uint8).reshape(-1, 4)
+    col = fr.rgba[cov]
+    lo = np.minimum(tmin, tmax)
+    hi = np.maximum(tmin, tmax)
+    assert np.all(col >= lo) and np.all(col <= hi)
+    assert np.all(fr.rgba[~cov] == 0)
+
+
+def test_one_view_colour_is_tv_min():
+    d = replace(S.display_tiny(), n_views=1)
+    fr = O.render(d, S.scene_tiny(), S.model_matrix(3))
+    live = fr.tri[:, O.F["live"]] == 1
+    assert np.array_equal(fr.tri[live, O.F["vpuv_min"]], fr.tri[live, O.F["vpuv_max"]])
+    cov = fr.keys[0] != EMPTY
+    pid = (fr.keys[0][cov] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    tmin = fr.points[pid, 2:3].copy().view(np.uint8).reshape(-1, 4)
+    assert np.array_equal(fr.rgba[0][cov], tmin)
+
+
+# ---------------------------------------------------------------------------
+# Reconstruction, crosstalk, interleave (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def test_constant_stack_stays_constant_through_recon_and_crosstalk():
+    d = replace(S.display_angular_ss(), view_w=8, view_h=6, panel_w=40, panel_h=24)
+    r = np.full((d.n_render_views, 6, 8, 4), 77, np.uint8)
+    dv = O.display_views(d, r)
+    assert np.all(np.abs(dv - 77) < 1e-4)
+    pan = O.interleave(d, r)
+    assert np.all(pan[..., :3] == 77) and np.all(pan[..., 3] == 255)
+
+
+def test_delta_spreads_over_the_tent_then_crosstalk():
+    N = 6
+    d = replace(S.display_angular_ss(), n_views=N, view_w=1, view_h=1, crosstalk=0.0)
+    r = np.zeros((2 * N, 1, 1, 4), np.uint8)
+    r[5, 0, 0, 0] = 200                 # odd supersampled view: halfway between views 2 and 3
+    dv = O.display_views(d, r)[:, 0, 0, 0]
+    assert np.allclose(dv, [0, 0, 50, 50, 0, 0])
+    r[:] = 0
+    r[4, 0, 0, 0] = 200                 # even: on view 2's centre
+    dv = O.display_views(d, r)[:, 0, 0, 0]
+    assert np.allclose(dv, [0, 0, 100, 0, 0, 0])
+    r[:] = 0
+    r[0, 0, 0, 0] = 240                 # left edge: view 0's taps are views 0, 1 only, renormalised by 3/4
+    dv = O.display_views(d, r)[:, 0, 0, 0]
+    assert np.allclose(dv, [160, 0, 0, 0, 0, 0])
+    d2 = replace(d, recon=0, crosstalk=0.15)
+    r2 = np.zeros((N, 1, 1, 4), np.uint8)
+    r2[0, 0, 0, 0] = 200
+    dv = O.display_views(d2, r2)[:, 0, 0, 0]
+    assert np.allclose(dv, [140, 30, 0, 0, 0, 30], atol=1e-4)   # wraps to view N-1
+
+
+@pytest.mark.parametrize("d", [S.display_tiny(), S.display_paper()])
+def test_interleave_view_histogram_is_even(d):
+    """Over one lens period horizontally and a whole number of slant periods
+    vertically, every view is shown equally often, within one subpixel."""
+    per_x = int(round(d.lens_pitch_px))
+    per_y = int(round(1.0 / d.slant))
+    counts = np.zeros(d.n_views, np.int64)
+    for y in range(per_y * 2):
+        for x in range(per_x):
+            for c in range(3):
+                counts[O.view_of_subpixel(d, x + 40, y + 7, c)] += 1
+    mean = counts.sum() / d.n_views
+    assert counts.min() >= math.floor(mean) - 1 and counts.max() <= math.ceil(mean) + 1
+
+
+def test_interleave_unslanted_is_column_cyclic():
+    d = replace(unit_display(), n_views=6, lens_pitch_px=2.0, slant=0.0)
+    for y in (0, 5):
+        for x in range(64):
+            for c in range(3):
+                assert O.view_of_subpixel(d, x, y, c) == (3 * x + c) % 6
+
+
+def test_interleave_nearest_texel_mapping():
+    d = replace(unit_display(view_w=4, view_h=2), n_views=1, panel_w=8, panel_h=4)
+    r = np.zeros((1, 2, 4, 4), np.uint8)
+    r[0, :, :, 0] = np.arange(8).reshape(2, 4) * 10
+    pan = O.interleave(d, r)
+    assert np.array_equal(pan[..., 0], np.repeat(np.repeat(r[0, :, :, 0], 2, 0), 2, 1))
+
+
+# ---------------------------------------------------------------------------
+# Targeted pins for single steps
+# ---------------------------------------------------------------------------
+
+def test_culling_by_near_and_far_alone():
+    d = S.display_tiny()
+    e4 = float(O.eyes(d)[4])
+    too_near = [[e4, 0, 3.95], [e4 + 0.001, 0, 3.95], [e4, 0.001, 3.95]]  # depth 0.05 < near 0.1
+    too_far = [[0, 0, -200], [0.5, 0, -200], [0, 0.5, -200]]           # depth 204 > far 100
+    just_in = [[e4, 0, 3.8], [e4 + 0.001, 0, 3.8], [e4, 0.001, 3.8]]   # depth 0.2, on view 4's axis
+    _, rec, _ = O.setup(d, tri_scene(too_near + too_far + just_in), I4)
+    assert list(rec[:, O.F["live"]]) == [0, 0, 1]
+
+
+def test_cell_centres_fetch_texel_centres():
+    """Axis-aligned right triangle at the focal plane whose UVs map one texel
+    onto one lattice cell: the cell centre is the texel centre and LOD_min is
+    0, so tv_min of point (i, j) is texel (i, j) exactly (a transposed or
+    shifted UV map, or a wrong level, picks another texel)."""
+    s = 2.0 ** -6
+    mu, mv = 8, 4
+    rng = np.random.default_rng(5)
+    tex = rng.integers(0, 256, (mv, mu, 4), dtype=np.uint8)
+    d = unit_display()
+    sc = tri_scene([[0, 0, 0], [mu * s, 0, 0], [0, mv * s, 0]], uvs=[[0, 0], [1, 0], [0, 1]], tex=tex)
+    fr = O.render(d, sc, I4, splat=False)
+    assert fr.tri[0, O.F["lod_min"]] == 0.0
+    for p in fr.points:
+        i, j = int(p[1]) & 0xFFFF, int(p[1]) >> 16
+        assert np.array_equal(np.frombuffer(p[2].tobytes(), np.uint8), tex[j, i]), (i, j)
+
+
+def test_pixel_centres_on_cell_corners_are_filled_once():
+    """The lattice origin sits on a pixel centre and cells are one pixel, so
+    every pixel centre is a cell corner: the half-open cells still give each
+    pixel exactly one splat, and exactly the pixels of the closed legs and the
+    interior are filled (centres on the hypotenuse fall in cells outside the
+    triangle)."""
+    d = unit_display(view_w=64, view_h=64, focal_w=1.0, focal_h=1.0)   # pixel 2^-6 at z = 0
+    px = 2.0 ** -6
+    m = 12
+    x0, y0 = -0.5 + 28.5 * px, 0.5 - 36.5 * px       # pixel (28, 36) centre; the eye is over the triangle
+    tri = [[x0, y0, 0], [x0 + m * px, y0, 0], [x0, y0 + m * px, 0]]
+    sc = tri_scene(tri)
+    st, rec, counts = O.setup(d, sc, I4, tex_wh=[4096, 4096])
+    assert rec[0, O.F["s_u"]] == px and rec[0, O.F["d_min"]] == 4.0
+    pts = O.emit(rec, counts)
+    hits = O.splat_hits(d, rec, pts, [0])[0]
+    assert hits.max() == 1
+    want = np.zeros((64, 64), np.int64)
+    for a in range(m):              # pixel column 28 + a, rows 36 - b (y grows downwards)
+        for b in range(m - a):
+            want[36 - b, 28 + a] = 1
+    assert np.array_equal(hits.astype(np.int64), want)
+
+
+def test_eq8_eq9_on_a_screen_parallel_triangle():
+    """Closed form of Eq. 8-9: for a triangle parallel to the focal plane the
+    splat's pixel area is the cell area scaled by (D/depth)^2 over a pixel's
+    area, in every view; the eye distances d_v are the depth and the in-plane
+    offset. The expected colour is then tv_min + w (tv_max - tv_min) with
+    w = clamp((A_uv / min(1, area_px) - vpuv_min) / (vpuv_max - vpuv_min), 0, 1)."""
+    d = replace(unit_display(view_w=128, view_h=128, focal_w=4.0, focal_h=4.0), n_views=2, cone_deg=60.0)
+    ex = O.eyes(d).astype(np.float64)
+    z0 = 2.0
+    dep = d.view_dist - z0
+    cx = float(ex[1])
+    L = 0.3
+    x0 = cx - 0.05
+    tri = [[x0, -0.05, z0], [x0 + L, -0.05, z0], [x0, -0.05 + L, z0]]
+    tex = np.random.default_rng(9).integers(0, 256, (16, 16, 4), dtype=np.uint8)
+    sc = tri_scene(tri, tex=tex)
+    fr = O.render(d, sc, I4, panel=False)
+    T = fr.tri[0].astype(np.float64)
+    # d_v from geometry: eye 1 is over the triangle, eye 0 is off to the left
+    d1 = dep
+    d0 = math.hypot(dep, x0 - ex[0])
+    assert abs(T[O.F["d_min"]] - d1) < 1e-5 and abs(T[O.F["d_max"]] - d0) < 1e-5
+    px = d.focal_w / (d.view_dist * d.view_w)
+    A_ws, A_ts = L * L / 2, 0.5
+    r = A_ts / A_ws
+    vmin, vmax = d1 * d1 * px * px * r, d0 * d0 * px * px * r
+    su, sv = T[O.F["s_u"]], T[O.F["s_v"]]
+    a_uv = su * sv * r
+    assert vmin < a_uv < vmax            # texture-limited, so min(1, .) matters
+    pix = (d.focal_w / d.view_w) * (d.focal_h / d.view_h)
+    area_px = su * sv * (d.view_dist / dep) ** 2 / pix
+    assert area_px > 1.0
+    w = min(max((a_uv / min(1.0, area_px) - vmin) / (vmax - vmin), 0.0), 1.0)
+    assert 0.05 < w < 0.95
+    k = fr.keys[1]
+    cov = k != EMPTY
+    pid = (k[cov] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    tmin = fr.points[pid, 2:3].copy().view(np.uint8).reshape(-1, 4).astype(np.float64)
+    tmax = fr.points[pid, 3:4].copy().view(np.uint8).reshape(-1, 4).astype(np.float64)
+    want = tmin + w * (tmax - tmin)
+    got = fr.rgba[1][cov].astype(np.float64)
+    assert np.all(np.abs(got - want) <= 0.5 + 1e-3)
+    assert int(cov.sum()) > 100
+    assert np.abs(tmax - tmin).max() >= 20     # the two LODs really differ here
