@@ -1,0 +1,367 @@
+"""Benchmark of the LFDPR per-frame path on GB300.
+
+A step is one whole frame of the paper-shaped workload (10^6 triangles, 48
+views of 420x560, 2560x1600 panel): set-up and point generation, fetch,
+splat, resolve and interleave, with the scene rotating 3 degrees per frame.
+Inputs are resident in HBM; L2 is flushed (a 512 MiB write) between timed
+steps and each step is timed with CUDA events on the rendering stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank renders its own frames of the same scene
+(weak scaling, no data-path collective); the timed total is the max over ranks.
+--impl reference times the CPU oracle (the only reference this paper has: it
+publishes no code) on a bounded sample of the same workload, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "48-view display frames/s and splatted points/s; learned vs plain at PSNR>=38 dB"
+WORKLOAD = ("paper-shaped LFDPR frame: 1,000,000 triangles (200 displaced meshes, log-uniform "
+            "areas over 3 decades), 64 RGBA8 textures 64^2-4096^2, 48 views over 40 deg at "
+            "420x560, 2560x1600 panel, slant 0.2")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", choices=["paper", "angular", "tiny"], default="paper")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(cfg):
+    from paper_2601_19901_gb300 import scenes as S
+    if cfg == "tiny":
+        return S.display_tiny(), S.scene_tiny(), "tiny: 2,048 triangles, 8 views 128x128, 512x512 panel"
+    if cfg == "angular":
+        return (S.display_angular_ss(), S.scene_paper(),
+                WORKLOAD.replace("48 views", "96 views tent-reconstructed to 48 (+crosstalk 0.15)"))
+    return S.display_paper(), S.scene_paper(), WORKLOAD
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline object and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_frame_estimate(d, sc, model, gpu_views=None, textures=None):
+    """Time the oracle on a bounded sample of one frame: the full per-triangle
+    set-up, emission and fetch; splat + resolve of two rendered views, scaled
+    to all of them; the interleave of the full panel. Returns (seconds per
+    frame, description)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    fr = O.render(d, sc, model, splat=False, textures=textures)
+    t_sef = time.perf_counter() - t0
+    nr = d.n_render_views
+    vs = [0, nr // 2]
+    t0 = time.perf_counter()
+    O.splat_resolve(d, fr.tri, fr.points, vs)
+    t_sr = (time.perf_counter() - t0) / len(vs)
+    if gpu_views is None:
+        gpu_views = np.zeros((nr, d.view_h, d.view_w, 4), np.uint8)
+    t0 = time.perf_counter()
+    O.interleave(d, gpu_views)
+    t_il = time.perf_counter() - t0
+    total = t_sef + t_sr * nr + t_il
+    desc = ("single-threaded C oracle: full set-up/emit/fetch (%.2f s), splat+resolve of views %s "
+            "(%.2f s/view, scaled to %d views), full-panel interleave (%.2f s)" % (t_sef, vs, t_sr, nr, t_il))
+    return total, desc, t_sef + t_sr * len(vs) + t_il
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2601_19901_gb300 import scenes as S
+    O.build()
+    d, sc, wl = workload(args.config)
+    tx = O.Textures(sc.textures)
+    times = []
+    sample = None
+    spent = []
+    for k in range(args.warmup + args.steps):
+        est, sample, cost = oracle_frame_estimate(d, sc, S.model_matrix(k), textures=tx)
+        spent.append(cost)
+        if k >= args.warmup:
+            times.append(est)
+    ms = 1000.0 * statistics.mean(times)
+    v = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": sample + "; each step is one such sample, extrapolated to a frame"},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def atomic_peak(n_words, sm_stream):
+    """Measured throughput of uncontended 64-bit atomicMin on a buffer of
+    n_words (global, resolved in L2) and in shared memory (ops/s)."""
+    import torch
+    from paper_2601_19901_gb300 import lfdpr
+    g = torch.Generator(device="cuda").manual_seed(7)
+    n_ops = 1 << 26
+    words = torch.full((n_words,), -1, dtype=torch.int64, device="cuda")
+    idx = torch.randint(0, n_words, (n_ops,), dtype=torch.int32, device="cuda", generator=g)
+    val = torch.randint(0, 1 << 62, (n_ops,), dtype=torch.int64, device="cuda", generator=g)
+    out = {}
+    for name, shared, nw in (("global", False, n_words), ("shared", True, 4096)):
+        for _ in range(2):
+            lfdpr.lfdpr_probe_atomic_min(words.data_ptr(), nw, idx.data_ptr(), val.data_ptr(), n_ops, shared,
+                                         sm_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = math.inf
+        for _ in range(3):
+            e0.record(sm_stream)
+            lfdpr.lfdpr_probe_atomic_min(words.data_ptr(), nw, idx.data_ptr(), val.data_ptr(), n_ops, shared,
+                                         sm_stream)
+            e1.record(sm_stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1000.0)
+        out[name] = n_ops / best
+    del words, idx, val
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2601_19901_gb300 import build as B, lfdpr, scenes as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    lfdpr.lib()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    d, sc, wl = workload(args.config)
+    stream = torch.cuda.Stream()
+    R = lfdpr.Renderer(d, sc, stream=stream)
+    R.set_stage_timing(True)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
+    frame0 = rank * 100000
+
+    def frame_model(k):
+        return S.model_matrix(frame0 + k)
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            R.render(frame_model(k), stream)
+            R.interleave(panel.data_ptr(), stream)
+            R.stats(stream)
+
+    peaks_atomic = atomic_peak(d.n_render_views * d.view_w * d.view_h, stream)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    step_ms, stage = [], {n: [] for n in lfdpr.STAGES}
+    n_points = []
+    n_writes = []
+    launches0 = R.stats(stream).kernel_launches
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.render(frame_model(args.warmup + k), stream)
+        R.interleave(panel.data_ptr(), stream)
+        e1.record(stream)
+        st = R.stats(stream)
+        step_ms.append(e0.elapsed_time(e1))
+        for i, n in enumerate(lfdpr.STAGES):
+            stage[n].append(st.stage_ms[i])
+        n_points.append(st.n_points)
+        n_writes.append(getattr(st, "n_splat_writes", 0))
+    torch.cuda.synchronize()
+    launches = R.stats(stream).kernel_launches - launches0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+    P = statistics.mean(n_points)
+
+    # e2e: the public API with host buffers (model matrix in, panel out to pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        host_panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8).pin_memory()
+        model_host = torch.empty((4, 4), dtype=torch.float32).pin_memory()
+        e2e_s = 0.0
+        n_e2e = max(3, args.steps // 2)
+        for k in range(n_e2e):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            torch.cuda.synchronize()
+            model_host.copy_(torch.from_numpy(frame_model(10000 + k)))
+            t0 = time.perf_counter()
+            R.render(model_host.numpy(), stream)
+            R.interleave(host_panel.data_ptr(), stream)   # copies to host and waits
+            e2e_s += time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n_e2e / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 64,
+               "d2h_bytes_per_step": 4 * d.panel_w * d.panel_h}
+
+    if rank != 0:
+        R.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    st_mean = {n: statistics.mean(v) for n, v in stage.items()}
+    splat_ms = st_mean["splat"]
+    npix = d.n_render_views * d.view_w * d.view_h
+    b = R.buffers()
+    n_live = R.stats(stream).n_live_tris
+    splat_bytes = 8 * P + 80 * n_live + 16 * npix
+    achieved = splat_bytes / (splat_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_splat",
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": splat_bytes}
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl, "l2": "flushed (512 MiB write) between timed steps",
+                       "points_per_frame": P, "rendered_views": d.n_render_views},
+            "points_per_s": value * P,
+            "point_view_splats_per_s": P * d.n_render_views / (splat_ms / 1000.0),
+            "stage_ms": st_mean,
+            "roofline": roofline,
+            "atomic_peak_ops_per_s": peaks_atomic,
+            "gpu_launches": int(launches),
+            "clocks": clk}
+    if e2e:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        views = lfdpr.device_to_numpy(b.views, (d.n_render_views, d.view_h, d.view_w, 4), np.uint8)
+        est, desc, _ = oracle_frame_estimate(d, sc, frame_model(0), gpu_views=views)
+        line["cpu_baseline"] = {"value": 1.0 / est, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * lfdpr.h — C ABI of liblfdpr.so: light field display point rendering (LFDPR,
+ * Gavane & Watson, ACM TOG 2024) on one GB300 GPU (sm_103a).
+ *
+ * Per frame the library samples a textured triangle mesh into a point cloud
+ * fitted to a lenticular display (Sec. 3.1), splats every point into every
+ * display view with a 64-bit depth|id test (Sec. 3.2, Sec. 5.1), textures the
+ * splats by multiview mipmapping (Sec. 3.3, Eq. 4-9), and interleaves the views
+ * into one panel image after optional angular supersampling, reconstruction
+ * and crosstalk (Sec. 4).
+ *
+ * Conventions
+ *  - Opaque handles are owned by the library; destroy them with the matching
+ *    lfdpr_destroy_*.
+ *  - Input arrays passed by pointer are owned by the caller and copied before
+ *    the call returns unless stated otherwise.
+ *  - Output buffers are owned by the caller.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    launch work are asynchronous with respect to the host on that stream.
+ *  - Every call returns an lfdpr_status and never aborts the process. On error
+ *    lfdpr_last_error() (per thread) holds a one-line description. Errors of
+ *    asynchronous device work (point-buffer overflow, a launch failure) are
+ *    reported by the next lfdpr_frame_stats().
+ *  - One display and its meshes must be used from one host thread at a time.
+ */
+#ifndef LFDPR_H
+#define LFDPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFDPR_VERSION 1
+
+typedef struct lfdpr_display lfdpr_display;
+typedef struct lfdpr_mesh lfdpr_mesh;
+
+typedef enum {
+    LFDPR_OK = 0,
+    LFDPR_EINVAL = 1,     /* invalid argument: null pointer, bad size, bad descriptor */
+    LFDPR_ENOMEM = 2,     /* device or host allocation failed */
+    LFDPR_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    LFDPR_EOVERFLOW = 4,  /* the frame needed more points than the point buffer holds */
+    LFDPR_EDEVICE = 5     /* no usable CUDA device */
+} lfdpr_status;
+
+/*
+ * Display and view set (Sec. 3: views defined by the LFD; Sec. 5.1: the
+ * prototype; Sec. 4: interleave, supersampling, reconstruction).
+ * The N views are pinhole eyes on the line y = 0, z = view_dist, at the centres
+ * of N equal angular intervals of a cone of cone_deg degrees; all look down -z
+ * through one focal rectangle focal_w x focal_h centred on the origin at z = 0.
+ * Each view is view_w x view_h pixels. Depths (view_dist - z) outside
+ * [near_z, far_z] are not drawn. bias_h, bias_v multiply the horizontal and
+ * vertical point spacings (LFD-biased sampling, Sec. 3.1). The panel is
+ * panel_w x panel_h RGBA8 under slanted lenses of lens_pitch_px pixels, slant
+ * `slant` pixels per row, phase offset phase_offset (in lens periods).
+ * recon = 1 renders 2N views at half-interval steps and reconstructs N with a
+ * [1/4, 1/2, 1/4] tent; crosstalk x > 0 mixes each view with its +-1
+ * neighbours at weight x before interleaving. max_points is the point-buffer
+ * capacity (0 = 1 << 25).
+ */
+typedef struct {
+    int32_t n_views, view_w, view_h;
+    float cone_deg, view_dist, focal_w, focal_h, near_z, far_z, bias_h, bias_v;
+    int32_t panel_w, panel_h;
+    float lens_pitch_px, slant, phase_offset;
+    int32_t recon;
+    float crosstalk;
+    int64_t max_points;
+} lfdpr_display_desc;
+
+/* Stages of a frame, in launch order (Sec. 5.3 reports point generation,
+ * view generation and EIA construction times separately). */
+enum {
+    LFDPR_STAGE_SETUP = 0,      /* per-triangle set-up and count (Sec. 3.1) */
+    LFDPR_STAGE_SCAN = 1,       /* exclusive scan of the counts */
+    LFDPR_STAGE_EMIT = 2,       /* point emission */
+    LFDPR_STAGE_FETCH = 3,      /* tv_min / tv_max fetch (Sec. 3.3) */
+    LFDPR_STAGE_CLEAR = 4,      /* view key buffers reset */
+    LFDPR_STAGE_SPLAT = 5,      /* splatting with the depth test (Sec. 3.2) */
+    LFDPR_STAGE_RESOLVE = 6,    /* Eq. 8-9 per view pixel */
+    LFDPR_STAGE_INTERLEAVE = 7, /* reconstruction, crosstalk, interleave (Sec. 4) */
+    LFDPR_N_STAGES = 8
+};
+
+/* Per-frame counters read back by lfdpr_frame_stats. */
+typedef struct {
+    int64_t n_points;       /* points the last frame generated */
+    int64_t n_live_tris;    /* triangles not culled and of non-zero area */
+    int32_t overflow;       /* 1 if n_points exceeded max_points (frame not drawn) */
+    int32_t cell_overflow;  /* 1 if a triangle needed more than 65535 lattice columns or rows */
+    int64_t kernel_launches;/* kernels this display has launched since its creation */
+    float stage_ms[LFDPR_N_STAGES]; /* device time of each stage of the last frame and
+                                       interleave, from CUDA events on the caller's
+                                       stream; 0 unless lfdpr_set_stage_timing(.., 1) */
+} lfdpr_stats;
+
+/* Floats per triangle in the record array exposed by lfdpr_get_buffers. */
+#define LFDPR_TRI_FLOATS 32
+/* Offsets into one triangle record (float index). */
+enum {
+    LFDPR_TRI_P0 = 0,        /* 3: transformed first vertex */
+    LFDPR_TRI_SU = 3,        /* horizontal point spacing s_u */
+    LFDPR_TRI_EU = 4,        /* 3: horizontal sampling axis (T_align) */
+    LFDPR_TRI_SV = 7,        /* vertical point spacing s_v */
+    LFDPR_TRI_EV = 8,        /* 3: vertical sampling axis */
+    LFDPR_TRI_UMIN = 11,     /* lattice origin offset along u */
+    LFDPR_TRI_N = 12,        /* 3: unit normal */
+    LFDPR_TRI_VMIN = 15,     /* lattice origin offset along v */
+    LFDPR_TRI_A1 = 16,       /* 4: 2-D coordinates (a1, b1, a2, b2) of vertices 1, 2 */
+    LFDPR_TRI_SPL_UV = 20,   /* splat area in texture space (Eq. 8) */
+    LFDPR_TRI_VPUV_MIN = 21, /* Eq. 4 */
+    LFDPR_TRI_VPUV_MAX = 22, /* Eq. 5 */
+    LFDPR_TRI_UMAX = 23,     /* lattice extent along u */
+    LFDPR_TRI_S0 = 24,       /* 3: texture s = s0 + gu u + gv v over the lattice frame */
+    LFDPR_TRI_T0 = 27,       /* texture t offset */
+    LFDPR_TRI_TGU = 28,      /* 2: texture t gradients */
+    LFDPR_TRI_LOD_MIN = 30,  /* Eq. 6 */
+    LFDPR_TRI_LOD_MAX = 31   /* Eq. 7 */
+};
+
+/*
+ * Device buffers of the last frame, borrowed: valid until the next
+ * lfdpr_render_frame on the display or its destruction. Read them only after
+ * the frame's stream work has finished. Layouts:
+ *  counts   u32 [n_tris]                     points per triangle (0 = culled/degenerate)
+ *  offsets  u32 [n_tris]                     first point id of each triangle
+ *  points   u32 [max_points][4]              triangle id, i | j << 16 (lattice cell),
+ *                                            tv_min RGBA8, tv_max RGBA8 (Sec. 3.3)
+ *  tri      f32 [n_tris][LFDPR_TRI_FLOATS]   per-triangle sampling record
+ *  keys     u64 [n_render_views][view_h][view_w]  float_bits(t) << 32 | point id,
+ *                                            all ones where empty (Sec. 3.2)
+ *  views    u8  [n_render_views][view_h][view_w][4] resolved RGBA8 views
+ */
+typedef struct {
+    const uint32_t *counts, *offsets, *points;
+    const float *tri;
+    const uint64_t *keys;
+    const uint8_t *views;
+    int64_t n_tris, max_points;
+    int32_t n_render_views, view_w, view_h;
+} lfdpr_buffers;
+
+/*
+ * lfdpr_create_display: validate `desc` (positive sizes, 1 <= n_views <= 256,
+ * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1},
+ * 0 <= crosstalk < 0.5) and allocate the display's device buffers: view key
+ * buffers (8 B per rendered-view pixel, Sec. 5.2), RGBA8 views, the point
+ * buffer (16 B per point) and the panel scratch. Uses the current CUDA device.
+ * On success *out owns them. Errors: EINVAL, ENOMEM, EDEVICE, ECUDA.
+ */
+lfdpr_status lfdpr_create_display(const lfdpr_display_desc *desc, lfdpr_display **out);
+
+/* Free a display and every device buffer it owns (meshes must be destroyed first). */
+lfdpr_status lfdpr_destroy_display(lfdpr_display *disp);
+
+/*
+ * lfdpr_upload_mesh: copy a triangle mesh and its textures to the device and
+ * build each texture's mip chain there (Sec. 3.3 relies on mipmaps).
+ *  xyz      f32 [n_verts][3] object-space positions (host)
+ *  uv       f32 [n_verts][2] texture coordinates, wrap addressing (host)
+ *  idx      u32 [n_tris][3]  vertex indices < n_verts (host)
+ *  tri_tex  u32 [n_tris]     texture id < n_tex per triangle (host)
+ *  tex_rgba8[k]  u8 [h][w][4] level-0 texels of texture k (host)
+ *  tex_wh   u32 [n_tex][2]   (w, h) of texture k; powers of two, <= 16384
+ * All inputs are validated (indices and texture ids in range, sizes) and copied;
+ * the call synchronises `stream` before returning. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_upload_mesh(lfdpr_display *disp, const float *xyz, const float *uv,
+                               const uint32_t *idx, const uint32_t *tri_tex,
+                               uint32_t n_verts, uint32_t n_tris,
+                               const uint8_t *const *tex_rgba8, const uint32_t *tex_wh,
+                               uint32_t n_tex, void *stream, lfdpr_mesh **out);
+
+/* Free a mesh's device buffers. */
+lfdpr_status lfdpr_destroy_mesh(lfdpr_mesh *mesh);
+
+/*
+ * lfdpr_render_frame: one frame of the hot path (Sec. 3, Fig. 3) on `stream`:
+ * transform by `model` (row-major 4x4, host memory, affine rows 0-2 used),
+ * cull, per-triangle sampling set-up (Sec. 3.1, Eq. 1-7), scan, point emission,
+ * tv_min/tv_max fetch (Sec. 3.3), splatting into every rendered view
+ * (Sec. 3.2), and the per-view resolve of Eq. 8-9 into RGBA8 views. No host
+ * synchronisation; nothing is allocated. If the frame needs more points than
+ * max_points the frame is not drawn and the next lfdpr_frame_stats returns
+ * EOVERFLOW. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_render_frame(lfdpr_display *disp, lfdpr_mesh *mesh, const float model[16],
+                                void *stream);
+
+/*
+ * lfdpr_interleave: build the elemental image array from the last frame's
+ * views (Sec. 4): optional tent reconstruction of 2N supersampled views, then
+ * optional crosstalk mixing, then the slanted-lens subpixel interleave.
+ * `panel_rgba8` is u8 [panel_h][panel_w][4], caller-owned, in device memory or
+ * in host memory (pinned or pageable); for host memory the panel is built in
+ * device scratch and copied back on `stream`, and the call returns after the
+ * copy has completed. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_interleave(lfdpr_display *disp, uint8_t *panel_rgba8, void *stream);
+
+/*
+ * lfdpr_frame_stats: synchronise `stream`, then report the last frame's
+ * counters and any asynchronous error (EOVERFLOW, ECUDA). `out` may be NULL.
+ */
+lfdpr_status lfdpr_frame_stats(lfdpr_display *disp, void *stream, lfdpr_stats *out);
+
+/*
+ * lfdpr_set_stage_timing: enable (1) or disable (0) CUDA events between the
+ * stages of lfdpr_render_frame and around lfdpr_interleave, recorded on the
+ * caller's stream; lfdpr_frame_stats then reports each stage's device time.
+ * Off by default. Errors: EINVAL.
+ */
+lfdpr_status lfdpr_set_stage_timing(lfdpr_display *disp, int32_t enable);
+
+/* lfdpr_get_buffers: borrowed device pointers of the last frame (see lfdpr_buffers). */
+lfdpr_status lfdpr_get_buffers(lfdpr_display *disp, lfdpr_mesh *mesh, lfdpr_buffers *out);
+
+/* Eye x positions of the rendered views (host floats, n_render_views of them). */
+lfdpr_status lfdpr_view_eyes(const lfdpr_display *disp, float *out, int32_t capacity);
+
+/*
+ * lfdpr_probe_atomic_min: roofline probe for the splat's depth test (Sec. 5.1
+ * uses 64-bit buffers). Performs n_ops 64-bit atomicMin operations on `words`
+ * (u64 [n_words], device) at indices idx[k] (u32 [n_ops], device, < n_words)
+ * with values val[k] (u64 [n_ops], device); shared != 0 stages the words in
+ * shared memory per block (n_words <= 8192) and merges them back with one
+ * global atomicMin per word. Asynchronous on `stream`. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_probe_atomic_min(uint64_t *words, uint64_t n_words, const uint32_t *idx,
+                                    const uint64_t *val, uint64_t n_ops, int32_t shared,
+                                    void *stream);
+
+/* Description of the last error on this thread ("" if none). */
+const char *lfdpr_last_error(void);
+
+/* LFDPR_VERSION of the library. */
+int32_t lfdpr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFDPR_H */

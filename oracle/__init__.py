@@ -270,6 +270,18 @@ def splat_hits(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]) -> 
     return hits
 
 
+def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]):
+    """Steps 9-10 for the listed views, from existing records and points."""
+    dd = _disp(d)
+    vl = np.asarray(views, np.int32)
+    pts = np.ascontiguousarray(points, np.uint32)
+    keys = np.zeros((len(vl), d.view_h, d.view_w), np.uint64)
+    lib().orc_splat(C.byref(dd), _p(tri), _p(pts), len(pts), _p(vl), len(vl), _p(keys))
+    rgba = np.zeros((len(vl), d.view_h, d.view_w, 4), np.uint8)
+    lib().orc_resolve(C.byref(dd), _p(tri), _p(pts), _p(keys), _p(vl), len(vl), _p(rgba))
+    return keys, rgba
+
+
 def interleave(d, rendered: np.ndarray) -> np.ndarray:
     dd = _disp(d)
     pan = np.zeros((d.panel_h, d.panel_w, 4), np.uint8)

@@ -1,0 +1,160 @@
+// Internal declarations of liblfdpr: device data layouts, the display
+// constants every kernel reads, and the binary32 helpers of the bit-exact
+// steps. Compiled with -fmad=false: the only fused multiply-adds are the
+// explicit fmaf() calls, so every rounding below is the one written.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lfdpr.h"
+
+namespace lfdpr {
+
+constexpr int kMaxRenderViews = 512;
+constexpr int kMaxCell = 65535;          // lattice indices are stored as u16
+constexpr int kSetupThreads = 256;       // triangles per set-up / emit block
+
+// Display constants, passed by value to every kernel.
+struct DispConst {
+    int32_t n_views;      // display views N
+    int32_t nr;           // rendered views (2N with angular supersampling)
+    int32_t W, H;         // view pixels
+    int32_t Wp, Hp;       // panel pixels
+    int32_t recon;
+    float D;              // eye-line distance
+    float fw2, fh2;       // half focal rectangle
+    float near_z, far_z;
+    float bias_h, bias_v;
+    float px, py;         // pixel footprint per unit distance (fw/(D W), fh/(D H))
+    float pw, ph;         // pixel size on the focal plane (fw/W, fh/H)
+    float ipw, iph;       // W/fw, H/fh
+    float x0, y0;         // focal rectangle corner: -fw/2, fh/2
+    float inv_pitch, slant, phase_offset;
+    float xtalk, xtalk_c; // crosstalk weight x and centre weight 1 - 2x
+};
+
+// Per-texture descriptor of the mip pool.
+struct TexDesc {
+    uint64_t offset;      // byte offset of level 0 in the pool
+    uint32_t w, h;        // level-0 size (powers of two)
+    uint32_t levels;      // number of levels (log2(max(w, h)) + 1)
+    uint32_t pad;
+};
+
+// Device-side frame counters.
+struct Counters {
+    uint32_t n_points;
+    uint32_t overflow;
+    uint32_t cell_overflow;
+    uint32_t n_live;
+};
+
+// One triangle's sampling record: 8 float4 (layout = LFDPR_TRI_* in lfdpr.h).
+struct TriRec {
+    float4 q[8];
+};
+
+// ---------------------------------------------------------------------------
+// binary32 helpers (each rounding explicit)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {
+    return fmaf(ax, bx, fmaf(ay, by, az * bz));
+}
+
+// Doubled signed area of (p, r, q): edge function of p->r evaluated at q.
+__device__ __forceinline__ float edge_fn(float px, float py, float rx, float ry, float qx, float qy) {
+    return fmaf(rx - px, qy - py, -((ry - py) * (qx - px)));
+}
+
+// Squared distance from q to the segment p-r.
+__device__ __forceinline__ float seg_dist2(float px, float py, float rx, float ry, float qx, float qy) {
+    const float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+    const float ee = fmaf(ex, ex, ey * ey);
+    float t = ee > 0.0f ? __fdiv_rn(fmaf(wx, ex, wy * ey), ee) : 0.0f;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    const float dx = fmaf(-t, ex, wx), dy = fmaf(-t, ey, wy);
+    return fmaf(dx, dx, dy * dy);
+}
+
+__device__ __forceinline__ bool inside_either(float w0, float w1, float w2) {
+    return (w0 >= 0.0f && w1 >= 0.0f && w2 >= 0.0f) || (w0 <= 0.0f && w1 <= 0.0f && w2 <= 0.0f);
+}
+
+// log2 by the atanh series (Eq. 6-7): x = m 2^e from the bits, m folded into
+// [sqrt(1/2), sqrt(2)], ln m = 2 atanh(z) with z = (m-1)/(m+1) summed through
+// the z^9/9 term, log2 x = e + ln m / ln 2.
+__device__ __forceinline__ float log2_series(float x) {
+    if (isnan(x)) return x;
+    if (x <= 0.0f) return -INFINITY;
+    if (isinf(x)) return INFINITY;
+    uint32_t b = __float_as_uint(x);
+    int e;
+    if ((b >> 23) == 0u) {
+        b = __float_as_uint(x * 16777216.0f);
+        e = int(b >> 23) - 151;
+    } else {
+        e = int(b >> 23) - 127;
+    }
+    float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) { m = m * 0.5f; e += 1; }
+    const float z = __fdiv_rn(m - 1.0f, m + 1.0f);
+    const float z2 = z * z;
+    float s = fmaf(z2, (float)(1.0 / 9.0), (float)(1.0 / 7.0));   // atanh series coefficients
+    s = fmaf(z2, s, (float)(1.0 / 5.0));
+    s = fmaf(z2, s, (float)(1.0 / 3.0));
+    s = fmaf(z2, s, 1.0f);
+    const float ln_m = (2.0f * z) * s;
+    return fmaf(ln_m, (float)(1.0 / 0.69314718055994530942), float(e));   // / ln 2
+}
+
+__device__ __forceinline__ uint8_t round_u8(float v) {
+    float r = rintf(v);
+    r = fminf(fmaxf(r, 0.0f), 255.0f);   // NaN -> 0 through fmaxf
+    return (uint8_t)r;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host side, defined next to their kernels)
+// ---------------------------------------------------------------------------
+
+struct FrameArgs {
+    DispConst dc;
+    const float* ex;                 // eye x per rendered view (device)
+    float model[12];                 // affine rows of the model matrix
+    const float* xyz;
+    const float* uv;
+    const uint32_t* idx;
+    const uint32_t* tri_tex;
+    const TexDesc* tex;
+    const uint8_t* pool;
+    uint32_t n_tris, n_tex;
+    TriRec* rec;
+    uint32_t* counts;
+    uint32_t* offsets;
+    uint32_t* block_sums;            // [n_blocks]
+    uint32_t n_blocks;
+    uint4* points;
+    uint32_t max_points;
+    uint64_t* keys;
+    uint8_t* views;
+    Counters* ctr;
+    int sm_count;
+};
+
+cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel,
+                              cudaStream_t s);
+cudaError_t launch_mip_level(const uint8_t* src, uint32_t sw, uint32_t sh, uint8_t* dst,
+                             uint32_t dw, uint32_t dh, cudaStream_t s);
+cudaError_t launch_probe_atomic(uint64_t* words, uint64_t n_words, const uint32_t* idx,
+                                const uint64_t* val, uint64_t n_ops, bool shared, int sm_count,
+                                cudaStream_t s);
+
+}  // namespace lfdpr

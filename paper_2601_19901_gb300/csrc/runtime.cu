@@ -1,0 +1,501 @@
+// C ABI of liblfdpr (declared in include/lfdpr.h): display and mesh objects,
+// device allocation, argument validation, and the per-frame launch sequence.
+// Host arithmetic that feeds the kernels' bit-exact steps (eye positions,
+// pixel footprints) is done in double and rounded once to binary32; this file
+// is compiled with -ffp-contract=off so no host multiply-add is fused.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lfdpr_internal.cuh"
+
+using namespace lfdpr;
+
+struct lfdpr_display {
+    lfdpr_display_desc desc;
+    DispConst dc;
+    int device = 0;
+    int sm_count = 1;
+    std::vector<float> h_ex;
+    float* d_ex = nullptr;
+    uint4* points = nullptr;
+    uint32_t max_points = 0;
+    uint64_t* keys = nullptr;
+    uint8_t* views = nullptr;
+    uint8_t* panel = nullptr;      // device scratch for host-memory panels
+    Counters* ctr = nullptr;
+    int n_meshes = 0;
+    int64_t launches = 0;
+    bool timing = false;
+    cudaEvent_t ev[LFDPR_N_STAGES + 2] = {};
+    bool ev_frame = false;        // the frame's stage events were recorded
+    bool ev_interleave = false;   // the interleave's events were recorded
+};
+
+struct lfdpr_mesh {
+    lfdpr_display* disp = nullptr;
+    uint32_t n_verts = 0, n_tris = 0, n_tex = 0, n_blocks = 0;
+    float* xyz = nullptr;
+    float* uv = nullptr;
+    uint32_t* idx = nullptr;
+    uint32_t* tri_tex = nullptr;
+    uint8_t* pool = nullptr;
+    TexDesc* tex = nullptr;
+    TriRec* rec = nullptr;
+    uint32_t* counts = nullptr;
+    uint32_t* offsets = nullptr;
+    uint32_t* block_sums = nullptr;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lfdpr_status fail(lfdpr_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+lfdpr_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? LFDPR_ENOMEM : LFDPR_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+uint32_t mip_levels(uint32_t w, uint32_t h) {
+    uint32_t m = w > h ? w : h, l = 0;
+    while ((1u << l) < m) l++;
+    return l + 1;
+}
+
+uint64_t mip_bytes(uint32_t w, uint32_t h) {
+    uint64_t n = 0;
+    const uint32_t L = mip_levels(w, h);
+    for (uint32_t l = 0; l < L; l++) {
+        const uint64_t lw = (w >> l) ? (w >> l) : 1, lh = (h >> l) ? (h >> l) : 1;
+        n += lw * lh * 4u;
+    }
+    return n;
+}
+
+void free_display(lfdpr_display* d) {
+    if (!d) return;
+    for (auto& e : d->ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(d->d_ex);
+    cudaFree(d->points);
+    cudaFree(d->keys);
+    cudaFree(d->views);
+    cudaFree(d->panel);
+    cudaFree(d->ctr);
+    delete d;
+}
+
+void free_mesh(lfdpr_mesh* m) {
+    if (!m) return;
+    cudaFree(m->xyz);
+    cudaFree(m->uv);
+    cudaFree(m->idx);
+    cudaFree(m->tri_tex);
+    cudaFree(m->pool);
+    cudaFree(m->tex);
+    cudaFree(m->rec);
+    cudaFree(m->counts);
+    cudaFree(m->offsets);
+    cudaFree(m->block_sums);
+    delete m;
+}
+
+// Eye x of rendered view k: centres of N equal angular intervals, or 2N
+// half-interval steps with angular supersampling (even ones on the centres).
+double eye_angle_deg(const lfdpr_display_desc& d, int k) {
+    const double cone = d.cone_deg;
+    return d.recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * d.n_views)
+                        : -cone / 2.0 + cone * (k + 0.5) / d.n_views;
+}
+
+void mark(lfdpr_display* d, int k, cudaStream_t s) {
+    if (d->timing) cudaEventRecord(d->ev[k], s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lfdpr_last_error(void) { return g_err; }
+
+int32_t lfdpr_version(void) { return LFDPR_VERSION; }
+
+lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display** out) {
+    g_err[0] = 0;
+    if (!desc || !out) return fail(LFDPR_EINVAL, "create_display: null argument");
+    *out = nullptr;
+    const lfdpr_display_desc& s = *desc;
+    if (s.n_views < 1 || s.n_views > 256) return fail(LFDPR_EINVAL, "n_views must be in [1, 256]");
+    if (s.view_w < 1 || s.view_h < 1 || s.view_w > 16384 || s.view_h > 16384)
+        return fail(LFDPR_EINVAL, "view size must be in [1, 16384]");
+    if (s.panel_w < 1 || s.panel_h < 1 || s.panel_w > 32768 || s.panel_h > 32768)
+        return fail(LFDPR_EINVAL, "panel size must be in [1, 32768]");
+    if (!(s.view_dist > 0.0f) || !(s.focal_w > 0.0f) || !(s.focal_h > 0.0f))
+        return fail(LFDPR_EINVAL, "view_dist, focal_w, focal_h must be positive");
+    if (!(s.near_z > 0.0f) || !(s.far_z > s.near_z) || !std::isfinite(s.far_z))
+        return fail(LFDPR_EINVAL, "need 0 < near_z < far_z < inf");
+    if (!(s.cone_deg >= 0.0f) || !(s.cone_deg < 179.0f)) return fail(LFDPR_EINVAL, "cone_deg must be in [0, 179)");
+    if (!(s.bias_h > 0.0f) || !(s.bias_v > 0.0f) || !std::isfinite(s.bias_h) || !std::isfinite(s.bias_v))
+        return fail(LFDPR_EINVAL, "bias_h, bias_v must be positive and finite");
+    if (!(s.lens_pitch_px > 0.0f) || !std::isfinite(s.slant) || !std::isfinite(s.phase_offset))
+        return fail(LFDPR_EINVAL, "lens_pitch_px must be positive; slant, phase_offset finite");
+    if (s.recon != 0 && s.recon != 1) return fail(LFDPR_EINVAL, "recon must be 0 or 1");
+    if (!(s.crosstalk >= 0.0f) || !(s.crosstalk < 0.5f)) return fail(LFDPR_EINVAL, "crosstalk must be in [0, 0.5)");
+    if (s.max_points < 0 || s.max_points > 0x7fffffffLL) return fail(LFDPR_EINVAL, "max_points must be in [0, 2^31)");
+    const int nr = s.recon == 1 ? 2 * s.n_views : s.n_views;
+    if (nr > kMaxRenderViews) return fail(LFDPR_EINVAL, "too many rendered views");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(LFDPR_EDEVICE, "no CUDA device");
+    }
+    lfdpr_display* d = new (std::nothrow) lfdpr_display();
+    if (!d) return fail(LFDPR_ENOMEM, "host allocation failed");
+    d->desc = s;
+    if (d->desc.max_points == 0) d->desc.max_points = 1LL << 25;
+    d->max_points = uint32_t(d->desc.max_points);
+    CK(cudaGetDevice(&d->device), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device), "sm count");
+
+    DispConst& c = d->dc;
+    c.n_views = s.n_views;
+    c.nr = nr;
+    c.W = s.view_w;
+    c.H = s.view_h;
+    c.Wp = s.panel_w;
+    c.Hp = s.panel_h;
+    c.recon = s.recon;
+    c.D = s.view_dist;
+    c.fw2 = 0.5f * s.focal_w;
+    c.fh2 = 0.5f * s.focal_h;
+    c.near_z = s.near_z;
+    c.far_z = s.far_z;
+    c.bias_h = s.bias_h;
+    c.bias_v = s.bias_v;
+    c.px = float(double(s.focal_w) / (double(s.view_dist) * s.view_w));
+    c.py = float(double(s.focal_h) / (double(s.view_dist) * s.view_h));
+    c.pw = float(double(s.focal_w) / s.view_w);
+    c.ph = float(double(s.focal_h) / s.view_h);
+    c.ipw = float(double(s.view_w) / s.focal_w);
+    c.iph = float(double(s.view_h) / s.focal_h);
+    c.x0 = -0.5f * s.focal_w;
+    c.y0 = 0.5f * s.focal_h;
+    c.inv_pitch = float(1.0 / double(s.lens_pitch_px));
+    c.slant = s.slant;
+    c.phase_offset = s.phase_offset;
+    c.xtalk = s.crosstalk;
+    c.xtalk_c = float(1.0 - 2.0 * double(s.crosstalk));
+
+    d->h_ex.resize(nr);
+    for (int k = 0; k < nr; k++)
+        d->h_ex[k] = float(double(s.view_dist) * std::tan(eye_angle_deg(s, k) * M_PI / 180.0));
+
+    const uint64_t npix = uint64_t(s.view_w) * s.view_h * nr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->keys, 8u * npix)) != cudaSuccess ||
+        (e = cudaMalloc(&d->views, 4u * npix)) != cudaSuccess ||
+        (e = cudaMalloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
+        (e = cudaMalloc(&d->ctr, sizeof(Counters))) != cudaSuccess) {
+        free_display(d);
+        return cuda_fail(e, "create_display: cudaMalloc");
+    }
+    if ((e = cudaMemcpy(d->d_ex, d->h_ex.data(), sizeof(float) * nr, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(d->ctr, 0, sizeof(Counters))) != cudaSuccess ||
+        (e = cudaMemset(d->keys, 0xff, 8u * npix)) != cudaSuccess ||
+        (e = cudaMemset(d->views, 0, 4u * npix)) != cudaSuccess) {
+        free_display(d);
+        return cuda_fail(e, "create_display: init");
+    }
+    *out = d;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_destroy_display(lfdpr_display* disp) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "destroy_display: null");
+    if (disp->n_meshes != 0) return fail(LFDPR_EINVAL, "destroy_display: meshes still alive");
+    free_display(disp);
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_view_eyes(const lfdpr_display* disp, float* out, int32_t capacity) {
+    if (!disp || !out) return fail(LFDPR_EINVAL, "view_eyes: null");
+    if (capacity < disp->dc.nr) return fail(LFDPR_EINVAL, "view_eyes: capacity < rendered views");
+    std::memcpy(out, disp->h_ex.data(), sizeof(float) * disp->dc.nr);
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const float* uv, const uint32_t* idx,
+                               const uint32_t* tri_tex, uint32_t n_verts, uint32_t n_tris,
+                               const uint8_t* const* tex_rgba8, const uint32_t* tex_wh, uint32_t n_tex,
+                               void* stream, lfdpr_mesh** out) {
+    g_err[0] = 0;
+    if (!disp || !out) return fail(LFDPR_EINVAL, "upload_mesh: null display or out");
+    *out = nullptr;
+    if (n_tris > 0 && (!xyz || !uv || !idx || !tri_tex)) return fail(LFDPR_EINVAL, "upload_mesh: null array");
+    if (n_tex == 0 || !tex_rgba8 || !tex_wh) return fail(LFDPR_EINVAL, "upload_mesh: need >= 1 texture");
+    if (n_tris > (1u << 30)) return fail(LFDPR_EINVAL, "upload_mesh: too many triangles");
+    for (uint64_t k = 0; k < 3ull * n_tris; k++)
+        if (idx[k] >= n_verts) return fail(LFDPR_EINVAL, "upload_mesh: index %u out of range at %llu", idx[k], (unsigned long long)k);
+    for (uint32_t t = 0; t < n_tris; t++)
+        if (tri_tex[t] >= n_tex) return fail(LFDPR_EINVAL, "upload_mesh: texture id out of range at triangle %u", t);
+    for (uint64_t k = 0; k < 3ull * n_verts; k++)
+        if (!std::isfinite(xyz[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite vertex coordinate");
+    for (uint64_t k = 0; k < 2ull * n_verts; k++)
+        if (!std::isfinite(uv[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite texture coordinate");
+    std::vector<TexDesc> td(n_tex);
+    uint64_t pool_bytes = 0;
+    for (uint32_t k = 0; k < n_tex; k++) {
+        const uint32_t w = tex_wh[2 * k], h = tex_wh[2 * k + 1];
+        if (!pow2(w) || !pow2(h) || w > 16384 || h > 16384)
+            return fail(LFDPR_EINVAL, "upload_mesh: texture %u size %ux%u not a power of two <= 16384", k, w, h);
+        if (!tex_rgba8[k]) return fail(LFDPR_EINVAL, "upload_mesh: null texture %u", k);
+        td[k].offset = pool_bytes;
+        td[k].w = w;
+        td[k].h = h;
+        td[k].levels = mip_levels(w, h);
+        td[k].pad = 0;
+        pool_bytes += (mip_bytes(w, h) + 255) & ~uint64_t(255);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lfdpr_mesh* m = new (std::nothrow) lfdpr_mesh();
+    if (!m) return fail(LFDPR_ENOMEM, "host allocation failed");
+    m->disp = disp;
+    m->n_verts = n_verts;
+    m->n_tris = n_tris;
+    m->n_tex = n_tex;
+    m->n_blocks = (n_tris + kSetupThreads - 1) / kSetupThreads;
+    const uint64_t nt = n_tris ? n_tris : 1, nv = n_verts ? n_verts : 1;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->xyz, 12u * nv)) != cudaSuccess || (e = cudaMalloc(&m->uv, 8u * nv)) != cudaSuccess ||
+        (e = cudaMalloc(&m->idx, 12u * nt)) != cudaSuccess || (e = cudaMalloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->pool, pool_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
+        (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
+        free_mesh(m);
+        return cuda_fail(e, "upload_mesh: cudaMalloc");
+    }
+#define CKM(call, what)                         \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) {                \
+            free_mesh(m);                       \
+            return cuda_fail(e_, what);         \
+        }                                       \
+    } while (0)
+    if (n_verts) {
+        CKM(cudaMemcpyAsync(m->xyz, xyz, 12u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload xyz");
+        CKM(cudaMemcpyAsync(m->uv, uv, 8u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload uv");
+    }
+    if (n_tris) {
+        CKM(cudaMemcpyAsync(m->idx, idx, 12u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload idx");
+        CKM(cudaMemcpyAsync(m->tri_tex, tri_tex, 4u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload tri_tex");
+    }
+    CKM(cudaMemcpyAsync(m->tex, td.data(), sizeof(TexDesc) * n_tex, cudaMemcpyHostToDevice, s), "upload tex table");
+    for (uint32_t k = 0; k < n_tex; k++) {
+        uint32_t w = td[k].w, h = td[k].h;
+        uint8_t* lvl = m->pool + td[k].offset;
+        CKM(cudaMemcpyAsync(lvl, tex_rgba8[k], 4u * (uint64_t)w * h, cudaMemcpyHostToDevice, s), "upload texels");
+        for (uint32_t l = 1; l < td[k].levels; l++) {
+            const uint32_t nw = w > 1 ? w / 2 : 1, nh = h > 1 ? h / 2 : 1;
+            uint8_t* nxt = lvl + 4u * (uint64_t)w * h;
+            CKM(launch_mip_level(lvl, w, h, nxt, nw, nh, s), "mip build");
+            lvl = nxt;
+            w = nw;
+            h = nh;
+        }
+    }
+    CKM(cudaStreamSynchronize(s), "upload_mesh: synchronize");
+#undef CKM
+    disp->n_meshes++;
+    *out = m;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_destroy_mesh(lfdpr_mesh* mesh) {
+    g_err[0] = 0;
+    if (!mesh) return fail(LFDPR_EINVAL, "destroy_mesh: null");
+    if (mesh->disp) mesh->disp->n_meshes--;
+    free_mesh(mesh);
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const float model[16], void* stream) {
+    g_err[0] = 0;
+    if (!disp || !mesh || !model) return fail(LFDPR_EINVAL, "render_frame: null argument");
+    if (mesh->disp != disp) return fail(LFDPR_EINVAL, "render_frame: mesh uploaded to another display");
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(model[k])) return fail(LFDPR_EINVAL, "render_frame: non-finite model matrix");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FrameArgs a{};
+    a.dc = disp->dc;
+    a.ex = disp->d_ex;
+    for (int k = 0; k < 12; k++) a.model[k] = model[k];
+    a.xyz = mesh->xyz;
+    a.uv = mesh->uv;
+    a.idx = mesh->idx;
+    a.tri_tex = mesh->tri_tex;
+    a.tex = mesh->tex;
+    a.pool = mesh->pool;
+    a.n_tris = mesh->n_tris;
+    a.n_tex = mesh->n_tex;
+    a.rec = mesh->rec;
+    a.counts = mesh->counts;
+    a.offsets = mesh->offsets;
+    a.block_sums = mesh->block_sums;
+    a.n_blocks = mesh->n_blocks;
+    a.points = disp->points;
+    a.max_points = disp->max_points;
+    a.keys = disp->keys;
+    a.views = disp->views;
+    a.ctr = disp->ctr;
+    a.sm_count = disp->sm_count;
+    const uint64_t npix = uint64_t(disp->dc.W) * disp->dc.H * disp->dc.nr;
+    CK(cudaMemsetAsync(disp->ctr, 0, sizeof(Counters), s), "render_frame: reset counters");
+    mark(disp, 0, s);
+    if (mesh->n_tris) {
+        CK(launch_setup(a, s), "launch k_setup");
+        mark(disp, 1, s);
+        CK(launch_scan(a, s), "launch k_scan");
+        mark(disp, 2, s);
+        CK(launch_emit(a, s), "launch k_emit");
+        mark(disp, 3, s);
+        CK(launch_fetch(a, s), "launch k_fetch");
+        disp->launches += 4;
+    } else {
+        for (int k = 1; k <= 3; k++) mark(disp, k, s);
+    }
+    mark(disp, 4, s);
+    CK(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "render_frame: clear keys");
+    mark(disp, 5, s);
+    if (mesh->n_tris) {
+        CK(launch_splat(a, s), "launch k_splat");
+        disp->launches += 1;
+    }
+    mark(disp, 6, s);
+    CK(launch_resolve(a, s), "launch k_resolve");
+    disp->launches += 1;
+    mark(disp, 7, s);
+    disp->ev_frame = disp->timing;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_interleave(lfdpr_display* disp, uint8_t* panel_rgba8, void* stream) {
+    g_err[0] = 0;
+    if (!disp || !panel_rgba8) return fail(LFDPR_EINVAL, "interleave: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaPointerAttributes at;
+    bool on_device = false;
+    if (cudaPointerGetAttributes(&at, panel_rgba8) == cudaSuccess)
+        on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
+    uint8_t* dst = on_device ? panel_rgba8 : disp->panel;
+    mark(disp, LFDPR_N_STAGES, s);
+    CK(launch_interleave(disp->dc, disp->views, dst, s), "launch k_interleave");
+    disp->launches += 1;
+    mark(disp, LFDPR_N_STAGES + 1, s);
+    disp->ev_interleave = disp->timing;
+    if (!on_device) {
+        const uint64_t bytes = 4u * uint64_t(disp->dc.Wp) * disp->dc.Hp;
+        CK(cudaMemcpyAsync(panel_rgba8, disp->panel, bytes, cudaMemcpyDeviceToHost, s), "interleave: copy to host");
+        CK(cudaStreamSynchronize(s), "interleave: synchronize");
+    }
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_frame_stats(lfdpr_display* disp, void* stream, lfdpr_stats* out) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "frame_stats: null display");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(s), "frame_stats: synchronize");
+    CK(cudaGetLastError(), "frame_stats: pending error");
+    Counters c;
+    CK(cudaMemcpy(&c, disp->ctr, sizeof c, cudaMemcpyDeviceToHost), "frame_stats: read counters");
+    if (out) {
+        out->n_points = c.n_points;
+        out->n_live_tris = c.n_live;
+        out->overflow = int32_t(c.overflow);
+        out->cell_overflow = int32_t(c.cell_overflow);
+        out->kernel_launches = disp->launches;
+        for (int k = 0; k < LFDPR_N_STAGES; k++) out->stage_ms[k] = 0.0f;
+        if (disp->ev_frame)
+            for (int k = 0; k < LFDPR_STAGE_INTERLEAVE; k++)
+                CK(cudaEventElapsedTime(&out->stage_ms[k], disp->ev[k], disp->ev[k + 1]), "stage time");
+        if (disp->ev_interleave)
+            CK(cudaEventElapsedTime(&out->stage_ms[LFDPR_STAGE_INTERLEAVE], disp->ev[LFDPR_N_STAGES],
+                                    disp->ev[LFDPR_N_STAGES + 1]),
+               "interleave time");
+    }
+    if (c.overflow)
+        return fail(LFDPR_EOVERFLOW, "frame needed %u points, capacity %u", c.n_points, disp->max_points);
+    if (c.cell_overflow) return fail(LFDPR_EOVERFLOW, "a triangle needed more than 65535 lattice cells per axis");
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_stage_timing(lfdpr_display* disp, int32_t enable) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "set_stage_timing: null display");
+    if (enable && !disp->ev[0]) {
+        for (auto& e : disp->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    disp->timing = enable != 0;
+    disp->ev_frame = disp->ev_interleave = false;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_get_buffers(lfdpr_display* disp, lfdpr_mesh* mesh, lfdpr_buffers* out) {
+    g_err[0] = 0;
+    if (!disp || !mesh || !out) return fail(LFDPR_EINVAL, "get_buffers: null argument");
+    out->counts = mesh->counts;
+    out->offsets = mesh->offsets;
+    out->points = reinterpret_cast<const uint32_t*>(disp->points);
+    out->tri = reinterpret_cast<const float*>(mesh->rec);
+    out->keys = disp->keys;
+    out->views = disp->views;
+    out->n_tris = mesh->n_tris;
+    out->max_points = disp->max_points;
+    out->n_render_views = disp->dc.nr;
+    out->view_w = disp->dc.W;
+    out->view_h = disp->dc.H;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_probe_atomic_min(uint64_t* words, uint64_t n_words, const uint32_t* idx, const uint64_t* val,
+                                    uint64_t n_ops, int32_t shared, void* stream) {
+    g_err[0] = 0;
+    if (!words || !idx || !val || n_words == 0) return fail(LFDPR_EINVAL, "probe: null or empty argument");
+    if (shared && n_words > 8192) return fail(LFDPR_EINVAL, "probe: shared variant holds at most 8192 words");
+    int dev = 0, sms = 1;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    CK(launch_probe_atomic(words, n_words, idx, val, n_ops, shared != 0, sms, static_cast<cudaStream_t>(stream)),
+       "launch probe");
+    return LFDPR_OK;
+}
+
+}  // extern "C"

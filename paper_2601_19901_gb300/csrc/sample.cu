@@ -1,0 +1,482 @@
+// Triangle sampling (Sec. 3.1) and multiview-mip fetch (Sec. 3.3).
+//
+//   k_setup  one thread per triangle: model transform, visibility against every
+//            view (Sec. 3), T_align frame, LFD-biased spacings from the closest
+//            eye, Eq. 1-3 texture limit, Eq. 4-7 mip set-up, point count by the
+//            lattice column walk; block sums for the scan.
+//   k_scan   one block: exclusive scan of the block sums -> block offsets,
+//            total point count, overflow flag.
+//   k_emit   one thread per triangle: warp-shuffle block scan of the counts
+//            plus the block offset gives each triangle's first point id; the
+//            column walk writes (triangle, cell) for each of its points.
+//   k_fetch  one thread per point: texture coordinate of the cell centre and
+//            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7).
+//
+// Every floating-point step here is bit-specified (binary32, explicit fmaf,
+// IEEE division and square root) so the point set is identical to the CPU
+// oracle's.
+#include "lfdpr_internal.cuh"
+
+namespace lfdpr {
+namespace {
+
+__device__ __forceinline__ void transform(const float* m, float x, float y, float z, float* o) {
+    o[0] = fmaf(m[0], x, fmaf(m[1], y, fmaf(m[2], z, m[3])));
+    o[1] = fmaf(m[4], x, fmaf(m[5], y, fmaf(m[6], z, m[7])));
+    o[2] = fmaf(m[8], x, fmaf(m[9], y, fmaf(m[10], z, m[11])));
+}
+
+// Visibility (Sec. 3): dropped iff for every view all three vertices are on
+// the outer side of one common frustum plane. Planes as linear forms,
+// negative outside; top, bottom, near and far are shared by all views.
+__device__ bool culled(const DispConst& c, const float* __restrict__ ex, const float P[3][3]) {
+    bool out_t = true, out_b = true, out_n = true, out_f = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float dep = c.D - P[k][2];
+        const float top = fmaf(c.fh2, dep, -(P[k][1] * c.D));
+        const float bot = fmaf(P[k][1], c.D, c.fh2 * dep);
+        out_t &= top < 0.0f;
+        out_b &= bot < 0.0f;
+        out_n &= (dep - c.near_z) < 0.0f;
+        out_f &= (c.far_z - dep) < 0.0f;
+    }
+    if (out_t || out_b || out_n || out_f) return true;
+    for (int v = 0; v < c.nr; v++) {
+        const float e = ex[v];
+        const float lx = -c.fw2 - e, rx = c.fw2 - e;
+        bool out_l = true, out_r = true;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float dep = c.D - P[k][2];
+            const float l = fmaf(P[k][0] - e, c.D, -(lx * dep));
+            const float r = fmaf(rx, dep, -((P[k][0] - e) * c.D));
+            out_l &= l < 0.0f;
+            out_r &= r < 0.0f;
+        }
+        if (!(out_l || out_r)) return false;
+    }
+    return true;
+}
+
+// Rows [j0, j1) of lattice column i overlapping the triangle (conservative
+// rule): the triangle's v range over the column slab [i s_u, (i+1) s_u]
+// from the vertices inside the slab and the edge crossings of its borders.
+__device__ __forceinline__ int column_rows(const float U[3], const float V[3], float su, float sv,
+                                           float umax, int i, int* j0, int* j1) {
+    const float a = float(i) * su;
+    const float b = fminf(float(i + 1) * su, umax);
+    float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (U[k] >= a && U[k] <= b) { lo = fminf(lo, V[k]); hi = fmaxf(hi, V[k]); }
+    }
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const int p = e, r = e == 2 ? 0 : e + 1;
+        if (U[p] == U[r]) continue;
+        const float umn = fminf(U[p], U[r]), umx = fmaxf(U[p], U[r]);
+        const float du = U[r] - U[p], dv = V[r] - V[p];
+        if (a >= umn && a <= umx) {
+            const float vx = fmaf(__fdiv_rn(a - U[p], du), dv, V[p]);
+            lo = fminf(lo, vx);
+            hi = fmaxf(hi, vx);
+        }
+        if (b >= umn && b <= umx) {
+            const float vx = fmaf(__fdiv_rn(b - U[p], du), dv, V[p]);
+            lo = fminf(lo, vx);
+            hi = fmaxf(hi, vx);
+        }
+    }
+    if (lo > hi) { *j0 = 0; *j1 = 0; return 0; }
+    *j0 = int(floorf(__fdiv_rn(lo, sv)));
+    *j1 = int(ceilf(__fdiv_rn(hi, sv)));
+    if (*j1 < *j0) *j1 = *j0;
+    return *j1 - *j0;
+}
+
+__device__ __forceinline__ void shifted_uv(const TriRec& r, float U[3], float V[3]) {
+    const float umin = r.q[2].w, vmin = r.q[3].w;
+    U[0] = 0.0f - umin; U[1] = r.q[4].x - umin; U[2] = r.q[4].z - umin;
+    V[0] = 0.0f - vmin; V[1] = r.q[4].y - vmin; V[2] = r.q[4].w - vmin;
+}
+
+struct SetupOut {
+    uint32_t count;
+    bool live;
+    bool cell_overflow;
+};
+
+__device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
+    const DispConst& c = a.dc;
+    SetupOut res{0u, false, false};
+    float P[3][3], Q[3][2];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const uint32_t vi = a.idx[3 * (size_t)t + k];
+        transform(a.model, a.xyz[3 * (size_t)vi], a.xyz[3 * (size_t)vi + 1], a.xyz[3 * (size_t)vi + 2], P[k]);
+        Q[k][0] = a.uv[2 * (size_t)vi];
+        Q[k][1] = a.uv[2 * (size_t)vi + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) r.q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.q[0] = make_float4(P[0][0], P[0][1], P[0][2], 0.0f);
+    if (culled(c, a.ex, P)) return res;
+
+    // area and unit normal
+    float e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) { e1[k] = P[1][k] - P[0][k]; e2[k] = P[2][k] - P[0][k]; }
+    const float crx = fmaf(e1[1], e2[2], -(e1[2] * e2[1]));
+    const float cry = fmaf(e1[2], e2[0], -(e1[0] * e2[2]));
+    const float crz = fmaf(e1[0], e2[1], -(e1[1] * e2[0]));
+    const float len = __fsqrt_rn(dot3(crx, cry, crz, crx, cry, crz));
+    if (!(len > 0.0f) || isinf(len)) return res;
+    const float nx = __fdiv_rn(crx, len), ny = __fdiv_rn(cry, len), nz = __fdiv_rn(crz, len);
+    const float A_ws = 0.5f * len;
+
+    // T_align frame (Sec. 3.1): v-hat along the world vertical projected into
+    // the plane, u-hat = v-hat x n; near-horizontal planes use world x instead.
+    float ux, uy, uz, vx, vy, vz;
+    {
+        const float tx = -(ny * nx), ty = fmaf(-ny, ny, 1.0f), tz = -(ny * nz);
+        const float l2 = dot3(tx, ty, tz, tx, ty, tz);
+        if (l2 >= 1e-6f) {
+            const float l = __fsqrt_rn(l2);
+            vx = __fdiv_rn(tx, l); vy = __fdiv_rn(ty, l); vz = __fdiv_rn(tz, l);
+            ux = fmaf(vy, nz, -(vz * ny));
+            uy = fmaf(vz, nx, -(vx * nz));
+            uz = fmaf(vx, ny, -(vy * nx));
+        } else {
+            const float sx = fmaf(-nx, nx, 1.0f), sy = -(nx * ny), sz = -(nx * nz);
+            const float l = __fsqrt_rn(dot3(sx, sy, sz, sx, sy, sz));
+            ux = __fdiv_rn(sx, l); uy = __fdiv_rn(sy, l); uz = __fdiv_rn(sz, l);
+            vx = fmaf(ny, uz, -(nz * uy));
+            vy = fmaf(nz, ux, -(nx * uz));
+            vz = fmaf(nx, uy, -(ny * ux));
+        }
+    }
+
+    // 2-D coordinates relative to P0 and the lattice origin (bbox min)
+    const float a1 = dot3(e1[0], e1[1], e1[2], ux, uy, uz), b1 = dot3(e1[0], e1[1], e1[2], vx, vy, vz);
+    const float a2 = dot3(e2[0], e2[1], e2[2], ux, uy, uz), b2 = dot3(e2[0], e2[1], e2[2], vx, vy, vz);
+    const float umin = fminf(fminf(0.0f, a1), a2), vmin = fminf(fminf(0.0f, b1), b2);
+    const float U[3] = {0.0f - umin, a1 - umin, a2 - umin};
+    const float V[3] = {0.0f - vmin, b1 - vmin, b2 - vmin};
+    const float umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
+
+    // closest and farthest eye (Fig. 4): height over the plane plus the
+    // in-plane distance to the 2-D triangle, over every rendered view
+    float d2min = INFINITY, d2max = -INFINITY;
+    for (int v = 0; v < c.nr; v++) {
+        const float qx = a.ex[v] - P[0][0], qy = 0.0f - P[0][1], qz = c.D - P[0][2];
+        const float qu = dot3(qx, qy, qz, ux, uy, uz);
+        const float qv = dot3(qx, qy, qz, vx, vy, vz);
+        const float h = dot3(qx, qy, qz, nx, ny, nz);
+        const float w0 = edge_fn(a1, b1, a2, b2, qu, qv);
+        const float w1 = edge_fn(a2, b2, 0.0f, 0.0f, qu, qv);
+        const float w2 = edge_fn(0.0f, 0.0f, a1, b1, qu, qv);
+        float d2 = 0.0f;
+        if (!inside_either(w0, w1, w2))
+            d2 = fminf(fminf(seg_dist2(0.0f, 0.0f, a1, b1, qu, qv), seg_dist2(a1, b1, a2, b2, qu, qv)),
+                       seg_dist2(a2, b2, 0.0f, 0.0f, qu, qv));
+        const float dd = fmaf(h, h, d2);
+        d2min = fminf(d2min, dd);
+        d2max = fmaxf(d2max, dd);
+    }
+    const float dmin = fmaxf(__fsqrt_rn(d2min), c.near_z);
+    const float dmax = fmaxf(__fsqrt_rn(d2max), c.near_z);
+
+    // LFD-biased spacings and Eq. 1-3
+    const float su0 = (c.bias_h * dmin) * c.px, sv0 = (c.bias_v * dmin) * c.py;
+    const float size_xy = su0 * sv0;
+    const uint32_t tex = a.tri_tex[t];
+    const TexDesc td = a.tex[tex];
+    const float X = float(td.w), Y = float(td.h);
+    const float ds1 = Q[1][0] - Q[0][0], dt1 = Q[1][1] - Q[0][1];
+    const float ds2 = Q[2][0] - Q[0][0], dt2 = Q[2][1] - Q[0][1];
+    const float A_ts = 0.5f * fabsf(fmaf(ds1, dt2, -(dt1 * ds2)));
+    float n_tex = (A_ts * X) * Y;
+    if (n_tex < 1.0f) n_tex = 1.0f;
+    const float size_uv = __fdiv_rn(A_ws, n_tex);
+    float su = su0, sv = sv0;
+    if (size_uv > size_xy) {
+        const float f = __fsqrt_rn(__fdiv_rn(size_uv, size_xy));
+        su = su0 * f;
+        sv = sv0 * f;
+    }
+
+    // Eq. 4-7
+    const float ratio = __fdiv_rn(A_ts, A_ws);
+    const float size_xy_max = ((c.bias_h * dmax) * c.px) * ((c.bias_v * dmax) * c.py);
+    const float vpuv_min = size_xy * ratio, vpuv_max = size_xy_max * ratio;
+    const float spl_uv = (su * sv) * ratio;
+    const float lod_min = 0.5f * log2_series((vpuv_min * X) * Y);
+    const float lod_max = 0.5f * log2_series((vpuv_max * X) * Y);
+
+    // affine texture map over the lattice frame
+    const float det = fmaf(a1, b2, -(a2 * b1));
+    float gsu = 0.0f, gsv = 0.0f, gtu = 0.0f, gtv = 0.0f;
+    if (det != 0.0f) {
+        gsu = __fdiv_rn(fmaf(ds1, b2, -(ds2 * b1)), det);
+        gsv = __fdiv_rn(fmaf(ds2, a1, -(ds1 * a2)), det);
+        gtu = __fdiv_rn(fmaf(dt1, b2, -(dt2 * b1)), det);
+        gtv = __fdiv_rn(fmaf(dt2, a1, -(dt1 * a2)), det);
+    }
+    const float s0 = fmaf(gsu, umin, fmaf(gsv, vmin, Q[0][0]));
+    const float t0 = fmaf(gtu, umin, fmaf(gtv, vmin, Q[0][1]));
+
+    r.q[0].w = su;
+    r.q[1] = make_float4(ux, uy, uz, sv);
+    r.q[2] = make_float4(vx, vy, vz, umin);
+    r.q[3] = make_float4(nx, ny, nz, vmin);
+    r.q[4] = make_float4(a1, b1, a2, b2);
+    r.q[5] = make_float4(spl_uv, vpuv_min, vpuv_max, umax);
+    r.q[6] = make_float4(s0, gsu, gsv, t0);
+    r.q[7] = make_float4(gtu, gtv, lod_min, lod_max);
+
+    // point count: one per lattice cell overlapping the triangle
+    const float ncol = ceilf(__fdiv_rn(umax, su));
+    if (!(ncol <= float(kMaxCell))) { res.cell_overflow = true; return res; }
+    const int cols = int(ncol);
+    uint32_t cnt = 0;
+    for (int i = 0; i < cols; i++) {
+        int j0, j1;
+        const int rows = column_rows(U, V, su, sv, umax, i, &j0, &j1);
+        if (j1 > kMaxCell + 1) { res.cell_overflow = true; return res; }
+        cnt += uint32_t(rows);
+    }
+    res.count = cnt;
+    res.live = true;
+    return res;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* smem) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    T tot = 0;
+    if (threadIdx.x < 32) {
+        tot = threadIdx.x < (blockDim.x >> 5) ? smem[threadIdx.x] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    return tot;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kSetupThreads) k_setup(FrameArgs a) {
+    __shared__ uint32_t s_cnt[kSetupThreads / 32];
+    __shared__ uint32_t s_live[kSetupThreads / 32];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t count = 0, live = 0;
+    if (t < a.n_tris) {
+        TriRec r;
+        const SetupOut o = setup_triangle(a, t, r);
+        TriRec* dst = a.rec + t;
+#pragma unroll
+        for (int k = 0; k < 8; k++) dst->q[k] = r.q[k];
+        count = o.count;
+        live = o.live ? 1u : 0u;
+        a.counts[t] = count;
+        if (o.cell_overflow) atomicExch(&a.ctr->cell_overflow, 1u);
+    }
+    const uint32_t bs = block_sum(count, s_cnt);
+    const uint32_t bl = block_sum(live, s_live);
+    if (threadIdx.x == 0) {
+        a.block_sums[blockIdx.x] = bs;
+        if (bl) atomicAdd(&a.ctr->n_live, bl);
+    }
+}
+
+// Exclusive scan of the per-block point counts (one block of 1024 threads,
+// chunks of 1024 with a running carry); the total decides overflow.
+__global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < a.n_blocks; base += 1024) {
+        const uint32_t k = base + threadIdx.x;
+        const unsigned long long v = k < a.n_blocks ? a.block_sums[k] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long n = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += n;
+            }
+            s_warp[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned long long excl = s_carry + (warp > 0 ? s_warp[warp - 1] : 0ull) + inc - v;
+        if (k < a.n_blocks) a.block_sums[k] = uint32_t(excl > 0xffffffffull ? 0xffffffffull : excl);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_warp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_carry;
+        a.ctr->n_points = uint32_t(total > 0xffffffffull ? 0xffffffffull : total);
+        a.ctr->overflow = total > (unsigned long long)a.max_points ? 1u : 0u;
+    }
+}
+
+// Block-level exclusive scan of the counts (warp shuffles), plus the block's
+// offset: each triangle's first point id. Then emit its points in (column,
+// row) order.
+__global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
+    __shared__ uint32_t s_warp[kSetupThreads / 32];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t cnt = t < a.n_tris ? a.counts[t] : 0u;
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += n;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kSetupThreads / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += n;
+        }
+        if (lane < kSetupThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (t >= a.n_tris) return;
+    const uint32_t first = a.block_sums[blockIdx.x] + (warp > 0 ? s_warp[warp - 1] : 0u) + inc - cnt;
+    a.offsets[t] = first;
+    if (cnt == 0 || a.ctr->overflow) return;
+    const TriRec* rp = a.rec + t;
+    TriRec r;
+    r.q[0] = rp->q[0]; r.q[1] = rp->q[1]; r.q[2] = rp->q[2]; r.q[3] = rp->q[3];
+    r.q[4] = rp->q[4]; r.q[5] = rp->q[5];
+    float U[3], V[3];
+    shifted_uv(r, U, V);
+    const float su = r.q[0].w, sv = r.q[1].w, umax = r.q[5].w;
+    const int cols = int(ceilf(__fdiv_rn(umax, su)));
+    uint32_t p = first;
+    for (int i = 0; i < cols; i++) {
+        int j0, j1;
+        column_rows(U, V, su, sv, umax, i, &j0, &j1);
+        for (int j = j0; j < j1; j++) {
+            *reinterpret_cast<uint2*>(a.points + p) = make_uint2(t, uint32_t(i) | (uint32_t(j) << 16));
+            p++;
+        }
+    }
+}
+
+// Bilinear sample of one mip level, wrap addressing, texel centres at (k+1/2)/w.
+__device__ __forceinline__ void bilinear(const uint8_t* __restrict__ lvl, uint32_t w, uint32_t h,
+                                         float s, float t, float out[4]) {
+    if (!isfinite(s)) s = 0.0f;
+    if (!isfinite(t)) t = 0.0f;
+    const float fs = s - floorf(s), ft = t - floorf(t);
+    const float x = fmaf(fs, float(w), -0.5f), y = fmaf(ft, float(h), -0.5f);
+    const float xf = floorf(x), yf = floorf(y);
+    const float fx = x - xf, fy = y - yf;
+    const uint32_t ix0 = uint32_t(int(xf)) & (w - 1), iy0 = uint32_t(int(yf)) & (h - 1);
+    const uint32_t ix1 = (ix0 + 1) & (w - 1), iy1 = (iy0 + 1) & (h - 1);
+    const uint32_t* L = reinterpret_cast<const uint32_t*>(lvl);
+    const uint32_t t00 = __ldg(L + (size_t)iy0 * w + ix0), t10 = __ldg(L + (size_t)iy0 * w + ix1);
+    const uint32_t t01 = __ldg(L + (size_t)iy1 * w + ix0), t11 = __ldg(L + (size_t)iy1 * w + ix1);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const float va = float((t00 >> (8 * c)) & 255u), vb = float((t10 >> (8 * c)) & 255u);
+        const float vc = float((t01 >> (8 * c)) & 255u), vd = float((t11 >> (8 * c)) & 255u);
+        const float top = fmaf(fx, vb - va, va);
+        const float bot = fmaf(fx, vd - vc, vc);
+        out[c] = fmaf(fy, bot - top, top);
+    }
+}
+
+// Trilinear fetch at a level of detail: clamp to [0, L_max], level floor,
+// blend to the next level by the fraction, round half-even to RGBA8.
+__device__ uint32_t trilinear(const uint8_t* __restrict__ pool, const TexDesc& td, float s, float t,
+                              float lod) {
+    const int L = int(td.levels) - 1;
+    lod = fminf(fmaxf(lod, 0.0f), float(L));
+    const int l = int(floorf(lod));
+    const float f = lod - float(l);
+    uint64_t off = td.offset;
+    uint32_t lw = td.w, lh = td.h;
+    for (int k = 0; k < l; k++) {
+        off += (uint64_t)lw * lh * 4u;
+        lw = lw > 1 ? lw >> 1 : 1;
+        lh = lh > 1 ? lh >> 1 : 1;
+    }
+    float c0[4];
+    bilinear(pool + off, lw, lh, s, t, c0);
+    uint32_t out = 0;
+    if (f > 0.0f && l < L) {
+        float c1[4];
+        const uint64_t off1 = off + (uint64_t)lw * lh * 4u;
+        bilinear(pool + off1, lw > 1 ? lw >> 1 : 1, lh > 1 ? lh >> 1 : 1, s, t, c1);
+#pragma unroll
+        for (int c = 0; c < 4; c++) out |= uint32_t(round_u8(fmaf(f, c1[c] - c0[c], c0[c]))) << (8 * c);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) out |= uint32_t(round_u8(c0[c])) << (8 * c);
+    }
+    return out;
+}
+
+__global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
+    if (a.ctr->overflow) return;
+    const uint32_t n = a.ctr->n_points;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        const TriRec* r = a.rec + pt.x;
+        const float su = __ldg(&r->q[0].w), sv = __ldg(&r->q[1].w);
+        const float4 q6 = __ldg(&r->q[6]), q7 = __ldg(&r->q[7]);
+        const uint32_t i = pt.y & 0xffffu, j = pt.y >> 16;
+        const float uc = (float(i) + 0.5f) * su;
+        const float vc = (float(j) + 0.5f) * sv;
+        const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
+        const float t = fmaf(q7.x, uc, fmaf(q7.y, vc, q6.w));
+        const TexDesc td = a.tex[__ldg(a.tri_tex + pt.x)];
+        const uint32_t tmin = trilinear(a.pool, td, s, t, q7.z);
+        const uint32_t tmax = trilinear(a.pool, td, s, t, q7.w);
+        *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s) {
+    k_setup<<<a.n_blocks, kSetupThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s) {
+    k_emit<<<a.n_blocks, kSetupThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s) {
+    k_fetch<<<a.sm_count * 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lfdpr

@@ -1,0 +1,281 @@
+"""Python binding of liblfdpr.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls
+(include/lfdpr.h) and converts arguments; all computation happens in the
+library's CUDA kernels. Device memory and streams come from PyTorch tensors
+(`data_ptr()`) and `torch.cuda.Stream.cuda_stream`. If the library is missing
+or no GPU is present, the calls raise: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblfdpr.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, EDEVICE = range(6)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "EDEVICE"}
+TRI_FLOATS = 32
+TRI = dict(P0=0, s_u=3, eu=4, s_v=7, ev=8, umin=11, n=12, vmin=15, a1=16, b1=17, a2=18, b2=19,
+           spl_uv=20, vpuv_min=21, vpuv_max=22, u_max=23, s0=24, sgu=25, sgv=26, t0=27, tgu=28,
+           tgv=29, lod_min=30, lod_max=31)
+
+# Names the C ABI exports (every declaration of include/lfdpr.h).
+EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
+           "lfdpr_destroy_mesh", "lfdpr_render_frame", "lfdpr_interleave", "lfdpr_frame_stats",
+           "lfdpr_get_buffers", "lfdpr_view_eyes", "lfdpr_probe_atomic_min", "lfdpr_last_error",
+           "lfdpr_version", "lfdpr_set_stage_timing"]
+
+
+class LfdprError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class DisplayDesc(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("view_w", C.c_int32), ("view_h", C.c_int32),
+                ("cone_deg", C.c_float), ("view_dist", C.c_float), ("focal_w", C.c_float),
+                ("focal_h", C.c_float), ("near_z", C.c_float), ("far_z", C.c_float),
+                ("bias_h", C.c_float), ("bias_v", C.c_float),
+                ("panel_w", C.c_int32), ("panel_h", C.c_int32),
+                ("lens_pitch_px", C.c_float), ("slant", C.c_float), ("phase_offset", C.c_float),
+                ("recon", C.c_int32), ("crosstalk", C.c_float), ("max_points", C.c_int64)]
+
+
+N_STAGES = 8
+STAGES = ["setup", "scan", "emit", "fetch", "clear", "splat", "resolve", "interleave"]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_live_tris", C.c_int64), ("overflow", C.c_int32),
+                ("cell_overflow", C.c_int32), ("kernel_launches", C.c_int64),
+                ("stage_ms", C.c_float * N_STAGES)]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("counts", C.c_void_p), ("offsets", C.c_void_p), ("points", C.c_void_p),
+                ("tri", C.c_void_p), ("keys", C.c_void_p), ("views", C.c_void_p),
+                ("n_tris", C.c_int64), ("max_points", C.c_int64),
+                ("n_render_views", C.c_int32), ("view_w", C.c_int32), ("view_h", C.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load liblfdpr.so (built by paper_2601_19901_gb300.build); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblfdpr.so is not built (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        P, S = C.c_void_p, C.c_int
+        L.lfdpr_create_display.argtypes = [C.POINTER(DisplayDesc), C.POINTER(C.c_void_p)]
+        L.lfdpr_destroy_display.argtypes = [P]
+        L.lfdpr_upload_mesh.argtypes = [P, P, P, P, P, C.c_uint32, C.c_uint32, P, P, C.c_uint32,
+                                        P, C.POINTER(C.c_void_p)]
+        L.lfdpr_destroy_mesh.argtypes = [P]
+        L.lfdpr_render_frame.argtypes = [P, P, P, P]
+        L.lfdpr_interleave.argtypes = [P, P, P]
+        L.lfdpr_frame_stats.argtypes = [P, P, C.POINTER(Stats)]
+        L.lfdpr_get_buffers.argtypes = [P, P, C.POINTER(Buffers)]
+        L.lfdpr_view_eyes.argtypes = [P, P, C.c_int32]
+        L.lfdpr_set_stage_timing.argtypes = [P, C.c_int32]
+        L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
+        for name in EXPORTS:
+            fn = getattr(L, name)
+            if name == "lfdpr_last_error":
+                fn.restype = C.c_char_p
+                fn.argtypes = []
+            elif name == "lfdpr_version":
+                fn.restype = C.c_int32
+                fn.argtypes = []
+            else:
+                fn.restype = S
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise LfdprError(status, lib().lfdpr_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def desc_of(display, max_points: int = 0) -> DisplayDesc:
+    d = display
+    return DisplayDesc(d.n_views, d.view_w, d.view_h, d.cone_deg, d.view_dist, d.focal_w,
+                       d.focal_h, d.near_z, d.far_z, d.bias_h, d.bias_v, d.panel_w, d.panel_h,
+                       d.lens_pitch_px, d.slant, d.phase_offset, d.recon, d.crosstalk, max_points)
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def lfdpr_create_display(desc: DisplayDesc) -> int:
+    h = C.c_void_p()
+    _check(lib().lfdpr_create_display(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def lfdpr_destroy_display(disp: int):
+    _check(lib().lfdpr_destroy_display(disp))
+
+
+def lfdpr_upload_mesh(disp: int, xyz: np.ndarray, uv: np.ndarray, idx: np.ndarray,
+                      tri_tex: np.ndarray, textures: Sequence[np.ndarray], stream=None) -> int:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    uv = np.ascontiguousarray(uv, np.float32)
+    idx = np.ascontiguousarray(idx, np.uint32)
+    tri_tex = np.ascontiguousarray(tri_tex, np.uint32)
+    texs = [np.ascontiguousarray(t, np.uint8) for t in textures]
+    ptrs = (C.c_void_p * len(texs))(*[t.ctypes.data for t in texs])
+    wh = np.array([[t.shape[1], t.shape[0]] for t in texs], np.uint32).ravel()
+    h = C.c_void_p()
+    _check(lib().lfdpr_upload_mesh(disp, _ptr(xyz), _ptr(uv), _ptr(idx), _ptr(tri_tex),
+                                   xyz.shape[0], idx.reshape(-1, 3).shape[0], ptrs, _ptr(wh),
+                                   len(texs), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def lfdpr_destroy_mesh(mesh: int):
+    _check(lib().lfdpr_destroy_mesh(mesh))
+
+
+def lfdpr_render_frame(disp: int, mesh: int, model: np.ndarray, stream=None):
+    m = np.ascontiguousarray(model, np.float32).ravel()
+    _check(lib().lfdpr_render_frame(disp, mesh, _ptr(m), _stream(stream)))
+
+
+def lfdpr_interleave(disp: int, panel_ptr: int, stream=None):
+    _check(lib().lfdpr_interleave(disp, C.c_void_p(panel_ptr), _stream(stream)))
+
+
+def lfdpr_frame_stats(disp: int, stream=None) -> Stats:
+    st = Stats()
+    _check(lib().lfdpr_frame_stats(disp, _stream(stream), C.byref(st)))
+    return st
+
+
+def lfdpr_set_stage_timing(disp: int, enable: bool):
+    _check(lib().lfdpr_set_stage_timing(disp, 1 if enable else 0))
+
+
+def lfdpr_get_buffers(disp: int, mesh: int) -> Buffers:
+    b = Buffers()
+    _check(lib().lfdpr_get_buffers(disp, mesh, C.byref(b)))
+    return b
+
+
+def lfdpr_view_eyes(disp: int, n: int) -> np.ndarray:
+    out = np.zeros(n, np.float32)
+    _check(lib().lfdpr_view_eyes(disp, _ptr(out), n))
+    return out
+
+
+def lfdpr_probe_atomic_min(words_ptr: int, n_words: int, idx_ptr: int, val_ptr: int, n_ops: int,
+                           shared: bool, stream=None):
+    _check(lib().lfdpr_probe_atomic_min(C.c_void_p(words_ptr), n_words, C.c_void_p(idx_ptr),
+                                        C.c_void_p(val_ptr), n_ops, 1 if shared else 0,
+                                        _stream(stream)))
+
+
+def lfdpr_version() -> int:
+    return int(lib().lfdpr_version())
+
+
+# ---------------------------------------------------------------------------
+# Owning wrappers (destroy on close)
+# ---------------------------------------------------------------------------
+
+class Renderer:
+    """One display and one mesh on the current CUDA device."""
+
+    def __init__(self, display, scene, max_points: int = 0, stream=None):
+        self.display = display
+        self.disp = lfdpr_create_display(desc_of(display, max_points))
+        self.mesh = None
+        try:
+            self.mesh = lfdpr_upload_mesh(self.disp, scene.xyz, scene.uv, scene.idx,
+                                          scene.tri_tex, scene.textures, stream)
+        except Exception:
+            lfdpr_destroy_display(self.disp)
+            raise
+
+    def render(self, model: np.ndarray, stream=None):
+        lfdpr_render_frame(self.disp, self.mesh, model, stream)
+
+    def interleave(self, panel_ptr: int, stream=None):
+        lfdpr_interleave(self.disp, panel_ptr, stream)
+
+    def stats(self, stream=None) -> Stats:
+        return lfdpr_frame_stats(self.disp, stream)
+
+    def set_stage_timing(self, enable: bool):
+        lfdpr_set_stage_timing(self.disp, enable)
+
+    def buffers(self) -> Buffers:
+        return lfdpr_get_buffers(self.disp, self.mesh)
+
+    def eyes(self) -> np.ndarray:
+        return lfdpr_view_eyes(self.disp, self.display.n_render_views)
+
+    def close(self):
+        if self.mesh is not None:
+            lfdpr_destroy_mesh(self.mesh)
+            self.mesh = None
+        if self.disp is not None:
+            lfdpr_destroy_display(self.disp)
+            self.disp = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """Describes library-owned device memory to torch (__cuda_array_interface__)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, dtype):
+    """A torch tensor aliasing device memory at `ptr` (no copy). 64-bit
+    unsigned buffers are exposed as int64 (view the numpy copy as uint64)."""
+    import torch
+    dt = np.dtype(dtype)
+    if dt == np.uint64:
+        dt = np.dtype(np.int64)
+    if dt == np.uint32:
+        dt = np.dtype(np.int32)
+    return torch.as_tensor(_DeviceArray(ptr, shape, dt.str), device="cuda")
+
+
+def device_to_numpy(ptr: int, shape, dtype) -> np.ndarray:
+    return device_view(ptr, shape, dtype).cpu().numpy().view(dtype).reshape(shape)

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs (tolerances in tests/parity.py)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_19901_gb300 import lfdpr, scenes as S
+
+from parity import check_sampling, check_views, gpu_frame, psnr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_19901_gb300 import build
+    build.build()
+    lfdpr.lib()
+
+
+def mini_paper_scene(seed=3):
+    """Paper-shaped scene at a size the oracle renders in seconds: 6 instances
+    of 2 x 20^2 triangles (4,800 triangles: 18 full set-up blocks and a ragged
+    tail), textures 16^2 .. 512^2."""
+    return S.scene_paper(n_instances=6, res=20, n_textures=6, max_tex=512, min_tex=16, seed=seed,
+                         r_max=0.6)
+
+
+def mini_paper_display(ss=False):
+    d = S.display_angular_ss() if ss else S.display_paper()
+    return replace(d, view_w=105, view_h=140, panel_w=640, panel_h=400)
+
+
+def full_check(d, sc, model, views=None):
+    o = O.render(d, sc, model)
+    g = gpu_frame(d, sc, model)
+    assert np.array_equal(g.eyes.view(np.uint32), O.eyes(d).view(np.uint32)), "eye positions"
+    assert g.stats.overflow == 0 and g.stats.n_points == len(o.points)
+    check_sampling(g, o)
+    agree, p = check_views(g, o)
+    # interleave: bit-exact on the same views, and close to the oracle's panel
+    assert np.array_equal(g.panel, O.interleave(d, g.views))
+    assert psnr(g.panel, o.panel) >= 50.0
+    return g, o, agree
+
+
+@pytest.mark.parametrize("frame", [0, 7])
+def test_tiny_scene_full_frame(frame):
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    g, o, agree = full_check(d, sc, S.model_matrix(frame))
+    assert g.stats.n_live_tris == int((o.tri[:, O.F["live"]] == 1).sum())
+
+
+@pytest.mark.parametrize("frame", [0, 3])
+def test_paper_shaped_mini_full_frame(frame):
+    d = mini_paper_display()
+    sc = mini_paper_scene()
+    full_check(d, sc, S.model_matrix(frame))
+
+
+def test_angular_supersampling_mini_full_frame():
+    d = mini_paper_display(ss=True)
+    assert d.n_render_views == 96 and d.crosstalk == 0.15
+    sc = mini_paper_scene(seed=5)
+    full_check(d, sc, S.model_matrix(2))
+
+
+def test_several_frames_on_one_renderer_match_fresh_frames():
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    with lfdpr.Renderer(d, sc) as R:
+        for frame in (1, 40, 2):
+            m = S.model_matrix(frame)
+            g = gpu_frame(d, sc, m, renderer=R)
+            o = O.render(d, sc, m, panel=False)
+            check_sampling(g, o)
+            check_views(g, o)
+
+
+def test_host_panel_equals_device_panel():
+    import torch
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    with lfdpr.Renderer(d, sc) as R:
+        s = torch.cuda.current_stream()
+        R.render(S.model_matrix(3), s)
+        dev = torch.zeros((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
+        R.interleave(dev.data_ptr(), s)
+        host = torch.zeros((d.panel_h, d.panel_w, 4), dtype=torch.uint8).pin_memory()
+        R.interleave(host.data_ptr(), s)
+        pageable = np.zeros((d.panel_h, d.panel_w, 4), np.uint8)
+        R.interleave(pageable.ctypes.data, s)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), host.numpy())
+        assert np.array_equal(host.numpy(), pageable)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def tri_scene(tris, uvs=None, tex=None):
+    tris = np.asarray(tris, np.float32).reshape(-1, 3, 3)
+    n = len(tris)
+    uv = np.tile(np.array([[0, 0], [1, 0], [0, 1]], np.float32), (n, 1)) if uvs is None \
+        else np.asarray(uvs, np.float32).reshape(-1, 2)
+    t = tex if tex is not None else S.value_noise_texture(64, 64, 7)
+    return S.Scene(xyz=tris.reshape(-1, 3), uv=uv, idx=np.arange(3 * n, dtype=np.uint32).reshape(n, 3),
+                   tri_tex=np.zeros(n, np.uint32), textures=[t])
+
+
+def test_empty_mesh():
+    d = S.display_tiny()
+    sc = S.Scene(xyz=np.zeros((0, 3), np.float32), uv=np.zeros((0, 2), np.float32),
+                 idx=np.zeros((0, 3), np.uint32), tri_tex=np.zeros(0, np.uint32),
+                 textures=[S.value_noise_texture(8, 8, 1)])
+    g = gpu_frame(d, sc, S.model_matrix(0))
+    assert g.stats.n_points == 0
+    assert np.all(g.keys == np.uint64(0xFFFFFFFFFFFFFFFF)) and np.all(g.views == 0)
+    assert np.all(g.panel[..., :3] == 0) and np.all(g.panel[..., 3] == 255)
+
+
+def test_all_culled_and_degenerate_triangles():
+    d = S.display_tiny()
+    tris = [[[-50, 0, 0], [-49, 0, 0], [-50, 1, 0]],            # outside every view
+            [[0, 0, 10], [1, 0, 10], [0, 1, 10]],                # behind the eyes
+            [[0, 0, 0], [0.2, 0.2, 0], [0.4, 0.4, 0]],           # zero area
+            [[0.1, 0.1, 0], [0.1, 0.1, 0], [0.1, 0.1, 0]],       # a point
+            [[-0.3, -0.2, 0.1], [0.3, -0.2, 0.0], [0.0, 0.4, 0.2]]]  # ordinary, degenerate UVs below
+    uvs = np.array([[0, 0], [1, 0], [0, 1]] * 4 + [[0.5, 0.5]] * 3, np.float32)
+    sc = tri_scene(tris, uvs=uvs)
+    m = np.eye(4, dtype=np.float32)
+    o = O.render(d, sc, m)
+    g = gpu_frame(d, sc, m)
+    assert list(g.counts[:4]) == [0, 0, 0, 0] and g.counts[4] > 0
+    check_sampling(g, o)
+    check_views(g, o)
+
+
+def test_overflow_reported_then_recovers():
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    m = S.model_matrix(0)
+    need = int(O.setup(d, sc, m)[2].sum())
+    with lfdpr.Renderer(d, sc, max_points=need - 1) as R:
+        R.render(m)
+        with pytest.raises(lfdpr.LfdprError) as e:
+            R.stats()
+        assert e.value.status == lfdpr.EOVERFLOW
+    g = gpu_frame(d, sc, m, max_points=need)
+    assert g.stats.n_points == need
+
+
+@pytest.mark.parametrize("case", ["index", "texture_id", "nan_vertex", "npot_texture", "no_texture"])
+def test_invalid_mesh_rejected(case):
+    d = S.display_tiny()
+    sc = S.scene_tiny()
+    xyz, uv, idx, tt, tex = sc.xyz.copy(), sc.uv.copy(), sc.idx.copy(), sc.tri_tex.copy(), list(sc.textures)
+    if case == "index":
+        idx[5, 1] = len(xyz)
+    elif case == "texture_id":
+        tt[3] = 1
+    elif case == "nan_vertex":
+        xyz[2, 0] = np.nan
+    elif case == "npot_texture":
+        tex = [np.zeros((48, 64, 4), np.uint8)]
+    elif case == "no_texture":
+        tex = []
+    disp = lfdpr.lfdpr_create_display(lfdpr.desc_of(d))
+    try:
+        with pytest.raises(lfdpr.LfdprError) as e:
+            lfdpr.lfdpr_upload_mesh(disp, xyz, uv, idx, tt, tex)
+        assert e.value.status == lfdpr.EINVAL
+    finally:
+        lfdpr.lfdpr_destroy_display(disp)
+
+
+def test_nonfinite_model_rejected():
+    d = S.display_tiny()
+    with lfdpr.Renderer(d, S.scene_tiny()) as R:
+        m = S.model_matrix(0)
+        m[1, 3] = np.inf
+        with pytest.raises(lfdpr.LfdprError) as e:
+            R.render(m)
+        assert e.value.status == lfdpr.EINVAL
