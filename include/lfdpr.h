@@ -94,6 +94,7 @@ typedef struct {
     int32_t overflow;       /* 1 if n_points exceeded max_points (frame not drawn) */
     int32_t cell_overflow;  /* 1 if a triangle needed more than 65535 lattice columns or rows */
     int64_t kernel_launches;/* kernels this display has launched since its creation */
+    int64_t n_splat_writes; /* depth-test atomics (accepted pixel tests) of the last splat */
     float stage_ms[LFDPR_N_STAGES]; /* device time of each stage of the last frame and
                                        interleave, from CUDA events on the caller's
                                        stream; 0 unless lfdpr_set_stage_timing(.., 1) */

@@ -48,6 +48,8 @@ struct Counters {
     uint32_t overflow;
     uint32_t cell_overflow;
     uint32_t n_live;
+    uint32_t n_writes;    // depth-test atomics the splat issued
+    uint32_t pad[3];
 };
 
 // One triangle's sampling record: 8 float4 (layout = LFDPR_TRI_* in lfdpr.h).

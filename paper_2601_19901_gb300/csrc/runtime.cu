@@ -442,6 +442,7 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display* disp, void* stream, lfdpr_stats* o
         out->overflow = int32_t(c.overflow);
         out->cell_overflow = int32_t(c.cell_overflow);
         out->kernel_launches = disp->launches;
+        out->n_splat_writes = c.n_writes;
         for (int k = 0; k < LFDPR_N_STAGES; k++) out->stage_ms[k] = 0.0f;
         if (disp->ev_frame)
             for (int k = 0; k < LFDPR_STAGE_INTERLEAVE; k++)

@@ -28,80 +28,196 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
-__global__ void __launch_bounds__(256) k_splat(FrameArgs a) {
-    if (a.ctr->overflow) return;
+// Plane-space form of the per-pixel test (the oracle's formula): the pixel
+// centre's ray meets the triangle's plane at t; accept iff the hit lies in
+// the half-open cell and in the closed triangle and t D is in [near, far].
+// Used for the rare points whose cell or triangle reaches the eyes' plane,
+// where the screen-space form below does not apply; the box is the whole view.
+__device__ __noinline__ uint32_t splat_exact(const FrameArgs& a, uint32_t p, int i, int j, int v,
+                                             const float4& q0, const float4& q1, const float4& q2,
+                                             const float4& q3, const float4& q4) {
     const DispConst& c = a.dc;
-    const uint64_t n_pairs = (uint64_t)a.ctr->n_points * (uint64_t)c.nr;
-    const uint64_t npix = (uint64_t)c.W * c.H;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs;
-         q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = uint32_t(q / (uint32_t)c.nr);
-        const int v = int(q - (uint64_t)p * (uint32_t)c.nr);
+    const float Ex = __ldg(a.ex + v);
+    const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
+    const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
+    const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
+    const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
+    unsigned long long* kv = reinterpret_cast<unsigned long long*>(a.keys) + (uint64_t)v * c.W * c.H;
+    uint32_t writes = 0;
+    for (int y = 0; y < c.H; y++) {
+        const float Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
+        for (int x = 0; x < c.W; x++) {
+            const float Fx = fmaf(float(x) + 0.5f, c.pw, c.x0);
+            const float dx = Fx - Ex, dy = Fy - 0.0f, dz = -c.D;
+            const float den = dot3(q3.x, q3.y, q3.z, dx, dy, dz);
+            if (den == 0.0f) continue;
+            const float t = __fdiv_rn(num, den);
+            const float depth = t * c.D;
+            if (!(depth >= c.near_z && depth <= c.far_z)) continue;
+            const float hx = fmaf(t, dx, qEx), hy = fmaf(t, dy, qEy), hz = fmaf(t, dz, qEz);
+            const float uq = dot3(hx, hy, hz, q1.x, q1.y, q1.z);
+            const float vq = dot3(hx, hy, hz, q2.x, q2.y, q2.z);
+            const float u = uq - q2.w, vv = vq - q3.w;
+            if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) continue;
+            const float w0 = edge_fn(q4.x, q4.y, q4.z, q4.w, uq, vq);
+            const float w1 = edge_fn(q4.z, q4.w, 0.0f, 0.0f, uq, vq);
+            const float w2 = edge_fn(0.0f, 0.0f, q4.x, q4.y, uq, vq);
+            if (!inside_either(w0, w1, w2)) continue;
+            atomicMin(kv + (uint64_t)y * c.W + x, ((unsigned long long)__float_as_uint(t) << 32) | p);
+            writes++;
+        }
+    }
+    return writes;
+}
+
+// Screen-space edge function of the directed segment (px, py) -> (qx, qy) at (x, y).
+__device__ __forceinline__ float sedge(float px, float py, float qx, float qy, float x, float y) {
+    return fmaf(qx - px, y - py, -((qy - py) * (x - px)));
+}
+
+// One thread per point, looping over the rendered views. Every eye lies on
+// y = 0, z = D, so a world point C projects to pixel coordinates
+//   qx = A + B Ex,  qy (the same in every view),
+// with s = D / (D - C.z), A = (C.x s - x0) W/fw, B = (1 - s) W/fw,
+// qy = (y0 - C.y s) H/fh: the cell's four corners and the triangle's three
+// vertices are projected once per point and then cost one fma per view. The
+// per-pixel test uses edge functions of the projected cell (half-open: the
+// u = i and v = j sides included, the u = i+1 and v = j+1 sides excluded, so
+// neighbouring cells, which share bit-identical corners, partition their
+// triangle's pixels) and of the projected triangle (closed). The orientation
+// sign is the side of the triangle's plane the eye is on. The ray parameter t
+// is divided out only for accepted pixels, by the plane-space formula.
+__global__ void __launch_bounds__(256) k_splat(FrameArgs a) {
+    __shared__ float s_ex[kMaxRenderViews];
+    const DispConst& c = a.dc;
+    for (int v = threadIdx.x; v < c.nr; v += blockDim.x) s_ex[v] = a.ex[v];
+    __syncthreads();
+    if (a.ctr->overflow) return;
+    const uint32_t n = a.ctr->n_points;
+    const float W1 = float(c.W - 1), H1 = float(c.H - 1);
+    uint32_t writes = 0;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
-        const TriRec* r = a.rec + pt.x;
+        const uint32_t tri = pt.x;
+        const TriRec* r = a.rec + tri;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
         const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
-        const float Ex = __ldg(a.ex + v);
 
-        // conservative pixel box of the projected cell
-        int bx0 = 0, bx1 = c.W - 1, by0 = 0, by1 = c.H - 1;
+        // cell corners 00, 10, 11, 01 and triangle vertices, projected per point
+        float cA[4], cB[4], cY[4], tA[3], tB[3], tY[3];
+        bool behind = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float C[3];
+            cell_corner(q0, q1, q2, q3, i + (k == 1 || k == 2), j + (k >= 2), C);
+            const float dep = c.D - C[2];
+            behind |= !(dep > 1e-4f * c.D);
+            const float s = __fdiv_rn(c.D, dep);
+            cA[k] = fmaf(C[0], s, -c.x0) * c.ipw;
+            cB[k] = (1.0f - s) * c.ipw;
+            cY[k] = (c.y0 - C[1] * s) * c.iph;
+        }
+        float zmin = INFINITY, zmax = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t vi = __ldg(a.idx + 3 * (size_t)tri + k);
+            const float x = __ldg(a.xyz + 3 * (size_t)vi), y = __ldg(a.xyz + 3 * (size_t)vi + 1),
+                        z = __ldg(a.xyz + 3 * (size_t)vi + 2);
+            const float* m = a.model;
+            const float X = fmaf(m[0], x, fmaf(m[1], y, fmaf(m[2], z, m[3])));
+            const float Y = fmaf(m[4], x, fmaf(m[5], y, fmaf(m[6], z, m[7])));
+            const float Z = fmaf(m[8], x, fmaf(m[9], y, fmaf(m[10], z, m[11])));
+            zmin = fminf(zmin, Z);
+            zmax = fmaxf(zmax, Z);
+            const float dep = c.D - Z;
+            behind |= !(dep > 1e-4f * c.D);
+            const float s = __fdiv_rn(c.D, dep);
+            tA[k] = fmaf(X, s, -c.x0) * c.ipw;
+            tB[k] = (1.0f - s) * c.ipw;
+            tY[k] = (c.y0 - Y * s) * c.iph;
+        }
+        // every hit on the triangle has depth D - z within [near, far]?
+        const bool depth_ok = (c.D - zmax) >= c.near_z && (c.D - zmin) <= c.far_z;
+        // the cell inside the closed triangle: no triangle-edge test needed
+        bool interior;
         {
-            float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
-            bool behind = false;
+            const float u0 = float(i) * q0.w + q2.w, u1 = float(i + 1) * q0.w + q2.w;
+            const float v0 = float(j) * q1.w + q3.w, v1 = float(j + 1) * q1.w + q3.w;
+            interior = true;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                float C[3];
-                cell_corner(q0, q1, q2, q3, i + (k == 1 || k == 2), j + (k >= 2), C);
-                const float dep = c.D - C[2];
-                if (!(dep > 1e-6f)) { behind = true; break; }
-                const float s = __fdiv_rn(c.D, dep);
-                const float qx = (fmaf(C[0] - Ex, s, Ex) - c.x0) * c.ipw;
-                const float qy = (c.y0 - C[1] * s) * c.iph;
-                mnx = fminf(mnx, qx); mxx = fmaxf(mxx, qx);
-                mny = fminf(mny, qy); mxy = fmaxf(mxy, qy);
-            }
-            if (!behind) {
-                const float fx0 = ceilf(mnx - 0.5f - kBoxPad), fx1 = floorf(mxx - 0.5f + kBoxPad);
-                const float fy0 = ceilf(mny - 0.5f - kBoxPad), fy1 = floorf(mxy - 0.5f + kBoxPad);
-                if (fx1 < 0.0f || fy1 < 0.0f || fx0 > float(c.W - 1) || fy0 > float(c.H - 1)) continue;
-                bx0 = fx0 < 0.0f ? 0 : int(fx0);
-                bx1 = fx1 > float(c.W - 1) ? c.W - 1 : int(fx1);
-                by0 = fy0 < 0.0f ? 0 : int(fy0);
-                by1 = fy1 > float(c.H - 1) ? c.H - 1 : int(fy1);
+                const float uu = (k == 1 || k == 2) ? u1 : u0, vv = k >= 2 ? v1 : v0;
+                interior &= edge_fn(q4.x, q4.y, q4.z, q4.w, uu, vv) >= 0.0f &&
+                            edge_fn(q4.z, q4.w, 0.0f, 0.0f, uu, vv) >= 0.0f &&
+                            edge_fn(0.0f, 0.0f, q4.x, q4.y, uu, vv) >= 0.0f;
             }
         }
+        const float ymin = fminf(fminf(cY[0], cY[1]), fminf(cY[2], cY[3]));
+        const float ymax = fmaxf(fmaxf(cY[0], cY[1]), fmaxf(cY[2], cY[3]));
+        const float fy0 = ceilf(ymin - 0.5f - kBoxPad), fy1 = floorf(ymax - 0.5f + kBoxPad);
+        if (fy1 < 0.0f || fy0 > H1) continue;
+        const int y0 = fy0 < 0.0f ? 0 : int(fy0), y1 = fy1 > H1 ? c.H - 1 : int(fy1);
+        // n . (E - P0) = n.x Ex + kn
+        const float kn = fmaf(q3.y, 0.0f - q0.y, q3.z * (c.D - q0.z)) - q3.x * q0.x;
 
-        const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
-        const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-        const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
-        const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
-        unsigned long long* kv = reinterpret_cast<unsigned long long*>(a.keys) + (uint64_t)v * npix;
-        for (int y = by0; y <= by1; y++) {
-            const float Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
-            for (int x = bx0; x <= bx1; x++) {
-                const float Fx = fmaf(float(x) + 0.5f, c.pw, c.x0);
-                const float dx = Fx - Ex, dy = Fy - 0.0f, dz = -c.D;
-                const float den = dot3(q3.x, q3.y, q3.z, dx, dy, dz);
-                if (den == 0.0f) continue;
-                const float t = __fdiv_rn(num, den);
-                const float depth = t * c.D;
-                if (!(depth >= c.near_z && depth <= c.far_z)) continue;
-                const float hx = fmaf(t, dx, qEx), hy = fmaf(t, dy, qEy), hz = fmaf(t, dz, qEz);
-                const float uq = dot3(hx, hy, hz, q1.x, q1.y, q1.z);
-                const float vq = dot3(hx, hy, hz, q2.x, q2.y, q2.z);
-                const float u = uq - q2.w, vv = vq - q3.w;
-                if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) continue;
-                const float w0 = edge_fn(q4.x, q4.y, q4.z, q4.w, uq, vq);
-                const float w1 = edge_fn(q4.z, q4.w, 0.0f, 0.0f, uq, vq);
-                const float w2 = edge_fn(0.0f, 0.0f, q4.x, q4.y, uq, vq);
-                if (!inside_either(w0, w1, w2)) continue;
-                const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)p;
-                atomicMin(kv + (uint64_t)y * c.W + x, key);
+        for (int v = 0; v < c.nr; v++) {
+            if (behind) {
+                writes += splat_exact(a, p, i, j, v, q0, q1, q2, q3, q4);
+                continue;
+            }
+            const float Ex = s_ex[v];
+            float X[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) X[k] = fmaf(cB[k], Ex, cA[k]);
+            const float xmin = fminf(fminf(X[0], X[1]), fminf(X[2], X[3]));
+            const float xmax = fmaxf(fmaxf(X[0], X[1]), fmaxf(X[2], X[3]));
+            const float fx0 = ceilf(xmin - 0.5f - kBoxPad), fx1 = floorf(xmax - 0.5f + kBoxPad);
+            if (fx1 < 0.0f || fx0 > W1 || fx0 > fx1) continue;
+            const float nE = fmaf(q3.x, Ex, kn);
+            if (nE == 0.0f) continue;                 // plane seen edge-on
+            const float sg = nE > 0.0f ? 1.0f : -1.0f;
+            const int x0 = fx0 < 0.0f ? 0 : int(fx0), x1 = fx1 > W1 ? c.W - 1 : int(fx1);
+            float TX[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) TX[k] = fmaf(tB[k], Ex, tA[k]);
+            // plane-space ray set-up for the depth key (the oracle's formula)
+            const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
+            const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
+            unsigned long long* kv = reinterpret_cast<unsigned long long*>(a.keys) + (uint64_t)v * c.W * c.H;
+            for (int y = y0; y <= y1; y++) {
+                const float py = float(y) + 0.5f;
+                for (int x = x0; x <= x1; x++) {
+                    const float px = float(x) + 0.5f;
+                    const float eL = sg * sedge(X[0], cY[0], X[3], cY[3], px, py);
+                    const float eR = sg * sedge(X[1], cY[1], X[2], cY[2], px, py);
+                    const float eB = sg * sedge(X[0], cY[0], X[1], cY[1], px, py);
+                    const float eT = sg * sedge(X[3], cY[3], X[2], cY[2], px, py);
+                    if (!(eL >= 0.0f && eR < 0.0f && eB <= 0.0f && eT > 0.0f)) continue;
+                    if (!interior) {
+                        const float t0 = sg * sedge(TX[0], tY[0], TX[1], tY[1], px, py);
+                        const float t1 = sg * sedge(TX[1], tY[1], TX[2], tY[2], px, py);
+                        const float t2 = sg * sedge(TX[2], tY[2], TX[0], tY[0], px, py);
+                        if (!(t0 <= 0.0f && t1 <= 0.0f && t2 <= 0.0f)) continue;
+                    }
+                    const float Fx = fmaf(px, c.pw, c.x0), Fy = fmaf(py, -c.ph, c.y0);
+                    const float den = dot3(q3.x, q3.y, q3.z, Fx - Ex, Fy - 0.0f, -c.D);
+                    const float t = __fdiv_rn(num, den);
+                    if (!(t > 0.0f)) continue;
+                    if (!depth_ok) {
+                        const float depth = t * c.D;
+                        if (!(depth >= c.near_z && depth <= c.far_z)) continue;
+                    }
+                    atomicMin(kv + (uint64_t)y * c.W + x, ((unsigned long long)__float_as_uint(t) << 32) | p);
+                    writes++;
+                }
             }
         }
     }
+    // warp-aggregated count of depth-test writes (the atomics issued)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
+    if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
 }
 
 __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {

@@ -54,6 +54,7 @@ STAGES = ["setup", "scan", "emit", "fetch", "clear", "splat", "resolve", "interl
 class Stats(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("n_live_tris", C.c_int64), ("overflow", C.c_int32),
                 ("cell_overflow", C.c_int32), ("kernel_launches", C.c_int64),
+                ("n_splat_writes", C.c_int64),
                 ("stage_ms", C.c_float * N_STAGES)]
 
 
@@ -262,7 +263,7 @@ class _DeviceArray:
 
     def __init__(self, ptr: int, shape, typestr: str):
         self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def device_view(ptr: int, shape, dtype):
