@@ -208,7 +208,7 @@ def atomic_peak(n_words, sm_stream):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_2601_19901_gb300 import build as B, lfdpr, scenes as S
+    from paper_2601_19901_gb300 import build as B, lfdpr, multigpu, scenes as S
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -232,10 +232,11 @@ def run_ours(args):
     R.set_stage_timing(True)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
-    frame0 = rank * 100000
+    frames = multigpu.rank_frames(rank, world, args.warmup + args.steps)
+    e2e_frames = multigpu.rank_frames(rank, world, max(3, args.steps // 2), start=50000)
 
     def frame_model(k):
-        return S.model_matrix(frame0 + k)
+        return S.model_matrix(frames[k])
 
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
@@ -278,14 +279,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = R.stats(stream).kernel_launches - launches0
     clk = clocks.stop()
-    total_ms = sum(step_ms)
+    total_ms = multigpu.max_over_ranks(sum(step_ms), device="cuda")
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = multigpu.job_rate(world, args.steps, total_ms / 1000.0)
     P = statistics.mean(n_points)
 
     # e2e: the public API with host buffers (model matrix in, panel out to pinned memory)
@@ -294,21 +292,18 @@ def run_ours(args):
         host_panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8).pin_memory()
         model_host = torch.empty((4, 4), dtype=torch.float32).pin_memory()
         e2e_s = 0.0
-        n_e2e = max(3, args.steps // 2)
+        n_e2e = len(e2e_frames)
         for k in range(n_e2e):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 255)
             torch.cuda.synchronize()
-            model_host.copy_(torch.from_numpy(frame_model(10000 + k)))
+            model_host.copy_(torch.from_numpy(S.model_matrix(e2e_frames[k])))
             t0 = time.perf_counter()
             R.render(model_host.numpy(), stream)
             R.interleave(host_panel.data_ptr(), stream)   # copies to host and waits
             e2e_s += time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n_e2e / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": 64,
+        e2e_s = multigpu.max_over_ranks(e2e_s, device="cuda")
+        e2e = {"value": multigpu.job_rate(world, n_e2e, e2e_s), "unit": "frames/s", "h2d_bytes_per_step": 64,
                "d2h_bytes_per_step": 4 * d.panel_w * d.panel_h}
 
     if rank != 0:

@@ -404,8 +404,12 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
         float e1[3], e2[3], cr[3];
         for (int c = 0; c < 3; c++) { e1[c] = P[1][c] - P[0][c]; e2[c] = P[2][c] - P[0][c]; }
         cross3(e1, e2, cr);
-        float len = sqrtf(dot3(cr, cr));
-        if (!(len > 0.0f) || !isfinite(len)) continue;  /* zero-area: no points */
+        float len2 = dot3(cr, cr);
+        float len = sqrtf(len2);
+        /* zero area: no points. Collinear vertices can leave a cross product of
+         * rounding size, so an area below 2^-20 |e1| |e2| / 2 (the sine of the
+         * vertex angle below 2^-20) counts as zero. */
+        if (!(len2 > 0x1p-40f * (dot3(e1, e1) * dot3(e2, e2))) || !isfinite(len)) continue;
         float n[3] = {cr[0] / len, cr[1] / len, cr[2] / len};
         float A_ws = 0.5f * len;
 

@@ -130,8 +130,12 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
     const float crx = fmaf(e1[1], e2[2], -(e1[2] * e2[1]));
     const float cry = fmaf(e1[2], e2[0], -(e1[0] * e2[2]));
     const float crz = fmaf(e1[0], e2[1], -(e1[1] * e2[0]));
-    const float len = __fsqrt_rn(dot3(crx, cry, crz, crx, cry, crz));
-    if (!(len > 0.0f) || isinf(len)) return res;
+    const float len2 = dot3(crx, cry, crz, crx, cry, crz);
+    const float len = __fsqrt_rn(len2);
+    // zero area (up to rounding: vertex-angle sine below 2^-20) emits no points
+    const float e11 = dot3(e1[0], e1[1], e1[2], e1[0], e1[1], e1[2]);
+    const float e22 = dot3(e2[0], e2[1], e2[2], e2[0], e2[1], e2[2]);
+    if (!(len2 > 0x1p-40f * (e11 * e22)) || isinf(len)) return res;
     const float nx = __fdiv_rn(crx, len), ny = __fdiv_rn(cry, len), nz = __fdiv_rn(crz, len);
     const float A_ws = 0.5f * len;
 
