@@ -236,6 +236,43 @@ lfdpr_status lfdpr_probe_atomic_min(uint64_t *words, uint64_t n_words, const uin
                                     const uint64_t *val, uint64_t n_ops, int32_t shared,
                                     void *stream);
 
+/*
+ * lfdpr_sample_points_noalloc: the point-generation stage alone (per-triangle
+ * set-up and count, scan, emission; the steps of lfdpr_render_frame before the
+ * texture fetch) for callers that must not allocate. The paper has no
+ * counterpart: it exists because some callers cannot call cudaMalloc, or any
+ * routine that allocates, while they run - a real-time render loop that only
+ * allocates at start-up, or a plug-in whose host application owns all device
+ * memory and its budget. This call allocates nothing: its scratch (triangle
+ * records, first-point offsets, block sums, counters, eye positions, texture
+ * sizes) is one fixed file-scope device array of about 4.3 MB, held by every
+ * GPU that loads the library until the process exits.
+ *  desc, model, tex_wh  host: display, row-major 4x4 model matrix, (w, h) of
+ *                       each of the n_tex textures (powers of two <= 16384)
+ *  xyz, uv, idx, tri_tex  device, caller-owned, layouts as lfdpr_upload_mesh;
+ *                       indices and texture ids must be in range (not checked)
+ *  points   device u32 [max_points][4]: words 0-1 of each point receive
+ *           triangle id and i | j << 16 (words 2-3 are left untouched)
+ *  counts   device u32 [n_tris]: points per triangle
+ *  frame_counters  device u32 [4]: points needed, overflow flag (points beyond
+ *           max_points are not written), lattice-overflow flag, live triangles
+ * Limits: n_tris <= LFDPR_NOALLOC_MAX_TRIS, 1 <= n_tex <= LFDPR_NOALLOC_MAX_TEX;
+ * larger sizes return EINVAL with a message. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call shares
+ * the one array, which keeps the last call's contents (the counters are
+ * cleared by each call): calls that overlap on the GPU, from any stream or
+ * thread, race. Asynchronous on `stream`. Errors: EINVAL, EDEVICE, ECUDA.
+ */
+#define LFDPR_NOALLOC_MAX_TRIS 32768
+#define LFDPR_NOALLOC_MAX_TEX 256
+lfdpr_status lfdpr_sample_points_noalloc(const lfdpr_display_desc *desc, const float model[16],
+                                         const float *xyz, const float *uv, const uint32_t *idx,
+                                         const uint32_t *tri_tex, uint32_t n_tris,
+                                         const uint32_t *tex_wh, uint32_t n_tex, uint32_t *points,
+                                         uint32_t max_points, uint32_t *counts,
+                                         uint32_t *frame_counters, void *stream);
+
 /* Description of the last error on this thread ("" if none). */
 const char *lfdpr_last_error(void);
 

@@ -117,6 +117,9 @@ __device__ __forceinline__ uint8_t round_u8(float v) {
     return (uint8_t)r;
 }
 
+// Per-thread description of the last error, read by lfdpr_last_error().
+__attribute__((visibility("hidden"))) extern thread_local char g_last_error[512];
+
 // ---------------------------------------------------------------------------
 // Launchers (host side, defined next to their kernels)
 // ---------------------------------------------------------------------------

@@ -50,9 +50,13 @@ struct lfdpr_mesh {
     uint32_t* block_sums = nullptr;
 };
 
+namespace lfdpr {
+thread_local char g_last_error[512] = "";
+}
+
 namespace {
 
-thread_local char g_err[512] = "";
+#define g_err lfdpr::g_last_error
 
 lfdpr_status fail(lfdpr_status s, const char* fmt, ...) {
     va_list ap;

@@ -28,7 +28,7 @@ TRI = dict(P0=0, s_u=3, eu=4, s_v=7, ev=8, umin=11, n=12, vmin=15, a1=16, b1=17,
 EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_destroy_mesh", "lfdpr_render_frame", "lfdpr_interleave", "lfdpr_frame_stats",
            "lfdpr_get_buffers", "lfdpr_view_eyes", "lfdpr_probe_atomic_min", "lfdpr_last_error",
-           "lfdpr_version", "lfdpr_set_stage_timing"]
+           "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc"]
 
 
 class LfdprError(RuntimeError):
@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
         L.lfdpr_get_buffers.argtypes = [P, P, C.POINTER(Buffers)]
         L.lfdpr_view_eyes.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_stage_timing.argtypes = [P, C.c_int32]
+        L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
+                                                  P, C.c_uint32, P, C.c_uint32, P, P, P]
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
         for name in EXPORTS:
             fn = getattr(L, name)
@@ -195,6 +197,26 @@ def lfdpr_probe_atomic_min(words_ptr: int, n_words: int, idx_ptr: int, val_ptr: 
     _check(lib().lfdpr_probe_atomic_min(C.c_void_p(words_ptr), n_words, C.c_void_p(idx_ptr),
                                         C.c_void_p(val_ptr), n_ops, 1 if shared else 0,
                                         _stream(stream)))
+
+
+NOALLOC_MAX_TRIS = 32768
+NOALLOC_MAX_TEX = 256
+
+
+def lfdpr_sample_points_noalloc(desc: DisplayDesc, model: np.ndarray, xyz_ptr: int, uv_ptr: int,
+                                idx_ptr: int, tri_tex_ptr: int, n_tris: int, tex_wh: np.ndarray,
+                                points_ptr: int, max_points: int, counts_ptr: int,
+                                frame_counters_ptr: int, stream=None):
+    """Point generation into caller-owned device buffers, allocating nothing
+    (see include/lfdpr.h). Pointers are device addresses (e.g. data_ptr())."""
+    m = np.ascontiguousarray(model, np.float32).ravel()
+    wh = np.ascontiguousarray(tex_wh, np.uint32).ravel()
+    _check(lib().lfdpr_sample_points_noalloc(C.byref(desc), _ptr(m), C.c_void_p(xyz_ptr),
+                                             C.c_void_p(uv_ptr), C.c_void_p(idx_ptr),
+                                             C.c_void_p(tri_tex_ptr), n_tris, _ptr(wh), len(wh) // 2,
+                                             C.c_void_p(points_ptr), max_points,
+                                             C.c_void_p(counts_ptr), C.c_void_p(frame_counters_ptr),
+                                             _stream(stream)))
 
 
 def lfdpr_version() -> int:
