@@ -97,11 +97,19 @@ static float edge2(float px, float py, float rx, float ry, float qx, float qy) {
     return fmaf(rx - px, qy - py, -((ry - py) * (qx - px)));
 }
 
-/* Squared distance from q to segment p-r. */
-static float segd2(float px, float py, float rx, float ry, float qx, float qy) {
-    float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+/* Reciprocal squared length of segment p-r (0 for a zero-length segment). */
+static float seg_inv_len2(float px, float py, float rx, float ry) {
+    float ex = rx - px, ey = ry - py;
     float ee = fmaf(ex, ex, ey * ey);
-    float t = ee > 0.0f ? fmaf(wx, ex, wy * ey) / ee : 0.0f;
+    return ee > 0.0f ? 1.0f / ee : 0.0f;
+}
+
+/* Squared distance from q to segment p-r; inv_ee = seg_inv_len2(p, r). The
+ * closest point's parameter along the segment is (q-p).(r-p) / |r-p|^2,
+ * clamped to [0, 1]. */
+static float segd2(float px, float py, float rx, float ry, float inv_ee, float qx, float qy) {
+    float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+    float t = fmaf(wx, ex, wy * ey) * inv_ee;
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     float dx = fmaf(-t, ex, wx), dy = fmaf(-t, ey, wy);
     return fmaf(dx, dx, dy * dy);
@@ -450,6 +458,8 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
          * eye). The eye's distance to the triangle: its height over the plane
          * and its in-plane distance to the 2-D triangle. */
         float d2min = INFINITY, d2max = -INFINITY;
+        float ie01 = seg_inv_len2(0.0f, 0.0f, a1, b1), ie12 = seg_inv_len2(a1, b1, a2, b2);
+        float ie20 = seg_inv_len2(a2, b2, 0.0f, 0.0f);
         for (int v = 0; v < nr; v++) {
             float q[3] = {ex[v] - P[0][0], 0.0f - P[0][1], D - P[0][2]};
             float qu = dot3(q, eu), qv = dot3(q, ev), h = dot3(q, n);
@@ -458,8 +468,8 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
             float w2 = edge2(0.0f, 0.0f, a1, b1, qu, qv);
             float d2 = 0.0f;
             if (!inside3(w0, w1, w2))
-                d2 = fminf(fminf(segd2(0.0f, 0.0f, a1, b1, qu, qv), segd2(a1, b1, a2, b2, qu, qv)),
-                           segd2(a2, b2, 0.0f, 0.0f, qu, qv));
+                d2 = fminf(fminf(segd2(0.0f, 0.0f, a1, b1, ie01, qu, qv), segd2(a1, b1, a2, b2, ie12, qu, qv)),
+                           segd2(a2, b2, 0.0f, 0.0f, ie20, qu, qv));
             float dd = fmaf(h, h, d2);
             d2min = fminf(d2min, dd);
             d2max = fmaxf(d2max, dd);

@@ -14,6 +14,7 @@ namespace lfdpr {
 constexpr int kMaxRenderViews = 512;
 constexpr int kMaxCell = 65535;          // lattice indices are stored as u16
 constexpr int kSetupThreads = 256;       // triangles per set-up / emit block
+constexpr float kBoxPad = 1.0f / 16.0f;  // margin (pixels) of candidate pixel ranges against rounding
 
 // Display constants, passed by value to every kernel.
 struct DispConst {
@@ -49,13 +50,47 @@ struct Counters {
     uint32_t cell_overflow;
     uint32_t n_live;
     uint32_t n_writes;    // depth-test atomics the splat issued
-    uint32_t pad[3];
+    uint32_t n_work;      // points with at least one candidate pixel row
+    uint32_t pad[2];
 };
 
 // One triangle's sampling record: 8 float4 (layout = LFDPR_TRI_* in lfdpr.h).
 struct TriRec {
     float4 q[8];
 };
+
+// Projection of a world point C into every view (all eyes on y = 0, z = D):
+// pixel x = A + B Ex, pixel y = Y, with s = D / (D - C.z), A = (C.x s - x0) W/fw,
+// B = (1 - s) W/fw, Y = (y0 - C.y s) H/fh. The same formula for every point,
+// so a vertex or cell corner shared by two primitives projects identically.
+__device__ __forceinline__ void project_point(float D, float x0, float y0, float ipw, float iph,
+                                              float X, float Y, float Z, float& A, float& B, float& Yp) {
+    const float s = __fdividef(D, D - Z);
+    A = fmaf(X, s, -x0) * ipw;
+    B = (1.0f - s) * ipw;
+    Yp = (y0 - Y * s) * iph;
+}
+
+// Per-triangle projection constants for the splat: the three vertices'
+// (A, B, Y), and the triangle's z range.
+struct TriProj {
+    float4 a;   // A0 A1 A2 zmin
+    float4 b;   // B0 B1 B2 zmax
+    float4 y;   // Y0 Y1 Y2 (unused)
+};
+
+// Per-point splat record: the cell corners' projections (corners 00, 10, 11,
+// 01), the first candidate pixel row and the number of rows (rows inside both
+// the cell's and the triangle's y-extent, the same in every view), flags and
+// the triangle id.
+struct SplatRec {
+    float4 A, B, Y;
+    uint4 meta;   // y0, n_rows, flags, triangle
+};
+constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
+constexpr uint32_t kFlagSingle = 2u;    // the triangle has this one point (it lies inside the cell)
+constexpr uint32_t kFlagBehind = 4u;    // a corner or vertex reaches the eyes' plane
+constexpr uint32_t kFlagDepthOk = 8u;   // every hit on the triangle is within [near, far]
 
 // ---------------------------------------------------------------------------
 // binary32 helpers (each rounding explicit)
@@ -70,11 +105,19 @@ __device__ __forceinline__ float edge_fn(float px, float py, float rx, float ry,
     return fmaf(rx - px, qy - py, -((ry - py) * (qx - px)));
 }
 
-// Squared distance from q to the segment p-r.
-__device__ __forceinline__ float seg_dist2(float px, float py, float rx, float ry, float qx, float qy) {
-    const float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+// Reciprocal squared length of the segment p-r (0 for a zero-length segment).
+__device__ __forceinline__ float seg_inv_len2(float px, float py, float rx, float ry) {
+    const float ex = rx - px, ey = ry - py;
     const float ee = fmaf(ex, ex, ey * ey);
-    float t = ee > 0.0f ? __fdiv_rn(fmaf(wx, ex, wy * ey), ee) : 0.0f;
+    return ee > 0.0f ? __fdiv_rn(1.0f, ee) : 0.0f;
+}
+
+// Squared distance from q to the segment p-r, inv_ee = seg_inv_len2(p, r):
+// the closest point's parameter (q-p).(r-p) / |r-p|^2 clamped to [0, 1].
+__device__ __forceinline__ float seg_dist2(float px, float py, float rx, float ry, float inv_ee, float qx,
+                                           float qy) {
+    const float ex = rx - px, ey = ry - py, wx = qx - px, wy = qy - py;
+    float t = fmaf(wx, ex, wy * ey) * inv_ee;
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     const float dx = fmaf(-t, ex, wx), dy = fmaf(-t, ey, wy);
     return fmaf(dx, dx, dy * dy);
@@ -142,6 +185,9 @@ struct FrameArgs {
     uint32_t n_blocks;
     uint4* points;
     uint32_t max_points;
+    TriProj* tproj;                  // [n_tris] (optional: null skips it)
+    SplatRec* srec;                  // [max_points]
+    uint32_t* work;                  // [max_points] points the splat visits
     uint64_t* keys;
     uint8_t* views;
     Counters* ctr;

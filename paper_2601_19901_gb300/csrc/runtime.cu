@@ -23,6 +23,8 @@ struct lfdpr_display {
     float* d_ex = nullptr;
     uint4* points = nullptr;
     uint32_t max_points = 0;
+    SplatRec* srec = nullptr;
+    uint32_t* work = nullptr;
     uint64_t* keys = nullptr;
     uint8_t* views = nullptr;
     uint8_t* panel = nullptr;      // device scratch for host-memory panels
@@ -45,6 +47,7 @@ struct lfdpr_mesh {
     uint8_t* pool = nullptr;
     TexDesc* tex = nullptr;
     TriRec* rec = nullptr;
+    TriProj* tproj = nullptr;
     uint32_t* counts = nullptr;
     uint32_t* offsets = nullptr;
     uint32_t* block_sums = nullptr;
@@ -101,6 +104,8 @@ void free_display(lfdpr_display* d) {
         if (e) cudaEventDestroy(e);
     cudaFree(d->d_ex);
     cudaFree(d->points);
+    cudaFree(d->srec);
+    cudaFree(d->work);
     cudaFree(d->keys);
     cudaFree(d->views);
     cudaFree(d->panel);
@@ -117,6 +122,7 @@ void free_mesh(lfdpr_mesh* m) {
     cudaFree(m->pool);
     cudaFree(m->tex);
     cudaFree(m->rec);
+    cudaFree(m->tproj);
     cudaFree(m->counts);
     cudaFree(m->offsets);
     cudaFree(m->block_sums);
@@ -176,7 +182,7 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     lfdpr_display* d = new (std::nothrow) lfdpr_display();
     if (!d) return fail(LFDPR_ENOMEM, "host allocation failed");
     d->desc = s;
-    if (d->desc.max_points == 0) d->desc.max_points = 1LL << 25;
+    if (d->desc.max_points == 0) d->desc.max_points = 1LL << 24;
     d->max_points = uint32_t(d->desc.max_points);
     CK(cudaGetDevice(&d->device), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device), "sm count");
@@ -218,6 +224,8 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     cudaError_t e;
     if ((e = cudaMalloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->srec, sizeof(SplatRec) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->work, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->keys, 8u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->views, 4u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
@@ -298,6 +306,7 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
         (e = cudaMalloc(&m->pool, pool_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&m->tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
         (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
         (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
         (e = cudaMalloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
         free_mesh(m);
@@ -374,6 +383,9 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     a.n_blocks = mesh->n_blocks;
     a.points = disp->points;
     a.max_points = disp->max_points;
+    a.tproj = mesh->tproj;
+    a.srec = disp->srec;
+    a.work = disp->work;
     a.keys = disp->keys;
     a.views = disp->views;
     a.ctr = disp->ctr;

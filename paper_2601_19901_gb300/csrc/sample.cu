@@ -10,7 +10,10 @@
 //            plus the block offset gives each triangle's first point id; the
 //            column walk writes (triangle, cell) for each of its points.
 //   k_fetch  one thread per point: texture coordinate of the cell centre and
-//            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7).
+//            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7); then the
+//            point's splat record (its cell projected into the views) and,
+//            if some pixel row can receive it, its place in the splat's work
+//            list.
 //
 // Every floating-point step here is bit-specified (binary32, explicit fmaf,
 // IEEE division and square root) so the point set is identical to the CPU
@@ -107,7 +110,7 @@ struct SetupOut {
     bool cell_overflow;
 };
 
-__device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
+__device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, TriProj& tp) {
     const DispConst& c = a.dc;
     SetupOut res{0u, false, false};
     float P[3][3], Q[3][2];
@@ -172,6 +175,8 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
     // closest and farthest eye (Fig. 4): height over the plane plus the
     // in-plane distance to the 2-D triangle, over every rendered view
     float d2min = INFINITY, d2max = -INFINITY;
+    const float ie01 = seg_inv_len2(0.0f, 0.0f, a1, b1), ie12 = seg_inv_len2(a1, b1, a2, b2);
+    const float ie20 = seg_inv_len2(a2, b2, 0.0f, 0.0f);
     for (int v = 0; v < c.nr; v++) {
         const float qx = a.ex[v] - P[0][0], qy = 0.0f - P[0][1], qz = c.D - P[0][2];
         const float qu = dot3(qx, qy, qz, ux, uy, uz);
@@ -182,8 +187,8 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
         const float w2 = edge_fn(0.0f, 0.0f, a1, b1, qu, qv);
         float d2 = 0.0f;
         if (!inside_either(w0, w1, w2))
-            d2 = fminf(fminf(seg_dist2(0.0f, 0.0f, a1, b1, qu, qv), seg_dist2(a1, b1, a2, b2, qu, qv)),
-                       seg_dist2(a2, b2, 0.0f, 0.0f, qu, qv));
+            d2 = fminf(fminf(seg_dist2(0.0f, 0.0f, a1, b1, ie01, qu, qv), seg_dist2(a1, b1, a2, b2, ie12, qu, qv)),
+                       seg_dist2(a2, b2, 0.0f, 0.0f, ie20, qu, qv));
         const float dd = fmaf(h, h, d2);
         d2min = fminf(d2min, dd);
         d2max = fmaxf(d2max, dd);
@@ -252,6 +257,14 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r) {
     }
     res.count = cnt;
     res.live = true;
+    // the splat's per-triangle projection constants
+    float pA[3], pB[3], pY[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        project_point(c.D, c.x0, c.y0, c.ipw, c.iph, P[k][0], P[k][1], P[k][2], pA[k], pB[k], pY[k]);
+    tp.a = make_float4(pA[0], pA[1], pA[2], fminf(fminf(P[0][2], P[1][2]), P[2][2]));
+    tp.b = make_float4(pB[0], pB[1], pB[2], fmaxf(fmaxf(P[0][2], P[1][2]), P[2][2]));
+    tp.y = make_float4(pY[0], pY[1], pY[2], 0.0f);
     return res;
 }
 
@@ -278,10 +291,12 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(FrameArgs a) {
     uint32_t count = 0, live = 0;
     if (t < a.n_tris) {
         TriRec r;
-        const SetupOut o = setup_triangle(a, t, r);
+        TriProj tp;
+        const SetupOut o = setup_triangle(a, t, r, tp);
         TriRec* dst = a.rec + t;
 #pragma unroll
         for (int k = 0; k < 8; k++) dst->q[k] = r.q[k];
+        if (o.live && a.tproj) a.tproj[t] = tp;
         count = o.count;
         live = o.live ? 1u : 0u;
         a.counts[t] = count;
@@ -441,15 +456,33 @@ __device__ uint32_t trilinear(const uint8_t* __restrict__ pool, const TexDesc& t
     return out;
 }
 
+// Cell corner (a s_u + umin, b s_v + vmin) of the lattice frame in world space.
+__device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q1, const float4& q2,
+                                               const float4& q3, int ia, int jb, float* o) {
+    const float cu = float(ia) * q0.w + q2.w;
+    const float cv = float(jb) * q1.w + q3.w;
+    o[0] = fmaf(cu, q1.x, fmaf(cv, q2.x, q0.x));
+    o[1] = fmaf(cu, q1.y, fmaf(cv, q2.y, q0.y));
+    o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
+}
+
+// One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
+// record (its cell's projection into the views, candidate rows, flags), and
+// the point joins the splat's work list if any pixel row can receive it.
 __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
     if (a.ctr->overflow) return;
+    const DispConst& c = a.dc;
     const uint32_t n = a.ctr->n_points;
+    const float H1 = float(c.H - 1);
+    const int lane = threadIdx.x & 31;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
         const TriRec* r = a.rec + pt.x;
-        const float su = __ldg(&r->q[0].w), sv = __ldg(&r->q[1].w);
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
         const float4 q6 = __ldg(&r->q[6]), q7 = __ldg(&r->q[7]);
         const uint32_t i = pt.y & 0xffffu, j = pt.y >> 16;
+        const float su = q0.w, sv = q1.w;
         const float uc = (float(i) + 0.5f) * su;
         const float vc = (float(j) + 0.5f) * sv;
         const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
@@ -458,6 +491,52 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         const uint32_t tmin = trilinear(a.pool, td, s, t, q7.z);
         const uint32_t tmax = trilinear(a.pool, td, s, t, q7.w);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
+
+        // splat record
+        const TriProj tp = a.tproj[pt.x];
+        float A[4], B[4], Y[4];
+        bool behind = !((c.D - tp.b.w) > 1e-4f * c.D);
+        bool interior = true;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int ia = int(i) + (k == 1 || k == 2), jb = int(j) + (k >= 2);
+            float C[3];
+            lattice_corner(q0, q1, q2, q3, ia, jb, C);
+            behind |= !((c.D - C[2]) > 1e-4f * c.D);
+            project_point(c.D, c.x0, c.y0, c.ipw, c.iph, C[0], C[1], C[2], A[k], B[k], Y[k]);
+            const float uu = float(ia) * su + q2.w, vv = float(jb) * sv + q3.w;
+            interior &= edge_fn(q4.x, q4.y, q4.z, q4.w, uu, vv) >= 0.0f &&
+                        edge_fn(q4.z, q4.w, 0.0f, 0.0f, uu, vv) >= 0.0f &&
+                        edge_fn(0.0f, 0.0f, q4.x, q4.y, uu, vv) >= 0.0f;
+        }
+        const float cymn = fminf(fminf(Y[0], Y[1]), fminf(Y[2], Y[3]));
+        const float cymx = fmaxf(fmaxf(Y[0], Y[1]), fmaxf(Y[2], Y[3]));
+        const float tymn = fminf(fminf(tp.y.x, tp.y.y), tp.y.z), tymx = fmaxf(fmaxf(tp.y.x, tp.y.y), tp.y.z);
+        const float fy0 = fmaxf(ceilf(fmaxf(cymn, tymn) - 0.5f - kBoxPad), 0.0f);
+        const float fy1 = fminf(floorf(fminf(cymx, tymx) - 0.5f + kBoxPad), H1);
+        uint32_t y0 = 0, ny = 0;
+        if (!behind && fy0 <= fy1) {
+            y0 = uint32_t(int(fy0));
+            ny = uint32_t(int(fy1) - int(fy0) + 1);
+        }
+        const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
+        const uint32_t flags = (interior ? kFlagInterior : 0u) | (__ldg(a.counts + pt.x) == 1u ? kFlagSingle : 0u) |
+                               (behind ? kFlagBehind : 0u) | (depth_ok ? kFlagDepthOk : 0u);
+        SplatRec* sr = a.srec + p;
+        sr->A = make_float4(A[0], A[1], A[2], A[3]);
+        sr->B = make_float4(B[0], B[1], B[2], B[3]);
+        sr->Y = make_float4(Y[0], Y[1], Y[2], Y[3]);
+        sr->meta = make_uint4(y0, ny, flags, pt.x);
+
+        // warp-aggregated append to the work list
+        const bool want = ny > 0 || behind;
+        const unsigned mask = __activemask();
+        const unsigned bal = __ballot_sync(mask, want);
+        const int leader = __ffs(mask) - 1;
+        uint32_t base = 0;
+        if (lane == leader && bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
+        base = __shfl_sync(mask, base, leader);
+        if (want) a.work[base + __popc(bal & ((1u << lane) - 1u))] = p;
     }
 }
 
