@@ -51,7 +51,8 @@ struct Counters {
     uint32_t n_live;
     uint32_t n_writes;    // depth-test atomics the splat issued
     uint32_t n_work;      // points with at least one candidate pixel row
-    uint32_t pad[2];
+    uint32_t n_behind;    // points whose cell or triangle reaches the eyes' plane
+    uint32_t pad;
 };
 
 // One triangle's sampling record: 8 float4 (layout = LFDPR_TRI_* in lfdpr.h).
@@ -81,11 +82,11 @@ struct TriProj {
 
 // Per-point splat record: the cell corners' projections (corners 00, 10, 11,
 // 01), the first candidate pixel row and the number of rows (rows inside both
-// the cell's and the triangle's y-extent, the same in every view), flags and
-// the triangle id.
+// the cell's and the triangle's y-extent, the same in every view), the cell,
+// flags and the triangle id.
 struct SplatRec {
     float4 A, B, Y;
-    uint4 meta;   // y0, n_rows, flags, triangle
+    uint4 meta;   // y0 | n_rows << 16, i | j << 16, flags, triangle
 };
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagSingle = 2u;    // the triangle has this one point (it lies inside the cell)
@@ -187,7 +188,8 @@ struct FrameArgs {
     uint32_t max_points;
     TriProj* tproj;                  // [n_tris] (optional: null skips it)
     SplatRec* srec;                  // [max_points]
-    uint32_t* work;                  // [max_points] points the splat visits
+    uint32_t* work;                  // [max_points] points the splat visits; points that reach
+                                     // the eyes' plane are listed from the end backwards
     uint64_t* keys;
     uint8_t* views;
     Counters* ctr;
@@ -199,6 +201,7 @@ cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel,
                               cudaStream_t s);

@@ -410,7 +410,8 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     mark(disp, 5, s);
     if (mesh->n_tris) {
         CK(launch_splat(a, s), "launch k_splat");
-        disp->launches += 1;
+        CK(launch_splat_near(a, s), "launch k_splat_near");
+        disp->launches += 2;
     }
     mark(disp, 6, s);
     CK(launch_resolve(a, s), "launch k_resolve");

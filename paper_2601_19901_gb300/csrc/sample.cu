@@ -526,17 +526,24 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         sr->A = make_float4(A[0], A[1], A[2], A[3]);
         sr->B = make_float4(B[0], B[1], B[2], B[3]);
         sr->Y = make_float4(Y[0], Y[1], Y[2], Y[3]);
-        sr->meta = make_uint4(y0, ny, flags, pt.x);
+        sr->meta = make_uint4(y0 | (ny << 16), pt.y, flags, pt.x);
 
-        // warp-aggregated append to the work list
-        const bool want = ny > 0 || behind;
+        // warp-aggregated append to the work list (points reaching the eyes'
+        // plane go to its end, counted separately)
         const unsigned mask = __activemask();
-        const unsigned bal = __ballot_sync(mask, want);
         const int leader = __ffs(mask) - 1;
-        uint32_t base = 0;
-        if (lane == leader && bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
+        const unsigned below = (1u << lane) - 1u;
+        const unsigned bal = __ballot_sync(mask, ny > 0);
+        const unsigned bnear = __ballot_sync(mask, behind);
+        uint32_t base = 0, bnb = 0;
+        if (lane == leader) {
+            if (bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
+            if (bnear) bnb = atomicAdd(&a.ctr->n_behind, uint32_t(__popc(bnear)));
+        }
         base = __shfl_sync(mask, base, leader);
-        if (want) a.work[base + __popc(bal & ((1u << lane) - 1u))] = p;
+        bnb = __shfl_sync(mask, bnb, leader);
+        if (ny > 0) a.work[base + __popc(bal & below)] = p;
+        if (behind) a.work[a.max_points - 1u - (bnb + __popc(bnear & below))] = p;
     }
 }
 

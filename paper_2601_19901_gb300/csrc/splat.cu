@@ -22,35 +22,57 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
-// Screen-space edge function of the directed segment (px, py) -> (qx, qy) at (x, y).
-__device__ __forceinline__ float sedge(float px, float py, float qx, float qy, float x, float y) {
-    return fmaf(qx - px, y - py, -((qy - py) * (x - px)));
-}
-
 // One warp per point of the work list (points with at least one candidate
 // pixel row), lanes over the rendered views.
 //
-// The point's splat record holds its cell corners projected into every view
-// (pixel x = A + B Ex, pixel y = Y, the same in all views since every eye
-// lies on y = 0, z = D) and its candidate rows: rows inside both the cell's
-// and the triangle's y-extent. Per chunk of 32 views each lane forms its
-// view's candidate columns (the cell's and the triangle's x-extents
-// intersected); a warp scan of the candidate counts then gives every lane one
-// candidate pixel per pass, so no lane loops over pixels on its own.
+// Candidates. The point's splat record holds its cell corners projected into
+// every view (pixel x = A + B Ex, pixel y = Y, the same in all views since
+// every eye lies on y = 0, z = D) and its candidate rows: rows inside both the
+// cell's and the triangle's y-extent. Per group of views (up to 32 per lane
+// slot) each lane forms its view's candidate columns, the cell's and the
+// triangle's x-extents intersected and widened by a small margin; a warp scan
+// of the candidate counts then gives every lane one candidate pixel per pass,
+// so no lane loops over pixels on its own.
 //
-// The per-pixel test: edge functions of the projected cell (half-open: the
-// u = i and v = j sides included, u = i+1 and v = j+1 excluded, so cells,
-// which share bit-identical corners, partition their triangle's pixels) and
-// of the projected triangle (closed); the orientation sign is the side of the
-// triangle's plane the eye is on. A cell inside its triangle skips the
-// triangle test; a triangle with a single point lies inside that point's cell
-// and skips the cell test. The ray parameter t (the depth key) is divided out
-// only for accepted pixels, by the plane-space formula.
+// Test. Each candidate takes the per-pixel test in the oracle's plane-space
+// form: the pixel centre's ray from the eye meets the triangle's plane at t
+// (the division also yields the depth key); the hit must lie in the half-open
+// cell and in the closed triangle (2-D edge functions of the lattice frame),
+// at a depth t D in [near, far]. A cell inside its triangle skips the triangle
+// test. The margin of the candidate ranges only admits extra candidates; the
+// test alone decides.
 //
-// Points whose cell or triangle reaches the eyes' plane (never in front-only
-// scenes) take the plane-space form of the test (the oracle's formula) over
-// the whole view instead, one view per lane.
+// Points whose cell or triangle reaches the eyes' plane (none in front-only
+// scenes) are listed apart and splatted by k_splat_near.
 constexpr int kSplatWarps = 8;
+
+__device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float num, float qEx, float qEy,
+                                           float qEz, const float4& q1, const float4& q2, const float4& q3,
+                                           const float4& q4, float ulo, float uhi, float vlo, float vhi,
+                                           bool interior, bool depth_ok, int x, int y, float& t) {
+    const float Fx = fmaf(float(x) + 0.5f, c.pw, c.x0);
+    const float Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
+    const float dx = Fx - Ex, dy = Fy - 0.0f, dz = -c.D;
+    const float den = dot3(q3.x, q3.y, q3.z, dx, dy, dz);
+    if (den == 0.0f) return false;
+    t = __fdiv_rn(num, den);
+    if (depth_ok) {
+        if (!(t > 0.0f)) return false;
+    } else {
+        const float depth = t * c.D;
+        if (!(depth >= c.near_z && depth <= c.far_z)) return false;
+    }
+    const float hx = fmaf(t, dx, qEx), hy = fmaf(t, dy, qEy), hz = fmaf(t, dz, qEz);
+    const float uq = dot3(hx, hy, hz, q1.x, q1.y, q1.z);
+    const float vq = dot3(hx, hy, hz, q2.x, q2.y, q2.z);
+    const float u = uq - q2.w, vv = vq - q3.w;
+    if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) return false;
+    if (interior) return true;
+    const float w0 = edge_fn(q4.x, q4.y, q4.z, q4.w, uq, vq);
+    const float w1 = edge_fn(q4.z, q4.w, 0.0f, 0.0f, uq, vq);
+    const float w2 = edge_fn(0.0f, 0.0f, q4.x, q4.y, uq, vq);
+    return inside_either(w0, w1, w2);
+}
 
 __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     __shared__ float s_ex[kMaxRenderViews];
@@ -70,58 +92,23 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     for (uint32_t k = warp; k < n; k += n_warps) {
         const uint32_t p = __ldg(a.work + k);
         const SplatRec* srp = a.srec + p;
-        const float4 cA = __ldg(&srp->A), cB = __ldg(&srp->B), cY = __ldg(&srp->Y);
         const uint4 meta = __ldg(&srp->meta);
         const uint32_t tri = meta.w, flags = meta.z;
         const TriRec* r = a.rec + tri;
-        const float4 q0 = __ldg(&r->q[0]), q3 = __ldg(&r->q[3]);
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+        const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
+        const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
+        const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
+        const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
+        const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
+        const unsigned long long pid = p;
 
-        if (flags & kFlagBehind) {
-            const float4 q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]), q4 = __ldg(&r->q[4]);
-            const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
-            const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
-            const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
-            const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
-            for (int v = lane; v < c.nr; v += 32) {
-                const float Ex = s_ex[v];
-                const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
-                const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-                for (int y = 0; y < c.H; y++) {
-                    const float Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
-                    for (int x = 0; x < c.W; x++) {
-                        const float Fx = fmaf(float(x) + 0.5f, c.pw, c.x0);
-                        const float dx = Fx - Ex, dy = Fy - 0.0f, dz = -c.D;
-                        const float den = dot3(q3.x, q3.y, q3.z, dx, dy, dz);
-                        if (den == 0.0f) continue;
-                        const float t = __fdiv_rn(num, den);
-                        const float depth = t * c.D;
-                        if (!(depth >= c.near_z && depth <= c.far_z)) continue;
-                        const float hx = fmaf(t, dx, qEx), hy = fmaf(t, dy, qEy), hz = fmaf(t, dz, qEz);
-                        const float uq = dot3(hx, hy, hz, q1.x, q1.y, q1.z);
-                        const float vq = dot3(hx, hy, hz, q2.x, q2.y, q2.z);
-                        const float u = uq - q2.w, vv = vq - q3.w;
-                        if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) continue;
-                        const float w0 = edge_fn(q4.x, q4.y, q4.z, q4.w, uq, vq);
-                        const float w1 = edge_fn(q4.z, q4.w, 0.0f, 0.0f, uq, vq);
-                        const float w2 = edge_fn(0.0f, 0.0f, q4.x, q4.y, uq, vq);
-                        if (!inside_either(w0, w1, w2)) continue;
-                        atomicMin(keys + (uint64_t)v * npix + (uint64_t)y * c.W + x,
-                                  ((unsigned long long)__float_as_uint(t) << 32) | p);
-                        writes++;
-                    }
-                }
-            }
-            continue;
-        }
-
+        const float4 cA = __ldg(&srp->A), cB = __ldg(&srp->B);
         const TriProj* tpp = a.tproj + tri;
-        const float4 tA = __ldg(&tpp->a), tB = __ldg(&tpp->b), tY = __ldg(&tpp->y);
-        const int y0 = int(meta.x);
-        const uint32_t ny = meta.y;
-        const bool single = flags & kFlagSingle, interior = flags & kFlagInterior;
-        const bool depth_ok = flags & kFlagDepthOk;
-        // n . (E - P0) = n.x Ex + kn
-        const float kn = fmaf(q3.y, 0.0f - q0.y, q3.z * (c.D - q0.z)) - q3.x * q0.x;
+        const float4 tA = __ldg(&tpp->a), tB = __ldg(&tpp->b);
+        const int y0 = int(meta.x & 0xffffu);
+        const uint32_t ny = meta.x >> 16;
 
         for (int base = 0; base < c.nr; base += 32) {
             const int v = base + lane;
@@ -163,44 +150,19 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                 const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own);
                 const uint32_t o_nx = __shfl_sync(0xffffffffu, nx, own);
                 const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
-                const float o_Ex = __shfl_sync(0xffffffffu, Ex, own);
                 if (q >= total) continue;
                 const uint32_t rr = q - o_excl;
                 const uint32_t ry = ny == 1 ? 0u : rr / o_nx;
-                const uint32_t rx = rr - ry * o_nx;
-                const int x = o_x0 + int(rx), y = y0 + int(ry);
-                const float px = float(x) + 0.5f, pyc = float(y) + 0.5f;
-                const float nE = fmaf(q3.x, o_Ex, kn);
-                if (nE == 0.0f) continue;              // plane seen edge-on
-                const float sg = nE > 0.0f ? 1.0f : -1.0f;
-                if (!single) {
-                    const float X0 = fmaf(cB.x, o_Ex, cA.x), X1 = fmaf(cB.y, o_Ex, cA.y);
-                    const float X2 = fmaf(cB.z, o_Ex, cA.z), X3 = fmaf(cB.w, o_Ex, cA.w);
-                    const float eL = sg * sedge(X0, cY.x, X3, cY.w, px, pyc);
-                    const float eR = sg * sedge(X1, cY.y, X2, cY.z, px, pyc);
-                    const float eB = sg * sedge(X0, cY.x, X1, cY.y, px, pyc);
-                    const float eT = sg * sedge(X3, cY.w, X2, cY.z, px, pyc);
-                    if (!(eL >= 0.0f && eR < 0.0f && eB <= 0.0f && eT > 0.0f)) continue;
-                }
-                if (!interior) {
-                    const float T0 = fmaf(tB.x, o_Ex, tA.x), T1 = fmaf(tB.y, o_Ex, tA.y), T2 = fmaf(tB.z, o_Ex, tA.z);
-                    const float e0 = sg * sedge(T0, tY.x, T1, tY.y, px, pyc);
-                    const float e1 = sg * sedge(T1, tY.y, T2, tY.z, px, pyc);
-                    const float e2 = sg * sedge(T2, tY.z, T0, tY.x, px, pyc);
-                    if (!(e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f)) continue;
-                }
-                const float qEx = o_Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
+                const int x = o_x0 + int(rr - ry * o_nx), y = y0 + int(ry);
+                const float Ex_o = s_ex[base + own];
+                const float qEx = Ex_o - q0.x;
                 const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-                const float Fx = fmaf(px, c.pw, c.x0), Fy = fmaf(pyc, -c.ph, c.y0);
-                const float den = dot3(q3.x, q3.y, q3.z, Fx - o_Ex, Fy - 0.0f, -c.D);
-                const float t = __fdiv_rn(num, den);
-                if (!(t > 0.0f)) continue;
-                if (!depth_ok) {
-                    const float depth = t * c.D;
-                    if (!(depth >= c.near_z && depth <= c.far_z)) continue;
-                }
+                float t;
+                if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, depth_ok,
+                                x, y, t))
+                    continue;
                 atomicMin(keys + (uint64_t)(base + own) * npix + (uint64_t)y * c.W + x,
-                          ((unsigned long long)__float_as_uint(t) << 32) | p);
+                          ((unsigned long long)__float_as_uint(t) << 32) | pid);
                 writes++;
             }
         }
@@ -209,6 +171,50 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
     if (lane == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
+}
+
+// Points whose cell or triangle reaches the eyes' plane: their projections
+// are unbounded, so every pixel of every view takes the plane-space test,
+// one (point, view) pair per thread. None occur in front-only scenes.
+__global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
+    if (a.ctr->overflow) return;
+    const DispConst& c = a.dc;
+    const uint32_t n = a.ctr->n_behind;
+    const uint64_t pairs = (uint64_t)n * c.nr;
+    const uint64_t npix = (uint64_t)c.W * c.H;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
+    uint32_t writes = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < pairs;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = uint32_t(g / c.nr);
+        const int v = int(g - (uint64_t)k * c.nr);
+        const uint32_t p = a.work[a.max_points - 1u - k];
+        const uint4 meta = a.srec[p].meta;
+        const TriRec* r = a.rec + meta.w;
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+        const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
+        const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
+        const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
+        const float Ex = __ldg(a.ex + v);
+        const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
+        const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
+        const bool interior = meta.z & kFlagInterior;
+        for (int y = 0; y < c.H; y++) {
+            for (int x = 0; x < c.W; x++) {
+                float t;
+                if (!pixel_test(c, Ex, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, false, x,
+                                y, t))
+                    continue;
+                atomicMin(keys + (uint64_t)v * npix + (uint64_t)y * c.W + x,
+                          ((unsigned long long)__float_as_uint(t) << 32) | p);
+                writes++;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
+    if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
 }
 
 __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
@@ -263,6 +269,11 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
 
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
     k_splat<<<a.sm_count * 16, kSplatWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s) {
+    k_splat_near<<<a.sm_count * 2, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
