@@ -51,7 +51,7 @@ struct Counters {
     uint32_t n_live;
     uint32_t n_writes;    // depth-test atomics the splat issued
     uint32_t n_work;      // points with at least one candidate pixel row
-    uint32_t n_behind;    // points whose cell or triangle reaches the eyes' plane
+    uint32_t n_near;      // points whose cell or triangle reaches the eyes' plane
     uint32_t pad;
 };
 
@@ -80,18 +80,17 @@ struct TriProj {
     float4 y;   // Y0 Y1 Y2 (unused)
 };
 
-// Per-point splat record: the cell corners' projections (corners 00, 10, 11,
-// 01), the first candidate pixel row and the number of rows (rows inside both
-// the cell's and the triangle's y-extent, the same in every view), the cell,
-// flags and the triangle id.
-struct SplatRec {
-    float4 A, B, Y;
-    uint4 meta;   // y0 | n_rows << 16, i | j << 16, flags, triangle
+// Splat work record of a point with at least one candidate pixel row: its
+// cell corners' projections (corners 00, 10, 11, 01), the first candidate row
+// and the number of rows (rows inside both the cell's and the triangle's
+// y-extent, the same in every view), flags, the cell, the triangle and the
+// point id. Written compacted by the fetch pass, in no particular order.
+struct WorkRec {
+    float4 A, B;
+    uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
-constexpr uint32_t kFlagSingle = 2u;    // the triangle has this one point (it lies inside the cell)
-constexpr uint32_t kFlagBehind = 4u;    // a corner or vertex reaches the eyes' plane
-constexpr uint32_t kFlagDepthOk = 8u;   // every hit on the triangle is within [near, far]
+constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]
 
 // ---------------------------------------------------------------------------
 // binary32 helpers (each rounding explicit)
@@ -187,9 +186,8 @@ struct FrameArgs {
     uint4* points;
     uint32_t max_points;
     TriProj* tproj;                  // [n_tris] (optional: null skips it)
-    SplatRec* srec;                  // [max_points]
-    uint32_t* work;                  // [max_points] points the splat visits; points that reach
-                                     // the eyes' plane are listed from the end backwards
+    WorkRec* work;                   // [max_points] the splat's work list
+    uint32_t* near;                  // [max_points] points whose cell or triangle reaches the eyes' plane
     uint64_t* keys;
     uint8_t* views;
     Counters* ctr;

@@ -23,8 +23,8 @@ struct lfdpr_display {
     float* d_ex = nullptr;
     uint4* points = nullptr;
     uint32_t max_points = 0;
-    SplatRec* srec = nullptr;
-    uint32_t* work = nullptr;
+    WorkRec* work = nullptr;
+    uint32_t* near = nullptr;
     uint64_t* keys = nullptr;
     uint8_t* views = nullptr;
     uint8_t* panel = nullptr;      // device scratch for host-memory panels
@@ -104,8 +104,8 @@ void free_display(lfdpr_display* d) {
         if (e) cudaEventDestroy(e);
     cudaFree(d->d_ex);
     cudaFree(d->points);
-    cudaFree(d->srec);
     cudaFree(d->work);
+    cudaFree(d->near);
     cudaFree(d->keys);
     cudaFree(d->views);
     cudaFree(d->panel);
@@ -224,8 +224,8 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     cudaError_t e;
     if ((e = cudaMalloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->srec, sizeof(SplatRec) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->work, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->work, sizeof(WorkRec) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->near, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->keys, 8u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->views, 4u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
@@ -384,8 +384,8 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     a.points = disp->points;
     a.max_points = disp->max_points;
     a.tproj = mesh->tproj;
-    a.srec = disp->srec;
     a.work = disp->work;
+    a.near = disp->near;
     a.keys = disp->keys;
     a.views = disp->views;
     a.ctr = disp->ctr;

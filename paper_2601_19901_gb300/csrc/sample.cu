@@ -492,17 +492,17 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         const uint32_t tmax = trilinear(a.pool, td, s, t, q7.w);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
 
-        // splat record
+        // splat work record
         const TriProj tp = a.tproj[pt.x];
         float A[4], B[4], Y[4];
-        bool behind = !((c.D - tp.b.w) > 1e-4f * c.D);
+        bool near = !((c.D - tp.b.w) > 1e-4f * c.D);
         bool interior = true;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int ia = int(i) + (k == 1 || k == 2), jb = int(j) + (k >= 2);
             float C[3];
             lattice_corner(q0, q1, q2, q3, ia, jb, C);
-            behind |= !((c.D - C[2]) > 1e-4f * c.D);
+            near |= !((c.D - C[2]) > 1e-4f * c.D);
             project_point(c.D, c.x0, c.y0, c.ipw, c.iph, C[0], C[1], C[2], A[k], B[k], Y[k]);
             const float uu = float(ia) * su + q2.w, vv = float(jb) * sv + q3.w;
             interior &= edge_fn(q4.x, q4.y, q4.z, q4.w, uu, vv) >= 0.0f &&
@@ -515,35 +515,34 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         const float fy0 = fmaxf(ceilf(fmaxf(cymn, tymn) - 0.5f - kBoxPad), 0.0f);
         const float fy1 = fminf(floorf(fminf(cymx, tymx) - 0.5f + kBoxPad), H1);
         uint32_t y0 = 0, ny = 0;
-        if (!behind && fy0 <= fy1) {
+        if (!near && fy0 <= fy1) {
             y0 = uint32_t(int(fy0));
             ny = uint32_t(int(fy1) - int(fy0) + 1);
         }
         const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
-        const uint32_t flags = (interior ? kFlagInterior : 0u) | (__ldg(a.counts + pt.x) == 1u ? kFlagSingle : 0u) |
-                               (behind ? kFlagBehind : 0u) | (depth_ok ? kFlagDepthOk : 0u);
-        SplatRec* sr = a.srec + p;
-        sr->A = make_float4(A[0], A[1], A[2], A[3]);
-        sr->B = make_float4(B[0], B[1], B[2], B[3]);
-        sr->Y = make_float4(Y[0], Y[1], Y[2], Y[3]);
-        sr->meta = make_uint4(y0 | (ny << 16), pt.y, flags, pt.x);
+        const uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
 
-        // warp-aggregated append to the work list (points reaching the eyes'
-        // plane go to its end, counted separately)
+        // warp-aggregated appends: points with candidate rows to the work
+        // list, points reaching the eyes' plane to the near list
         const unsigned mask = __activemask();
         const int leader = __ffs(mask) - 1;
         const unsigned below = (1u << lane) - 1u;
         const unsigned bal = __ballot_sync(mask, ny > 0);
-        const unsigned bnear = __ballot_sync(mask, behind);
-        uint32_t base = 0, bnb = 0;
+        const unsigned bnear = __ballot_sync(mask, near);
+        uint32_t base = 0, nbase = 0;
         if (lane == leader) {
             if (bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
-            if (bnear) bnb = atomicAdd(&a.ctr->n_behind, uint32_t(__popc(bnear)));
+            if (bnear) nbase = atomicAdd(&a.ctr->n_near, uint32_t(__popc(bnear)));
         }
         base = __shfl_sync(mask, base, leader);
-        bnb = __shfl_sync(mask, bnb, leader);
-        if (ny > 0) a.work[base + __popc(bal & below)] = p;
-        if (behind) a.work[a.max_points - 1u - (bnb + __popc(bnear & below))] = p;
+        nbase = __shfl_sync(mask, nbase, leader);
+        if (ny > 0) {
+            WorkRec* w = a.work + base + __popc(bal & below);
+            w->A = make_float4(A[0], A[1], A[2], A[3]);
+            w->B = make_float4(B[0], B[1], B[2], B[3]);
+            w->meta = make_uint4(y0 | (ny << 14) | (flags << 29), pt.y, pt.x, p);
+        }
+        if (near) a.near[nbase + __popc(bnear & below)] = p;
     }
 }
 

@@ -22,17 +22,17 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
-// One warp per point of the work list (points with at least one candidate
-// pixel row), lanes over the rendered views.
+// One half-warp (16 lanes) per point of the work list, lanes over the
+// rendered views in chunks of 16; a warp carries two points at a time.
 //
-// Candidates. The point's splat record holds its cell corners projected into
+// Candidates. The point's work record holds its cell corners projected into
 // every view (pixel x = A + B Ex, pixel y = Y, the same in all views since
 // every eye lies on y = 0, z = D) and its candidate rows: rows inside both the
-// cell's and the triangle's y-extent. Per group of views (up to 32 per lane
-// slot) each lane forms its view's candidate columns, the cell's and the
-// triangle's x-extents intersected and widened by a small margin; a warp scan
-// of the candidate counts then gives every lane one candidate pixel per pass,
-// so no lane loops over pixels on its own.
+// cell's and the triangle's y-extent. Per chunk each lane forms its view's
+// candidate columns, the cell's and the triangle's x-extents intersected and
+// widened by a small margin; a scan of the 16 candidate counts then gives
+// every lane one candidate pixel per pass, so no lane loops over pixels on
+// its own.
 //
 // Test. Each candidate takes the per-pixel test in the oracle's plane-space
 // form: the pixel centre's ray from the eye meets the triangle's plane at t
@@ -81,42 +81,41 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     __syncthreads();
     if (a.ctr->overflow) return;
     const uint32_t n = a.ctr->n_work;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, sub = lane & 15;
+    const unsigned hmask = 0xffffu << (lane & 16);
+    const uint32_t hw = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const uint32_t n_hw = (gridDim.x * blockDim.x) >> 4;
     const float W1 = float(c.W - 1);
     const uint64_t npix = (uint64_t)c.W * c.H;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
     uint32_t writes = 0;
 
-    for (uint32_t k = warp; k < n; k += n_warps) {
-        const uint32_t p = __ldg(a.work + k);
-        const SplatRec* srp = a.srec + p;
-        const uint4 meta = __ldg(&srp->meta);
-        const uint32_t tri = meta.w, flags = meta.z;
+    for (uint32_t k = hw; k < n; k += n_hw) {
+        const WorkRec* wr = a.work + k;
+        const float4 cA = __ldg(&wr->A), cB = __ldg(&wr->B);
+        const uint4 meta = __ldg(&wr->meta);
+        const uint32_t tri = meta.z;
+        const unsigned long long pid = meta.w;
         const TriRec* r = a.rec + tri;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+        const TriProj* tpp = a.tproj + tri;
+        const float4 tA = __ldg(&tpp->a), tB = __ldg(&tpp->b);
+        const int y0 = int(meta.x & 0x3fffu);
+        const uint32_t ny = (meta.x >> 14) & 0x7fffu;
+        const uint32_t flags = meta.x >> 29;
+        const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
         const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
         const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
         const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
         const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
-        const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
-        const unsigned long long pid = p;
 
-        const float4 cA = __ldg(&srp->A), cB = __ldg(&srp->B);
-        const TriProj* tpp = a.tproj + tri;
-        const float4 tA = __ldg(&tpp->a), tB = __ldg(&tpp->b);
-        const int y0 = int(meta.x & 0xffffu);
-        const uint32_t ny = meta.x >> 16;
-
-        for (int base = 0; base < c.nr; base += 32) {
-            const int v = base + lane;
-            float Ex = 0.0f;
+        for (int base = 0; base < c.nr; base += 16) {
+            const int v = base + sub;
             uint32_t nx = 0;
             int x0 = 0;
             if (v < c.nr) {
-                Ex = s_ex[v];
+                const float Ex = s_ex[v];
                 const float X0 = fmaf(cB.x, Ex, cA.x), X1 = fmaf(cB.y, Ex, cA.y);
                 const float X2 = fmaf(cB.z, Ex, cA.z), X3 = fmaf(cB.w, Ex, cA.w);
                 const float T0 = fmaf(tB.x, Ex, tA.x), T1 = fmaf(tB.y, Ex, tA.y), T2 = fmaf(tB.z, Ex, tA.z);
@@ -132,42 +131,44 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
             const uint32_t cnt = nx * ny;
             uint32_t incl = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
+            for (int o = 1; o < 16; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(hmask, incl, o, 16);
+                if (sub >= o) incl += t;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t total = __shfl_sync(hmask, incl, 15, 16);
             const uint32_t excl = incl - cnt;
-            for (uint32_t pass = 0; pass < total; pass += 32) {
-                const uint32_t q = pass + lane;
+            for (uint32_t pass = 0; pass < total; pass += 16) {
+                const uint32_t q = pass + sub;
                 // owner: the first lane whose inclusive count exceeds q
                 int own = 0;
 #pragma unroll
-                for (int st = 16; st >= 1; st >>= 1) {
-                    const uint32_t t = __shfl_sync(0xffffffffu, incl, own + st - 1);
+                for (int st = 8; st >= 1; st >>= 1) {
+                    const uint32_t t = __shfl_sync(hmask, incl, own + st - 1, 16);
                     if (t <= q) own += st;
                 }
-                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own);
-                const uint32_t o_nx = __shfl_sync(0xffffffffu, nx, own);
-                const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
+                const uint32_t o_excl = __shfl_sync(hmask, excl, own, 16);
+                const uint32_t o_nx = __shfl_sync(hmask, nx, own, 16);
+                const int o_x0 = __shfl_sync(hmask, x0, own, 16);
                 if (q >= total) continue;
                 const uint32_t rr = q - o_excl;
                 const uint32_t ry = ny == 1 ? 0u : rr / o_nx;
                 const int x = o_x0 + int(rr - ry * o_nx), y = y0 + int(ry);
-                const float Ex_o = s_ex[base + own];
+                const int vo = base + own;
+                const float Ex_o = s_ex[vo];
                 const float qEx = Ex_o - q0.x;
                 const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
                 float t;
                 if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, depth_ok,
                                 x, y, t))
                     continue;
-                atomicMin(keys + (uint64_t)(base + own) * npix + (uint64_t)y * c.W + x,
+                atomicMin(keys + (uint64_t)vo * npix + (uint64_t)y * c.W + x,
                           ((unsigned long long)__float_as_uint(t) << 32) | pid);
                 writes++;
             }
         }
     }
     // warp-aggregated count of depth-test writes (the atomics issued)
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
     if (lane == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
 __global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
     if (a.ctr->overflow) return;
     const DispConst& c = a.dc;
-    const uint32_t n = a.ctr->n_behind;
+    const uint32_t n = a.ctr->n_near;
     const uint64_t pairs = (uint64_t)n * c.nr;
     const uint64_t npix = (uint64_t)c.W * c.H;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
@@ -188,23 +189,22 @@ __global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
          g += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t k = uint32_t(g / c.nr);
         const int v = int(g - (uint64_t)k * c.nr);
-        const uint32_t p = a.work[a.max_points - 1u - k];
-        const uint4 meta = a.srec[p].meta;
-        const TriRec* r = a.rec + meta.w;
+        const uint32_t p = a.near[k];
+        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        const TriRec* r = a.rec + pt.x;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
-        const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
+        const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
         const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
         const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
         const float Ex = __ldg(a.ex + v);
         const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
         const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-        const bool interior = meta.z & kFlagInterior;
         for (int y = 0; y < c.H; y++) {
             for (int x = 0; x < c.W; x++) {
                 float t;
-                if (!pixel_test(c, Ex, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, false, x,
-                                y, t))
+                if (!pixel_test(c, Ex, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, false, false, x, y,
+                                t))
                     continue;
                 atomicMin(keys + (uint64_t)v * npix + (uint64_t)y * c.W + x,
                           ((unsigned long long)__float_as_uint(t) << 32) | p);
