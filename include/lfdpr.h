@@ -149,6 +149,7 @@ typedef struct {
 
 /*
  * lfdpr_create_display: validate `desc` (positive sizes, 1 <= n_views <= 256,
+ * views of at most 16384 pixels a side and 2^26 pixels,
  * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1},
  * 0 <= crosstalk < 0.5) and allocate the display's device buffers: view key
  * buffers (8 B per rendered-view pixel, Sec. 5.2), RGBA8 views, the point

@@ -80,17 +80,23 @@ struct TriProj {
     float4 y;   // Y0 Y1 Y2 (unused)
 };
 
-// Splat work record of a point with at least one candidate pixel row: its
-// cell corners' projections (corners 00, 10, 11, 01), the first candidate row
-// and the number of rows (rows inside both the cell's and the triangle's
-// y-extent, the same in every view), flags, the cell, the triangle and the
-// point id. Written compacted by the fetch pass, in no particular order.
+// Splat work record of a point with at least one candidate pixel row.
+// Candidate rows are the pixel-centre rows inside both the cell's and the
+// triangle's projected y-extent (the same in every view, since every eye lies
+// on y = 0, z = D). With a single candidate row, L0 and L1 hold the lines
+// x = alpha + beta Ex along which the projected cell's two boundary crossings
+// (L0) and the projected triangle's two crossings (L1) of that row move with
+// the eye position, so a view's candidate columns lie between them. Otherwise
+// (flag kFlagBox) L0 and L1 hold the cell corners' A and B of
+// project_point() and candidates come from the x-extents. Written compacted
+// by the fetch pass, in no particular order.
 struct WorkRec {
-    float4 A, B;
+    float4 L0, L1;
     uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]
+constexpr uint32_t kFlagBox = 4u;       // candidates from x-extents (L0, L1 = corner A, B)
 
 // ---------------------------------------------------------------------------
 // binary32 helpers (each rounding explicit)

@@ -155,8 +155,9 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     *out = nullptr;
     const lfdpr_display_desc& s = *desc;
     if (s.n_views < 1 || s.n_views > 256) return fail(LFDPR_EINVAL, "n_views must be in [1, 256]");
-    if (s.view_w < 1 || s.view_h < 1 || s.view_w > 16384 || s.view_h > 16384)
-        return fail(LFDPR_EINVAL, "view size must be in [1, 16384]");
+    if (s.view_w < 1 || s.view_h < 1 || s.view_w > 16384 || s.view_h > 16384 ||
+        (int64_t)s.view_w * s.view_h > (1LL << 26))
+        return fail(LFDPR_EINVAL, "view size must be in [1, 16384] with at most 2^26 pixels");
     if (s.panel_w < 1 || s.panel_h < 1 || s.panel_w > 32768 || s.panel_h > 32768)
         return fail(LFDPR_EINVAL, "panel size must be in [1, 32768]");
     if (!(s.view_dist > 0.0f) || !(s.focal_w > 0.0f) || !(s.focal_h > 0.0f))

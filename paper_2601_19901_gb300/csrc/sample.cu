@@ -466,6 +466,32 @@ __device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
+// Crossings of the pixel row y = yc with a convex polygon of n projected
+// vertices (pixel x = A + B Ex, y = Y): for each edge crossing the row
+// (half-open in y, so a convex polygon has exactly two when yc lies strictly
+// inside its y-extent) the line alpha + beta Ex of the crossing's x. Returns
+// false unless there are exactly two.
+template <int N>
+__device__ __forceinline__ bool row_crossings(const float* A, const float* B, const float* Y, float yc,
+                                              float4& lines) {
+    float al[2], be[2];
+    int m = 0;
+#pragma unroll
+    for (int e = 0; e < N; e++) {
+        const int p = e, q = e + 1 == N ? 0 : e + 1;
+        const bool cross = (Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]);
+        if (!cross) continue;
+        if (m == 2) return false;
+        const float f = __fdividef(yc - Y[p], Y[q] - Y[p]);
+        al[m] = fmaf(f, A[q] - A[p], A[p]);
+        be[m] = fmaf(f, B[q] - B[p], B[p]);
+        m++;
+    }
+    if (m != 2) return false;
+    lines = make_float4(al[0], be[0], al[1], be[1]);
+    return true;
+}
+
 // One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
 // record (its cell's projection into the views, candidate rows, flags), and
 // the point joins the splat's work list if any pixel row can receive it.
@@ -520,7 +546,31 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
             ny = uint32_t(int(fy1) - int(fy0) + 1);
         }
         const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
-        const uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
+        uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
+        // one candidate row: the row's crossing lines of the cell and the
+        // triangle (the row is moved just inside both y-extents if it only
+        // lies within their margin); otherwise the corner projections
+        float4 L0 = make_float4(A[0], A[1], A[2], A[3]), L1 = make_float4(B[0], B[1], B[2], B[3]);
+        bool box = true;
+        if (ny == 1) {
+            const float yc = float(y0) + 0.5f;
+            const float kEps = 1e-3f;
+            const float tA3[3] = {tp.a.x, tp.a.y, tp.a.z}, tB3[3] = {tp.b.x, tp.b.y, tp.b.z};
+            const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
+            float4 lc, lt;
+            const bool flat = !(cymx - cymn > 4.0f * kEps) || !(tymx - tymn > 4.0f * kEps);
+            const float ycc = fminf(fmaxf(yc, cymn + kEps), cymx - kEps);
+            const float yct = fminf(fmaxf(yc, tymn + kEps), tymx - kEps);
+            const bool single = __ldg(a.counts + pt.x) == 1u;
+            const bool okc = single || row_crossings<4>(A, B, Y, ycc, lc);
+            const bool okt = interior || row_crossings<3>(tA3, tB3, tY3, yct, lt);
+            if (!flat && okc && okt) {
+                box = false;
+                L0 = single ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lc;
+                L1 = interior ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lt;
+            }
+        }
+        if (box) flags |= kFlagBox;
 
         // warp-aggregated appends: points with candidate rows to the work
         // list, points reaching the eyes' plane to the near list
@@ -538,8 +588,8 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         nbase = __shfl_sync(mask, nbase, leader);
         if (ny > 0) {
             WorkRec* w = a.work + base + __popc(bal & below);
-            w->A = make_float4(A[0], A[1], A[2], A[3]);
-            w->B = make_float4(B[0], B[1], B[2], B[3]);
+            w->L0 = L0;
+            w->L1 = L1;
             w->meta = make_uint4(y0 | (ny << 14) | (flags << 29), pt.y, pt.x, p);
         }
         if (near) a.near[nbase + __popc(bnear & below)] = p;

@@ -22,17 +22,20 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
-// One half-warp (16 lanes) per point of the work list, lanes over the
-// rendered views in chunks of 16; a warp carries two points at a time.
+// One half-warp (16 lanes) per point of the work list, each lane taking up to
+// kSlots views of the point (views g + 16 s + lane of a group g of 64); a
+// warp carries two points at a time.
 //
-// Candidates. The point's work record holds its cell corners projected into
-// every view (pixel x = A + B Ex, pixel y = Y, the same in all views since
-// every eye lies on y = 0, z = D) and its candidate rows: rows inside both the
-// cell's and the triangle's y-extent. Per chunk each lane forms its view's
-// candidate columns, the cell's and the triangle's x-extents intersected and
-// widened by a small margin; a scan of the 16 candidate counts then gives
-// every lane one candidate pixel per pass, so no lane loops over pixels on
-// its own.
+// Candidates. Candidate rows are the pixel-centre rows inside both the
+// cell's and the triangle's projected y-extent, the same in every view since
+// every eye lies on y = 0, z = D. A lane forms each of its views' candidate
+// columns: for a point with one candidate row, between the row's crossings
+// with the projected cell and with the projected triangle, which move along
+// lines x = alpha + beta Ex; otherwise within the intersected x-extents
+// (pixel x = A + B Ex per vertex). Ranges are widened by a small margin. A
+// scan of the lanes' candidate counts over the whole group then hands every
+// lane one candidate pixel per pass, so no lane loops over pixels on its own
+// and a point with few candidates needs a single pass.
 //
 // Test. Each candidate takes the per-pixel test in the oracle's plane-space
 // form: the pixel centre's ray from the eye meets the triangle's plane at t
@@ -45,6 +48,7 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
 // Points whose cell or triangle reaches the eyes' plane (none in front-only
 // scenes) are listed apart and splatted by k_splat_near.
 constexpr int kSplatWarps = 8;
+constexpr int kSlots = 4;
 
 __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float num, float qEx, float qEy,
                                            float qEz, const float4& q1, const float4& q2, const float4& q3,
@@ -92,43 +96,61 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
 
     for (uint32_t k = hw; k < n; k += n_hw) {
         const WorkRec* wr = a.work + k;
-        const float4 cA = __ldg(&wr->A), cB = __ldg(&wr->B);
+        const float4 L0 = __ldg(&wr->L0), L1 = __ldg(&wr->L1);
         const uint4 meta = __ldg(&wr->meta);
         const uint32_t tri = meta.z;
         const unsigned long long pid = meta.w;
         const TriRec* r = a.rec + tri;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
-        const TriProj* tpp = a.tproj + tri;
-        const float4 tA = __ldg(&tpp->a), tB = __ldg(&tpp->b);
         const int y0 = int(meta.x & 0x3fffu);
         const uint32_t ny = (meta.x >> 14) & 0x7fffu;
         const uint32_t flags = meta.x >> 29;
         const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
+        const bool box = flags & kFlagBox;
+        float4 tA = make_float4(0.f, 0.f, 0.f, 0.f), tB = tA;
+        if (box) {
+            const TriProj* tpp = a.tproj + tri;
+            tA = __ldg(&tpp->a);
+            tB = __ldg(&tpp->b);
+        }
         const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
         const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
         const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
         const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
 
-        for (int base = 0; base < c.nr; base += 16) {
-            const int v = base + sub;
-            uint32_t nx = 0;
-            int x0 = 0;
-            if (v < c.nr) {
-                const float Ex = s_ex[v];
-                const float X0 = fmaf(cB.x, Ex, cA.x), X1 = fmaf(cB.y, Ex, cA.y);
-                const float X2 = fmaf(cB.z, Ex, cA.z), X3 = fmaf(cB.w, Ex, cA.w);
-                const float T0 = fmaf(tB.x, Ex, tA.x), T1 = fmaf(tB.y, Ex, tA.y), T2 = fmaf(tB.z, Ex, tA.z);
-                const float xmn = fmaxf(fminf(fminf(X0, X1), fminf(X2, X3)), fminf(fminf(T0, T1), T2));
-                const float xmx = fminf(fmaxf(fmaxf(X0, X1), fmaxf(X2, X3)), fmaxf(fmaxf(T0, T1), T2));
-                const float fx0 = fmaxf(ceilf(xmn - 0.5f - kBoxPad), 0.0f);
-                const float fx1 = fminf(floorf(xmx - 0.5f + kBoxPad), W1);
-                if (fx0 <= fx1) {
-                    x0 = int(fx0);
-                    nx = uint32_t(int(fx1) - x0 + 1);
+        for (int g = 0; g < c.nr; g += 16 * kSlots) {
+            uint32_t pk[kSlots];      // x0 | n_columns << 14 of the lane's views
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int sl = 0; sl < kSlots; sl++) {
+                const int v = g + 16 * sl + sub;
+                pk[sl] = 0u;
+                if (v < c.nr) {
+                    const float Ex = s_ex[v];
+                    float lo, hi;
+                    if (!box) {
+                        const float xa = fmaf(L0.y, Ex, L0.x), xb = fmaf(L0.w, Ex, L0.z);
+                        const float ta = fmaf(L1.y, Ex, L1.x), tb = fmaf(L1.w, Ex, L1.z);
+                        lo = fmaxf(fminf(xa, xb), fminf(ta, tb));
+                        hi = fminf(fmaxf(xa, xb), fmaxf(ta, tb));
+                    } else {
+                        const float X0 = fmaf(L1.x, Ex, L0.x), X1 = fmaf(L1.y, Ex, L0.y);
+                        const float X2 = fmaf(L1.z, Ex, L0.z), X3 = fmaf(L1.w, Ex, L0.w);
+                        const float T0 = fmaf(tB.x, Ex, tA.x), T1 = fmaf(tB.y, Ex, tA.y);
+                        const float T2 = fmaf(tB.z, Ex, tA.z);
+                        lo = fmaxf(fminf(fminf(X0, X1), fminf(X2, X3)), fminf(fminf(T0, T1), T2));
+                        hi = fminf(fmaxf(fmaxf(X0, X1), fmaxf(X2, X3)), fmaxf(fmaxf(T0, T1), T2));
+                    }
+                    const float fx0 = fmaxf(ceilf(lo - 0.5f - kBoxPad), 0.0f);
+                    const float fx1 = fminf(floorf(hi - 0.5f + kBoxPad), W1);
+                    if (fx0 <= fx1) {
+                        const uint32_t x0 = uint32_t(int(fx0)), nx = uint32_t(int(fx1)) - x0 + 1u;
+                        pk[sl] = x0 | (nx << 14);
+                        cnt += nx * ny;
+                    }
                 }
             }
-            const uint32_t cnt = nx * ny;
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 16; o <<= 1) {
@@ -147,13 +169,26 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                     if (t <= q) own += st;
                 }
                 const uint32_t o_excl = __shfl_sync(hmask, excl, own, 16);
-                const uint32_t o_nx = __shfl_sync(hmask, nx, own, 16);
-                const int o_x0 = __shfl_sync(hmask, x0, own, 16);
+                uint32_t opk[kSlots];
+#pragma unroll
+                for (int sl = 0; sl < kSlots; sl++) opk[sl] = __shfl_sync(hmask, pk[sl], own, 16);
                 if (q >= total) continue;
-                const uint32_t rr = q - o_excl;
+                // the owner's view slot holding candidate q
+                uint32_t rr = q - o_excl, sel = opk[0];
+                int slot = 0;
+#pragma unroll
+                for (int sl = 0; sl + 1 < kSlots; sl++) {
+                    const uint32_t cs = (opk[sl] >> 14) * ny;
+                    if (slot == sl && rr >= cs) {
+                        rr -= cs;
+                        slot = sl + 1;
+                        sel = opk[sl + 1];
+                    }
+                }
+                const uint32_t o_nx = sel >> 14;
                 const uint32_t ry = ny == 1 ? 0u : rr / o_nx;
-                const int x = o_x0 + int(rr - ry * o_nx), y = y0 + int(ry);
-                const int vo = base + own;
+                const int x = int(sel & 0x3fffu) + int(rr - ry * o_nx), y = y0 + int(ry);
+                const int vo = g + 16 * slot + own;
                 const float Ex_o = s_ex[vo];
                 const float qEx = Ex_o - q0.x;
                 const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
