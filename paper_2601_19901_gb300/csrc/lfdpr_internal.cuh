@@ -14,7 +14,8 @@ namespace lfdpr {
 constexpr int kMaxRenderViews = 512;
 constexpr int kMaxCell = 65535;          // lattice indices are stored as u16
 constexpr int kSetupThreads = 256;       // triangles per set-up / emit block
-constexpr float kBoxPad = 1.0f / 16.0f;  // margin (pixels) of candidate pixel ranges against rounding
+constexpr float kBoxPad = 1.0f / 256.0f; // margin (pixels) of candidate pixel ranges against rounding
+                                         // (projection error is about 1e-4 pixel)
 
 // Display constants, passed by value to every kernel.
 struct DispConst {
@@ -31,6 +32,7 @@ struct DispConst {
     float pw, ph;         // pixel size on the focal plane (fw/W, fh/H)
     float ipw, iph;       // W/fw, H/fh
     float x0, y0;         // focal rectangle corner: -fw/2, fh/2
+    float ex_max;         // largest |eye x| of the rendered views
     float inv_pitch, slant, phase_offset;
     float xtalk, xtalk_c; // crosstalk weight x and centre weight 1 - 2x
 };

@@ -220,6 +220,8 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     d->h_ex.resize(nr);
     for (int k = 0; k < nr; k++)
         d->h_ex[k] = float(double(s.view_dist) * std::tan(eye_angle_deg(s, k) * M_PI / 180.0));
+    c.ex_max = 0.0f;
+    for (int k = 0; k < nr; k++) c.ex_max = std::fmax(c.ex_max, std::fabs(d->h_ex[k]));
 
     const uint64_t npix = uint64_t(s.view_w) * s.view_h * nr;
     cudaError_t e;

@@ -470,10 +470,13 @@ __device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q
 // vertices (pixel x = A + B Ex, y = Y): for each edge crossing the row
 // (half-open in y, so a convex polygon has exactly two when yc lies strictly
 // inside its y-extent) the line alpha + beta Ex of the crossing's x. Returns
-// false unless there are exactly two.
+// false unless there are exactly two, each on an edge whose y-span is at
+// least 1/8 of its largest x-span over the views (the crossing's x error is
+// about |dx| / |dy| times the projection error, about 1e-4 pixel, so it stays
+// an order of magnitude inside the candidate margin).
 template <int N>
 __device__ __forceinline__ bool row_crossings(const float* A, const float* B, const float* Y, float yc,
-                                              float4& lines) {
+                                              float ex_max, float4& lines) {
     float al[2], be[2];
     int m = 0;
 #pragma unroll
@@ -481,7 +484,8 @@ __device__ __forceinline__ bool row_crossings(const float* A, const float* B, co
         const int p = e, q = e + 1 == N ? 0 : e + 1;
         const bool cross = (Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]);
         if (!cross) continue;
-        if (m == 2) return false;
+        const float dxmax = fmaf(fabsf(B[q] - B[p]), ex_max, fabsf(A[q] - A[p]));
+        if (m == 2 || !(fabsf(Y[q] - Y[p]) >= 0.125f * dxmax)) return false;
         const float f = __fdividef(yc - Y[p], Y[q] - Y[p]);
         al[m] = fmaf(f, A[q] - A[p], A[p]);
         be[m] = fmaf(f, B[q] - B[p], B[p]);
@@ -548,23 +552,19 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
         uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
         // one candidate row: the row's crossing lines of the cell and the
-        // triangle (the row is moved just inside both y-extents if it only
-        // lies within their margin); otherwise the corner projections
+        // triangle when each polygon has exactly two well-conditioned
+        // crossings; otherwise the corner projections (x-extents)
         float4 L0 = make_float4(A[0], A[1], A[2], A[3]), L1 = make_float4(B[0], B[1], B[2], B[3]);
         bool box = true;
         if (ny == 1) {
             const float yc = float(y0) + 0.5f;
-            const float kEps = 1e-3f;
             const float tA3[3] = {tp.a.x, tp.a.y, tp.a.z}, tB3[3] = {tp.b.x, tp.b.y, tp.b.z};
             const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
             float4 lc, lt;
-            const bool flat = !(cymx - cymn > 4.0f * kEps) || !(tymx - tymn > 4.0f * kEps);
-            const float ycc = fminf(fmaxf(yc, cymn + kEps), cymx - kEps);
-            const float yct = fminf(fmaxf(yc, tymn + kEps), tymx - kEps);
             const bool single = __ldg(a.counts + pt.x) == 1u;
-            const bool okc = single || row_crossings<4>(A, B, Y, ycc, lc);
-            const bool okt = interior || row_crossings<3>(tA3, tB3, tY3, yct, lt);
-            if (!flat && okc && okt) {
+            const bool okc = single || row_crossings<4>(A, B, Y, yc, c.ex_max, lc);
+            const bool okt = interior || row_crossings<3>(tA3, tB3, tY3, yc, c.ex_max, lt);
+            if (okc && okt) {
                 box = false;
                 L0 = single ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lc;
                 L1 = interior ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lt;
