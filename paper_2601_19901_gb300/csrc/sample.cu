@@ -32,6 +32,20 @@ __device__ __forceinline__ void transform(const float* m, float x, float y, floa
 // Visibility (Sec. 3): dropped iff for every view all three vertices are on
 // the outer side of one common frustum plane. Planes as linear forms,
 // negative outside; top, bottom, near and far are shared by all views.
+__device__ __forceinline__ bool seen_by(const DispConst& c, float e, const float P[3][3]) {
+    const float lx = -c.fw2 - e, rx = c.fw2 - e;
+    bool out_l = true, out_r = true;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float dep = c.D - P[k][2];
+        const float l = fmaf(P[k][0] - e, c.D, -(lx * dep));
+        const float r = fmaf(rx, dep, -((P[k][0] - e) * c.D));
+        out_l &= l < 0.0f;
+        out_r &= r < 0.0f;
+    }
+    return !(out_l || out_r);
+}
+
 __device__ bool culled(const DispConst& c, const float* __restrict__ ex, const float P[3][3]) {
     bool out_t = true, out_b = true, out_n = true, out_f = true;
 #pragma unroll
@@ -45,20 +59,21 @@ __device__ bool culled(const DispConst& c, const float* __restrict__ ex, const f
         out_f &= (c.far_z - dep) < 0.0f;
     }
     if (out_t || out_b || out_n || out_f) return true;
+    // Any one view that sees the triangle settles it. Try first the view
+    // whose eye centres the centroid in the focal rectangle (the eye x at
+    // which the centroid projects to x = 0 is x_c D / z_c), then all views.
+    const float cx = (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f);
+    const float cz = (P[0][2] + P[1][2] + P[2][2]) * (1.0f / 3.0f);
+    const float target = fabsf(cz) > 1e-6f ? __fdividef(cx * c.D, cz) : 0.0f;
+    int vb = 0;
+    float best = INFINITY;
     for (int v = 0; v < c.nr; v++) {
-        const float e = ex[v];
-        const float lx = -c.fw2 - e, rx = c.fw2 - e;
-        bool out_l = true, out_r = true;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const float dep = c.D - P[k][2];
-            const float l = fmaf(P[k][0] - e, c.D, -(lx * dep));
-            const float r = fmaf(rx, dep, -((P[k][0] - e) * c.D));
-            out_l &= l < 0.0f;
-            out_r &= r < 0.0f;
-        }
-        if (!(out_l || out_r)) return false;
+        const float dx = fabsf(ex[v] - target);
+        if (dx < best) { best = dx; vb = v; }
     }
+    if (seen_by(c, ex[vb], P)) return false;
+    for (int v = 0; v < c.nr; v++)
+        if (seen_by(c, ex[v], P)) return false;
     return true;
 }
 
@@ -173,12 +188,19 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     const float umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
 
     // closest and farthest eye (Fig. 4): height over the plane plus the
-    // in-plane distance to the 2-D triangle, over every rendered view
-    float d2min = INFINITY, d2max = -INFINITY;
+    // in-plane distance to the 2-D triangle; min and max over every rendered
+    // view. exact_d2(v) is the defining formula for view v. Only views that
+    // can hold the minimum or the maximum are evaluated with it: cheap bounds
+    // h^2 + max(0, |q - c| - R)^2 <= d_v^2 <= h^2 + |q - c|^2 (c the 2-D
+    // centroid, R the largest vertex distance from it, both widened against
+    // rounding) rule the others out against the exact values of the view
+    // whose eye is nearest the triangle's centroid and of the two end views.
+    // The result equals the minimum and maximum over all views.
     const float ie01 = seg_inv_len2(0.0f, 0.0f, a1, b1), ie12 = seg_inv_len2(a1, b1, a2, b2);
     const float ie20 = seg_inv_len2(a2, b2, 0.0f, 0.0f);
-    for (int v = 0; v < c.nr; v++) {
-        const float qx = a.ex[v] - P[0][0], qy = 0.0f - P[0][1], qz = c.D - P[0][2];
+    const float qy = 0.0f - P[0][1], qz = c.D - P[0][2];
+    auto exact_d2 = [&](int v) -> float {
+        const float qx = a.ex[v] - P[0][0];
         const float qu = dot3(qx, qy, qz, ux, uy, uz);
         const float qv = dot3(qx, qy, qz, vx, vy, vz);
         const float h = dot3(qx, qy, qz, nx, ny, nz);
@@ -189,9 +211,53 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
         if (!inside_either(w0, w1, w2))
             d2 = fminf(fminf(seg_dist2(0.0f, 0.0f, a1, b1, ie01, qu, qv), seg_dist2(a1, b1, a2, b2, ie12, qu, qv)),
                        seg_dist2(a2, b2, 0.0f, 0.0f, ie20, qu, qv));
-        const float dd = fmaf(h, h, d2);
-        d2min = fminf(d2min, dd);
-        d2max = fmaxf(d2max, dd);
+        return fmaf(h, h, d2);
+    };
+    int vs = 0;
+    {
+        const float cxw = (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f);
+        float best = INFINITY;
+        for (int v = 0; v < c.nr; v++) {
+            const float dx = fabsf(a.ex[v] - cxw);
+            if (dx < best) { best = dx; vs = v; }
+        }
+    }
+    float d2min = exact_d2(vs), d2max = d2min;
+    {
+        const float e0 = exact_d2(0), e1 = exact_d2(c.nr - 1);
+        d2min = fminf(d2min, fminf(e0, e1));
+        d2max = fmaxf(d2max, fmaxf(e0, e1));
+    }
+    {
+        const float cu = (a1 + a2) * (1.0f / 3.0f), cv = (b1 + b2) * (1.0f / 3.0f);
+        const float r0 = fmaf(cu, cu, cv * cv);
+        const float r1 = fmaf(a1 - cu, a1 - cu, (b1 - cv) * (b1 - cv));
+        const float r2 = fmaf(a2 - cu, a2 - cu, (b2 - cv) * (b2 - cv));
+        const float R = sqrtf(fmaxf(fmaxf(r0, r1), r2)) * 1.0001f + 1e-7f;
+        const float ku = fmaf(qy, uy, qz * uz), kv = fmaf(qy, vy, qz * vz), kh = fmaf(qy, ny, qz * nz);
+        for (int blk = 0; blk < c.nr; blk += 64) {
+            const int nb = c.nr - blk < 64 ? c.nr - blk : 64;
+            unsigned long long mask = 0ull;
+            for (int b = 0; b < nb; b++) {
+                const float qx = a.ex[blk + b] - P[0][0];
+                const float du = fmaf(qx, ux, ku) - cu, dv = fmaf(qx, vx, kv) - cv;
+                const float h = fmaf(qx, nx, kh);
+                const float hh = h * h;
+                const float rho2 = fmaf(du, du, dv * dv);
+                const float rho = rho2 * rsqrtf(fmaxf(rho2, 1e-30f));
+                const float g = fmaxf(fmaf(rho, 0.99999f, -R), 0.0f);
+                const float lo = fmaf(g, g, hh) * 0.9999f - 1e-12f;
+                const float hi = (hh + rho2) * 1.0001f + 1e-12f;
+                if (lo < d2min || hi > d2max) mask |= 1ull << b;
+            }
+            while (mask) {
+                const int b = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
+                const float e = exact_d2(blk + b);
+                d2min = fminf(d2min, e);
+                d2max = fmaxf(d2max, e);
+            }
+        }
     }
     const float dmin = fmaxf(__fsqrt_rn(d2min), c.near_z);
     const float dmax = fmaxf(__fsqrt_rn(d2max), c.near_z);

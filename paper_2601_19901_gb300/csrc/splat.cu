@@ -49,6 +49,8 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
 // scenes) are listed apart and splatted by k_splat_near.
 constexpr int kSplatWarps = 8;
 constexpr int kSlots = 4;
+// Ask L2 for the line holding p (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float num, float qEx, float qEy,
                                            float qEz, const float4& q1, const float4& q2, const float4& q3,
@@ -96,11 +98,13 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
 
     for (uint32_t k = hw; k < n; k += n_hw) {
         const WorkRec* wr = a.work + k;
+        if (sub == 0 && k + n_hw < n) prefetch_l2(a.work + k + n_hw);   // next point's record
         const float4 L0 = __ldg(&wr->L0), L1 = __ldg(&wr->L1);
         const uint4 meta = __ldg(&wr->meta);
         const uint32_t tri = meta.z;
         const unsigned long long pid = meta.w;
         const TriRec* r = a.rec + tri;
+        if (sub == 1 && k + n_hw < n) prefetch_l2(a.rec + __ldg(&a.work[k + n_hw].meta.z));
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
         const int y0 = int(meta.x & 0x3fffu);
