@@ -61,8 +61,9 @@ typedef enum {
  * recon = 1 renders 2N views at half-interval steps and reconstructs N with a
  * [1/4, 1/2, 1/4] tent; crosstalk x > 0 mixes each view with its +-1
  * neighbours at weight x before interleaving. max_points is the point-buffer
- * capacity (0 = 1 << 24); each point of capacity takes 68 B of device memory
- * (the 16-B point record, a 48-B splat work record, a 4-B near-list entry).
+ * capacity (0 = 1 << 23); each point of capacity takes 148 B of device
+ * memory (the 16-B point record, a 48-B splat work record, a 4-B near-list
+ * entry and an 80-B resolve record).
  */
 typedef struct {
     int32_t n_views, view_w, view_h;
@@ -153,7 +154,7 @@ typedef struct {
  * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1},
  * 0 <= crosstalk < 0.5) and allocate the display's device buffers: view key
  * buffers (8 B per rendered-view pixel, Sec. 5.2), RGBA8 views, the point
- * buffers (68 B per point of capacity) and the panel scratch. Uses the current CUDA device.
+ * buffers (148 B per point of capacity) and the panel scratch. Uses the current CUDA device.
  * On success *out owns them. Errors: EINVAL, ENOMEM, EDEVICE, ECUDA.
  */
 lfdpr_status lfdpr_create_display(const lfdpr_display_desc *desc, lfdpr_display **out);

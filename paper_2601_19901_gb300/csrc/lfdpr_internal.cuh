@@ -96,6 +96,18 @@ struct WorkRec {
     float4 L0, L1;
     uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
+// Per-point data of the resolve (Eq. 8-9): the cell's four world corners
+// (x, y) and their projection factors s = D / (D - z) (computed exactly as
+// the resolve's defining formula does), the splat's texture area, the two
+// Eq. 4-5 bounds and tv_min / tv_max.
+struct ResolveRec {
+    float4 c0;    // x0 y0 s0 x1
+    float4 c1;    // y1 s1 x2 y2
+    float4 c2;    // s2 x3 y3 s3
+    float4 m;     // splat texture area, vpuv_min, vpuv_max, (unused)
+    uint4 tv;     // tv_min RGBA8, tv_max RGBA8, (unused)
+};
+
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]
 constexpr uint32_t kFlagBox = 4u;       // candidates from x-extents (L0, L1 = corner A, B)
@@ -196,6 +208,7 @@ struct FrameArgs {
     TriProj* tproj;                  // [n_tris] (optional: null skips it)
     WorkRec* work;                   // [max_points] the splat's work list
     uint32_t* near;                  // [max_points] points whose cell or triangle reaches the eyes' plane
+    ResolveRec* rrec;                // [max_points] per-point resolve data
     uint64_t* keys;
     uint8_t* views;
     Counters* ctr;

@@ -25,6 +25,7 @@ struct lfdpr_display {
     uint32_t max_points = 0;
     WorkRec* work = nullptr;
     uint32_t* near = nullptr;
+    ResolveRec* rrec = nullptr;
     uint64_t* keys = nullptr;
     uint8_t* views = nullptr;
     uint8_t* panel = nullptr;      // device scratch for host-memory panels
@@ -106,6 +107,7 @@ void free_display(lfdpr_display* d) {
     cudaFree(d->points);
     cudaFree(d->work);
     cudaFree(d->near);
+    cudaFree(d->rrec);
     cudaFree(d->keys);
     cudaFree(d->views);
     cudaFree(d->panel);
@@ -183,7 +185,7 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     lfdpr_display* d = new (std::nothrow) lfdpr_display();
     if (!d) return fail(LFDPR_ENOMEM, "host allocation failed");
     d->desc = s;
-    if (d->desc.max_points == 0) d->desc.max_points = 1LL << 24;
+    if (d->desc.max_points == 0) d->desc.max_points = 1LL << 23;
     d->max_points = uint32_t(d->desc.max_points);
     CK(cudaGetDevice(&d->device), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device), "sm count");
@@ -229,6 +231,7 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
         (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->work, sizeof(WorkRec) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->near, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = cudaMalloc(&d->rrec, sizeof(ResolveRec) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->keys, 8u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->views, 4u * npix)) != cudaSuccess ||
         (e = cudaMalloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
@@ -389,6 +392,7 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     a.tproj = mesh->tproj;
     a.work = disp->work;
     a.near = disp->near;
+    a.rrec = disp->rrec;
     a.keys = disp->keys;
     a.views = disp->views;
     a.ctr = disp->ctr;

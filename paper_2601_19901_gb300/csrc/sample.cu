@@ -565,7 +565,7 @@ __device__ __forceinline__ bool row_crossings(const float* A, const float* B, co
 // One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
 // record (its cell's projection into the views, candidate rows, flags), and
 // the point joins the splat's work list if any pixel row can receive it.
-__global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
+__global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
     if (a.ctr->overflow) return;
     const DispConst& c = a.dc;
     const uint32_t n = a.ctr->n_points;
@@ -587,10 +587,11 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
         const uint32_t tmin = trilinear(a.pool, td, s, t, q7.z);
         const uint32_t tmax = trilinear(a.pool, td, s, t, q7.w);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
+        const float4 q5 = __ldg(&r->q[5]);
 
         // splat work record
         const TriProj tp = a.tproj[pt.x];
-        float A[4], B[4], Y[4];
+        float A[4], B[4], Y[4], Cx[4], Cy[4], Cs[4];
         bool near = !((c.D - tp.b.w) > 1e-4f * c.D);
         bool interior = true;
 #pragma unroll
@@ -598,6 +599,9 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
             const int ia = int(i) + (k == 1 || k == 2), jb = int(j) + (k >= 2);
             float C[3];
             lattice_corner(q0, q1, q2, q3, ia, jb, C);
+            Cx[k] = C[0];
+            Cy[k] = C[1];
+            Cs[k] = __fdiv_rn(c.D, c.D - C[2]);
             near |= !((c.D - C[2]) > 1e-4f * c.D);
             project_point(c.D, c.x0, c.y0, c.ipw, c.iph, C[0], C[1], C[2], A[k], B[k], Y[k]);
             const float uu = float(ia) * su + q2.w, vv = float(jb) * sv + q3.w;
@@ -637,6 +641,13 @@ __global__ void __launch_bounds__(256) k_fetch(FrameArgs a) {
             }
         }
         if (box) flags |= kFlagBox;
+
+        ResolveRec* rr = a.rrec + p;
+        rr->c0 = make_float4(Cx[0], Cy[0], Cs[0], Cx[1]);
+        rr->c1 = make_float4(Cy[1], Cs[1], Cx[2], Cy[2]);
+        rr->c2 = make_float4(Cs[2], Cx[3], Cy[3], Cs[3]);
+        rr->m = make_float4(q5.x, q5.y, q5.z, 0.0f);
+        rr->tv = make_uint4(tmin, tmax, 0u, 0u);
 
         // warp-aggregated appends: points with candidate rows to the work
         // list, points reaching the eyes' plane to the near list

@@ -5,9 +5,10 @@
 //              inside the point's projected cell and its projected triangle,
 //              at a depth in [near, far], does
 //              atomicMin(key, float_bits(t) << 32 | point id).
-//   k_resolve  one thread per view pixel: the winning point's cell corners are
-//              projected for the splat's pixel area (shoelace), Eq. 8 gives the
-//              view's texture area, Eq. 9 interpolates tv_min..tv_max.
+//   k_resolve  one thread per view pixel: the winning point's cell corners
+//              (from its resolve record) are projected for the splat's pixel
+//              area (shoelace), Eq. 8 gives the view's texture area, Eq. 9
+//              interpolates tv_min..tv_max.
 #include "lfdpr_internal.cuh"
 
 namespace lfdpr {
@@ -267,19 +268,17 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
         if (key != ~0ull) {
             const int v = int(o / npix);
             const float Ex = __ldg(a.ex + v);
-            const uint4 pt = a.points[uint32_t(key)];
-            const TriRec* r = a.rec + pt.x;
-            const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
-            const float4 q3 = __ldg(&r->q[3]), q5 = __ldg(&r->q[5]);
-            const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
+            const ResolveRec* rp = a.rrec + uint32_t(key);
+            const float4 c0 = __ldg(&rp->c0), c1 = __ldg(&rp->c1), c2 = __ldg(&rp->c2);
+            const float4 m = __ldg(&rp->m);
+            const uint4 tv = __ldg(&rp->tv);
+            const float cx[4] = {c0.x, c0.w, c1.z, c2.y}, cy[4] = {c0.y, c1.x, c1.w, c2.z};
+            const float cs[4] = {c0.z, c1.y, c2.x, c2.w};
             float X[4], Y[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                float C[3];
-                cell_corner(q0, q1, q2, q3, i + (k == 1 || k == 2), j + (k >= 2), C);
-                const float s = __fdiv_rn(c.D, c.D - C[2]);
-                const float sx = fmaf(C[0] - Ex, s, Ex);
-                const float sy = C[1] * s;
+                const float sx = fmaf(cx[k] - Ex, cs[k], Ex);
+                const float sy = cy[k] * cs[k];
                 X[k] = (sx - c.x0) * c.ipw;
                 Y[k] = (c.y0 - sy) * c.iph;
             }
@@ -290,13 +289,13 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
                 acc = acc + fmaf(X[k], Y[k1], -(X[k1] * Y[k]));
             }
             const float area_px = 0.5f * fabsf(acc);
-            const float vmin = q5.y, vmax = q5.z;
-            const float size_vse = __fdiv_rn(q5.x, fminf(1.0f, area_px));
+            const float vmin = m.y, vmax = m.z;
+            const float size_vse = __fdiv_rn(m.x, fminf(1.0f, area_px));
             const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
             const float w = vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
 #pragma unroll
             for (int ch = 0; ch < 4; ch++) {
-                const float lo = float((pt.z >> (8 * ch)) & 255u), hi = float((pt.w >> (8 * ch)) & 255u);
+                const float lo = float((tv.x >> (8 * ch)) & 255u), hi = float((tv.y >> (8 * ch)) & 255u);
                 out |= uint32_t(round_u8(fmaf(w, hi - lo, lo))) << (8 * ch);
             }
         }
