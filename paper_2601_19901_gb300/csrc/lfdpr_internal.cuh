@@ -13,6 +13,7 @@ namespace lfdpr {
 
 constexpr int kMaxRenderViews = 512;
 constexpr int kMaxCell = 65535;          // lattice indices are stored as u16
+constexpr int kMaxLevels = 16;           // mip levels of a texture (16384 = 2^14 texels a side)
 constexpr int kSetupThreads = 256;       // triangles per set-up / emit block
 constexpr float kBoxPad = 1.0f / 256.0f; // margin (pixels) of candidate pixel ranges against rounding
                                          // (projection error is about 1e-4 pixel)
@@ -197,6 +198,7 @@ struct FrameArgs {
     const uint32_t* tri_tex;
     const TexDesc* tex;
     const uint8_t* pool;
+    const uint64_t* lvl;             // [n_tex][kMaxLevels] byte offset of each mip level in the pool
     uint32_t n_tris, n_tex;
     TriRec* rec;
     uint32_t* counts;

@@ -47,6 +47,7 @@ struct lfdpr_mesh {
     uint32_t* tri_tex = nullptr;
     uint8_t* pool = nullptr;
     TexDesc* tex = nullptr;
+    uint64_t* lvl = nullptr;
     TriRec* rec = nullptr;
     TriProj* tproj = nullptr;
     uint32_t* counts = nullptr;
@@ -123,6 +124,7 @@ void free_mesh(lfdpr_mesh* m) {
     cudaFree(m->tri_tex);
     cudaFree(m->pool);
     cudaFree(m->tex);
+    cudaFree(m->lvl);
     cudaFree(m->rec);
     cudaFree(m->tproj);
     cudaFree(m->counts);
@@ -284,6 +286,7 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
     for (uint64_t k = 0; k < 2ull * n_verts; k++)
         if (!std::isfinite(uv[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite texture coordinate");
     std::vector<TexDesc> td(n_tex);
+    std::vector<uint64_t> lvl((size_t)n_tex * kMaxLevels, 0);
     uint64_t pool_bytes = 0;
     for (uint32_t k = 0; k < n_tex; k++) {
         const uint32_t w = tex_wh[2 * k], h = tex_wh[2 * k + 1];
@@ -295,6 +298,12 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
         td[k].h = h;
         td[k].levels = mip_levels(w, h);
         td[k].pad = 0;
+        uint64_t off = pool_bytes;
+        for (uint32_t l = 0; l < td[k].levels; l++) {
+            lvl[(size_t)k * kMaxLevels + l] = off;
+            const uint64_t lw = (w >> l) ? (w >> l) : 1, lh = (h >> l) ? (h >> l) : 1;
+            off += lw * lh * 4u;
+        }
         pool_bytes += (mip_bytes(w, h) + 255) & ~uint64_t(255);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -311,6 +320,7 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
         (e = cudaMalloc(&m->idx, 12u * nt)) != cudaSuccess || (e = cudaMalloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
         (e = cudaMalloc(&m->pool, pool_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&m->tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
+        (e = cudaMalloc(&m->lvl, sizeof(uint64_t) * kMaxLevels * n_tex)) != cudaSuccess ||
         (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
         (e = cudaMalloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
         (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
@@ -335,6 +345,8 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
         CKM(cudaMemcpyAsync(m->tri_tex, tri_tex, 4u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload tri_tex");
     }
     CKM(cudaMemcpyAsync(m->tex, td.data(), sizeof(TexDesc) * n_tex, cudaMemcpyHostToDevice, s), "upload tex table");
+    CKM(cudaMemcpyAsync(m->lvl, lvl.data(), sizeof(uint64_t) * kMaxLevels * n_tex, cudaMemcpyHostToDevice, s),
+        "upload level offsets");
     for (uint32_t k = 0; k < n_tex; k++) {
         uint32_t w = td[k].w, h = td[k].h;
         uint8_t* lvl = m->pool + td[k].offset;
@@ -380,6 +392,7 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     a.tri_tex = mesh->tri_tex;
     a.tex = mesh->tex;
     a.pool = mesh->pool;
+    a.lvl = mesh->lvl;
     a.n_tris = mesh->n_tris;
     a.n_tex = mesh->n_tex;
     a.rec = mesh->rec;

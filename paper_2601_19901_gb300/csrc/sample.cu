@@ -467,59 +467,69 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
     }
 }
 
-// Bilinear sample of one mip level, wrap addressing, texel centres at (k+1/2)/w.
-__device__ __forceinline__ void bilinear(const uint8_t* __restrict__ lvl, uint32_t w, uint32_t h,
-                                         float s, float t, float out[4]) {
+// The two trilinear fetches of a point (Sec. 3.3: tv_min at lod_a, tv_max at
+// lod_b). Each: LOD clamped to [0, L_max], level floor(LOD) blended to the
+// next by the fraction (FP32 weights), bilinear with wrap addressing and
+// texel centres at (k+1/2)/w, rounded half-even to RGBA8. All sixteen texel
+// loads are issued before any blending: per LOD, level floor(LOD) and the
+// next level (clamped to the last; unused when the fraction is 0). loff[l] is
+// the byte offset of level l in the pool.
+__device__ __forceinline__ void trilinear_pair(const uint8_t* __restrict__ pool, const uint64_t* __restrict__ loff,
+                                               uint32_t w, uint32_t h, int L, float s, float t, float lod_a,
+                                               float lod_b, uint32_t& out_a, uint32_t& out_b) {
     if (!isfinite(s)) s = 0.0f;
     if (!isfinite(t)) t = 0.0f;
     const float fs = s - floorf(s), ft = t - floorf(t);
-    const float x = fmaf(fs, float(w), -0.5f), y = fmaf(ft, float(h), -0.5f);
-    const float xf = floorf(x), yf = floorf(y);
-    const float fx = x - xf, fy = y - yf;
-    const uint32_t ix0 = uint32_t(int(xf)) & (w - 1), iy0 = uint32_t(int(yf)) & (h - 1);
-    const uint32_t ix1 = (ix0 + 1) & (w - 1), iy1 = (iy0 + 1) & (h - 1);
-    const uint32_t* L = reinterpret_cast<const uint32_t*>(lvl);
-    const uint32_t t00 = __ldg(L + (size_t)iy0 * w + ix0), t10 = __ldg(L + (size_t)iy0 * w + ix1);
-    const uint32_t t01 = __ldg(L + (size_t)iy1 * w + ix0), t11 = __ldg(L + (size_t)iy1 * w + ix1);
+    float lods[2] = {lod_a, lod_b}, frac[2];
+    int lev[2];
+    uint32_t tex[2][2][4];
+    float fx[2][2], fy[2][2];
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const float va = float((t00 >> (8 * c)) & 255u), vb = float((t10 >> (8 * c)) & 255u);
-        const float vc = float((t01 >> (8 * c)) & 255u), vd = float((t11 >> (8 * c)) & 255u);
-        const float top = fmaf(fx, vb - va, va);
-        const float bot = fmaf(fx, vd - vc, vc);
-        out[c] = fmaf(fy, bot - top, top);
-    }
-}
-
-// Trilinear fetch at a level of detail: clamp to [0, L_max], level floor,
-// blend to the next level by the fraction, round half-even to RGBA8.
-__device__ uint32_t trilinear(const uint8_t* __restrict__ pool, const TexDesc& td, float s, float t,
-                              float lod) {
-    const int L = int(td.levels) - 1;
-    lod = fminf(fmaxf(lod, 0.0f), float(L));
-    const int l = int(floorf(lod));
-    const float f = lod - float(l);
-    uint64_t off = td.offset;
-    uint32_t lw = td.w, lh = td.h;
-    for (int k = 0; k < l; k++) {
-        off += (uint64_t)lw * lh * 4u;
-        lw = lw > 1 ? lw >> 1 : 1;
-        lh = lh > 1 ? lh >> 1 : 1;
-    }
-    float c0[4];
-    bilinear(pool + off, lw, lh, s, t, c0);
-    uint32_t out = 0;
-    if (f > 0.0f && l < L) {
-        float c1[4];
-        const uint64_t off1 = off + (uint64_t)lw * lh * 4u;
-        bilinear(pool + off1, lw > 1 ? lw >> 1 : 1, lh > 1 ? lh >> 1 : 1, s, t, c1);
+    for (int q = 0; q < 2; q++) {
+        const float lod = fminf(fmaxf(lods[q], 0.0f), float(L));
+        lev[q] = int(floorf(lod));
+        frac[q] = lod - float(lev[q]);
 #pragma unroll
-        for (int c = 0; c < 4; c++) out |= uint32_t(round_u8(fmaf(f, c1[c] - c0[c], c0[c]))) << (8 * c);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; c++) out |= uint32_t(round_u8(c0[c])) << (8 * c);
+        for (int m = 0; m < 2; m++) {
+            const int l = lev[q] + m > L ? L : lev[q] + m;
+            const uint32_t lw = (w >> l) ? (w >> l) : 1u, lh = (h >> l) ? (h >> l) : 1u;
+            const float x = fmaf(fs, float(lw), -0.5f), y = fmaf(ft, float(lh), -0.5f);
+            const float xf = floorf(x), yf = floorf(y);
+            fx[q][m] = x - xf;
+            fy[q][m] = y - yf;
+            const uint32_t ix0 = uint32_t(int(xf)) & (lw - 1), iy0 = uint32_t(int(yf)) & (lh - 1);
+            const uint32_t ix1 = (ix0 + 1) & (lw - 1), iy1 = (iy0 + 1) & (lh - 1);
+            const uint32_t* T = reinterpret_cast<const uint32_t*>(pool + __ldg(loff + l));
+            tex[q][m][0] = __ldg(T + (size_t)iy0 * lw + ix0);
+            tex[q][m][1] = __ldg(T + (size_t)iy0 * lw + ix1);
+            tex[q][m][2] = __ldg(T + (size_t)iy1 * lw + ix0);
+            tex[q][m][3] = __ldg(T + (size_t)iy1 * lw + ix1);
+        }
     }
-    return out;
+    uint32_t out[2] = {0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        float cv[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++) {
+                const float va = float((tex[q][m][0] >> (8 * ch)) & 255u), vb = float((tex[q][m][1] >> (8 * ch)) & 255u);
+                const float vc = float((tex[q][m][2] >> (8 * ch)) & 255u), vd = float((tex[q][m][3] >> (8 * ch)) & 255u);
+                const float top = fmaf(fx[q][m], vb - va, va);
+                const float bot = fmaf(fx[q][m], vd - vc, vc);
+                cv[m][ch] = fmaf(fy[q][m], bot - top, top);
+            }
+        }
+        const bool blend = frac[q] > 0.0f && lev[q] < L;
+#pragma unroll
+        for (int ch = 0; ch < 4; ch++) {
+            const float v = blend ? fmaf(frac[q], cv[1][ch] - cv[0][ch], cv[0][ch]) : cv[0][ch];
+            out[q] |= uint32_t(round_u8(v)) << (8 * ch);
+        }
+    }
+    out_a = out[0];
+    out_b = out[1];
 }
 
 // Cell corner (a s_u + umin, b s_v + vmin) of the lattice frame in world space.
@@ -583,9 +593,11 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         const float vc = (float(j) + 0.5f) * sv;
         const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
         const float t = fmaf(q7.x, uc, fmaf(q7.y, vc, q6.w));
-        const TexDesc td = a.tex[__ldg(a.tri_tex + pt.x)];
-        const uint32_t tmin = trilinear(a.pool, td, s, t, q7.z);
-        const uint32_t tmax = trilinear(a.pool, td, s, t, q7.w);
+        const uint32_t texid = __ldg(a.tri_tex + pt.x);
+        const TexDesc td = a.tex[texid];
+        uint32_t tmin, tmax;
+        trilinear_pair(a.pool, a.lvl + (size_t)texid * kMaxLevels, td.w, td.h, int(td.levels) - 1, s, t, q7.z,
+                       q7.w, tmin, tmax);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
         const float4 q5 = __ldg(&r->q[5]);
 
