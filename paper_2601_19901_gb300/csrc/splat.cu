@@ -88,28 +88,31 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     __syncthreads();
     if (a.ctr->overflow) return;
     const uint32_t n = a.ctr->n_work;
-    const int lane = threadIdx.x & 31, sub = lane & 15;
-    const unsigned hmask = 0xffffu << (lane & 16);
-    const uint32_t hw = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-    const uint32_t n_hw = (gridDim.x * blockDim.x) >> 4;
+    const int lane = threadIdx.x & 31, sub = lane & 15, half = lane >> 4;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const float W1 = float(c.W - 1);
     const uint64_t npix = (uint64_t)c.W * c.H;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
     uint32_t writes = 0;
 
-    for (uint32_t k = hw; k < n; k += n_hw) {
-        const WorkRec* wr = a.work + k;
-        if (sub == 0 && k + n_hw < n) prefetch_l2(a.work + k + n_hw);   // next point's record
+    // Every loop below has the same trip count in both halves of the warp
+    // (pairs of points; the larger pass count of the two), so each warp
+    // instruction serves both points.
+    for (uint32_t kk = warp; 2 * kk < n; kk += n_warps) {
+        const uint32_t k = 2 * kk + uint32_t(half);
+        const bool act = k < n;
+        const WorkRec* wr = a.work + (act ? k : 2 * kk);
+        if (sub == 0 && k + 2 * n_warps < n) prefetch_l2(a.work + k + 2 * n_warps);   // next pair's record
         const float4 L0 = __ldg(&wr->L0), L1 = __ldg(&wr->L1);
         const uint4 meta = __ldg(&wr->meta);
         const uint32_t tri = meta.z;
         const unsigned long long pid = meta.w;
         const TriRec* r = a.rec + tri;
-        if (sub == 1 && k + n_hw < n) prefetch_l2(a.rec + __ldg(&a.work[k + n_hw].meta.z));
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
         const int y0 = int(meta.x & 0x3fffu);
-        const uint32_t ny = (meta.x >> 14) & 0x7fffu;
+        const uint32_t ny = act ? (meta.x >> 14) & 0x7fffu : 0u;
         const uint32_t flags = meta.x >> 29;
         const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
         const bool box = flags & kFlagBox;
@@ -159,24 +162,25 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
             uint32_t incl = cnt;
 #pragma unroll
             for (int o = 1; o < 16; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(hmask, incl, o, 16);
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o, 16);
                 if (sub >= o) incl += t;
             }
-            const uint32_t total = __shfl_sync(hmask, incl, 15, 16);
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 15, 16);
+            const uint32_t both = max(total, __shfl_xor_sync(0xffffffffu, total, 16));
             const uint32_t excl = incl - cnt;
-            for (uint32_t pass = 0; pass < total; pass += 16) {
+            for (uint32_t pass = 0; pass < both; pass += 16) {
                 const uint32_t q = pass + sub;
-                // owner: the first lane whose inclusive count exceeds q
+                // owner: the first lane of this half whose inclusive count exceeds q
                 int own = 0;
 #pragma unroll
                 for (int st = 8; st >= 1; st >>= 1) {
-                    const uint32_t t = __shfl_sync(hmask, incl, own + st - 1, 16);
+                    const uint32_t t = __shfl_sync(0xffffffffu, incl, own + st - 1, 16);
                     if (t <= q) own += st;
                 }
-                const uint32_t o_excl = __shfl_sync(hmask, excl, own, 16);
+                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own, 16);
                 uint32_t opk[kSlots];
 #pragma unroll
-                for (int sl = 0; sl < kSlots; sl++) opk[sl] = __shfl_sync(hmask, pk[sl], own, 16);
+                for (int sl = 0; sl < kSlots; sl++) opk[sl] = __shfl_sync(0xffffffffu, pk[sl], own, 16);
                 if (q >= total) continue;
                 // the owner's view slot holding candidate q
                 uint32_t rr = q - o_excl, sel = opk[0];
@@ -208,7 +212,6 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
         }
     }
     // warp-aggregated count of depth-test writes (the atomics issued)
-    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
     if (lane == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
