@@ -94,7 +94,7 @@ struct TriProj {
 // project_point() and candidates come from the x-extents. Written compacted
 // by the fetch pass, in no particular order.
 struct WorkRec {
-    float4 L0, L1;
+    float4 L0, L1;   // lower a, b, upper a, b of the cell's (L0) and triangle's (L1) x-extent: x = a + b Ex
     uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
 // Per-point data of the resolve (Eq. 8-9): the cell's four world corners
@@ -111,7 +111,6 @@ struct ResolveRec {
 
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]
-constexpr uint32_t kFlagBox = 4u;       // candidates from x-extents (L0, L1 = corner A, B)
 
 // ---------------------------------------------------------------------------
 // binary32 helpers (each rounding explicit)

@@ -542,34 +542,66 @@ __device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q
     o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
 }
 
-// Crossings of the pixel row y = yc with a convex polygon of n projected
-// vertices (pixel x = A + B Ex, y = Y): for each edge crossing the row
-// (half-open in y, so a convex polygon has exactly two when yc lies strictly
-// inside its y-extent) the line alpha + beta Ex of the crossing's x. Returns
-// false unless there are exactly two, each on an edge whose y-span is at
-// least 1/8 of its largest x-span over the views (the crossing's x error is
-// about |dx| / |dy| times the projection error, about 1e-4 pixel, so it stays
-// an order of magnitude inside the candidate margin).
+// Bounds of a convex polygon's x-extent within the band of pixel rows
+// ya <= y <= yb, for every eye in [-E, E] (projected vertices: pixel
+// x = A + B Ex, y = Y): a lower and an upper line x = a + b Ex, as
+// L = (lower a, b, upper a, b).
+//
+// The extent within the band is reached at the vertices inside it or where
+// its two boundary rows cross the edges (half-open in y); each such point
+// moves along a line in Ex. A crossing is taken as its own line where the
+// edge's y-span is at least 1/8 of its largest x-span over the eyes (the
+// crossing's x error is about |dx| / |dy| times the projection error, about
+// 1e-4 pixel, an order of magnitude inside the candidate margin), else as the
+// edge's two end lines, between which it lies. A band that misses the
+// polygon (a margin row) takes every vertex. The lower bound is the chord,
+// between the extreme eyes -E and +E, of the minimum of those lines: the
+// minimum of lines is concave, so the chord lies below it, and it is the
+// minimum itself where one line stays lowest. The upper bound likewise.
+// Each point enters only through its x at the two extreme eyes, so the
+// bounds need no branch per point.
 template <int N>
-__device__ __forceinline__ bool row_crossings(const float* A, const float* B, const float* Y, float yc,
-                                              float ex_max, float4& lines) {
-    float al[2], be[2];
-    int m = 0;
+__device__ __forceinline__ void band_bounds(const float* A, const float* B, const float* Y, float ya, float yb,
+                                            float E, float4& L) {
+    float xm[N], xp[N];   // x at eye -E and at eye +E
 #pragma unroll
-    for (int e = 0; e < N; e++) {
-        const int p = e, q = e + 1 == N ? 0 : e + 1;
-        const bool cross = (Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]);
-        if (!cross) continue;
-        const float dxmax = fmaf(fabsf(B[q] - B[p]), ex_max, fabsf(A[q] - A[p]));
-        if (m == 2 || !(fabsf(Y[q] - Y[p]) >= 0.125f * dxmax)) return false;
-        const float f = __fdividef(yc - Y[p], Y[q] - Y[p]);
-        al[m] = fmaf(f, A[q] - A[p], A[p]);
-        be[m] = fmaf(f, B[q] - B[p], B[p]);
-        m++;
+    for (int k = 0; k < N; k++) {
+        xm[k] = fmaf(-B[k], E, A[k]);
+        xp[k] = fmaf(B[k], E, A[k]);
     }
-    if (m != 2) return false;
-    lines = make_float4(al[0], be[0], al[1], be[1]);
-    return true;
+    float lm = INFINITY, lp = INFINITY, um = -INFINITY, up = -INFINITY;
+    auto fold = [&](bool on, float m, float p) {
+        if (on) {
+            lm = fminf(lm, m);
+            lp = fminf(lp, p);
+            um = fmaxf(um, m);
+            up = fmaxf(up, p);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < N; k++) fold(Y[k] >= ya && Y[k] <= yb, xm[k], xp[k]);
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float yc = r ? yb : ya;
+        const bool row = r == 0 || yb > ya;
+#pragma unroll
+        for (int e = 0; e < N; e++) {
+            const int p = e, q = e + 1 == N ? 0 : e + 1;
+            const bool cross = row && ((Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]));
+            const float dxm = xm[q] - xm[p], dxp = xp[q] - xp[p], dy = Y[q] - Y[p];
+            const bool sharp = fabsf(dy) >= 0.125f * fmaxf(fabsf(dxm), fabsf(dxp));
+            const float f = __fdividef(yc - Y[p], cross ? dy : 1.0f);
+            fold(cross && sharp, fmaf(f, dxm, xm[p]), fmaf(f, dxp, xp[p]));
+            fold(cross && !sharp, xm[p], xp[p]);
+            fold(cross && !sharp, xm[q], xp[q]);
+        }
+    }
+    if (!(lm <= um)) {
+#pragma unroll
+        for (int k = 0; k < N; k++) fold(true, xm[k], xp[k]);
+    }
+    const float hE = E > 0.0f ? __fdividef(0.5f, E) : 0.0f;
+    L = make_float4(0.5f * (lm + lp), (lp - lm) * hE, 0.5f * (um + up), (up - um) * hE);
 }
 
 // One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
@@ -633,26 +665,17 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         }
         const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
         uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
-        // one candidate row: the row's crossing lines of the cell and the
-        // triangle when each polygon has exactly two well-conditioned
-        // crossings; otherwise the corner projections (x-extents)
-        float4 L0 = make_float4(A[0], A[1], A[2], A[3]), L1 = make_float4(B[0], B[1], B[2], B[3]);
-        bool box = true;
-        if (ny == 1) {
-            const float yc = float(y0) + 0.5f;
+        // candidate columns: lower and upper lines of the cell's and of the
+        // triangle's x-extent within the band of candidate rows (none where
+        // the triangle is one cell, or the cell lies inside its triangle)
+        float4 L0 = make_float4(-INFINITY, 0.0f, INFINITY, 0.0f), L1 = L0;
+        if (ny > 0) {
+            const float ya = float(y0) + 0.5f, yb = float(y0 + ny - 1u) + 0.5f;
             const float tA3[3] = {tp.a.x, tp.a.y, tp.a.z}, tB3[3] = {tp.b.x, tp.b.y, tp.b.z};
             const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
-            float4 lc, lt;
-            const bool single = __ldg(a.counts + pt.x) == 1u;
-            const bool okc = single || row_crossings<4>(A, B, Y, yc, c.ex_max, lc);
-            const bool okt = interior || row_crossings<3>(tA3, tB3, tY3, yc, c.ex_max, lt);
-            if (okc && okt) {
-                box = false;
-                L0 = single ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lc;
-                L1 = interior ? make_float4(-INFINITY, 0.0f, INFINITY, 0.0f) : lt;
-            }
+            if (__ldg(a.counts + pt.x) != 1u) band_bounds<4>(A, B, Y, ya, yb, c.ex_max, L0);
+            if (!interior) band_bounds<3>(tA3, tB3, tY3, ya, yb, c.ex_max, L1);
         }
-        if (box) flags |= kFlagBox;
 
         ResolveRec* rr = a.rrec + p;
         rr->c0 = make_float4(Cx[0], Cy[0], Cs[0], Cx[1]);

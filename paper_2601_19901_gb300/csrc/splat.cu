@@ -24,19 +24,20 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
 }
 
 // One half-warp (16 lanes) per point of the work list, each lane taking up to
-// kSlots views of the point (views g + 16 s + lane of a group g of 64); a
-// warp carries two points at a time.
+// S views of the point (views g + 16 s + lane of a group g of 16 S views, S
+// chosen so that one group holds every rendered view where it can); a warp
+// carries two points at a time.
 //
 // Candidates. Candidate rows are the pixel-centre rows inside both the
 // cell's and the triangle's projected y-extent, the same in every view since
 // every eye lies on y = 0, z = D. A lane forms each of its views' candidate
-// columns: for a point with one candidate row, between the row's crossings
-// with the projected cell and with the projected triangle, which move along
-// lines x = alpha + beta Ex; otherwise within the intersected x-extents
-// (pixel x = A + B Ex per vertex). Ranges are widened by a small margin. A
-// scan of the lanes' candidate counts over the whole group then hands every
-// lane one candidate pixel per pass, so no lane loops over pixels on its own
-// and a point with few candidates needs a single pass.
+// columns between a lower and an upper line x = alpha + beta Ex for the cell
+// and for the triangle, which bound each one's projected x-extent within the
+// band of candidate rows (the row's exact crossings for most points with one
+// row), widened by a small margin. A scan of the lanes' candidate counts over
+// the whole group then hands every lane one candidate pixel per pass, so no
+// lane loops over pixels on its own and a point with few candidates needs a
+// single pass.
 //
 // Test. Each candidate takes the per-pixel test in the oracle's plane-space
 // form: the pixel centre's ray from the eye meets the triangle's plane at t
@@ -49,7 +50,6 @@ __device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, 
 // Points whose cell or triangle reaches the eyes' plane (none in front-only
 // scenes) are listed apart and splatted by k_splat_near.
 constexpr int kSplatWarps = 8;
-constexpr int kSlots = 4;
 // Ask L2 for the line holding p (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
@@ -81,6 +81,7 @@ __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float n
     return inside_either(w0, w1, w2);
 }
 
+template <int S>
 __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     __shared__ float s_ex[kMaxRenderViews];
     const DispConst& c = a.dc;
@@ -91,7 +92,6 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
     const int lane = threadIdx.x & 31, sub = lane & 15, half = lane >> 4;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    const float W1 = float(c.W - 1);
     const uint64_t npix = (uint64_t)c.W * c.H;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
     uint32_t writes = 0;
@@ -115,45 +115,26 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
         const uint32_t ny = act ? (meta.x >> 14) & 0x7fffu : 0u;
         const uint32_t flags = meta.x >> 29;
         const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
-        const bool box = flags & kFlagBox;
-        float4 tA = make_float4(0.f, 0.f, 0.f, 0.f), tB = tA;
-        if (box) {
-            const TriProj* tpp = a.tproj + tri;
-            tA = __ldg(&tpp->a);
-            tB = __ldg(&tpp->b);
-        }
         const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
         const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
         const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
         const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
 
-        for (int g = 0; g < c.nr; g += 16 * kSlots) {
-            uint32_t pk[kSlots];      // x0 | n_columns << 14 of the lane's views
+        for (int g = 0; g < c.nr; g += 16 * S) {
+            uint32_t pk[S];      // x0 | n_columns << 14 of the lane's views
             uint32_t cnt = 0;
 #pragma unroll
-            for (int sl = 0; sl < kSlots; sl++) {
+            for (int sl = 0; sl < S; sl++) {
                 const int v = g + 16 * sl + sub;
                 pk[sl] = 0u;
                 if (v < c.nr) {
                     const float Ex = s_ex[v];
-                    float lo, hi;
-                    if (!box) {
-                        const float xa = fmaf(L0.y, Ex, L0.x), xb = fmaf(L0.w, Ex, L0.z);
-                        const float ta = fmaf(L1.y, Ex, L1.x), tb = fmaf(L1.w, Ex, L1.z);
-                        lo = fmaxf(fminf(xa, xb), fminf(ta, tb));
-                        hi = fminf(fmaxf(xa, xb), fmaxf(ta, tb));
-                    } else {
-                        const float X0 = fmaf(L1.x, Ex, L0.x), X1 = fmaf(L1.y, Ex, L0.y);
-                        const float X2 = fmaf(L1.z, Ex, L0.z), X3 = fmaf(L1.w, Ex, L0.w);
-                        const float T0 = fmaf(tB.x, Ex, tA.x), T1 = fmaf(tB.y, Ex, tA.y);
-                        const float T2 = fmaf(tB.z, Ex, tA.z);
-                        lo = fmaxf(fminf(fminf(X0, X1), fminf(X2, X3)), fminf(fminf(T0, T1), T2));
-                        hi = fminf(fmaxf(fmaxf(X0, X1), fmaxf(X2, X3)), fmaxf(fmaxf(T0, T1), T2));
-                    }
-                    const float fx0 = fmaxf(ceilf(lo - 0.5f - kBoxPad), 0.0f);
-                    const float fx1 = fminf(floorf(hi - 0.5f + kBoxPad), W1);
-                    if (fx0 <= fx1) {
-                        const uint32_t x0 = uint32_t(int(fx0)), nx = uint32_t(int(fx1)) - x0 + 1u;
+                    const float lo = fmaxf(fmaf(L0.y, Ex, L0.x), fmaf(L1.y, Ex, L1.x));
+                    const float hi = fminf(fmaf(L0.w, Ex, L0.z), fmaf(L1.w, Ex, L1.z));
+                    const int ix0 = max(__float2int_ru(lo - 0.5f - kBoxPad), 0);
+                    const int ix1 = min(__float2int_rd(hi - 0.5f + kBoxPad), int(c.W) - 1);
+                    if (ix0 <= ix1) {
+                        const uint32_t x0 = uint32_t(ix0), nx = uint32_t(ix1 - ix0) + 1u;
                         pk[sl] = x0 | (nx << 14);
                         cnt += nx * ny;
                     }
@@ -178,15 +159,15 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                     if (t <= q) own += st;
                 }
                 const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own, 16);
-                uint32_t opk[kSlots];
+                uint32_t opk[S];
 #pragma unroll
-                for (int sl = 0; sl < kSlots; sl++) opk[sl] = __shfl_sync(0xffffffffu, pk[sl], own, 16);
+                for (int sl = 0; sl < S; sl++) opk[sl] = __shfl_sync(0xffffffffu, pk[sl], own, 16);
                 if (q >= total) continue;
                 // the owner's view slot holding candidate q
                 uint32_t rr = q - o_excl, sel = opk[0];
                 int slot = 0;
 #pragma unroll
-                for (int sl = 0; sl + 1 < kSlots; sl++) {
+                for (int sl = 0; sl + 1 < S; sl++) {
                     const uint32_t cs = (opk[sl] >> 14) * ny;
                     if (slot == sl && rr >= cs) {
                         rr -= cs;
@@ -309,7 +290,21 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
 }  // namespace
 
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
-    k_splat<<<a.sm_count * 16, kSplatWarps * 32, 0, s>>>(a);
+    // the fewest view slots per lane that hold every rendered view in one
+    // group (more than 128 views take several groups of 128)
+    const int nr = a.dc.nr, grid = a.sm_count * 16, block = kSplatWarps * 32;
+    if (nr <= 16)
+        k_splat<1><<<grid, block, 0, s>>>(a);
+    else if (nr <= 32)
+        k_splat<2><<<grid, block, 0, s>>>(a);
+    else if (nr <= 48)
+        k_splat<3><<<grid, block, 0, s>>>(a);
+    else if (nr <= 64)
+        k_splat<4><<<grid, block, 0, s>>>(a);
+    else if (nr <= 96)
+        k_splat<6><<<grid, block, 0, s>>>(a);
+    else
+        k_splat<8><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
