@@ -549,17 +549,17 @@ __device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q
 //
 // The extent within the band is reached at the vertices inside it or where
 // its two boundary rows cross the edges (half-open in y); each such point
-// moves along a line in Ex. A crossing is taken as its own line where the
-// edge's y-span is at least 1/8 of its largest x-span over the eyes (the
-// crossing's x error is about |dx| / |dy| times the projection error, about
-// 1e-4 pixel, an order of magnitude inside the candidate margin), else as the
-// edge's two end lines, between which it lies. A band that misses the
-// polygon (a margin row) takes every vertex. The lower bound is the chord,
-// between the extreme eyes -E and +E, of the minimum of those lines: the
-// minimum of lines is concave, so the chord lies below it, and it is the
-// minimum itself where one line stays lowest. The upper bound likewise.
-// Each point enters only through its x at the two extreme eyes, so the
-// bounds need no branch per point.
+// moves along a line in Ex. A crossing at fraction f along its edge is taken
+// as the two lines at f -+ kCrossDy / |dy| (clamped to the edge's ends): the
+// projected y carry errors of about 2e-4 pixel, so the true crossing lies
+// between them, and a steep edge gives two nearly equal lines while a flat
+// one gives its two ends. A band that misses the polygon (a margin row)
+// takes every vertex. The lower bound is the chord, between the extreme eyes
+// -E and +E, of the minimum of those lines: the minimum of lines is concave,
+// so the chord lies below it, and it is the minimum itself where one line
+// stays lowest. The upper bound likewise. Each point enters only through its
+// x at the two extreme eyes, so the bounds need no branch per point.
+constexpr float kCrossDy = 1e-3f;
 template <int N>
 __device__ __forceinline__ void band_bounds(const float* A, const float* B, const float* Y, float ya, float yb,
                                             float E, float4& L) {
@@ -588,12 +588,12 @@ __device__ __forceinline__ void band_bounds(const float* A, const float* B, cons
         for (int e = 0; e < N; e++) {
             const int p = e, q = e + 1 == N ? 0 : e + 1;
             const bool cross = row && ((Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]));
-            const float dxm = xm[q] - xm[p], dxp = xp[q] - xp[p], dy = Y[q] - Y[p];
-            const bool sharp = fabsf(dy) >= 0.125f * fmaxf(fabsf(dxm), fabsf(dxp));
-            const float f = __fdividef(yc - Y[p], cross ? dy : 1.0f);
-            fold(cross && sharp, fmaf(f, dxm, xm[p]), fmaf(f, dxp, xp[p]));
-            fold(cross && !sharp, xm[p], xp[p]);
-            fold(cross && !sharp, xm[q], xp[q]);
+            const float dxm = xm[q] - xm[p], dxp = xp[q] - xp[p];
+            const float rdy = __fdividef(1.0f, cross ? Y[q] - Y[p] : 1.0f);
+            const float f = (yc - Y[p]) * rdy, d = kCrossDy * fabsf(rdy);
+            const float f0 = fmaxf(f - d, 0.0f), f1 = fminf(f + d, 1.0f);
+            fold(cross, fmaf(f0, dxm, xm[p]), fmaf(f0, dxp, xp[p]));
+            fold(cross, fmaf(f1, dxm, xm[p]), fmaf(f1, dxp, xp[p]));
         }
     }
     if (!(lm <= um)) {
