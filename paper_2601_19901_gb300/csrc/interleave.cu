@@ -1,29 +1,50 @@
 // Elemental image array construction (Sec. 4): optional angular tent
 // reconstruction of the 2N supersampled views, optional +-1 crosstalk mixing,
-// then the slanted-lens subpixel interleave. One thread per 4 horizontally
-// adjacent panel pixels, one 16-byte store; the view reads are gathers that
-// follow the lens phase.
+// then the slanted-lens subpixel interleave.
+//
+// Every panel pixel samples one view pixel (nearest, pixel centres) of the
+// views its three subpixels select, and neighbouring subpixels select
+// different views, so reading views straight from global memory is a gather
+// touching a new sector per byte. k_interleave_tile instead takes one view
+// row and a strip of 1024 panel columns: it stages the strip's source
+// segment of that row for every rendered view in shared memory with
+// coalesced loads, then forms every panel row that samples that view row,
+// one thread per 4 adjacent panel pixels and one 16-byte store per row.
+// k_interleave (the direct gather) serves displays whose tile would not fit.
 #include "lfdpr_internal.cuh"
 
 namespace lfdpr {
 namespace {
 
-__device__ __forceinline__ float texel(const uint8_t* __restrict__ views, uint64_t npix, int view,
-                                       uint64_t pix, int ch) {
-    return float(__ldg(views + ((uint64_t)view * npix + pix) * 4u + ch));
-}
+// View pixel channel as stored: global views [view][H][W][RGBA8].
+struct GlobalTexels {
+    const uint8_t* __restrict__ views;
+    uint64_t npix, pix;
+    __device__ __forceinline__ float operator()(int view, int ch) const {
+        return float(__ldg(views + ((uint64_t)view * npix + pix) * 4u + ch));
+    }
+};
 
-// Display view k, channel ch, at pixel pix, as binary32 before rounding.
-__device__ __forceinline__ float display_value(const DispConst& c, const uint8_t* __restrict__ views,
-                                               uint64_t npix, int k, uint64_t pix, int ch) {
-    if (c.recon != 1) return texel(views, npix, k, pix, ch);
+// The same from a staged row segment: s[view * stride + i], RGBA8 words.
+struct SharedTexels {
+    const uint32_t* s;
+    int stride, i;
+    __device__ __forceinline__ float operator()(int view, int ch) const {
+        return float((s[view * stride + i] >> (8 * ch)) & 255u);
+    }
+};
+
+// Display view k, channel ch, as binary32 before rounding.
+template <class T>
+__device__ __forceinline__ float display_value(const DispConst& c, const T& tex, int k, int ch) {
+    if (c.recon != 1) return tex(k, ch);
     float acc = 0.0f, ws = 0.0f;
 #pragma unroll
     for (int q = 0; q < 3; q++) {
         const int m = 2 * k - 1 + q;
         if (m < 0 || m >= c.nr) continue;
         const float w = q == 1 ? 0.5f : 0.25f;
-        acc = fmaf(w, texel(views, npix, m, pix, ch), acc);
+        acc = fmaf(w, tex(m, ch), acc);
         ws += w;
     }
     return __fdiv_rn(acc, ws);
@@ -40,6 +61,85 @@ __device__ __forceinline__ int view_of_subpixel(const DispConst& c, int x, int y
     return k;
 }
 
+// Panel pixel (x, y) as RGBA8 (alpha 255) from its view pixel's texels.
+template <class T>
+__device__ __forceinline__ uint32_t panel_pixel(const DispConst& c, const T& tex, int x, int y) {
+    uint32_t o = 0xff000000u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const int k = view_of_subpixel(c, x, y, ch);
+        float val;
+        if (c.xtalk > 0.0f) {
+            const int km = k == 0 ? c.n_views - 1 : k - 1;
+            const int kp = k == c.n_views - 1 ? 0 : k + 1;
+            float acc = display_value(c, tex, k, ch) * c.xtalk_c;
+            acc = fmaf(c.xtalk, display_value(c, tex, km, ch), acc);
+            acc = fmaf(c.xtalk, display_value(c, tex, kp, ch), acc);
+            val = acc;
+        } else {
+            val = display_value(c, tex, k, ch);
+        }
+        o |= uint32_t(round_u8(val)) << (8 * ch);
+    }
+    return o;
+}
+
+// Nearest view pixel of panel column x (row y): pixel centres aligned. In
+// 32 bits: (2 x + 1) W < 2^31 for panels up to 32768 and views up to 16384.
+__device__ __forceinline__ int source_x(const DispConst& c, int x) {
+    return int((2u * uint32_t(x) + 1u) * uint32_t(c.W) / (2u * uint32_t(c.Wp)));
+}
+__device__ __forceinline__ int source_y(const DispConst& c, int y) {
+    return int((2u * uint32_t(y) + 1u) * uint32_t(c.H) / (2u * uint32_t(c.Hp)));
+}
+
+__device__ __forceinline__ void store4(const DispConst& c, uint8_t* __restrict__ panel, int xg, int y,
+                                       const uint32_t* px) {
+    uint8_t* dst = panel + ((uint64_t)y * c.Wp + xg) * 4u;
+    if (xg + 4 <= c.Wp && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
+    } else {
+        for (int e = 0; e < 4 && xg + e < c.Wp; e++) reinterpret_cast<uint32_t*>(dst)[e] = px[e];
+    }
+}
+
+constexpr int kTileThreads = 256;
+constexpr int kTileCols = 4 * kTileThreads;   // panel columns per tile
+
+// Block (strip bx, view row sy): view pixels sx_lo..sx_lo + n - 1 of row sy
+// for every rendered view, then the panel rows whose source row is sy.
+__global__ void __launch_bounds__(kTileThreads) k_interleave_tile(DispConst c, const uint8_t* __restrict__ views,
+                                                                  uint8_t* __restrict__ panel, int stride) {
+    extern __shared__ uint32_t s_row[];
+    const int sy = blockIdx.y;
+    const int x0 = blockIdx.x * kTileCols;
+    const int x1 = min(x0 + kTileCols, c.Wp);   // exclusive
+    // panel rows sampling view row sy: y_first.. while source_y(y) == sy
+    int y = max(0, int(uint32_t(sy) * uint32_t(c.Hp) / uint32_t(c.H)) - 1);
+    while (y < c.Hp && source_y(c, y) < sy) y++;
+    if (y >= c.Hp || source_y(c, y) != sy) return;
+    const int sx_lo = source_x(c, x0), n = source_x(c, x1 - 1) - sx_lo + 1;
+    const uint64_t npix = (uint64_t)c.W * c.H;
+    const uint32_t* v32 = reinterpret_cast<const uint32_t*>(views);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int m = warp; m < c.nr; m += kTileThreads / 32) {
+        const uint32_t* src = v32 + (uint64_t)m * npix + (uint64_t)sy * c.W + sx_lo;
+        for (int i = lane; i < n; i += 32) s_row[m * stride + i] = __ldg(src + i);
+    }
+    __syncthreads();
+    const int xg = x0 + 4 * threadIdx.x;
+    if (xg >= x1) return;
+    int sxi[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) sxi[e] = min(source_x(c, min(xg + e, x1 - 1)) - sx_lo, n - 1);
+    for (; y < c.Hp && source_y(c, y) == sy; y++) {
+        uint32_t px[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) px[e] = panel_pixel(c, SharedTexels{s_row, stride, sxi[e]}, xg + e, y);
+        store4(c, panel, xg, y, px);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* __restrict__ views,
                                                      uint8_t* __restrict__ panel) {
     const uint64_t npix = (uint64_t)c.W * c.H;
@@ -49,50 +149,37 @@ __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* 
          g += (uint64_t)gridDim.x * blockDim.x) {
         const int y = int(g / groups_x);
         const int xg = int(g - (uint64_t)y * groups_x) * 4;
-        const int sy = int(((int64_t)(2 * y + 1) * c.H) / (2 * (int64_t)c.Hp));
+        const int sy = source_y(c, y);
         uint32_t px[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            const int x = xg + e;
-            uint32_t o = 0xff000000u;
-            if (x < c.Wp) {
-                const int sx = int(((int64_t)(2 * x + 1) * c.W) / (2 * (int64_t)c.Wp));
-                const uint64_t pix = (uint64_t)sy * c.W + sx;
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++) {
-                    const int k = view_of_subpixel(c, x, y, ch);
-                    float val;
-                    if (c.xtalk > 0.0f) {
-                        const int km = k == 0 ? c.n_views - 1 : k - 1;
-                        const int kp = k == c.n_views - 1 ? 0 : k + 1;
-                        float acc = display_value(c, views, npix, k, pix, ch) * c.xtalk_c;
-                        acc = fmaf(c.xtalk, display_value(c, views, npix, km, pix, ch), acc);
-                        acc = fmaf(c.xtalk, display_value(c, views, npix, kp, pix, ch), acc);
-                        val = acc;
-                    } else {
-                        val = display_value(c, views, npix, k, pix, ch);
-                    }
-                    o |= uint32_t(round_u8(val)) << (8 * ch);
-                }
-            }
-            px[e] = o;
+            const int x = min(xg + e, c.Wp - 1);
+            const uint64_t pix = (uint64_t)sy * c.W + source_x(c, x);
+            px[e] = panel_pixel(c, GlobalTexels{views, npix, pix}, x, y);
         }
-        uint8_t* dst = panel + ((uint64_t)y * c.Wp + xg) * 4u;
-        if (xg + 4 <= c.Wp && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-            *reinterpret_cast<uint4*>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
-        } else {
-            for (int e = 0; e < 4 && xg + e < c.Wp; e++) reinterpret_cast<uint32_t*>(dst)[e] = px[e];
-        }
+        store4(c, panel, xg, y, px);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel, cudaStream_t s) {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_interleave<<<sms * 8, 256, 0, s>>>(dc, views, panel);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // widest source segment of a tile: (kTileCols - 1) W / Wp + 2 pixels
+    const int64_t seg = ((int64_t)(kTileCols - 1) * dc.W) / dc.Wp + 2;
+    const int64_t bytes = (int64_t)dc.nr * seg * 4;
+    if (bytes <= smem_max / 2) {
+        cudaError_t e = cudaFuncSetAttribute(k_interleave_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(bytes));
+        if (e != cudaSuccess) return e;
+        const dim3 grid((dc.Wp + kTileCols - 1) / kTileCols, dc.H);
+        k_interleave_tile<<<grid, kTileThreads, size_t(bytes), s>>>(dc, views, panel, int(seg));
+    } else {
+        k_interleave<<<sms * 8, 256, 0, s>>>(dc, views, panel);
+    }
     return cudaGetLastError();
 }
 

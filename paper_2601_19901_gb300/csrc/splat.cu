@@ -1,7 +1,7 @@
 // EPR splatting into every view (Sec. 3.2) with the 64-bit depth|id test
 // (Sec. 5.1), and the per-view resolve of Eq. 8-9 (Sec. 3.3).
 //
-//   k_splat    one warp per point, lanes over the views: every pixel centre
+//   k_splat    one half-warp per point, lanes over the views: every pixel centre
 //              inside the point's projected cell and its projected triangle,
 //              at a depth in [near, far], does
 //              atomicMin(key, float_bits(t) << 32 | point id).
@@ -241,50 +241,57 @@ __global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
     if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
 }
 
+// Eq. 8-9 for one view pixel whose depth test kept point record rp (the
+// caller has already loaded it): the splat's pixel area in view Ex is the
+// shoelace area of its cell corners projected from the eye.
+__device__ __forceinline__ uint32_t resolve_pixel(const DispConst& c, float Ex, const float4& c0, const float4& c1,
+                                                  const float4& c2, const float4& m, const uint4& tv) {
+    const float cx[4] = {c0.x, c0.w, c1.z, c2.y}, cy[4] = {c0.y, c1.x, c1.w, c2.z};
+    const float cs[4] = {c0.z, c1.y, c2.x, c2.w};
+    float X[4], Y[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float sx = fmaf(cx[k] - Ex, cs[k], Ex);
+        const float sy = cy[k] * cs[k];
+        X[k] = (sx - c.x0) * c.ipw;
+        Y[k] = (c.y0 - sy) * c.iph;
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int k1 = (k + 1) & 3;
+        acc = acc + fmaf(X[k], Y[k1], -(X[k1] * Y[k]));
+    }
+    const float area_px = 0.5f * fabsf(acc);
+    const float vmin = m.y, vmax = m.z;
+    const float size_vse = __fdiv_rn(m.x, fminf(1.0f, area_px));
+    const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
+    const float w = vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
+    uint32_t out = 0u;
+#pragma unroll
+    for (int ch = 0; ch < 4; ch++) {
+        const float lo = float((tv.x >> (8 * ch)) & 255u), hi = float((tv.y >> (8 * ch)) & 255u);
+        out |= uint32_t(round_u8(fmaf(w, hi - lo, lo))) << (8 * ch);
+    }
+    return out;
+}
+
+// One view pixel per thread (grid: pixels x views).
 __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
     const DispConst& c = a.dc;
-    const uint64_t npix = (uint64_t)c.W * c.H;
-    const uint64_t total = npix * (uint64_t)c.nr;
-    for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-         o += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = a.keys[o];
-        uint32_t out = 0u;
-        if (key != ~0ull) {
-            const int v = int(o / npix);
-            const float Ex = __ldg(a.ex + v);
-            const ResolveRec* rp = a.rrec + uint32_t(key);
-            const float4 c0 = __ldg(&rp->c0), c1 = __ldg(&rp->c1), c2 = __ldg(&rp->c2);
-            const float4 m = __ldg(&rp->m);
-            const uint4 tv = __ldg(&rp->tv);
-            const float cx[4] = {c0.x, c0.w, c1.z, c2.y}, cy[4] = {c0.y, c1.x, c1.w, c2.z};
-            const float cs[4] = {c0.z, c1.y, c2.x, c2.w};
-            float X[4], Y[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float sx = fmaf(cx[k] - Ex, cs[k], Ex);
-                const float sy = cy[k] * cs[k];
-                X[k] = (sx - c.x0) * c.ipw;
-                Y[k] = (c.y0 - sy) * c.iph;
-            }
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int k1 = (k + 1) & 3;
-                acc = acc + fmaf(X[k], Y[k1], -(X[k1] * Y[k]));
-            }
-            const float area_px = 0.5f * fabsf(acc);
-            const float vmin = m.y, vmax = m.z;
-            const float size_vse = __fdiv_rn(m.x, fminf(1.0f, area_px));
-            const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
-            const float w = vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
-#pragma unroll
-            for (int ch = 0; ch < 4; ch++) {
-                const float lo = float((tv.x >> (8 * ch)) & 255u), hi = float((tv.y >> (8 * ch)) & 255u);
-                out |= uint32_t(round_u8(fmaf(w, hi - lo, lo))) << (8 * ch);
-            }
-        }
-        reinterpret_cast<uint32_t*>(a.views)[o] = out;
+    const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const int v = blockIdx.y;
+    const uint64_t o = (uint64_t)v * npix + p;
+    const unsigned long long key = a.keys[o];
+    uint32_t out = 0u;
+    if (key != ~0ull) {
+        const ResolveRec* rp = a.rrec + uint32_t(key);
+        out = resolve_pixel(c, __ldg(a.ex + v), __ldg(&rp->c0), __ldg(&rp->c1), __ldg(&rp->c2), __ldg(&rp->m),
+                            __ldg(&rp->tv));
     }
+    reinterpret_cast<uint32_t*>(a.views)[o] = out;
 }
 
 }  // namespace
@@ -314,7 +321,9 @@ cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {
-    k_resolve<<<a.sm_count * 8, 256, 0, s>>>(a);
+    const uint32_t npix = uint32_t(a.dc.W) * uint32_t(a.dc.H);
+    const dim3 grid((npix + 255u) / 256u, uint32_t(a.dc.nr));
+    k_resolve<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
