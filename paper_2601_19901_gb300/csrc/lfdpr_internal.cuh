@@ -94,7 +94,10 @@ struct TriProj {
 // project_point() and candidates come from the x-extents. Written compacted
 // by the fetch pass, in no particular order.
 struct WorkRec {
-    float4 L0, L1;   // lower a, b, upper a, b of the cell's (L0) and triangle's (L1) x-extent: x = a + b Ex
+    // lower a, b, upper a, b of the cell's (L0) and triangle's (L1) x-extent,
+    // x = a + b Ex, less 1/2 + kBoxPad (lower) and 1/2 - kBoxPad (upper): the
+    // candidate pixel columns are ceil(lower) .. floor(upper)
+    float4 L0, L1;
     uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
 // Per-point data of the resolve (Eq. 8-9): the cell's four world corners

@@ -675,6 +675,12 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
             const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
             if (__ldg(a.counts + pt.x) != 1u) band_bounds<4>(A, B, Y, ya, yb, c.ex_max, L0);
             if (!interior) band_bounds<3>(tA3, tB3, tY3, ya, yb, c.ex_max, L1);
+            // shifted so the splat converts them straight to pixel columns:
+            // pixel centres at x + 1/2, candidate margin kBoxPad on each side
+            L0.x = L0.x - (0.5f + kBoxPad);
+            L1.x = L1.x - (0.5f + kBoxPad);
+            L0.z = L0.z - (0.5f - kBoxPad);
+            L1.z = L1.z - (0.5f - kBoxPad);
         }
 
         ResolveRec* rr = a.rrec + p;

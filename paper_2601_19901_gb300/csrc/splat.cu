@@ -53,6 +53,8 @@ constexpr int kSplatWarps = 8;
 // Ask L2 for the line holding p (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// The per-pixel test; every condition is evaluated (no early exits), so the
+// two points of a warp and the lanes' different candidates do not diverge.
 __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float num, float qEx, float qEy,
                                            float qEz, const float4& q1, const float4& q2, const float4& q3,
                                            const float4& q4, float ulo, float uhi, float vlo, float vhi,
@@ -61,24 +63,18 @@ __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float n
     const float Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
     const float dx = Fx - Ex, dy = Fy - 0.0f, dz = -c.D;
     const float den = dot3(q3.x, q3.y, q3.z, dx, dy, dz);
-    if (den == 0.0f) return false;
     t = __fdiv_rn(num, den);
-    if (depth_ok) {
-        if (!(t > 0.0f)) return false;
-    } else {
-        const float depth = t * c.D;
-        if (!(depth >= c.near_z && depth <= c.far_z)) return false;
-    }
+    const float depth = t * c.D;
+    const bool in_depth = depth_ok ? t > 0.0f : (depth >= c.near_z && depth <= c.far_z);
     const float hx = fmaf(t, dx, qEx), hy = fmaf(t, dy, qEy), hz = fmaf(t, dz, qEz);
     const float uq = dot3(hx, hy, hz, q1.x, q1.y, q1.z);
     const float vq = dot3(hx, hy, hz, q2.x, q2.y, q2.z);
     const float u = uq - q2.w, vv = vq - q3.w;
-    if (!(u >= ulo && u < uhi && vv >= vlo && vv < vhi)) return false;
-    if (interior) return true;
+    const bool in_cell = u >= ulo && u < uhi && vv >= vlo && vv < vhi;
     const float w0 = edge_fn(q4.x, q4.y, q4.z, q4.w, uq, vq);
     const float w1 = edge_fn(q4.z, q4.w, 0.0f, 0.0f, uq, vq);
     const float w2 = edge_fn(0.0f, 0.0f, q4.x, q4.y, uq, vq);
-    return inside_either(w0, w1, w2);
+    return (den != 0.0f) & in_depth & in_cell & (interior | inside_either(w0, w1, w2));
 }
 
 template <int S>
@@ -131,8 +127,8 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                     const float Ex = s_ex[v];
                     const float lo = fmaxf(fmaf(L0.y, Ex, L0.x), fmaf(L1.y, Ex, L1.x));
                     const float hi = fminf(fmaf(L0.w, Ex, L0.z), fmaf(L1.w, Ex, L1.z));
-                    const int ix0 = max(__float2int_ru(lo - 0.5f - kBoxPad), 0);
-                    const int ix1 = min(__float2int_rd(hi - 0.5f + kBoxPad), int(c.W) - 1);
+                    const int ix0 = max(__float2int_ru(lo), 0);
+                    const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
                     if (ix0 <= ix1) {
                         const uint32_t x0 = uint32_t(ix0), nx = uint32_t(ix1 - ix0) + 1u;
                         pk[sl] = x0 | (nx << 14);
@@ -186,7 +182,8 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                 if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, depth_ok,
                                 x, y, t))
                     continue;
-                atomicMin(keys + (uint64_t)vo * npix + (uint64_t)y * c.W + x,
+                // a view holds at most 2^26 pixels: 32-bit offset within it
+                atomicMin(keys + ((uint64_t)uint32_t(vo) * uint32_t(npix) + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
                           ((unsigned long long)__float_as_uint(t) << 32) | pid);
                 writes++;
             }
