@@ -37,6 +37,8 @@ extern "C" {
 
 typedef struct lfdpr_display lfdpr_display;
 typedef struct lfdpr_mesh lfdpr_mesh;
+typedef struct lfdpr_texture_set lfdpr_texture_set;
+typedef struct lfdpr_batch lfdpr_batch;
 
 typedef enum {
     LFDPR_OK = 0,
@@ -275,6 +277,86 @@ lfdpr_status lfdpr_sample_points_noalloc(const lfdpr_display_desc *desc, const f
                                          const uint32_t *tex_wh, uint32_t n_tex, uint32_t *points,
                                          uint32_t max_points, uint32_t *counts,
                                          uint32_t *frame_counters, void *stream);
+
+/*
+ * Texture sets: textures (with their mip chains, Sec. 3.3) uploaded once and
+ * shared by any number of meshes, of any display, on the same device.
+ *
+ * lfdpr_create_texture_set: tex_rgba8[k] u8 [h][w][4] level-0 texels of
+ * texture k (host); tex_wh u32 [n_tex][2] their (w, h), powers of two
+ * <= 16384. Copied; mip chains built on the device; the call synchronises
+ * `stream`. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_create_texture_set(const uint8_t *const *tex_rgba8, const uint32_t *tex_wh,
+                                      uint32_t n_tex, void *stream, lfdpr_texture_set **out);
+
+/* Free a texture set (EINVAL while meshes still use it). */
+lfdpr_status lfdpr_destroy_texture_set(lfdpr_texture_set *set);
+
+/*
+ * lfdpr_upload_mesh_textured: lfdpr_upload_mesh with the textures of a
+ * texture set (tri_tex ids index it) instead of its own copy. The set must
+ * outlive the mesh. Errors as lfdpr_upload_mesh.
+ */
+lfdpr_status lfdpr_upload_mesh_textured(lfdpr_display *disp, const float *xyz, const float *uv,
+                                        const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_verts,
+                                        uint32_t n_tris, lfdpr_texture_set *set, void *stream,
+                                        lfdpr_mesh **out);
+
+/*
+ * Batched frames: n (display, mesh) scenes, each with its own display (view
+ * count, view size, panel), rendered and interleaved together. One call runs
+ * every scene's frame, Sec. 3.1-4 as lfdpr_render_frame followed by
+ * lfdpr_interleave, as one CUDA graph: per-scene set-up, scan, emission and
+ * fetch on `branches` concurrent graph branches, then one persistent splat
+ * launch over the point pairs of all scenes, then per-scene resolve and
+ * interleave into each display's own panel buffer (lfdpr_batch_panel). The
+ * graph is captured on the first lfdpr_render_batch after creation or a
+ * configuration change; later calls replay it with new model matrices. Each
+ * scene's views, keys and panel are bit-identical to rendering it alone.
+ */
+typedef struct {
+    int32_t branches;             /* concurrent graph branches for the per-scene stages, 1..32 */
+    int32_t splat_blocks_per_sm;  /* persistent splat grid: blocks of 256 threads per SM, 1..64 */
+    int32_t splat_slots;          /* views per lane in the splat: 1, 2, 3, 4, 6 or 8 */
+} lfdpr_batch_config;
+
+/*
+ * lfdpr_create_batch: displays[i], meshes[i] for i < n (1 <= n <= 64); each
+ * mesh uploaded to its display, each display at most once, rendered views
+ * summed over the batch <= 4096. Default configuration: 4 branches, 16
+ * blocks per SM, the fewest slots holding the largest view count (up to 8).
+ * The batch borrows the displays and meshes: they must outlive it.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_create_batch(lfdpr_display *const *displays, lfdpr_mesh *const *meshes, int32_t n,
+                                lfdpr_batch **out);
+lfdpr_status lfdpr_destroy_batch(lfdpr_batch *batch);
+/* Read or replace the configuration (EINVAL outside the ranges above). */
+lfdpr_status lfdpr_batch_get_config(const lfdpr_batch *batch, lfdpr_batch_config *out);
+lfdpr_status lfdpr_batch_set_config(lfdpr_batch *batch, const lfdpr_batch_config *cfg);
+
+/*
+ * lfdpr_render_batch: models f32 [n][16] (host, row-major, as in
+ * lfdpr_render_frame) for the scenes in order; asynchronous on `stream`.
+ * The graph must be replayed from one host thread at a time. Per-scene
+ * overflow is reported by lfdpr_frame_stats on that scene's display.
+ * Errors: EINVAL (non-finite model), ECUDA.
+ */
+lfdpr_status lfdpr_render_batch(lfdpr_batch *batch, const float *models, void *stream);
+
+/*
+ * lfdpr_batch_autotune: time every configuration of a fixed candidate set
+ * (branches x blocks per SM x slots) over `reps` replays each with the given
+ * models, keep the fastest, and return it (and its mean ms per batch) if the
+ * pointers are non-NULL. Synchronises `stream`. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_batch_autotune(lfdpr_batch *batch, const float *models, int32_t reps, void *stream,
+                                  lfdpr_batch_config *best, float *best_ms);
+
+/* Device panel u8 [panel_h][panel_w][4] of scene i after lfdpr_render_batch
+ * (borrowed; valid until the batch or its display is destroyed). */
+lfdpr_status lfdpr_batch_panel(const lfdpr_batch *batch, int32_t i, const uint8_t **panel);
 
 /* Description of the last error on this thread ("" if none). */
 const char *lfdpr_last_error(void);

@@ -194,6 +194,7 @@ struct FrameArgs {
     DispConst dc;
     const float* ex;                 // eye x per rendered view (device)
     float model[12];                 // affine rows of the model matrix
+    const float* model_dev;          // if set, the 12 model values are read from here (device) instead
     const float* xyz;
     const float* uv;
     const uint32_t* idx;
@@ -224,6 +225,23 @@ cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s);
+
+// One scene of a batched splat: its display constants and the buffers the
+// splat reads and writes.
+struct SplatScene {
+    DispConst dc;
+    const float* ex;
+    Counters* ctr;
+    const WorkRec* work;
+    const TriRec* rec;
+    uint64_t* keys;
+};
+constexpr int kMaxBatchScenes = 64;
+constexpr int kMaxBatchViews = 4096;   // rendered views summed over a batch
+// Splat every scene of a batch in one persistent launch: grid_per_sm blocks
+// per SM, slots view slots per lane (1, 2, 3, 4, 6 or 8).
+cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots, int grid_per_sm, int sm_count,
+                               cudaStream_t s);
 cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel,

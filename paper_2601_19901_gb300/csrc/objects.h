@@ -1,0 +1,71 @@
+// Library objects behind the opaque handles of include/lfdpr.h, shared by
+// runtime.cu (displays, meshes, texture sets, single frames) and batch.cu
+// (batched frames).
+#pragma once
+#include <vector>
+
+#include "lfdpr_internal.cuh"
+
+struct lfdpr_texture_set {
+    uint32_t n_tex = 0;
+    uint8_t* pool = nullptr;
+    lfdpr::TexDesc* tex = nullptr;
+    uint64_t* lvl = nullptr;
+    int n_meshes = 0;
+};
+
+struct lfdpr_display {
+    lfdpr_display_desc desc;
+    lfdpr::DispConst dc;
+    int device = 0;
+    int sm_count = 1;
+    std::vector<float> h_ex;
+    float* d_ex = nullptr;
+    uint4* points = nullptr;
+    uint32_t max_points = 0;
+    lfdpr::WorkRec* work = nullptr;
+    uint32_t* near = nullptr;
+    lfdpr::ResolveRec* rrec = nullptr;
+    uint64_t* keys = nullptr;
+    uint8_t* views = nullptr;
+    uint8_t* panel = nullptr;      // device scratch for host-memory panels
+    lfdpr::Counters* ctr = nullptr;
+    int n_meshes = 0;
+    int64_t launches = 0;
+    bool timing = false;
+    cudaEvent_t ev[LFDPR_N_STAGES + 2] = {};
+    bool ev_frame = false;        // the frame's stage events were recorded
+    bool ev_interleave = false;   // the interleave's events were recorded
+};
+
+struct lfdpr_mesh {
+    lfdpr_display* disp = nullptr;
+    uint32_t n_verts = 0, n_tris = 0, n_tex = 0, n_blocks = 0;
+    float* xyz = nullptr;
+    float* uv = nullptr;
+    uint32_t* idx = nullptr;
+    uint32_t* tri_tex = nullptr;
+    lfdpr_texture_set* shared = nullptr;   // the texture set whose pool/tex/lvl the mesh uses
+    bool owns_textures = false;            // pool/tex/lvl are the mesh's own (freed with it)
+    uint8_t* pool = nullptr;
+    lfdpr::TexDesc* tex = nullptr;
+    uint64_t* lvl = nullptr;
+    lfdpr::TriRec* rec = nullptr;
+    lfdpr::TriProj* tproj = nullptr;
+    uint32_t* counts = nullptr;
+    uint32_t* offsets = nullptr;
+    uint32_t* block_sums = nullptr;
+};
+
+namespace lfdpr {
+// Set the thread's last-error text and return s.
+lfdpr_status fail(lfdpr_status s, const char* fmt, ...);
+lfdpr_status cuda_fail(cudaError_t e, const char* what);
+// Kernel arguments of one frame of `mesh` on `disp` (model left unset).
+FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh);
+// The frame up to the splat on stream s: counters reset, set-up, scan,
+// emission, fetch, key clear, and (if near) the near-plane splat; stage
+// events 0-5 recorded if marks.
+lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
+                                bool marks, bool near);
+}  // namespace lfdpr

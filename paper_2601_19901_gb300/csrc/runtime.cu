@@ -10,63 +10,17 @@
 #include <new>
 #include <vector>
 
-#include "lfdpr_internal.cuh"
+#include "objects.h"
 
 using namespace lfdpr;
 
-struct lfdpr_display {
-    lfdpr_display_desc desc;
-    DispConst dc;
-    int device = 0;
-    int sm_count = 1;
-    std::vector<float> h_ex;
-    float* d_ex = nullptr;
-    uint4* points = nullptr;
-    uint32_t max_points = 0;
-    WorkRec* work = nullptr;
-    uint32_t* near = nullptr;
-    ResolveRec* rrec = nullptr;
-    uint64_t* keys = nullptr;
-    uint8_t* views = nullptr;
-    uint8_t* panel = nullptr;      // device scratch for host-memory panels
-    Counters* ctr = nullptr;
-    int n_meshes = 0;
-    int64_t launches = 0;
-    bool timing = false;
-    cudaEvent_t ev[LFDPR_N_STAGES + 2] = {};
-    bool ev_frame = false;        // the frame's stage events were recorded
-    bool ev_interleave = false;   // the interleave's events were recorded
-};
-
-struct lfdpr_mesh {
-    lfdpr_display* disp = nullptr;
-    uint32_t n_verts = 0, n_tris = 0, n_tex = 0, n_blocks = 0;
-    float* xyz = nullptr;
-    float* uv = nullptr;
-    uint32_t* idx = nullptr;
-    uint32_t* tri_tex = nullptr;
-    uint8_t* pool = nullptr;
-    TexDesc* tex = nullptr;
-    uint64_t* lvl = nullptr;
-    TriRec* rec = nullptr;
-    TriProj* tproj = nullptr;
-    uint32_t* counts = nullptr;
-    uint32_t* offsets = nullptr;
-    uint32_t* block_sums = nullptr;
-};
-
 namespace lfdpr {
 thread_local char g_last_error[512] = "";
-}
-
-namespace {
-
-#define g_err lfdpr::g_last_error
 
 lfdpr_status fail(lfdpr_status s, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
     va_end(ap);
     return s;
 }
@@ -75,6 +29,78 @@ lfdpr_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? LFDPR_ENOMEM : LFDPR_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
+
+FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
+    FrameArgs a{};
+    a.dc = disp->dc;
+    a.ex = disp->d_ex;
+    a.xyz = mesh->xyz;
+    a.uv = mesh->uv;
+    a.idx = mesh->idx;
+    a.tri_tex = mesh->tri_tex;
+    a.tex = mesh->tex;
+    a.pool = mesh->pool;
+    a.lvl = mesh->lvl;
+    a.n_tris = mesh->n_tris;
+    a.n_tex = mesh->n_tex;
+    a.rec = mesh->rec;
+    a.counts = mesh->counts;
+    a.offsets = mesh->offsets;
+    a.block_sums = mesh->block_sums;
+    a.n_blocks = mesh->n_blocks;
+    a.points = disp->points;
+    a.max_points = disp->max_points;
+    a.tproj = mesh->tproj;
+    a.work = disp->work;
+    a.near = disp->near;
+    a.rrec = disp->rrec;
+    a.keys = disp->keys;
+    a.views = disp->views;
+    a.ctr = disp->ctr;
+    a.sm_count = disp->sm_count;
+    return a;
+}
+
+lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
+                                bool marks, bool near) {
+    auto mk = [&](int k) {
+        if (marks) cudaEventRecord(disp->ev[k], s);
+    };
+    const uint64_t npix = uint64_t(disp->dc.W) * disp->dc.H * disp->dc.nr;
+#define CKF(call, what)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+    CKF(cudaMemsetAsync(disp->ctr, 0, sizeof(Counters), s), "reset counters");
+    mk(0);
+    if (mesh->n_tris) {
+        CKF(launch_setup(a, s), "launch k_setup");
+        mk(1);
+        CKF(launch_scan(a, s), "launch k_scan");
+        mk(2);
+        CKF(launch_emit(a, s), "launch k_emit");
+        mk(3);
+        CKF(launch_fetch(a, s), "launch k_fetch");
+        disp->launches += 4;
+    } else {
+        for (int k = 1; k <= 3; k++) mk(k);
+    }
+    mk(4);
+    CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
+    mk(5);
+    if (near && mesh->n_tris) {
+        CKF(launch_splat_near(a, s), "launch k_splat_near");
+        disp->launches += 1;
+    }
+#undef CKF
+    return LFDPR_OK;
+}
+}  // namespace lfdpr
+
+namespace {
+
+#define g_err lfdpr::g_last_error
 
 #define CK(call, what)                                  \
     do {                                                \
@@ -122,9 +148,11 @@ void free_mesh(lfdpr_mesh* m) {
     cudaFree(m->uv);
     cudaFree(m->idx);
     cudaFree(m->tri_tex);
-    cudaFree(m->pool);
-    cudaFree(m->tex);
-    cudaFree(m->lvl);
+    if (m->owns_textures) {
+        cudaFree(m->pool);
+        cudaFree(m->tex);
+        cudaFree(m->lvl);
+    }
     cudaFree(m->rec);
     cudaFree(m->tproj);
     cudaFree(m->counts);
@@ -139,6 +167,135 @@ double eye_angle_deg(const lfdpr_display_desc& d, int k) {
     const double cone = d.cone_deg;
     return d.recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * d.n_views)
                         : -cone / 2.0 + cone * (k + 0.5) / d.n_views;
+}
+
+// Validate and upload n_tex textures with their mip chains into one pool.
+// On success the caller owns *pool, *tex, *lvl; on failure nothing is left.
+lfdpr_status upload_textures(const uint8_t* const* tex_rgba8, const uint32_t* tex_wh, uint32_t n_tex,
+                             cudaStream_t s, uint8_t** pool_out, TexDesc** tex_out, uint64_t** lvl_out) {
+    if (n_tex == 0 || !tex_rgba8 || !tex_wh) return fail(LFDPR_EINVAL, "textures: need >= 1 texture");
+    std::vector<TexDesc> td(n_tex);
+    std::vector<uint64_t> lvl((size_t)n_tex * kMaxLevels, 0);
+    uint64_t pool_bytes = 0;
+    for (uint32_t k = 0; k < n_tex; k++) {
+        const uint32_t w = tex_wh[2 * k], h = tex_wh[2 * k + 1];
+        if (!pow2(w) || !pow2(h) || w > 16384 || h > 16384)
+            return fail(LFDPR_EINVAL, "textures: texture %u size %ux%u not a power of two <= 16384", k, w, h);
+        if (!tex_rgba8[k]) return fail(LFDPR_EINVAL, "textures: null texture %u", k);
+        td[k].offset = pool_bytes;
+        td[k].w = w;
+        td[k].h = h;
+        td[k].levels = mip_levels(w, h);
+        td[k].pad = 0;
+        uint64_t off = pool_bytes;
+        for (uint32_t l = 0; l < td[k].levels; l++) {
+            lvl[(size_t)k * kMaxLevels + l] = off;
+            const uint64_t lw = (w >> l) ? (w >> l) : 1, lh = (h >> l) ? (h >> l) : 1;
+            off += lw * lh * 4u;
+        }
+        pool_bytes += (mip_bytes(w, h) + 255) & ~uint64_t(255);
+    }
+    uint8_t* pool = nullptr;
+    TexDesc* tex = nullptr;
+    uint64_t* dl = nullptr;
+    auto undo = [&]() {
+        cudaFree(pool);
+        cudaFree(tex);
+        cudaFree(dl);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&pool, pool_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
+        (e = cudaMalloc(&dl, sizeof(uint64_t) * kMaxLevels * n_tex)) != cudaSuccess) {
+        undo();
+        return cuda_fail(e, "textures: cudaMalloc");
+    }
+#define CKT(call, what)                 \
+    do {                                \
+        cudaError_t e_ = (call);        \
+        if (e_ != cudaSuccess) {        \
+            undo();                     \
+            return cuda_fail(e_, what); \
+        }                               \
+    } while (0)
+    CKT(cudaMemcpyAsync(tex, td.data(), sizeof(TexDesc) * n_tex, cudaMemcpyHostToDevice, s), "upload tex table");
+    CKT(cudaMemcpyAsync(dl, lvl.data(), sizeof(uint64_t) * kMaxLevels * n_tex, cudaMemcpyHostToDevice, s),
+        "upload level offsets");
+    for (uint32_t k = 0; k < n_tex; k++) {
+        uint32_t w = td[k].w, h = td[k].h;
+        uint8_t* cur = pool + td[k].offset;
+        CKT(cudaMemcpyAsync(cur, tex_rgba8[k], 4u * (uint64_t)w * h, cudaMemcpyHostToDevice, s), "upload texels");
+        for (uint32_t l = 1; l < td[k].levels; l++) {
+            const uint32_t nw = w > 1 ? w / 2 : 1, nh = h > 1 ? h / 2 : 1;
+            uint8_t* nxt = cur + 4u * (uint64_t)w * h;
+            CKT(launch_mip_level(cur, w, h, nxt, nw, nh, s), "mip build");
+            cur = nxt;
+            w = nw;
+            h = nh;
+        }
+    }
+    CKT(cudaStreamSynchronize(s), "textures: synchronize");
+#undef CKT
+    *pool_out = pool;
+    *tex_out = tex;
+    *lvl_out = dl;
+    return LFDPR_OK;
+}
+
+// Validate a mesh's geometry against n_tex textures and upload it into a new
+// mesh object whose textures are not yet set. On success *out is the mesh.
+lfdpr_status upload_geometry(lfdpr_display* disp, const float* xyz, const float* uv, const uint32_t* idx,
+                             const uint32_t* tri_tex, uint32_t n_verts, uint32_t n_tris, uint32_t n_tex,
+                             cudaStream_t s, lfdpr_mesh** out) {
+    if (n_tris > 0 && (!xyz || !uv || !idx || !tri_tex)) return fail(LFDPR_EINVAL, "upload_mesh: null array");
+    if (n_tris > (1u << 30)) return fail(LFDPR_EINVAL, "upload_mesh: too many triangles");
+    for (uint64_t k = 0; k < 3ull * n_tris; k++)
+        if (idx[k] >= n_verts)
+            return fail(LFDPR_EINVAL, "upload_mesh: index %u out of range at %llu", idx[k], (unsigned long long)k);
+    for (uint32_t t = 0; t < n_tris; t++)
+        if (tri_tex[t] >= n_tex) return fail(LFDPR_EINVAL, "upload_mesh: texture id out of range at triangle %u", t);
+    for (uint64_t k = 0; k < 3ull * n_verts; k++)
+        if (!std::isfinite(xyz[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite vertex coordinate");
+    for (uint64_t k = 0; k < 2ull * n_verts; k++)
+        if (!std::isfinite(uv[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite texture coordinate");
+    lfdpr_mesh* m = new (std::nothrow) lfdpr_mesh();
+    if (!m) return fail(LFDPR_ENOMEM, "host allocation failed");
+    m->disp = disp;
+    m->n_verts = n_verts;
+    m->n_tris = n_tris;
+    m->n_tex = n_tex;
+    m->n_blocks = (n_tris + kSetupThreads - 1) / kSetupThreads;
+    const uint64_t nt = n_tris ? n_tris : 1, nv = n_verts ? n_verts : 1;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->xyz, 12u * nv)) != cudaSuccess || (e = cudaMalloc(&m->uv, 8u * nv)) != cudaSuccess ||
+        (e = cudaMalloc(&m->idx, 12u * nt)) != cudaSuccess || (e = cudaMalloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
+        (e = cudaMalloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
+        free_mesh(m);
+        return cuda_fail(e, "upload_mesh: cudaMalloc");
+    }
+#define CKM(call, what)                 \
+    do {                                \
+        cudaError_t e_ = (call);        \
+        if (e_ != cudaSuccess) {        \
+            free_mesh(m);               \
+            return cuda_fail(e_, what); \
+        }                               \
+    } while (0)
+    if (n_verts) {
+        CKM(cudaMemcpyAsync(m->xyz, xyz, 12u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload xyz");
+        CKM(cudaMemcpyAsync(m->uv, uv, 8u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload uv");
+    }
+    if (n_tris) {
+        CKM(cudaMemcpyAsync(m->idx, idx, 12u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload idx");
+        CKM(cudaMemcpyAsync(m->tri_tex, tri_tex, 4u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload tri_tex");
+    }
+    CKM(cudaStreamSynchronize(s), "upload_mesh: synchronize");
+#undef CKM
+    *out = m;
+    return LFDPR_OK;
 }
 
 void mark(lfdpr_display* d, int k, cudaStream_t s) {
@@ -274,94 +431,77 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display* disp, const float* xyz, const floa
     g_err[0] = 0;
     if (!disp || !out) return fail(LFDPR_EINVAL, "upload_mesh: null display or out");
     *out = nullptr;
-    if (n_tris > 0 && (!xyz || !uv || !idx || !tri_tex)) return fail(LFDPR_EINVAL, "upload_mesh: null array");
     if (n_tex == 0 || !tex_rgba8 || !tex_wh) return fail(LFDPR_EINVAL, "upload_mesh: need >= 1 texture");
-    if (n_tris > (1u << 30)) return fail(LFDPR_EINVAL, "upload_mesh: too many triangles");
-    for (uint64_t k = 0; k < 3ull * n_tris; k++)
-        if (idx[k] >= n_verts) return fail(LFDPR_EINVAL, "upload_mesh: index %u out of range at %llu", idx[k], (unsigned long long)k);
-    for (uint32_t t = 0; t < n_tris; t++)
-        if (tri_tex[t] >= n_tex) return fail(LFDPR_EINVAL, "upload_mesh: texture id out of range at triangle %u", t);
-    for (uint64_t k = 0; k < 3ull * n_verts; k++)
-        if (!std::isfinite(xyz[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite vertex coordinate");
-    for (uint64_t k = 0; k < 2ull * n_verts; k++)
-        if (!std::isfinite(uv[k])) return fail(LFDPR_EINVAL, "upload_mesh: non-finite texture coordinate");
-    std::vector<TexDesc> td(n_tex);
-    std::vector<uint64_t> lvl((size_t)n_tex * kMaxLevels, 0);
-    uint64_t pool_bytes = 0;
     for (uint32_t k = 0; k < n_tex; k++) {
         const uint32_t w = tex_wh[2 * k], h = tex_wh[2 * k + 1];
         if (!pow2(w) || !pow2(h) || w > 16384 || h > 16384)
             return fail(LFDPR_EINVAL, "upload_mesh: texture %u size %ux%u not a power of two <= 16384", k, w, h);
         if (!tex_rgba8[k]) return fail(LFDPR_EINVAL, "upload_mesh: null texture %u", k);
-        td[k].offset = pool_bytes;
-        td[k].w = w;
-        td[k].h = h;
-        td[k].levels = mip_levels(w, h);
-        td[k].pad = 0;
-        uint64_t off = pool_bytes;
-        for (uint32_t l = 0; l < td[k].levels; l++) {
-            lvl[(size_t)k * kMaxLevels + l] = off;
-            const uint64_t lw = (w >> l) ? (w >> l) : 1, lh = (h >> l) ? (h >> l) : 1;
-            off += lw * lh * 4u;
-        }
-        pool_bytes += (mip_bytes(w, h) + 255) & ~uint64_t(255);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    lfdpr_mesh* m = new (std::nothrow) lfdpr_mesh();
-    if (!m) return fail(LFDPR_ENOMEM, "host allocation failed");
-    m->disp = disp;
-    m->n_verts = n_verts;
-    m->n_tris = n_tris;
-    m->n_tex = n_tex;
-    m->n_blocks = (n_tris + kSetupThreads - 1) / kSetupThreads;
-    const uint64_t nt = n_tris ? n_tris : 1, nv = n_verts ? n_verts : 1;
-    cudaError_t e;
-    if ((e = cudaMalloc(&m->xyz, 12u * nv)) != cudaSuccess || (e = cudaMalloc(&m->uv, 8u * nv)) != cudaSuccess ||
-        (e = cudaMalloc(&m->idx, 12u * nt)) != cudaSuccess || (e = cudaMalloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->pool, pool_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&m->tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
-        (e = cudaMalloc(&m->lvl, sizeof(uint64_t) * kMaxLevels * n_tex)) != cudaSuccess ||
-        (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
+    lfdpr_mesh* m = nullptr;
+    lfdpr_status st = upload_geometry(disp, xyz, uv, idx, tri_tex, n_verts, n_tris, n_tex, s, &m);
+    if (st != LFDPR_OK) return st;
+    st = upload_textures(tex_rgba8, tex_wh, n_tex, s, &m->pool, &m->tex, &m->lvl);
+    if (st != LFDPR_OK) {
         free_mesh(m);
-        return cuda_fail(e, "upload_mesh: cudaMalloc");
+        return st;
     }
-#define CKM(call, what)                         \
-    do {                                        \
-        cudaError_t e_ = (call);                \
-        if (e_ != cudaSuccess) {                \
-            free_mesh(m);                       \
-            return cuda_fail(e_, what);         \
-        }                                       \
-    } while (0)
-    if (n_verts) {
-        CKM(cudaMemcpyAsync(m->xyz, xyz, 12u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload xyz");
-        CKM(cudaMemcpyAsync(m->uv, uv, 8u * (uint64_t)n_verts, cudaMemcpyHostToDevice, s), "upload uv");
+    m->owns_textures = true;
+    disp->n_meshes++;
+    *out = m;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_create_texture_set(const uint8_t* const* tex_rgba8, const uint32_t* tex_wh, uint32_t n_tex,
+                                      void* stream, lfdpr_texture_set** out) {
+    g_err[0] = 0;
+    if (!out) return fail(LFDPR_EINVAL, "create_texture_set: null out");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(LFDPR_EDEVICE, "no CUDA device");
     }
-    if (n_tris) {
-        CKM(cudaMemcpyAsync(m->idx, idx, 12u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload idx");
-        CKM(cudaMemcpyAsync(m->tri_tex, tri_tex, 4u * (uint64_t)n_tris, cudaMemcpyHostToDevice, s), "upload tri_tex");
+    lfdpr_texture_set* t = new (std::nothrow) lfdpr_texture_set();
+    if (!t) return fail(LFDPR_ENOMEM, "host allocation failed");
+    const lfdpr_status st =
+        upload_textures(tex_rgba8, tex_wh, n_tex, static_cast<cudaStream_t>(stream), &t->pool, &t->tex, &t->lvl);
+    if (st != LFDPR_OK) {
+        delete t;
+        return st;
     }
-    CKM(cudaMemcpyAsync(m->tex, td.data(), sizeof(TexDesc) * n_tex, cudaMemcpyHostToDevice, s), "upload tex table");
-    CKM(cudaMemcpyAsync(m->lvl, lvl.data(), sizeof(uint64_t) * kMaxLevels * n_tex, cudaMemcpyHostToDevice, s),
-        "upload level offsets");
-    for (uint32_t k = 0; k < n_tex; k++) {
-        uint32_t w = td[k].w, h = td[k].h;
-        uint8_t* lvl = m->pool + td[k].offset;
-        CKM(cudaMemcpyAsync(lvl, tex_rgba8[k], 4u * (uint64_t)w * h, cudaMemcpyHostToDevice, s), "upload texels");
-        for (uint32_t l = 1; l < td[k].levels; l++) {
-            const uint32_t nw = w > 1 ? w / 2 : 1, nh = h > 1 ? h / 2 : 1;
-            uint8_t* nxt = lvl + 4u * (uint64_t)w * h;
-            CKM(launch_mip_level(lvl, w, h, nxt, nw, nh, s), "mip build");
-            lvl = nxt;
-            w = nw;
-            h = nh;
-        }
-    }
-    CKM(cudaStreamSynchronize(s), "upload_mesh: synchronize");
-#undef CKM
+    t->n_tex = n_tex;
+    *out = t;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_destroy_texture_set(lfdpr_texture_set* set) {
+    g_err[0] = 0;
+    if (!set) return fail(LFDPR_EINVAL, "destroy_texture_set: null");
+    if (set->n_meshes != 0) return fail(LFDPR_EINVAL, "destroy_texture_set: meshes still use it");
+    cudaFree(set->pool);
+    cudaFree(set->tex);
+    cudaFree(set->lvl);
+    delete set;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_upload_mesh_textured(lfdpr_display* disp, const float* xyz, const float* uv, const uint32_t* idx,
+                                        const uint32_t* tri_tex, uint32_t n_verts, uint32_t n_tris,
+                                        lfdpr_texture_set* set, void* stream, lfdpr_mesh** out) {
+    g_err[0] = 0;
+    if (!disp || !out || !set) return fail(LFDPR_EINVAL, "upload_mesh_textured: null display, set or out");
+    *out = nullptr;
+    lfdpr_mesh* m = nullptr;
+    const lfdpr_status st = upload_geometry(disp, xyz, uv, idx, tri_tex, n_verts, n_tris, set->n_tex,
+                                            static_cast<cudaStream_t>(stream), &m);
+    if (st != LFDPR_OK) return st;
+    m->shared = set;
+    m->pool = set->pool;
+    m->tex = set->tex;
+    m->lvl = set->lvl;
+    set->n_meshes++;
     disp->n_meshes++;
     *out = m;
     return LFDPR_OK;
@@ -371,6 +511,7 @@ lfdpr_status lfdpr_destroy_mesh(lfdpr_mesh* mesh) {
     g_err[0] = 0;
     if (!mesh) return fail(LFDPR_EINVAL, "destroy_mesh: null");
     if (mesh->disp) mesh->disp->n_meshes--;
+    if (mesh->shared) mesh->shared->n_meshes--;
     free_mesh(mesh);
     return LFDPR_OK;
 }
@@ -382,52 +523,10 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     for (int k = 0; k < 12; k++)
         if (!std::isfinite(model[k])) return fail(LFDPR_EINVAL, "render_frame: non-finite model matrix");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    FrameArgs a{};
-    a.dc = disp->dc;
-    a.ex = disp->d_ex;
+    FrameArgs a = frame_args(disp, mesh);
     for (int k = 0; k < 12; k++) a.model[k] = model[k];
-    a.xyz = mesh->xyz;
-    a.uv = mesh->uv;
-    a.idx = mesh->idx;
-    a.tri_tex = mesh->tri_tex;
-    a.tex = mesh->tex;
-    a.pool = mesh->pool;
-    a.lvl = mesh->lvl;
-    a.n_tris = mesh->n_tris;
-    a.n_tex = mesh->n_tex;
-    a.rec = mesh->rec;
-    a.counts = mesh->counts;
-    a.offsets = mesh->offsets;
-    a.block_sums = mesh->block_sums;
-    a.n_blocks = mesh->n_blocks;
-    a.points = disp->points;
-    a.max_points = disp->max_points;
-    a.tproj = mesh->tproj;
-    a.work = disp->work;
-    a.near = disp->near;
-    a.rrec = disp->rrec;
-    a.keys = disp->keys;
-    a.views = disp->views;
-    a.ctr = disp->ctr;
-    a.sm_count = disp->sm_count;
-    const uint64_t npix = uint64_t(disp->dc.W) * disp->dc.H * disp->dc.nr;
-    CK(cudaMemsetAsync(disp->ctr, 0, sizeof(Counters), s), "render_frame: reset counters");
-    mark(disp, 0, s);
-    if (mesh->n_tris) {
-        CK(launch_setup(a, s), "launch k_setup");
-        mark(disp, 1, s);
-        CK(launch_scan(a, s), "launch k_scan");
-        mark(disp, 2, s);
-        CK(launch_emit(a, s), "launch k_emit");
-        mark(disp, 3, s);
-        CK(launch_fetch(a, s), "launch k_fetch");
-        disp->launches += 4;
-    } else {
-        for (int k = 1; k <= 3; k++) mark(disp, k, s);
-    }
-    mark(disp, 4, s);
-    CK(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "render_frame: clear keys");
-    mark(disp, 5, s);
+    const lfdpr_status st = record_frame_front(disp, mesh, a, s, disp->timing, false);
+    if (st != LFDPR_OK) return st;
     if (mesh->n_tris) {
         CK(launch_splat(a, s), "launch k_splat");
         CK(launch_splat_near(a, s), "launch k_splat_near");

@@ -128,11 +128,13 @@ struct SetupOut {
 __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, TriProj& tp) {
     const DispConst& c = a.dc;
     SetupOut res{0u, false, false};
-    float P[3][3], Q[3][2];
+    float P[3][3], Q[3][2], M[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) M[k] = a.model_dev ? __ldg(a.model_dev + k) : a.model[k];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const uint32_t vi = a.idx[3 * (size_t)t + k];
-        transform(a.model, a.xyz[3 * (size_t)vi], a.xyz[3 * (size_t)vi + 1], a.xyz[3 * (size_t)vi + 2], P[k]);
+        transform(M, a.xyz[3 * (size_t)vi], a.xyz[3 * (size_t)vi + 1], a.xyz[3 * (size_t)vi + 2], P[k]);
         Q[k][0] = a.uv[2 * (size_t)vi];
         Q[k][1] = a.uv[2 * (size_t)vi + 1];
     }

@@ -77,34 +77,106 @@ __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float n
     return (den != 0.0f) & in_depth & in_cell & (interior | inside_either(w0, w1, w2));
 }
 
-template <int S>
-__global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
-    __shared__ float s_ex[kMaxRenderViews];
-    const DispConst& c = a.dc;
-    for (int v = threadIdx.x; v < c.nr; v += blockDim.x) s_ex[v] = a.ex[v];
-    __syncthreads();
-    if (a.ctr->overflow) return;
-    const uint32_t n = a.ctr->n_work;
+// Eye x of view v from the eye array at shared-memory address ex_s.
+__device__ __forceinline__ float eye_x(uint32_t ex_s, int v) {
+    float e;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(e) : "r"(ex_s + 4u * uint32_t(v)));
+    return e;
+}
+
+// warp-aggregated count of depth-test writes (the atomics issued)
+__device__ __forceinline__ void add_writes(Counters* ctr, uint32_t writes) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
+    if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&ctr->n_writes, writes);
+}
+
+// Where the splat's point pairs come from: one scene (its constants in the
+// kernel's parameters), or every scene of a batch (constants in shared
+// memory; the pairs of all scenes form one index range, scene by scene).
+struct OneScene {
+    static constexpr bool kMany = false;
+    const FrameArgs& a;
+    uint32_t n;       // work points
+    uint32_t ex_s;    // shared-memory address of the eye positions
+    __device__ __forceinline__ int scene(uint32_t) const { return 0; }
+    __device__ __forceinline__ uint32_t first_pair(int) const { return 0u; }
+    __device__ __forceinline__ const DispConst& dc(int) const { return a.dc; }
+    __device__ __forceinline__ uint32_t eyes(int) const { return ex_s; }
+    __device__ __forceinline__ uint32_t points(int) const { return n; }
+    __device__ __forceinline__ const WorkRec* work(int) const { return a.work; }
+    __device__ __forceinline__ const TriRec* rec(int) const { return a.rec; }
+    __device__ __forceinline__ unsigned long long* keys(int) const {
+        return reinterpret_cast<unsigned long long*>(a.keys);
+    }
+    __device__ __forceinline__ Counters* ctr(int) const { return a.ctr; }
+};
+
+struct ManyScenes {
+    static constexpr bool kMany = true;
+    const SplatScene* scenes;
+    int n_scenes;
+    const DispConst* s_dc;
+    const uint32_t* s_pair0;   // first pair of each scene, then the total
+    const uint32_t* s_n;       // work points of each scene
+    uint32_t ex_s;             // shared-memory address of all scenes' eye positions
+    const uint32_t* s_ex0;     // first eye of each scene
+    // the scene holding pair g: the last with s_pair0 <= g
+    __device__ __forceinline__ int scene(uint32_t g) const {
+        int lo = 0, hi = n_scenes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pair0[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ uint32_t first_pair(int q) const { return s_pair0[q]; }
+    __device__ __forceinline__ const DispConst& dc(int q) const { return s_dc[q]; }
+    __device__ __forceinline__ uint32_t eyes(int q) const { return ex_s + 4u * s_ex0[q]; }
+    __device__ __forceinline__ uint32_t points(int q) const { return s_n[q]; }
+    __device__ __forceinline__ const WorkRec* work(int q) const { return scenes[q].work; }
+    __device__ __forceinline__ const TriRec* rec(int q) const { return scenes[q].rec; }
+    __device__ __forceinline__ unsigned long long* keys(int q) const {
+        return reinterpret_cast<unsigned long long*>(scenes[q].keys);
+    }
+    __device__ __forceinline__ Counters* ctr(int q) const { return scenes[q].ctr; }
+};
+
+// The splat proper: warps stride through point pairs 0 .. total-1 of `src`,
+// one work point per half-warp (both halves always in the same scene).
+template <int S, class Src>
+__device__ __forceinline__ void splat_pairs(const Src& src, uint32_t total) {
     const int lane = threadIdx.x & 31, sub = lane & 15, half = lane >> 4;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    const uint64_t npix = (uint64_t)c.W * c.H;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
     uint32_t writes = 0;
+    int cur = 0;
 
-    // Every loop below has the same trip count in both halves of the warp
-    // (pairs of points; the larger pass count of the two), so each warp
-    // instruction serves both points.
-    for (uint32_t kk = warp; 2 * kk < n; kk += n_warps) {
+    for (uint32_t g = warp; g < total; g += n_warps) {
+        const int sc = src.scene(g);
+        if constexpr (Src::kMany) {
+            if (sc != cur) {
+                add_writes(src.ctr(cur), writes);
+                writes = 0;
+                cur = sc;
+            }
+        }
+        const DispConst& c = src.dc(sc);
+        const uint32_t ex_s = src.eyes(sc), n = src.points(sc);
+        const WorkRec* work = src.work(sc);
+        unsigned long long* keys = src.keys(sc);
+        const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
+        const uint32_t kk = g - src.first_pair(sc);
         const uint32_t k = 2 * kk + uint32_t(half);
         const bool act = k < n;
-        const WorkRec* wr = a.work + (act ? k : 2 * kk);
-        if (sub == 0 && k + 2 * n_warps < n) prefetch_l2(a.work + k + 2 * n_warps);   // next pair's record
+        const WorkRec* wr = work + (act ? k : 2 * kk);
+        if (sub == 0 && k + 2 * n_warps < n) prefetch_l2(work + k + 2 * n_warps);   // next pair's record
         const float4 L0 = __ldg(&wr->L0), L1 = __ldg(&wr->L1);
         const uint4 meta = __ldg(&wr->meta);
         const uint32_t tri = meta.z;
         const unsigned long long pid = meta.w;
-        const TriRec* r = a.rec + tri;
+        const TriRec* r = src.rec(sc) + tri;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
         const int y0 = int(meta.x & 0x3fffu);
@@ -116,15 +188,18 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
         const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
         const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
 
-        for (int g = 0; g < c.nr; g += 16 * S) {
+        // Every loop below has the same trip count in both halves of the
+        // warp (the larger pass count of the two points), so each warp
+        // instruction serves both points.
+        for (int g0 = 0; g0 < c.nr; g0 += 16 * S) {
             uint32_t pk[S];      // x0 | n_columns << 14 of the lane's views
             uint32_t cnt = 0;
 #pragma unroll
             for (int sl = 0; sl < S; sl++) {
-                const int v = g + 16 * sl + sub;
+                const int v = g0 + 16 * sl + sub;
                 pk[sl] = 0u;
                 if (v < c.nr) {
-                    const float Ex = s_ex[v];
+                    const float Ex = eye_x(ex_s, v);
                     const float lo = fmaxf(fmaf(L0.y, Ex, L0.x), fmaf(L1.y, Ex, L1.x));
                     const float hi = fminf(fmaf(L0.w, Ex, L0.z), fmaf(L1.w, Ex, L1.z));
                     const int ix0 = max(__float2int_ru(lo), 0);
@@ -142,8 +217,8 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o, 16);
                 if (sub >= o) incl += t;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 15, 16);
-            const uint32_t both = max(total, __shfl_xor_sync(0xffffffffu, total, 16));
+            const uint32_t total_h = __shfl_sync(0xffffffffu, incl, 15, 16);
+            const uint32_t both = max(total_h, __shfl_xor_sync(0xffffffffu, total_h, 16));
             const uint32_t excl = incl - cnt;
             for (uint32_t pass = 0; pass < both; pass += 16) {
                 const uint32_t q = pass + sub;
@@ -158,7 +233,7 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                 uint32_t opk[S];
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) opk[sl] = __shfl_sync(0xffffffffu, pk[sl], own, 16);
-                if (q >= total) continue;
+                if (q >= total_h) continue;
                 // the owner's view slot holding candidate q
                 uint32_t rr = q - o_excl, sel = opk[0];
                 int slot = 0;
@@ -174,25 +249,70 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
                 const uint32_t o_nx = sel >> 14;
                 const uint32_t ry = ny == 1 ? 0u : rr / o_nx;
                 const int x = int(sel & 0x3fffu) + int(rr - ry * o_nx), y = y0 + int(ry);
-                const int vo = g + 16 * slot + own;
-                const float Ex_o = s_ex[vo];
+                const int vo = g0 + 16 * slot + own;
+                const float Ex_o = eye_x(ex_s, vo);
                 const float qEx = Ex_o - q0.x;
                 const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
                 float t;
-                if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior, depth_ok,
-                                x, y, t))
+                if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior,
+                                depth_ok, x, y, t))
                     continue;
                 // a view holds at most 2^26 pixels: 32-bit offset within it
-                atomicMin(keys + ((uint64_t)uint32_t(vo) * uint32_t(npix) + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
+                atomicMin(keys + ((uint64_t)uint32_t(vo) * npix + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
                           ((unsigned long long)__float_as_uint(t) << 32) | pid);
                 writes++;
             }
         }
     }
-    // warp-aggregated count of depth-test writes (the atomics issued)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
-    if (lane == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
+    add_writes(src.ctr(cur), writes);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
+    __shared__ float s_ex[kMaxRenderViews];
+    for (int v = threadIdx.x; v < a.dc.nr; v += blockDim.x) s_ex[v] = a.ex[v];
+    __syncthreads();
+    if (a.ctr->overflow) return;
+    const uint32_t n = a.ctr->n_work;
+    const OneScene src{a, n, uint32_t(__cvta_generic_to_shared(s_ex))};
+    splat_pairs<S>(src, (n + 1u) >> 1);
+}
+
+// Every scene of a batch in one persistent launch: warps stride through the
+// point pairs of all scenes, so scenes of uneven size share the machine.
+// Each block keeps every scene's display constants and eye positions in
+// shared memory.
+template <int S>
+__global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat_batch(const SplatScene* __restrict__ scenes,
+                                                                     int n_scenes) {
+    __shared__ DispConst s_dc[kMaxBatchScenes];
+    __shared__ uint32_t s_pair0[kMaxBatchScenes + 1];   // first pair of each scene
+    __shared__ uint32_t s_n[kMaxBatchScenes];           // work points (0 after an overflow)
+    __shared__ uint32_t s_ex0[kMaxBatchScenes + 1];     // first eye of each scene in s_ex
+    __shared__ float s_ex[kMaxBatchViews];
+    for (int q = threadIdx.x; q < n_scenes; q += blockDim.x) {
+        s_dc[q] = scenes[q].dc;
+        const Counters* ct = scenes[q].ctr;
+        s_n[q] = ct->overflow ? 0u : ct->n_work;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t p = 0, e = 0;
+        for (int q = 0; q < n_scenes; q++) {
+            s_pair0[q] = p;
+            s_ex0[q] = e;
+            p += (s_n[q] + 1u) >> 1;
+            e += uint32_t(s_dc[q].nr);
+        }
+        s_pair0[n_scenes] = p;
+        s_ex0[n_scenes] = e;
+    }
+    __syncthreads();
+    for (int q = 0; q < n_scenes; q++)
+        for (int v = threadIdx.x; v < s_dc[q].nr; v += blockDim.x) s_ex[s_ex0[q] + v] = scenes[q].ex[v];
+    __syncthreads();
+    const ManyScenes src{scenes, n_scenes, s_dc, s_pair0, s_n, uint32_t(__cvta_generic_to_shared(s_ex)), s_ex0};
+    splat_pairs<S>(src, s_pair0[n_scenes]);
 }
 
 // Points whose cell or triangle reaches the eyes' plane: their projections
@@ -309,6 +429,22 @@ cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
         k_splat<6><<<grid, block, 0, s>>>(a);
     else
         k_splat<8><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots, int grid_per_sm, int sm_count,
+                               cudaStream_t s) {
+    if (n_scenes < 1 || n_scenes > kMaxBatchScenes || grid_per_sm < 1) return cudaErrorInvalidValue;
+    const int grid = sm_count * grid_per_sm, block = kSplatWarps * 32;
+    switch (slots) {
+        case 1: k_splat_batch<1><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 2: k_splat_batch<2><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 3: k_splat_batch<3><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 4: k_splat_batch<4><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 6: k_splat_batch<6><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 8: k_splat_batch<8><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -28,7 +28,10 @@ TRI = dict(P0=0, s_u=3, eu=4, s_v=7, ev=8, umin=11, n=12, vmin=15, a1=16, b1=17,
 EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_destroy_mesh", "lfdpr_render_frame", "lfdpr_interleave", "lfdpr_frame_stats",
            "lfdpr_get_buffers", "lfdpr_view_eyes", "lfdpr_probe_atomic_min", "lfdpr_last_error",
-           "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc"]
+           "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc",
+           "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
+           "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
+           "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel"]
 
 
 class LfdprError(RuntimeError):
@@ -56,6 +59,13 @@ class Stats(C.Structure):
                 ("cell_overflow", C.c_int32), ("kernel_launches", C.c_int64),
                 ("n_splat_writes", C.c_int64),
                 ("stage_ms", C.c_float * N_STAGES)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("branches", C.c_int32), ("splat_blocks_per_sm", C.c_int32), ("splat_slots", C.c_int32)]
+
+    def as_tuple(self):
+        return (self.branches, self.splat_blocks_per_sm, self.splat_slots)
 
 
 class Buffers(C.Structure):
@@ -90,6 +100,18 @@ def lib() -> C.CDLL:
         L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
                                                   P, C.c_uint32, P, C.c_uint32, P, P, P]
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
+        L.lfdpr_create_texture_set.argtypes = [P, P, C.c_uint32, P, C.POINTER(C.c_void_p)]
+        L.lfdpr_destroy_texture_set.argtypes = [P]
+        L.lfdpr_upload_mesh_textured.argtypes = [P, P, P, P, P, C.c_uint32, C.c_uint32, P, P,
+                                                 C.POINTER(C.c_void_p)]
+        L.lfdpr_create_batch.argtypes = [P, P, C.c_int32, C.POINTER(C.c_void_p)]
+        L.lfdpr_destroy_batch.argtypes = [P]
+        L.lfdpr_batch_get_config.argtypes = [P, C.POINTER(BatchConfig)]
+        L.lfdpr_batch_set_config.argtypes = [P, C.POINTER(BatchConfig)]
+        L.lfdpr_render_batch.argtypes = [P, P, P]
+        L.lfdpr_batch_autotune.argtypes = [P, P, C.c_int32, P, C.POINTER(BatchConfig),
+                                           C.POINTER(C.c_float)]
+        L.lfdpr_batch_panel.argtypes = [P, C.c_int32, C.POINTER(C.c_void_p)]
         for name in EXPORTS:
             fn = getattr(L, name)
             if name == "lfdpr_last_error":
@@ -223,6 +245,80 @@ def lfdpr_version() -> int:
     return int(lib().lfdpr_version())
 
 
+def _textures(textures: Sequence[np.ndarray]):
+    texs = [np.ascontiguousarray(t, np.uint8) for t in textures]
+    ptrs = (C.c_void_p * len(texs))(*[t.ctypes.data for t in texs])
+    wh = np.array([[t.shape[1], t.shape[0]] for t in texs], np.uint32).ravel()
+    return texs, ptrs, wh
+
+
+def lfdpr_create_texture_set(textures: Sequence[np.ndarray], stream=None) -> int:
+    texs, ptrs, wh = _textures(textures)
+    h = C.c_void_p()
+    _check(lib().lfdpr_create_texture_set(ptrs, _ptr(wh), len(texs), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def lfdpr_destroy_texture_set(tex_set: int):
+    _check(lib().lfdpr_destroy_texture_set(tex_set))
+
+
+def lfdpr_upload_mesh_textured(disp: int, xyz: np.ndarray, uv: np.ndarray, idx: np.ndarray,
+                               tri_tex: np.ndarray, tex_set: int, stream=None) -> int:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    uv = np.ascontiguousarray(uv, np.float32)
+    idx = np.ascontiguousarray(idx, np.uint32)
+    tri_tex = np.ascontiguousarray(tri_tex, np.uint32)
+    h = C.c_void_p()
+    _check(lib().lfdpr_upload_mesh_textured(disp, _ptr(xyz), _ptr(uv), _ptr(idx), _ptr(tri_tex),
+                                            xyz.shape[0], idx.reshape(-1, 3).shape[0], tex_set,
+                                            _stream(stream), C.byref(h)))
+    return h.value
+
+
+def lfdpr_create_batch(displays: Sequence[int], meshes: Sequence[int]) -> int:
+    n = len(displays)
+    dp = (C.c_void_p * n)(*displays)
+    mp = (C.c_void_p * len(meshes))(*meshes)
+    h = C.c_void_p()
+    _check(lib().lfdpr_create_batch(dp, mp, n, C.byref(h)))
+    return h.value
+
+
+def lfdpr_destroy_batch(batch: int):
+    _check(lib().lfdpr_destroy_batch(batch))
+
+
+def lfdpr_batch_get_config(batch: int) -> BatchConfig:
+    c = BatchConfig()
+    _check(lib().lfdpr_batch_get_config(batch, C.byref(c)))
+    return c
+
+
+def lfdpr_batch_set_config(batch: int, branches: int, splat_blocks_per_sm: int, splat_slots: int):
+    c = BatchConfig(branches, splat_blocks_per_sm, splat_slots)
+    _check(lib().lfdpr_batch_set_config(batch, C.byref(c)))
+
+
+def lfdpr_render_batch(batch: int, models: np.ndarray, stream=None):
+    m = np.ascontiguousarray(models, np.float32).reshape(-1, 16)
+    _check(lib().lfdpr_render_batch(batch, _ptr(m), _stream(stream)))
+
+
+def lfdpr_batch_autotune(batch: int, models: np.ndarray, reps: int = 3, stream=None):
+    m = np.ascontiguousarray(models, np.float32).reshape(-1, 16)
+    c = BatchConfig()
+    ms = C.c_float()
+    _check(lib().lfdpr_batch_autotune(batch, _ptr(m), reps, _stream(stream), C.byref(c), C.byref(ms)))
+    return c, ms.value
+
+
+def lfdpr_batch_panel(batch: int, i: int) -> int:
+    h = C.c_void_p()
+    _check(lib().lfdpr_batch_panel(batch, i, C.byref(h)))
+    return h.value
+
+
 # ---------------------------------------------------------------------------
 # Owning wrappers (destroy on close)
 # ---------------------------------------------------------------------------
@@ -278,6 +374,84 @@ class Renderer:
             self.close()
         except Exception:
             pass
+
+
+class TextureSet:
+    """Textures uploaded once and shared by meshes."""
+
+    def __init__(self, textures: Sequence[np.ndarray], stream=None):
+        self.n_tex = len(textures)
+        self.handle = lfdpr_create_texture_set(textures, stream)
+
+    def close(self):
+        if self.handle is not None:
+            lfdpr_destroy_texture_set(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Several scenes, each with its own display and a mesh on a shared
+    texture set, rendered and interleaved by one replayed CUDA graph."""
+
+    def __init__(self, displays, scenes, tex_set: TextureSet, max_points: Sequence[int] = None,
+                 stream=None):
+        self.displays = list(displays)
+        self.disps, self.meshes = [], []
+        self.batch = None
+        try:
+            for k, (d, sc) in enumerate(zip(displays, scenes)):
+                mp = max_points[k] if max_points is not None else 0
+                self.disps.append(lfdpr_create_display(desc_of(d, mp)))
+                self.meshes.append(lfdpr_upload_mesh_textured(self.disps[-1], sc.xyz, sc.uv, sc.idx,
+                                                              sc.tri_tex, tex_set.handle, stream))
+            self.batch = lfdpr_create_batch(self.disps, self.meshes)
+        except Exception:
+            self.close()
+            raise
+
+    def render(self, models: np.ndarray, stream=None):
+        lfdpr_render_batch(self.batch, models, stream)
+
+    def autotune(self, models: np.ndarray, reps: int = 3, stream=None):
+        return lfdpr_batch_autotune(self.batch, models, reps, stream)
+
+    def config(self) -> BatchConfig:
+        return lfdpr_batch_get_config(self.batch)
+
+    def set_config(self, branches: int, splat_blocks_per_sm: int, splat_slots: int):
+        lfdpr_batch_set_config(self.batch, branches, splat_blocks_per_sm, splat_slots)
+
+    def panel(self, i: int) -> int:
+        return lfdpr_batch_panel(self.batch, i)
+
+    def stats(self, i: int, stream=None) -> Stats:
+        return lfdpr_frame_stats(self.disps[i], stream)
+
+    def buffers(self, i: int) -> Buffers:
+        return lfdpr_get_buffers(self.disps[i], self.meshes[i])
+
+    def close(self):
+        if self.batch is not None:
+            lfdpr_destroy_batch(self.batch)
+            self.batch = None
+        for m in self.meshes:
+            lfdpr_destroy_mesh(m)
+        self.meshes = []
+        for d in self.disps:
+            lfdpr_destroy_display(d)
+        self.disps = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class _DeviceArray:

@@ -277,27 +277,26 @@ def _random_rotation(rng) -> np.ndarray:
                      [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
 
 
-def scene_paper(n_instances: int = 200, res: int = 50, n_textures: int = 64,
-                max_tex: int = 4096, min_tex: int = 64, seed: int = 3,
-                r_max: float = 0.2, r_decades: float = 1.5,
-                extent=(0.75, 1.05, 0.9)) -> Scene:
-    """Paper-shaped scene: n_instances displaced parametric meshes of
-    2*res^2 triangles each (200 x 5,000 = 10^6 by default). Instance radii are
-    log-uniform over r_decades decades, so triangle areas are log-uniform over
-    2*r_decades decades. Textures run from min_tex^2 to max_tex^2 (powers of
-    two, cycled), assigned per instance, so texel density per triangle varies
-    by about three orders of magnitude. With the 48-view display the default
-    radius gives about 2.7 million points per frame, the density of the
-    paper's sponza and gallery frames (2.29 and 2.60 million points from about
-    a million triangles, Table 1)."""
-    rng = np.random.default_rng(seed)
+def textures_paper(n_textures: int = 64, max_tex: int = 4096, min_tex: int = 64,
+                   seed: int = 3) -> List[np.ndarray]:
+    """The paper-shaped scene's textures: value noise from min_tex^2 to
+    max_tex^2 (powers of two, cycled)."""
     sizes = []
     s = min_tex
     while s <= max_tex:
         sizes.append(s)
         s *= 2
-    textures = [value_noise_texture(sizes[k % len(sizes)], sizes[k % len(sizes)],
-                                    seed * 1000 + k) for k in range(n_textures)]
+    return [value_noise_texture(sizes[k % len(sizes)], sizes[k % len(sizes)], seed * 1000 + k)
+            for k in range(n_textures)]
+
+
+def geometry_paper(n_instances: int = 200, res: int = 50, n_textures: int = 64, seed: int = 3,
+                   r_max: float = 0.2, r_decades: float = 1.5, extent=(0.75, 1.05, 0.9)) -> Scene:
+    """The paper-shaped scene's meshes (no textures; texture ids < n_textures):
+    n_instances displaced parametric meshes of 2*res^2 triangles each with
+    log-uniform radii over r_decades decades, random rotations and positions
+    within +-extent, UV repeats of 1, 2 or 4."""
+    rng = np.random.default_rng(seed)
     xyz, uv, idx, ttex = [], [], [], []
     base = 0
     for k in range(n_instances):
@@ -315,4 +314,49 @@ def scene_paper(n_instances: int = 200, res: int = 50, n_textures: int = 64,
     return Scene(xyz=np.concatenate(xyz).astype(np.float32),
                  uv=np.concatenate(uv).astype(np.float32),
                  idx=np.concatenate(idx).astype(np.uint32),
-                 tri_tex=np.concatenate(ttex), textures=textures)
+                 tri_tex=np.concatenate(ttex), textures=[])
+
+
+def scene_paper(n_instances: int = 200, res: int = 50, n_textures: int = 64,
+                max_tex: int = 4096, min_tex: int = 64, seed: int = 3,
+                r_max: float = 0.2, r_decades: float = 1.5,
+                extent=(0.75, 1.05, 0.9)) -> Scene:
+    """Paper-shaped scene: n_instances displaced parametric meshes of
+    2*res^2 triangles each (200 x 5,000 = 10^6 by default). Instance radii are
+    log-uniform over r_decades decades, so triangle areas are log-uniform over
+    2*r_decades decades. Textures run from min_tex^2 to max_tex^2 (powers of
+    two, cycled), assigned per instance, so texel density per triangle varies
+    by about three orders of magnitude. With the 48-view display the default
+    radius gives about 2.7 million points per frame, the density of the
+    paper's sponza and gallery frames (2.29 and 2.60 million points from about
+    a million triangles, Table 1)."""
+    textures = textures_paper(n_textures, max_tex, min_tex, seed)
+    sc = geometry_paper(n_instances, res, n_textures, seed, r_max, r_decades, extent)
+    sc.textures = textures
+    return sc
+
+
+def batch_paper(n_scenes: int = 32, seed: int = 11, tris_range=(5.0e4, 2.0e6), res: int = 50,
+                n_textures: int = 64):
+    """Batched multi-scene workload: n_scenes paper-shaped scenes whose
+    triangle counts are log-uniform over tris_range (whole instances of
+    2*res^2 triangles), each on its own display: 24, 48 or 96 views over a
+    40 degree cone at 420x560 or 640x360 (square pixels), 2560x1600 panel,
+    slant 0.2. All scenes index one texture set of n_textures textures
+    (textures_paper). Returns (displays, scenes without textures)."""
+    rng = np.random.default_rng(seed)
+    displays, scenes = [], []
+    lo, hi = math.log(tris_range[0]), math.log(tris_range[1])
+    per_inst = 2 * res * res
+    for k in range(n_scenes):
+        tris = math.exp(rng.uniform(lo, hi))
+        n_inst = max(1, int(round(tris / per_inst)))
+        views = int(rng.choice([24, 48, 96]))
+        w, h = [(420, 560), (640, 360)][int(rng.integers(0, 2))]
+        displays.append(Display(n_views=views, view_w=w, view_h=h, cone_deg=40.0, view_dist=4.0,
+                                focal_w=2.4 * w / h, focal_h=2.4, near_z=0.1, far_z=100.0,
+                                bias_h=1.0, bias_v=1.0, panel_w=2560, panel_h=1600,
+                                lens_pitch_px=8.0, slant=0.2))
+        scenes.append(geometry_paper(n_instances=n_inst, res=res, n_textures=n_textures,
+                                     seed=seed * 1000 + k))
+    return displays, scenes
