@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--config", choices=["paper", "angular", "tiny", "batch"], default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
+    p.add_argument("--batch-tris", type=str, default="50000,2000000",
+                   help="--config batch: triangle-count range per scene (log-uniform)")
     return p.parse_args()
 
 
@@ -413,7 +416,8 @@ def run_batch(args):
     if world > 1:
         dist.barrier()
     lfdpr.lib()
-    ds, scs = S.batch_paper()
+    lo, hi = (float(x) for x in args.batch_tris.split(","))
+    ds, scs = S.batch_paper(n_scenes=args.batch_scenes, tris_range=(lo, hi))
     n = len(ds)
     stream = torch.cuda.Stream()
     ts = lfdpr.TextureSet(S.textures_paper(), stream)
@@ -425,6 +429,7 @@ def run_batch(args):
         return np.stack([S.model_matrix(base + f + 7 * k) for k in range(n)]).astype(np.float32)
 
     cfg, tuned_ms = B.autotune(models(0), reps=2, stream=stream)
+    table = B.autotune_table()
     for w in range(args.warmup):
         B.render(models(1 + w), stream)
     for i in range(n):
@@ -494,7 +499,8 @@ def run_batch(args):
                 "points_per_batch": points, "points_per_s": points * args.steps * world / (total_ms / 1000.0),
                 "sequential_frames_per_s": seq_rate, "speedup_vs_sequential": value / world / seq_rate,
                 "autotuned": {"branches": cfg.branches, "splat_blocks_per_sm": cfg.splat_blocks_per_sm,
-                              "splat_slots": cfg.splat_slots, "ms_per_batch_while_tuning": tuned_ms},
+                              "splat_slots": cfg.splat_slots, "ms_per_batch_while_tuning": tuned_ms,
+                              "candidates_ms": {"%d/%d/%d" % t[:3]: round(t[3], 3) for t in table}},
                 "gpu_launches": int(args.steps * (7 * n + 1)),
                 "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -354,6 +354,12 @@ lfdpr_status lfdpr_render_batch(lfdpr_batch *batch, const float *models, void *s
 lfdpr_status lfdpr_batch_autotune(lfdpr_batch *batch, const float *models, int32_t reps, void *stream,
                                   lfdpr_batch_config *best, float *best_ms);
 
+/* The last autotune's candidates and their mean ms per batch, in the order
+ * tried: the first min(*n, capacity) entries are written (either array may be
+ * NULL); *n is the number of candidates (0 before any autotune). */
+lfdpr_status lfdpr_batch_autotune_table(const lfdpr_batch *batch, lfdpr_batch_config *cfgs, float *ms,
+                                        int32_t capacity, int32_t *n);
+
 /* Device panel u8 [panel_h][panel_w][4] of scene i after lfdpr_render_batch
  * (borrowed; valid until the batch or its display is destroyed). */
 lfdpr_status lfdpr_batch_panel(const lfdpr_batch *batch, int32_t i, const uint8_t **panel);

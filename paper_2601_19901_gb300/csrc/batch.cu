@@ -34,6 +34,8 @@ struct lfdpr_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool stale = true;               // capture again before the next replay
+    std::vector<lfdpr_batch_config> tried;   // the last autotune's candidates
+    std::vector<float> tried_ms;             // and their mean ms per batch
 };
 
 namespace {
@@ -289,6 +291,8 @@ lfdpr_status lfdpr_batch_autotune(lfdpr_batch* b, const float* models, int32_t r
     lfdpr_batch_config best = b->cfg;
     float best_ms = INFINITY;
     lfdpr_status st = LFDPR_OK;
+    b->tried.clear();
+    b->tried_ms.clear();
     for (int k : ks)
         for (int g : gs)
             for (int sl : ss) {
@@ -307,6 +311,8 @@ lfdpr_status lfdpr_batch_autotune(lfdpr_batch* b, const float* models, int32_t r
                     break;
                 }
                 ms /= float(reps);
+                b->tried.push_back(c);
+                b->tried_ms.push_back(ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = c;
@@ -319,6 +325,18 @@ lfdpr_status lfdpr_batch_autotune(lfdpr_batch* b, const float* models, int32_t r
     if (st != LFDPR_OK) return st;
     if (best_out) *best_out = best;
     if (best_ms_out) *best_ms_out = best_ms;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_batch_autotune_table(const lfdpr_batch* batch, lfdpr_batch_config* cfgs, float* ms,
+                                        int32_t capacity, int32_t* n) {
+    g_err[0] = 0;
+    if (!batch || !n) return fail(LFDPR_EINVAL, "batch_autotune_table: null argument");
+    *n = int32_t(batch->tried.size());
+    for (int32_t k = 0; k < *n && k < capacity; k++) {
+        if (cfgs) cfgs[k] = batch->tried[k];
+        if (ms) ms[k] = batch->tried_ms[k];
+    }
     return LFDPR_OK;
 }
 

@@ -31,7 +31,8 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc",
            "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
-           "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel"]
+           "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
+           "lfdpr_batch_autotune_table"]
 
 
 class LfdprError(RuntimeError):
@@ -112,6 +113,7 @@ def lib() -> C.CDLL:
         L.lfdpr_batch_autotune.argtypes = [P, P, C.c_int32, P, C.POINTER(BatchConfig),
                                            C.POINTER(C.c_float)]
         L.lfdpr_batch_panel.argtypes = [P, C.c_int32, C.POINTER(C.c_void_p)]
+        L.lfdpr_batch_autotune_table.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
         for name in EXPORTS:
             fn = getattr(L, name)
             if name == "lfdpr_last_error":
@@ -313,6 +315,16 @@ def lfdpr_batch_autotune(batch: int, models: np.ndarray, reps: int = 3, stream=N
     return c, ms.value
 
 
+def lfdpr_batch_autotune_table(batch: int):
+    """[(branches, splat_blocks_per_sm, splat_slots, ms), ...] of the last autotune."""
+    n = C.c_int32()
+    _check(lib().lfdpr_batch_autotune_table(batch, None, None, 0, C.byref(n)))
+    cfgs = (BatchConfig * max(n.value, 1))()
+    ms = (C.c_float * max(n.value, 1))()
+    _check(lib().lfdpr_batch_autotune_table(batch, cfgs, ms, n.value, C.byref(n)))
+    return [cfgs[k].as_tuple() + (ms[k],) for k in range(n.value)]
+
+
 def lfdpr_batch_panel(batch: int, i: int) -> int:
     h = C.c_void_p()
     _check(lib().lfdpr_batch_panel(batch, i, C.byref(h)))
@@ -426,6 +438,9 @@ class Batch:
 
     def set_config(self, branches: int, splat_blocks_per_sm: int, splat_slots: int):
         lfdpr_batch_set_config(self.batch, branches, splat_blocks_per_sm, splat_slots)
+
+    def autotune_table(self):
+        return lfdpr_batch_autotune_table(self.batch)
 
     def panel(self, i: int) -> int:
         return lfdpr_batch_panel(self.batch, i)

@@ -107,6 +107,10 @@ def test_autotune_keeps_a_candidate_and_the_results(batch):
     cfg, ms = B.autotune(_models(2), reps=1)
     assert ms > 0.0 and 1 <= cfg.branches <= 3 and cfg.splat_slots in (1, 2, 3, 4, 6, 8)
     assert B.config().as_tuple() == cfg.as_tuple()
+    table = B.autotune_table()
+    assert len(table) >= 2 and all(t[3] > 0.0 for t in table)
+    assert min(t[3] for t in table) == pytest.approx(ms)
+    assert cfg.as_tuple() in [t[:3] for t in table]
     _check_all(ds, scs, B, 5)
 
 
