@@ -1,0 +1,83 @@
+/*
+ * lfdpr_recon.h — learned angular reconstruction on top of liblfdpr.so.
+ *
+ * A display frame can be rendered for a quarter of its views and the rest
+ * predicted: LFDPR (lfdpr.h) renders n views (a display with n_views = n over
+ * the same cone puts its eyes midway between output views 4j+1 and 4j+2 of
+ * the 4n-view display), and a small U-Net predicts the 4n views of the full
+ * display after angular supersampling and reconstruction (Sec. 4's 2x
+ * angular rate with the [1/4, 1/2, 1/4] tent). The full render is its
+ * fallback and the judge of its error.
+ *
+ * Network (fixed architecture, weights supplied by the caller): input = the n
+ * views' RGB / 255 as 3n channels (zero padded to 48), views padded with zeros
+ * to multiples of 8 pixels; four levels of two 3x3 convolutions + bias + ReLU
+ * (channels 32, 64, 128, 256), 2x2 average pooling down, nearest 2x
+ * upsampling concatenated with the level's features (upsampled first) up;
+ * then a 1x1 convolution to 3 * 4n channels added to the linear angular
+ * interpolation of the input views (input j at output index 4j + 3/2,
+ * clamped at the ends), clamped to [0, 1], times 255, rounded half to even.
+ * Activations and 3x3 weights are bf16 with fp32 accumulation (tensor
+ * cores); the 1x1 layer runs in fp32 from bf16 weights.
+ *
+ * 3x3 layers in order, (input channels, output channels):
+ *   (48,32) (32,32) | (32,64) (64,64) | (64,128) (128,128) | (128,256) (256,256)
+ *   | (384,128) (128,128) | (192,64) (64,64) | (96,32) (32,32)
+ * Weight blob (bf16 as uint16): each 3x3 layer's [out][3][3][in] in order,
+ * then the 1x1 layer's [3 * 4n][32]. Bias blob (f32): each layer's [out] in
+ * the same order, then the 1x1 layer's [3 * 4n].
+ *
+ * Conventions as in lfdpr.h (status codes, lfdpr_last_error, streams).
+ */
+#ifndef LFDPR_RECON_H
+#define LFDPR_RECON_H
+
+#include "lfdpr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lfdpr_recon lfdpr_recon;
+
+/* Number of weights and biases for n input views (the blob sizes above). */
+int64_t lfdpr_recon_weight_count(int32_t in_views);
+int64_t lfdpr_recon_bias_count(int32_t in_views);
+
+/*
+ * lfdpr_create_recon: a network for in_views (1..16) input views of
+ * view_w x view_h pixels (8..4096 a side); weights_bf16 and biases (host)
+ * are copied; the activation buffers are allocated once here.
+ * Errors: EINVAL (counts not as above), ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views, const uint16_t *weights_bf16,
+                                int64_t n_weights, const float *biases, int64_t n_biases, lfdpr_recon **out);
+lfdpr_status lfdpr_destroy_recon(lfdpr_recon *recon);
+
+/*
+ * lfdpr_recon_run: predict the views of display `dst` (4 in_views rendered
+ * views, no angular supersampling, same view size) from the rendered views of
+ * display `src` (in_views rendered views), asynchronously on `stream`. The
+ * result is in dst's view buffer (lfdpr_get_buffers), so lfdpr_interleave(dst,
+ * ...) builds its panel. One network runs one forward pass at a time.
+ */
+lfdpr_status lfdpr_recon_run(lfdpr_recon *recon, const lfdpr_display *src, lfdpr_display *dst, void *stream);
+
+/* The same on raw device buffers: in_views u8 [in_views][H][W][4],
+ * out_views u8 [4 in_views][H][W][4]. */
+lfdpr_status lfdpr_recon_forward(lfdpr_recon *recon, const uint8_t *in_views, uint8_t *out_views, void *stream);
+
+/*
+ * lfdpr_conv3x3_bf16: one 3x3 layer of the network (test hook): in bf16
+ * [H][W][cin], wgt bf16 [cout][3][3][cin], bias f32 [cout], out bf16
+ * [H][W][cout], zero padding 1, + bias, ReLU if relu; cin % 16 == 0,
+ * cout % 32 == 0; device buffers, 16-byte aligned.
+ */
+lfdpr_status lfdpr_conv3x3_bf16(const void *in, int32_t H, int32_t W, int32_t cin, const void *wgt,
+                                const float *bias, void *out, int32_t cout, int32_t relu, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFDPR_RECON_H */

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblfdpr.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["runtime.cu", "sample.cu", "splat.cu", "interleave.cu", "mip.cu", "probe.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["runtime.cu", "sample.cu", "splat.cu", "interleave.cu", "mip.cu", "probe.cu", "noalloc.cu", "batch.cu", "recon.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]

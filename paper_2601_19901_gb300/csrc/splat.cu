@@ -14,15 +14,6 @@
 namespace lfdpr {
 namespace {
 
-__device__ __forceinline__ void cell_corner(const float4& q0, const float4& q1, const float4& q2,
-                                            const float4& q3, int ia, int jb, float* o) {
-    const float cu = float(ia) * q0.w + q2.w;
-    const float cv = float(jb) * q1.w + q3.w;
-    o[0] = fmaf(cu, q1.x, fmaf(cv, q2.x, q0.x));
-    o[1] = fmaf(cu, q1.y, fmaf(cv, q2.y, q0.y));
-    o[2] = fmaf(cu, q1.z, fmaf(cv, q2.z, q0.z));
-}
-
 // One half-warp (16 lanes) per point of the work list, each lane taking up to
 // S views of the point (views g + 16 s + lane of a group g of 16 S views, S
 // chosen so that one group holds every rendered view where it can); a warp

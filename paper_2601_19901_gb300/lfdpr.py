@@ -32,7 +32,9 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
-           "lfdpr_batch_autotune_table"]
+           "lfdpr_batch_autotune_table",
+           "lfdpr_recon_weight_count", "lfdpr_recon_bias_count", "lfdpr_create_recon",
+           "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_conv3x3_bf16"]
 
 
 class LfdprError(RuntimeError):
@@ -114,6 +116,14 @@ def lib() -> C.CDLL:
                                            C.POINTER(C.c_float)]
         L.lfdpr_batch_panel.argtypes = [P, C.c_int32, C.POINTER(C.c_void_p)]
         L.lfdpr_batch_autotune_table.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
+        L.lfdpr_recon_weight_count.argtypes = [C.c_int32]
+        L.lfdpr_recon_bias_count.argtypes = [C.c_int32]
+        L.lfdpr_create_recon.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, C.c_int64, P, C.c_int64,
+                                         C.POINTER(C.c_void_p)]
+        L.lfdpr_destroy_recon.argtypes = [P]
+        L.lfdpr_recon_run.argtypes = [P, P, P, P]
+        L.lfdpr_recon_forward.argtypes = [P, P, P, P]
+        L.lfdpr_conv3x3_bf16.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int32, C.c_int32, P]
         for name in EXPORTS:
             fn = getattr(L, name)
             if name == "lfdpr_last_error":
@@ -122,6 +132,8 @@ def lib() -> C.CDLL:
             elif name == "lfdpr_version":
                 fn.restype = C.c_int32
                 fn.argtypes = []
+            elif name in ("lfdpr_recon_weight_count", "lfdpr_recon_bias_count"):
+                fn.restype = C.c_int64
             else:
                 fn.restype = S
         _lib = L
@@ -331,6 +343,41 @@ def lfdpr_batch_panel(batch: int, i: int) -> int:
     return h.value
 
 
+def lfdpr_recon_weight_count(in_views: int) -> int:
+    return int(lib().lfdpr_recon_weight_count(in_views))
+
+
+def lfdpr_recon_bias_count(in_views: int) -> int:
+    return int(lib().lfdpr_recon_bias_count(in_views))
+
+
+def lfdpr_create_recon(view_w: int, view_h: int, in_views: int, weights_bf16: np.ndarray,
+                       biases: np.ndarray) -> int:
+    w = np.ascontiguousarray(weights_bf16, np.uint16).ravel()
+    b = np.ascontiguousarray(biases, np.float32).ravel()
+    h = C.c_void_p()
+    _check(lib().lfdpr_create_recon(view_w, view_h, in_views, _ptr(w), w.size, _ptr(b), b.size, C.byref(h)))
+    return h.value
+
+
+def lfdpr_destroy_recon(recon: int):
+    _check(lib().lfdpr_destroy_recon(recon))
+
+
+def lfdpr_recon_run(recon: int, src_disp: int, dst_disp: int, stream=None):
+    _check(lib().lfdpr_recon_run(recon, src_disp, dst_disp, _stream(stream)))
+
+
+def lfdpr_recon_forward(recon: int, in_ptr: int, out_ptr: int, stream=None):
+    _check(lib().lfdpr_recon_forward(recon, C.c_void_p(in_ptr), C.c_void_p(out_ptr), _stream(stream)))
+
+
+def lfdpr_conv3x3_bf16(in_ptr: int, H: int, W: int, cin: int, w_ptr: int, b_ptr: int, out_ptr: int,
+                       cout: int, relu: bool = True, stream=None):
+    _check(lib().lfdpr_conv3x3_bf16(C.c_void_p(in_ptr), H, W, cin, C.c_void_p(w_ptr), C.c_void_p(b_ptr),
+                                    C.c_void_p(out_ptr), cout, int(relu), _stream(stream)))
+
+
 # ---------------------------------------------------------------------------
 # Owning wrappers (destroy on close)
 # ---------------------------------------------------------------------------
@@ -461,6 +508,31 @@ class Batch:
         for d in self.disps:
             lfdpr_destroy_display(d)
         self.disps = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Recon:
+    """The learned angular reconstruction network (include/lfdpr_recon.h)."""
+
+    def __init__(self, view_w: int, view_h: int, in_views: int, weights_bf16: np.ndarray, biases: np.ndarray):
+        self.in_views = in_views
+        self.handle = lfdpr_create_recon(view_w, view_h, in_views, weights_bf16, biases)
+
+    def run(self, src_disp: int, dst_disp: int, stream=None):
+        lfdpr_recon_run(self.handle, src_disp, dst_disp, stream)
+
+    def forward(self, in_ptr: int, out_ptr: int, stream=None):
+        lfdpr_recon_forward(self.handle, in_ptr, out_ptr, stream)
+
+    def close(self):
+        if self.handle is not None:
+            lfdpr_destroy_recon(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self

@@ -1,6 +1,6 @@
 """The C ABI without a GPU: the library builds for sm_103a, loads, exports
-every entry point include/lfdpr.h declares, and rejects invalid descriptors
-on the host before touching a device."""
+every entry point include/*.h declares, and rejects invalid descriptors on
+the host before touching a device."""
 import os
 import re
 from dataclasses import replace
@@ -19,9 +19,13 @@ def L():
 
 
 def declared_entry_points():
-    src = open(os.path.join(ROOT, "include", "lfdpr.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lfdpr_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(lfdpr_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_binding_names():
