@@ -8,6 +8,12 @@ steps and each step is timed with CUDA events on the rendering stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--config learned times the learned quarter-view path (12 views rendered, the
+U-Net's tensor-core kernels predict the 48 reconstructed views, interleave)
+against the plain full render (96 views at 2x angular rate, tent, crosstalk,
+interleave) on the paper-shaped scene, with PSNR and SSIM of the prediction
+against the full render's reconstruction per frame.
+
 --config batch times batched multi-scene frames instead: 32 paper-shaped
 scenes of 50k-2M triangles, each on its own display (24, 48 or 96 views at
 420x560 or 640x360, 2560x1600 panel), one texture set, rendered and
@@ -49,7 +55,7 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["paper", "angular", "tiny", "batch"], default="paper")
+    p.add_argument("--config", choices=["paper", "angular", "tiny", "batch", "learned"], default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
@@ -157,9 +163,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.config == "batch":
+    if args.config in ("batch", "learned"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single frames "
-                          "(--config paper); a batch is those frames for 32 scenes"}), flush=True)
+                          "(--config paper)"}), flush=True)
         return
     import oracle as O
     from paper_2601_19901_gb300 import scenes as S
@@ -510,12 +516,107 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    import torch
+    from dataclasses import replace
+    from paper_2601_19901_gb300 import build as B_, lfdpr, recon_net as RN, scenes as S
+
+    B_.build()
+    lfdpr.lib()
+    w, b, nin = RN.load_weights()
+    sc = S.scene_paper()
+    d_in = replace(S.display_paper(), n_views=nin)
+    d_full = S.display_angular_ss()
+    d_out = replace(S.display_paper(), n_views=4 * nin, crosstalk=d_full.crosstalk)
+    H, W = d_in.view_h, d_in.view_w
+    stream = torch.cuda.Stream()
+    ts = lfdpr.TextureSet(sc.textures, stream)
+    dis = [lfdpr.lfdpr_create_display(lfdpr.desc_of(d)) for d in (d_in, d_full, d_out)]
+    me = [lfdpr.lfdpr_upload_mesh_textured(dis[k], sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle, stream)
+          for k in range(2)]
+    R = lfdpr.Recon(W, H, nin, w, b)
+    panel = torch.empty((d_out.panel_h, d_out.panel_w, 4), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def learned(f):
+        lfdpr.lfdpr_render_frame(dis[0], me[0], S.model_matrix(f), stream)
+        R.run(dis[0], dis[2], stream)
+        lfdpr.lfdpr_interleave(dis[2], panel.data_ptr(), stream)
+
+    def plain(f):
+        lfdpr.lfdpr_render_frame(dis[1], me[1], S.model_matrix(f), stream)
+        lfdpr.lfdpr_interleave(dis[1], panel.data_ptr(), stream)
+
+    def timed(fn, first):
+        for k in range(args.warmup):
+            fn(first + k)
+        ms = []
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(first + args.warmup + k)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    # the network alone
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    learned(0)
+    e0.record(stream)
+    for _ in range(10):
+        R.run(dis[0], dis[2], stream)
+    e1.record(stream)
+    e1.synchronize()
+    net_ms = e0.elapsed_time(e1) / 10
+    ms_learned = timed(learned, 0)
+    ms_plain = timed(plain, 0)
+    # quality over the 120-frame orbit (every 8th frame)
+    q = []
+    for f in range(0, 120, 8):
+        learned(f)
+        plain(f)
+        torch.cuda.synchronize()
+        bf = lfdpr.lfdpr_get_buffers(dis[1], me[1])
+        judge = RN.tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
+        bo = lfdpr.lfdpr_get_buffers(dis[2], me[0])
+        pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
+        q.append((RN.psnr(pred, judge), RN.ssim(pred, judge)))
+    flops = 0
+    hp, wp = RN.padded(H, W)
+    for ci, co, lev in RN.LAYERS:
+        flops += 2 * 9 * ci * co * (hp >> lev) * (wp >> lev)
+    line = {"metric": "learned quarter-view path frames/s at PSNR vs the plain full render",
+            "value": 1000.0 / ms_learned, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (network), f32 (render)", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("48 views", "%d views rendered, 48 predicted" % nin),
+                       "l2": "flushed (512 MiB write) between timed steps"},
+            "plain_full_render_frames_per_s": 1000.0 / ms_plain,
+            "speedup_vs_plain": ms_plain / ms_learned,
+            "network_ms": net_ms, "network_tflops": flops / (net_ms / 1000.0) / 1e12,
+            "psnr_db": {"mean": statistics.mean(p for p, _ in q), "min": min(p for p, _ in q)},
+            "ssim": {"mean": statistics.mean(s_ for _, s_ in q), "min": min(s_ for _, s_ in q)},
+            "quality_frames": len(q)}
+    print(json.dumps(line), flush=True)
+    R.close()
+    for m_ in me:
+        lfdpr.lfdpr_destroy_mesh(m_)
+    for d_ in dis:
+        lfdpr.lfdpr_destroy_display(d_)
+    ts.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batch":
         run_batch(args)
+    elif args.config == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

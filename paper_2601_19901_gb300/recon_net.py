@@ -293,6 +293,50 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 12, seed: int = 0, 
     return {"setup_s": setup_s, "train_s": train_s, "iters": iters}
 
 
+def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=range(0, 120, 15), stream=None):
+    """PSNR and SSIM per frame of the learned path against the plain full
+    render on the paper-shaped scene (orbit frames, 3 degrees each): the
+    library renders the n-view display and the 2x-angular full display, its
+    kernels run the network into the 4n-view display, and the prediction is
+    compared with the full render's tent reconstruction."""
+    torch = _torch()
+    from . import lfdpr, scenes as S
+    sc = S.scene_paper()
+    d_in = replace(S.display_paper(), n_views=nin)
+    d_full = S.display_angular_ss()
+    d_out = replace(S.display_paper(), n_views=4 * nin, crosstalk=d_full.crosstalk)
+    H, W = d_in.view_h, d_in.view_w
+    ts = lfdpr.TextureSet(sc.textures)
+    disps = [lfdpr.lfdpr_create_display(lfdpr.desc_of(d)) for d in (d_in, d_full, d_out)]
+    meshes = [lfdpr.lfdpr_upload_mesh_textured(disps[k], sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle)
+              for k in range(2)]
+    res = []
+    with lfdpr.Recon(W, H, nin, weights, biases) as R:
+        for f in frames:
+            m = S.model_matrix(f)
+            lfdpr.lfdpr_render_frame(disps[0], meshes[0], m, stream)
+            lfdpr.lfdpr_render_frame(disps[1], meshes[1], m, stream)
+            R.run(disps[0], disps[2], stream)
+            bf = lfdpr.lfdpr_get_buffers(disps[1], meshes[1])
+            judge = tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
+            bo = lfdpr.lfdpr_get_buffers(disps[2], meshes[0])
+            pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
+            bi = lfdpr.lfdpr_get_buffers(disps[0], meshes[0])
+            inp = lfdpr.device_view(bi.views, (nin, H, W, 4), np.uint8)
+            x = network_input(inp, nin, *padded(H, W))
+            base = torch.einsum("oc,bchw->bohw", torch.from_numpy(base_matrix(nin)).to(x.device), x)
+            base = torch.round(base.clamp(0, 1) * 255.0)[0, :, :H, :W].reshape(4 * nin, 3, H, W)
+            base = base.permute(0, 2, 3, 1).to(torch.uint8)
+            res.append({"frame": int(f), "psnr": psnr(pred, judge), "ssim": ssim(pred, judge),
+                        "psnr_interp": psnr(base, judge)})
+    for m_ in meshes:
+        lfdpr.lfdpr_destroy_mesh(m_)
+    for d_ in disps:
+        lfdpr.lfdpr_destroy_display(d_)
+    ts.close()
+    return res
+
+
 def load_weights(path: str = None):
     """(weights, biases, in_views) of the shipped (or given) weights file."""
     path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "recon_weights.npz")
@@ -308,5 +352,12 @@ if __name__ == "__main__":
     p.add_argument("--scenes", type=int, default=12)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lr", type=float, default=1e-3)
+    p.add_argument("--eval", action="store_true", help="evaluate the written weights on the paper-shaped scene")
     a = p.parse_args()
-    print(train(a.out, a.iters, a.scenes, a.seed, a.lr))
+    import torch
+    torch.backends.cudnn.benchmark = True
+    print(train(a.out, a.iters, a.scenes, a.seed, a.lr), flush=True)
+    if a.eval:
+        w, b, nin = load_weights(a.out)
+        for r in evaluate(w, b, nin):
+            print(r, flush=True)
