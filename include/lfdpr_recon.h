@@ -17,8 +17,10 @@
  * then a 1x1 convolution to 3 * 4n channels added to the linear angular
  * interpolation of the input views (input j at output index 4j + 3/2,
  * clamped at the ends), clamped to [0, 1], times 255, rounded half to even.
- * Activations and 3x3 weights are bf16 with fp32 accumulation (tensor
- * cores); the 1x1 layer runs in fp32 from bf16 weights.
+ * Activations and weights are bf16 with fp32 accumulation (tensor cores);
+ * the 1x1 layer and the angular interpolation run as one product over
+ * [features (32), input channels (48)] (the interpolation weights 0, 1/8,
+ * 3/8, 5/8, 7/8, 1 are exact in bf16).
  *
  * 3x3 layers in order, (input channels, output channels):
  *   (48,32) (32,32) | (32,64) (64,64) | (64,128) (128,128) | (128,256) (256,256)
@@ -45,7 +47,7 @@ int64_t lfdpr_recon_weight_count(int32_t in_views);
 int64_t lfdpr_recon_bias_count(int32_t in_views);
 
 /*
- * lfdpr_create_recon: a network for in_views (1..16) input views of
+ * lfdpr_create_recon: a network for in_views (even, 2..16) input views of
  * view_w x view_h pixels (8..4096 a side); weights_bf16 and biases (host)
  * are copied; the activation buffers are allocated once here.
  * Errors: EINVAL (counts not as above), ENOMEM, ECUDA.

@@ -5,8 +5,9 @@
 //   k_conv3x3     3x3 convolution, stride 1, zero padding 1, + bias, ReLU:
 //                 implicit GEMM (pixels x output channels x 9 Cin). A block
 //                 takes 8 rows x 32 pixels x 64 (or 32) output channels; per
-//                 chunk of 16 input channels it stages the 10 x 34 pixel halo
-//                 tile and the 64 x 9 x 16 weights in shared memory, and each warp
+//                 chunk of 16 input channels it stages (cp.async, two stages,
+//                 so copies overlap the MMAs) the 10 x 34 pixel halo tile and
+//                 the 64 x 9 x 16 weights in shared memory, and each warp
 //                 (one row, two m16 tiles) runs ldmatrix + mma.m16n8k16 over
 //                 the 9 taps, reading the tap-shifted pixel rows straight
 //                 from the halo tile.
@@ -16,9 +17,9 @@
 //   k_recon_in    12 rendered views RGBA8 -> the network input (36 channels
 //                 of [0, 1] values, zero padded to 48 channels and to a
 //                 width divisible by 8).
-//   k_recon_out   1x1 convolution of the last features to 144 channels plus
-//                 the fixed angular interpolation of the input views, clamped
-//                 and rounded to the 48 output views RGBA8.
+//   k_recon_out   the 1x1 output layer plus the fixed angular interpolation
+//                 of the input views as one tensor-core GEMM per 16 pixels,
+//                 clamped and rounded to the 48 output views RGBA8.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -51,18 +52,32 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// 16-byte global -> shared copy that bypasses L1 (cp.async); src_bytes 0
+// fills the 16 bytes with zeros without reading src.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
 // in [H][W][Cin], wgt [Cout][9][Cin] (tap = 3 dy + dx), bias [Cout] f32,
 // out [H][W][Cout]; Cin % 16 == 0, Cout % CO == 0 (CO = 32 or 64 output
-// channels per block). Grid (ceil(W/32), ceil(H/8), Cout/CO), 256 threads.
+// channels per block). Grid (ceil(W/32), ceil(H/8), Cout/CO), 256 threads,
+// dynamic shared memory conv_smem_bytes(CO): two stages of (halo tile,
+// weights) so the next chunk's copies run during this chunk's MMAs.
 template <int CO>
 __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ in, int H, int W, int Cin,
                                                  const __nv_bfloat16* __restrict__ wgt,
                                                  const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
                                                  int Cout, int relu) {
     constexpr int HP = kConvTH + 2, WP = kConvTW + 2;
-    __shared__ __align__(16) __nv_bfloat16 s_in[HP * WP * kConvRow];
-    constexpr int NT = CO / 8;   // n8 tiles per warp
-    __shared__ __align__(16) __nv_bfloat16 s_w[CO * 9 * kConvRow];
+    constexpr int NT = CO / 8;                               // n8 tiles per warp
+    constexpr int IN_ELEMS = HP * WP * kConvRow, W_ELEMS = CO * 9 * kConvRow;
+    constexpr int STAGE = IN_ELEMS + W_ELEMS;                // elements per stage
+    extern __shared__ __align__(16) __nv_bfloat16 smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * kConvTW, y0 = blockIdx.y * kConvTH, n0 = blockIdx.z * CO;
     float acc[2][NT][4];
@@ -73,30 +88,41 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
 #pragma unroll
             for (int q = 0; q < 4; q++) acc[m][t][q] = 0.0f;
 
-    const uint32_t s_in_a = uint32_t(__cvta_generic_to_shared(s_in));
-    const uint32_t s_w_a = uint32_t(__cvta_generic_to_shared(s_w));
+    const uint32_t s_base = uint32_t(__cvta_generic_to_shared(smem));
     // ldmatrix row addresses of this lane: A (pixels) and B (output channels)
     const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_k = 8 * (lane >> 4);
     const int b_row = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
 
-    for (int c0 = 0; c0 < Cin; c0 += kConvCK) {
-        // halo tile: HP x WP pixels x 16 channels, two 16-byte parts each
+    // copies of channel chunk c0 into stage st
+    auto stage_copy = [&](int c0, int st) {
+        const uint32_t s_in = s_base + uint32_t(st * STAGE * 2), s_w = s_in + uint32_t(IN_ELEMS * 2);
         for (int idx = tid; idx < HP * WP * 2; idx += 256) {
             const int p = idx >> 1, part = idx & 1;
             const int gy = y0 + p / WP - 1, gx = x0 + p % WP - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                v = *reinterpret_cast<const uint4*>(in + ((size_t)gy * W + gx) * Cin + c0 + 8 * part);
-            *reinterpret_cast<uint4*>(s_in + p * kConvRow + 8 * part) = v;
+            const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const __nv_bfloat16* src = ok ? in + ((size_t)gy * W + gx) * Cin + c0 + 8 * part : in;
+            cp_async16(s_in + uint32_t((p * kConvRow + 8 * part) * 2), src, ok ? 16u : 0u);
         }
-        // weights: CO output channels x 9 taps x 16 channels
         for (int idx = tid; idx < CO * 9 * 2; idx += 256) {
             const int row = idx >> 1, part = idx & 1;   // row = co * 9 + tap
             const int co = row / 9, tap = row - 9 * co;
-            const uint4 v = *reinterpret_cast<const uint4*>(wgt + ((size_t)(n0 + co) * 9 + tap) * Cin + c0 + 8 * part);
-            *reinterpret_cast<uint4*>(s_w + row * kConvRow + 8 * part) = v;
+            cp_async16(s_w + uint32_t((row * kConvRow + 8 * part) * 2),
+                       wgt + ((size_t)(n0 + co) * 9 + tap) * Cin + c0 + 8 * part, 16u);
+        }
+        cp_async_commit();
+    };
+
+    const int n_chunks = Cin / kConvCK;
+    stage_copy(0, 0);
+    for (int ch = 0; ch < n_chunks; ch++) {
+        if (ch + 1 < n_chunks) {
+            stage_copy((ch + 1) * kConvCK, (ch + 1) & 1);
+            cp_async_wait<1>();   // this chunk's group has landed
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const uint32_t s_in_a = s_base + uint32_t((ch & 1) * STAGE * 2), s_w_a = s_in_a + uint32_t(IN_ELEMS * 2);
 #pragma unroll
         for (int tap = 0; tap < 9; tap++) {
             const int dy = tap / 3, dx = tap - 3 * (tap / 3);
@@ -118,7 +144,7 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();   // the stage is refilled two chunks later
     }
     // epilogue: bias, ReLU, bf16 pairs
     const int y = y0 + warp;
@@ -141,6 +167,10 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
                 *reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * W + x) * Cout + co) = __floats2bfloat162_rn(v0, v1);
             }
         }
+}
+
+constexpr size_t conv_smem_bytes(int co) {
+    return size_t(2) * (size_t((kConvTH + 2) * (kConvTW + 2) * kConvRow) + size_t(co * 9 * kConvRow)) * 2;
 }
 
 // out [H/2][W/2][C] = mean of 2x2 blocks of in [H][W][C] (H, W even; C % 8 == 0).
@@ -217,56 +247,76 @@ __global__ void k_recon_in(const uint8_t* __restrict__ views, int nin, int H, in
     }
 }
 
-// Output view k of 4 nin, channel c, at an H x W pixel: w_out [3 nout][32]
-// . d0[pixel] + b_out + the angular interpolation of the input views (input
-// j sits at output index 4 j + 3/2), clamped to [0, 1], times 255, rounded
-// half to even; alpha 255. views_out [nout][H][W][4].
-__global__ void __launch_bounds__(128) k_recon_out(const __nv_bfloat16* __restrict__ d0, const __nv_bfloat16* __restrict__ x0,
-                                                   int nin, int H, int W, int Wp, const float* __restrict__ w_out,
+// The output layer as one tensor-core GEMM per 16 pixels: [d0 (32) | x0 (48)]
+// x [w_out ; angular base] (80 x 3 nout, bf16 in shared memory as
+// [3 nout][kOutK]) + b_out, clamped to [0, 1], times 255, rounded half to
+// even, alpha 255 -> views_out [nout][H][W][4]. The base rows give output
+// view k, channel c the linear angular interpolation of the input views
+// (input j at output index 4 j + 3/2, clamped at the ends); its weights
+// (0, 1/8, 3/8, 5/8, 7/8, 1) are exact in bf16. Each warp stages its 16
+// pixels' RGBA8 words in shared memory and writes them view by view.
+constexpr int kOutK = 80 + 8;   // smem row stride of the output weights (elements)
+__global__ void __launch_bounds__(256) k_recon_out(const __nv_bfloat16* __restrict__ d0,
+                                                   const __nv_bfloat16* __restrict__ x0, int nin, int H, int W,
+                                                   int Hp, int Wp, const __nv_bfloat16* __restrict__ w_out,
                                                    const float* __restrict__ b_out, uint8_t* __restrict__ views_out) {
-    extern __shared__ float s_w[];   // [3 nout][33]: weights then bias
-    const int nout = 4 * nin;
-    for (int i = threadIdx.x; i < 3 * nout * 33; i += blockDim.x) {
-        const int o = i / 33, k = i - 33 * o;
-        s_w[i] = k < 32 ? w_out[o * 32 + k] : b_out[o];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nout = 4 * nin, no3 = 3 * nout, nt = no3 / 8;   // n8 tiles (no3 % 8 == 0: nin even)
+    __nv_bfloat16* s_w = reinterpret_cast<__nv_bfloat16*>(smem_raw);                        // [no3][kOutK]
+    float* s_b = reinterpret_cast<float*>(smem_raw + sizeof(__nv_bfloat16) * no3 * kOutK);  // [no3]
+    uint32_t* s_px = reinterpret_cast<uint32_t*>(s_b + no3);                                // [8 warps][16][nout]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < no3 * 80; i += blockDim.x) {
+        const int o = i / 80, k = i - 80 * o;
+        s_w[o * kOutK + k] = w_out[i];
     }
+    for (int i = tid; i < no3; i += blockDim.x) s_b[i] = b_out[i];
     __syncthreads();
-    const size_t npix = (size_t)H * W;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
-        const int x = int(p % W), y = int(p / W);
-        const size_t q = (size_t)y * Wp + x;
-        float f[32];
+    uint32_t* px = s_px + warp * 16 * nout;
+    const size_t npix = (size_t)H * W, ptot = (size_t)Hp * Wp;
+    const int r0 = lane >> 2, kq = 2 * (lane & 3);
+    for (size_t t0 = ((size_t)blockIdx.x * 8 + warp) * 16; t0 < ptot; t0 += (size_t)gridDim.x * 8 * 16) {
+        // A fragments: rows t0 + r0 and t0 + r0 + 8 (padded pixels), 5 k16 steps over [d0 | x0]
+        uint32_t a[5][4];
 #pragma unroll
-        for (int k = 0; k < 32; k += 8) {
-            const uint4 v = *reinterpret_cast<const uint4*>(d0 + q * 32 + k);
-            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+        for (int ks = 0; ks < 5; ks++)
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const float2 t = __bfloat1622float2(h[e]);
-                f[k + 2 * e] = t.x;
-                f[k + 2 * e + 1] = t.y;
+            for (int q = 0; q < 4; q++) {
+                const size_t p = t0 + r0 + 8 * (q & 1);
+                const int k = 16 * ks + kq + 8 * (q >> 1);
+                const __nv_bfloat16* src = k < 32 ? d0 + p * 32 + k : x0 + p * 48 + (k - 32);
+                a[ks][q] = p < ptot ? *reinterpret_cast<const uint32_t*>(src) : 0u;
+            }
+        for (int i = lane; i < 16 * nout; i += 32) px[i] = 0xff000000u;
+        __syncwarp();
+        for (int t = 0; t < nt; t++) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            const int n = 8 * t + r0;
+#pragma unroll
+            for (int ks = 0; ks < 5; ks++) {
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(s_w + n * kOutK + 16 * ks + kq);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(s_w + n * kOutK + 16 * ks + kq + 8);
+                mma_bf16(acc, a[ks][0], a[ks][1], a[ks][2], a[ks][3], b0, b1);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int o = 8 * t + kq + (q & 1), row = r0 + 8 * (q >> 1);
+                const float v = fminf(fmaxf(acc[q] + s_b[o], 0.0f), 1.0f) * 255.0f;
+                const int kv = o / 3, c = o - 3 * kv;
+                reinterpret_cast<uint8_t*>(px + row * nout + kv)[c] = uint8_t(rintf(v));
             }
         }
-        for (int kv = 0; kv < nout; kv++) {
-            const float pos = (float(kv) - 1.5f) * 0.25f;
-            const int j0 = min(max(int(floorf(pos)), 0), nin - 2 < 0 ? 0 : nin - 2);
-            const float t = nin > 1 ? fminf(fmaxf(pos - float(j0), 0.0f), 1.0f) : 0.0f;
-            const int j1 = nin > 1 ? j0 + 1 : j0;
-            uint32_t px = 0xff000000u;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float* w = s_w + (3 * kv + c) * 33;
-                float acc = w[32];
-#pragma unroll
-                for (int k = 0; k < 32; k++) acc = fmaf(w[k], f[k], acc);
-                const float a0 = __bfloat162float(x0[q * 48 + 3 * j0 + c]);
-                const float a1 = __bfloat162float(x0[q * 48 + 3 * j1 + c]);
-                acc += fmaf(t, a1 - a0, a0);
-                const float v = fminf(fmaxf(acc, 0.0f), 1.0f) * 255.0f;
-                px |= uint32_t(rintf(v)) << (8 * c);
-            }
-            reinterpret_cast<uint32_t*>(views_out)[(size_t)kv * npix + p] = px;
+        __syncwarp();
+        // write the 16 pixels' words, view by view
+        for (int i = lane; i < 16 * nout; i += 32) {
+            const int kv = i >> 4, row = i & 15;
+            const size_t p = t0 + row;
+            if (p >= ptot) continue;
+            const int y = int(p / Wp), x = int(p - (size_t)y * Wp);
+            if (y < H && x < W)
+                reinterpret_cast<uint32_t*>(views_out)[(size_t)kv * npix + (size_t)y * W + x] = px[row * nout + kv];
         }
+        __syncwarp();
     }
 }
 
@@ -275,12 +325,25 @@ __global__ void __launch_bounds__(128) k_recon_out(const __nv_bfloat16* __restri
 cudaError_t launch_conv3x3(const __nv_bfloat16* in, int H, int W, int Cin, const __nv_bfloat16* wgt,
                            const float* bias, __nv_bfloat16* out, int Cout, bool relu, cudaStream_t s) {
     if (H < 1 || W < 1 || Cin < kConvCK || Cin % kConvCK || Cout < 32 || Cout % 32) return cudaErrorInvalidValue;
+    static bool attrs[64] = {};   // opt in to the two-stage shared memory once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attrs[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(conv_smem_bytes(64)));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_conv3x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(conv_smem_bytes(32)));
+        if (e != cudaSuccess) return e;
+        attrs[dev] = true;
+    }
     if (Cout % 64 == 0) {
         const dim3 grid((W + kConvTW - 1) / kConvTW, (H + kConvTH - 1) / kConvTH, Cout / 64);
-        k_conv3x3<64><<<grid, 256, 0, s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
+        k_conv3x3<64><<<grid, 256, conv_smem_bytes(64), s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
     } else {
         const dim3 grid((W + kConvTW - 1) / kConvTW, (H + kConvTH - 1) / kConvTH, Cout / 32);
-        k_conv3x3<32><<<grid, 256, 0, s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
+        k_conv3x3<32><<<grid, 256, conv_smem_bytes(32), s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
     }
     return cudaGetLastError();
 }
@@ -324,8 +387,8 @@ struct lfdpr_recon {
     int W = 0, H = 0, Wp = 0, Hp = 0, nin = 0, nout = 0, sm_count = 1;
     __nv_bfloat16* w = nullptr;   // all 3x3 weights, layer by layer [cout][9][cin]
     float* b = nullptr;           // all 3x3 biases
-    float* w_out = nullptr;       // [3 nout][32]
-    float* b_out = nullptr;       // [3 nout]
+    __nv_bfloat16* w_out = nullptr;   // [3 nout][80]: the 1x1 layer (32) then the angular base (48)
+    float* b_out = nullptr;           // [3 nout]
     int64_t w_off[14] = {}, b_off[14] = {};
     __nv_bfloat16* act = nullptr;  // activation arena
     __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *bb, *u2, *d2a, *d2, *u1, *d1a, *d1, *u0,
@@ -365,7 +428,8 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     lfdpr::g_last_error[0] = 0;
     if (!out || !weights_bf16 || !biases) return fail(LFDPR_EINVAL, "create_recon: null argument");
     *out = nullptr;
-    if (in_views < 1 || in_views > 16) return fail(LFDPR_EINVAL, "create_recon: in_views must be in [1, 16]");
+    if (in_views < 2 || in_views > 16 || (in_views & 1))
+        return fail(LFDPR_EINVAL, "create_recon: in_views must be even, in [2, 16]");
     if (view_w < 8 || view_h < 8 || view_w > 4096 || view_h > 4096)
         return fail(LFDPR_EINVAL, "create_recon: views must be 8..4096 pixels a side");
     if (n_weights != lfdpr_recon_weight_count(in_views) || n_biases != lfdpr_recon_bias_count(in_views))
@@ -402,7 +466,7 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     cudaError_t e;
     const int64_t nw3 = wo, nb3 = bo;
     if ((e = cudaMalloc(&r->w, 2 * nw3)) != cudaSuccess || (e = cudaMalloc(&r->b, 4 * nb3)) != cudaSuccess ||
-        (e = cudaMalloc(&r->w_out, 4 * int64_t(3 * r->nout) * 32)) != cudaSuccess ||
+        (e = cudaMalloc(&r->w_out, 2 * int64_t(3 * r->nout) * 80)) != cudaSuccess ||
         (e = cudaMalloc(&r->b_out, 4 * int64_t(3 * r->nout))) != cudaSuccess ||
         (e = cudaMalloc(&r->act, 2 * total)) != cudaSuccess) {
         free_recon(r);
@@ -411,15 +475,32 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     __nv_bfloat16** bufs[21] = {&r->x0, &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1, &r->p2, &r->e2a, &r->e2, &r->p3,
                                 &r->ba, &r->bb,  &r->u2, &r->d2a, &r->d2, &r->u1, &r->d1a, &r->d1, &r->u0, &r->d0a, &r->d0};
     for (int k = 0; k < 21; k++) *bufs[k] = r->act + offs[k];
-    // the output layer's weights as f32
-    std::vector<float> wout(size_t(3 * r->nout) * 32);
-    for (size_t k = 0; k < wout.size(); k++) {
-        const uint32_t bits = uint32_t(weights_bf16[nw3 + int64_t(k)]) << 16;
-        std::memcpy(&wout[k], &bits, 4);
+    // the output layer: its 32 weights, then the angular base over the 48
+    // input channels (bf16 bit patterns: 1/8, 3/8, 5/8, 7/8 and 1 are exact)
+    const int no3 = 3 * r->nout;
+    std::vector<uint16_t> wout(size_t(no3) * 80, 0);
+    auto bf16_bits = [](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return uint16_t(u >> 16);   // exact for the base weights
+    };
+    for (int o = 0; o < no3; o++) {
+        for (int k = 0; k < 32; k++) wout[size_t(o) * 80 + k] = weights_bf16[nw3 + int64_t(o) * 32 + k];
+        const int kv = o / 3, c = o - 3 * kv;
+        const float pos = (float(kv) - 1.5f) * 0.25f;
+        const int j0 = r->nin > 1 ? std::min(std::max(int(std::floor(pos)), 0), r->nin - 2) : 0;
+        const float t = r->nin > 1 ? std::min(std::max(pos - float(j0), 0.0f), 1.0f) : 0.0f;
+        const int j1 = r->nin > 1 ? j0 + 1 : j0;
+        if (j1 == j0) {
+            wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f);
+        } else {
+            wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f - t);
+            wout[size_t(o) * 80 + 32 + 3 * j1 + c] = bf16_bits(t);
+        }
     }
     if ((e = cudaMemcpy(r->w, weights_bf16, 2 * nw3, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(r->b, biases, 4 * nb3, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(r->w_out, wout.data(), 4 * wout.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(r->w_out, wout.data(), 2 * wout.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(r->b_out, biases + nb3, 4 * int64_t(3 * r->nout), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(r->act, 0, 2 * total)) != cudaSuccess) {
         free_recon(r);
@@ -472,9 +553,9 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     CKR(launch_up2_concat(r->d1, 64, r->e0, 32, H0, W0, r->u0, sm, s), "up 0");
     CKR(conv(12, r->u0, r->d0a, H0, W0), "conv 12");
     CKR(conv(13, r->d0a, r->d0, H0, W0), "conv 13");
-    const size_t smem = sizeof(float) * size_t(3 * r->nout) * 33;
+    const size_t smem = 2 * size_t(3 * r->nout) * kOutK + 4 * size_t(3 * r->nout) + 4 * size_t(8 * 16 * r->nout);
     CKR(cudaFuncSetAttribute(k_recon_out, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "recon_out smem");
-    k_recon_out<<<sm * 8, 128, smem, s>>>(r->d0, r->x0, r->nin, r->H, r->W, W0, r->w_out, r->b_out, out_views);
+    k_recon_out<<<sm * 2, 256, smem, s>>>(r->d0, r->x0, r->nin, r->H, r->W, H0, W0, r->w_out, r->b_out, out_views);
     CKR(cudaGetLastError(), "launch k_recon_out");
 #undef CKR
     return LFDPR_OK;

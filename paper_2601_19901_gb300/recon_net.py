@@ -203,8 +203,9 @@ def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin
     d2 = conv(9, conv(8, torch.cat([up(b), e2], 1)))
     d1 = conv(11, conv(10, torch.cat([up(d2), e1], 1)))
     d0 = conv(13, conv(12, torch.cat([up(d1), e0], 1)))
-    out = torch.einsum("ok,bkhw->bohw", w_out, d0) + b_out[None, :, None, None]
-    out = out + torch.einsum("oc,bchw->bohw", torch.from_numpy(base_matrix(nin)).to(dev), x0)
+    # the library's output layer: one product over [d0 (32) | x0 (48)]
+    w_all = torch.cat([w_out, torch.from_numpy(base_matrix(nin)).to(dev)], 1)
+    out = torch.einsum("ok,bkhw->bohw", w_all, torch.cat([d0, x0], 1)) + b_out[None, :, None, None]
     v = torch.round(out.clamp(0.0, 1.0) * 255.0)[0, :, :h, :w]
     rgb = v.reshape(4 * nin, 3, h, w).permute(0, 2, 3, 1).to(torch.uint8)
     res = torch.full((4 * nin, h, w, 4), 255, dtype=torch.uint8, device=dev)
