@@ -51,14 +51,27 @@ class OrcDisplay(C.Structure):
                 ("bias_h", C.c_float), ("bias_v", C.c_float),
                 ("panel_w", C.c_int32), ("panel_h", C.c_int32),
                 ("lens_pitch_px", C.c_float), ("slant", C.c_float), ("phase_offset", C.c_float),
-                ("recon", C.c_int32), ("crosstalk", C.c_float)]
+                ("recon", C.c_int32), ("crosstalk", C.c_float),
+                ("jitter", C.c_void_p), ("samples", C.c_void_p), ("n_samples", C.c_int32)]
 
 
-def _disp(d) -> OrcDisplay:
-    return OrcDisplay(d.n_views, d.view_w, d.view_h, d.cone_deg, d.view_dist,
-                      d.focal_w, d.focal_h, d.near_z, d.far_z, d.bias_h, d.bias_v,
-                      d.panel_w, d.panel_h, d.lens_pitch_px, d.slant, d.phase_offset,
-                      d.recon, d.crosstalk)
+def _disp(d, jitter=None, samples=None) -> OrcDisplay:
+    """The C display. jitter (float32 [rendered views], each in [0, 1]) places
+    each rendered view in its interval; samples (float32 [n][3]: dx, dy in
+    view pixels, dphi in display views) drive Gaussian reconstruction. Both
+    arrays are kept alive on the returned structure."""
+    o = OrcDisplay(d.n_views, d.view_w, d.view_h, d.cone_deg, d.view_dist,
+                   d.focal_w, d.focal_h, d.near_z, d.far_z, d.bias_h, d.bias_v,
+                   d.panel_w, d.panel_h, d.lens_pitch_px, d.slant, d.phase_offset,
+                   d.recon, d.crosstalk, None, None, 0)
+    if jitter is not None:
+        o._jitter = np.ascontiguousarray(jitter, np.float32)
+        o.jitter = o._jitter.ctypes.data
+    if samples is not None:
+        o._samples = np.ascontiguousarray(samples, np.float32).reshape(-1, 3)
+        o.samples = o._samples.ctypes.data
+        o.n_samples = o._samples.shape[0]
+    return o
 
 
 def lib():
@@ -91,6 +104,10 @@ def lib():
             L.orc_view_of_subpixel.restype = C.c_int
             L.orc_view_of_subpixel.argtypes = [P, C.c_int, C.c_int, C.c_int]
             L.orc_interleave.argtypes = [P, P, P]
+            L.orc_view_pos.restype = C.c_float
+            L.orc_view_pos.argtypes = [P, C.c_int]
+            L.orc_subpixel_phase.restype = C.c_float
+            L.orc_subpixel_phase.argtypes = [P, C.c_int, C.c_int, C.c_int]
             L.orc_raycast.restype = C.c_int32
             L.orc_raycast.argtypes = [P, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(C.c_double)]
@@ -111,8 +128,8 @@ def log2f(x: float) -> float:
     return float(lib().orc_log2f(C.c_float(x)))
 
 
-def eyes(d) -> np.ndarray:
-    dd = _disp(d)
+def eyes(d, jitter=None) -> np.ndarray:
+    dd = _disp(d, jitter)
     out = np.zeros(lib().orc_n_render_views(C.byref(dd)), np.float32)
     lib().orc_eyes(C.byref(dd), _p(out))
     return out
@@ -147,6 +164,16 @@ def trilinear(chain: np.ndarray, w: int, h: int, s: float, t: float, lod: float)
 def view_of_subpixel(d, x: int, y: int, c: int) -> int:
     dd = _disp(d)
     return int(lib().orc_view_of_subpixel(C.byref(dd), x, y, c))
+
+
+def subpixel_phase(d, x: int, y: int, c: int) -> float:
+    dd = _disp(d)
+    return float(lib().orc_subpixel_phase(C.byref(dd), x, y, c))
+
+
+def view_pos(d, m: int, jitter=None) -> float:
+    dd = _disp(d, jitter)
+    return float(lib().orc_view_pos(C.byref(dd), m))
 
 
 def transformed_tris(scene, model: np.ndarray) -> np.ndarray:
@@ -200,10 +227,10 @@ class Textures:
         self.ptrs = (C.c_void_p * len(self.chains))(*[c.ctypes.data for c in self.chains])
 
 
-def setup(d, scene, model, tex_wh=None):
+def setup(d, scene, model, tex_wh=None, jitter=None):
     """Steps 1-7 only: per-triangle records and point counts. tex_wh overrides
     the texture sizes (setup reads sizes, never texels)."""
-    dd = _disp(d)
+    dd = _disp(d, jitter)
     T = scene.n_tris
     tri = np.zeros((T, TRI_FLOATS), np.float32)
     counts = np.zeros(T, np.uint32)
@@ -229,12 +256,13 @@ def emit(tri: np.ndarray, counts: np.ndarray) -> np.ndarray:
 
 
 def render(d, scene, model, views: Optional[Sequence[int]] = None, panel: bool = True,
-           textures: Optional[Textures] = None, splat: bool = True) -> Frame:
+           textures: Optional[Textures] = None, splat: bool = True, jitter=None, samples=None) -> Frame:
     """One frame through every oracle step. `views` lists the rendered views
-    to splat and resolve (default all); the panel needs all of them."""
+    to splat and resolve (default all); the panel needs all of them. jitter
+    and samples: see _disp."""
     L = lib()
-    dd = _disp(d)
-    st, tri, counts = setup(d, scene, model)
+    dd = _disp(d, jitter, samples)
+    st, tri, counts = setup(d, scene, model, jitter=jitter)
     total = int(counts.sum(dtype=np.int64))
     points = np.zeros((max(total, 1), 4), np.uint32)
     n = L.orc_emit(_p(tri), _p(counts), scene.n_tris, _p(points), total)
@@ -270,9 +298,9 @@ def splat_hits(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]) -> 
     return hits
 
 
-def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]):
+def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int], jitter=None):
     """Steps 9-10 for the listed views, from existing records and points."""
-    dd = _disp(d)
+    dd = _disp(d, jitter)
     vl = np.asarray(views, np.int32)
     pts = np.ascontiguousarray(points, np.uint32)
     keys = np.zeros((len(vl), d.view_h, d.view_w), np.uint64)
@@ -282,8 +310,8 @@ def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]):
     return keys, rgba
 
 
-def interleave(d, rendered: np.ndarray) -> np.ndarray:
-    dd = _disp(d)
+def interleave(d, rendered: np.ndarray, jitter=None, samples=None) -> np.ndarray:
+    dd = _disp(d, jitter, samples)
     pan = np.zeros((d.panel_h, d.panel_w, 4), np.uint8)
     lib().orc_interleave(C.byref(dd), _p(np.ascontiguousarray(rendered, np.uint8)), _p(pan))
     return pan

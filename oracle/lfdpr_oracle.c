@@ -49,8 +49,11 @@ typedef struct {
     float cone_deg, view_dist, focal_w, focal_h, near_z, far_z, bias_h, bias_v;
     int32_t panel_w, panel_h;
     float lens_pitch_px, slant, phase_offset;
-    int32_t recon;
+    int32_t recon;          /* 0 none, 1 2x angular + tent, 2 2x angular + Gaussian, 3 Gaussian */
     float crosstalk;
+    const float *jitter;    /* NULL, or per rendered view u in [0, 1]: its place in its interval */
+    const float *samples;   /* recon 2, 3: n_samples x (dx, dy in view pixels, dphi in display views) */
+    int32_t n_samples;
 } orc_display;
 
 /* Per-triangle record, written by orc_setup as ORC_TRI_FLOATS floats. */
@@ -159,24 +162,38 @@ float orc_log2f(float x) {
 /* -------------------------------------------------------------------------- */
 
 int orc_n_render_views(const orc_display *d) {
-    return d->recon == 1 ? 2 * d->n_views : d->n_views;
+    return d->recon == 1 || d->recon == 2 ? 2 * d->n_views : d->n_views;
 }
 
 /*
  * Eye x positions. The N display views sit at the centres of N equal angular
- * intervals of the viewing cone, on the line y = 0, z = D. Sec. 4 projects
- * the splats into twice as many views placed randomly inside the view
- * intervals; the reading taken here is deterministic: 2N views at
- * half-interval steps, the even ones on the N display-view centres.
+ * intervals of the viewing cone, on the line y = 0, z = D. With angular
+ * supersampling (recon 1 or 2) Sec. 4 projects the splats into twice as many
+ * views, placed randomly inside their intervals: rendered view m sits at the
+ * fraction u_m of the half-interval [(m + 1/2), (m + 3/2)] / 2N of the cone
+ * (u_m = d->jitter[m], or 1/2 without jitter: then the even views fall on the
+ * N display-view centres). Without supersampling view k sits at the
+ * fraction u_k of its interval (1/2: the centre).
  */
+static double jitter_of(const orc_display *d, int m) {
+    return d->jitter ? (double)d->jitter[m] : 0.5;
+}
+
 void orc_eyes(const orc_display *d, float *ex) {
     int nr = orc_n_render_views(d);
     double cone = d->cone_deg, D = d->view_dist;
     for (int k = 0; k < nr; k++) {
-        double deg = d->recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * d->n_views)
-                                   : -cone / 2.0 + cone * (k + 0.5) / d->n_views;
+        double deg = nr == 2 * d->n_views ? -cone / 2.0 + cone * (k + 0.5 + jitter_of(d, k)) / (2.0 * d->n_views)
+                                          : -cone / 2.0 + cone * (k + jitter_of(d, k)) / d->n_views;
         ex[k] = (float)(D * tan(deg * M_PI / 180.0));
     }
+}
+
+/* Position of rendered view m on the display-view axis (display view k
+ * covers [k, k+1), its centre k + 1/2), the reading of the angle above. */
+float orc_view_pos(const orc_display *d, int m) {
+    int nr = orc_n_render_views(d);
+    return nr == 2 * d->n_views ? (float)((m + 0.5 + jitter_of(d, m)) / 2.0) : (float)(m + jitter_of(d, m));
 }
 
 /* -------------------------------------------------------------------------- */
@@ -842,30 +859,106 @@ void orc_display_views(const orc_display *d, const uint8_t *rendered, float *out
     free(o);
 }
 
-/* Subpixel phase -> view index under the slanted lenticular lens (reading of
- * the interleave of Sec. 4: a van Berkel-style slanted-lens phase taken at the
- * subpixel's centre, x + (c + 1/2)/3 for colour channel c of pixel x). */
-int orc_view_of_subpixel(const orc_display *d, int x, int y, int c) {
+/* Subpixel phase on the display-view axis under the slanted lenticular lens
+ * (reading of the interleave of Sec. 4: a van Berkel-style slanted-lens phase
+ * taken at the subpixel's centre, x + (c + 1/2)/3 for colour channel c of
+ * pixel x): phi in [0, N). */
+float orc_subpixel_phase(const orc_display *d, int x, int y, int c) {
     static const float third[3] = {(float)(1.0 / 6.0), 0.5f, (float)(5.0 / 6.0)};
     float inv_pitch = (float)(1.0 / (double)d->lens_pitch_px);
     float cx = (float)x + third[c];
     float a = fmaf(d->slant, (float)y, cx);
     float ph = fmaf(a, inv_pitch, d->phase_offset);
     float fr = ph - floorf(ph);
-    int k = (int)(fr * (float)d->n_views);
+    return fr * (float)d->n_views;
+}
+
+int orc_view_of_subpixel(const orc_display *d, int x, int y, int c) {
+    int k = (int)orc_subpixel_phase(d, x, y, c);
     if (k >= d->n_views) k = d->n_views - 1;
     if (k < 0) k = 0;
     return k;
 }
 
 /*
+ * Gaussian reconstruction (recon 2 over the 2N supersampled views, recon 3
+ * over the N views; Sec. 4: Gaussian filters in space and angle, integrated
+ * with a few random samples). The display value at phase
+ * phi, channel c, for panel pixel (x, y) is the mean over the samples s of
+ * the rendered view nearest (on the display-view axis; on a tie the later
+ * view) to phi + dphi_s, at the view pixel holding (vx + dx_s, vy + dy_s),
+ * clamped to the view, where (vx, vy) = ((x + 1/2) W / Wp, (y + 1/2) H / Hp).
+ * The samples (offsets drawn from the filters) are the caller's.
+ */
+float orc_gauss_value(const orc_display *d, const uint8_t *rendered, const float *pos, float phi, int x, int y,
+                      int c) {
+    int nr = orc_n_render_views(d), W = d->view_w, H = d->view_h;
+    size_t npix = (size_t)W * H;
+    float r = (float)(nr / d->n_views);
+    float sxw = (float)W / (float)d->panel_w, syh = (float)H / (float)d->panel_h;
+    float vx = ((float)x + 0.5f) * sxw, vy = ((float)y + 0.5f) * syh;
+    float acc = 0.0f;
+    for (int s = 0; s < d->n_samples; s++) {
+        float a = phi + d->samples[3 * s + 2];
+        int lo = (int)floorf(r * a) - 2;
+        if (lo > nr - 4) lo = nr - 4;
+        if (lo < 0) lo = 0;
+        int hi = lo + 3 < nr - 1 ? lo + 3 : nr - 1;
+        int m = lo;
+        float best = fabsf(pos[lo] - a);
+        for (int q = lo + 1; q <= hi; q++) {
+            float dq = fabsf(pos[q] - a);
+            if (dq <= best) {
+                best = dq;
+                m = q;
+            }
+        }
+        int px = (int)floorf(vx + d->samples[3 * s]), py = (int)floorf(vy + d->samples[3 * s + 1]);
+        px = px < 0 ? 0 : (px >= W ? W - 1 : px);
+        py = py < 0 ? 0 : (py >= H ? H - 1 : py);
+        acc += (float)rendered[((size_t)m * npix + (size_t)py * W + px) * 4 + c];
+    }
+    return acc / (float)d->n_samples;
+}
+
+/*
  * orc_interleave: the elemental image array. Panel subpixel (x, y, c) shows
  * channel c of display view orc_view_of_subpixel(x, y, c) at the nearest view
- * texel (floor((x+1/2) W / W_p), floor((y+1/2) H / H_p)); alpha is 255.
+ * texel (floor((x+1/2) W / W_p), floor((y+1/2) H / H_p)); alpha is 255. With
+ * Gaussian reconstruction (recon 2 or 3) it shows orc_gauss_value at the
+ * subpixel's phase phi, with crosstalk x mixing in the values at phi - 1 and
+ * phi + 1 (wrapping over the N views) at weight x each.
  */
 void orc_interleave(const orc_display *d, const uint8_t *rendered, uint8_t *panel) {
     int N = d->n_views, W = d->view_w, H = d->view_h, Wp = d->panel_w, Hp = d->panel_h;
     size_t npix = (size_t)W * H;
+    if (d->recon == 2 || d->recon == 3) {
+        int nr = orc_n_render_views(d);
+        float *pos = (float *)malloc(sizeof(float) * (size_t)nr);
+        for (int m = 0; m < nr; m++) pos[m] = orc_view_pos(d, m);
+        float x = d->crosstalk, c0 = (float)(1.0 - 2.0 * (double)d->crosstalk);
+        for (int y = 0; y < Hp; y++)
+            for (int xp = 0; xp < Wp; xp++) {
+                uint8_t *o = panel + ((size_t)y * Wp + xp) * 4;
+                for (int c = 0; c < 3; c++) {
+                    float phi = orc_subpixel_phase(d, xp, y, c);
+                    float v = orc_gauss_value(d, rendered, pos, phi, xp, y, c);
+                    if (x > 0.0f) {
+                        float pm = phi - 1.0f, pp = phi + 1.0f;
+                        if (pm < 0.0f) pm += (float)N;
+                        if (pp >= (float)N) pp -= (float)N;
+                        float acc = v * c0;
+                        acc = fmaf(x, orc_gauss_value(d, rendered, pos, pm, xp, y, c), acc);
+                        acc = fmaf(x, orc_gauss_value(d, rendered, pos, pp, xp, y, c), acc);
+                        v = acc;
+                    }
+                    o[c] = to_u8(v);
+                }
+                o[3] = 255;
+            }
+        free(pos);
+        return;
+    }
     float *dv = (float *)malloc(sizeof(float) * npix * 4 * (size_t)N);
     orc_display_views(d, rendered, dv);
     for (int y = 0; y < Hp; y++) {

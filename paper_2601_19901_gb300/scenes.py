@@ -47,12 +47,14 @@ class Display:
     lens_pitch_px: float
     slant: float
     phase_offset: float = 0.0
-    recon: int = 0          # 0: render n_views; 1: render 2*n_views, tent down to n_views
+    # 0: render n_views; 1: render 2*n_views, tent down to n_views; 2: render
+    # 2*n_views, Gaussian reconstruction; 3: render n_views, Gaussian reconstruction
+    recon: int = 0
     crosstalk: float = 0.0  # weight of each +-1 neighbour view before interleave
 
     @property
     def n_render_views(self) -> int:
-        return self.n_views * (2 if self.recon == 1 else 1)
+        return self.n_views * (2 if self.recon in (1, 2) else 1)
 
 
 def display_tiny() -> Display:

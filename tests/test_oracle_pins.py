@@ -582,3 +582,96 @@ def test_eq8_eq9_on_a_screen_parallel_triangle():
     assert np.all(np.abs(got - want) <= 0.5 + 1e-3)
     assert int(cov.sum()) > 100
     assert np.abs(tmax - tmin).max() >= 20     # the two LODs really differ here
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4's supersampling at random angles and Gaussian reconstruction
+# ---------------------------------------------------------------------------
+
+def _gauss_display(recon, n_views=8, crosstalk=0.0):
+    # tiny display: 128 x 128 views, 512 x 512 panel (view/panel ratio exact in binary32)
+    return replace(S.display_tiny(), n_views=n_views, recon=recon, crosstalk=crosstalk)
+
+
+def _random_views(d, seed=4):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, (d.n_render_views, d.view_h, d.view_w, 4), dtype=np.uint8)
+
+
+def test_jitter_of_one_half_gives_the_regular_eyes():
+    for recon in (0, 1, 3):
+        d = _gauss_display(recon)
+        half = np.full(d.n_render_views, 0.5, np.float32)
+        assert np.array_equal(O.eyes(d, half), O.eyes(d))
+
+
+def test_jitter_places_each_eye_inside_its_interval():
+    # supersampled: rendered view m covers the half-interval [(m + 1/2), (m + 3/2)] / 2N
+    # of the cone; jitter 0 and 1 put the eye at its two ends
+    d = _gauss_display(2)
+    nr = d.n_render_views
+    for u in (0.0, 1.0):
+        ex = O.eyes(d, np.full(nr, u, np.float32)).astype(np.float64)
+        ang = np.degrees(np.arctan(ex / d.view_dist))
+        want = -d.cone_deg / 2 + d.cone_deg * (np.arange(nr) + 0.5 + u) / (2 * d.n_views)
+        assert np.allclose(ang, want, atol=1e-4)
+
+
+def test_gauss_one_centred_sample_is_the_plain_interleave():
+    # recon 3 with a single zero offset samples, for each subpixel, the view it
+    # falls in at the nearest view pixel: the plain interleave
+    d0 = _gauss_display(0)
+    d3 = _gauss_display(3)
+    v = _random_views(d0)
+    assert np.array_equal(O.interleave(d3, v, samples=np.zeros((1, 3), np.float32)), O.interleave(d0, v))
+
+
+def test_gauss_identical_samples_average_to_one_sample():
+    d = _gauss_display(2)
+    v = _random_views(d)
+    one = np.array([[0.7, -1.3, 0.4]], np.float32)
+    assert np.array_equal(O.interleave(d, v, samples=np.repeat(one, 8, 0)), O.interleave(d, v, samples=one))
+
+
+def test_gauss_constant_views_stay_constant():
+    d = _gauss_display(2, crosstalk=0.15)
+    v = np.full((d.n_render_views, d.view_h, d.view_w, 4), 77, np.uint8)
+    rng = np.random.default_rng(2)
+    s = rng.normal(0.0, [0.5625, 0.5625, 0.5], (8, 3)).astype(np.float32)
+    jit = rng.random(d.n_render_views).astype(np.float32)
+    pan = O.interleave(d, v, jitter=jit, samples=s)
+    assert np.all(pan[..., :3] == 77) and np.all(pan[..., 3] == 255)
+
+
+def test_gauss_spatial_offset_reads_the_next_pixel():
+    # a +1 view-pixel offset reads each view one pixel to the right (clamped):
+    # the plain interleave of the views shifted left by one pixel
+    d0 = _gauss_display(0)
+    d3 = _gauss_display(3)
+    v = _random_views(d0, 6)
+    shifted = np.concatenate([v[:, :, 1:], v[:, :, -1:]], axis=2)
+    got = O.interleave(d3, v, samples=np.array([[1.0, 0.0, 0.0]], np.float32))
+    assert np.array_equal(got, O.interleave(d0, shifted))
+
+
+def test_gauss_takes_the_nearest_view_by_brute_force():
+    # random eye jitter and one random angular offset: every subpixel shows the
+    # rendered view whose position is nearest its phase (ties to the later
+    # view), found here by scanning all views
+    d = replace(_gauss_display(2), panel_w=96, panel_h=40)
+    rng = np.random.default_rng(11)
+    jit = rng.random(d.n_render_views).astype(np.float32)
+    nr = d.n_render_views
+    pos = np.array([O.view_pos(d, m, jit) for m in range(nr)], np.float32)
+    v = np.zeros((nr, d.view_h, d.view_w, 4), np.uint8)
+    v[..., :3] = (np.arange(nr, dtype=np.uint8) * 11)[:, None, None, None]   # view m carries 11 m
+    for dphi in (0.0, 0.37, -1.9, 6.2):
+        s = np.array([[0.0, 0.0, dphi]], np.float32)
+        pan = O.interleave(d, v, jitter=jit, samples=s)
+        for y in range(0, d.panel_h, 7):
+            for x in range(0, d.panel_w, 5):
+                for c in range(3):
+                    a = np.float32(O.subpixel_phase(d, x, y, c)) + np.float32(dphi)
+                    dist = np.abs(pos - a)
+                    m = int(np.flatnonzero(dist == dist.min())[-1])
+                    assert pan[y, x, c] == 11 * m, (dphi, x, y, c)
