@@ -61,8 +61,11 @@ typedef enum {
  * panel_w x panel_h RGBA8 under slanted lenses of lens_pitch_px pixels, slant
  * `slant` pixels per row, phase offset phase_offset (in lens periods).
  * recon = 1 renders 2N views at half-interval steps and reconstructs N with a
- * [1/4, 1/2, 1/4] tent; crosstalk x > 0 mixes each view with its +-1
- * neighbours at weight x before interleaving. max_points is the point-buffer
+ * [1/4, 1/2, 1/4] tent; recon = 2 renders 2N views and recon = 3 N views,
+ * both reconstructed by the Gaussian filters of Sec. 4 at sample offsets set
+ * with lfdpr_set_recon_samples (required before their interleave); crosstalk
+ * x > 0 mixes each view with its +-1 neighbours at weight x before
+ * interleaving (for recon 2 and 3: the reconstruction one view away). max_points is the point-buffer
  * capacity (0 = 1 << 23); each point of capacity takes 148 B of device
  * memory (the 16-B point record, a 48-B splat work record, a 4-B near-list
  * entry and an 80-B resolve record).
@@ -153,7 +156,7 @@ typedef struct {
 /*
  * lfdpr_create_display: validate `desc` (positive sizes, 1 <= n_views <= 256,
  * views of at most 16384 pixels a side and 2^26 pixels,
- * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1},
+ * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1, 2, 3},
  * 0 <= crosstalk < 0.5) and allocate the display's device buffers: view key
  * buffers (8 B per rendered-view pixel, Sec. 5.2), RGBA8 views, the point
  * buffers (148 B per point of capacity) and the panel scratch. Uses the current CUDA device.
@@ -163,6 +166,31 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc *desc, lfdpr_display 
 
 /* Free a display and every device buffer it owns (meshes must be destroyed first). */
 lfdpr_status lfdpr_destroy_display(lfdpr_display *disp);
+
+/*
+ * lfdpr_set_view_jitter: place each rendered view at a chosen point of its
+ * angular interval (Sec. 4: supersampled views at random angles in the view
+ * intervals; the caller draws the numbers). u f32 [n], n = the rendered view
+ * count (2N for recon 1 and 2, else N), each in [0, 1] (host, copied). With
+ * 2N views, view m's eye is at the angle -cone/2 + cone (m + 1/2 + u_m) / 2N;
+ * with N views, -cone/2 + cone (k + u_k) / N; u = 1/2 everywhere gives the
+ * default eyes. Applies from the next frame. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_set_view_jitter(lfdpr_display *disp, const float *u, int32_t n);
+
+/*
+ * lfdpr_set_recon_samples: the sample offsets of the Gaussian
+ * reconstruction (recon 2, 3; Sec. 4 integrates its filters with a few
+ * random samples; the caller draws them): samples f32 [n][3] (host, copied),
+ * 1 <= n <= 32, each (dx, dy) in view pixels and dphi in display views. A
+ * panel subpixel at lens phase phi (in display views, [0, N)) shows the mean
+ * over the samples of the rendered view nearest (on the display-view axis,
+ * where rendered view m sits at (m + 1/2 + u_m) / 2 with 2N views, k + u_k
+ * with N; ties to the later view) to phi + dphi, at the view pixel holding
+ * ((x + 1/2) W / panel_w + dx, (y + 1/2) H / panel_h + dy), clamped to the
+ * view. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_set_recon_samples(lfdpr_display *disp, const float *samples, int32_t n);
 
 /*
  * lfdpr_upload_mesh: copy a triangle mesh and its textures to the device and

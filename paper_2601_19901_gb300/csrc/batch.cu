@@ -113,7 +113,10 @@ lfdpr_status record_batch(lfdpr_batch* b) {
     for (int i = 0; i < b->n; i++) {
         const FrameArgs a = frame_args(b->disp[i], b->mesh[i]);
         CK(launch_resolve(a, b->br[i % K]), "launch k_resolve");
-        CK(launch_interleave(b->disp[i]->dc, b->disp[i]->views, b->disp[i]->panel, b->br[i % K]),
+        const lfdpr_display* d = b->disp[i];
+        if ((d->desc.recon == 2 || d->desc.recon == 3) && d->n_samples == 0)
+            return fail(LFDPR_EINVAL, "batch: scene %d needs lfdpr_set_recon_samples", i);
+        CK(launch_interleave(d->dc, d->views, d->d_pos, d->d_samples, d->n_samples, d->panel, b->br[i % K]),
            "launch k_interleave");
     }
     for (int j = 0; j < K; j++) {

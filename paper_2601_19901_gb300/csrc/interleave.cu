@@ -11,6 +11,10 @@
 // coalesced loads, then forms every panel row that samples that view row,
 // one thread per 4 adjacent panel pixels and one 16-byte store per row.
 // k_interleave (the direct gather) serves displays whose tile would not fit.
+// k_interleave_gauss is the Gaussian reconstruction of Sec. 4 (recon 2, 3):
+// per subpixel the mean of the caller's samples, each the nearest rendered
+// view to the subpixel's phase plus the sample's angular offset at the view
+// pixel holding its spatially offset position (gathers, so no row staging).
 #include "lfdpr_internal.cuh"
 
 namespace lfdpr {
@@ -50,13 +54,18 @@ __device__ __forceinline__ float display_value(const DispConst& c, const T& tex,
     return __fdiv_rn(acc, ws);
 }
 
-__device__ __forceinline__ int view_of_subpixel(const DispConst& c, int x, int y, int ch) {
+// Lens phase of subpixel (x, y, ch) on the display-view axis, [0, N).
+__device__ __forceinline__ float subpixel_phase(const DispConst& c, int x, int y, int ch) {
     const float third = ch == 0 ? (float)(1.0 / 6.0) : (ch == 1 ? 0.5f : (float)(5.0 / 6.0));
     const float cx = float(x) + third;
     const float a = fmaf(c.slant, float(y), cx);
     const float ph = fmaf(a, c.inv_pitch, c.phase_offset);
     const float fr = ph - floorf(ph);
-    int k = int(fr * float(c.n_views));
+    return fr * float(c.n_views);
+}
+
+__device__ __forceinline__ int view_of_subpixel(const DispConst& c, int x, int y, int ch) {
+    int k = int(subpixel_phase(c, x, y, ch));
     k = k >= c.n_views ? c.n_views - 1 : (k < 0 ? 0 : k);
     return k;
 }
@@ -161,12 +170,96 @@ __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* 
     }
 }
 
+// Gaussian reconstruction at phase phi, channel ch, panel pixel (x, y): the
+// mean over the samples of the rendered view nearest phi + dphi (positions
+// pos[], ties to the later view) at the view pixel holding (vx + dx, vy + dy)
+// (clamped), vx = (x + 1/2) W / Wp, vy = (y + 1/2) H / Hp.
+__device__ __forceinline__ float gauss_value(const DispConst& c, const uint8_t* __restrict__ views, const float* pos,
+                                             const float* smp, int ns, float phi, float vx, float vy, int ch) {
+    const int nr = c.nr, W = c.W, H = c.H;
+    const uint64_t npix = (uint64_t)W * H;
+    const float r = float(nr / c.n_views);
+    float acc = 0.0f;
+    for (int s = 0; s < ns; s++) {
+        const float a = phi + smp[3 * s + 2];
+        int lo = int(floorf(r * a)) - 2;
+        lo = lo > nr - 4 ? nr - 4 : lo;
+        lo = lo < 0 ? 0 : lo;
+        const int hi = lo + 3 < nr - 1 ? lo + 3 : nr - 1;
+        int m = lo;
+        float best = fabsf(pos[lo] - a);
+        for (int q = lo + 1; q <= hi; q++) {
+            const float dq = fabsf(pos[q] - a);
+            if (dq <= best) {
+                best = dq;
+                m = q;
+            }
+        }
+        int px = int(floorf(vx + smp[3 * s])), py = int(floorf(vy + smp[3 * s + 1]));
+        px = px < 0 ? 0 : (px >= W ? W - 1 : px);
+        py = py < 0 ? 0 : (py >= H ? H - 1 : py);
+        acc += float(__ldg(views + ((uint64_t)m * npix + (uint64_t)py * W + px) * 4u + ch));
+    }
+    return acc / float(ns);
+}
+
+__global__ void __launch_bounds__(256) k_interleave_gauss(DispConst c, const uint8_t* __restrict__ views,
+                                                          const float* __restrict__ pos,
+                                                          const float* __restrict__ samples, int ns,
+                                                          uint8_t* __restrict__ panel) {
+    __shared__ float s_pos[kMaxRenderViews];
+    __shared__ float s_smp[3 * 32];
+    for (int i = threadIdx.x; i < c.nr; i += blockDim.x) s_pos[i] = pos[i];
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) s_smp[i] = samples[i];
+    __syncthreads();
+    const int groups_x = (c.Wp + 3) >> 2;
+    const uint64_t total = (uint64_t)groups_x * c.Hp;
+    const float sxw = float(c.W) / float(c.Wp), syh = float(c.H) / float(c.Hp);
+    const float N = float(c.n_views);
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const int y = int(g / groups_x);
+        const int xg = int(g - (uint64_t)y * groups_x) * 4;
+        const float vy = (float(y) + 0.5f) * syh;
+        uint32_t px[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int x = min(xg + e, c.Wp - 1);
+            const float vx = (float(x) + 0.5f) * sxw;
+            uint32_t o = 0xff000000u;
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                const float phi = subpixel_phase(c, x, y, ch);
+                float v = gauss_value(c, views, s_pos, s_smp, ns, phi, vx, vy, ch);
+                if (c.xtalk > 0.0f) {
+                    float pm = phi - 1.0f, pp = phi + 1.0f;
+                    if (pm < 0.0f) pm += N;
+                    if (pp >= N) pp -= N;
+                    float acc = v * c.xtalk_c;
+                    acc = fmaf(c.xtalk, gauss_value(c, views, s_pos, s_smp, ns, pm, vx, vy, ch), acc);
+                    acc = fmaf(c.xtalk, gauss_value(c, views, s_pos, s_smp, ns, pp, vx, vy, ch), acc);
+                    v = acc;
+                }
+                o |= uint32_t(round_u8(v)) << (8 * ch);
+            }
+            px[e] = o;
+        }
+        store4(c, panel, xg, y, px);
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel, cudaStream_t s) {
+cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const float* pos, const float* samples,
+                              int n_samples, uint8_t* panel, cudaStream_t s) {
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dc.recon == 2 || dc.recon == 3) {
+        if (n_samples < 1 || n_samples > 32) return cudaErrorInvalidValue;
+        k_interleave_gauss<<<sms * 8, 256, 0, s>>>(dc, views, pos, samples, n_samples, panel);
+        return cudaGetLastError();
+    }
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // widest source segment of a tile: (kTileCols - 1) W / Wp + 2 pixels
     const int64_t seg = ((int64_t)(kTileCols - 1) * dc.W) / dc.Wp + 2;

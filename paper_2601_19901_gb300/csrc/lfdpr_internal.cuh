@@ -244,8 +244,10 @@ cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots
                                cudaStream_t s);
 cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
-cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, uint8_t* panel,
-                              cudaStream_t s);
+// pos [nr] (views on the display-view axis) and samples [n_samples][3] are
+// read only for Gaussian reconstruction (recon 2, 3).
+cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const float* pos, const float* samples,
+                              int n_samples, uint8_t* panel, cudaStream_t s);
 cudaError_t launch_mip_level(const uint8_t* src, uint32_t sw, uint32_t sh, uint8_t* dst,
                              uint32_t dw, uint32_t dh, cudaStream_t s);
 cudaError_t launch_probe_atomic(uint64_t* words, uint64_t n_words, const uint32_t* idx,

@@ -83,7 +83,7 @@ extern "C" lfdpr_status lfdpr_sample_points_noalloc(
         s.view_h > 16384 || !(s.view_dist > 0.0f) || !(s.focal_w > 0.0f) || !(s.focal_h > 0.0f) ||
         !(s.near_z > 0.0f) || !(s.far_z > s.near_z) || !std::isfinite(s.far_z) || !(s.cone_deg >= 0.0f) ||
         !(s.cone_deg < 179.0f) || !(s.bias_h > 0.0f) || !(s.bias_v > 0.0f) || !std::isfinite(s.bias_h) ||
-        !std::isfinite(s.bias_v) || (s.recon != 0 && s.recon != 1))
+        !std::isfinite(s.bias_v) || s.recon < 0 || s.recon > 3)
         return fail(LFDPR_EINVAL, "sample_points_noalloc: invalid display descriptor");
     for (int k = 0; k < 12; k++)
         if (!std::isfinite(model[k])) return fail(LFDPR_EINVAL, "sample_points_noalloc: non-finite model");
@@ -111,7 +111,8 @@ extern "C" lfdpr_status lfdpr_sample_points_noalloc(
     int sms = 1;
     CKN(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
 
-    const int nr = s.recon == 1 ? 2 * s.n_views : s.n_views;
+    const bool ss = s.recon == 1 || s.recon == 2;   // angular supersampling: 2N views
+    const int nr = ss ? 2 * s.n_views : s.n_views;
     FrameArgs a{};
     DispConst& c = a.dc;
     c.n_views = s.n_views;
@@ -140,7 +141,7 @@ extern "C" lfdpr_status lfdpr_sample_points_noalloc(
     float ex[kMaxRenderViews];
     const double cone = s.cone_deg;
     for (int k = 0; k < nr; k++) {
-        const double deg = s.recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * s.n_views)
+        const double deg = ss ? -cone / 2.0 + cone * (k + 1) / (2.0 * s.n_views)
                                         : -cone / 2.0 + cone * (k + 0.5) / s.n_views;
         ex[k] = float(double(s.view_dist) * std::tan(deg * M_PI / 180.0));
     }

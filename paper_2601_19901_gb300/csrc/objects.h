@@ -20,7 +20,11 @@ struct lfdpr_display {
     int device = 0;
     int sm_count = 1;
     std::vector<float> h_ex;
+    std::vector<float> h_jit;     // per rendered view: its place in its interval (1/2: the default eyes)
     float* d_ex = nullptr;
+    float* d_pos = nullptr;       // rendered views' positions on the display-view axis
+    float* d_samples = nullptr;   // Gaussian reconstruction samples [32][3]
+    int n_samples = 0;
     uint4* points = nullptr;
     uint32_t max_points = 0;
     lfdpr::WorkRec* work = nullptr;

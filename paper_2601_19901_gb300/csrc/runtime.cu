@@ -131,6 +131,8 @@ void free_display(lfdpr_display* d) {
     for (auto& e : d->ev)
         if (e) cudaEventDestroy(e);
     cudaFree(d->d_ex);
+    cudaFree(d->d_pos);
+    cudaFree(d->d_samples);
     cudaFree(d->points);
     cudaFree(d->work);
     cudaFree(d->near);
@@ -161,12 +163,34 @@ void free_mesh(lfdpr_mesh* m) {
     delete m;
 }
 
-// Eye x of rendered view k: centres of N equal angular intervals, or 2N
-// half-interval steps with angular supersampling (even ones on the centres).
-double eye_angle_deg(const lfdpr_display_desc& d, int k) {
+bool supersampled(const lfdpr_display_desc& d) { return d.recon == 1 || d.recon == 2; }
+
+// Eye angle of rendered view k at the fraction u of its interval: N equal
+// angular intervals, or 2N half-intervals with angular supersampling (u = 1/2
+// puts the even ones on the N view centres).
+double eye_angle_deg(const lfdpr_display_desc& d, int k, double u) {
     const double cone = d.cone_deg;
-    return d.recon == 1 ? -cone / 2.0 + cone * (k + 1) / (2.0 * d.n_views)
-                        : -cone / 2.0 + cone * (k + 0.5) / d.n_views;
+    return supersampled(d) ? -cone / 2.0 + cone * (k + 0.5 + u) / (2.0 * d.n_views)
+                           : -cone / 2.0 + cone * (k + u) / d.n_views;
+}
+
+// Eyes, their largest |x| and the views' positions on the display-view axis
+// from the display's jitter (host copies; the device copies follow).
+void place_eyes(lfdpr_display* d) {
+    const int nr = d->dc.nr;
+    d->h_ex.resize(nr);
+    for (int k = 0; k < nr; k++)
+        d->h_ex[k] = float(double(d->desc.view_dist) * std::tan(eye_angle_deg(d->desc, k, d->h_jit[k]) * M_PI / 180.0));
+    d->dc.ex_max = 0.0f;
+    for (int k = 0; k < nr; k++) d->dc.ex_max = std::fmax(d->dc.ex_max, std::fabs(d->h_ex[k]));
+}
+
+std::vector<float> view_positions(const lfdpr_display* d) {
+    const int nr = d->dc.nr;
+    std::vector<float> pos(nr);
+    for (int m = 0; m < nr; m++)
+        pos[m] = supersampled(d->desc) ? float((m + 0.5 + double(d->h_jit[m])) / 2.0) : float(m + double(d->h_jit[m]));
+    return pos;
 }
 
 // Validate and upload n_tex textures with their mip chains into one pool.
@@ -330,10 +354,10 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
         return fail(LFDPR_EINVAL, "bias_h, bias_v must be positive and finite");
     if (!(s.lens_pitch_px > 0.0f) || !std::isfinite(s.slant) || !std::isfinite(s.phase_offset))
         return fail(LFDPR_EINVAL, "lens_pitch_px must be positive; slant, phase_offset finite");
-    if (s.recon != 0 && s.recon != 1) return fail(LFDPR_EINVAL, "recon must be 0 or 1");
+    if (s.recon < 0 || s.recon > 3) return fail(LFDPR_EINVAL, "recon must be 0, 1, 2 or 3");
     if (!(s.crosstalk >= 0.0f) || !(s.crosstalk < 0.5f)) return fail(LFDPR_EINVAL, "crosstalk must be in [0, 0.5)");
     if (s.max_points < 0 || s.max_points > 0x7fffffffLL) return fail(LFDPR_EINVAL, "max_points must be in [0, 2^31)");
-    const int nr = s.recon == 1 ? 2 * s.n_views : s.n_views;
+    const int nr = supersampled(s) ? 2 * s.n_views : s.n_views;
     if (nr > kMaxRenderViews) return fail(LFDPR_EINVAL, "too many rendered views");
 
     int ndev = 0;
@@ -378,15 +402,14 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
     c.xtalk = s.crosstalk;
     c.xtalk_c = float(1.0 - 2.0 * double(s.crosstalk));
 
-    d->h_ex.resize(nr);
-    for (int k = 0; k < nr; k++)
-        d->h_ex[k] = float(double(s.view_dist) * std::tan(eye_angle_deg(s, k) * M_PI / 180.0));
-    c.ex_max = 0.0f;
-    for (int k = 0; k < nr; k++) c.ex_max = std::fmax(c.ex_max, std::fabs(d->h_ex[k]));
+    d->h_jit.assign(nr, 0.5f);
+    place_eyes(d);
 
     const uint64_t npix = uint64_t(s.view_w) * s.view_h * nr;
     cudaError_t e;
     if ((e = cudaMalloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&d->d_pos, sizeof(float) * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&d->d_samples, sizeof(float) * 3 * 32)) != cudaSuccess ||
         (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->work, sizeof(WorkRec) * (uint64_t)d->max_points)) != cudaSuccess ||
         (e = cudaMalloc(&d->near, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
@@ -398,7 +421,9 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
         free_display(d);
         return cuda_fail(e, "create_display: cudaMalloc");
     }
+    const std::vector<float> pos = view_positions(d);
     if ((e = cudaMemcpy(d->d_ex, d->h_ex.data(), sizeof(float) * nr, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d->d_pos, pos.data(), sizeof(float) * nr, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(d->ctr, 0, sizeof(Counters))) != cudaSuccess ||
         (e = cudaMemset(d->keys, 0xff, 8u * npix)) != cudaSuccess ||
         (e = cudaMemset(d->views, 0, 4u * npix)) != cudaSuccess) {
@@ -414,6 +439,31 @@ lfdpr_status lfdpr_destroy_display(lfdpr_display* disp) {
     if (!disp) return fail(LFDPR_EINVAL, "destroy_display: null");
     if (disp->n_meshes != 0) return fail(LFDPR_EINVAL, "destroy_display: meshes still alive");
     free_display(disp);
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_view_jitter(lfdpr_display* disp, const float* u, int32_t n) {
+    g_err[0] = 0;
+    if (!disp || !u) return fail(LFDPR_EINVAL, "set_view_jitter: null argument");
+    if (n != disp->dc.nr) return fail(LFDPR_EINVAL, "set_view_jitter: %d values for %d rendered views", n, disp->dc.nr);
+    for (int k = 0; k < n; k++)
+        if (!(u[k] >= 0.0f && u[k] <= 1.0f)) return fail(LFDPR_EINVAL, "set_view_jitter: value %d not in [0, 1]", k);
+    disp->h_jit.assign(u, u + n);
+    place_eyes(disp);
+    const std::vector<float> pos = view_positions(disp);
+    CK(cudaMemcpy(disp->d_ex, disp->h_ex.data(), sizeof(float) * n, cudaMemcpyHostToDevice), "set_view_jitter: eyes");
+    CK(cudaMemcpy(disp->d_pos, pos.data(), sizeof(float) * n, cudaMemcpyHostToDevice), "set_view_jitter: positions");
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_recon_samples(lfdpr_display* disp, const float* samples, int32_t n) {
+    g_err[0] = 0;
+    if (!disp || !samples) return fail(LFDPR_EINVAL, "set_recon_samples: null argument");
+    if (n < 1 || n > 32) return fail(LFDPR_EINVAL, "set_recon_samples: 1..32 samples");
+    for (int k = 0; k < 3 * n; k++)
+        if (!std::isfinite(samples[k])) return fail(LFDPR_EINVAL, "set_recon_samples: non-finite offset");
+    CK(cudaMemcpy(disp->d_samples, samples, sizeof(float) * 3 * n, cudaMemcpyHostToDevice), "set_recon_samples");
+    disp->n_samples = n;
     return LFDPR_OK;
 }
 
@@ -552,7 +602,10 @@ lfdpr_status lfdpr_interleave(lfdpr_display* disp, uint8_t* panel_rgba8, void* s
         cudaGetLastError();
     uint8_t* dst = on_device ? panel_rgba8 : disp->panel;
     mark(disp, LFDPR_N_STAGES, s);
-    CK(launch_interleave(disp->dc, disp->views, dst, s), "launch k_interleave");
+    if ((disp->desc.recon == 2 || disp->desc.recon == 3) && disp->n_samples == 0)
+        return fail(LFDPR_EINVAL, "interleave: Gaussian reconstruction needs lfdpr_set_recon_samples");
+    CK(launch_interleave(disp->dc, disp->views, disp->d_pos, disp->d_samples, disp->n_samples, dst, s),
+       "launch k_interleave");
     disp->launches += 1;
     mark(disp, LFDPR_N_STAGES + 1, s);
     disp->ev_interleave = disp->timing;

@@ -29,6 +29,7 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_destroy_mesh", "lfdpr_render_frame", "lfdpr_interleave", "lfdpr_frame_stats",
            "lfdpr_get_buffers", "lfdpr_view_eyes", "lfdpr_probe_atomic_min", "lfdpr_last_error",
            "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc",
+           "lfdpr_set_view_jitter", "lfdpr_set_recon_samples",
            "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
@@ -100,6 +101,8 @@ def lib() -> C.CDLL:
         L.lfdpr_get_buffers.argtypes = [P, P, C.POINTER(Buffers)]
         L.lfdpr_view_eyes.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_stage_timing.argtypes = [P, C.c_int32]
+        L.lfdpr_set_view_jitter.argtypes = [P, P, C.c_int32]
+        L.lfdpr_set_recon_samples.argtypes = [P, P, C.c_int32]
         L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
                                                   P, C.c_uint32, P, C.c_uint32, P, P, P]
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
@@ -200,6 +203,16 @@ def lfdpr_destroy_mesh(mesh: int):
 def lfdpr_render_frame(disp: int, mesh: int, model: np.ndarray, stream=None):
     m = np.ascontiguousarray(model, np.float32).ravel()
     _check(lib().lfdpr_render_frame(disp, mesh, _ptr(m), _stream(stream)))
+
+
+def lfdpr_set_view_jitter(disp: int, u: np.ndarray):
+    u = np.ascontiguousarray(u, np.float32).ravel()
+    _check(lib().lfdpr_set_view_jitter(disp, _ptr(u), u.size))
+
+
+def lfdpr_set_recon_samples(disp: int, samples: np.ndarray):
+    s = np.ascontiguousarray(samples, np.float32).reshape(-1, 3)
+    _check(lib().lfdpr_set_recon_samples(disp, _ptr(s), s.shape[0]))
 
 
 def lfdpr_interleave(disp: int, panel_ptr: int, stream=None):
@@ -401,6 +414,12 @@ class Renderer:
 
     def interleave(self, panel_ptr: int, stream=None):
         lfdpr_interleave(self.disp, panel_ptr, stream)
+
+    def set_view_jitter(self, u: np.ndarray):
+        lfdpr_set_view_jitter(self.disp, u)
+
+    def set_recon_samples(self, samples: np.ndarray):
+        lfdpr_set_recon_samples(self.disp, samples)
 
     def stats(self, stream=None) -> Stats:
         return lfdpr_frame_stats(self.disp, stream)

@@ -51,7 +51,7 @@ def _torch_gpu():
 
 @pytest.mark.parametrize("field,value", [
     ("n_views", 0), ("n_views", 257), ("view_w", 0), ("near_z", 0.0), ("far_z", 0.05),
-    ("view_dist", -1.0), ("recon", 2), ("crosstalk", 0.5), ("bias_h", 0.0),
+    ("view_dist", -1.0), ("recon", 4), ("recon", -1), ("crosstalk", 0.5), ("bias_h", 0.0),
     ("lens_pitch_px", 0.0), ("panel_w", 0), ("cone_deg", 180.0)])
 def test_invalid_descriptor_rejected_on_host(L, field, value):
     d = replace(scenes.display_tiny(), **{field: value})
