@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["paper", "angular", "tiny", "batch", "learned"], default="paper")
+    p.add_argument("--config", choices=["paper", "angular", "gauss", "tiny", "batch", "learned"], default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
@@ -65,12 +65,18 @@ def parse():
 
 
 def workload(cfg):
+    from dataclasses import replace
     from paper_2601_19901_gb300 import scenes as S
     if cfg == "tiny":
         return S.display_tiny(), S.scene_tiny(), "tiny: 2,048 triangles, 8 views 128x128, 512x512 panel"
     if cfg == "angular":
         return (S.display_angular_ss(), S.scene_paper(),
                 WORKLOAD.replace("48 views", "96 views tent-reconstructed to 48 (+crosstalk 0.15)"))
+    if cfg == "gauss":
+        return (replace(S.display_angular_ss(), recon=2), S.scene_paper(),
+                WORKLOAD.replace("48 views", "96 views at random angles in their intervals, Gaussian "
+                                             "reconstruction (8 samples, spatial diameter 2.25 px, angular "
+                                             "support 2 views) to 48 (+crosstalk 0.15)"))
     return S.display_paper(), S.scene_paper(), WORKLOAD
 
 
@@ -272,6 +278,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     R = lfdpr.Renderer(d, sc, stream=stream)
     R.set_stage_timing(True)
+    if d.recon in (2, 3):
+        # Sec. 4's random angles and Gaussian samples (seeded; sigma = diameter / 4)
+        rng = np.random.default_rng(2024)
+        R.set_view_jitter(rng.random(d.n_render_views).astype(np.float32))
+        R.set_recon_samples((rng.normal(0.0, 1.0, (8, 3)) * [2.25 / 4, 2.25 / 4, 0.5]).astype(np.float32))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
     frames = multigpu.rank_frames(rank, world, args.warmup + args.steps)
@@ -393,7 +404,7 @@ def run_ours(args):
             "clocks": clk}
     if e2e:
         line["e2e"] = e2e
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and d.recon in (0, 1):
         import oracle as O
         O.build()
         views = lfdpr.device_to_numpy(b.views, (d.n_render_views, d.view_h, d.view_w, 4), np.uint8)

@@ -14,7 +14,9 @@
 // k_interleave_gauss is the Gaussian reconstruction of Sec. 4 (recon 2, 3):
 // per subpixel the mean of the caller's samples, each the nearest rendered
 // view to the subpixel's phase plus the sample's angular offset at the view
-// pixel holding its spatially offset position (gathers, so no row staging).
+// pixel holding its spatially offset position. It is bound by its nearest-view
+// searches (72 per pixel with crosstalk), not by the gathers (L1 / L2 hits):
+// staging bands of views in shared memory measured slower.
 #include "lfdpr_internal.cuh"
 
 namespace lfdpr {
@@ -170,37 +172,80 @@ __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* 
     }
 }
 
-// Gaussian reconstruction at phase phi, channel ch, panel pixel (x, y): the
-// mean over the samples of the rendered view nearest phi + dphi (positions
-// pos[], ties to the later view) at the view pixel holding (vx + dx, vy + dy)
-// (clamped), vx = (x + 1/2) W / Wp, vy = (y + 1/2) H / Hp.
-__device__ __forceinline__ float gauss_value(const DispConst& c, const uint8_t* __restrict__ views, const float* pos,
-                                             const float* smp, int ns, float phi, float vx, float vy, int ch) {
+// Rendered view nearest a on the display-view axis (positions pos[], ties to
+// the later view), from the window of four views around it.
+__device__ __forceinline__ int nearest_view(const float* pos, int nr, float r, float a) {
+    int lo = int(floorf(r * a)) - 2;
+    lo = lo > nr - 4 ? nr - 4 : lo;
+    lo = lo < 0 ? 0 : lo;
+    const int hi = lo + 3 < nr - 1 ? lo + 3 : nr - 1;
+    int m = lo;
+    float best = fabsf(pos[lo] - a);
+#pragma unroll
+    for (int q = 1; q < 4; q++) {
+        if (lo + q > hi) break;
+        const float dq = fabsf(pos[lo + q] - a);
+        if (dq <= best) {
+            best = dq;
+            m = lo + q;
+        }
+    }
+    return m;
+}
+
+// Panel pixel (x, y) under Gaussian reconstruction (+ crosstalk): for each
+// channel the mean over the samples of the rendered view nearest phi + dphi
+// at the view pixel holding (vx + dx, vy + dy), clamped; with crosstalk the
+// same at phi - 1 and phi + 1 (wrapping) mixed in. The samples are the outer
+// loop (each sample's pixel is found once); each of the nine sums still adds
+// its samples in order.
+__device__ __forceinline__ uint32_t gauss_pixel(const DispConst& c, const uint32_t* __restrict__ v32, const float* pos,
+                                                const float* smp, int ns, int x, int y, float sxw, float syh) {
     const int nr = c.nr, W = c.W, H = c.H;
     const uint64_t npix = (uint64_t)W * H;
-    const float r = float(nr / c.n_views);
-    float acc = 0.0f;
+    const float r = float(nr / c.n_views), N = float(c.n_views);
+    const float vx = (float(x) + 0.5f) * sxw, vy = (float(y) + 0.5f) * syh;
+    const bool xt = c.xtalk > 0.0f;
+    float phi[3][3];   // [channel][own, -1, +1]
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const float p0 = subpixel_phase(c, x, y, ch);
+        float pm = p0 - 1.0f, pp = p0 + 1.0f;
+        if (pm < 0.0f) pm += N;
+        if (pp >= N) pp -= N;
+        phi[ch][0] = p0;
+        phi[ch][1] = pm;
+        phi[ch][2] = pp;
+    }
+    float acc[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     for (int s = 0; s < ns; s++) {
-        const float a = phi + smp[3 * s + 2];
-        int lo = int(floorf(r * a)) - 2;
-        lo = lo > nr - 4 ? nr - 4 : lo;
-        lo = lo < 0 ? 0 : lo;
-        const int hi = lo + 3 < nr - 1 ? lo + 3 : nr - 1;
-        int m = lo;
-        float best = fabsf(pos[lo] - a);
-        for (int q = lo + 1; q <= hi; q++) {
-            const float dq = fabsf(pos[q] - a);
-            if (dq <= best) {
-                best = dq;
-                m = q;
-            }
-        }
         int px = int(floorf(vx + smp[3 * s])), py = int(floorf(vy + smp[3 * s + 1]));
         px = px < 0 ? 0 : (px >= W ? W - 1 : px);
         py = py < 0 ? 0 : (py >= H ? H - 1 : py);
-        acc += float(__ldg(views + ((uint64_t)m * npix + (uint64_t)py * W + px) * 4u + ch));
+        const uint32_t* row = v32 + (uint64_t)py * W + px;
+        const float dphi = smp[3 * s + 2];
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k > 0 && !xt) continue;
+                const int m = nearest_view(pos, nr, r, phi[ch][k] + dphi);
+                acc[ch][k] += float((__ldg(row + (uint64_t)m * npix) >> (8 * ch)) & 255u);
+            }
     }
-    return acc / float(ns);
+    uint32_t o = 0xff000000u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float v = acc[ch][0] / float(ns);
+        if (xt) {
+            float t = v * c.xtalk_c;
+            t = fmaf(c.xtalk, acc[ch][1] / float(ns), t);
+            t = fmaf(c.xtalk, acc[ch][2] / float(ns), t);
+            v = t;
+        }
+        o |= uint32_t(round_u8(v)) << (8 * ch);
+    }
+    return o;
 }
 
 __global__ void __launch_bounds__(256) k_interleave_gauss(DispConst c, const uint8_t* __restrict__ views,
@@ -212,39 +257,13 @@ __global__ void __launch_bounds__(256) k_interleave_gauss(DispConst c, const uin
     for (int i = threadIdx.x; i < c.nr; i += blockDim.x) s_pos[i] = pos[i];
     for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) s_smp[i] = samples[i];
     __syncthreads();
-    const int groups_x = (c.Wp + 3) >> 2;
-    const uint64_t total = (uint64_t)groups_x * c.Hp;
+    const uint64_t total = (uint64_t)c.Wp * c.Hp;
     const float sxw = float(c.W) / float(c.Wp), syh = float(c.H) / float(c.Hp);
-    const float N = float(c.n_views);
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        const int y = int(g / groups_x);
-        const int xg = int(g - (uint64_t)y * groups_x) * 4;
-        const float vy = (float(y) + 0.5f) * syh;
-        uint32_t px[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int x = min(xg + e, c.Wp - 1);
-            const float vx = (float(x) + 0.5f) * sxw;
-            uint32_t o = 0xff000000u;
-#pragma unroll
-            for (int ch = 0; ch < 3; ch++) {
-                const float phi = subpixel_phase(c, x, y, ch);
-                float v = gauss_value(c, views, s_pos, s_smp, ns, phi, vx, vy, ch);
-                if (c.xtalk > 0.0f) {
-                    float pm = phi - 1.0f, pp = phi + 1.0f;
-                    if (pm < 0.0f) pm += N;
-                    if (pp >= N) pp -= N;
-                    float acc = v * c.xtalk_c;
-                    acc = fmaf(c.xtalk, gauss_value(c, views, s_pos, s_smp, ns, pm, vx, vy, ch), acc);
-                    acc = fmaf(c.xtalk, gauss_value(c, views, s_pos, s_smp, ns, pp, vx, vy, ch), acc);
-                    v = acc;
-                }
-                o |= uint32_t(round_u8(v)) << (8 * ch);
-            }
-            px[e] = o;
-        }
-        store4(c, panel, xg, y, px);
+    const uint32_t* v32 = reinterpret_cast<const uint32_t*>(views);
+    for (uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+         gi += (uint64_t)gridDim.x * blockDim.x) {
+        const int y = int(gi / c.Wp), x = int(gi - (uint64_t)y * c.Wp);
+        reinterpret_cast<uint32_t*>(panel)[gi] = gauss_pixel(c, v32, s_pos, s_smp, ns, x, y, sxw, syh);
     }
 }
 
@@ -255,12 +274,12 @@ cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const f
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (dc.recon == 2 || dc.recon == 3) {
         if (n_samples < 1 || n_samples > 32) return cudaErrorInvalidValue;
-        k_interleave_gauss<<<sms * 8, 256, 0, s>>>(dc, views, pos, samples, n_samples, panel);
+        k_interleave_gauss<<<sms * 16, 256, 0, s>>>(dc, views, pos, samples, n_samples, panel);
         return cudaGetLastError();
     }
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // widest source segment of a tile: (kTileCols - 1) W / Wp + 2 pixels
     const int64_t seg = ((int64_t)(kTileCols - 1) * dc.W) / dc.Wp + 2;
     const int64_t bytes = (int64_t)dc.nr * seg * 4;
