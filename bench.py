@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["paper", "angular", "gauss", "tiny", "batch", "learned"], default="paper")
+    p.add_argument("--config", choices=["paper", "angular", "gauss", "gauss2x", "tiny", "batch", "learned"],
+                   default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
@@ -72,6 +73,12 @@ def workload(cfg):
     if cfg == "angular":
         return (S.display_angular_ss(), S.scene_paper(),
                 WORKLOAD.replace("48 views", "96 views tent-reconstructed to 48 (+crosstalk 0.15)"))
+    if cfg == "gauss2x":
+        d = S.display_angular_ss()
+        return (replace(d, recon=2, view_w=2 * d.view_w, view_h=2 * d.view_h), S.scene_paper(),
+                WORKLOAD.replace("48 views over 40 deg at 420x560", "96 views at 840x1120 (2x spatial and 2x "
+                                 "angular supersampling, random angles), Gaussian reconstruction (8 samples) to 48 "
+                                 "views over 40 deg at 420x560 (+crosstalk 0.15)"))
     if cfg == "gauss":
         return (replace(S.display_angular_ss(), recon=2), S.scene_paper(),
                 WORKLOAD.replace("48 views", "96 views at random angles in their intervals, Gaussian "
@@ -276,13 +283,15 @@ def run_ours(args):
 
     d, sc, wl = workload(args.config)
     stream = torch.cuda.Stream()
-    R = lfdpr.Renderer(d, sc, stream=stream)
+    R = lfdpr.Renderer(d, sc, max_points=(1 << 24) if args.config == "gauss2x" else 0, stream=stream)
     R.set_stage_timing(True)
     if d.recon in (2, 3):
-        # Sec. 4's random angles and Gaussian samples (seeded; sigma = diameter / 4)
+        # Sec. 4's random angles and Gaussian samples (seeded; sigma = diameter / 4, in output
+        # pixels: view pixels times the spatial supersampling factor)
+        ss = 2.0 if args.config == "gauss2x" else 1.0
         rng = np.random.default_rng(2024)
         R.set_view_jitter(rng.random(d.n_render_views).astype(np.float32))
-        R.set_recon_samples((rng.normal(0.0, 1.0, (8, 3)) * [2.25 / 4, 2.25 / 4, 0.5]).astype(np.float32))
+        R.set_recon_samples((rng.normal(0.0, 1.0, (8, 3)) * [ss * 2.25 / 4, ss * 2.25 / 4, 0.5]).astype(np.float32))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
     frames = multigpu.rank_frames(rank, world, args.warmup + args.steps)
