@@ -46,6 +46,22 @@ __device__ __forceinline__ bool seen_by(const DispConst& c, float e, const float
     return !(out_l || out_r);
 }
 
+// The eye whose x is nearest `target` (eyes ascending in x): binary search
+// for the first eye at or beyond it, then the nearer of it and the one
+// before (the earlier on a tie). Only a starting guess for the searches
+// below: culling and the closest / farthest eye do not depend on it.
+__device__ __forceinline__ int nearest_eye(const float* __restrict__ ex, int nr, float target) {
+    int lo = 0, hi = nr;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ex[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo == 0) return 0;
+    if (lo == nr) return nr - 1;
+    return fabsf(ex[lo] - target) < fabsf(ex[lo - 1] - target) ? lo : lo - 1;
+}
+
 __device__ bool culled(const DispConst& c, const float* __restrict__ ex, const float P[3][3]) {
     bool out_t = true, out_b = true, out_n = true, out_f = true;
 #pragma unroll
@@ -65,12 +81,7 @@ __device__ bool culled(const DispConst& c, const float* __restrict__ ex, const f
     const float cx = (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f);
     const float cz = (P[0][2] + P[1][2] + P[2][2]) * (1.0f / 3.0f);
     const float target = fabsf(cz) > 1e-6f ? __fdividef(cx * c.D, cz) : 0.0f;
-    int vb = 0;
-    float best = INFINITY;
-    for (int v = 0; v < c.nr; v++) {
-        const float dx = fabsf(ex[v] - target);
-        if (dx < best) { best = dx; vb = v; }
-    }
+    const int vb = nearest_eye(ex, c.nr, target);
     if (seen_by(c, ex[vb], P)) return false;
     for (int v = 0; v < c.nr; v++)
         if (seen_by(c, ex[v], P)) return false;
@@ -215,15 +226,7 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
                        seg_dist2(a2, b2, 0.0f, 0.0f, ie20, qu, qv));
         return fmaf(h, h, d2);
     };
-    int vs = 0;
-    {
-        const float cxw = (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f);
-        float best = INFINITY;
-        for (int v = 0; v < c.nr; v++) {
-            const float dx = fabsf(a.ex[v] - cxw);
-            if (dx < best) { best = dx; vs = v; }
-        }
-    }
+    const int vs = nearest_eye(a.ex, c.nr, (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f));
     float d2min = exact_d2(vs), d2max = d2min;
     {
         const float e0 = exact_d2(0), e1 = exact_d2(c.nr - 1);
