@@ -355,7 +355,7 @@ __device__ __forceinline__ T block_sum(T v, T* smem) {
     return tot;   // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kSetupThreads) k_setup(FrameArgs a) {
+__global__ void __launch_bounds__(kSetupThreads, 4) k_setup(FrameArgs a) {
     __shared__ uint32_t s_cnt[kSetupThreads / 32];
     __shared__ uint32_t s_live[kSetupThreads / 32];
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
