@@ -17,10 +17,12 @@
  * then a 1x1 convolution to 3 * 4n channels added to the linear angular
  * interpolation of the input views (input j at output index 4j + 3/2,
  * clamped at the ends), clamped to [0, 1], times 255, rounded half to even.
- * Activations and weights are bf16 with fp32 accumulation (tensor cores);
+ * Activations and weights are bf16 with fp32 accumulation on the tensor
+ * cores (tcgen05.mma, accumulators in tensor memory, operands staged by TMA);
  * the 1x1 layer and the angular interpolation run as one product over
  * [features (32), input channels (48)] (the interpolation weights 0, 1/8,
- * 3/8, 5/8, 7/8, 1 are exact in bf16).
+ * 3/8, 5/8, 7/8, 1 are exact in bf16). Activations are held as images with
+ * a one-pixel ring of zeros (the 3x3 padding), channels in chunks of eight.
  *
  * 3x3 layers in order, (input channels, output channels):
  *   (48,32) (32,32) | (32,64) (64,64) | (64,128) (128,128) | (128,256) (256,256)
@@ -70,13 +72,25 @@ lfdpr_status lfdpr_recon_run(lfdpr_recon *recon, const lfdpr_display *src, lfdpr
 lfdpr_status lfdpr_recon_forward(lfdpr_recon *recon, const uint8_t *in_views, uint8_t *out_views, void *stream);
 
 /*
+ * lfdpr_recon_status: the failed-wait flags the network's kernels recorded
+ * since the last call (0 = none; bit 0: a copy never landed, bit 1: a stage
+ * never arrived at the MMA thread, bit 2: the accumulators never completed;
+ * each such wait gives up after one second and its block still returns).
+ * Synchronous: waits for the device, then clears the flags.
+ */
+lfdpr_status lfdpr_recon_status(lfdpr_recon *recon, int32_t *flags);
+
+/*
  * lfdpr_conv3x3_bf16: one 3x3 layer of the network (test hook): in bf16
  * [H][W][cin], wgt bf16 [cout][3][3][cin], bias f32 [cout], out bf16
- * [H][W][cout], zero padding 1, + bias, ReLU if relu; cin % 16 == 0,
- * cout % 32 == 0; device buffers, 16-byte aligned.
+ * [H][W][cout]: zero padding 1, + bias, ReLU, on the network's tensor-core
+ * kernel (the hook converts to and from the network's activation layout).
+ * cin % 16 == 0 (<= 512), cout % 32 == 0 (<= 256); device buffers, 16-byte
+ * aligned; status: a device int32 that receives the failed-wait flags
+ * (OR-ed in, as lfdpr_recon_status describes). Asynchronous on `stream`.
  */
 lfdpr_status lfdpr_conv3x3_bf16(const void *in, int32_t H, int32_t W, int32_t cin, const void *wgt,
-                                const float *bias, void *out, int32_t cout, int32_t relu, void *stream);
+                                const float *bias, void *out, int32_t cout, int32_t *status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1,27 +1,53 @@
-// Learned angular reconstruction: the U-Net's layers as BF16 tensor-core
-// kernels with FP32 accumulation (activations NHWC bf16, channels padded to
-// multiples of 16).
+// Learned angular reconstruction: the U-Net's layers on the 5th-generation
+// tensor cores (tcgen05: BF16 operands in shared memory, FP32 accumulators in
+// tensor memory), operands staged by TMA.
 //
-//   k_conv3x3     3x3 convolution, stride 1, zero padding 1, + bias, ReLU:
-//                 implicit GEMM (pixels x output channels x 9 Cin). A block
-//                 takes 8 rows x 32 pixels x 64 (or 32) output channels; per
-//                 chunk of 16 input channels it stages (cp.async, two stages,
-//                 so copies overlap the MMAs) the 10 x 34 pixel halo tile and
-//                 the 64 x 9 x 16 weights in shared memory, and each warp
-//                 (one row, two m16 tiles) runs ldmatrix + mma.m16n8k16 over
-//                 the 9 taps, reading the tap-shifted pixel rows straight
-//                 from the halo tile.
-//   k_avgpool2    2x2 average pooling.
-//   k_up2_concat  nearest 2x upsampling of one tensor concatenated (along
-//                 channels) with another of the upsampled size.
-//   k_recon_in    12 rendered views RGBA8 -> the network input (36 channels
-//                 of [0, 1] values, zero padded to 48 channels and to a
-//                 width divisible by 8).
-//   k_recon_out   the 1x1 output layer plus the fixed angular interpolation
-//                 of the input views as one tensor-core GEMM per 16 pixels,
-//                 clamped and rounded to the 48 output views RGBA8.
+// Activation layout. Every activation of resolution level l is a bordered
+// image of (Hl + 2) x (Wl + 2) positions q = y (Wl + 2) + x: the level's
+// Hl x Wl image with a ring of zeros, which is the 3x3 convolution's zero
+// padding. The tap (dy, dx) of a 3x3 convolution is then the constant offset
+// dy (Wl + 2) + dx, so an output tile of 128 consecutive positions reads, for
+// every tap, 128 consecutive input positions: one contiguous span of the
+// input holds the operands of all nine taps. Channels are stored in chunks
+// of eight, [C / 8][Qp][8] bf16 (Qp = the positions rounded up to 32), so a
+// chunk's span is one contiguous run of 16-byte rows: exactly the K-major
+// core-matrix layout (8 positions x 8 channels = 128 contiguous bytes) the
+// MMAs read, copied by TMA as one box of 512-byte rows (32 positions each).
+//
+//   k_conv_tc<0>  3x3 convolution + bias + ReLU as an implicit GEMM
+//                 (M = positions, N = output channels, K = 9 x input
+//                 channels). A block takes R x 128 positions and NT output
+//                 channels. Per K step of 16 input channels one thread issues
+//                 TMA copies of the input span (one box per 8-channel chunk,
+//                 starting at the 32-position row at or before the span) and
+//                 of the step's packed weights into a pipeline stage; another
+//                 issues tcgen05.mma (M 128, N NT, K 16) for the nine taps x R
+//                 row groups with shared-memory descriptors offset by the tap's
+//                 shift; tcgen05.commit frees the stage when its MMAs are
+//                 done. The four warps then read the accumulators back
+//                 (tcgen05.ld), add the bias, apply ReLU and store bf16, with
+//                 zeros on the border ring, one 16-byte store per chunk.
+//   k_conv_tc<1>  the output layer: a 1x1 product over [d0 (32 channels) |
+//                 x0 (48 input channels)] that gives the 1x1 convolution
+//                 plus the fixed angular interpolation of the input views,
+//                 clamped, scaled to 255, rounded half to even, written as
+//                 RGBA8 output views.
+//   k_pack_w      weights [cout][taps][cin] -> the per-K-step stage images
+//                 [n tile][K step][tap][2][NT][8] the MMAs read.
+//   k_avgpool2, k_up2_concat, k_recon_in   pooling, upsampling + skip
+//                 concatenation and the input packing, between chunked
+//                 bordered tensors (interiors only; the borders stay zero).
+//   k_to_chunked, k_from_chunked   plain NHWC <-> chunked bordered (test hook).
+//
+// Every wait (mbarrier phases) gives up after 2e9 SM cycles (about one
+// second): the block records
+// the failure in a status word, waits (again bounded) for its own copies and
+// MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -32,336 +58,654 @@
 namespace lfdpr {
 namespace {
 
-constexpr int kConvTH = 8;           // tile rows (one warp each)
-constexpr int kConvTW = 32;          // tile pixels per row (two m16 tiles)
-constexpr int kConvCK = 16;          // input channels per chunk
-constexpr int kConvRow = kConvCK + 8;  // smem row stride (elements): 48 B, conflict-free ldmatrix rows
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA / mbarrier building blocks (inline PTX)
+// ---------------------------------------------------------------------------
+namespace tc {
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
+// A wait gives up after this many SM clock cycles (about one second).
+constexpr long long kWaitCycles = 2000000000ll;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t par) {
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(par)
+                 : "memory");
+    return ok != 0;
 }
 
-__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// 16-byte global -> shared copy that bypasses L1 (cp.async); src_bytes 0
-// fills the 16 bytes with zeros without reading src.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N));
-}
-
-// in [H][W][Cin], wgt [Cout][9][Cin] (tap = 3 dy + dx), bias [Cout] f32,
-// out [H][W][Cout]; Cin % 16 == 0, Cout % CO == 0 (CO = 32 or 64 output
-// channels per block). Grid (ceil(W/32), ceil(H/8), Cout/CO), 256 threads,
-// dynamic shared memory conv_smem_bytes(CO): two stages of (halo tile,
-// weights) so the next chunk's copies run during this chunk's MMAs.
-template <int CO>
-__global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ in, int H, int W, int Cin,
-                                                 const __nv_bfloat16* __restrict__ wgt,
-                                                 const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
-                                                 int Cout, int relu) {
-    constexpr int HP = kConvTH + 2, WP = kConvTW + 2;
-    constexpr int NT = CO / 8;                               // n8 tiles per warp
-    constexpr int IN_ELEMS = HP * WP * kConvRow, W_ELEMS = CO * 9 * kConvRow;
-    constexpr int STAGE = IN_ELEMS + W_ELEMS;                // elements per stage
-    extern __shared__ __align__(16) __nv_bfloat16 smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * kConvTW, y0 = blockIdx.y * kConvTH, n0 = blockIdx.z * CO;
-    float acc[2][NT][4];
-#pragma unroll
-    for (int m = 0; m < 2; m++)
-#pragma unroll
-        for (int t = 0; t < NT; t++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc[m][t][q] = 0.0f;
-
-    const uint32_t s_base = uint32_t(__cvta_generic_to_shared(smem));
-    // ldmatrix row addresses of this lane: A (pixels) and B (output channels)
-    const int a_row = (lane & 7) + 8 * ((lane >> 3) & 1), a_k = 8 * (lane >> 4);
-    const int b_row = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
-
-    // copies of channel chunk c0 into stage st
-    auto stage_copy = [&](int c0, int st) {
-        const uint32_t s_in = s_base + uint32_t(st * STAGE * 2), s_w = s_in + uint32_t(IN_ELEMS * 2);
-        for (int idx = tid; idx < HP * WP * 2; idx += 256) {
-            const int p = idx >> 1, part = idx & 1;
-            const int gy = y0 + p / WP - 1, gx = x0 + p % WP - 1;
-            const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const __nv_bfloat16* src = ok ? in + ((size_t)gy * W + gx) * Cin + c0 + 8 * part : in;
-            cp_async16(s_in + uint32_t((p * kConvRow + 8 * part) * 2), src, ok ? 16u : 0u);
-        }
-        for (int idx = tid; idx < CO * 9 * 2; idx += 256) {
-            const int row = idx >> 1, part = idx & 1;   // row = co * 9 + tap
-            const int co = row / 9, tap = row - 9 * co;
-            cp_async16(s_w + uint32_t((row * kConvRow + 8 * part) * 2),
-                       wgt + ((size_t)(n0 + co) * 9 + tap) * Cin + c0 + 8 * part, 16u);
-        }
-        cp_async_commit();
-    };
-
-    const int n_chunks = Cin / kConvCK;
-    stage_copy(0, 0);
-    for (int ch = 0; ch < n_chunks; ch++) {
-        if (ch + 1 < n_chunks) {
-            stage_copy((ch + 1) * kConvCK, (ch + 1) & 1);
-            cp_async_wait<1>();   // this chunk's group has landed
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const uint32_t s_in_a = s_base + uint32_t((ch & 1) * STAGE * 2), s_w_a = s_in_a + uint32_t(IN_ELEMS * 2);
-#pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-            uint32_t a[2][4];
-#pragma unroll
-            for (int m = 0; m < 2; m++) {
-                const int p = (warp + dy) * WP + 16 * m + a_row + dx;
-                ldmatrix_x4(s_in_a + uint32_t((p * kConvRow + a_k) * 2), a[m][0], a[m][1], a[m][2], a[m][3]);
-            }
-#pragma unroll
-            for (int t2 = 0; t2 < NT / 2; t2++) {
-                uint32_t b0, b1, b2, b3;
-                const int row = (16 * t2 + b_row) * 9 + tap;
-                ldmatrix_x4(s_w_a + uint32_t((row * kConvRow + b_k) * 2), b0, b1, b2, b3);
-#pragma unroll
-                for (int m = 0; m < 2; m++) {
-                    mma_bf16(acc[m][2 * t2], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
-                    mma_bf16(acc[m][2 * t2 + 1], a[m][0], a[m][1], a[m][2], a[m][3], b2, b3);
-                }
-            }
-        }
-        __syncthreads();   // the stage is refilled two chunks later
+// Wait until the phase of parity `par` of the mbarrier at `bar` completes;
+// false after kWaitCycles. The clock is read only once the phase is found
+// incomplete.
+__device__ __forceinline__ bool wait(uint32_t bar, uint32_t par) {
+    if (try_wait(bar, par)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (try_wait(bar, par)) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
     }
-    // epilogue: bias, ReLU, bf16 pairs
-    const int y = y0 + warp;
-    if (y >= H) return;
+}
+
+__device__ __forceinline__ void init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// TMA: one box of a 3-D tensor map at coordinates (x, y, z) -> shared memory.
+__device__ __forceinline__ void load_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void load_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: core matrices of 8
+// rows x 16 bytes (128 contiguous bytes); `lbo` = byte distance between core
+// matrices adjacent in K, `sbo` = between core matrices adjacent in M (N).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A[a] B[b]^T; accumulate into D when acc != 0.
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// The mbarrier at `bar` receives one arrival when every MMA this thread has
+// issued so far is complete.
+__device__ __forceinline__ void commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes (one lane
+// per thread). The load and its wait are one statement, so no register is
+// read before the asynchronous load has written it.
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
-    for (int m = 0; m < 2; m++)
-#pragma unroll
-        for (int t = 0; t < NT; t++) {
-            const int co = n0 + 8 * t + 2 * (lane & 3);
-            const float b0 = bias[co], b1 = bias[co + 1];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int x = x0 + 16 * m + (lane >> 2) + 8 * h;
-                if (x >= W) continue;
-                float v0 = acc[m][t][2 * h] + b0, v1 = acc[m][t][2 * h + 1] + b1;
-                if (relu) {
-                    v0 = fmaxf(v0, 0.0f);
-                    v1 = fmaxf(v1, 0.0f);
-                }
-                *reinterpret_cast<__nv_bfloat162*>(out + ((size_t)y * W + x) * Cout + co) = __floats2bfloat162_rn(v0, v1);
-            }
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// The tensor-core layer
+// ---------------------------------------------------------------------------
+
+// Warp roles of the persistent layer kernel: warp 0 issues the copies, warp 1
+// the MMAs, warps 2-5 drain the accumulators (warp w reads tensor-memory lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, so the four cover the 128 rows of a tile).
+constexpr int kTcThreads = 192;
+
+// Geometry of one tensor-core layer launch (host-computed).
+struct TcGeom {
+    int Hb, Wb, Q;            // bordered rows, columns, positions Hb Wb
+    int taps;                 // 9 (3x3) or 1 (1x1)
+    int NT, R;                // output channels per tile; 128-position row groups per tile
+    int ksteps;               // K steps of 16 input channels
+    int split;                // 8-channel chunks read through map a (the rest through map b)
+    int rows, span;           // TMA box rows of 32 positions per chunk; span = 32 rows positions in shared memory
+    int Qp;                   // positions per chunk in memory (Q rounded up to 32)
+    int stages;               // pipeline depth
+    uint32_t a_bytes, b_bytes, stage_bytes;
+    uint32_t tmem_cols;       // power of two >= 2 R NT (two accumulator buffers)
+    int m_tiles, n_tiles;     // tiles: ceil(Q / 128 R) position tiles x output-channel tiles
+    int cout;                 // channels of the bf16 output tensor (3x3 layers)
+    int nout, H, W;           // output layer: views written, view size
+};
+
+// A wait that also gives up as soon as another role of the block has given
+// up (the abort word in shared memory), and sets that word when it times out.
+// `backoff_ns` > 0 sleeps between polls (for waits off the critical path, so
+// polling does not compete with the copies for the shared-memory pipe).
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t par, uint32_t abort_addr,
+                                              unsigned backoff_ns = 0) {
+    if (tc::try_wait(bar, par)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (backoff_ns) __nanosleep(backoff_ns);
+        if (tc::try_wait(bar, par)) return true;
+        uint32_t ab;
+        asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(ab) : "r"(abort_addr));
+        if (ab) return false;
+        if (clock64() - t0 > tc::kWaitCycles) {
+            asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(abort_addr), "r"(1u));
+            return false;
         }
+    }
 }
 
-constexpr size_t conv_smem_bytes(int co) {
-    return size_t(2) * (size_t((kConvTH + 2) * (kConvTW + 2) * kConvRow) + size_t(co * 9 * kConvRow)) * 2;
+constexpr int kMaxStages = 8;
+
+// Shared memory: [stages x (A span: 2 chunks x span x 16 B | B: taps x 2 x NT x 16 B)]
+// then the barriers: full[8] +0, empty[8] +64, acc_full[2] +128, acc_empty[2]
+// +144, drain +160, tensor-memory address +168, abort word +172.
+// Tile t (t = blockIdx.x, + gridDim.x, ...) covers positions (t % m_tiles) 128 R
+// .. + 128 R - 1 and output channels (t / m_tiles) NT .. + NT - 1; its
+// accumulators live in tensor-memory buffer (local tile index) % 2.
+template <int EPI, int TAPS, int R>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap ma,
+                                                           const __grid_constant__ CUtensorMap mb,
+                                                           const uint8_t* __restrict__ wpk,
+                                                           const float* __restrict__ bias, void* __restrict__ out,
+                                                           const TcGeom g, int* __restrict__ status) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t s0 = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bars = s0 + uint32_t(g.stages) * g.stage_bytes;
+    const uint32_t empty = bars + 64, acc_full = bars + 128, acc_empty = bars + 144, drain = bars + 160,
+                   slot = bars + 168, abort_w = bars + 172;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = g.m_tiles * g.n_tiles;
+    const uint32_t acc_cols = uint32_t(R * g.NT);
+
+    if (tid == 0) {
+        for (int s = 0; s < g.stages; s++) {
+            tc::init(bars + 8 * s, 1);
+            tc::init(empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::init(acc_full + 8 * b, 1);
+            tc::init(acc_empty + 8 * b, 4);   // one arrival per epilogue warp
+        }
+        tc::init(drain, 1);
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_w), "r"(0u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                     "r"(g.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot));
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: the block's K steps, tile after tile, into stage kc % stages
+            int kc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int q0 = (t % g.m_tiles) * 128 * R, nt = t / g.m_tiles;
+                const int qs = q0 - (TAPS == 9 ? g.Wb + 1 : 0);
+                const int y0 = (qs >= 0 ? qs : qs - 31) / 32;   // the 32-position row holding the span's start
+                const uint8_t* wsrc = wpk + size_t(nt) * g.ksteps * g.b_bytes;
+                for (int ks = 0; ks < g.ksteps; ks++, kc++) {
+                    const int s = kc % g.stages;
+                    if (kc >= g.stages && !wait_or_abort(empty + 8 * s, uint32_t((kc / g.stages - 1) & 1), abort_w)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t a = s0 + uint32_t(s) * g.stage_bytes, b = a + g.a_bytes, full = bars + 8 * s;
+                    tc::expect_tx(full, g.a_bytes + g.b_bytes);
+                    // both 8-channel chunks of the K step in one box (chunk pairs never straddle the maps)
+                    const int c8 = 2 * ks;
+                    tc::load_box(a, c8 < g.split ? &ma : &mb, 0, y0, c8 < g.split ? c8 : c8 - g.split, full);
+                    tc::load_bulk(b, wsrc + size_t(ks) * g.b_bytes, g.b_bytes, full);
+                }
+            }
+            // the copies issued last on each stage have landed before the block moves on
+            for (int k = max(0, kc - g.stages); k < kc; k++)
+                tc::wait(bars + 8 * (k % g.stages), uint32_t((k / g.stages) & 1));
+            if (!ok) atomicOr(status, 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer. Descriptors are built once per stage; taps and row groups
+            // move the start address by whole 16-byte units (one position), added to
+            // the 14-bit address field (shared addresses stay below 256 KB, so the
+            // field never carries).
+            const uint32_t idesc = tc::idesc_bf16(128, g.NT);
+            uint32_t toff[TAPS];
+#pragma unroll
+            for (int tp = 0; tp < TAPS; tp++) toff[tp] = TAPS == 9 ? uint32_t((tp / 3) * g.Wb + (tp % 3)) : 0u;
+            const uint64_t a_desc0 = tc::sdesc(s0, uint32_t(g.span * 16), 128);
+            const uint64_t b_desc0 = tc::sdesc(s0 + g.a_bytes, uint32_t(g.NT * 16), 128);
+            const uint32_t b_tap = uint32_t(2 * g.NT);   // 16-byte units between taps' weights
+            int kc = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, it++) {
+                const int q0 = (t % g.m_tiles) * 128 * R;
+                const int qs = q0 - (TAPS == 9 ? g.Wb + 1 : 0);
+                const uint32_t delta = uint32_t(qs - 32 * ((qs >= 0 ? qs : qs - 31) / 32));   // span start in its first row
+                const int buf = it & 1;
+                // the epilogue has drained this buffer (its use two tiles ago)
+                if (it >= 2 && !wait_or_abort(acc_empty + 8 * buf, uint32_t((it / 2 - 1) & 1), abort_w)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t dacc = tmem + uint32_t(buf) * acc_cols;
+                for (int ks = 0; ks < g.ksteps; ks++, kc++) {
+                    const int s = kc % g.stages;
+                    if (!wait_or_abort(bars + 8 * s, uint32_t((kc / g.stages) & 1), abort_w)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t st16 = (uint32_t(s) * g.stage_bytes) >> 4;
+                    const uint64_t ad = a_desc0 + st16 + delta, bd = b_desc0 + st16;
+#pragma unroll
+                    for (int tp = 0; tp < TAPS; tp++)
+#pragma unroll
+                        for (int r = 0; r < R; r++)
+                            tc::mma(dacc + uint32_t(r * g.NT), ad + toff[tp] + uint32_t(r * 128), bd + tp * b_tap, idesc,
+                                    uint32_t(ks | tp));
+                    tc::commit(empty + 8 * s);
+                }
+                if (ok) tc::commit(acc_full + 8 * buf);
+            }
+            // every MMA issued has completed before the block moves on
+            tc::commit(drain);
+            tc::wait(drain, 0);
+            if (!ok) atomicOr(status, 2);
+        }
+    } else {
+        // epilogue warps
+        const int lq = warp & 3;   // tensor-memory lane quarter
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, it++) {
+            const int q0 = (t % g.m_tiles) * 128 * R, n0 = (t / g.m_tiles) * g.NT;
+            const int buf = it & 1;
+            // one lane per warp polls (with backoff); the others wait at the shuffle
+            int got = 0;
+            if (lane == 0) got = wait_or_abort(acc_full + 8 * buf, uint32_t((it / 2) & 1), abort_w, 128) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+            if (!ok) break;
+            tc::fence_after();
+            const uint32_t trow = tmem + (uint32_t(lq * 32) << 16) + uint32_t(buf) * acc_cols;
+            for (int r = 0; r < R; r++) {
+                const int q = q0 + r * 128 + lq * 32 + lane;
+                const int y = q / g.Wb, x = q - y * g.Wb;
+                if (EPI == 0) {
+                    const bool border = y == 0 || y >= g.Hb - 1 || x == 0 || x == g.Wb - 1;
+                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + size_t(q) * 8;
+                    for (int j = 0; j < g.NT; j += 32) {
+                        float v[32];
+                        tc::ld16(trow + uint32_t(r * g.NT + j), v);
+                        tc::ld16(trow + uint32_t(r * g.NT + j + 16), v + 16);
+                        uint4 pk[4];
+                        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            const float a0 = border ? 0.0f : fmaxf(v[2 * i] + __ldg(bias + n0 + j + 2 * i), 0.0f);
+                            const float a1 =
+                                border ? 0.0f : fmaxf(v[2 * i + 1] + __ldg(bias + n0 + j + 2 * i + 1), 0.0f);
+                            h[i] = __floats2bfloat162_rn(a0, a1);
+                        }
+                        if (q < g.Q) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                *reinterpret_cast<uint4*>(o + size_t((n0 + j) / 8 + k) * g.Qp * 8) = pk[k];
+                        }
+                    }
+                } else {
+                    // output views: column o = 3 view + channel
+                    const int vy = y - 1, vx = x - 1;
+                    const bool inside = q < g.Q && vy >= 0 && vy < g.H && vx >= 0 && vx < g.W;
+                    uint32_t* views = static_cast<uint32_t*>(out);
+                    const size_t npix = size_t(g.H) * g.W, pix = size_t(vy) * g.W + vx;
+                    for (int j = 0; j < g.NT; j += 48) {
+                        float v[48];
+                        tc::ld16(trow + uint32_t(r * g.NT + j), v);
+                        tc::ld16(trow + uint32_t(r * g.NT + j + 16), v + 16);
+                        tc::ld16(trow + uint32_t(r * g.NT + j + 32), v + 32);
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            const int view = j / 3 + k;
+                            uint32_t word = 0xff000000u;
+#pragma unroll
+                            for (int c = 0; c < 3; c++) {
+                                const float f =
+                                    fminf(fmaxf(v[3 * k + c] + __ldg(bias + j + 3 * k + c), 0.0f), 1.0f) * 255.0f;
+                                word |= uint32_t(rintf(f)) << (8 * c);
+                            }
+                            if (inside && view < g.nout) views[size_t(view) * npix + pix] = word;
+                        }
+                    }
+                }
+            }
+            // this warp's reads of the buffer are done
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acc_empty + 8 * buf) : "memory");
+        }
+        if (!ok && lane == 0) atomicOr(status, 4);
+    }
+    __syncwarp();
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
 }
 
-// out [H/2][W/2][C] = mean of 2x2 blocks of in [H][W][C] (H, W even; C % 8 == 0).
+// dst [n_tiles][ksteps][taps][2][NT][8] from src [cout][taps][cin]; rows co >=
+// cout are zero (cin % 16 == 0).
+__global__ void k_pack_w(const __nv_bfloat16* __restrict__ src, int cout, int taps, int cin, int NT, int n_tiles,
+                         __nv_bfloat16* __restrict__ dst) {
+    const int ksteps = cin / 16;
+    const size_t total = size_t(n_tiles) * ksteps * taps * 2 * NT * 8;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        size_t r = i;
+        const int e = int(r % 8);
+        r /= 8;
+        const int n = int(r % NT);
+        r /= NT;
+        const int c2 = int(r % 2);
+        r /= 2;
+        const int t = int(r % taps);
+        r /= taps;
+        const int ks = int(r % ksteps);
+        const int ntile = int(r / ksteps);
+        const int co = ntile * NT + n, ci = ks * 16 + c2 * 8 + e;
+        dst[i] = co < cout ? src[(size_t(co) * taps + t) * cin + ci] : __float2bfloat16_rn(0.0f);
+    }
+}
+
+// Chunked bordered tensors: channel c of level-image pixel (y, x) (H x W) is
+// element ((c / 8) Qp + q) 8 + c % 8 with q = (y + 1) (W + 2) + x + 1 and
+// Qp = (H + 2) (W + 2) rounded up to 32.
+__host__ __device__ __forceinline__ size_t qpad(int H, int W) { return (size_t(H + 2) * (W + 2) + 31) / 32 * 32; }
+__device__ __forceinline__ size_t bpos(int y, int x, int W) { return size_t(y + 1) * (W + 2) + (x + 1); }
+
+__device__ __forceinline__ void bf16x8_to_f32(const uint4& v, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const float2 t = __bfloat1622float2(h[e]);
+        f[2 * e] = t.x;
+        f[2 * e + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
+    uint4 o;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int e = 0; e < 4; e++) h[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+    return o;
+}
+
+// out (level H/2 x W/2) = mean of 2x2 blocks of in (level H x W); C % 8 == 0.
+// One thread per (chunk, output pixel), pixels fastest.
 __global__ void k_avgpool2(const __nv_bfloat16* __restrict__ in, int H, int W, int C, __nv_bfloat16* __restrict__ out) {
-    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
-    const size_t total = (size_t)Ho * Wo * C8;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c8 = int(i % C8);
-        const size_t p = i / C8;
+    const int Ho = H / 2, Wo = W / 2;
+    const size_t npx = size_t(Ho) * Wo, total = npx * (C / 8), qi = qpad(H, W), qo = qpad(Ho, Wo);
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        const int c8 = int(i / npx);
+        const size_t p = i - c8 * npx;
         const int xo = int(p % Wo), yo = int(p / Wo);
+        const __nv_bfloat16* src = in + size_t(c8) * qi * 8;
         float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int yy = 2 * yo + (q >> 1), xx = 2 * xo + (q & 1);
-            const uint4 v = *reinterpret_cast<const uint4*>(in + ((size_t)yy * W + xx) * C + 8 * c8);
-            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+            float f[8];
+            bf16x8_to_f32(*reinterpret_cast<const uint4*>(src + bpos(2 * yo + (q >> 1), 2 * xo + (q & 1), W) * 8), f);
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const float2 f = __bfloat1622float2(h[e]);
-                s[2 * e] += f.x;
-                s[2 * e + 1] += f.y;
-            }
+            for (int e = 0; e < 8; e++) s[e] += f[e];
         }
-        uint4 o;
-        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
 #pragma unroll
-        for (int e = 0; e < 4; e++) oh[e] = __floats2bfloat162_rn(0.25f * s[2 * e], 0.25f * s[2 * e + 1]);
-        *reinterpret_cast<uint4*>(out + p * C + 8 * c8) = o;
+        for (int e = 0; e < 8; e++) s[e] *= 0.25f;
+        *reinterpret_cast<uint4*>(out + (size_t(c8) * qo + bpos(yo, xo, Wo)) * 8) = f32_to_bf16x8(s);
     }
 }
 
-// out [H][W][Ca + Cb]: channels [0, Ca) = a [H/2][W/2][Ca] at (y/2, x/2),
-// channels [Ca, Ca + Cb) = b [H][W][Cb] (Ca, Cb % 8 == 0).
+// out (level H x W, Ca + Cb channels): [0, Ca) = a (level H/2 x W/2) at
+// (y/2, x/2), [Ca, Ca + Cb) = b (level H x W); Ca, Cb % 8 == 0.
 __global__ void k_up2_concat(const __nv_bfloat16* __restrict__ a, int Ca, const __nv_bfloat16* __restrict__ b, int Cb,
                              int H, int W, __nv_bfloat16* __restrict__ out) {
-    const int C = Ca + Cb, C8 = C / 8;
-    const size_t total = (size_t)H * W * C8;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = 8 * int(i % C8);
-        const size_t p = i / C8;
+    const size_t npx = size_t(H) * W, total = npx * ((Ca + Cb) / 8), q1 = qpad(H, W), qh = qpad(H / 2, W / 2);
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        const int c8 = int(i / npx);
+        const size_t p = i - c8 * npx;
         const int x = int(p % W), y = int(p / W);
-        uint4 v;
-        if (c < Ca)
-            v = *reinterpret_cast<const uint4*>(a + ((size_t)(y / 2) * (W / 2) + x / 2) * Ca + c);
-        else
-            v = *reinterpret_cast<const uint4*>(b + p * Cb + (c - Ca));
-        *reinterpret_cast<uint4*>(out + p * C + c) = v;
+        const uint4 v = 8 * c8 < Ca
+                            ? *reinterpret_cast<const uint4*>(a + (size_t(c8) * qh + bpos(y / 2, x / 2, W / 2)) * 8)
+                            : *reinterpret_cast<const uint4*>(b + (size_t(c8 - Ca / 8) * q1 + bpos(y, x, W)) * 8);
+        *reinterpret_cast<uint4*>(out + (size_t(c8) * q1 + bpos(y, x, W)) * 8) = v;
     }
 }
 
-// x0 [Hp][Wp][48]: channel 3 j + c = channel c of input view j / 255 for
-// j < nin (nin <= 16), zero elsewhere and outside the H x W views.
+// x0 (level Hp x Wp, 48 channels): channel 3 j + c = channel c of input view
+// j / 255 for j < nin (nin <= 16), zero elsewhere and outside the H x W views.
+// One thread per pixel: its nin RGBA8 words, six 16-byte chunk stores.
 __global__ void k_recon_in(const uint8_t* __restrict__ views, int nin, int H, int W, int Hp, int Wp,
                            __nv_bfloat16* __restrict__ x0) {
-    const size_t total = (size_t)Hp * Wp * 6;   // 6 groups of 8 channels
-    const size_t npix = (size_t)H * W;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int g = int(i % 6);
-        const size_t p = i / 6;
+    const size_t total = size_t(Hp) * Wp, npix = size_t(H) * W, qp = qpad(Hp, Wp);
+    for (size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x; p < total; p += size_t(gridDim.x) * blockDim.x) {
         const int x = int(p % Wp), y = int(p / Wp);
-        float v[8];
+        float v[48];
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int ch = 8 * g + e, j = ch / 3, c = ch - 3 * j;
-            v[e] = 0.0f;
-            if (j < nin && x < W && y < H)
-                v[e] = float(views[((size_t)j * npix + (size_t)y * W + x) * 4 + c]) * (1.0f / 255.0f);
+        for (int j = 0; j < 16; j++) {
+            uint32_t w = 0u;
+            if (j < nin && x < W && y < H) w = __ldg(reinterpret_cast<const uint32_t*>(views) + size_t(j) * npix + size_t(y) * W + x);
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[3 * j + c] = float((w >> (8 * c)) & 255u) * (1.0f / 255.0f);
         }
-        uint4 o;
-        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+        const size_t q = bpos(y, x, Wp);
 #pragma unroll
-        for (int e = 0; e < 4; e++) oh[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-        *reinterpret_cast<uint4*>(x0 + p * 48 + 8 * g) = o;
+        for (int g = 0; g < 6; g++) *reinterpret_cast<uint4*>(x0 + (size_t(g) * qp + q) * 8) = f32_to_bf16x8(v + 8 * g);
     }
 }
 
-// The output layer as one tensor-core GEMM per 16 pixels: [d0 (32) | x0 (48)]
-// x [w_out ; angular base] (80 x 3 nout, bf16 in shared memory as
-// [3 nout][kOutK]) + b_out, clamped to [0, 1], times 255, rounded half to
-// even, alpha 255 -> views_out [nout][H][W][4]. The base rows give output
-// view k, channel c the linear angular interpolation of the input views
-// (input j at output index 4 j + 3/2, clamped at the ends); its weights
-// (0, 1/8, 3/8, 5/8, 7/8, 1) are exact in bf16. Each warp stages its 16
-// pixels' RGBA8 words in shared memory and writes them view by view.
-constexpr int kOutK = 80 + 8;   // smem row stride of the output weights (elements)
-__global__ void __launch_bounds__(256) k_recon_out(const __nv_bfloat16* __restrict__ d0,
-                                                   const __nv_bfloat16* __restrict__ x0, int nin, int H, int W,
-                                                   int Hp, int Wp, const __nv_bfloat16* __restrict__ w_out,
-                                                   const float* __restrict__ b_out, uint8_t* __restrict__ views_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nout = 4 * nin, no3 = 3 * nout, nt = no3 / 8;   // n8 tiles (no3 % 8 == 0: nin even)
-    __nv_bfloat16* s_w = reinterpret_cast<__nv_bfloat16*>(smem_raw);                        // [no3][kOutK]
-    float* s_b = reinterpret_cast<float*>(smem_raw + sizeof(__nv_bfloat16) * no3 * kOutK);  // [no3]
-    uint32_t* s_px = reinterpret_cast<uint32_t*>(s_b + no3);                                // [8 warps][16][nout]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < no3 * 80; i += blockDim.x) {
-        const int o = i / 80, k = i - 80 * o;
-        s_w[o * kOutK + k] = w_out[i];
+// Plain NHWC [H][W][C] <-> chunked bordered (test hook; C % 8 == 0).
+__global__ void k_to_chunked(const __nv_bfloat16* __restrict__ in, int H, int W, int C, __nv_bfloat16* __restrict__ out) {
+    const size_t npx = size_t(H) * W, total = npx * (C / 8), qp = qpad(H, W);
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        const int c8 = int(i / npx);
+        const size_t p = i - c8 * npx;
+        *reinterpret_cast<uint4*>(out + (size_t(c8) * qp + bpos(int(p / W), int(p % W), W)) * 8) =
+            *reinterpret_cast<const uint4*>(in + p * C + 8 * c8);
     }
-    for (int i = tid; i < no3; i += blockDim.x) s_b[i] = b_out[i];
-    __syncthreads();
-    uint32_t* px = s_px + warp * 16 * nout;
-    const size_t npix = (size_t)H * W, ptot = (size_t)Hp * Wp;
-    const int r0 = lane >> 2, kq = 2 * (lane & 3);
-    for (size_t t0 = ((size_t)blockIdx.x * 8 + warp) * 16; t0 < ptot; t0 += (size_t)gridDim.x * 8 * 16) {
-        // A fragments: rows t0 + r0 and t0 + r0 + 8 (padded pixels), 5 k16 steps over [d0 | x0]
-        uint32_t a[5][4];
-#pragma unroll
-        for (int ks = 0; ks < 5; ks++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const size_t p = t0 + r0 + 8 * (q & 1);
-                const int k = 16 * ks + kq + 8 * (q >> 1);
-                const __nv_bfloat16* src = k < 32 ? d0 + p * 32 + k : x0 + p * 48 + (k - 32);
-                a[ks][q] = p < ptot ? *reinterpret_cast<const uint32_t*>(src) : 0u;
-            }
-        for (int i = lane; i < 16 * nout; i += 32) px[i] = 0xff000000u;
-        __syncwarp();
-        for (int t = 0; t < nt; t++) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            const int n = 8 * t + r0;
-#pragma unroll
-            for (int ks = 0; ks < 5; ks++) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(s_w + n * kOutK + 16 * ks + kq);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(s_w + n * kOutK + 16 * ks + kq + 8);
-                mma_bf16(acc, a[ks][0], a[ks][1], a[ks][2], a[ks][3], b0, b1);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int o = 8 * t + kq + (q & 1), row = r0 + 8 * (q >> 1);
-                const float v = fminf(fmaxf(acc[q] + s_b[o], 0.0f), 1.0f) * 255.0f;
-                const int kv = o / 3, c = o - 3 * kv;
-                reinterpret_cast<uint8_t*>(px + row * nout + kv)[c] = uint8_t(rintf(v));
-            }
-        }
-        __syncwarp();
-        // write the 16 pixels' words, view by view
-        for (int i = lane; i < 16 * nout; i += 32) {
-            const int kv = i >> 4, row = i & 15;
-            const size_t p = t0 + row;
-            if (p >= ptot) continue;
-            const int y = int(p / Wp), x = int(p - (size_t)y * Wp);
-            if (y < H && x < W)
-                reinterpret_cast<uint32_t*>(views_out)[(size_t)kv * npix + (size_t)y * W + x] = px[row * nout + kv];
-        }
-        __syncwarp();
+}
+__global__ void k_from_chunked(const __nv_bfloat16* __restrict__ in, int H, int W, int C, __nv_bfloat16* __restrict__ out) {
+    const size_t npx = size_t(H) * W, total = npx * (C / 8), qp = qpad(H, W);
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        const int c8 = int(i / npx);
+        const size_t p = i - c8 * npx;
+        *reinterpret_cast<uint4*>(out + p * C + 8 * c8) =
+            *reinterpret_cast<const uint4*>(in + (size_t(c8) * qp + bpos(int(p / W), int(p % W), W)) * 8);
     }
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// Host side of the tensor-core layers
+// ---------------------------------------------------------------------------
 
-cudaError_t launch_conv3x3(const __nv_bfloat16* in, int H, int W, int Cin, const __nv_bfloat16* wgt,
-                           const float* bias, __nv_bfloat16* out, int Cout, bool relu, cudaStream_t s) {
-    if (H < 1 || W < 1 || Cin < kConvCK || Cin % kConvCK || Cout < 32 || Cout % 32) return cudaErrorInvalidValue;
-    static bool attrs[64] = {};   // opt in to the two-stage shared memory once per device
+constexpr uint32_t kTcSmemMax = 227 * 1024;
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D map over a chunked bordered tensor [C / 8][Qp][8] bf16 seen as
+// (256 elements = 32 positions x 8 channels, Qp / 32 rows, C / 8 chunks):
+// boxes of `rows` 512-byte rows of two consecutive chunks.
+cudaError_t make_map(CUtensorMap* m, const void* base, int C, size_t Qp, int rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || C % 8 || Qp % 32 || rows < 1 || rows > 256)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[3] = {256, cuuint64_t(Qp / 32), cuuint64_t(C / 8)};
+    const cuuint64_t strides[2] = {512, cuuint64_t(Qp) * 16};
+    const cuuint32_t box[3] = {256, cuuint32_t(rows), 2}, es[3] = {1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+uint32_t pow2_cols(int n) {
+    uint32_t c = 32;
+    while (c < uint32_t(n)) c <<= 1;
+    return c;
+}
+
+// Geometry of a layer over the bordered level image Hl x Wl: cin = cin_a +
+// cin_b input channels (map a, then map b), NT output channels per block, R
+// row groups of 128 positions per block.
+TcGeom tc_geom(int Hl, int Wl, int cin_a, int cin_b, int taps, int NT, int R, int n_tiles, int cout) {
+    TcGeom g{};
+    g.Hb = Hl + 2;
+    g.Wb = Wl + 2;
+    g.Q = g.Hb * g.Wb;
+    g.taps = taps;
+    g.NT = NT;
+    g.R = R;
+    g.ksteps = (cin_a + cin_b) / 16;
+    g.split = cin_a / 8;
+    g.Qp = (g.Q + 31) / 32 * 32;
+    // the span plus up to 31 positions before it in its first 32-position row
+    const int L = 128 * R + (taps == 9 ? 2 * g.Wb + 2 : 0);
+    g.rows = (L + 31 + 31) / 32;
+    g.span = 32 * g.rows;
+    g.a_bytes = uint32_t(2 * g.span * 16);
+    g.b_bytes = uint32_t(taps * 2 * NT * 16);
+    g.stage_bytes = (g.a_bytes + g.b_bytes + 1023u) & ~1023u;
+    // one block per SM, as many stages as fit
+    g.stages = int(std::min<uint32_t>(uint32_t(kMaxStages), (kTcSmemMax - 2048u) / g.stage_bytes));
+    g.tmem_cols = pow2_cols(2 * R * NT);
+    g.m_tiles = (g.Q + 128 * R - 1) / (128 * R);
+    g.n_tiles = n_tiles;
+    g.cout = cout;
+    return g;
+}
+
+// Shared memory of one SM (bytes), queried once per process.
+size_t smem_per_sm() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || v <= 0)
+            v = 228 * 1024;
+    }
+    return size_t(v);
+}
+
+// Dynamic shared memory of a block: the stages, the barriers, the 1024-byte
+// alignment slack, and more than half of the SM's, so that one block holds
+// an SM (and its tensor memory) at a time.
+size_t tc_smem(const TcGeom& g) {
+    return std::max(size_t(g.stages) * g.stage_bytes + 1024 + 1024, smem_per_sm() / 2 + 1024);
+}
+
+int sm_count_cached() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    }
+    return v;
+}
+
+bool tc_valid(const TcGeom& g) {
+    return g.stages >= 2 && g.ksteps >= 1 && g.NT % 16 == 0 && g.NT >= 16 && g.NT <= 256 && g.tmem_cols <= 512 &&
+           (g.taps == 9 || g.taps == 1) && g.split % 2 == 0 && g.rows <= 256 && g.m_tiles >= 1 && g.n_tiles >= 1 &&
+           tc_smem(g) <= kTcSmemMax;
+}
+
+cudaError_t launch_tc(int epi, const TcGeom& g, const CUtensorMap& ma, const CUtensorMap& mb, const void* wpk,
+                      const float* bias, void* out, int* status, cudaStream_t s) {
+    if (!tc_valid(g)) return cudaErrorInvalidValue;
+    static bool attrs[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attrs[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(conv_smem_bytes(64)));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_conv3x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(conv_smem_bytes(32)));
-        if (e != cudaSuccess) return e;
+        const void* fns[4] = {reinterpret_cast<const void*>(k_conv_tc<1, 1, 1>), reinterpret_cast<const void*>(k_conv_tc<0, 9, 1>),
+                              reinterpret_cast<const void*>(k_conv_tc<0, 9, 2>), reinterpret_cast<const void*>(k_conv_tc<0, 9, 4>)};
+        for (const void* f : fns) {
+            const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmemMax));
+            if (e != cudaSuccess) return e;
+        }
         attrs[dev] = true;
     }
-    if (Cout % 64 == 0) {
-        const dim3 grid((W + kConvTW - 1) / kConvTW, (H + kConvTH - 1) / kConvTH, Cout / 64);
-        k_conv3x3<64><<<grid, 256, conv_smem_bytes(64), s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
-    } else {
-        const dim3 grid((W + kConvTW - 1) / kConvTW, (H + kConvTH - 1) / kConvTH, Cout / 32);
-        k_conv3x3<32><<<grid, 256, conv_smem_bytes(32), s>>>(in, H, W, Cin, wgt, bias, out, Cout, relu ? 1 : 0);
+    const int grid = std::min(g.m_tiles * g.n_tiles, sm_count_cached());
+    const size_t smem = tc_smem(g);
+    const uint8_t* w = static_cast<const uint8_t*>(wpk);
+    if (epi == 1 && g.taps == 1 && g.R == 1)
+        k_conv_tc<1, 1, 1><<<grid, kTcThreads, smem, s>>>(ma, mb, w, bias, out, g, status);
+    else if (epi == 0 && g.taps == 9 && g.R == 1)
+        k_conv_tc<0, 9, 1><<<grid, kTcThreads, smem, s>>>(ma, mb, w, bias, out, g, status);
+    else if (epi == 0 && g.taps == 9 && g.R == 2)
+        k_conv_tc<0, 9, 2><<<grid, kTcThreads, smem, s>>>(ma, mb, w, bias, out, g, status);
+    else if (epi == 0 && g.taps == 9 && g.R == 4)
+        k_conv_tc<0, 9, 4><<<grid, kTcThreads, smem, s>>>(ma, mb, w, bias, out, g, status);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const __nv_bfloat16* src, int cout, int taps, int cin, int NT, int n_tiles, __nv_bfloat16* dst,
+                        cudaStream_t s) {
+    k_pack_w<<<256, 256, 0, s>>>(src, cout, taps, cin, NT, n_tiles, dst);
+    return cudaGetLastError();
+}
+
+// Output channels and row groups per tile of a 3x3 layer: 32 or 64 channels;
+// the most row groups (two accumulator buffers of R NT <= 256 columns each)
+// that still give every SM two tiles or more.
+void pick_tile(int Hl, int Wl, int cout, int sm_count, int& NT, int& R) {
+    NT = cout % 64 == 0 ? 64 : 32;
+    const int64_t Q = int64_t(Hl + 2) * (Wl + 2);
+    R = 1;
+    for (int r : {4, 2}) {
+        if (r * NT > 128) continue;
+        if ((Q + 128 * r - 1) / (128 * r) * (cout / NT) >= 2 * sm_count) {
+            R = r;
+            break;
+        }
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_avgpool2(const __nv_bfloat16* in, int H, int W, int C, __nv_bfloat16* out, int sm_count,
-                            cudaStream_t s) {
-    if (H < 2 || W < 2 || (H & 1) || (W & 1) || C % 8) return cudaErrorInvalidValue;
-    k_avgpool2<<<sm_count * 8, 256, 0, s>>>(in, H, W, C, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_up2_concat(const __nv_bfloat16* a, int Ca, const __nv_bfloat16* b, int Cb, int H, int W,
-                              __nv_bfloat16* out, int sm_count, cudaStream_t s) {
-    if (H < 2 || W < 2 || (H & 1) || (W & 1) || Ca % 8 || Cb % 8) return cudaErrorInvalidValue;
-    k_up2_concat<<<sm_count * 8, 256, 0, s>>>(a, Ca, b, Cb, H, W, out);
-    return cudaGetLastError();
-}
-
+}  // namespace
 }  // namespace lfdpr
 
 // ---------------------------------------------------------------------------
@@ -385,12 +729,15 @@ const ConvSpec kLayers[14] = {{48, 32, 0},  {32, 32, 0},   {32, 64, 1},   {64, 6
 
 struct lfdpr_recon {
     int W = 0, H = 0, Wp = 0, Hp = 0, nin = 0, nout = 0, sm_count = 1;
-    __nv_bfloat16* w = nullptr;   // all 3x3 weights, layer by layer [cout][9][cin]
-    float* b = nullptr;           // all 3x3 biases
-    __nv_bfloat16* w_out = nullptr;   // [3 nout][80]: the 1x1 layer (32) then the angular base (48)
-    float* b_out = nullptr;           // [3 nout]
+    __nv_bfloat16* w = nullptr;       // packed 3x3 weights, layer by layer
+    float* b = nullptr;               // all 3x3 biases
+    __nv_bfloat16* w_out = nullptr;   // packed output layer: [32 (1x1 weights) | 48 (angular base)] x NT_out
+    float* b_out = nullptr;           // [NT_out] (zero past 3 nout)
+    int* status = nullptr;            // device: failed waits (bit 0 copies, 1 MMA, 2 epilogue)
     int64_t w_off[14] = {}, b_off[14] = {};
-    __nv_bfloat16* act = nullptr;  // activation arena
+    TcGeom geom[14] = {}, geom_out = {};
+    CUtensorMap in_map[14], out_d0, out_x0;
+    __nv_bfloat16* act = nullptr;     // activation arena (bordered tensors)
     __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *bb, *u2, *d2a, *d2, *u1, *d1a, *d1, *u0,
         *d0a, *d0;
 };
@@ -403,9 +750,13 @@ void free_recon(lfdpr_recon* r) {
     cudaFree(r->b);
     cudaFree(r->w_out);
     cudaFree(r->b_out);
+    cudaFree(r->status);
     cudaFree(r->act);
     delete r;
 }
+
+// Output channels of the output layer's blocks: 3 nout padded to a multiple of 48.
+int out_nt(int nout) { return (3 * nout + 47) / 48 * 48; }
 
 }  // namespace
 
@@ -435,6 +786,7 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     if (n_weights != lfdpr_recon_weight_count(in_views) || n_biases != lfdpr_recon_bias_count(in_views))
         return fail(LFDPR_EINVAL, "create_recon: expected %lld weights and %lld biases",
                     (long long)lfdpr_recon_weight_count(in_views), (long long)lfdpr_recon_bias_count(in_views));
+    if (!tensor_map_encoder()) return fail(LFDPR_ECUDA, "create_recon: the driver has no tensor-map encoder");
     lfdpr_recon* r = new (std::nothrow) lfdpr_recon();
     if (!r) return fail(LFDPR_ENOMEM, "host allocation failed");
     r->W = view_w;
@@ -453,22 +805,30 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         wo += int64_t(kLayers[l].cout) * 9 * kLayers[l].cin;
         bo += kLayers[l].cout;
     }
-    // activation arena: every tensor of the forward pass, 256-byte aligned
-    const int64_t P0 = int64_t(r->Hp) * r->Wp, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
-    const int64_t sizes[21] = {P0 * 48, P0 * 32, P0 * 32, P1 * 32, P1 * 64, P1 * 64, P2 * 64,
-                               P2 * 128, P2 * 128, P3 * 128, P3 * 256, P3 * 256, P2 * 384, P2 * 128,
-                               P2 * 128, P1 * 192, P1 * 64, P1 * 64, P0 * 96, P0 * 32, P0 * 32};
+    // activation arena: every bordered tensor of the forward pass, 256-byte aligned
+    int64_t Ql[4];   // positions per chunk of each level
+    for (int l = 0; l < 4; l++) Ql[l] = int64_t(qpad(r->Hp >> l, r->Wp >> l));
+    const int64_t sizes[21] = {Ql[0] * 48,  Ql[0] * 32,  Ql[0] * 32,  Ql[1] * 32,  Ql[1] * 64,  Ql[1] * 64,  Ql[2] * 64,
+                               Ql[2] * 128, Ql[2] * 128, Ql[3] * 128, Ql[3] * 256, Ql[3] * 256, Ql[2] * 384, Ql[2] * 128,
+                               Ql[2] * 128, Ql[1] * 192, Ql[1] * 64,  Ql[1] * 64,  Ql[0] * 96,  Ql[0] * 32,  Ql[0] * 32};
     int64_t offs[21], total = 0;
     for (int k = 0; k < 21; k++) {
         offs[k] = total;
         total += (sizes[k] + 127) / 128 * 128;
     }
+    const int ntout = out_nt(r->nout), no3 = 3 * r->nout;
     cudaError_t e;
     const int64_t nw3 = wo, nb3 = bo;
+    uint16_t* w_raw = nullptr;   // device staging of the 3x3 blob before packing
+    uint16_t* wout_raw = nullptr;
     if ((e = cudaMalloc(&r->w, 2 * nw3)) != cudaSuccess || (e = cudaMalloc(&r->b, 4 * nb3)) != cudaSuccess ||
-        (e = cudaMalloc(&r->w_out, 2 * int64_t(3 * r->nout) * 80)) != cudaSuccess ||
-        (e = cudaMalloc(&r->b_out, 4 * int64_t(3 * r->nout))) != cudaSuccess ||
-        (e = cudaMalloc(&r->act, 2 * total)) != cudaSuccess) {
+        (e = cudaMalloc(&r->w_out, 2 * int64_t(ntout) * 80)) != cudaSuccess ||
+        (e = cudaMalloc(&r->b_out, 4 * int64_t(ntout))) != cudaSuccess ||
+        (e = cudaMalloc(&r->status, sizeof(int))) != cudaSuccess || (e = cudaMalloc(&r->act, 2 * total)) != cudaSuccess ||
+        (e = cudaMalloc(&w_raw, 2 * nw3)) != cudaSuccess ||
+        (e = cudaMalloc(&wout_raw, 2 * int64_t(no3) * 80)) != cudaSuccess) {
+        cudaFree(w_raw);
+        cudaFree(wout_raw);
         free_recon(r);
         return cuda_fail(e, "create_recon: cudaMalloc");
     }
@@ -477,7 +837,6 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     for (int k = 0; k < 21; k++) *bufs[k] = r->act + offs[k];
     // the output layer: its 32 weights, then the angular base over the 48
     // input channels (bf16 bit patterns: 1/8, 3/8, 5/8, 7/8 and 1 are exact)
-    const int no3 = 3 * r->nout;
     std::vector<uint16_t> wout(size_t(no3) * 80, 0);
     auto bf16_bits = [](float f) {
         uint32_t u;
@@ -488,21 +847,55 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         for (int k = 0; k < 32; k++) wout[size_t(o) * 80 + k] = weights_bf16[nw3 + int64_t(o) * 32 + k];
         const int kv = o / 3, c = o - 3 * kv;
         const float pos = (float(kv) - 1.5f) * 0.25f;
-        const int j0 = r->nin > 1 ? std::min(std::max(int(std::floor(pos)), 0), r->nin - 2) : 0;
-        const float t = r->nin > 1 ? std::min(std::max(pos - float(j0), 0.0f), 1.0f) : 0.0f;
-        const int j1 = r->nin > 1 ? j0 + 1 : j0;
-        if (j1 == j0) {
-            wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f);
-        } else {
-            wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f - t);
-            wout[size_t(o) * 80 + 32 + 3 * j1 + c] = bf16_bits(t);
-        }
+        const int j0 = std::min(std::max(int(std::floor(pos)), 0), r->nin - 2);
+        const float t = std::min(std::max(pos - float(j0), 0.0f), 1.0f);
+        wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f - t);
+        wout[size_t(o) * 80 + 32 + 3 * (j0 + 1) + c] = bf16_bits(t);
     }
-    if ((e = cudaMemcpy(r->w, weights_bf16, 2 * nw3, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(r->b, biases, 4 * nb3, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(r->w_out, wout.data(), 2 * wout.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(r->b_out, biases + nb3, 4 * int64_t(3 * r->nout), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(r->act, 0, 2 * total)) != cudaSuccess) {
+    std::vector<float> bout(ntout, 0.0f);
+    for (int o = 0; o < no3; o++) bout[o] = biases[nb3 + o];
+    // layer geometry and packed weights
+    for (int l = 0; l < 14; l++) {
+        const ConvSpec& L = kLayers[l];
+        const int Hl = r->Hp >> L.level, Wl = r->Wp >> L.level;
+        int NT, R;
+        pick_tile(Hl, Wl, L.cout, r->sm_count, NT, R);
+        r->geom[l] = tc_geom(Hl, Wl, L.cin, 0, 9, NT, R, L.cout / NT, L.cout);
+    }
+    r->geom_out = tc_geom(r->Hp, r->Wp, 32, 48, 1, ntout, 1, 1, 0);
+    r->geom_out.nout = r->nout;
+    r->geom_out.H = r->H;
+    r->geom_out.W = r->W;
+    const __nv_bfloat16* conv_in[14] = {r->x0, r->e0a, r->p1, r->e1a, r->p2, r->e2a, r->p3,
+                                        r->ba, r->u2,  r->d2a, r->u1, r->d1a, r->u0, r->d0a};
+    bool maps_ok = true;
+    for (int l = 0; l < 14 && maps_ok; l++)
+        maps_ok = tc_valid(r->geom[l]) &&
+                  make_map(&r->in_map[l], conv_in[l], kLayers[l].cin, r->geom[l].Qp, r->geom[l].rows) == cudaSuccess;
+    maps_ok = maps_ok && tc_valid(r->geom_out) &&
+              make_map(&r->out_d0, r->d0, 32, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess &&
+              make_map(&r->out_x0, r->x0, 48, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess;
+    if (!maps_ok) {
+        cudaFree(w_raw);
+        cudaFree(wout_raw);
+        free_recon(r);
+        return fail(LFDPR_EINVAL, "create_recon: no tensor-core layout for %dx%d views", view_w, view_h);
+    }
+    if ((e = cudaMemcpy(w_raw, weights_bf16, 2 * nw3, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(wout_raw, wout.data(), 2 * wout.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(r->b, biases, 4 * nb3, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(r->b_out, bout.data(), 4 * bout.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemset(r->act, 0, 2 * total)) == cudaSuccess && (e = cudaMemset(r->status, 0, sizeof(int))) == cudaSuccess) {
+        for (int l = 0; l < 14 && e == cudaSuccess; l++)
+            e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(w_raw) + r->w_off[l], kLayers[l].cout, 9,
+                            kLayers[l].cin, r->geom[l].NT, r->geom[l].n_tiles, r->w + r->w_off[l], 0);
+        if (e == cudaSuccess)
+            e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(wout_raw), no3, 1, 80, ntout, 1, r->w_out, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(w_raw);
+    cudaFree(wout_raw);
+    if (e != cudaSuccess) {
         free_recon(r);
         return cuda_fail(e, "create_recon: upload");
     }
@@ -522,9 +915,19 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     if (!r || !in_views || !out_views) return fail(LFDPR_EINVAL, "recon_forward: null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H0 = r->Hp, W0 = r->Wp, sm = r->sm_count;
-    auto conv = [&](int l, const __nv_bfloat16* in, __nv_bfloat16* o, int H, int W) {
-        return launch_conv3x3(in, H, W, kLayers[l].cin, r->w + r->w_off[l], r->b + r->b_off[l], o, kLayers[l].cout,
-                              true, s);
+    __nv_bfloat16* conv_out[14] = {r->e0a, r->e0, r->e1a, r->e1, r->e2a, r->e2, r->ba,
+                                   r->bb,  r->d2a, r->d2, r->d1a, r->d1, r->d0a, r->d0};
+    auto conv = [&](int l) {
+        return launch_tc(0, r->geom[l], r->in_map[l], r->in_map[l], r->w + r->w_off[l], r->b + r->b_off[l],
+                         conv_out[l], r->status, s);
+    };
+    auto pool = [&](const __nv_bfloat16* in, int H, int W, int C, __nv_bfloat16* o) {
+        k_avgpool2<<<sm * 8, 256, 0, s>>>(in, H, W, C, o);
+        return cudaGetLastError();
+    };
+    auto up = [&](const __nv_bfloat16* a, int Ca, const __nv_bfloat16* b, int Cb, int H, int W, __nv_bfloat16* o) {
+        k_up2_concat<<<sm * 8, 256, 0, s>>>(a, Ca, b, Cb, H, W, o);
+        return cudaGetLastError();
     };
 #define CKR(call, what)                                      \
     do {                                                     \
@@ -533,30 +936,28 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     } while (0)
     k_recon_in<<<sm * 8, 256, 0, s>>>(in_views, r->nin, r->H, r->W, H0, W0, r->x0);
     CKR(cudaGetLastError(), "launch k_recon_in");
-    CKR(conv(0, r->x0, r->e0a, H0, W0), "conv 0");
-    CKR(conv(1, r->e0a, r->e0, H0, W0), "conv 1");
-    CKR(launch_avgpool2(r->e0, H0, W0, 32, r->p1, sm, s), "pool 1");
-    CKR(conv(2, r->p1, r->e1a, H0 / 2, W0 / 2), "conv 2");
-    CKR(conv(3, r->e1a, r->e1, H0 / 2, W0 / 2), "conv 3");
-    CKR(launch_avgpool2(r->e1, H0 / 2, W0 / 2, 64, r->p2, sm, s), "pool 2");
-    CKR(conv(4, r->p2, r->e2a, H0 / 4, W0 / 4), "conv 4");
-    CKR(conv(5, r->e2a, r->e2, H0 / 4, W0 / 4), "conv 5");
-    CKR(launch_avgpool2(r->e2, H0 / 4, W0 / 4, 128, r->p3, sm, s), "pool 3");
-    CKR(conv(6, r->p3, r->ba, H0 / 8, W0 / 8), "conv 6");
-    CKR(conv(7, r->ba, r->bb, H0 / 8, W0 / 8), "conv 7");
-    CKR(launch_up2_concat(r->bb, 256, r->e2, 128, H0 / 4, W0 / 4, r->u2, sm, s), "up 2");
-    CKR(conv(8, r->u2, r->d2a, H0 / 4, W0 / 4), "conv 8");
-    CKR(conv(9, r->d2a, r->d2, H0 / 4, W0 / 4), "conv 9");
-    CKR(launch_up2_concat(r->d2, 128, r->e1, 64, H0 / 2, W0 / 2, r->u1, sm, s), "up 1");
-    CKR(conv(10, r->u1, r->d1a, H0 / 2, W0 / 2), "conv 10");
-    CKR(conv(11, r->d1a, r->d1, H0 / 2, W0 / 2), "conv 11");
-    CKR(launch_up2_concat(r->d1, 64, r->e0, 32, H0, W0, r->u0, sm, s), "up 0");
-    CKR(conv(12, r->u0, r->d0a, H0, W0), "conv 12");
-    CKR(conv(13, r->d0a, r->d0, H0, W0), "conv 13");
-    const size_t smem = 2 * size_t(3 * r->nout) * kOutK + 4 * size_t(3 * r->nout) + 4 * size_t(8 * 16 * r->nout);
-    CKR(cudaFuncSetAttribute(k_recon_out, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "recon_out smem");
-    k_recon_out<<<sm * 2, 256, smem, s>>>(r->d0, r->x0, r->nin, r->H, r->W, H0, W0, r->w_out, r->b_out, out_views);
-    CKR(cudaGetLastError(), "launch k_recon_out");
+    CKR(conv(0), "conv 0");
+    CKR(conv(1), "conv 1");
+    CKR(pool(r->e0, H0, W0, 32, r->p1), "pool 1");
+    CKR(conv(2), "conv 2");
+    CKR(conv(3), "conv 3");
+    CKR(pool(r->e1, H0 / 2, W0 / 2, 64, r->p2), "pool 2");
+    CKR(conv(4), "conv 4");
+    CKR(conv(5), "conv 5");
+    CKR(pool(r->e2, H0 / 4, W0 / 4, 128, r->p3), "pool 3");
+    CKR(conv(6), "conv 6");
+    CKR(conv(7), "conv 7");
+    CKR(up(r->bb, 256, r->e2, 128, H0 / 4, W0 / 4, r->u2), "up 2");
+    CKR(conv(8), "conv 8");
+    CKR(conv(9), "conv 9");
+    CKR(up(r->d2, 128, r->e1, 64, H0 / 2, W0 / 2, r->u1), "up 1");
+    CKR(conv(10), "conv 10");
+    CKR(conv(11), "conv 11");
+    CKR(up(r->d1, 64, r->e0, 32, H0, W0, r->u0), "up 0");
+    CKR(conv(12), "conv 12");
+    CKR(conv(13), "conv 13");
+    CKR(launch_tc(1, r->geom_out, r->out_d0, r->out_x0, r->w_out, r->b_out, out_views, r->status, s),
+        "output layer");
 #undef CKR
     return LFDPR_OK;
 }
@@ -571,15 +972,56 @@ lfdpr_status lfdpr_recon_run(lfdpr_recon* r, const lfdpr_display* src, lfdpr_dis
     return lfdpr_recon_forward(r, src->views, dst->views, stream);
 }
 
-lfdpr_status lfdpr_conv3x3_bf16(const void* in, int32_t H, int32_t W, int32_t cin, const void* wgt, const float* bias,
-                                void* out, int32_t cout, int32_t relu, void* stream) {
+lfdpr_status lfdpr_recon_status(lfdpr_recon* r, int32_t* flags) {
     lfdpr::g_last_error[0] = 0;
-    if (!in || !wgt || !bias || !out) return fail(LFDPR_EINVAL, "conv3x3: null argument");
-    if (H < 1 || W < 1 || cin < 16 || cin % 16 || cout < 32 || cout % 32)
-        return fail(LFDPR_EINVAL, "conv3x3: need cin %% 16 == 0, cout %% 32 == 0");
-    const cudaError_t e =
-        launch_conv3x3(static_cast<const __nv_bfloat16*>(in), H, W, cin, static_cast<const __nv_bfloat16*>(wgt), bias,
-                       static_cast<__nv_bfloat16*>(out), cout, relu != 0, static_cast<cudaStream_t>(stream));
+    if (!r || !flags) return fail(LFDPR_EINVAL, "recon_status: null argument");
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, r->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(r->status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "recon_status");
+    *flags = v;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_conv3x3_bf16(const void* in, int32_t H, int32_t W, int32_t cin, const void* wgt, const float* bias,
+                                void* out, int32_t cout, int32_t* status, void* stream) {
+    lfdpr::g_last_error[0] = 0;
+    if (!in || !wgt || !bias || !out || !status) return fail(LFDPR_EINVAL, "conv3x3: null argument");
+    if (H < 1 || W < 1 || H > 8192 || W > 8192 || cin < 16 || cin % 16 || cin > 512 || cout < 32 || cout % 32 ||
+        cout > 256)
+        return fail(LFDPR_EINVAL, "conv3x3: need cin %% 16 == 0 (<= 512), cout %% 32 == 0 (<= 256)");
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(wgt)) & 15)
+        return fail(LFDPR_EINVAL, "conv3x3: buffers must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int NT, R;
+    pick_tile(H, W, cout, sms, NT, R);
+    const TcGeom g = tc_geom(H, W, cin, 0, 9, NT, R, cout / NT, cout);
+    if (!tc_valid(g)) return fail(LFDPR_EINVAL, "conv3x3: no tensor-core layout for a %d-wide image", W);
+    // chunked bordered copies of the input and output, and the packed weights
+    const size_t qp = qpad(H, W);
+    __nv_bfloat16 *ci = nullptr, *co = nullptr, *wpk = nullptr;
+    cudaError_t e = cudaMallocAsync(&ci, 2 * qp * cin, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&co, 2 * qp * cout, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&wpk, size_t(2) * cout * 9 * cin, s);
+    CUtensorMap m;
+    if (e == cudaSuccess) e = cudaMemsetAsync(ci, 0, 2 * qp * cin, s);
+    if (e == cudaSuccess) e = make_map(&m, ci, cin, qp, g.rows);
+    if (e == cudaSuccess) {
+        k_to_chunked<<<sms * 8, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(in), H, W, cin, ci);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_pack(static_cast<const __nv_bfloat16*>(wgt), cout, 9, cin, NT, cout / NT, wpk, s);
+    if (e == cudaSuccess) e = launch_tc(0, g, m, m, wpk, bias, co, reinterpret_cast<int*>(status), s);
+    if (e == cudaSuccess) {
+        k_from_chunked<<<sms * 8, 256, 0, s>>>(co, H, W, cout, static_cast<__nv_bfloat16*>(out));
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(ci, s);
+    cudaFreeAsync(co, s);
+    cudaFreeAsync(wpk, s);
     if (e != cudaSuccess) return cuda_fail(e, "conv3x3");
     return LFDPR_OK;
 }

@@ -35,7 +35,8 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
            "lfdpr_batch_autotune_table",
            "lfdpr_recon_weight_count", "lfdpr_recon_bias_count", "lfdpr_create_recon",
-           "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_conv3x3_bf16"]
+           "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_recon_status",
+           "lfdpr_conv3x3_bf16"]
 
 
 class LfdprError(RuntimeError):
@@ -126,7 +127,8 @@ def lib() -> C.CDLL:
         L.lfdpr_destroy_recon.argtypes = [P]
         L.lfdpr_recon_run.argtypes = [P, P, P, P]
         L.lfdpr_recon_forward.argtypes = [P, P, P, P]
-        L.lfdpr_conv3x3_bf16.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int32, C.c_int32, P]
+        L.lfdpr_recon_status.argtypes = [P, P]
+        L.lfdpr_conv3x3_bf16.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int32, P, P]
         for name in EXPORTS:
             fn = getattr(L, name)
             if name == "lfdpr_last_error":
@@ -385,10 +387,16 @@ def lfdpr_recon_forward(recon: int, in_ptr: int, out_ptr: int, stream=None):
     _check(lib().lfdpr_recon_forward(recon, C.c_void_p(in_ptr), C.c_void_p(out_ptr), _stream(stream)))
 
 
+def lfdpr_recon_status(recon: int) -> int:
+    f = C.c_int32(0)
+    _check(lib().lfdpr_recon_status(recon, C.byref(f)))
+    return int(f.value)
+
+
 def lfdpr_conv3x3_bf16(in_ptr: int, H: int, W: int, cin: int, w_ptr: int, b_ptr: int, out_ptr: int,
-                       cout: int, relu: bool = True, stream=None):
+                       cout: int, status_ptr: int, stream=None):
     _check(lib().lfdpr_conv3x3_bf16(C.c_void_p(in_ptr), H, W, cin, C.c_void_p(w_ptr), C.c_void_p(b_ptr),
-                                    C.c_void_p(out_ptr), cout, int(relu), _stream(stream)))
+                                    C.c_void_p(out_ptr), cout, C.c_void_p(status_ptr), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------
@@ -547,6 +555,9 @@ class Recon:
 
     def forward(self, in_ptr: int, out_ptr: int, stream=None):
         lfdpr_recon_forward(self.handle, in_ptr, out_ptr, stream)
+
+    def status(self) -> int:
+        return lfdpr_recon_status(self.handle)
 
     def close(self):
         if self.handle is not None:

@@ -29,19 +29,23 @@ def torch():
 
 
 @pytest.mark.parametrize("cin,cout,h,w", [(48, 32, 20, 45), (64, 64, 17, 70), (384, 128, 9, 13),
-                                          (32, 256, 8, 8), (96, 32, 33, 31)])
+                                          (32, 256, 8, 8), (96, 32, 33, 31), (16, 32, 1, 1),
+                                          (32, 32, 70, 300), (256, 256, 12, 20)])
 def test_conv3x3_matches_fp32_reference(torch, cin, cout, h, w):
     g = torch.Generator(device="cpu").manual_seed(cin * 1000 + cout + h)
     x = torch.randn((h, w, cin), generator=g).to(torch.bfloat16).cuda()
     wt = (torch.randn((cout, 3, 3, cin), generator=g) * (2.0 / (9 * cin)) ** 0.5).to(torch.bfloat16).cuda()
     b = (torch.randn((cout,), generator=g) * 0.1).float().cuda()
-    out = torch.empty((h, w, cout), dtype=torch.bfloat16, device="cuda")
-    lfdpr.lfdpr_conv3x3_bf16(x.data_ptr(), h, w, cin, wt.data_ptr(), b.data_ptr(), out.data_ptr(), cout, True)
+    out = torch.full((h, w, cout), 7.0, dtype=torch.bfloat16, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lfdpr.lfdpr_conv3x3_bf16(x.data_ptr(), h, w, cin, wt.data_ptr(), b.data_ptr(), out.data_ptr(), cout,
+                             status.data_ptr())
     torch.cuda.synchronize()
+    assert int(status.item()) == 0
     ref = torch.nn.functional.conv2d(x.float().permute(2, 0, 1)[None], wt.float().permute(0, 3, 1, 2), b,
                                      padding=1)[0].permute(1, 2, 0).relu()
     # one bf16 rounding of the result, plus the fp32 summation-order bound of
-    # a dot product of K = 9 cin terms: K 2^-24 sum |x w| (taken as 2^-22 sum)
+    # a dot product of K = 9 cin terms: K 2^-24 sum |x w|
     mag = torch.nn.functional.conv2d(x.float().abs().permute(2, 0, 1)[None], wt.float().abs().permute(0, 3, 1, 2),
                                      b.abs(), padding=1)[0].permute(1, 2, 0)
     got = out.float()
@@ -51,12 +55,10 @@ def test_conv3x3_matches_fp32_reference(torch, cin, cout, h, w):
 
 
 def test_conv3x3_rejects_unsupported_channels(torch):
-    with pytest.raises(lfdpr.LfdprError) as e:
-        lfdpr.lfdpr_conv3x3_bf16(256, 8, 8, 40, 256, 256, 256, 32, True)
-    assert e.value.status == lfdpr.EINVAL
-    with pytest.raises(lfdpr.LfdprError) as e:
-        lfdpr.lfdpr_conv3x3_bf16(256, 8, 8, 32, 256, 256, 256, 48, True)
-    assert e.value.status == lfdpr.EINVAL
+    for cin, cout in ((40, 32), (32, 48), (528, 32), (32, 288)):
+        with pytest.raises(lfdpr.LfdprError) as e:
+            lfdpr.lfdpr_conv3x3_bf16(256, 8, 8, cin, 256, 256, 256, cout, 256)
+        assert e.value.status == lfdpr.EINVAL
 
 
 def _random_net(torch, seed):
@@ -65,7 +67,7 @@ def _random_net(torch, seed):
     return RN.export(model)
 
 
-@pytest.mark.parametrize("h,w", [(40, 44), (64, 56)])
+@pytest.mark.parametrize("h,w", [(40, 44), (64, 56), (560, 420)])
 def test_forward_matches_reference(torch, h, w):
     wts, bs = _random_net(torch, 7)
     g = torch.Generator(device="cpu").manual_seed(h * w)
@@ -78,6 +80,7 @@ def test_forward_matches_reference(torch, h, w):
     with lfdpr.Recon(w, h, 12, wts, bs) as R:
         R.forward(views.data_ptr(), out.data_ptr())
         torch.cuda.synchronize()
+        assert R.status() == 0
     ref = RN.reference_forward(wts, bs, views, 12)
     d = (out.int() - ref.int()).abs()
     assert torch.all(out[..., 3] == 255)
