@@ -34,9 +34,12 @@
 //                 RGBA8 output views.
 //   k_pack_w      weights [cout][taps][cin] -> the per-K-step stage images
 //                 [n tile][K step][tap][2][NT][8] the MMAs read.
-//   k_avgpool2, k_up2_concat, k_recon_in   pooling, upsampling + skip
-//                 concatenation and the input packing, between chunked
+//   k_avgpool2, k_recon_in   pooling and the input packing, between chunked
 //                 bordered tensors (interiors only; the borders stay zero).
+// The up path needs no concatenation: the last layer of each lower level
+// writes its output 2x upsampled (nearest) into a tensor of the next level's
+// size, and the next layer reads its first channels from that tensor (map a)
+// and the skip channels from the encoder's tensor (map b).
 //   k_to_chunked, k_from_chunked   plain NHWC <-> chunked bordered (test hook).
 //
 // Every wait (mbarrier phases) gives up after 2e9 SM cycles (about one
@@ -159,6 +162,26 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 48 consecutive columns (three loads, one wait).
+__device__ __forceinline__ void ld48(uint32_t taddr, float* v) {
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+          "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+          "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(taddr), "r"(taddr + 16), "r"(taddr + 32)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 48; i++) v[i] = __uint_as_float(r[i]);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -166,9 +189,11 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 
 // Warp roles of the persistent layer kernel: warp 0 issues the copies, warp 1
-// the MMAs, warps 2-5 drain the accumulators (warp w reads tensor-memory lanes
-// 32 (w % 4) .. 32 (w % 4) + 31, so the four cover the 128 rows of a tile).
-constexpr int kTcThreads = 192;
+// the MMAs, warps 2-9 drain the accumulators in two column halves (warp w
+// reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31, so each group of
+// four covers the 128 rows of a tile).
+constexpr int kTcThreads = 320;
+constexpr int kEpiWarps = 8;
 
 // Geometry of one tensor-core layer launch (host-computed).
 struct TcGeom {
@@ -184,7 +209,10 @@ struct TcGeom {
     uint32_t tmem_cols;       // power of two >= 2 R NT (two accumulator buffers)
     int m_tiles, n_tiles;     // tiles: ceil(Q / 128 R) position tiles x output-channel tiles
     int cout;                 // channels of the bf16 output tensor (3x3 layers)
+    int up;                   // 3x3 layers: write the output 2x upsampled (nearest) into a tensor of twice the size
+    int Wbo, Qpo;             // that tensor's bordered width and positions per chunk
     int nout, H, W;           // output layer: views written, view size
+    int bias_n;               // biases staged in shared memory (<= 256)
 };
 
 // A wait that also gives up as soon as another role of the block has given
@@ -212,7 +240,8 @@ constexpr int kMaxStages = 8;
 
 // Shared memory: [stages x (A span: 2 chunks x span x 16 B | B: taps x 2 x NT x 16 B)]
 // then the barriers: full[8] +0, empty[8] +64, acc_full[2] +128, acc_empty[2]
-// +144, drain +160, tensor-memory address +168, abort word +172.
+// +144, drain +160, tensor-memory address +168, abort word +172; then the
+// layer's biases (up to 256 floats) at +1024.
 // Tile t (t = blockIdx.x, + gridDim.x, ...) covers positions (t % m_tiles) 128 R
 // .. + 128 R - 1 and output channels (t / m_tiles) NT .. + NT - 1; its
 // accumulators live in tensor-memory buffer (local tile index) % 2.
@@ -238,13 +267,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
         }
         for (int b = 0; b < 2; b++) {
             tc::init(acc_full + 8 * b, 1);
-            tc::init(acc_empty + 8 * b, 4);   // one arrival per epilogue warp
+            tc::init(acc_empty + 8 * b, kEpiWarps);   // one arrival per epilogue warp
         }
         tc::init(drain, 1);
         asm volatile("st.shared.u32 [%0], %1;" ::"r"(abort_w), "r"(0u));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    float* s_bias = reinterpret_cast<float*>(smem_raw + (bars + 1024 - tc::smem_u32(smem_raw)));
+    for (int i = tid; i < g.bias_n; i += kTcThreads) s_bias[i] = bias[i];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
                      "r"(g.tmem_cols));
@@ -337,8 +368,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
             if (!ok) atomicOr(status, 2);
         }
     } else {
-        // epilogue warps
-        const int lq = warp & 3;   // tensor-memory lane quarter
+        // epilogue warps: group cg drains column half cg of every row group
+        const int ew = warp - 2, lq = warp & 3, cg = ew >> 2;   // lane quarter, column group
         int it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, it++) {
@@ -351,53 +382,69 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
             if (!ok) break;
             tc::fence_after();
             const uint32_t trow = tmem + (uint32_t(lq * 32) << 16) + uint32_t(buf) * acc_cols;
+#pragma unroll
             for (int r = 0; r < R; r++) {
                 const int q = q0 + r * 128 + lq * 32 + lane;
                 const int y = q / g.Wb, x = q - y * g.Wb;
                 if (EPI == 0) {
                     const bool border = y == 0 || y >= g.Hb - 1 || x == 0 || x == g.Wb - 1;
-                    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + size_t(q) * 8;
-                    for (int j = 0; j < g.NT; j += 32) {
-                        float v[32];
+                    const int half = g.NT >> 1;
+                    for (int j = cg * half; j < (cg + 1) * half; j += 16) {
+                        float v[16], bv[16];
                         tc::ld16(trow + uint32_t(r * g.NT + j), v);
-                        tc::ld16(trow + uint32_t(r * g.NT + j + 16), v + 16);
-                        uint4 pk[4];
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            *reinterpret_cast<float4*>(bv + 4 * i) = reinterpret_cast<const float4*>(s_bias + n0 + j)[i];
+                        uint4 pk[2];
                         __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
 #pragma unroll
-                        for (int i = 0; i < 16; i++) {
-                            const float a0 = border ? 0.0f : fmaxf(v[2 * i] + __ldg(bias + n0 + j + 2 * i), 0.0f);
-                            const float a1 =
-                                border ? 0.0f : fmaxf(v[2 * i + 1] + __ldg(bias + n0 + j + 2 * i + 1), 0.0f);
+                        for (int i = 0; i < 8; i++) {
+                            const float a0 = border ? 0.0f : fmaxf(v[2 * i] + bv[2 * i], 0.0f);
+                            const float a1 = border ? 0.0f : fmaxf(v[2 * i + 1] + bv[2 * i + 1], 0.0f);
                             h[i] = __floats2bfloat162_rn(a0, a1);
                         }
-                        if (q < g.Q) {
+                        const int c8 = (n0 + j) / 8;
+                        if (!g.up) {
+                            if (q < g.Q) {
+                                __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + (size_t(c8) * g.Qp + q) * 8;
+                                *reinterpret_cast<uint4*>(o) = pk[0];
+                                *reinterpret_cast<uint4*>(o + size_t(g.Qp) * 8) = pk[1];
+                            }
+                        } else if (q < g.Q && !border) {
+                            // nearest 2x: pixel (y - 1, x - 1) -> the 2x2 block at (2 y - 2, 2 x - 2) of the larger image
+                            const size_t qh = size_t(2 * y - 1) * g.Wbo + size_t(2 * x - 1);
+                            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + (size_t(c8) * g.Qpo + qh) * 8;
 #pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                *reinterpret_cast<uint4*>(o + size_t((n0 + j) / 8 + k) * g.Qp * 8) = pk[k];
+                            for (int k = 0; k < 2; k++) {
+                                __nv_bfloat16* ok_ = o + size_t(k) * g.Qpo * 8;
+                                *reinterpret_cast<uint4*>(ok_) = pk[k];
+                                *reinterpret_cast<uint4*>(ok_ + 8) = pk[k];
+                                *reinterpret_cast<uint4*>(ok_ + size_t(g.Wbo) * 8) = pk[k];
+                                *reinterpret_cast<uint4*>(ok_ + size_t(g.Wbo) * 8 + 8) = pk[k];
+                            }
                         }
                     }
                 } else {
-                    // output views: column o = 3 view + channel
+                    // output views: column o = 3 view + channel; 48-column steps alternate between the groups
                     const int vy = y - 1, vx = x - 1;
                     const bool inside = q < g.Q && vy >= 0 && vy < g.H && vx >= 0 && vx < g.W;
                     uint32_t* views = static_cast<uint32_t*>(out);
                     const size_t npix = size_t(g.H) * g.W, pix = size_t(vy) * g.W + vx;
-                    for (int j = 0; j < g.NT; j += 48) {
-                        float v[48];
-                        tc::ld16(trow + uint32_t(r * g.NT + j), v);
-                        tc::ld16(trow + uint32_t(r * g.NT + j + 16), v + 16);
-                        tc::ld16(trow + uint32_t(r * g.NT + j + 32), v + 32);
+                    for (int j = cg * 48; j < g.NT; j += 96) {
+                        float v[48], bv[48];
+                        tc::ld48(trow + uint32_t(r * g.NT + j), v);
+#pragma unroll
+                        for (int i = 0; i < 12; i++)
+                            *reinterpret_cast<float4*>(bv + 4 * i) = reinterpret_cast<const float4*>(s_bias + j)[i];
 #pragma unroll
                         for (int k = 0; k < 16; k++) {
                             const int view = j / 3 + k;
-                            uint32_t word = 0xff000000u;
-#pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                const float f =
-                                    fminf(fmaxf(v[3 * k + c] + __ldg(bias + j + 3 * k + c), 0.0f), 1.0f) * 255.0f;
-                                word |= uint32_t(rintf(f)) << (8 * c);
-                            }
-                            if (inside && view < g.nout) views[size_t(view) * npix + pix] = word;
+                            // round(clamp(x + b, 0, 1) 255), half to even: saturating add, scale, convert
+                            const uint32_t r0 = __float2uint_rn(__saturatef(v[3 * k] + bv[3 * k]) * 255.0f);
+                            const uint32_t g0 = __float2uint_rn(__saturatef(v[3 * k + 1] + bv[3 * k + 1]) * 255.0f);
+                            const uint32_t b0 = __float2uint_rn(__saturatef(v[3 * k + 2] + bv[3 * k + 2]) * 255.0f);
+                            if (inside && view < g.nout)
+                                views[size_t(view) * npix + pix] = 0xff000000u | r0 | (g0 << 8) | (b0 << 16);
                         }
                     }
                 }
@@ -483,22 +530,6 @@ __global__ void k_avgpool2(const __nv_bfloat16* __restrict__ in, int H, int W, i
 #pragma unroll
         for (int e = 0; e < 8; e++) s[e] *= 0.25f;
         *reinterpret_cast<uint4*>(out + (size_t(c8) * qo + bpos(yo, xo, Wo)) * 8) = f32_to_bf16x8(s);
-    }
-}
-
-// out (level H x W, Ca + Cb channels): [0, Ca) = a (level H/2 x W/2) at
-// (y/2, x/2), [Ca, Ca + Cb) = b (level H x W); Ca, Cb % 8 == 0.
-__global__ void k_up2_concat(const __nv_bfloat16* __restrict__ a, int Ca, const __nv_bfloat16* __restrict__ b, int Cb,
-                             int H, int W, __nv_bfloat16* __restrict__ out) {
-    const size_t npx = size_t(H) * W, total = npx * ((Ca + Cb) / 8), q1 = qpad(H, W), qh = qpad(H / 2, W / 2);
-    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
-        const int c8 = int(i / npx);
-        const size_t p = i - c8 * npx;
-        const int x = int(p % W), y = int(p / W);
-        const uint4 v = 8 * c8 < Ca
-                            ? *reinterpret_cast<const uint4*>(a + (size_t(c8) * qh + bpos(y / 2, x / 2, W / 2)) * 8)
-                            : *reinterpret_cast<const uint4*>(b + (size_t(c8 - Ca / 8) * q1 + bpos(y, x, W)) * 8);
-        *reinterpret_cast<uint4*>(out + (size_t(c8) * q1 + bpos(y, x, W)) * 8) = v;
     }
 }
 
@@ -608,11 +639,12 @@ TcGeom tc_geom(int Hl, int Wl, int cin_a, int cin_b, int taps, int NT, int R, in
     g.b_bytes = uint32_t(taps * 2 * NT * 16);
     g.stage_bytes = (g.a_bytes + g.b_bytes + 1023u) & ~1023u;
     // one block per SM, as many stages as fit
-    g.stages = int(std::min<uint32_t>(uint32_t(kMaxStages), (kTcSmemMax - 2048u) / g.stage_bytes));
+    g.stages = int(std::min<uint32_t>(uint32_t(kMaxStages), (kTcSmemMax - 3072u) / g.stage_bytes));
     g.tmem_cols = pow2_cols(2 * R * NT);
     g.m_tiles = (g.Q + 128 * R - 1) / (128 * R);
     g.n_tiles = n_tiles;
     g.cout = cout;
+    g.bias_n = n_tiles * NT;
     return g;
 }
 
@@ -632,7 +664,7 @@ size_t smem_per_sm() {
 // alignment slack, and more than half of the SM's, so that one block holds
 // an SM (and its tensor memory) at a time.
 size_t tc_smem(const TcGeom& g) {
-    return std::max(size_t(g.stages) * g.stage_bytes + 1024 + 1024, smem_per_sm() / 2 + 1024);
+    return std::max(size_t(g.stages) * g.stage_bytes + 2048 + 1024, smem_per_sm() / 2 + 1024);
 }
 
 int sm_count_cached() {
@@ -648,7 +680,7 @@ int sm_count_cached() {
 bool tc_valid(const TcGeom& g) {
     return g.stages >= 2 && g.ksteps >= 1 && g.NT % 16 == 0 && g.NT >= 16 && g.NT <= 256 && g.tmem_cols <= 512 &&
            (g.taps == 9 || g.taps == 1) && g.split % 2 == 0 && g.rows <= 256 && g.m_tiles >= 1 && g.n_tiles >= 1 &&
-           tc_smem(g) <= kTcSmemMax;
+           g.bias_n >= 1 && g.bias_n <= 256 && (g.taps == 1 || (g.NT / 2) % 16 == 0) && tc_smem(g) <= kTcSmemMax;
 }
 
 cudaError_t launch_tc(int epi, const TcGeom& g, const CUtensorMap& ma, const CUtensorMap& mb, const void* wpk,
@@ -689,11 +721,12 @@ cudaError_t launch_pack(const __nv_bfloat16* src, int cout, int taps, int cin, i
     return cudaGetLastError();
 }
 
-// Output channels and row groups per tile of a 3x3 layer: 32 or 64 channels;
+// Output channels and row groups per tile of a 3x3 layer: 128, 64 or 32 channels
+// (wider tiles re-read each input span for fewer output channels);
 // the most row groups (two accumulator buffers of R NT <= 256 columns each)
 // that still give every SM two tiles or more.
 void pick_tile(int Hl, int Wl, int cout, int sm_count, int& NT, int& R) {
-    NT = cout % 64 == 0 ? 64 : 32;
+    NT = cout % 128 == 0 ? 128 : cout % 64 == 0 ? 64 : 32;
     const int64_t Q = int64_t(Hl + 2) * (Wl + 2);
     R = 1;
     for (int r : {4, 2}) {
@@ -736,10 +769,10 @@ struct lfdpr_recon {
     int* status = nullptr;            // device: failed waits (bit 0 copies, 1 MMA, 2 epilogue)
     int64_t w_off[14] = {}, b_off[14] = {};
     TcGeom geom[14] = {}, geom_out = {};
-    CUtensorMap in_map[14], out_d0, out_x0;
-    __nv_bfloat16* act = nullptr;     // activation arena (bordered tensors)
-    __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *bb, *u2, *d2a, *d2, *u1, *d1a, *d1, *u0,
-        *d0a, *d0;
+    CUtensorMap in_map[14], in_map_b[14], out_d0, out_x0;
+    __nv_bfloat16* act = nullptr;     // activation arena (chunked bordered tensors)
+    // encoder e*, pooled p*, bottleneck ba, upsampled U* (written by layers 7, 9, 11), decoder d*
+    __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *U2, *d2a, *U1, *d1a, *U0, *d0a, *d0;
 };
 
 namespace {
@@ -808,11 +841,12 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     // activation arena: every bordered tensor of the forward pass, 256-byte aligned
     int64_t Ql[4];   // positions per chunk of each level
     for (int l = 0; l < 4; l++) Ql[l] = int64_t(qpad(r->Hp >> l, r->Wp >> l));
-    const int64_t sizes[21] = {Ql[0] * 48,  Ql[0] * 32,  Ql[0] * 32,  Ql[1] * 32,  Ql[1] * 64,  Ql[1] * 64,  Ql[2] * 64,
-                               Ql[2] * 128, Ql[2] * 128, Ql[3] * 128, Ql[3] * 256, Ql[3] * 256, Ql[2] * 384, Ql[2] * 128,
-                               Ql[2] * 128, Ql[1] * 192, Ql[1] * 64,  Ql[1] * 64,  Ql[0] * 96,  Ql[0] * 32,  Ql[0] * 32};
-    int64_t offs[21], total = 0;
-    for (int k = 0; k < 21; k++) {
+    constexpr int kTensors = 18;
+    const int64_t sizes[kTensors] = {Ql[0] * 48,  Ql[0] * 32,  Ql[0] * 32, Ql[1] * 32, Ql[1] * 64,  Ql[1] * 64,
+                                     Ql[2] * 64,  Ql[2] * 128, Ql[2] * 128, Ql[3] * 128, Ql[3] * 256, Ql[2] * 256,
+                                     Ql[2] * 128, Ql[1] * 128, Ql[1] * 64,  Ql[0] * 64,  Ql[0] * 32,  Ql[0] * 32};
+    int64_t offs[kTensors], total = 0;
+    for (int k = 0; k < kTensors; k++) {
         offs[k] = total;
         total += (sizes[k] + 127) / 128 * 128;
     }
@@ -832,9 +866,9 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         free_recon(r);
         return cuda_fail(e, "create_recon: cudaMalloc");
     }
-    __nv_bfloat16** bufs[21] = {&r->x0, &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1, &r->p2, &r->e2a, &r->e2, &r->p3,
-                                &r->ba, &r->bb,  &r->u2, &r->d2a, &r->d2, &r->u1, &r->d1a, &r->d1, &r->u0, &r->d0a, &r->d0};
-    for (int k = 0; k < 21; k++) *bufs[k] = r->act + offs[k];
+    __nv_bfloat16** bufs[kTensors] = {&r->x0,  &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1,  &r->p2,  &r->e2a, &r->e2,
+                                      &r->p3,  &r->ba,  &r->U2, &r->d2a, &r->U1, &r->d1a, &r->U0, &r->d0a, &r->d0};
+    for (int k = 0; k < kTensors; k++) *bufs[k] = r->act + offs[k];
     // the output layer: its 32 weights, then the angular base over the 48
     // input channels (bf16 bit patterns: 1/8, 3/8, 5/8, 7/8 and 1 are exact)
     std::vector<uint16_t> wout(size_t(no3) * 80, 0);
@@ -860,18 +894,33 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         const int Hl = r->Hp >> L.level, Wl = r->Wp >> L.level;
         int NT, R;
         pick_tile(Hl, Wl, L.cout, r->sm_count, NT, R);
-        r->geom[l] = tc_geom(Hl, Wl, L.cin, 0, 9, NT, R, L.cout / NT, L.cout);
+        // layers 8, 10, 12 read [upsampled (map a) | skip (map b)]
+        const int cin_b = (l == 8 || l == 10 || l == 12) ? L.cin / 3 : 0;
+        r->geom[l] = tc_geom(Hl, Wl, L.cin - cin_b, cin_b, 9, NT, R, L.cout / NT, L.cout);
+        if (l == 7 || l == 9 || l == 11) {   // write 2x upsampled into the next level's tensor
+            r->geom[l].up = 1;
+            r->geom[l].Wbo = 2 * Wl + 2;
+            r->geom[l].Qpo = int(qpad(2 * Hl, 2 * Wl));
+        }
     }
     r->geom_out = tc_geom(r->Hp, r->Wp, 32, 48, 1, ntout, 1, 1, 0);
     r->geom_out.nout = r->nout;
     r->geom_out.H = r->H;
     r->geom_out.W = r->W;
     const __nv_bfloat16* conv_in[14] = {r->x0, r->e0a, r->p1, r->e1a, r->p2, r->e2a, r->p3,
-                                        r->ba, r->u2,  r->d2a, r->u1, r->d1a, r->u0, r->d0a};
+                                        r->ba, r->U2,  r->d2a, r->U1, r->d1a, r->U0, r->d0a};
+    const __nv_bfloat16* conv_skip[14] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                          nullptr, r->e2,  nullptr, r->e1,  nullptr, r->e0,  nullptr};
     bool maps_ok = true;
-    for (int l = 0; l < 14 && maps_ok; l++)
-        maps_ok = tc_valid(r->geom[l]) &&
-                  make_map(&r->in_map[l], conv_in[l], kLayers[l].cin, r->geom[l].Qp, r->geom[l].rows) == cudaSuccess;
+    for (int l = 0; l < 14 && maps_ok; l++) {
+        const TcGeom& g = r->geom[l];
+        const int cin_a = 8 * g.split;
+        maps_ok = tc_valid(g) && make_map(&r->in_map[l], conv_in[l], cin_a, g.Qp, g.rows) == cudaSuccess;
+        if (maps_ok && conv_skip[l])
+            maps_ok = make_map(&r->in_map_b[l], conv_skip[l], kLayers[l].cin - cin_a, g.Qp, g.rows) == cudaSuccess;
+        else
+            r->in_map_b[l] = r->in_map[l];
+    }
     maps_ok = maps_ok && tc_valid(r->geom_out) &&
               make_map(&r->out_d0, r->d0, 32, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess &&
               make_map(&r->out_x0, r->x0, 48, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess;
@@ -916,17 +965,13 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H0 = r->Hp, W0 = r->Wp, sm = r->sm_count;
     __nv_bfloat16* conv_out[14] = {r->e0a, r->e0, r->e1a, r->e1, r->e2a, r->e2, r->ba,
-                                   r->bb,  r->d2a, r->d2, r->d1a, r->d1, r->d0a, r->d0};
+                                   r->U2,  r->d2a, r->U1, r->d1a, r->U0, r->d0a, r->d0};
     auto conv = [&](int l) {
-        return launch_tc(0, r->geom[l], r->in_map[l], r->in_map[l], r->w + r->w_off[l], r->b + r->b_off[l],
+        return launch_tc(0, r->geom[l], r->in_map[l], r->in_map_b[l], r->w + r->w_off[l], r->b + r->b_off[l],
                          conv_out[l], r->status, s);
     };
     auto pool = [&](const __nv_bfloat16* in, int H, int W, int C, __nv_bfloat16* o) {
         k_avgpool2<<<sm * 8, 256, 0, s>>>(in, H, W, C, o);
-        return cudaGetLastError();
-    };
-    auto up = [&](const __nv_bfloat16* a, int Ca, const __nv_bfloat16* b, int Cb, int H, int W, __nv_bfloat16* o) {
-        k_up2_concat<<<sm * 8, 256, 0, s>>>(a, Ca, b, Cb, H, W, o);
         return cudaGetLastError();
     };
 #define CKR(call, what)                                      \
@@ -947,13 +992,10 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     CKR(pool(r->e2, H0 / 4, W0 / 4, 128, r->p3), "pool 3");
     CKR(conv(6), "conv 6");
     CKR(conv(7), "conv 7");
-    CKR(up(r->bb, 256, r->e2, 128, H0 / 4, W0 / 4, r->u2), "up 2");
     CKR(conv(8), "conv 8");
     CKR(conv(9), "conv 9");
-    CKR(up(r->d2, 128, r->e1, 64, H0 / 2, W0 / 2, r->u1), "up 1");
     CKR(conv(10), "conv 10");
     CKR(conv(11), "conv 11");
-    CKR(up(r->d1, 64, r->e0, 32, H0, W0, r->u0), "up 0");
     CKR(conv(12), "conv 12");
     CKR(conv(13), "conv 13");
     CKR(launch_tc(1, r->geom_out, r->out_d0, r->out_x0, r->w_out, r->b_out, out_views, r->status, s),
