@@ -609,10 +609,17 @@ def run_learned(args):
         b4 = lfdpr.lfdpr_get_buffers(dis[3], me[2])
         plain48 = lfdpr.device_view(b4.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
         q.append((RN.psnr(pred, judge), RN.ssim(pred, judge), RN.psnr(plain48, judge)))
+    # algorithmic FLOPs of one forward pass: the 3x3 layers over the padded
+    # views plus the output product over [features | inputs] (32 + 48) x 3 * 4n
     flops = 0
     hp, wp = RN.padded(H, W)
     for ci, co, lev in RN.LAYERS:
         flops += 2 * 9 * ci * co * (hp >> lev) * (wp >> lev)
+    flops += 2 * 80 * 3 * 4 * nin * hp * wp
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    net_tf = flops / (net_ms / 1000.0) / 1e12
     line = {"metric": "learned quarter-view path frames/s at PSNR vs the plain full render",
             "value": 1000.0 / ms_learned, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
@@ -621,7 +628,11 @@ def run_learned(args):
                        "l2": "flushed (512 MiB write) between timed steps"},
             "plain_full_render_frames_per_s": 1000.0 / ms_plain,
             "speedup_vs_plain": ms_plain / ms_learned,
-            "network_ms": net_ms, "network_tflops": flops / (net_ms / 1000.0) / 1e12,
+            "network_ms": net_ms, "network_tflops": net_tf,
+            "roofline": {"bound": "tensor", "achieved": net_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": net_tf / peak_tf, "traffic": None, "kernel": "the network (k_conv_tc, tcgen05)",
+                         "peak_source": "measured bf16 dense GEMM, burst" if "bf16_tflops" in peaks
+                         else "fallback 1.9 PFLOP/s bf16"},
             "psnr_db": {"mean": statistics.mean(x[0] for x in q), "min": min(x[0] for x in q)},
             "ssim": {"mean": statistics.mean(x[1] for x in q), "min": min(x[1] for x in q)},
             "psnr_db_plain_48_views_without_angular_ss": statistics.mean(x[2] for x in q),
