@@ -108,11 +108,37 @@ def lib():
             L.orc_view_pos.argtypes = [P, C.c_int]
             L.orc_subpixel_phase.restype = C.c_float
             L.orc_subpixel_phase.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            L.orc_setup_mat.restype = C.c_int
+            L.orc_setup_mat.argtypes = [P, P, P, P, P, C.c_uint32, P, C.c_uint32, P, C.c_uint32, P, P, P]
+            L.orc_fetch_mat.argtypes = [P, P, C.c_int64, P, P, P, P]
+            L.orc_resolve_pbr.argtypes = [P, P, P, P, P, P, C.c_int, P, P]
+            L.orc_pbr_shade.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P, P]
             L.orc_raycast.restype = C.c_int32
             L.orc_raycast.argtypes = [P, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(C.c_double)]
             _lib = L
     return _lib
+
+
+class OrcShading(C.Structure):
+    _fields_ = [("light_dir", C.c_float * 3), ("light_rgb", C.c_float * 3), ("ambient", C.c_float * 3)]
+
+
+def _shading(sh) -> OrcShading:
+    return OrcShading((C.c_float * 3)(*sh.light_dir), (C.c_float * 3)(*sh.light_rgb), (C.c_float * 3)(*sh.ambient))
+
+
+def pbr_shade(albedo, rough: float, metal: float, n, v, l, light_rgb, ambient) -> np.ndarray:
+    """The oracle's BRDF for one sample (unit vectors n, v, l): linear RGB
+    before clamping."""
+    a = np.ascontiguousarray(albedo, np.float64)
+    vecs = [np.ascontiguousarray(x, np.float64) for x in (n, v, l)]
+    lr = np.ascontiguousarray(light_rgb, np.float32)
+    am = np.ascontiguousarray(ambient, np.float32)
+    out = np.zeros(3, np.float64)
+    lib().orc_pbr_shade(_p(a), float(rough), float(metal), _p(vecs[0]), _p(vecs[1]), _p(vecs[2]), _p(lr), _p(am),
+                        _p(out))
+    return out
 
 
 def _p(a: np.ndarray):
@@ -210,6 +236,7 @@ class Frame:
     keys: Optional[np.ndarray] = None    # (n_list, H, W) uint64
     rgba: Optional[np.ndarray] = None    # (n_list, H, W, 4) uint8
     panel: Optional[np.ndarray] = None   # (Hp, Wp, 4) uint8
+    tvx: Optional[np.ndarray] = None     # (P, 6) uint32: normal, roughness, metallic tv_min / tv_max (materials)
 
     @property
     def offsets(self) -> np.ndarray:
@@ -238,12 +265,15 @@ def setup(d, scene, model, tex_wh=None, jitter=None):
         wh = np.array([[t.shape[1], t.shape[0]] for t in scene.textures], np.uint32).ravel()
     else:
         wh = np.ascontiguousarray(tex_wh, np.uint32).ravel()
-    st = lib().orc_setup(C.byref(dd), _p(np.ascontiguousarray(scene.xyz, np.float32)),
-                         _p(np.ascontiguousarray(scene.uv, np.float32)),
-                         _p(np.ascontiguousarray(scene.idx, np.uint32)),
-                         _p(np.ascontiguousarray(scene.tri_tex, np.uint32)), T, _p(wh),
-                         len(wh) // 2,
-                         _p(np.ascontiguousarray(model, np.float32).ravel()), _p(tri), _p(counts))
+    args = (C.byref(dd), _p(np.ascontiguousarray(scene.xyz, np.float32)),
+            _p(np.ascontiguousarray(scene.uv, np.float32)), _p(np.ascontiguousarray(scene.idx, np.uint32)),
+            _p(np.ascontiguousarray(scene.tri_tex, np.uint32)), T, _p(wh), len(wh) // 2)
+    mdl = _p(np.ascontiguousarray(model, np.float32).ravel())
+    if getattr(scene, "materials", None) is not None:
+        mats = np.ascontiguousarray(scene.materials, np.uint32)
+        st = lib().orc_setup_mat(*args, _p(mats), mats.shape[0], mdl, _p(tri), _p(counts))
+    else:
+        st = lib().orc_setup(*args, mdl, _p(tri), _p(counts))
     return st, tri, counts
 
 
@@ -256,10 +286,13 @@ def emit(tri: np.ndarray, counts: np.ndarray) -> np.ndarray:
 
 
 def render(d, scene, model, views: Optional[Sequence[int]] = None, panel: bool = True,
-           textures: Optional[Textures] = None, splat: bool = True, jitter=None, samples=None) -> Frame:
+           textures: Optional[Textures] = None, splat: bool = True, jitter=None, samples=None,
+           shading=None) -> Frame:
     """One frame through every oracle step. `views` lists the rendered views
     to splat and resolve (default all); the panel needs all of them. jitter
-    and samples: see _disp."""
+    and samples: see _disp. A scene with materials is sampled by Eq. 1 over
+    all four of a triangle's textures and fetches all four; `shading` (a
+    scenes.Shading) shades it physically (else the albedo is drawn unlit)."""
     L = lib()
     dd = _disp(d, jitter, samples)
     st, tri, counts = setup(d, scene, model, jitter=jitter)
@@ -269,8 +302,18 @@ def render(d, scene, model, views: Optional[Sequence[int]] = None, panel: bool =
     assert n == total
     points = points[:total]
     tx = textures or Textures(scene.textures)
-    L.orc_fetch(_p(tri), _p(points), total, tx.ptrs, _p(tx.wh))
+    mats = getattr(scene, "materials", None)
+    tvx = None
+    if mats is not None:
+        mats = np.ascontiguousarray(mats, np.uint32)
+        tvx = np.zeros((max(total, 1), 6), np.uint32)
+        L.orc_fetch_mat(_p(tri), _p(points), total, tx.ptrs, _p(tx.wh), _p(mats), _p(tvx))
+        tvx = tvx[:total]
+    else:
+        assert shading is None, "physically based shading needs a scene with materials"
+        L.orc_fetch(_p(tri), _p(points), total, tx.ptrs, _p(tx.wh))
     fr = Frame(status=st, tri=tri, counts=counts, points=points)
+    fr.tvx = tvx
     if not splat:
         return fr
     nr = d.n_render_views
@@ -278,7 +321,13 @@ def render(d, scene, model, views: Optional[Sequence[int]] = None, panel: bool =
     keys = np.zeros((len(vl), d.view_h, d.view_w), np.uint64)
     L.orc_splat(C.byref(dd), _p(tri), _p(points), total, _p(vl), len(vl), _p(keys))
     rgba = np.zeros((len(vl), d.view_h, d.view_w, 4), np.uint8)
-    L.orc_resolve(C.byref(dd), _p(tri), _p(points), _p(keys), _p(vl), len(vl), _p(rgba))
+    if shading is not None:
+        sh = _shading(shading)
+        tv = np.ascontiguousarray(tvx if total else np.zeros((1, 6), np.uint32))
+        L.orc_resolve_pbr(C.byref(dd), _p(tri), _p(points), _p(tv), _p(keys), _p(vl), len(vl), C.byref(sh),
+                          _p(rgba))
+    else:
+        L.orc_resolve(C.byref(dd), _p(tri), _p(points), _p(keys), _p(vl), len(vl), _p(rgba))
     fr.views_list, fr.keys, fr.rgba = vl, keys, rgba
     if panel:
         assert len(vl) == nr and np.all(vl == np.arange(nr)), "the panel needs every view"

@@ -397,10 +397,16 @@ static int n_columns(const float *T) {
  * or ORC_EOVERFLOW if some triangle needs more than ORC_MAX_CELL lattice
  * columns or rows (its count is then 0).
  */
-int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
-              const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_tris,
-              const uint32_t *tex_wh, uint32_t n_tex, const float *model,
-              float *tri_out, uint32_t *counts) {
+/* mat_tex: NULL (tri_tex holds one texture per triangle), or a material
+ * table of n_mat x 4 texture indices (albedo, normal, roughness, metallic;
+ * tri_tex then holds material indices): Eq. 1 takes the largest texel count
+ * over the material's four textures, and the record's LOD pair is the
+ * albedo's (the other textures' pairs follow from Eq. 6-7 in the fetch). */
+static int setup_impl(const orc_display *d, const float *xyz, const float *uvs,
+                      const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_tris,
+                      const uint32_t *tex_wh, uint32_t n_tex, const uint32_t *mat_tex, uint32_t n_mat,
+                      const float *model, float *tri_out, uint32_t *counts) {
+    const uint32_t n_textures = n_tex;   /* the float n_tex below shadows the count */
     int nr = orc_n_render_views(d);
     float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
     orc_eyes(d, ex);
@@ -420,8 +426,15 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
             Q[k][0] = uvs[2 * (size_t)vi];
             Q[k][1] = uvs[2 * (size_t)vi + 1];
         }
-        uint32_t tex = tri_tex[t] < n_tex ? tri_tex[t] : 0;
-        T[T_TEX] = (float)tex;
+        uint32_t tex, mat = 0;
+        if (mat_tex) {
+            mat = tri_tex[t] < n_mat ? tri_tex[t] : 0;
+            tex = mat_tex[4 * (size_t)mat] < n_tex ? mat_tex[4 * (size_t)mat] : 0;
+            T[T_TEX] = (float)mat;
+        } else {
+            tex = tri_tex[t] < n_tex ? tri_tex[t] : 0;
+            T[T_TEX] = (float)tex;
+        }
         memcpy(T + T_P0, P[0], sizeof(float) * 3);
         if (culled(d, ex, nr, P)) continue;
 
@@ -506,6 +519,12 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
         float ds2 = Q[2][0] - Q[0][0], dt2 = Q[2][1] - Q[0][1];
         float A_ts = 0.5f * fabsf(fmaf(ds1, dt2, -(dt1 * ds2)));
         float n_tex = (A_ts * (float)X) * (float)Y;
+        if (mat_tex) {   /* Eq. 1: the maximum over the material's textures */
+            for (int k = 1; k < 4; k++) {
+                uint32_t tk = mat_tex[4 * (size_t)mat + k] < n_textures ? mat_tex[4 * (size_t)mat + k] : 0;
+                n_tex = fmaxf(n_tex, (A_ts * (float)tex_wh[2 * tk]) * (float)tex_wh[2 * tk + 1]);
+            }
+        }
         if (n_tex < 1.0f) n_tex = 1.0f;   /* a triangle spans at least one texel */
         float size_uv = A_ws / n_tex;
 
@@ -564,6 +583,23 @@ int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
     return status;
 }
 
+int orc_setup(const orc_display *d, const float *xyz, const float *uvs,
+              const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_tris,
+              const uint32_t *tex_wh, uint32_t n_tex, const float *model,
+              float *tri_out, uint32_t *counts) {
+    return setup_impl(d, xyz, uvs, idx, tri_tex, n_tris, tex_wh, n_tex, NULL, 0, model, tri_out, counts);
+}
+
+/* orc_setup_mat: orc_setup for a mesh of materials (tri_mat: material per
+ * triangle, mat_tex: n_mat x 4 texture indices). */
+int orc_setup_mat(const orc_display *d, const float *xyz, const float *uvs,
+                  const uint32_t *idx, const uint32_t *tri_mat, uint32_t n_tris,
+                  const uint32_t *tex_wh, uint32_t n_tex, const uint32_t *mat_tex, uint32_t n_mat,
+                  const float *model, float *tri_out, uint32_t *counts) {
+    if (!mat_tex || n_mat == 0) return ORC_EINVAL;
+    return setup_impl(d, xyz, uvs, idx, tri_mat, n_tris, tex_wh, n_tex, mat_tex, n_mat, model, tri_out, counts);
+}
+
 /*
  * orc_emit: the point buffer. Points are numbered by triangle (exclusive
  * prefix sum of counts), then column i, then row j. Each point is four u32:
@@ -617,6 +653,46 @@ void orc_fetch(const float *tri, uint32_t *points, int64_t n_points,
         orc_trilinear(chains[tex], w, h, s, t, T[T_LOD_MAX], b);
         memcpy(&o[2], a, 4);
         memcpy(&o[3], b, 4);
+    }
+}
+
+/*
+ * orc_fetch_mat: the fetch of a mesh of materials (Sec. 3.3 with several
+ * textures): every texture of the point's material gets its own Eq. 6-7 LOD
+ * pair from the record's size_vpuv bounds and its own resolution, and its
+ * own tv_min / tv_max. The albedo's pair goes to the point (as orc_fetch);
+ * the normal, roughness and metallic pairs to tvx[6 p .. 6 p + 5].
+ */
+void orc_fetch_mat(const float *tri, uint32_t *points, int64_t n_points,
+                   const uint8_t *const *chains, const uint32_t *tex_wh,
+                   const uint32_t *mat_tex, uint32_t *tvx) {
+    for (int64_t p = 0; p < n_points; p++) {
+        uint32_t *o = points + 4 * p;
+        const float *T = tri + (size_t)o[0] * ORC_TRI_FLOATS;
+        uint32_t i = o[1] & 0xffffu, j = o[1] >> 16;
+        float uc = ((float)i + 0.5f) * T[T_SU];
+        float vc = ((float)j + 0.5f) * T[T_SV];
+        float s = fmaf(T[T_SGU], uc, fmaf(T[T_SGV], vc, T[T_S0]));
+        float t = fmaf(T[T_TGU], uc, fmaf(T[T_TGV], vc, T[T_T0]));
+        uint32_t mat = (uint32_t)T[T_TEX];
+        for (int k = 0; k < 4; k++) {
+            uint32_t tex = mat_tex[4 * (size_t)mat + k];
+            uint32_t w = tex_wh[2 * tex], h = tex_wh[2 * tex + 1];
+            float lo, hi;
+            if (k == 0) {
+                lo = T[T_LOD_MIN];
+                hi = T[T_LOD_MAX];
+            } else {
+                lo = 0.5f * orc_log2f((T[T_VPUV_MIN] * (float)w) * (float)h);
+                hi = 0.5f * orc_log2f((T[T_VPUV_MAX] * (float)w) * (float)h);
+            }
+            uint8_t a[4], b[4];
+            orc_trilinear(chains[tex], w, h, s, t, lo, a);
+            orc_trilinear(chains[tex], w, h, s, t, hi, b);
+            uint32_t *dst = k == 0 ? &o[2] : &tvx[6 * (size_t)p + 2 * (size_t)(k - 1)];
+            memcpy(&dst[0], a, 4);
+            memcpy(&dst[1], b, 4);
+        }
     }
 }
 
@@ -804,6 +880,188 @@ void orc_resolve(const orc_display *d, const float *tri, const uint32_t *points,
                 float a = tmin[c], b = tmax[c];
                 out[c] = to_u8(fmaf(w, b - a, a));
             }
+        }
+    }
+    free(ex);
+}
+
+/* -------------------------------------------------------------------------- */
+/* Physically based shading of a mesh of materials (Sec. 3.3 shades during     */
+/* view generation; Sec. 5 names a PBR shader over albedo, roughness,          */
+/* metallic and normal textures without defining it: this is the reading)      */
+/* -------------------------------------------------------------------------- */
+
+typedef struct {
+    float light_dir[3];   /* toward the light (normalised here) */
+    float light_rgb[3];   /* radiance of the directional light */
+    float ambient[3];     /* constant ambient, times albedo */
+} orc_shading;
+
+static const double kPi = 3.14159265358979323846;
+
+static void dnorm(double *v) {
+    double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (l > 0.0) { v[0] /= l; v[1] /= l; v[2] /= l; }
+}
+static double ddot(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/*
+ * orc_pbr_shade: outgoing colour (linear, 0..1 before clamping) of one
+ * surface sample: metallic-roughness microfacet BRDF with the GGX normal
+ * distribution D = a^2 / (pi ((n.h)^2 (a^2 - 1) + 1)^2), a = r^2 (r >= 0.045),
+ * Schlick-GGX visibility G = G1(n.l) G1(n.v), G1(x) = x / (x (1 - k) + k),
+ * k = (r + 1)^2 / 8, Schlick Fresnel F = F0 + (1 - F0)(1 - v.h)^5 with
+ * F0 = 0.04 (1 - m) + albedo m, diffuse (1 - F)(1 - m) albedo / pi:
+ *   rgb = (diffuse + D G F / (4 n.l n.v)) light n.l + ambient albedo,
+ * n.l clamped at 0, n.v at 1e-4. n, v, l are unit vectors.
+ */
+void orc_pbr_shade(const double *albedo, double rough, double metal, const double *n, const double *v,
+                   const double *l, const float *light_rgb, const float *ambient, double *out) {
+    double h[3] = {l[0] + v[0], l[1] + v[1], l[2] + v[2]};
+    dnorm(h);
+    double nl = ddot(n, l), nv = ddot(n, v), nh = ddot(n, h), vh = ddot(v, h);
+    if (nl < 0.0) nl = 0.0;
+    if (nv < 1e-4) nv = 1e-4;
+    if (nh < 0.0) nh = 0.0;
+    if (vh < 0.0) vh = 0.0;
+    double r = rough < 0.045 ? 0.045 : rough;
+    double a = r * r, a2 = a * a;
+    double dn = nh * nh * (a2 - 1.0) + 1.0;
+    double Dg = a2 / (kPi * dn * dn);
+    double k = (r + 1.0) * (r + 1.0) / 8.0;
+    double G = (nl / (nl * (1.0 - k) + k)) * (nv / (nv * (1.0 - k) + k));
+    double f5 = (1.0 - vh) * (1.0 - vh);
+    f5 = f5 * f5 * (1.0 - vh);
+    double den = 4.0 * nl * nv;
+    if (den < 1e-4) den = 1e-4;
+    for (int c = 0; c < 3; c++) {
+        double F0 = 0.04 * (1.0 - metal) + albedo[c] * metal;
+        double F = F0 + (1.0 - F0) * f5;
+        double diffuse = (1.0 - F) * (1.0 - metal) * albedo[c] / kPi;
+        double spec = Dg * G * F / den;
+        out[c] = (diffuse + spec) * light_rgb[c] * nl + ambient[c] * albedo[c];
+    }
+}
+
+/*
+ * Shading frame of a triangle from its record: N the unit normal; the
+ * tangent and bitangent are the world directions of increasing texture s and
+ * t (the inverse of the record's affine map over the lattice frame u-hat,
+ * v-hat), the tangent made orthogonal to N and the bitangent N x T with the
+ * sign of the t direction. A degenerate map gives u-hat and v-hat.
+ */
+static void shading_frame(const float *T, double *tg, double *bt, double *nn) {
+    for (int c = 0; c < 3; c++) nn[c] = T[T_N + c];
+    double gsu = T[T_SGU], gsv = T[T_SGV], gtu = T[T_TGU], gtv = T[T_TGV];
+    double det = gsu * gtv - gsv * gtu;
+    double dus = 1.0, dvs = 0.0, dut = 0.0, dvt = 1.0;   /* d(u, v) / d(s, t) */
+    if (det != 0.0) {
+        dus = gtv / det; dvs = -gtu / det;
+        dut = -gsv / det; dvt = gsu / det;
+    }
+    double ts[3], tt[3];
+    for (int c = 0; c < 3; c++) {
+        ts[c] = T[T_EU + c] * dus + T[T_EV + c] * dvs;
+        tt[c] = T[T_EU + c] * dut + T[T_EV + c] * dvt;
+    }
+    double dn = ddot(ts, nn);
+    for (int c = 0; c < 3; c++) tg[c] = ts[c] - nn[c] * dn;
+    dnorm(tg);
+    double cb[3] = {nn[1] * tg[2] - nn[2] * tg[1], nn[2] * tg[0] - nn[0] * tg[2], nn[0] * tg[1] - nn[1] * tg[0]};
+    double sg = ddot(cb, tt) < 0.0 ? -1.0 : 1.0;
+    for (int c = 0; c < 3; c++) bt[c] = cb[c] * sg;
+}
+
+/*
+ * orc_resolve_pbr: orc_resolve for a mesh of materials under one directional
+ * light. Per pixel: Eq. 8's weight w as in orc_resolve; each texture's value
+ * interpolated by Eq. 9 (unrounded); the surface point where the pixel
+ * centre's ray meets the triangle (the depth key's t: P = E + t (F - E)); the
+ * shading normal = the normal map's (2 c / 255 - 1) vector in the triangle's
+ * frame, flipped with the frame when the triangle faces away from the eye;
+ * colour = orc_pbr_shade, clamped to [0, 1], times 255, rounded half to even,
+ * alpha 255. tvx as written by orc_fetch_mat.
+ */
+void orc_resolve_pbr(const orc_display *d, const float *tri, const uint32_t *points, const uint32_t *tvx,
+                     const uint64_t *keys, const int32_t *views, int n_list, const orc_shading *sh,
+                     uint8_t *rgba) {
+    int nr = orc_n_render_views(d);
+    float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
+    orc_eyes(d, ex);
+    int W = d->view_w, H = d->view_h;
+    float D = d->view_dist;
+    float pw = (float)((double)d->focal_w / W), ph = (float)((double)d->focal_h / H);
+    float ipw = (float)((double)W / d->focal_w), iph = (float)((double)H / d->focal_h);
+    float x0 = -0.5f * d->focal_w, y0 = 0.5f * d->focal_h;
+    double L[3] = {sh->light_dir[0], sh->light_dir[1], sh->light_dir[2]};
+    dnorm(L);
+    size_t npix = (size_t)W * H;
+    for (int li = 0; li < n_list; li++) {
+        float Ex = ex[views[li]];
+        for (size_t o = 0; o < npix; o++) {
+            uint64_t key = keys[(size_t)li * npix + o];
+            uint8_t *out = rgba + ((size_t)li * npix + o) * 4;
+            if (key == ~0ull) { out[0] = out[1] = out[2] = out[3] = 0; continue; }
+            uint32_t p = (uint32_t)key;
+            const uint32_t *pt = points + 4 * (size_t)p;
+            const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
+            int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
+            /* Eq. 8 weight, exactly as orc_resolve */
+            float C[4][3], X[4], Y[4];
+            cell_corner(T, i, j, C[0]);
+            cell_corner(T, i + 1, j, C[1]);
+            cell_corner(T, i + 1, j + 1, C[2]);
+            cell_corner(T, i, j + 1, C[3]);
+            for (int c = 0; c < 4; c++) {
+                float s = D / (D - C[c][2]);
+                float sx = fmaf(C[c][0] - Ex, s, Ex);
+                float sy = C[c][1] * s;
+                X[c] = (sx - x0) * ipw;
+                Y[c] = (y0 - sy) * iph;
+            }
+            float acc = 0.0f;
+            for (int c = 0; c < 4; c++) {
+                int c1 = (c + 1) & 3;
+                acc = acc + fmaf(X[c], Y[c1], -(X[c1] * Y[c]));
+            }
+            float area_px = 0.5f * fabsf(acc);
+            float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
+            float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
+            float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
+            double w = vmax > vmin ? (double)((size_vs - vmin) / (vmax - vmin)) : 0.0;
+            /* Eq. 9 per texture (unrounded) */
+            const uint8_t *amin = (const uint8_t *)&pt[2], *amax = (const uint8_t *)&pt[3];
+            const uint8_t *nmin = (const uint8_t *)&tvx[6 * (size_t)p], *nmax = (const uint8_t *)&tvx[6 * (size_t)p + 1];
+            const uint8_t *rmin = (const uint8_t *)&tvx[6 * (size_t)p + 2], *rmax = (const uint8_t *)&tvx[6 * (size_t)p + 3];
+            const uint8_t *mmin = (const uint8_t *)&tvx[6 * (size_t)p + 4], *mmax = (const uint8_t *)&tvx[6 * (size_t)p + 5];
+            double alb[3], nt[3];
+            for (int c = 0; c < 3; c++) {
+                alb[c] = (amin[c] + w * ((double)amax[c] - amin[c])) / 255.0;
+                nt[c] = 2.0 * (nmin[c] + w * ((double)nmax[c] - nmin[c])) / 255.0 - 1.0;
+            }
+            double rough = (rmin[0] + w * ((double)rmax[0] - rmin[0])) / 255.0;
+            double metal = (mmin[0] + w * ((double)mmax[0] - mmin[0])) / 255.0;
+            /* surface point and view direction */
+            int px = (int)(o % (size_t)W), py = (int)(o / (size_t)W);
+            double Fx = fmaf((float)px + 0.5f, pw, x0), Fy = fmaf((float)py + 0.5f, -ph, y0);
+            double t = (double)bitsf((uint32_t)(key >> 32));
+            double P[3] = {Ex + t * (Fx - Ex), t * Fy, D - t * D};
+            double V[3] = {Ex - P[0], -P[1], D - P[2]};
+            dnorm(V);
+            double tg[3], bt[3], nn[3];
+            shading_frame(T, tg, bt, nn);
+            double n[3];
+            for (int c = 0; c < 3; c++) n[c] = nt[0] * tg[c] + nt[1] * bt[c] + nt[2] * nn[c];
+            if (ddot(n, n) == 0.0) memcpy(n, nn, sizeof n);
+            dnorm(n);
+            if (ddot(nn, V) < 0.0) for (int c = 0; c < 3; c++) n[c] = -n[c];
+            double rgb[3];
+            orc_pbr_shade(alb, rough, metal, n, V, L, sh->light_rgb, sh->ambient, rgb);
+            for (int c = 0; c < 3; c++) {
+                double v = rgb[c] < 0.0 ? 0.0 : rgb[c] > 1.0 ? 1.0 : rgb[c];
+                out[c] = (uint8_t)nearbyint(v * 255.0);
+            }
+            out[3] = 255;
         }
     }
     free(ex);

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -57,6 +57,16 @@ class Display:
         return self.n_views * (2 if self.recon in (1, 2) else 1)
 
 
+@dataclass(frozen=True)
+class Shading:
+    """Physically based shading of scenes with materials: one directional
+    light (direction toward the light, radiance per channel) and a constant
+    ambient term times albedo."""
+    light_dir: tuple = (0.35, 0.8, 0.5)
+    light_rgb: tuple = (2.4, 2.3, 2.1)
+    ambient: tuple = (0.10, 0.10, 0.12)
+
+
 def display_tiny() -> Display:
     """8 views over a 30 degree cone, 128x128 each, 512x512 panel, 8 views per
     lenslet with slant 1/6, horizontal:vertical sampling bias 4:1."""
@@ -91,9 +101,11 @@ class Scene:
     xyz: np.ndarray        # (V, 3) float32, object space
     uv: np.ndarray         # (V, 2) float32, texture coordinates (wrap addressing)
     idx: np.ndarray        # (T, 3) uint32 vertex indices
-    tri_tex: np.ndarray    # (T,) uint32 texture id per triangle
+    tri_tex: np.ndarray    # (T,) uint32 texture id per triangle (material id when `materials` is set)
     textures: List[np.ndarray] = field(default_factory=list)  # (h, w, 4) uint8
     centre: tuple = (0.0, 0.0, 0.0)
+    # (M, 4) uint32 texture ids of each material: albedo, normal, roughness, metallic
+    materials: Optional[np.ndarray] = None
 
     @property
     def n_tris(self) -> int:
@@ -158,6 +170,43 @@ def value_noise_texture(w: int, h: int, seed: int, base: int = 8,
         out[:, :, ch] = np.clip(np.rint(acc * 255.0), 0, 255).astype(np.uint8)
     out[:, :, 3] = 255
     return out
+
+
+def normal_map_texture(w: int, h: int, seed: int, strength: float = 2.0, base: int = 8) -> np.ndarray:
+    """Tangent-space normal map (RGBA8, n = 2 c / 255 - 1) of a tileable
+    value-noise height field: n = normalize(-s dh/dx, -s dh/dy, 1), with
+    periodic central differences in texels scaled to the unit square."""
+    hgt = value_noise_texture(w, h, seed, base)[:, :, 0].astype(np.float64) / 255.0
+    dx = (np.roll(hgt, -1, 1) - np.roll(hgt, 1, 1)) * (w / 2.0) / w * 8.0
+    dy = (np.roll(hgt, -1, 0) - np.roll(hgt, 1, 0)) * (h / 2.0) / h * 8.0
+    n = np.stack([-strength * dx, -strength * dy, np.ones_like(hgt)], -1)
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    out = np.empty((h, w, 4), np.uint8)
+    out[:, :, :3] = np.clip(np.rint((n * 0.5 + 0.5) * 255.0), 0, 255).astype(np.uint8)
+    out[:, :, 3] = 255
+    return out
+
+
+def scalar_texture(w: int, h: int, seed: int, lo: float, hi: float, sharpen: float = 1.0) -> np.ndarray:
+    """Tileable scalar map in R (G = B = R, alpha 255): value noise mapped to
+    [lo, hi]; sharpen > 1 pushes it towards the ends (a mostly binary mask)."""
+    v = value_noise_texture(w, h, seed)[:, :, 0].astype(np.float64) / 255.0
+    if sharpen != 1.0:
+        v = np.clip((v - 0.5) * sharpen + 0.5, 0.0, 1.0)
+    c = np.clip(np.rint((lo + (hi - lo) * v) * 255.0), 0, 255).astype(np.uint8)
+    out = np.empty((h, w, 4), np.uint8)
+    out[:, :, 0] = out[:, :, 1] = out[:, :, 2] = c
+    out[:, :, 3] = 255
+    return out
+
+
+def material_textures(sizes, seed: int) -> List[np.ndarray]:
+    """One material's four textures, sizes (albedo, normal, roughness,
+    metallic) square powers of two: value-noise albedo, a normal map, roughness
+    in [0.15, 0.95], a mostly binary metallic mask."""
+    sa, sn, sr, sm = sizes
+    return [value_noise_texture(sa, sa, seed), normal_map_texture(sn, sn, seed + 1),
+            scalar_texture(sr, sr, seed + 2, 0.15, 0.95), scalar_texture(sm, sm, seed + 3, 0.0, 1.0, sharpen=4.0)]
 
 
 # -- meshes -------------------------------------------------------------------
@@ -236,6 +285,21 @@ def scene_tiny(seed_mesh: int = 1, seed_tex: int = 2, tex_size: int = 256) -> Sc
     tex = value_noise_texture(tex_size, tex_size, seed_tex)
     return Scene(xyz=xyz, uv=uv, idx=idx, tri_tex=np.zeros(n, np.uint32),
                  textures=[tex])
+
+
+def scene_pbr_tiny(seed_mesh: int = 1, seed_tex: int = 5) -> Scene:
+    """The tiny scene with two materials (sphere, ground) of four textures
+    each (albedo, normal, roughness, metallic), coarse enough that Eq. 1
+    lowers the sampling density and with the largest texture not the albedo:
+    32/64/16/8 texels a side on the sphere (the normal map largest), 16/32/8/64
+    on the ground (the metallic mask largest)."""
+    sc = scene_tiny(seed_mesh=seed_mesh)
+    n_sph = 1280
+    mat = np.zeros(sc.n_tris, np.uint32)
+    mat[n_sph:] = 1
+    tex = material_textures((32, 64, 16, 8), seed_tex) + material_textures((16, 32, 8, 64), seed_tex + 10)
+    return Scene(xyz=sc.xyz, uv=sc.uv, idx=sc.idx, tri_tex=mat, textures=tex,
+                 materials=np.arange(8, dtype=np.uint32).reshape(2, 4))
 
 
 def _param_surface(kind: int, res: int, rng):
@@ -335,6 +399,28 @@ def scene_paper(n_instances: int = 200, res: int = 50, n_textures: int = 64,
     textures = textures_paper(n_textures, max_tex, min_tex, seed)
     sc = geometry_paper(n_instances, res, n_textures, seed, r_max, r_decades, extent)
     sc.textures = textures
+    return sc
+
+
+def scene_pbr_paper(n_materials: int = 16, seed: int = 3, min_tex: int = 64, max_tex: int = 4096, **geom) -> Scene:
+    """The paper-shaped geometry (geometry_paper) with materials instead of
+    single textures: n_materials materials of four textures each (64 textures
+    for 16 materials, as the plain scene), each texture's size drawn from the
+    powers of two min_tex^2 .. max_tex^2, so the four textures of a triangle
+    differ in resolution and Eq. 1 takes the largest."""
+    rng = np.random.default_rng(seed + 77)
+    sizes = []
+    s_ = min_tex
+    while s_ <= max_tex:
+        sizes.append(s_)
+        s_ *= 2
+    tex = []
+    for m in range(n_materials):
+        tex += material_textures(tuple(int(sizes[int(rng.integers(0, len(sizes)))]) for _ in range(4)),
+                                 seed * 1000 + 17 * m)
+    sc = geometry_paper(n_textures=n_materials, seed=seed, **geom)
+    sc.textures = tex
+    sc.materials = np.arange(4 * n_materials, dtype=np.uint32).reshape(n_materials, 4)
     return sc
 
 
