@@ -143,6 +143,12 @@ enum {
  *  keys     u64 [n_render_views][view_h][view_w]  float_bits(t) << 32 | point id,
  *                                            all ones where empty (Sec. 3.2)
  *  views    u8  [n_render_views][view_h][view_w][4] resolved RGBA8 views
+ *  resolve  u32 [max_points][20]             the resolve's per-point record: 12 f32
+ *                                            cell-corner values, splat texture area, size_vpuv
+ *                                            min, max (f32), word 15 the roughness / metallic
+ *                                            tv_min, tv_max bytes (R channels; meshes of
+ *                                            materials), words 16-19 albedo tv_min, tv_max and
+ *                                            normal-map tv_min, tv_max RGBA8 (materials)
  */
 typedef struct {
     const uint32_t *counts, *offsets, *points;
@@ -151,6 +157,7 @@ typedef struct {
     const uint8_t *views;
     int64_t n_tris, max_points;
     int32_t n_render_views, view_w, view_h;
+    const uint32_t *resolve;
 } lfdpr_buffers;
 
 /*
@@ -330,6 +337,54 @@ lfdpr_status lfdpr_upload_mesh_textured(lfdpr_display *disp, const float *xyz, c
                                         const uint32_t *idx, const uint32_t *tri_tex, uint32_t n_verts,
                                         uint32_t n_tris, lfdpr_texture_set *set, void *stream,
                                         lfdpr_mesh **out);
+
+/*
+ * Meshes of materials (several textures per triangle, Sec. 3.1 Eq. 1 and
+ * Sec. 3.3). A material is four textures of a texture set: albedo (RGB),
+ * tangent-space normal map (n = 2 c / 255 - 1 per channel), roughness (R),
+ * metallic (R), each with its own resolution. Eq. 1 takes a triangle's
+ * texel count as the largest over its material's four textures; each texture
+ * is fetched at its own Eq. 6-7 LOD pair (its resolution); the resolve
+ * interpolates every texture by Eq. 9 with the same weight.
+ *
+ * lfdpr_upload_mesh_materials: as lfdpr_upload_mesh_textured with tri_mat u32
+ * [n_tris] material per triangle and mat_tex u32 [n_mat][4] the texture ids
+ * (albedo, normal, roughness, metallic) of each material. Unlit displays draw
+ * the albedo; displays set to LFDPR_SHADING_PBR shade physically.
+ * Errors: EINVAL (ids out of range), ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_upload_mesh_materials(lfdpr_display *disp, const float *xyz, const float *uv,
+                                         const uint32_t *idx, const uint32_t *tri_mat, uint32_t n_verts,
+                                         uint32_t n_tris, const uint32_t *mat_tex, uint32_t n_mat,
+                                         lfdpr_texture_set *set, void *stream, lfdpr_mesh **out);
+
+#define LFDPR_SHADING_UNLIT 0
+#define LFDPR_SHADING_PBR 1
+
+/*
+ * Shading during view generation (Sec. 3.3). LFDPR_SHADING_UNLIT draws the
+ * interpolated albedo (the default). LFDPR_SHADING_PBR (meshes of materials
+ * only) shades every view pixel where its splat's surface point lies (the
+ * pixel centre's ray meets the triangle at the depth-tested t) for that
+ * view's own eye, under one directional light:
+ *   metallic-roughness microfacet BRDF, GGX distribution with a = r^2
+ *   (r >= 0.045), Schlick-GGX visibility with k = (r + 1)^2 / 8, Schlick
+ *   Fresnel with F0 = 0.04 (1 - m) + albedo m, diffuse (1 - F)(1 - m)
+ *   albedo / pi; rgb = (diffuse + D G F / (4 n.l n.v)) light_rgb n.l
+ *   + ambient albedo, clamped to [0, 1], times 255, rounded half to even.
+ * The shading normal is the normal map's vector in the triangle's frame
+ * (tangent and bitangent along increasing texture s and t), turned toward
+ * the eye for triangles seen from behind.
+ */
+typedef struct {
+    int32_t model;        /* LFDPR_SHADING_UNLIT or LFDPR_SHADING_PBR */
+    float light_dir[3];   /* direction toward the light (normalised by the library) */
+    float light_rgb[3];   /* radiance of the light per channel (>= 0) */
+    float ambient[3];     /* ambient term per channel, times albedo (>= 0) */
+} lfdpr_shading;
+
+/* lfdpr_set_shading: the display's shading (NULL = unlit). Errors: EINVAL. */
+lfdpr_status lfdpr_set_shading(lfdpr_display *disp, const lfdpr_shading *shading);
 
 /*
  * Batched frames: n (display, mesh) scenes, each with its own display (view

@@ -103,13 +103,21 @@ struct WorkRec {
 // Per-point data of the resolve (Eq. 8-9): the cell's four world corners
 // (x, y) and their projection factors s = D / (D - z) (computed exactly as
 // the resolve's defining formula does), the splat's texture area, the two
-// Eq. 4-5 bounds and tv_min / tv_max.
+// Eq. 4-5 bounds and tv_min / tv_max. A mesh of materials also keeps the
+// normal map's tv_min / tv_max and, in m.w's bits, the roughness and
+// metallic tv_min / tv_max (R channels, bytes 0-3).
 struct ResolveRec {
     float4 c0;    // x0 y0 s0 x1
     float4 c1;    // y1 s1 x2 y2
     float4 c2;    // s2 x3 y3 s3
-    float4 m;     // splat texture area, vpuv_min, vpuv_max, (unused)
-    uint4 tv;     // tv_min RGBA8, tv_max RGBA8, (unused)
+    float4 m;     // splat texture area, vpuv_min, vpuv_max, roughness/metallic bytes (materials)
+    uint4 tv;     // tv_min RGBA8, tv_max RGBA8, normal tv_min, tv_max (materials)
+};
+
+// Physically based shading of a mesh of materials: one directional light
+// (unit direction toward the light, radiance) and an ambient term.
+struct Shading {
+    float l[3], rgb[3], amb[3];
 };
 
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
@@ -198,7 +206,10 @@ struct FrameArgs {
     const float* xyz;
     const float* uv;
     const uint32_t* idx;
-    const uint32_t* tri_tex;
+    const uint32_t* tri_tex;         // texture per triangle, or material per triangle when mat_tex is set
+    const uint4* mat_tex;            // null, or [materials] texture ids: albedo, normal, roughness, metallic
+    int pbr;                         // shade physically (needs mat_tex)
+    Shading sh;
     const TexDesc* tex;
     const uint8_t* pool;
     const uint64_t* lvl;             // [n_tex][kMaxLevels] byte offset of each mip level in the pool
@@ -224,6 +235,7 @@ cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_fetch_mat(const FrameArgs& a, cudaStream_t s);   // meshes of materials, after launch_fetch
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s);
 
 // One scene of a batched splat: its display constants and the buffers the

@@ -40,6 +40,8 @@ struct lfdpr_display {
     cudaEvent_t ev[LFDPR_N_STAGES + 2] = {};
     bool ev_frame = false;        // the frame's stage events were recorded
     bool ev_interleave = false;   // the interleave's events were recorded
+    int shading = LFDPR_SHADING_UNLIT;
+    lfdpr::Shading sh{};          // light (unit direction), radiance, ambient
 };
 
 struct lfdpr_mesh {
@@ -48,7 +50,9 @@ struct lfdpr_mesh {
     float* xyz = nullptr;
     float* uv = nullptr;
     uint32_t* idx = nullptr;
-    uint32_t* tri_tex = nullptr;
+    uint32_t* tri_tex = nullptr;              // texture (or, with materials, material) per triangle
+    uint4* mat_tex = nullptr;                 // materials: [n_mat] albedo, normal, roughness, metallic texture ids
+    uint32_t n_mat = 0;
     lfdpr_texture_set* shared = nullptr;   // the texture set whose pool/tex/lvl the mesh uses
     bool owns_textures = false;            // pool/tex/lvl are the mesh's own (freed with it)
     uint8_t* pool = nullptr;

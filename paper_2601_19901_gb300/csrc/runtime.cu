@@ -38,6 +38,9 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.uv = mesh->uv;
     a.idx = mesh->idx;
     a.tri_tex = mesh->tri_tex;
+    a.mat_tex = mesh->mat_tex;
+    a.pbr = mesh->mat_tex != nullptr && disp->shading == LFDPR_SHADING_PBR;
+    a.sh = disp->sh;
     a.tex = mesh->tex;
     a.pool = mesh->pool;
     a.lvl = mesh->lvl;
@@ -83,6 +86,10 @@ lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const Fra
         mk(3);
         CKF(launch_fetch(a, s), "launch k_fetch");
         disp->launches += 4;
+        if (a.mat_tex) {
+            CKF(launch_fetch_mat(a, s), "launch k_fetch_mat");
+            disp->launches += 1;
+        }
     } else {
         for (int k = 1; k <= 3; k++) mk(k);
     }
@@ -150,6 +157,7 @@ void free_mesh(lfdpr_mesh* m) {
     cudaFree(m->uv);
     cudaFree(m->idx);
     cudaFree(m->tri_tex);
+    cudaFree(m->mat_tex);
     if (m->owns_textures) {
         cudaFree(m->pool);
         cudaFree(m->tex);
@@ -557,6 +565,66 @@ lfdpr_status lfdpr_upload_mesh_textured(lfdpr_display* disp, const float* xyz, c
     return LFDPR_OK;
 }
 
+lfdpr_status lfdpr_upload_mesh_materials(lfdpr_display* disp, const float* xyz, const float* uv, const uint32_t* idx,
+                                         const uint32_t* tri_mat, uint32_t n_verts, uint32_t n_tris,
+                                         const uint32_t* mat_tex, uint32_t n_mat, lfdpr_texture_set* set,
+                                         void* stream, lfdpr_mesh** out) {
+    g_err[0] = 0;
+    if (!disp || !out || !set || !mat_tex) return fail(LFDPR_EINVAL, "upload_mesh_materials: null argument");
+    *out = nullptr;
+    if (n_mat == 0 || n_mat > (1u << 24)) return fail(LFDPR_EINVAL, "upload_mesh_materials: 1..2^24 materials");
+    for (uint64_t k = 0; k < 4ull * n_mat; k++)
+        if (mat_tex[k] >= set->n_tex)
+            return fail(LFDPR_EINVAL, "upload_mesh_materials: material %llu names texture %u of %u",
+                        (unsigned long long)(k / 4), mat_tex[k], set->n_tex);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lfdpr_mesh* m = nullptr;
+    // the material ids are checked against n_mat like texture ids
+    const lfdpr_status st = upload_geometry(disp, xyz, uv, idx, tri_mat, n_verts, n_tris, n_mat, s, &m);
+    if (st != LFDPR_OK) return st;
+    cudaError_t e = cudaMalloc(&m->mat_tex, 16ull * n_mat);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->mat_tex, mat_tex, 16ull * n_mat, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_mesh(m);
+        return cuda_fail(e, "upload_mesh_materials: material table");
+    }
+    m->n_mat = n_mat;
+    m->shared = set;
+    m->pool = set->pool;
+    m->tex = set->tex;
+    m->lvl = set->lvl;
+    set->n_meshes++;
+    disp->n_meshes++;
+    *out = m;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_shading(lfdpr_display* disp, const lfdpr_shading* sh) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "set_shading: null display");
+    if (!sh || sh->model == LFDPR_SHADING_UNLIT) {
+        disp->shading = LFDPR_SHADING_UNLIT;
+        return LFDPR_OK;
+    }
+    if (sh->model != LFDPR_SHADING_PBR) return fail(LFDPR_EINVAL, "set_shading: unknown model %d", sh->model);
+    for (int k = 0; k < 3; k++)
+        if (!std::isfinite(sh->light_dir[k]) || !std::isfinite(sh->light_rgb[k]) || !std::isfinite(sh->ambient[k]) ||
+            sh->light_rgb[k] < 0.0f || sh->ambient[k] < 0.0f)
+            return fail(LFDPR_EINVAL, "set_shading: light values must be finite, radiance and ambient >= 0");
+    const double l2 = double(sh->light_dir[0]) * sh->light_dir[0] + double(sh->light_dir[1]) * sh->light_dir[1] +
+                      double(sh->light_dir[2]) * sh->light_dir[2];
+    if (!(l2 > 0.0)) return fail(LFDPR_EINVAL, "set_shading: zero light direction");
+    const double l = std::sqrt(l2);
+    for (int k = 0; k < 3; k++) {
+        disp->sh.l[k] = float(sh->light_dir[k] / l);
+        disp->sh.rgb[k] = sh->light_rgb[k];
+        disp->sh.amb[k] = sh->ambient[k];
+    }
+    disp->shading = LFDPR_SHADING_PBR;
+    return LFDPR_OK;
+}
+
 lfdpr_status lfdpr_destroy_mesh(lfdpr_mesh* mesh) {
     g_err[0] = 0;
     if (!mesh) return fail(LFDPR_EINVAL, "destroy_mesh: null");
@@ -570,6 +638,8 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     g_err[0] = 0;
     if (!disp || !mesh || !model) return fail(LFDPR_EINVAL, "render_frame: null argument");
     if (mesh->disp != disp) return fail(LFDPR_EINVAL, "render_frame: mesh uploaded to another display");
+    if (disp->shading == LFDPR_SHADING_PBR && !mesh->mat_tex)
+        return fail(LFDPR_EINVAL, "render_frame: physically based shading needs a mesh of materials");
     for (int k = 0; k < 12; k++)
         if (!std::isfinite(model[k])) return fail(LFDPR_EINVAL, "render_frame: non-finite model matrix");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -672,6 +742,7 @@ lfdpr_status lfdpr_get_buffers(lfdpr_display* disp, lfdpr_mesh* mesh, lfdpr_buff
     out->n_render_views = disp->dc.nr;
     out->view_w = disp->dc.W;
     out->view_h = disp->dc.H;
+    out->resolve = reinterpret_cast<const uint32_t*>(disp->rrec);
     return LFDPR_OK;
 }
 

@@ -270,13 +270,28 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     // LFD-biased spacings and Eq. 1-3
     const float su0 = (c.bias_h * dmin) * c.px, sv0 = (c.bias_v * dmin) * c.py;
     const float size_xy = su0 * sv0;
-    const uint32_t tex = a.tri_tex[t];
+    // a mesh of materials: the albedo sets the record's LOD pair, Eq. 1 takes
+    // the largest texel count of the material's four textures
+    uint32_t tex = a.tri_tex[t];
+    uint4 mt = make_uint4(0u, 0u, 0u, 0u);
+    if (a.mat_tex) {
+        mt = a.mat_tex[tex];
+        tex = mt.x;
+    }
     const TexDesc td = a.tex[tex];
     const float X = float(td.w), Y = float(td.h);
     const float ds1 = Q[1][0] - Q[0][0], dt1 = Q[1][1] - Q[0][1];
     const float ds2 = Q[2][0] - Q[0][0], dt2 = Q[2][1] - Q[0][1];
     const float A_ts = 0.5f * fabsf(fmaf(ds1, dt2, -(dt1 * ds2)));
     float n_tex = (A_ts * X) * Y;
+    if (a.mat_tex) {
+        const uint32_t ids[3] = {mt.y, mt.z, mt.w};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const TexDesc tk = a.tex[ids[k]];
+            n_tex = fmaxf(n_tex, (A_ts * float(tk.w)) * float(tk.h));
+        }
+    }
     if (n_tex < 1.0f) n_tex = 1.0f;
     const float size_uv = __fdiv_rn(A_ws, n_tex);
     float su = su0, sv = sv0;
@@ -630,7 +645,8 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         const float vc = (float(j) + 0.5f) * sv;
         const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
         const float t = fmaf(q7.x, uc, fmaf(q7.y, vc, q6.w));
-        const uint32_t texid = __ldg(a.tri_tex + pt.x);
+        uint32_t texid = __ldg(a.tri_tex + pt.x);
+        if (a.mat_tex) texid = __ldg(&a.mat_tex[texid].x);   // a material's albedo (k_fetch_mat: its other maps)
         const TexDesc td = a.tex[texid];
         uint32_t tmin, tmax;
         trilinear_pair(a.pool, a.lvl + (size_t)texid * kMaxLevels, td.w, td.h, int(td.levels) - 1, s, t, q7.z,
@@ -719,6 +735,44 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
     }
 }
 
+// The normal, roughness and metallic maps of every point of a mesh of
+// materials (run after k_fetch): each texture at its own Eq. 6-7 LOD pair
+// (the record's size_vpuv bounds and its resolution), at the cell centre's
+// texture coordinate (as k_fetch); the normal map's two RGBA8 values go to
+// the resolve record's tv.z / tv.w, the roughness and metallic R channels to
+// m.w as bytes (min, max, min, max).
+__global__ void __launch_bounds__(256) k_fetch_mat(FrameArgs a) {
+    if (a.ctr->overflow) return;
+    const uint32_t n = a.ctr->n_points;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        const TriRec* r = a.rec + pt.x;
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q5 = __ldg(&r->q[5]);
+        const float4 q6 = __ldg(&r->q[6]), q7 = __ldg(&r->q[7]);
+        const uint32_t i = pt.y & 0xffffu, j = pt.y >> 16;
+        const float uc = (float(i) + 0.5f) * q0.w;
+        const float vc = (float(j) + 0.5f) * q1.w;
+        const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
+        const float t = fmaf(q7.x, uc, fmaf(q7.y, vc, q6.w));
+        const uint4 mt = __ldg(a.mat_tex + __ldg(a.tri_tex + pt.x));
+        uint32_t lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t id = k == 0 ? mt.y : k == 1 ? mt.z : mt.w;
+            const TexDesc tk = a.tex[id];
+            const float lod_lo = 0.5f * log2_series((q5.y * float(tk.w)) * float(tk.h));
+            const float lod_hi = 0.5f * log2_series((q5.z * float(tk.w)) * float(tk.h));
+            trilinear_pair(a.pool, a.lvl + (size_t)id * kMaxLevels, tk.w, tk.h, int(tk.levels) - 1, s, t, lod_lo,
+                           lod_hi, lo[k], hi[k]);
+        }
+        ResolveRec* rr = a.rrec + p;
+        rr->tv.z = lo[0];
+        rr->tv.w = hi[0];
+        rr->m.w = __uint_as_float((lo[1] & 255u) | ((hi[1] & 255u) << 8) | ((lo[2] & 255u) << 16) |
+                                  ((hi[2] & 255u) << 24));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s) {
@@ -733,6 +787,11 @@ cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s) {
 
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s) {
     k_emit<<<a.n_blocks, kSetupThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fetch_mat(const FrameArgs& a, cudaStream_t s) {
+    k_fetch_mat<<<a.sm_count * 8, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

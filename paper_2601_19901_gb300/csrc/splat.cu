@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
 // Eq. 8-9 for one view pixel whose depth test kept point record rp (the
 // caller has already loaded it): the splat's pixel area in view Ex is the
 // shoelace area of its cell corners projected from the eye.
-__device__ __forceinline__ uint32_t resolve_pixel(const DispConst& c, float Ex, const float4& c0, const float4& c1,
-                                                  const float4& c2, const float4& m, const uint4& tv) {
+__device__ __forceinline__ float eq8_weight(const DispConst& c, float Ex, const float4& c0, const float4& c1,
+                                            const float4& c2, const float4& m) {
     const float cx[4] = {c0.x, c0.w, c1.z, c2.y}, cy[4] = {c0.y, c1.x, c1.w, c2.z};
     const float cs[4] = {c0.z, c1.y, c2.x, c2.w};
     float X[4], Y[4];
@@ -374,7 +374,12 @@ __device__ __forceinline__ uint32_t resolve_pixel(const DispConst& c, float Ex, 
     const float vmin = m.y, vmax = m.z;
     const float size_vse = __fdiv_rn(m.x, fminf(1.0f, area_px));
     const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
-    const float w = vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
+    return vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
+}
+
+__device__ __forceinline__ uint32_t resolve_pixel(const DispConst& c, float Ex, const float4& c0, const float4& c1,
+                                                  const float4& c2, const float4& m, const uint4& tv) {
+    const float w = eq8_weight(c, Ex, c0, c1, c2, m);
     uint32_t out = 0u;
 #pragma unroll
     for (int ch = 0; ch < 4; ch++) {
@@ -398,6 +403,128 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
         const ResolveRec* rp = a.rrec + uint32_t(key);
         out = resolve_pixel(c, __ldg(a.ex + v), __ldg(&rp->c0), __ldg(&rp->c1), __ldg(&rp->c2), __ldg(&rp->m),
                             __ldg(&rp->tv));
+    }
+    reinterpret_cast<uint32_t*>(a.views)[o] = out;
+}
+
+// ---------------------------------------------------------------------------
+// Physically based resolve of a mesh of materials
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float dot(const float3& a, const float3& b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+__device__ __forceinline__ float3 normalized(const float3& v) {
+    const float l = __fsqrt_rn(dot(v, v));
+    return l > 0.0f ? f3(__fdiv_rn(v.x, l), __fdiv_rn(v.y, l), __fdiv_rn(v.z, l)) : v;
+}
+
+// Outgoing linear RGB of one surface sample (unit n, v, l): metallic-roughness
+// microfacet BRDF, GGX distribution D = a^2 / (pi ((n.h)^2 (a^2 - 1) + 1)^2),
+// a = r^2 (r >= 0.045), Schlick-GGX visibility G1(x) = x / (x (1 - k) + k),
+// k = (r + 1)^2 / 8, Schlick Fresnel F = F0 + (1 - F0)(1 - v.h)^5, F0 = 0.04
+// (1 - m) + albedo m, diffuse (1 - F)(1 - m) albedo / pi:
+//   rgb = (diffuse + D G F / (4 n.l n.v)) light n.l + ambient albedo.
+__device__ __forceinline__ float3 pbr_shade(const float3& albedo, float rough, float metal, const float3& n,
+                                            const float3& v, const float3& l, const Shading& sh) {
+    const float3 h = normalized(f3(l.x + v.x, l.y + v.y, l.z + v.z));
+    const float nl = fmaxf(dot(n, l), 0.0f), nv = fmaxf(dot(n, v), 1e-4f);
+    const float nh = fmaxf(dot(n, h), 0.0f), vh = fmaxf(dot(v, h), 0.0f);
+    const float r = fmaxf(rough, 0.045f);
+    const float a = r * r, a2 = a * a;
+    const float dn = fmaf(nh * nh, a2 - 1.0f, 1.0f);
+    const float Dg = __fdiv_rn(a2, 3.14159265358979f * dn * dn);
+    const float k = (r + 1.0f) * (r + 1.0f) * 0.125f;
+    const float G = __fdiv_rn(nl, fmaf(nl, 1.0f - k, k)) * __fdiv_rn(nv, fmaf(nv, 1.0f - k, k));
+    const float om = 1.0f - vh;
+    const float f5 = (om * om) * (om * om) * om;
+    const float den = fmaxf(4.0f * nl * nv, 1e-4f);
+    const float spec_dg = __fdiv_rn(Dg * G, den);
+    const float alb[3] = {albedo.x, albedo.y, albedo.z};
+    float o[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const float F0 = fmaf(alb[ch], metal, 0.04f * (1.0f - metal));
+        const float F = fmaf(1.0f - F0, f5, F0);
+        const float diffuse = __fdiv_rn((1.0f - F) * (1.0f - metal) * alb[ch], 3.14159265358979f);
+        o[ch] = fmaf((diffuse + spec_dg * F) * sh.rgb[ch], nl, sh.amb[ch] * alb[ch]);
+    }
+    return f3(o[0], o[1], o[2]);
+}
+
+// One view pixel per thread: Eq. 8's weight as k_resolve; each map's value
+// interpolated by Eq. 9 (unrounded); the surface point where the pixel
+// centre's ray meets the triangle (the key's t: P = E + t (F - E)); the
+// shading normal = the normal map's (2 c / 255 - 1) vector in the triangle's
+// frame (tangent and bitangent = world directions of increasing s and t, from
+// the inverse of the record's texture map over u-hat, v-hat; tangent made
+// orthogonal to N, bitangent = N x T signed by the t direction), flipped when
+// the triangle faces away from the eye; RGB = pbr_shade clamped, times 255,
+// rounded half to even, alpha 255.
+__global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
+    const DispConst& c = a.dc;
+    const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
+    const uint32_t px = blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= npix) return;
+    const int v = blockIdx.y;
+    const uint64_t o = (uint64_t)v * npix + px;
+    const unsigned long long key = a.keys[o];
+    uint32_t out = 0u;
+    if (key != ~0ull) {
+        const uint32_t p = uint32_t(key);
+        const float t = __uint_as_float(uint32_t(key >> 32));
+        const float Ex = __ldg(a.ex + v);
+        const ResolveRec* rp = a.rrec + p;
+        const float4 m = __ldg(&rp->m);
+        const uint4 tv = __ldg(&rp->tv);
+        const float w = eq8_weight(c, Ex, __ldg(&rp->c0), __ldg(&rp->c1), __ldg(&rp->c2), m);
+        auto lerp8 = [w](uint32_t lo, uint32_t hi, int ch) {
+            const float a0 = float((lo >> (8 * ch)) & 255u), b0 = float((hi >> (8 * ch)) & 255u);
+            return fmaf(w, b0 - a0, a0);
+        };
+        const float3 albedo = f3(lerp8(tv.x, tv.y, 0) * (1.0f / 255.0f), lerp8(tv.x, tv.y, 1) * (1.0f / 255.0f),
+                                 lerp8(tv.x, tv.y, 2) * (1.0f / 255.0f));
+        const float3 nt = f3(fmaf(lerp8(tv.z, tv.w, 0), 2.0f / 255.0f, -1.0f), fmaf(lerp8(tv.z, tv.w, 1), 2.0f / 255.0f, -1.0f),
+                             fmaf(lerp8(tv.z, tv.w, 2), 2.0f / 255.0f, -1.0f));
+        const uint32_t rm = __float_as_uint(m.w);
+        const float rough = fmaf(w, float((rm >> 8) & 255u) - float(rm & 255u), float(rm & 255u)) * (1.0f / 255.0f);
+        const float metal =
+            fmaf(w, float(rm >> 24) - float((rm >> 16) & 255u), float((rm >> 16) & 255u)) * (1.0f / 255.0f);
+        // surface point and view direction
+        const int x = int(px % uint32_t(c.W)), y = int(px / uint32_t(c.W));
+        const float Fx = fmaf(float(x) + 0.5f, c.pw, c.x0), Fy = fmaf(float(y) + 0.5f, -c.ph, c.y0);
+        const float3 P = f3(fmaf(t, Fx - Ex, Ex), t * Fy, fmaf(-t, c.D, c.D));
+        const float3 V = normalized(f3(Ex - P.x, -P.y, c.D - P.z));
+        // the triangle's shading frame
+        const TriRec* r = a.rec + __ldg(&a.points[p].x);
+        const float4 q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]), q3 = __ldg(&r->q[3]);
+        const float4 q6 = __ldg(&r->q[6]), q7 = __ldg(&r->q[7]);
+        const float3 N = f3(q3.x, q3.y, q3.z);
+        const float gsu = q6.y, gsv = q6.z, gtu = q7.x, gtv = q7.y;
+        const float det = fmaf(gsu, gtv, -(gsv * gtu));
+        float dus = 1.0f, dvs = 0.0f, dut = 0.0f, dvt = 1.0f;
+        if (det != 0.0f) {
+            dus = __fdiv_rn(gtv, det);
+            dvs = __fdiv_rn(-gtu, det);
+            dut = __fdiv_rn(-gsv, det);
+            dvt = __fdiv_rn(gsu, det);
+        }
+        const float3 ts = f3(fmaf(q1.x, dus, q2.x * dvs), fmaf(q1.y, dus, q2.y * dvs), fmaf(q1.z, dus, q2.z * dvs));
+        const float3 tt = f3(fmaf(q1.x, dut, q2.x * dvt), fmaf(q1.y, dut, q2.y * dvt), fmaf(q1.z, dut, q2.z * dvt));
+        const float dn = dot(ts, N);
+        const float3 Tg = normalized(f3(fmaf(-N.x, dn, ts.x), fmaf(-N.y, dn, ts.y), fmaf(-N.z, dn, ts.z)));
+        float3 Bt = f3(fmaf(N.y, Tg.z, -(N.z * Tg.y)), fmaf(N.z, Tg.x, -(N.x * Tg.z)), fmaf(N.x, Tg.y, -(N.y * Tg.x)));
+        if (dot(Bt, tt) < 0.0f) Bt = f3(-Bt.x, -Bt.y, -Bt.z);
+        float3 n = f3(fmaf(nt.x, Tg.x, fmaf(nt.y, Bt.x, nt.z * N.x)), fmaf(nt.x, Tg.y, fmaf(nt.y, Bt.y, nt.z * N.y)),
+                      fmaf(nt.x, Tg.z, fmaf(nt.y, Bt.z, nt.z * N.z)));
+        if (dot(n, n) == 0.0f) n = N;
+        n = normalized(n);
+        if (dot(N, V) < 0.0f) n = f3(-n.x, -n.y, -n.z);
+        const float3 rgb = pbr_shade(albedo, rough, metal, n, V, f3(a.sh.l[0], a.sh.l[1], a.sh.l[2]), a.sh);
+        out = 0xff000000u | (uint32_t(__float2uint_rn(__saturatef(rgb.x) * 255.0f))) |
+              (uint32_t(__float2uint_rn(__saturatef(rgb.y) * 255.0f)) << 8) |
+              (uint32_t(__float2uint_rn(__saturatef(rgb.z) * 255.0f)) << 16);
     }
     reinterpret_cast<uint32_t*>(a.views)[o] = out;
 }
@@ -447,7 +574,10 @@ cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s) {
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {
     const uint32_t npix = uint32_t(a.dc.W) * uint32_t(a.dc.H);
     const dim3 grid((npix + 255u) / 256u, uint32_t(a.dc.nr));
-    k_resolve<<<grid, 256, 0, s>>>(a);
+    if (a.pbr)
+        k_resolve_pbr<<<grid, 256, 0, s>>>(a);
+    else
+        k_resolve<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

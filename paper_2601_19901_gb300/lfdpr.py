@@ -31,6 +31,7 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc",
            "lfdpr_set_view_jitter", "lfdpr_set_recon_samples",
            "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
+           "lfdpr_upload_mesh_materials", "lfdpr_set_shading",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
            "lfdpr_batch_autotune_table",
@@ -77,7 +78,16 @@ class Buffers(C.Structure):
     _fields_ = [("counts", C.c_void_p), ("offsets", C.c_void_p), ("points", C.c_void_p),
                 ("tri", C.c_void_p), ("keys", C.c_void_p), ("views", C.c_void_p),
                 ("n_tris", C.c_int64), ("max_points", C.c_int64),
-                ("n_render_views", C.c_int32), ("view_w", C.c_int32), ("view_h", C.c_int32)]
+                ("n_render_views", C.c_int32), ("view_w", C.c_int32), ("view_h", C.c_int32),
+                ("resolve", C.c_void_p)]
+
+
+SHADING_UNLIT, SHADING_PBR = 0, 1
+
+
+class ShadingDesc(C.Structure):
+    _fields_ = [("model", C.c_int32), ("light_dir", C.c_float * 3), ("light_rgb", C.c_float * 3),
+                ("ambient", C.c_float * 3)]
 
 
 _lib = None
@@ -109,6 +119,9 @@ def lib() -> C.CDLL:
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
         L.lfdpr_create_texture_set.argtypes = [P, P, C.c_uint32, P, C.POINTER(C.c_void_p)]
         L.lfdpr_destroy_texture_set.argtypes = [P]
+        L.lfdpr_upload_mesh_materials.argtypes = [P, P, P, P, P, C.c_uint32, C.c_uint32, P, C.c_uint32, P, P,
+                                                  C.POINTER(C.c_void_p)]
+        L.lfdpr_set_shading.argtypes = [P, P]
         L.lfdpr_upload_mesh_textured.argtypes = [P, P, P, P, P, C.c_uint32, C.c_uint32, P, P,
                                                  C.POINTER(C.c_void_p)]
         L.lfdpr_create_batch.argtypes = [P, P, C.c_int32, C.POINTER(C.c_void_p)]
@@ -305,6 +318,31 @@ def lfdpr_upload_mesh_textured(disp: int, xyz: np.ndarray, uv: np.ndarray, idx: 
     return h.value
 
 
+def lfdpr_upload_mesh_materials(disp: int, xyz: np.ndarray, uv: np.ndarray, idx: np.ndarray,
+                                tri_mat: np.ndarray, mat_tex: np.ndarray, tex_set: int, stream=None) -> int:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    uv = np.ascontiguousarray(uv, np.float32)
+    idx = np.ascontiguousarray(idx, np.uint32)
+    tri_mat = np.ascontiguousarray(tri_mat, np.uint32)
+    mat_tex = np.ascontiguousarray(mat_tex, np.uint32).reshape(-1, 4)
+    h = C.c_void_p()
+    _check(lib().lfdpr_upload_mesh_materials(disp, _ptr(xyz), _ptr(uv), _ptr(idx), _ptr(tri_mat), xyz.shape[0],
+                                             idx.reshape(-1, 3).shape[0], _ptr(mat_tex), mat_tex.shape[0], tex_set,
+                                             _stream(stream), C.byref(h)))
+    return h.value
+
+
+def lfdpr_set_shading(disp: int, shading=None):
+    """shading: None (unlit) or an object with light_dir, light_rgb, ambient
+    (three floats each; e.g. scenes.Shading) for physically based shading."""
+    if shading is None:
+        _check(lib().lfdpr_set_shading(disp, None))
+        return
+    d = ShadingDesc(SHADING_PBR, (C.c_float * 3)(*shading.light_dir), (C.c_float * 3)(*shading.light_rgb),
+                    (C.c_float * 3)(*shading.ambient))
+    _check(lib().lfdpr_set_shading(disp, C.byref(d)))
+
+
 def lfdpr_create_batch(displays: Sequence[int], meshes: Sequence[int]) -> int:
     n = len(displays)
     dp = (C.c_void_p * n)(*displays)
@@ -406,14 +444,29 @@ def lfdpr_conv3x3_bf16(in_ptr: int, H: int, W: int, cin: int, w_ptr: int, b_ptr:
 class Renderer:
     """One display and one mesh on the current CUDA device."""
 
-    def __init__(self, display, scene, max_points: int = 0, stream=None):
+    def __init__(self, display, scene, max_points: int = 0, stream=None, shading=None):
+        """A scene with materials is uploaded as a mesh of materials (its
+        textures as a texture set); `shading` (e.g. scenes.Shading) shades it
+        physically."""
         self.display = display
         self.disp = lfdpr_create_display(desc_of(display, max_points))
         self.mesh = None
+        self.texset = None
         try:
-            self.mesh = lfdpr_upload_mesh(self.disp, scene.xyz, scene.uv, scene.idx,
-                                          scene.tri_tex, scene.textures, stream)
+            if getattr(scene, "materials", None) is not None:
+                self.texset = TextureSet(scene.textures, stream)
+                self.mesh = lfdpr_upload_mesh_materials(self.disp, scene.xyz, scene.uv, scene.idx, scene.tri_tex,
+                                                        scene.materials, self.texset.handle, stream)
+            else:
+                self.mesh = lfdpr_upload_mesh(self.disp, scene.xyz, scene.uv, scene.idx,
+                                              scene.tri_tex, scene.textures, stream)
+            if shading is not None:
+                lfdpr_set_shading(self.disp, shading)
         except Exception:
+            if self.mesh is not None:
+                lfdpr_destroy_mesh(self.mesh)
+            if self.texset is not None:
+                self.texset.close()
             lfdpr_destroy_display(self.disp)
             raise
 
@@ -445,6 +498,9 @@ class Renderer:
         if self.mesh is not None:
             lfdpr_destroy_mesh(self.mesh)
             self.mesh = None
+        if getattr(self, "texset", None) is not None:
+            self.texset.close()
+            self.texset = None
         if self.disp is not None:
             lfdpr_destroy_display(self.disp)
             self.disp = None
