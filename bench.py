@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["paper", "angular", "gauss", "gauss2x", "tiny", "batch", "learned"],
+    p.add_argument("--config", choices=["paper", "angular", "gauss", "gauss2x", "tiny", "pbr", "batch", "learned"],
                    default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -84,7 +84,17 @@ def workload(cfg):
                 WORKLOAD.replace("48 views", "96 views at random angles in their intervals, Gaussian "
                                              "reconstruction (8 samples, spatial diameter 2.25 px, angular "
                                              "support 2 views) to 48 (+crosstalk 0.15)"))
+    if cfg == "pbr":
+        return (S.display_paper(), S.scene_pbr_paper(),
+                WORKLOAD.replace("64 RGBA8 textures 64^2-4096^2",
+                                 "16 materials of four RGBA8 textures (albedo, normal, roughness, metallic) "
+                                 "64^2-4096^2 each, physically based shading (one directional light + ambient)"))
     return S.display_paper(), S.scene_paper(), WORKLOAD
+
+
+def shading_of(cfg):
+    from paper_2601_19901_gb300 import scenes as S
+    return S.Shading() if cfg == "pbr" else None
 
 
 # ---------------------------------------------------------------------------
@@ -147,7 +157,7 @@ class ClockSampler:
 # CPU oracle timing (the cpu_baseline object and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_frame_estimate(d, sc, model, gpu_views=None, textures=None):
+def oracle_frame_estimate(d, sc, model, gpu_views=None, textures=None, shading=None):
     """Time the oracle on a bounded sample of one frame: the full per-triangle
     set-up, emission and fetch; splat + resolve of two rendered views, scaled
     to all of them; the interleave of the full panel. Returns (seconds per
@@ -159,7 +169,7 @@ def oracle_frame_estimate(d, sc, model, gpu_views=None, textures=None):
     nr = d.n_render_views
     vs = [0, nr // 2]
     t0 = time.perf_counter()
-    O.splat_resolve(d, fr.tri, fr.points, vs)
+    O.splat_resolve(d, fr.tri, fr.points, vs, tvx=fr.tvx, shading=shading)
     t_sr = (time.perf_counter() - t0) / len(vs)
     if gpu_views is None:
         gpu_views = np.zeros((nr, d.view_h, d.view_w, 4), np.uint8)
@@ -189,7 +199,7 @@ def run_reference(args):
     sample = None
     spent = []
     for k in range(args.warmup + args.steps):
-        est, sample, cost = oracle_frame_estimate(d, sc, S.model_matrix(k), textures=tx)
+        est, sample, cost = oracle_frame_estimate(d, sc, S.model_matrix(k), textures=tx, shading=shading_of(args.config))
         spent.append(cost)
         if k >= args.warmup:
             times.append(est)
@@ -283,7 +293,8 @@ def run_ours(args):
 
     d, sc, wl = workload(args.config)
     stream = torch.cuda.Stream()
-    R = lfdpr.Renderer(d, sc, max_points=(1 << 24) if args.config == "gauss2x" else 0, stream=stream)
+    R = lfdpr.Renderer(d, sc, max_points=(1 << 24) if args.config == "gauss2x" else 0, stream=stream,
+                       shading=shading_of(args.config))
     R.set_stage_timing(True)
     if d.recon in (2, 3):
         # Sec. 4's random angles and Gaussian samples (seeded; sigma = diameter / 4, in output
@@ -417,7 +428,7 @@ def run_ours(args):
         import oracle as O
         O.build()
         views = lfdpr.device_to_numpy(b.views, (d.n_render_views, d.view_h, d.view_w, 4), np.uint8)
-        est, desc, _ = oracle_frame_estimate(d, sc, frame_model(0), gpu_views=views)
+        est, desc, _ = oracle_frame_estimate(d, sc, frame_model(0), gpu_views=views, shading=shading_of(args.config))
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": "frames/s", "cores": 1, "kind": "oracle",
                                 "sample": desc}
     print(json.dumps(line), flush=True)

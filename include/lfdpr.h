@@ -221,7 +221,7 @@ lfdpr_status lfdpr_upload_mesh(lfdpr_display *disp, const float *xyz, const floa
 lfdpr_status lfdpr_destroy_mesh(lfdpr_mesh *mesh);
 
 /*
- * lfdpr_render_frame: one frame of the hot path (Sec. 3, Fig. 3) on `stream`:
+ * lfdpr_render_frame: one frame of the hot path (Sec. 3, Fig. 4) on `stream`:
  * transform by `model` (row-major 4x4, host memory, affine rows 0-2 used),
  * cull, per-triangle sampling set-up (Sec. 3.1, Eq. 1-7), scan, point emission,
  * tv_min/tv_max fetch (Sec. 3.3), splatting into every rendered view

@@ -347,15 +347,24 @@ def splat_hits(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int]) -> 
     return hits
 
 
-def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int], jitter=None):
-    """Steps 9-10 for the listed views, from existing records and points."""
+def splat_resolve(d, tri: np.ndarray, points: np.ndarray, views: Sequence[int], jitter=None,
+                  tvx: Optional[np.ndarray] = None, shading=None):
+    """Steps 9-10 for the listed views, from existing records and points
+    (with `shading`, the physically based resolve of a mesh of materials,
+    whose other maps' values `tvx` orc_fetch_mat wrote)."""
     dd = _disp(d, jitter)
     vl = np.asarray(views, np.int32)
     pts = np.ascontiguousarray(points, np.uint32)
     keys = np.zeros((len(vl), d.view_h, d.view_w), np.uint64)
     lib().orc_splat(C.byref(dd), _p(tri), _p(pts), len(pts), _p(vl), len(vl), _p(keys))
     rgba = np.zeros((len(vl), d.view_h, d.view_w, 4), np.uint8)
-    lib().orc_resolve(C.byref(dd), _p(tri), _p(pts), _p(keys), _p(vl), len(vl), _p(rgba))
+    if shading is not None:
+        sh = _shading(shading)
+        tv = np.ascontiguousarray(tvx if tvx is not None and len(tvx) else np.zeros((1, 6), np.uint32), np.uint32)
+        lib().orc_resolve_pbr(C.byref(dd), _p(tri), _p(pts), _p(tv), _p(keys), _p(vl), len(vl), C.byref(sh),
+                              _p(rgba))
+    else:
+        lib().orc_resolve(C.byref(dd), _p(tri), _p(pts), _p(keys), _p(vl), len(vl), _p(rgba))
     return keys, rgba
 
 

@@ -12,7 +12,7 @@
  *   3. the triangle's sampling frame aligned with the views' horizontal and
  *      vertical axes (Sec. 3.1, T_align);
  *   4. LFD-biased horizontal and vertical sample spacings from pixel edges
- *      reverse-projected at the closest point of the triangle (Sec. 3.1, Fig. 4);
+ *      reverse-projected at the closest point of the triangle (Sec. 3.1, Fig. 5);
  *   5. texture-based sampling, Eq. 1-3 (Sec. 3.1);
  *   6. multiview-mipmap setup, Eq. 4-7 (Sec. 3.3);
  *   7. one point per sampling-lattice cell overlapping the triangle;
@@ -483,7 +483,7 @@ static int setup_impl(const orc_display *d, const float *xyz, const float *uvs,
         T[T_UMAX] = fmaxf(fmaxf(U[0], U[1]), U[2]);
         T[T_VMAX] = fmaxf(fmaxf(V[0], V[1]), V[2]);
 
-        /* closest and farthest eye over all views (Fig. 4: pixel edges are
+        /* closest and farthest eye over all views (Fig. 5: pixel edges are
          * reverse-projected around the point of the triangle closest to the
          * eye). The eye's distance to the triangle: its height over the plane
          * and its in-plane distance to the 2-D triangle. */

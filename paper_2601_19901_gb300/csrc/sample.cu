@@ -200,7 +200,7 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     const float V[3] = {0.0f - vmin, b1 - vmin, b2 - vmin};
     const float umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
 
-    // closest and farthest eye (Fig. 4): height over the plane plus the
+    // closest and farthest eye (Fig. 5): height over the plane plus the
     // in-plane distance to the 2-D triangle; min and max over every rendered
     // view. exact_d2(v) is the defining formula for view v. Only views that
     // can hold the minimum or the maximum are evaluated with it: cheap bounds
