@@ -709,6 +709,38 @@ static void cell_corner(const float *T, int a, int b, float o[3]) {
 }
 
 /*
+ * Eq. 8's projected splat area, as an affine function of the eye's x. A world
+ * point C projects (from eye (Ex, 0, D) through z = 0) to pixel x = a + b Ex
+ * with s = D / (D - Cz), a = (Cx s - x0) W/fw, b = (1 - s) W/fw, and pixel
+ * y = (y0 - Cy s) H/fh, the same in every view. The shoelace sum of the cell's
+ * four projected corners is therefore alpha + beta Ex, alpha the sum over
+ * corners of a_k Y_k+1 - a_k+1 Y_k and beta the same with b; the pixel area is
+ * |alpha + beta Ex| / 2. Both sides take alpha and beta in this order.
+ */
+static void cell_area_coeffs(const float *T, int i, int j, float D, float x0, float y0, float ipw, float iph,
+                             float *alpha, float *beta) {
+    float C[4][3], a[4], b[4], Y[4];
+    cell_corner(T, i, j, C[0]);
+    cell_corner(T, i + 1, j, C[1]);
+    cell_corner(T, i + 1, j + 1, C[2]);
+    cell_corner(T, i, j + 1, C[3]);
+    for (int c = 0; c < 4; c++) {
+        float s = D / (D - C[c][2]);
+        a[c] = fmaf(C[c][0], s, -x0) * ipw;
+        b[c] = (1.0f - s) * ipw;
+        Y[c] = (y0 - C[c][1] * s) * iph;
+    }
+    float al = 0.0f, be = 0.0f;
+    for (int c = 0; c < 4; c++) {
+        int c1 = (c + 1) & 3;
+        al = al + fmaf(a[c], Y[c1], -(a[c1] * Y[c]));
+        be = be + fmaf(b[c], Y[c1], -(b[c1] * Y[c]));
+    }
+    *alpha = al;
+    *beta = be;
+}
+
+/*
  * orc_splat: for every point and every listed view, each pixel whose centre
  * ray hits the triangle's plane inside the point's cell and inside the
  * triangle (EPR's inside-triangle test), at a depth within [near, far], gets
@@ -827,7 +859,8 @@ void orc_splat_hits(const orc_display *d, const float *tri, const uint32_t *poin
 /*
  * orc_resolve: per listed view and pixel, the winning point's colour. The
  * splat's pixel area is the shoelace area of its cell's four corners
- * projected into the view (= size_ndc * 0.25 * X_v * Y_v of Eq. 8). Eq. 8
+ * projected into the view (= size_ndc * 0.25 * X_v * Y_v of Eq. 8), taken as
+ * |alpha + beta Ex| / 2 (cell_area_coeffs). Eq. 8
  * grows the splat's texture area when it covers less than a pixel and clamps
  * it to [size_vpuv_min, size_vpuv_max]; Eq. 9 interpolates tv between tv_min
  * and tv_max per channel. Empty pixels are (0, 0, 0, 0).
@@ -853,24 +886,9 @@ void orc_resolve(const orc_display *d, const float *tri, const uint32_t *points,
             const uint32_t *pt = points + 4 * (size_t)(uint32_t)key;
             const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
             int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
-            float C[4][3], X[4], Y[4];
-            cell_corner(T, i, j, C[0]);
-            cell_corner(T, i + 1, j, C[1]);
-            cell_corner(T, i + 1, j + 1, C[2]);
-            cell_corner(T, i, j + 1, C[3]);
-            for (int c = 0; c < 4; c++) {
-                float s = D / (D - C[c][2]);
-                float sx = fmaf(C[c][0] - Ex, s, Ex);
-                float sy = C[c][1] * s;
-                X[c] = (sx - x0) * ipw;
-                Y[c] = (y0 - sy) * iph;
-            }
-            float acc = 0.0f;
-            for (int c = 0; c < 4; c++) {
-                int c1 = (c + 1) & 3;
-                acc = acc + fmaf(X[c], Y[c1], -(X[c1] * Y[c]));
-            }
-            float area_px = 0.5f * fabsf(acc);
+            float alpha, beta;
+            cell_area_coeffs(T, i, j, D, x0, y0, ipw, iph, &alpha, &beta);
+            float area_px = 0.5f * fabsf(fmaf(beta, Ex, alpha));
             float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
             float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
             float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
@@ -1007,24 +1025,9 @@ void orc_resolve_pbr(const orc_display *d, const float *tri, const uint32_t *poi
             const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
             int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
             /* Eq. 8 weight, exactly as orc_resolve */
-            float C[4][3], X[4], Y[4];
-            cell_corner(T, i, j, C[0]);
-            cell_corner(T, i + 1, j, C[1]);
-            cell_corner(T, i + 1, j + 1, C[2]);
-            cell_corner(T, i, j + 1, C[3]);
-            for (int c = 0; c < 4; c++) {
-                float s = D / (D - C[c][2]);
-                float sx = fmaf(C[c][0] - Ex, s, Ex);
-                float sy = C[c][1] * s;
-                X[c] = (sx - x0) * ipw;
-                Y[c] = (y0 - sy) * iph;
-            }
-            float acc = 0.0f;
-            for (int c = 0; c < 4; c++) {
-                int c1 = (c + 1) & 3;
-                acc = acc + fmaf(X[c], Y[c1], -(X[c1] * Y[c]));
-            }
-            float area_px = 0.5f * fabsf(acc);
+            float alpha, beta;
+            cell_area_coeffs(T, i, j, D, x0, y0, ipw, iph, &alpha, &beta);
+            float area_px = 0.5f * fabsf(fmaf(beta, Ex, alpha));
             float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
             float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
             float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
