@@ -143,12 +143,14 @@ enum {
  *  keys     u64 [n_render_views][view_h][view_w]  float_bits(t) << 32 | point id,
  *                                            all ones where empty (Sec. 3.2)
  *  views    u8  [n_render_views][view_h][view_w][4] resolved RGBA8 views
- *  resolve  u32 [max_points][20]             the resolve's per-point record: 12 f32
- *                                            cell-corner values, splat texture area, size_vpuv
- *                                            min, max (f32), word 15 the roughness / metallic
- *                                            tv_min, tv_max bytes (R channels; meshes of
- *                                            materials), words 16-19 albedo tv_min, tv_max and
- *                                            normal-map tv_min, tv_max RGBA8 (materials)
+ *  resolve  u32 [max_points][8]              the resolve's per-point record: alpha, beta (the
+ *                                            splat's pixel area in the view of eye x Ex is
+ *                                            |alpha + beta Ex| / 2), splat texture area, size_vpuv
+ *                                            min, max (f32), tv_min, tv_max (RGBA8), roughness /
+ *                                            metallic tv_min, tv_max bytes (R channels; meshes of
+ *                                            materials)
+ *  resolve_mat u32 [max_points][2]           normal-map tv_min, tv_max RGBA8 (meshes of materials;
+ *                                            NULL before the display's first such mesh)
  */
 typedef struct {
     const uint32_t *counts, *offsets, *points;
@@ -157,7 +159,7 @@ typedef struct {
     const uint8_t *views;
     int64_t n_tris, max_points;
     int32_t n_render_views, view_w, view_h;
-    const uint32_t *resolve;
+    const uint32_t *resolve, *resolve_mat;
 } lfdpr_buffers;
 
 /*

@@ -100,18 +100,15 @@ struct WorkRec {
     float4 L0, L1;
     uint4 meta;   // y0 | n_rows << 14 | flags << 29, i | j << 16, triangle, point
 };
-// Per-point data of the resolve (Eq. 8-9): the cell's four world corners
-// (x, y) and their projection factors s = D / (D - z) (computed exactly as
-// the resolve's defining formula does), the splat's texture area, the two
-// Eq. 4-5 bounds and tv_min / tv_max. A mesh of materials also keeps the
-// normal map's tv_min / tv_max and, in m.w's bits, the roughness and
-// metallic tv_min / tv_max (R channels, bytes 0-3).
+// Per-point data of the resolve (Eq. 8-9): the splat's pixel area in view
+// Ex is |alpha + beta Ex| / 2 (the shoelace sum of its cell's projected
+// corners is affine in the eye's x, see k_fetch), the splat's texture area,
+// the two Eq. 4-5 bounds and tv_min / tv_max; for a mesh of materials also
+// the roughness and metallic tv_min / tv_max (R channels, bytes 0-3 of b.w).
+// 32 bytes: one sector per gather.
 struct ResolveRec {
-    float4 c0;    // x0 y0 s0 x1
-    float4 c1;    // y1 s1 x2 y2
-    float4 c2;    // s2 x3 y3 s3
-    float4 m;     // splat texture area, vpuv_min, vpuv_max, roughness/metallic bytes (materials)
-    uint4 tv;     // tv_min RGBA8, tv_max RGBA8, normal tv_min, tv_max (materials)
+    float4 a;     // alpha, beta, splat texture area, vpuv_min
+    uint4 b;      // vpuv_max bits, tv_min RGBA8, tv_max RGBA8, roughness/metallic bytes (materials)
 };
 
 // Physically based shading of a mesh of materials: one directional light
@@ -225,6 +222,7 @@ struct FrameArgs {
     WorkRec* work;                   // [max_points] the splat's work list
     uint32_t* near;                  // [max_points] points whose cell or triangle reaches the eyes' plane
     ResolveRec* rrec;                // [max_points] per-point resolve data
+    uint2* rmat;                     // [max_points] normal-map tv_min, tv_max (meshes of materials)
     uint64_t* keys;
     uint8_t* views;
     Counters* ctr;

@@ -30,6 +30,7 @@ struct lfdpr_display {
     lfdpr::WorkRec* work = nullptr;
     uint32_t* near = nullptr;
     lfdpr::ResolveRec* rrec = nullptr;
+    uint2* rmat = nullptr;        // normal-map tv_min / tv_max per point (allocated with the first mesh of materials)
     uint64_t* keys = nullptr;
     uint8_t* views = nullptr;
     uint8_t* panel = nullptr;      // device scratch for host-memory panels

@@ -57,6 +57,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.work = disp->work;
     a.near = disp->near;
     a.rrec = disp->rrec;
+    a.rmat = disp->rmat;
     a.keys = disp->keys;
     a.views = disp->views;
     a.ctr = disp->ctr;
@@ -144,6 +145,7 @@ void free_display(lfdpr_display* d) {
     cudaFree(d->work);
     cudaFree(d->near);
     cudaFree(d->rrec);
+    cudaFree(d->rmat);
     cudaFree(d->keys);
     cudaFree(d->views);
     cudaFree(d->panel);
@@ -578,6 +580,11 @@ lfdpr_status lfdpr_upload_mesh_materials(lfdpr_display* disp, const float* xyz, 
             return fail(LFDPR_EINVAL, "upload_mesh_materials: material %llu names texture %u of %u",
                         (unsigned long long)(k / 4), mat_tex[k], set->n_tex);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the display's per-point normal-map values, on its first mesh of materials
+    if (!disp->rmat) {
+        const cudaError_t e = cudaMalloc(&disp->rmat, sizeof(uint2) * (uint64_t)disp->max_points);
+        if (e != cudaSuccess) return cuda_fail(e, "upload_mesh_materials: normal-map buffer");
+    }
     lfdpr_mesh* m = nullptr;
     // the material ids are checked against n_mat like texture ids
     const lfdpr_status st = upload_geometry(disp, xyz, uv, idx, tri_mat, n_verts, n_tris, n_mat, s, &m);
@@ -743,6 +750,7 @@ lfdpr_status lfdpr_get_buffers(lfdpr_display* disp, lfdpr_mesh* mesh, lfdpr_buff
     out->view_w = disp->dc.W;
     out->view_h = disp->dc.H;
     out->resolve = reinterpret_cast<const uint32_t*>(disp->rrec);
+    out->resolve_mat = reinterpret_cast<const uint32_t*>(disp->rmat);
     return LFDPR_OK;
 }
 

@@ -704,12 +704,26 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
             L1.z = L1.z - (0.5f - kBoxPad);
         }
 
+        // Eq. 8's projected cell area is |alpha + beta Ex| / 2: a corner's pixel
+        // x is a + b Ex (a = (x s - x0) W/fw, b = (1 - s) W/fw, s = D / (D - z)),
+        // its pixel y the same in every view, so the shoelace sum is affine in Ex
+        float pa[4], pb[4], py[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            pa[k] = fmaf(Cx[k], Cs[k], -c.x0) * c.ipw;
+            pb[k] = (1.0f - Cs[k]) * c.ipw;
+            py[k] = (c.y0 - Cy[k] * Cs[k]) * c.iph;
+        }
+        float alpha = 0.0f, beta = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int k1 = (k + 1) & 3;
+            alpha = alpha + fmaf(pa[k], py[k1], -(pa[k1] * py[k]));
+            beta = beta + fmaf(pb[k], py[k1], -(pb[k1] * py[k]));
+        }
         ResolveRec* rr = a.rrec + p;
-        rr->c0 = make_float4(Cx[0], Cy[0], Cs[0], Cx[1]);
-        rr->c1 = make_float4(Cy[1], Cs[1], Cx[2], Cy[2]);
-        rr->c2 = make_float4(Cs[2], Cx[3], Cy[3], Cs[3]);
-        rr->m = make_float4(q5.x, q5.y, q5.z, 0.0f);
-        rr->tv = make_uint4(tmin, tmax, 0u, 0u);
+        rr->a = make_float4(alpha, beta, q5.x, q5.y);
+        rr->b = make_uint4(__float_as_uint(q5.z), tmin, tmax, 0u);
 
         // warp-aggregated appends: points with candidate rows to the work
         // list, points reaching the eyes' plane to the near list
@@ -739,8 +753,8 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
 // materials (run after k_fetch): each texture at its own Eq. 6-7 LOD pair
 // (the record's size_vpuv bounds and its resolution), at the cell centre's
 // texture coordinate (as k_fetch); the normal map's two RGBA8 values go to
-// the resolve record's tv.z / tv.w, the roughness and metallic R channels to
-// m.w as bytes (min, max, min, max).
+// rmat, the roughness and metallic R channels to the resolve record's b.w as
+// bytes (min, max, min, max).
 __global__ void __launch_bounds__(256) k_fetch_mat(FrameArgs a) {
     if (a.ctr->overflow) return;
     const uint32_t n = a.ctr->n_points;
@@ -765,11 +779,8 @@ __global__ void __launch_bounds__(256) k_fetch_mat(FrameArgs a) {
             trilinear_pair(a.pool, a.lvl + (size_t)id * kMaxLevels, tk.w, tk.h, int(tk.levels) - 1, s, t, lod_lo,
                            lod_hi, lo[k], hi[k]);
         }
-        ResolveRec* rr = a.rrec + p;
-        rr->tv.z = lo[0];
-        rr->tv.w = hi[0];
-        rr->m.w = __uint_as_float((lo[1] & 255u) | ((hi[1] & 255u) << 8) | ((lo[2] & 255u) << 16) |
-                                  ((hi[2] & 255u) << 24));
+        a.rmat[p] = make_uint2(lo[0], hi[0]);
+        a.rrec[p].b.w = (lo[1] & 255u) | ((hi[1] & 255u) << 8) | ((lo[2] & 255u) << 16) | ((hi[2] & 255u) << 24);
     }
 }
 

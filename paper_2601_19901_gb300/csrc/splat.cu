@@ -5,9 +5,9 @@
 //              inside the point's projected cell and its projected triangle,
 //              at a depth in [near, far], does
 //              atomicMin(key, float_bits(t) << 32 | point id).
-//   k_resolve  one thread per view pixel: the winning point's cell corners
-//              (from its resolve record) are projected for the splat's pixel
-//              area (shoelace), Eq. 8 gives the view's texture area, Eq. 9
+//   k_resolve  one thread per view pixel: the winning point's 32-byte resolve
+//              record gives the splat's pixel area in this view
+//              (|alpha + beta Ex| / 2), Eq. 8 the view's texture area, Eq. 9
 //              interpolates tv_min..tv_max.
 #include "lfdpr_internal.cuh"
 
@@ -349,41 +349,24 @@ __global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
     if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
 }
 
-// Eq. 8-9 for one view pixel whose depth test kept point record rp (the
-// caller has already loaded it): the splat's pixel area in view Ex is the
-// shoelace area of its cell corners projected from the eye.
-__device__ __forceinline__ float eq8_weight(const DispConst& c, float Ex, const float4& c0, const float4& c1,
-                                            const float4& c2, const float4& m) {
-    const float cx[4] = {c0.x, c0.w, c1.z, c2.y}, cy[4] = {c0.y, c1.x, c1.w, c2.z};
-    const float cs[4] = {c0.z, c1.y, c2.x, c2.w};
-    float X[4], Y[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float sx = fmaf(cx[k] - Ex, cs[k], Ex);
-        const float sy = cy[k] * cs[k];
-        X[k] = (sx - c.x0) * c.ipw;
-        Y[k] = (c.y0 - sy) * c.iph;
-    }
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int k1 = (k + 1) & 3;
-        acc = acc + fmaf(X[k], Y[k1], -(X[k1] * Y[k]));
-    }
-    const float area_px = 0.5f * fabsf(acc);
-    const float vmin = m.y, vmax = m.z;
-    const float size_vse = __fdiv_rn(m.x, fminf(1.0f, area_px));
+// Eq. 8's interpolation weight for one view pixel whose depth test kept the
+// point with resolve record (ra, rb): the splat's pixel area in view Ex is
+// the shoelace area of its cell corners projected from the eye,
+// |alpha + beta Ex| / 2.
+__device__ __forceinline__ float eq8_weight(float Ex, const float4& ra, const uint4& rb) {
+    const float area_px = 0.5f * fabsf(fmaf(ra.y, Ex, ra.x));
+    const float vmin = ra.w, vmax = __uint_as_float(rb.x);
+    const float size_vse = __fdiv_rn(ra.z, fminf(1.0f, area_px));
     const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
     return vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
 }
 
-__device__ __forceinline__ uint32_t resolve_pixel(const DispConst& c, float Ex, const float4& c0, const float4& c1,
-                                                  const float4& c2, const float4& m, const uint4& tv) {
-    const float w = eq8_weight(c, Ex, c0, c1, c2, m);
+__device__ __forceinline__ uint32_t resolve_pixel(float Ex, const float4& ra, const uint4& rb) {
+    const float w = eq8_weight(Ex, ra, rb);
     uint32_t out = 0u;
 #pragma unroll
     for (int ch = 0; ch < 4; ch++) {
-        const float lo = float((tv.x >> (8 * ch)) & 255u), hi = float((tv.y >> (8 * ch)) & 255u);
+        const float lo = float((rb.y >> (8 * ch)) & 255u), hi = float((rb.z >> (8 * ch)) & 255u);
         out |= uint32_t(round_u8(fmaf(w, hi - lo, lo))) << (8 * ch);
     }
     return out;
@@ -401,8 +384,7 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
     uint32_t out = 0u;
     if (key != ~0ull) {
         const ResolveRec* rp = a.rrec + uint32_t(key);
-        out = resolve_pixel(c, __ldg(a.ex + v), __ldg(&rp->c0), __ldg(&rp->c1), __ldg(&rp->c2), __ldg(&rp->m),
-                            __ldg(&rp->tv));
+        out = resolve_pixel(__ldg(a.ex + v), __ldg(&rp->a), __ldg(&rp->b));
     }
     reinterpret_cast<uint32_t*>(a.views)[o] = out;
 }
@@ -476,18 +458,19 @@ __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
         const float t = __uint_as_float(uint32_t(key >> 32));
         const float Ex = __ldg(a.ex + v);
         const ResolveRec* rp = a.rrec + p;
-        const float4 m = __ldg(&rp->m);
-        const uint4 tv = __ldg(&rp->tv);
-        const float w = eq8_weight(c, Ex, __ldg(&rp->c0), __ldg(&rp->c1), __ldg(&rp->c2), m);
+        const float4 ra = __ldg(&rp->a);
+        const uint4 rb = __ldg(&rp->b);
+        const uint2 nm = __ldg(a.rmat + p);
+        const float w = eq8_weight(Ex, ra, rb);
         auto lerp8 = [w](uint32_t lo, uint32_t hi, int ch) {
             const float a0 = float((lo >> (8 * ch)) & 255u), b0 = float((hi >> (8 * ch)) & 255u);
             return fmaf(w, b0 - a0, a0);
         };
-        const float3 albedo = f3(lerp8(tv.x, tv.y, 0) * (1.0f / 255.0f), lerp8(tv.x, tv.y, 1) * (1.0f / 255.0f),
-                                 lerp8(tv.x, tv.y, 2) * (1.0f / 255.0f));
-        const float3 nt = f3(fmaf(lerp8(tv.z, tv.w, 0), 2.0f / 255.0f, -1.0f), fmaf(lerp8(tv.z, tv.w, 1), 2.0f / 255.0f, -1.0f),
-                             fmaf(lerp8(tv.z, tv.w, 2), 2.0f / 255.0f, -1.0f));
-        const uint32_t rm = __float_as_uint(m.w);
+        const float3 albedo = f3(lerp8(rb.y, rb.z, 0) * (1.0f / 255.0f), lerp8(rb.y, rb.z, 1) * (1.0f / 255.0f),
+                                 lerp8(rb.y, rb.z, 2) * (1.0f / 255.0f));
+        const float3 nt = f3(fmaf(lerp8(nm.x, nm.y, 0), 2.0f / 255.0f, -1.0f), fmaf(lerp8(nm.x, nm.y, 1), 2.0f / 255.0f, -1.0f),
+                             fmaf(lerp8(nm.x, nm.y, 2), 2.0f / 255.0f, -1.0f));
+        const uint32_t rm = rb.w;
         const float rough = fmaf(w, float((rm >> 8) & 255u) - float(rm & 255u), float(rm & 255u)) * (1.0f / 255.0f);
         const float metal =
             fmaf(w, float(rm >> 24) - float((rm >> 16) & 255u), float((rm >> 16) & 255u)) * (1.0f / 255.0f);

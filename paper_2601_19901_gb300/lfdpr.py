@@ -79,7 +79,7 @@ class Buffers(C.Structure):
                 ("tri", C.c_void_p), ("keys", C.c_void_p), ("views", C.c_void_p),
                 ("n_tris", C.c_int64), ("max_points", C.c_int64),
                 ("n_render_views", C.c_int32), ("view_w", C.c_int32), ("view_h", C.c_int32),
-                ("resolve", C.c_void_p)]
+                ("resolve", C.c_void_p), ("resolve_mat", C.c_void_p)]
 
 
 SHADING_UNLIT, SHADING_PBR = 0, 1

@@ -34,11 +34,12 @@ def _gpu_tvx(R, n_points: int) -> np.ndarray:
     oracle's layout: (normal min, normal max, rough min, rough max, metal min,
     metal max), roughness and metallic as R bytes."""
     b = R.buffers()
-    rr = lfdpr.device_to_numpy(b.resolve, (n_points, 20), np.uint32)
-    rm = rr[:, 15]
+    rr = lfdpr.device_to_numpy(b.resolve, (n_points, 8), np.uint32)
+    nm = lfdpr.device_to_numpy(b.resolve_mat, (n_points, 2), np.uint32)
+    rm = rr[:, 7]
     out = np.zeros((n_points, 6), np.uint32)
-    out[:, 0] = rr[:, 18]
-    out[:, 1] = rr[:, 19]
+    out[:, 0] = nm[:, 0]
+    out[:, 1] = nm[:, 1]
     for k in range(4):
         out[:, 2 + k] = (rm >> np.uint32(8 * k)) & np.uint32(255)
     return out
