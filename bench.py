@@ -612,14 +612,14 @@ def run_learned(args):
         plain(f)
         torch.cuda.synchronize()
         bf = lfdpr.lfdpr_get_buffers(dis[1], me[1])
-        judge = RN.tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
+        truth = RN.tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
         bo = lfdpr.lfdpr_get_buffers(dis[2], me[0])
         pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
         lfdpr.lfdpr_render_frame(dis[3], me[2], S.model_matrix(f), stream)
         torch.cuda.synchronize()
         b4 = lfdpr.lfdpr_get_buffers(dis[3], me[2])
         plain48 = lfdpr.device_view(b4.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
-        q.append((RN.psnr(pred, judge), RN.ssim(pred, judge), RN.psnr(plain48, judge)))
+        q.append((RN.psnr(pred, truth), RN.ssim(pred, truth), RN.psnr(plain48, truth)))
     # algorithmic FLOPs of one forward pass: the 3x3 layers over the padded
     # views plus the output product over [features | inputs] (32 + 48) x 3 * 4n
     flops = 0

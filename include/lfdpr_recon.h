@@ -7,7 +7,7 @@
  * the 4n-view display), and a small U-Net predicts the 4n views of the full
  * display after angular supersampling and reconstruction (Sec. 4's 2x
  * angular rate with the [1/4, 1/2, 1/4] tent). The full render is its
- * fallback and the judge of its error.
+ * fallback and the ground truth its error is measured against.
  *
  * Network (fixed architecture, weights supplied by the caller): input = the n
  * views' RGB / 255 as 3n channels (zero padded to 48), views padded with zeros

@@ -9,7 +9,7 @@ linear angular interpolation of the input views. This module holds
   * reference_forward: the same forward pass in fp32 that rounds to bf16
     wherever the library's kernels store bf16 (the numerics reference the
     tests hold the library's tensor-core kernels to);
-  * the judge's views (tent_views) and the error measures (psnr, ssim);
+  * the ground-truth views (tent_views) and the error measures (psnr, ssim);
   * train: the offline trainer, which learns from view stacks the library
     itself renders (random procedural scenes and poses).
 
@@ -114,7 +114,7 @@ def network_input(views_u8, nin: int, hp: int, wp: int):
 
 
 def tent_views(views_u8):
-    """The judge's views: 2N rendered views [2N][H][W][4] (u8 torch tensor)
+    """The ground-truth views: 2N rendered views [2N][H][W][4] (u8 torch tensor)
     -> the N reconstructed views [N][H][W][3] u8: [1/4, 1/2, 1/4] over the
     rendered views 2k-1, 2k, 2k+1 that exist, divided by the weights used,
     rounded half to even (Sec. 4's tent, as the interleave applies it)."""
@@ -319,7 +319,7 @@ def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=rang
             lfdpr.lfdpr_render_frame(disps[1], meshes[1], m, stream)
             R.run(disps[0], disps[2], stream)
             bf = lfdpr.lfdpr_get_buffers(disps[1], meshes[1])
-            judge = tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
+            truth = tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
             bo = lfdpr.lfdpr_get_buffers(disps[2], meshes[0])
             pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
             bi = lfdpr.lfdpr_get_buffers(disps[0], meshes[0])
@@ -328,8 +328,8 @@ def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=rang
             base = torch.einsum("oc,bchw->bohw", torch.from_numpy(base_matrix(nin)).to(x.device), x)
             base = torch.round(base.clamp(0, 1) * 255.0)[0, :, :H, :W].reshape(4 * nin, 3, H, W)
             base = base.permute(0, 2, 3, 1).to(torch.uint8)
-            res.append({"frame": int(f), "psnr": psnr(pred, judge), "ssim": ssim(pred, judge),
-                        "psnr_interp": psnr(base, judge)})
+            res.append({"frame": int(f), "psnr": psnr(pred, truth), "ssim": ssim(pred, truth),
+                        "psnr_interp": psnr(base, truth)})
     for m_ in meshes:
         lfdpr.lfdpr_destroy_mesh(m_)
     for d_ in disps:
