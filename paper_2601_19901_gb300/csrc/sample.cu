@@ -12,8 +12,8 @@
 //   k_fetch  one thread per point: texture coordinate of the cell centre and
 //            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7); then the
 //            point's splat record (its cell projected into the views) and,
-//            if some pixel row can receive it, its place in the splat's work
-//            list.
+//            if some view can hold a candidate pixel of it, its place in the
+//            splat's work list.
 //
 // Every floating-point step here is bit-specified (binary32, explicit fmaf,
 // IEEE division and square root) so the point set is identical to the CPU
@@ -626,7 +626,8 @@ __device__ __forceinline__ void band_bounds(const float* A, const float* B, cons
 
 // One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
 // record (its cell's projection into the views, candidate rows, flags), and
-// the point joins the splat's work list if any pixel row can receive it.
+// the point joins the splat's work list if some view can hold a candidate
+// pixel of it.
 __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
     if (a.ctr->overflow) return;
     const DispConst& c = a.dc;
@@ -702,6 +703,22 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
             L1.x = L1.x - (0.5f + kBoxPad);
             L0.z = L0.z - (0.5f - kBoxPad);
             L1.z = L1.z - (0.5f - kBoxPad);
+            // No candidate column in any view: a correctly rounded fmaf is
+            // monotone in Ex, so over eyes in [-E, E] the splat's lower
+            // line stays above the larger of its two lines' smaller end
+            // values and its upper line below the smaller of their larger
+            // end values; no integer between those two leaves every view
+            // empty and the point joins no work list.
+            const float E = c.ex_max;
+            const float l0m = fmaf(L0.y, -E, L0.x), l0p = fmaf(L0.y, E, L0.x);
+            const float l1m = fmaf(L1.y, -E, L1.x), l1p = fmaf(L1.y, E, L1.x);
+            const float h0m = fmaf(L0.w, -E, L0.z), h0p = fmaf(L0.w, E, L0.z);
+            const float h1m = fmaf(L1.w, -E, L1.z), h1p = fmaf(L1.w, E, L1.z);
+            const bool ordered = !(isnan(l0m) | isnan(l0p) | isnan(l1m) | isnan(l1p) | isnan(h0m) | isnan(h0p) |
+                                   isnan(h1m) | isnan(h1p));
+            const float xlo = fmaxf(ceilf(fmaxf(fminf(l0m, l0p), fminf(l1m, l1p))), 0.0f);
+            const float xhi = fminf(floorf(fminf(fmaxf(h0m, h0p), fmaxf(h1m, h1p))), float(c.W - 1));
+            if (ordered && xlo > xhi) ny = 0;
         }
 
         // Eq. 8's projected cell area is |alpha + beta Ex| / 2: a corner's pixel

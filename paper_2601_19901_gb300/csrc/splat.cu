@@ -1,9 +1,10 @@
 // EPR splatting into every view (Sec. 3.2) with the 64-bit depth|id test
 // (Sec. 5.1), and the per-view resolve of Eq. 8-9 (Sec. 3.3).
 //
-//   k_splat    one half-warp per point, lanes over the views: every pixel centre
-//              inside the point's projected cell and its projected triangle,
-//              at a depth in [near, far], does
+//   k_splat    a half-warp per point forms the candidate pixels of every view,
+//              a warp's candidates of several points are pooled into 32-lane
+//              passes: every pixel centre inside the point's projected cell
+//              and its projected triangle, at a depth in [near, far], does
 //              atomicMin(key, float_bits(t) << 32 | point id).
 //   k_resolve  one thread per view pixel: the winning point's 32-byte resolve
 //              record gives the splat's pixel area in this view
@@ -14,10 +15,10 @@
 namespace lfdpr {
 namespace {
 
-// One half-warp (16 lanes) per point of the work list, each lane taking up to
-// S views of the point (views g + 16 s + lane of a group g of 16 S views, S
-// chosen so that one group holds every rendered view where it can); a warp
-// carries two points at a time.
+// A warp takes a unit of 2P consecutive points of the work list: for each of
+// its P pairs, one half-warp (16 lanes) per point, each lane taking up to S
+// views of the point (views g + 16 s + lane of a group g of 16 S views, S
+// chosen so that one group holds every rendered view where it can).
 //
 // Candidates. Candidate rows are the pixel-centre rows inside both the
 // cell's and the triangle's projected y-extent, the same in every view since
@@ -25,10 +26,17 @@ namespace {
 // columns between a lower and an upper line x = alpha + beta Ex for the cell
 // and for the triangle, which bound each one's projected x-extent within the
 // band of candidate rows (the row's exact crossings for most points with one
-// row), widened by a small margin. A scan of the lanes' candidate counts over
-// the whole group then hands every lane one candidate pixel per pass, so no
-// lane loops over pixels on its own and a point with few candidates needs a
-// single pass.
+// row), widened by a small margin.
+//
+// Pooling. The unit's candidates are numbered in (pair, lane, view slot)
+// order; the non-empty (point, view) segments of that numbering go to a
+// per-warp list in shared memory with their first number, and the points'
+// test constants beside it. Then every pass hands the warp's 32 lanes the
+// next 32 candidates of the whole unit: a lane's segment is the last one
+// starting at or before its number, found from the OR-reduction of the
+// start bits that fall in the pass (segments are numbered in start order).
+// Points with few candidates, most of the work list, thus share passes
+// instead of each filling a pass on its own.
 //
 // Test. Each candidate takes the per-pixel test in the oracle's plane-space
 // form: the pixel centre's ray from the eye meets the triangle's plane at t
@@ -45,7 +53,7 @@ constexpr int kSplatWarps = 8;
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // The per-pixel test; every condition is evaluated (no early exits), so the
-// two points of a warp and the lanes' different candidates do not diverge.
+// lanes' different candidates do not diverge.
 __device__ __forceinline__ bool pixel_test(const DispConst& c, float Ex, float num, float qEx, float qEy,
                                            float qEz, const float4& q1, const float4& q2, const float4& q3,
                                            const float4& q4, float ulo, float uhi, float vlo, float vhi,
@@ -82,18 +90,44 @@ __device__ __forceinline__ void add_writes(Counters* ctr, uint32_t writes) {
     if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&ctr->n_writes, writes);
 }
 
-// Where the splat's point pairs come from: one scene (its constants in the
-// kernel's parameters), or every scene of a batch (constants in shared
-// memory; the pairs of all scenes form one index range, scene by scene).
+// floor(r / n) for n >= 1: below 2^21 one approximate division of r + 1/2
+// (its quotient stays at least 1 / (2n) from an integer, more than the 2-ulp
+// error of __fdividef), else an integer division.
+__device__ __forceinline__ uint32_t div_floor(uint32_t r, uint32_t n) {
+    if (r < (1u << 21)) return uint32_t(__fdividef(float(r) + 0.5f, float(n)));
+    return r / n;
+}
+
+// Units of 2P points per warp: pairs per unit for S view slots per lane.
+template <int S>
+struct UnitPairs {
+    static constexpr int P = S <= 3 ? 2 : 1;
+};
+
+// Per-warp shared memory of the pooled splat: the unit's non-empty (point,
+// view) segments in candidate order (first candidate number,
+// x0 | n_columns << 14, view | point << 16, eye x) and its points' test
+// constants: (P0.x, -P0.y, D - P0.z, point id), (u-hat, work meta word),
+// (v-hat, u_min), (n-hat, v_min), the 2-D vertices, the cell's u and v bounds.
+template <int S>
+struct SplatWarpSmem {
+    static constexpr int P = UnitPairs<S>::P, kSegs = 32 * S * P;
+    uint4 seg[kSegs];
+    float4 pt[2 * P][6];
+};
+
+// Where the splat's units come from: one scene (its constants in the kernel's
+// parameters), or every scene of a batch (constants in shared memory; the
+// units of all scenes form one index range, scene by scene).
 struct OneScene {
     static constexpr bool kMany = false;
     const FrameArgs& a;
     uint32_t n;       // work points
     uint32_t ex_s;    // shared-memory address of the eye positions
     __device__ __forceinline__ int scene(uint32_t) const { return 0; }
-    __device__ __forceinline__ uint32_t first_pair(int) const { return 0u; }
+    __device__ __forceinline__ uint32_t first_unit(int) const { return 0u; }
     __device__ __forceinline__ const DispConst& dc(int) const { return a.dc; }
-    __device__ __forceinline__ uint32_t eyes(int) const { return ex_s; }
+    __device__ __forceinline__ float eye(int, int v) const { return eye_x(ex_s, v); }
     __device__ __forceinline__ uint32_t points(int) const { return n; }
     __device__ __forceinline__ const WorkRec* work(int) const { return a.work; }
     __device__ __forceinline__ const TriRec* rec(int) const { return a.rec; }
@@ -108,23 +142,21 @@ struct ManyScenes {
     const SplatScene* scenes;
     int n_scenes;
     const DispConst* s_dc;
-    const uint32_t* s_pair0;   // first pair of each scene, then the total
+    const uint32_t* s_unit0;   // first unit of each scene, then the total
     const uint32_t* s_n;       // work points of each scene
-    uint32_t ex_s;             // shared-memory address of all scenes' eye positions
-    const uint32_t* s_ex0;     // first eye of each scene
-    // the scene holding pair g: the last with s_pair0 <= g
+    // the scene holding unit g: the last with s_unit0 <= g
     __device__ __forceinline__ int scene(uint32_t g) const {
         int lo = 0, hi = n_scenes - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (s_pair0[mid] <= g) lo = mid;
+            if (s_unit0[mid] <= g) lo = mid;
             else hi = mid - 1;
         }
         return lo;
     }
-    __device__ __forceinline__ uint32_t first_pair(int q) const { return s_pair0[q]; }
+    __device__ __forceinline__ uint32_t first_unit(int q) const { return s_unit0[q]; }
     __device__ __forceinline__ const DispConst& dc(int q) const { return s_dc[q]; }
-    __device__ __forceinline__ uint32_t eyes(int q) const { return ex_s + 4u * s_ex0[q]; }
+    __device__ __forceinline__ float eye(int q, int v) const { return __ldg(scenes[q].ex + v); }
     __device__ __forceinline__ uint32_t points(int q) const { return s_n[q]; }
     __device__ __forceinline__ const WorkRec* work(int q) const { return scenes[q].work; }
     __device__ __forceinline__ const TriRec* rec(int q) const { return scenes[q].rec; }
@@ -134,17 +166,44 @@ struct ManyScenes {
     __device__ __forceinline__ Counters* ctr(int q) const { return scenes[q].ctr; }
 };
 
-// The splat proper: warps stride through point pairs 0 .. total-1 of `src`,
-// one work point per half-warp (both halves always in the same scene).
+// Candidate rr of segment e: its pixel, the test, and the depth-test atomic.
+template <int S>
+__device__ __forceinline__ void test_candidate(const DispConst& c, const SplatWarpSmem<S>& sm, const uint4& e,
+                                               uint32_t rr, unsigned long long* keys, uint32_t npix,
+                                               uint32_t& writes) {
+    const float4* d = sm.pt[e.z >> 16];
+    const float4 d0 = d[0], d1 = d[1], q2 = d[2], q3 = d[3], q4 = d[4], b = d[5];
+    const uint32_t meta = __float_as_uint(d1.w), flags = meta >> 29;
+    const uint32_t nx = e.y >> 14;
+    const uint32_t ry = div_floor(rr, nx);
+    const int x = int(e.y & 0x3fffu) + int(rr - ry * nx), y = int(meta & 0x3fffu) + int(ry);
+    const uint32_t vo = e.z & 0xffffu;
+    const float Ex = __uint_as_float(e.w);
+    const float qEx = Ex - d0.x, qEy = d0.y, qEz = d0.z;
+    const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
+    float t;
+    if (!pixel_test(c, Ex, num, qEx, qEy, qEz, d1, q2, q3, q4, b.x, b.y, b.z, b.w, flags & kFlagInterior,
+                    flags & kFlagDepthOk, x, y, t))
+        return;
+    // a view holds at most 2^26 pixels: 32-bit offset within it
+    atomicMin(keys + ((uint64_t)vo * npix + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
+              ((unsigned long long)__float_as_uint(t) << 32) | __float_as_uint(d0.w));
+    writes++;
+}
+
+// The splat proper: warps stride through units 0 .. total-1 of `src` (a
+// unit never spans two scenes).
 template <int S, class Src>
-__device__ __forceinline__ void splat_pairs(const Src& src, uint32_t total) {
+__device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units, SplatWarpSmem<S>& sm) {
+    constexpr int P = UnitPairs<S>::P;
     const int lane = threadIdx.x & 31, sub = lane & 15, half = lane >> 4;
+    const uint32_t lanes_below = (1u << lane) - 1u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     uint32_t writes = 0;
     int cur = 0;
 
-    for (uint32_t g = warp; g < total; g += n_warps) {
+    for (uint32_t g = warp; g < total_units; g += n_warps) {
         const int sc = src.scene(g);
         if constexpr (Src::kMany) {
             if (sc != cur) {
@@ -154,104 +213,116 @@ __device__ __forceinline__ void splat_pairs(const Src& src, uint32_t total) {
             }
         }
         const DispConst& c = src.dc(sc);
-        const uint32_t ex_s = src.eyes(sc), n = src.points(sc);
+        const uint32_t n = src.points(sc);
         const WorkRec* work = src.work(sc);
         unsigned long long* keys = src.keys(sc);
         const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
-        const uint32_t kk = g - src.first_pair(sc);
-        const uint32_t k = 2 * kk + uint32_t(half);
-        const bool act = k < n;
-        const WorkRec* wr = work + (act ? k : 2 * kk);
-        if (sub == 0 && k + 2 * n_warps < n) prefetch_l2(work + k + 2 * n_warps);   // next pair's record
-        const float4 L0 = __ldg(&wr->L0), L1 = __ldg(&wr->L1);
-        const uint4 meta = __ldg(&wr->meta);
-        const uint32_t tri = meta.z;
-        const unsigned long long pid = meta.w;
-        const TriRec* r = src.rec(sc) + tri;
-        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
-        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
-        const int y0 = int(meta.x & 0x3fffu);
-        const uint32_t ny = act ? (meta.x >> 14) & 0x7fffu : 0u;
-        const uint32_t flags = meta.x >> 29;
-        const bool interior = flags & kFlagInterior, depth_ok = flags & kFlagDepthOk;
-        const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
-        const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
-        const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
-        const float qEy = 0.0f - q0.y, qEz = c.D - q0.z;
-
-        // Every loop below has the same trip count in both halves of the
-        // warp (the larger pass count of the two points), so each warp
-        // instruction serves both points.
+        const uint32_t k0 = 2u * P * (g - src.first_unit(sc));   // the unit's first work point
+        {
+            const uint32_t kn = k0 + 2u * P * n_warps + uint32_t(lane);   // the next unit's records
+            if (lane < 2 * P && kn < n) prefetch_l2(work + kn);
+        }
         for (int g0 = 0; g0 < c.nr; g0 += 16 * S) {
-            uint32_t pk[S];      // x0 | n_columns << 14 of the lane's views
+            __syncwarp();   // the previous passes are done with sm
+            uint32_t pk[P][S], ny[P];
+            float ex[P][S];
             uint32_t cnt = 0;
 #pragma unroll
-            for (int sl = 0; sl < S; sl++) {
-                const int v = g0 + 16 * sl + sub;
-                pk[sl] = 0u;
-                if (v < c.nr) {
-                    const float Ex = eye_x(ex_s, v);
-                    const float lo = fmaxf(fmaf(L0.y, Ex, L0.x), fmaf(L1.y, Ex, L1.x));
-                    const float hi = fminf(fmaf(L0.w, Ex, L0.z), fmaf(L1.w, Ex, L1.z));
-                    const int ix0 = max(__float2int_ru(lo), 0);
-                    const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
-                    if (ix0 <= ix1) {
-                        const uint32_t x0 = uint32_t(ix0), nx = uint32_t(ix1 - ix0) + 1u;
-                        pk[sl] = x0 | (nx << 14);
-                        cnt += nx * ny;
+            for (int p = 0; p < P; p++) {
+                // a half past the end takes the unit's first record, with no rows
+                const uint32_t k = k0 + 2u * p + uint32_t(half);
+                const WorkRec* wr = work + (k < n ? k : k0);
+                const float4 l0 = __ldg(&wr->L0), l1 = __ldg(&wr->L1);
+                const uint4 meta = __ldg(&wr->meta);
+                ny[p] = k < n ? (meta.x >> 14) & 0x7fffu : 0u;
+                if (g0 == 0 && sub == 0) {   // the point's test constants
+                    const TriRec* r = src.rec(sc) + meta.z;
+                    const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+                    const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+                    const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
+                    float4* d = sm.pt[2 * p + half];
+                    d[0] = make_float4(q0.x, 0.0f - q0.y, c.D - q0.z, __uint_as_float(meta.w));
+                    d[1] = make_float4(q1.x, q1.y, q1.z, __uint_as_float(meta.x));
+                    d[2] = q2;
+                    d[3] = q3;
+                    d[4] = q4;
+                    d[5] = make_float4(float(i) * q0.w, float(i + 1) * q0.w, float(j) * q1.w, float(j + 1) * q1.w);
+                }
+#pragma unroll
+                for (int sl = 0; sl < S; sl++) {
+                    const int v = g0 + 16 * sl + sub;
+                    pk[p][sl] = 0u;
+                    ex[p][sl] = 0.0f;
+                    if (v < c.nr) {
+                        const float Ex = src.eye(sc, v);
+                        const float lo = fmaxf(fmaf(l0.y, Ex, l0.x), fmaf(l1.y, Ex, l1.x));
+                        const float hi = fminf(fmaf(l0.w, Ex, l0.z), fmaf(l1.w, Ex, l1.z));
+                        const int ix0 = max(__float2int_ru(lo), 0);
+                        const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
+                        ex[p][sl] = Ex;
+                        if (ix0 <= ix1 && ny[p] > 0u) {
+                            const uint32_t nx = uint32_t(ix1 - ix0) + 1u;
+                            pk[p][sl] = uint32_t(ix0) | (nx << 14);
+                            cnt += nx * ny[p];
+                        }
                     }
                 }
             }
+            // a segment holds at most 2^26 candidates (one view), so a lane
+            // below 2^24 keeps the unit's numbering below 2^32
+            const bool big = __any_sync(0xffffffffu, cnt >= (1u << 24));
+            // the unit's candidates numbered in (lane, pair, slot) order
             uint32_t incl = cnt;
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o, 16);
-                if (sub >= o) incl += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
             }
-            const uint32_t total_h = __shfl_sync(0xffffffffu, incl, 15, 16);
-            const uint32_t both = max(total_h, __shfl_xor_sync(0xffffffffu, total_h, 16));
-            const uint32_t excl = incl - cnt;
-            for (uint32_t pass = 0; pass < both; pass += 16) {
-                const uint32_t q = pass + sub;
-                // owner: the first lane of this half whose inclusive count exceeds q
-                int own = 0;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t first = incl - cnt, rank = 0, nseg = 0;
 #pragma unroll
-                for (int st = 8; st >= 1; st >>= 1) {
-                    const uint32_t t = __shfl_sync(0xffffffffu, incl, own + st - 1, 16);
-                    if (t <= q) own += st;
+            for (int p = 0; p < P; p++)
+#pragma unroll
+                for (int sl = 0; sl < S; sl++) {
+                    const uint32_t bal = __ballot_sync(0xffffffffu, pk[p][sl] != 0u);
+                    rank += __popc(bal & lanes_below);
+                    nseg += __popc(bal);
                 }
-                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own, 16);
-                uint32_t opk[S];
 #pragma unroll
-                for (int sl = 0; sl < S; sl++) opk[sl] = __shfl_sync(0xffffffffu, pk[sl], own, 16);
-                if (q >= total_h) continue;
-                // the owner's view slot holding candidate q
-                uint32_t rr = q - o_excl, sel = opk[0];
-                int slot = 0;
+            for (int p = 0; p < P; p++)
 #pragma unroll
-                for (int sl = 0; sl + 1 < S; sl++) {
-                    const uint32_t cs = (opk[sl] >> 14) * ny;
-                    if (slot == sl && rr >= cs) {
-                        rr -= cs;
-                        slot = sl + 1;
-                        sel = opk[sl + 1];
+                for (int sl = 0; sl < S; sl++) {
+                    if (pk[p][sl] != 0u) {
+                        sm.seg[rank] = make_uint4(first, pk[p][sl], uint32_t(g0 + 16 * sl + sub) | uint32_t(2 * p + half) << 16,
+                                                  __float_as_uint(ex[p][sl]));
+                        rank++;
+                        first += (pk[p][sl] >> 14) * ny[p];
                     }
                 }
-                const uint32_t o_nx = sel >> 14;
-                const uint32_t ry = ny == 1 ? 0u : rr / o_nx;
-                const int x = int(sel & 0x3fffu) + int(rr - ry * o_nx), y = y0 + int(ry);
-                const int vo = g0 + 16 * slot + own;
-                const float Ex_o = eye_x(ex_s, vo);
-                const float qEx = Ex_o - q0.x;
-                const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-                float t;
-                if (!pixel_test(c, Ex_o, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, interior,
-                                depth_ok, x, y, t))
-                    continue;
-                // a view holds at most 2^26 pixels: 32-bit offset within it
-                atomicMin(keys + ((uint64_t)uint32_t(vo) * npix + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
-                          ((unsigned long long)__float_as_uint(t) << 32) | pid);
-                writes++;
+            __syncwarp();
+            if (big) {
+                // huge cells: each lane walks whole segments
+                for (uint32_t s = uint32_t(lane); s < nseg; s += 32) {
+                    const uint4 e = sm.seg[s];
+                    const uint32_t ny = (__float_as_uint(sm.pt[e.z >> 16][1].w) >> 14) & 0x7fffu;
+                    const uint32_t m = (e.y >> 14) * ny;
+                    for (uint32_t rr = 0; rr < m; rr++) test_candidate<S>(c, sm, e, rr, keys, npix, writes);
+                }
+                continue;
+            }
+            uint32_t before = 0;   // segments starting before the pass
+            for (uint32_t pass = 0; pass < total; pass += 32) {
+                const uint32_t kw = before + uint32_t(lane);
+                const uint32_t st = kw < nseg ? sm.seg[kw].x : 0xffffffffu;
+                const uint32_t off = st - pass;   // starts from `before` on are >= pass
+                const uint32_t smask = __reduce_or_sync(0xffffffffu, off < 32u ? 1u << off : 0u);
+                const uint32_t own = before + uint32_t(__popc(smask & (lanes_below | (1u << lane)))) - 1u;
+                before += uint32_t(__popc(smask));
+                const uint32_t q = pass + uint32_t(lane);
+                if (q < total) {
+                    const uint4 e = sm.seg[own];
+                    test_candidate<S>(c, sm, e, q - e.x, keys, npix, writes);
+                }
             }
         }
     }
@@ -260,27 +331,28 @@ __device__ __forceinline__ void splat_pairs(const Src& src, uint32_t total) {
 
 template <int S>
 __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
+    extern __shared__ __align__(16) uint8_t s_dyn[];
     __shared__ float s_ex[kMaxRenderViews];
     for (int v = threadIdx.x; v < a.dc.nr; v += blockDim.x) s_ex[v] = a.ex[v];
     __syncthreads();
     if (a.ctr->overflow) return;
     const uint32_t n = a.ctr->n_work;
     const OneScene src{a, n, uint32_t(__cvta_generic_to_shared(s_ex))};
-    splat_pairs<S>(src, (n + 1u) >> 1);
+    constexpr uint32_t unit = 2u * UnitPairs<S>::P;
+    splat_units<S>(src, (n + unit - 1u) / unit, reinterpret_cast<SplatWarpSmem<S>*>(s_dyn)[threadIdx.x >> 5]);
 }
 
 // Every scene of a batch in one persistent launch: warps stride through the
-// point pairs of all scenes, so scenes of uneven size share the machine.
-// Each block keeps every scene's display constants and eye positions in
-// shared memory.
+// units of all scenes, so scenes of uneven size share the machine. Each block
+// keeps every scene's display constants in shared memory.
 template <int S>
 __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat_batch(const SplatScene* __restrict__ scenes,
                                                                      int n_scenes) {
+    extern __shared__ __align__(16) uint8_t s_dyn[];
     __shared__ DispConst s_dc[kMaxBatchScenes];
-    __shared__ uint32_t s_pair0[kMaxBatchScenes + 1];   // first pair of each scene
+    __shared__ uint32_t s_unit0[kMaxBatchScenes + 1];   // first unit of each scene
     __shared__ uint32_t s_n[kMaxBatchScenes];           // work points (0 after an overflow)
-    __shared__ uint32_t s_ex0[kMaxBatchScenes + 1];     // first eye of each scene in s_ex
-    __shared__ float s_ex[kMaxBatchViews];
+    constexpr uint32_t unit = 2u * UnitPairs<S>::P;
     for (int q = threadIdx.x; q < n_scenes; q += blockDim.x) {
         s_dc[q] = scenes[q].dc;
         const Counters* ct = scenes[q].ctr;
@@ -288,22 +360,16 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat_batch(const Splat
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t p = 0, e = 0;
+        uint32_t u = 0;
         for (int q = 0; q < n_scenes; q++) {
-            s_pair0[q] = p;
-            s_ex0[q] = e;
-            p += (s_n[q] + 1u) >> 1;
-            e += uint32_t(s_dc[q].nr);
+            s_unit0[q] = u;
+            u += (s_n[q] + unit - 1u) / unit;
         }
-        s_pair0[n_scenes] = p;
-        s_ex0[n_scenes] = e;
+        s_unit0[n_scenes] = u;
     }
     __syncthreads();
-    for (int q = 0; q < n_scenes; q++)
-        for (int v = threadIdx.x; v < s_dc[q].nr; v += blockDim.x) s_ex[s_ex0[q] + v] = scenes[q].ex[v];
-    __syncthreads();
-    const ManyScenes src{scenes, n_scenes, s_dc, s_pair0, s_n, uint32_t(__cvta_generic_to_shared(s_ex)), s_ex0};
-    splat_pairs<S>(src, s_pair0[n_scenes]);
+    const ManyScenes src{scenes, n_scenes, s_dc, s_unit0, s_n};
+    splat_units<S>(src, s_unit0[n_scenes], reinterpret_cast<SplatWarpSmem<S>*>(s_dyn)[threadIdx.x >> 5]);
 }
 
 // Points whose cell or triangle reaches the eyes' plane: their projections
@@ -517,41 +583,56 @@ __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
     reinterpret_cast<uint32_t*>(a.views)[o] = out;
 }
 
+// Launch with the per-warp pooling buffers as dynamic shared memory (above
+// 48 KB per block together with the static arrays only for the batched splat
+// with 8 view slots, which opts in once).
+template <int S>
+cudaError_t splat_one(const FrameArgs& a, int grid, cudaStream_t s) {
+    const size_t bytes = kSplatWarps * sizeof(SplatWarpSmem<S>);
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_splat<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (attr != cudaSuccess) return attr;
+    k_splat<S><<<grid, kSplatWarps * 32, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t splat_batch(const SplatScene* scenes, int n_scenes, int grid, cudaStream_t s) {
+    const size_t bytes = kSplatWarps * sizeof(SplatWarpSmem<S>);
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_splat_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (attr != cudaSuccess) return attr;
+    k_splat_batch<S><<<grid, kSplatWarps * 32, bytes, s>>>(scenes, n_scenes);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
     // the fewest view slots per lane that hold every rendered view in one
     // group (more than 128 views take several groups of 128)
-    const int nr = a.dc.nr, grid = a.sm_count * 16, block = kSplatWarps * 32;
-    if (nr <= 16)
-        k_splat<1><<<grid, block, 0, s>>>(a);
-    else if (nr <= 32)
-        k_splat<2><<<grid, block, 0, s>>>(a);
-    else if (nr <= 48)
-        k_splat<3><<<grid, block, 0, s>>>(a);
-    else if (nr <= 64)
-        k_splat<4><<<grid, block, 0, s>>>(a);
-    else if (nr <= 96)
-        k_splat<6><<<grid, block, 0, s>>>(a);
-    else
-        k_splat<8><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    const int nr = a.dc.nr, grid = a.sm_count * 16;
+    if (nr <= 16) return splat_one<1>(a, grid, s);
+    if (nr <= 32) return splat_one<2>(a, grid, s);
+    if (nr <= 48) return splat_one<3>(a, grid, s);
+    if (nr <= 64) return splat_one<4>(a, grid, s);
+    if (nr <= 96) return splat_one<6>(a, grid, s);
+    return splat_one<8>(a, grid, s);
 }
 
 cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots, int grid_per_sm, int sm_count,
                                cudaStream_t s) {
     if (n_scenes < 1 || n_scenes > kMaxBatchScenes || grid_per_sm < 1) return cudaErrorInvalidValue;
-    const int grid = sm_count * grid_per_sm, block = kSplatWarps * 32;
+    const int grid = sm_count * grid_per_sm;
     switch (slots) {
-        case 1: k_splat_batch<1><<<grid, block, 0, s>>>(scenes, n_scenes); break;
-        case 2: k_splat_batch<2><<<grid, block, 0, s>>>(scenes, n_scenes); break;
-        case 3: k_splat_batch<3><<<grid, block, 0, s>>>(scenes, n_scenes); break;
-        case 4: k_splat_batch<4><<<grid, block, 0, s>>>(scenes, n_scenes); break;
-        case 6: k_splat_batch<6><<<grid, block, 0, s>>>(scenes, n_scenes); break;
-        case 8: k_splat_batch<8><<<grid, block, 0, s>>>(scenes, n_scenes); break;
+        case 1: return splat_batch<1>(scenes, n_scenes, grid, s);
+        case 2: return splat_batch<2>(scenes, n_scenes, grid, s);
+        case 3: return splat_batch<3>(scenes, n_scenes, grid, s);
+        case 4: return splat_batch<4>(scenes, n_scenes, grid, s);
+        case 6: return splat_batch<6>(scenes, n_scenes, grid, s);
+        case 8: return splat_batch<8>(scenes, n_scenes, grid, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s) {
