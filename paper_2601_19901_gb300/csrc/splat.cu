@@ -225,7 +225,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
         for (int g0 = 0; g0 < c.nr; g0 += 16 * S) {
             __syncwarp();   // the previous passes are done with sm
             uint32_t pk[P][S], ny[P];
-            float ex[P][S];
+            float ex[S];   // the lane's views' eyes, the same for every pair
             uint32_t cnt = 0;
 #pragma unroll
             for (int p = 0; p < P; p++) {
@@ -251,15 +251,14 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) {
                     const int v = g0 + 16 * sl + sub;
+                    if (p == 0) ex[sl] = v < c.nr ? src.eye(sc, v) : 0.0f;
                     pk[p][sl] = 0u;
-                    ex[p][sl] = 0.0f;
                     if (v < c.nr) {
-                        const float Ex = src.eye(sc, v);
+                        const float Ex = ex[sl];
                         const float lo = fmaxf(fmaf(l0.y, Ex, l0.x), fmaf(l1.y, Ex, l1.x));
                         const float hi = fminf(fmaf(l0.w, Ex, l0.z), fmaf(l1.w, Ex, l1.z));
                         const int ix0 = max(__float2int_ru(lo), 0);
                         const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
-                        ex[p][sl] = Ex;
                         if (ix0 <= ix1 && ny[p] > 0u) {
                             const uint32_t nx = uint32_t(ix1 - ix0) + 1u;
                             pk[p][sl] = uint32_t(ix0) | (nx << 14);
@@ -294,7 +293,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                 for (int sl = 0; sl < S; sl++) {
                     if (pk[p][sl] != 0u) {
                         sm.seg[rank] = make_uint4(first, pk[p][sl], uint32_t(g0 + 16 * sl + sub) | uint32_t(2 * p + half) << 16,
-                                                  __float_as_uint(ex[p][sl]));
+                                                  __float_as_uint(ex[sl]));
                         rank++;
                         first += (pk[p][sl] >> 14) * ny[p];
                     }
