@@ -260,6 +260,17 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display *disp, void *stream, lfdpr_stats *o
  */
 lfdpr_status lfdpr_set_stage_timing(lfdpr_display *disp, int32_t enable);
 
+/*
+ * lfdpr_set_splat_lane_limit: the splat (Sec. 3.2) pools the candidate
+ * pixels of four points per warp into 32-lane passes numbered with 32-bit
+ * integers; a unit in which some lane's views hold `limit` or more candidates
+ * (huge cells) is instead walked segment by segment, one lane per (point,
+ * view). The default, and the largest value, 2^24, keeps every number below
+ * 2^32; smaller values send more units down the walk, which gives the same
+ * keys more slowly. Errors: EINVAL (null display, limit outside [1, 2^24]).
+ */
+lfdpr_status lfdpr_set_splat_lane_limit(lfdpr_display *disp, uint32_t limit);
+
 /* lfdpr_get_buffers: borrowed device pointers of the last frame (see lfdpr_buffers). */
 lfdpr_status lfdpr_get_buffers(lfdpr_display *disp, lfdpr_mesh *mesh, lfdpr_buffers *out);
 

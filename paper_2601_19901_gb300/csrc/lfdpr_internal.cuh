@@ -227,7 +227,11 @@ struct FrameArgs {
     uint8_t* views;
     Counters* ctr;
     int sm_count;
+    uint32_t splat_lane_limit;       // candidates per lane above which a splat unit is walked lane by lane
 };
+// The default splat_lane_limit: with every lane below 2^24 candidates a
+// unit's candidate numbers stay below 2^32.
+constexpr uint32_t kSplatLaneLimit = 1u << 24;
 
 cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);

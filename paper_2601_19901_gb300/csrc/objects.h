@@ -42,6 +42,7 @@ struct lfdpr_display {
     bool ev_frame = false;        // the frame's stage events were recorded
     bool ev_interleave = false;   // the interleave's events were recorded
     int shading = LFDPR_SHADING_UNLIT;
+    uint32_t splat_lane_limit = lfdpr::kSplatLaneLimit;
     lfdpr::Shading sh{};          // light (unit direction), radiance, ambient
 };
 

@@ -62,6 +62,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.views = disp->views;
     a.ctr = disp->ctr;
     a.sm_count = disp->sm_count;
+    a.splat_lane_limit = disp->splat_lane_limit;
     return a;
 }
 
@@ -721,6 +722,15 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display* disp, void* stream, lfdpr_stats* o
     if (c.overflow)
         return fail(LFDPR_EOVERFLOW, "frame needed %u points, capacity %u", c.n_points, disp->max_points);
     if (c.cell_overflow) return fail(LFDPR_EOVERFLOW, "a triangle needed more than 65535 lattice cells per axis");
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_splat_lane_limit(lfdpr_display* disp, uint32_t limit) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "set_splat_lane_limit: null display");
+    if (limit < 1u || limit > lfdpr::kSplatLaneLimit)
+        return fail(LFDPR_EINVAL, "set_splat_lane_limit: %u outside [1, 2^24]", limit);
+    disp->splat_lane_limit = limit;
     return LFDPR_OK;
 }
 

@@ -135,6 +135,7 @@ struct OneScene {
         return reinterpret_cast<unsigned long long*>(a.keys);
     }
     __device__ __forceinline__ Counters* ctr(int) const { return a.ctr; }
+    __device__ __forceinline__ uint32_t lane_limit() const { return a.splat_lane_limit; }
 };
 
 struct ManyScenes {
@@ -164,6 +165,7 @@ struct ManyScenes {
         return reinterpret_cast<unsigned long long*>(scenes[q].keys);
     }
     __device__ __forceinline__ Counters* ctr(int q) const { return scenes[q].ctr; }
+    __device__ __forceinline__ uint32_t lane_limit() const { return kSplatLaneLimit; }
 };
 
 // Candidate rr of segment e: its pixel, the test, and the depth-test atomic.
@@ -267,9 +269,9 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                     }
                 }
             }
-            // a segment holds at most 2^26 candidates (one view), so a lane
-            // below 2^24 keeps the unit's numbering below 2^32
-            const bool big = __any_sync(0xffffffffu, cnt >= (1u << 24));
+            // a segment holds at most 2^26 candidates (one view), so lanes
+            // below the limit (at most 2^24) keep the unit's numbering below 2^32
+            const bool big = __any_sync(0xffffffffu, cnt >= src.lane_limit());
             // the unit's candidates numbered in (lane, pair, slot) order
             uint32_t incl = cnt;
 #pragma unroll
@@ -437,21 +439,39 @@ __device__ __forceinline__ uint32_t resolve_pixel(float Ex, const float4& ra, co
     return out;
 }
 
-// One view pixel per thread (grid: pixels x views).
+// kResolvePix view pixels per thread, 256 apart (grid: pixel blocks x
+// views): every key is loaded, then every winner's record, so each thread
+// keeps that many dependent gathers in flight.
+constexpr int kResolvePix = 2;
 __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
     const DispConst& c = a.dc;
     const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+    const uint32_t p0 = blockIdx.x * (256u * kResolvePix) + threadIdx.x;
     const int v = blockIdx.y;
-    const uint64_t o = (uint64_t)v * npix + p;
-    const unsigned long long key = a.keys[o];
-    uint32_t out = 0u;
-    if (key != ~0ull) {
-        const ResolveRec* rp = a.rrec + uint32_t(key);
-        out = resolve_pixel(__ldg(a.ex + v), __ldg(&rp->a), __ldg(&rp->b));
+    const uint64_t o0 = (uint64_t)v * npix;
+    unsigned long long key[kResolvePix];
+#pragma unroll
+    for (int k = 0; k < kResolvePix; k++) {
+        const uint32_t p = p0 + 256u * k;
+        key[k] = p < npix ? a.keys[o0 + p] : ~0ull;
     }
-    reinterpret_cast<uint32_t*>(a.views)[o] = out;
+    float4 ra[kResolvePix];
+    uint4 rb[kResolvePix];
+#pragma unroll
+    for (int k = 0; k < kResolvePix; k++) {
+        if (key[k] != ~0ull) {
+            const ResolveRec* rp = a.rrec + uint32_t(key[k]);
+            ra[k] = __ldg(&rp->a);
+            rb[k] = __ldg(&rp->b);
+        }
+    }
+    const float Ex = __ldg(a.ex + v);
+#pragma unroll
+    for (int k = 0; k < kResolvePix; k++) {
+        const uint32_t p = p0 + 256u * k;
+        if (p < npix)
+            reinterpret_cast<uint32_t*>(a.views)[o0 + p] = key[k] != ~0ull ? resolve_pixel(Ex, ra[k], rb[k]) : 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -645,7 +665,7 @@ cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {
     if (a.pbr)
         k_resolve_pbr<<<grid, 256, 0, s>>>(a);
     else
-        k_resolve<<<grid, 256, 0, s>>>(a);
+        k_resolve<<<dim3((npix + 256u * kResolvePix - 1u) / (256u * kResolvePix), uint32_t(a.dc.nr)), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ TRI = dict(P0=0, s_u=3, eu=4, s_v=7, ev=8, umin=11, n=12, vmin=15, a1=16, b1=17,
 EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_destroy_mesh", "lfdpr_render_frame", "lfdpr_interleave", "lfdpr_frame_stats",
            "lfdpr_get_buffers", "lfdpr_view_eyes", "lfdpr_probe_atomic_min", "lfdpr_last_error",
-           "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_sample_points_noalloc",
+           "lfdpr_version", "lfdpr_set_stage_timing", "lfdpr_set_splat_lane_limit", "lfdpr_sample_points_noalloc",
            "lfdpr_set_view_jitter", "lfdpr_set_recon_samples",
            "lfdpr_create_texture_set", "lfdpr_destroy_texture_set", "lfdpr_upload_mesh_textured",
            "lfdpr_upload_mesh_materials", "lfdpr_set_shading",
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
         L.lfdpr_get_buffers.argtypes = [P, P, C.POINTER(Buffers)]
         L.lfdpr_view_eyes.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_stage_timing.argtypes = [P, C.c_int32]
+        L.lfdpr_set_splat_lane_limit.argtypes = [P, C.c_uint32]
         L.lfdpr_set_view_jitter.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_recon_samples.argtypes = [P, P, C.c_int32]
         L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
@@ -242,6 +243,10 @@ def lfdpr_frame_stats(disp: int, stream=None) -> Stats:
 
 def lfdpr_set_stage_timing(disp: int, enable: bool):
     _check(lib().lfdpr_set_stage_timing(disp, 1 if enable else 0))
+
+
+def lfdpr_set_splat_lane_limit(disp: int, limit: int):
+    _check(lib().lfdpr_set_splat_lane_limit(disp, int(limit)))
 
 
 def lfdpr_get_buffers(disp: int, mesh: int) -> Buffers:
