@@ -248,20 +248,30 @@ def atomic_peak(n_words, sm_stream):
     return out
 
 
+def source_digest(sources) -> str:
+    """sha256 of kernel sources with their comments and blank space removed,
+    so that a comment edit does not orphan an ncu summary of the same code."""
+    import hashlib
+    import re
+    hsh = hashlib.sha256()
+    for f in sources:
+        text = open(os.path.join(ROOT, "paper_2601_19901_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        hsh.update(" ".join(text.split()).encode())
+    return hsh.hexdigest()
+
+
 def profiled_traffic(profile: str, sources):
     """DRAM bytes (read + write) per launch from a committed ncu summary, if
     the kernel's sources still hash to what was captured; else None."""
-    import hashlib
     import re
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"sha256: ([0-9a-f]{64})", text)
-    hsh = hashlib.sha256()
-    for f in sources:
-        hsh.update(open(os.path.join(ROOT, "paper_2601_19901_gb300", "csrc", f), "rb").read())
-    if not m or m.group(1) != hsh.hexdigest():
+    if not m or m.group(1) != source_digest(sources):
         return None
     rd = re.search(r"dram__bytes_read\.sum`\) \| ([0-9.]+) Mbyte", text)
     wr = re.search(r"dram__bytes_write\.sum`\) \| ([0-9.]+) Mbyte", text)

@@ -28,7 +28,7 @@ namespace {
 // band of candidate rows (the row's exact crossings for most points with one
 // row), widened by a small margin.
 //
-// Pooling. The unit's candidates are numbered in (pair, lane, view slot)
+// Pooling. The unit's candidates are numbered in (lane, pair, view slot)
 // order; the non-empty (point, view) segments of that numbering go to a
 // per-warp list in shared memory with their first number, and the points'
 // test constants beside it. Then every pass hands the warp's 32 lanes the
