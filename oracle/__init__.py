@@ -17,8 +17,12 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "lfdpr_oracle.c")
-_LIB = os.path.join(_HERE, "liblfdpr_oracle.so")
+# LFDPR_ORACLE_SRC names another copy of the oracle's source (a mutation run
+# plants a mistake in such a copy and checks that the pins catch it); it is
+# built next to itself.
+_SRC = os.environ.get("LFDPR_ORACLE_SRC") or os.path.join(_HERE, "lfdpr_oracle.c")
+_LIB = os.path.join(os.path.dirname(os.path.abspath(_SRC)), "liblfdpr_oracle.so") \
+    if os.environ.get("LFDPR_ORACLE_SRC") else os.path.join(_HERE, "liblfdpr_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -113,6 +117,8 @@ def lib():
             L.orc_fetch_mat.argtypes = [P, P, C.c_int64, P, P, P, P]
             L.orc_resolve_pbr.argtypes = [P, P, P, P, P, P, C.c_int, P, P]
             L.orc_pbr_shade.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P, P]
+            L.orc_splat_area_px.restype = C.c_float
+            L.orc_splat_area_px.argtypes = [P, P, C.c_int, C.c_int, C.c_float]
             L.orc_raycast.restype = C.c_int32
             L.orc_raycast.argtypes = [P, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                       C.POINTER(C.c_double)]
@@ -202,6 +208,18 @@ def view_pos(d, m: int, jitter=None) -> float:
     return float(lib().orc_view_pos(C.byref(dd), m))
 
 
+def transform(model: np.ndarray, xyz: np.ndarray) -> np.ndarray:
+    """(n, 3) float32 points through orc_transform (the per-frame model
+    transform, affine rows 0-2 of the row-major 4x4 `model`)."""
+    L = lib()
+    m = np.ascontiguousarray(model, np.float32).ravel()
+    v = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    out = np.zeros_like(v)
+    for k in range(len(v)):
+        L.orc_transform(_p(m), _p(v[k]), _p(out[k]))
+    return out
+
+
 def transformed_tris(scene, model: np.ndarray) -> np.ndarray:
     """(T, 9) float32 transformed triangle vertices (same fmaf sequence as setup)."""
     L = lib()
@@ -213,6 +231,15 @@ def transformed_tris(scene, model: np.ndarray) -> np.ndarray:
         L.orc_transform(_p(m), _p(v[k]), _p(o))
         tv[k] = o
     return np.ascontiguousarray(tv[scene.idx.astype(np.int64)].reshape(-1, 9))
+
+
+def splat_area_px(d, rec_row: np.ndarray, i: int, j: int, ex: float) -> float:
+    """Eq. 8's projected splat area (view pixels) of lattice cell (i, j) of
+    one triangle's record, in the view of eye x `ex`."""
+    dd = _disp(d)
+    r = np.ascontiguousarray(rec_row, np.float32)
+    assert r.shape == (TRI_FLOATS,)
+    return float(lib().orc_splat_area_px(C.byref(dd), _p(r), i, j, C.c_float(ex)))
 
 
 def raycast(d, txyz: np.ndarray, v: int, x: int, y: int):

@@ -709,35 +709,42 @@ static void cell_corner(const float *T, int a, int b, float o[3]) {
 }
 
 /*
- * Eq. 8's projected splat area, as an affine function of the eye's x. A world
- * point C projects (from eye (Ex, 0, D) through z = 0) to pixel x = a + b Ex
- * with s = D / (D - Cz), a = (Cx s - x0) W/fw, b = (1 - s) W/fw, and pixel
- * y = (y0 - Cy s) H/fh, the same in every view. The shoelace sum of the cell's
- * four projected corners is therefore alpha + beta Ex, alpha the sum over
- * corners of a_k Y_k+1 - a_k+1 Y_k and beta the same with b; the pixel area is
- * |alpha + beta Ex| / 2. Both sides take alpha and beta in this order.
+ * Eq. 8's size_ndc^vs x 0.25 X_v Y_v: the area, in view pixels, of the splat
+ * (the point's cell) projected into the view of eye (Ex, 0, D). Each corner
+ * C of the cell is projected through the focal plane z = 0 by the plain
+ * perspective map, x_s = Ex + (C_x - Ex) D / (D - C_z), y_s = C_y D / (D - C_z),
+ * then to pixel coordinates ((x_s + fw/2) W/fw, (fh/2 - y_s) H/fh); the area
+ * is the shoelace sum of the four projected corners taken relative to the
+ * first one. Evaluated in double from the binary32 corners: the area only
+ * weights a colour (Eq. 9), it decides no integer.
  */
-static void cell_area_coeffs(const float *T, int i, int j, float D, float x0, float y0, float ipw, float iph,
-                             float *alpha, float *beta) {
-    float C[4][3], a[4], b[4], Y[4];
-    cell_corner(T, i, j, C[0]);
-    cell_corner(T, i + 1, j, C[1]);
-    cell_corner(T, i + 1, j + 1, C[2]);
-    cell_corner(T, i, j + 1, C[3]);
+static float splat_area_px(const orc_display *d, const float *T, int i, int j, float Ex) {
+    float Cf[4][3];
+    cell_corner(T, i, j, Cf[0]);
+    cell_corner(T, i + 1, j, Cf[1]);
+    cell_corner(T, i + 1, j + 1, Cf[2]);
+    cell_corner(T, i, j + 1, Cf[3]);
+    double D = d->view_dist, E = Ex, fw = d->focal_w, fh = d->focal_h;
+    double px[4], py[4];
     for (int c = 0; c < 4; c++) {
-        float s = D / (D - C[c][2]);
-        a[c] = fmaf(C[c][0], s, -x0) * ipw;
-        b[c] = (1.0f - s) * ipw;
-        Y[c] = (y0 - C[c][1] * s) * iph;
+        double k = D / (D - (double)Cf[c][2]);
+        double xs = E + ((double)Cf[c][0] - E) * k, ys = (double)Cf[c][1] * k;
+        px[c] = (xs + 0.5 * fw) * d->view_w / fw;
+        py[c] = (0.5 * fh - ys) * d->view_h / fh;
     }
-    float al = 0.0f, be = 0.0f;
-    for (int c = 0; c < 4; c++) {
-        int c1 = (c + 1) & 3;
-        al = al + fmaf(a[c], Y[c1], -(a[c1] * Y[c]));
-        be = be + fmaf(b[c], Y[c1], -(b[c1] * Y[c]));
+    double twice = 0.0;
+    for (int c = 1; c < 3; c++) {
+        double ax = px[c] - px[0], ay = py[c] - py[0];
+        double bx = px[c + 1] - px[0], by = py[c + 1] - py[0];
+        twice += ax * by - bx * ay;
     }
-    *alpha = al;
-    *beta = be;
+    return (float)(0.5 * fabs(twice));
+}
+
+/* orc_splat_area_px: splat_area_px of cell (i, j) of the record T (one
+ * triangle's ORC_TRI_FLOATS floats) in the view of eye x Ex. */
+float orc_splat_area_px(const orc_display *d, const float *T, int i, int j, float Ex) {
+    return splat_area_px(d, T, i, j, Ex);
 }
 
 /*
@@ -859,8 +866,8 @@ void orc_splat_hits(const orc_display *d, const float *tri, const uint32_t *poin
 /*
  * orc_resolve: per listed view and pixel, the winning point's colour. The
  * splat's pixel area is the shoelace area of its cell's four corners
- * projected into the view (= size_ndc * 0.25 * X_v * Y_v of Eq. 8), taken as
- * |alpha + beta Ex| / 2 (cell_area_coeffs). Eq. 8
+ * projected into the view (= size_ndc * 0.25 * X_v * Y_v of Eq. 8,
+ * splat_area_px). Eq. 8
  * grows the splat's texture area when it covers less than a pixel and clamps
  * it to [size_vpuv_min, size_vpuv_max]; Eq. 9 interpolates tv between tv_min
  * and tv_max per channel. Empty pixels are (0, 0, 0, 0).
@@ -871,11 +878,6 @@ void orc_resolve(const orc_display *d, const float *tri, const uint32_t *points,
     float *ex = (float *)malloc(sizeof(float) * (size_t)nr);
     orc_eyes(d, ex);
     int W = d->view_w, H = d->view_h;
-    float D = d->view_dist;
-    float pw = (float)((double)d->focal_w / W), ph = (float)((double)d->focal_h / H);
-    float ipw = (float)((double)W / d->focal_w), iph = (float)((double)H / d->focal_h);
-    float x0 = -0.5f * d->focal_w, y0 = 0.5f * d->focal_h;
-    (void)pw; (void)ph;
     size_t npix = (size_t)W * H;
     for (int li = 0; li < n_list; li++) {
         float Ex = ex[views[li]];
@@ -886,9 +888,7 @@ void orc_resolve(const orc_display *d, const float *tri, const uint32_t *points,
             const uint32_t *pt = points + 4 * (size_t)(uint32_t)key;
             const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
             int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
-            float alpha, beta;
-            cell_area_coeffs(T, i, j, D, x0, y0, ipw, iph, &alpha, &beta);
-            float area_px = 0.5f * fabsf(fmaf(beta, Ex, alpha));
+            float area_px = splat_area_px(d, T, i, j, Ex);
             float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
             float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
             float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
@@ -1009,7 +1009,6 @@ void orc_resolve_pbr(const orc_display *d, const float *tri, const uint32_t *poi
     int W = d->view_w, H = d->view_h;
     float D = d->view_dist;
     float pw = (float)((double)d->focal_w / W), ph = (float)((double)d->focal_h / H);
-    float ipw = (float)((double)W / d->focal_w), iph = (float)((double)H / d->focal_h);
     float x0 = -0.5f * d->focal_w, y0 = 0.5f * d->focal_h;
     double L[3] = {sh->light_dir[0], sh->light_dir[1], sh->light_dir[2]};
     dnorm(L);
@@ -1025,9 +1024,7 @@ void orc_resolve_pbr(const orc_display *d, const float *tri, const uint32_t *poi
             const float *T = tri + (size_t)pt[0] * ORC_TRI_FLOATS;
             int i = (int)(pt[1] & 0xffffu), j = (int)(pt[1] >> 16);
             /* Eq. 8 weight, exactly as orc_resolve */
-            float alpha, beta;
-            cell_area_coeffs(T, i, j, D, x0, y0, ipw, iph, &alpha, &beta);
-            float area_px = 0.5f * fabsf(fmaf(beta, Ex, alpha));
+            float area_px = splat_area_px(d, T, i, j, Ex);
             float vmin = T[T_VPUV_MIN], vmax = T[T_VPUV_MAX];
             float size_vse = T[T_SPL_UV] / fminf(1.0f, area_px);
             float size_vs = fminf(fmaxf(size_vse, vmin), vmax);

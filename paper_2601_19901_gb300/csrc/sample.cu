@@ -722,22 +722,20 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         }
 
         // Eq. 8's projected cell area is |alpha + beta Ex| / 2: a corner's pixel
-        // x is a + b Ex (a = (x s - x0) W/fw, b = (1 - s) W/fw, s = D / (D - z)),
-        // its pixel y the same in every view, so the shoelace sum is affine in Ex
-        float pa[4], pb[4], py[4];
+        // x is (x s - x0) W/fw + (1 - s) W/fw Ex (s = D / (D - z)), its pixel y
+        // (y0 - y s) H/fh the same in every view, so the shoelace sum of the
+        // corners taken relative to the first one is affine in Ex; the
+        // differences are formed before scaling so that x0 and y0 cancel exactly
+        float da[3], db[3], dy[3];
+        const float cx0 = Cx[0] * Cs[0], cy0 = Cy[0] * Cs[0];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            pa[k] = fmaf(Cx[k], Cs[k], -c.x0) * c.ipw;
-            pb[k] = (1.0f - Cs[k]) * c.ipw;
-            py[k] = (c.y0 - Cy[k] * Cs[k]) * c.iph;
+        for (int k = 0; k < 3; k++) {
+            da[k] = fmaf(Cx[k + 1], Cs[k + 1], -cx0) * c.ipw;
+            db[k] = (Cs[0] - Cs[k + 1]) * c.ipw;
+            dy[k] = fmaf(-Cy[k + 1], Cs[k + 1], cy0) * c.iph;
         }
-        float alpha = 0.0f, beta = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int k1 = (k + 1) & 3;
-            alpha = alpha + fmaf(pa[k], py[k1], -(pa[k1] * py[k]));
-            beta = beta + fmaf(pb[k], py[k1], -(pb[k1] * py[k]));
-        }
+        const float alpha = fmaf(da[0], dy[1], -(da[1] * dy[0])) + fmaf(da[1], dy[2], -(da[2] * dy[1]));
+        const float beta = fmaf(db[0], dy[1], -(db[1] * dy[0])) + fmaf(db[1], dy[2], -(db[2] * dy[1]));
         ResolveRec* rr = a.rrec + p;
         rr->a = make_float4(alpha, beta, q5.x, q5.y);
         rr->b = make_uint4(__float_as_uint(q5.z), tmin, tmax, 0u);
