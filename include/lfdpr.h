@@ -66,9 +66,10 @@ typedef enum {
  * with lfdpr_set_recon_samples (required before their interleave); crosstalk
  * x > 0 mixes each view with its +-1 neighbours at weight x before
  * interleaving (for recon 2 and 3: the reconstruction one view away). max_points is the point-buffer
- * capacity (0 = 1 << 23); each point of capacity takes 148 B of device
+ * capacity (0 = 1 << 23); each point of capacity takes 100 B of device
  * memory (the 16-B point record, a 48-B splat work record, a 4-B near-list
- * entry and an 80-B resolve record).
+ * entry and a 32-B resolve record), and 8 B more once a mesh of materials is
+ * uploaded to the display.
  */
 typedef struct {
     int32_t n_views, view_w, view_h;
@@ -168,7 +169,7 @@ typedef struct {
  * 0 < near_z < far_z, view_dist > 0, focal sizes > 0, recon in {0, 1, 2, 3},
  * 0 <= crosstalk < 0.5) and allocate the display's device buffers: view key
  * buffers (8 B per rendered-view pixel, Sec. 5.2), RGBA8 views, the point
- * buffers (148 B per point of capacity) and the panel scratch. Uses the current CUDA device.
+ * buffers (100 B per point of capacity) and the panel scratch. Uses the current CUDA device.
  * On success *out owns them. Errors: EINVAL, ENOMEM, EDEVICE, ECUDA.
  */
 lfdpr_status lfdpr_create_display(const lfdpr_display_desc *desc, lfdpr_display **out);
@@ -280,14 +281,20 @@ lfdpr_status lfdpr_view_eyes(const lfdpr_display *disp, float *out, int32_t capa
 /*
  * lfdpr_probe_atomic_min: roofline probe for the splat's depth test (Sec. 5.1
  * uses 64-bit buffers). Performs n_ops 64-bit atomicMin operations on `words`
- * (u64 [n_words], device) at indices idx[k] (u32 [n_ops], device, < n_words)
- * with values val[k] (u64 [n_ops], device); shared != 0 stages the words in
- * shared memory per block (n_words <= 8192) and merges them back with one
- * global atomicMin per word. Asynchronous on `stream`. Errors: EINVAL, ECUDA.
+ * (u64 [n_words], device) with values val[k] (u64 [n_ops], device), at
+ * addresses chosen by `mode` from idx (u32 [n_ops], device):
+ *  0  word idx[k] (random indices: every lane of a warp instruction hits its
+ *     own line);
+ *  1  word idx[k] mod n_words of a per-block copy in shared memory
+ *     (n_words <= 8192), merged back with one global atomicMin per word;
+ *  2  word (idx[32 q] rounded down to a multiple of 32) + (k mod 32) for
+ *     k in the group q of 32 consecutive operations (one warp instruction
+ *     hits 32 consecutive words, 256 bytes: the most coherent pattern).
+ * Indices at or beyond n_words are skipped. Asynchronous on `stream`.
+ * Errors: EINVAL (null or empty buffers, mode outside 0-2), ECUDA.
  */
 lfdpr_status lfdpr_probe_atomic_min(uint64_t *words, uint64_t n_words, const uint32_t *idx,
-                                    const uint64_t *val, uint64_t n_ops, int32_t shared,
-                                    void *stream);
+                                    const uint64_t *val, uint64_t n_ops, int32_t mode, void *stream);
 
 /*
  * lfdpr_sample_points_noalloc: the point-generation stage alone (per-triangle
@@ -312,10 +319,14 @@ lfdpr_status lfdpr_probe_atomic_min(uint64_t *words, uint64_t n_words, const uin
  * Limits: n_tris <= LFDPR_NOALLOC_MAX_TRIS, 1 <= n_tex <= LFDPR_NOALLOC_MAX_TEX;
  * larger sizes return EINVAL with a message. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Every call shares
- * the one array, which keeps the last call's contents (the counters are
- * cleared by each call): calls that overlap on the GPU, from any stream or
- * thread, race. Asynchronous on `stream`. Errors: EINVAL, EDEVICE, ECUDA.
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and make no call after a cudaDeviceReset of that
+ * device (the kept address would belong to the destroyed context). The eye
+ * positions and texture sizes reach the device as a kernel parameter, so
+ * nothing on the host has to outlive the call. Every call shares the one
+ * array, which keeps the last call's contents (the counters are cleared by
+ * each call): calls that overlap on the GPU, from any stream or thread, race.
+ * Asynchronous on `stream`. Errors: EINVAL, EDEVICE, ECUDA.
  */
 #define LFDPR_NOALLOC_MAX_TRIS 32768
 #define LFDPR_NOALLOC_MAX_TEX 256

@@ -714,9 +714,13 @@ static void cell_corner(const float *T, int a, int b, float o[3]) {
  * C of the cell is projected through the focal plane z = 0 by the plain
  * perspective map, x_s = Ex + (C_x - Ex) D / (D - C_z), y_s = C_y D / (D - C_z),
  * then to pixel coordinates ((x_s + fw/2) W/fw, (fh/2 - y_s) H/fh); the area
- * is the shoelace sum of the four projected corners taken relative to the
- * first one. Evaluated in double from the binary32 corners: the area only
- * weights a colour (Eq. 9), it decides no integer.
+ * is the shoelace sum of the projected corners taken relative to the first
+ * one. A cell that reaches within near_z of the eyes' plane has no bounded
+ * projection; its splat is the part that can be drawn, the cell clipped to
+ * depth D - z >= near_z (a plane shared by every view, since all eyes lie at
+ * z = D), which leaves every other cell as it is. Evaluated in double from
+ * the binary32 corners: the area only weights a colour (Eq. 9), it decides
+ * no integer.
  */
 static float splat_area_px(const orc_display *d, const float *T, int i, int j, float Ex) {
     float Cf[4][3];
@@ -725,15 +729,33 @@ static float splat_area_px(const orc_display *d, const float *T, int i, int j, f
     cell_corner(T, i + 1, j + 1, Cf[2]);
     cell_corner(T, i, j + 1, Cf[3]);
     double D = d->view_dist, E = Ex, fw = d->focal_w, fh = d->focal_h;
-    double px[4], py[4];
+    double zc = D - (double)d->near_z;
+    double P[5][3];
+    int m = 0;
     for (int c = 0; c < 4; c++) {
-        double k = D / (D - (double)Cf[c][2]);
-        double xs = E + ((double)Cf[c][0] - E) * k, ys = (double)Cf[c][1] * k;
+        const float *p = Cf[c], *q = Cf[(c + 1) & 3];
+        int pin = p[2] <= zc, qin = q[2] <= zc;
+        if (pin) {
+            for (int k = 0; k < 3; k++) P[m][k] = p[k];
+            m++;
+        }
+        if (pin != qin) {
+            double f = (zc - p[2]) / ((double)q[2] - p[2]);
+            for (int k = 0; k < 3; k++) P[m][k] = p[k] + f * ((double)q[k] - p[k]);
+            P[m][2] = zc;
+            m++;
+        }
+    }
+    if (m < 3) return 0.0f;
+    double px[5], py[5];
+    for (int c = 0; c < m; c++) {
+        double k = D / (D - P[c][2]);
+        double xs = E + (P[c][0] - E) * k, ys = P[c][1] * k;
         px[c] = (xs + 0.5 * fw) * d->view_w / fw;
         py[c] = (0.5 * fh - ys) * d->view_h / fh;
     }
     double twice = 0.0;
-    for (int c = 1; c < 3; c++) {
+    for (int c = 1; c + 1 < m; c++) {
         double ax = px[c] - px[0], ay = py[c] - py[0];
         double bx = px[c + 1] - px[0], by = py[c + 1] - py[0];
         twice += ax * by - bx * ay;

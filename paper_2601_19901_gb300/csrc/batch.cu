@@ -99,7 +99,7 @@ lfdpr_status record_batch(lfdpr_batch* b) {
     for (int i = 0; i < b->n; i++) {
         FrameArgs a = frame_args(b->disp[i], b->mesh[i]);
         a.model_dev = b->d_models + 12 * i;
-        const lfdpr_status st = record_frame_front(b->disp[i], b->mesh[i], a, b->br[i % K], false, true);
+        const lfdpr_status st = record_frame_front(b->disp[i], b->mesh[i], a, b->br[i % K], false);
         if (st != LFDPR_OK) return st;
     }
     for (int j = 0; j < K; j++) {
@@ -268,7 +268,9 @@ lfdpr_status lfdpr_render_batch(lfdpr_batch* b, const float* models, void* strea
     CK(cudaGraphLaunch(b->exec, s), "render_batch: graph launch");
     for (int i = 0; i < b->n; i++) {
         b->disp[i]->ev_frame = b->disp[i]->ev_interleave = false;
-        b->disp[i]->launches += b->mesh[i]->n_tris ? 7 : 2;
+        // set-up, scan, emission, fetch, near-limit records (and the materials'
+        // fetch), resolve, interleave
+        b->disp[i]->launches += b->mesh[i]->n_tris ? (b->mesh[i]->mat_tex ? 8 : 7) : 2;
     }
     b->disp[0]->launches += 1;
     return LFDPR_OK;

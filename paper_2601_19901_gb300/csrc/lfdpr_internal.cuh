@@ -54,7 +54,7 @@ struct Counters {
     uint32_t n_live;
     uint32_t n_writes;    // depth-test atomics the splat issued
     uint32_t n_work;      // points with at least one candidate pixel row
-    uint32_t n_near;      // points whose cell or triangle reaches the eyes' plane
+    uint32_t n_near;      // points whose cell or triangle reaches within near_z of the eyes' plane
     uint32_t pad;
 };
 
@@ -188,6 +188,19 @@ __device__ __forceinline__ uint8_t round_u8(float v) {
     return (uint8_t)r;
 }
 
+// Angular supersampling renders 2N views (recon 1 and 2).
+inline bool supersampled(const lfdpr_display_desc& d) { return d.recon == 1 || d.recon == 2; }
+
+// Eye angle (degrees) of rendered view k at the fraction u of its interval
+// (Sec. 3: N equal angular intervals of the cone; Sec. 4: 2N half-intervals
+// with angular supersampling, where u = 1/2 puts the even ones on the N view
+// centres). Host code; the eye x is D tan(angle), rounded once to binary32.
+inline double eye_angle_deg(const lfdpr_display_desc& d, int k, double u) {
+    const double cone = d.cone_deg;
+    return supersampled(d) ? -cone / 2.0 + cone * (k + 0.5 + u) / (2.0 * d.n_views)
+                           : -cone / 2.0 + cone * (k + u) / d.n_views;
+}
+
 // Per-thread description of the last error, read by lfdpr_last_error().
 __attribute__((visibility("hidden"))) extern thread_local char g_last_error[512];
 
@@ -220,7 +233,7 @@ struct FrameArgs {
     uint32_t max_points;
     TriProj* tproj;                  // [n_tris] (optional: null skips it)
     WorkRec* work;                   // [max_points] the splat's work list
-    uint32_t* near;                  // [max_points] points whose cell or triangle reaches the eyes' plane
+    uint32_t* near;                  // [max_points] points whose cell or triangle reaches within near_z of the eyes' plane
     ResolveRec* rrec;                // [max_points] per-point resolve data
     uint2* rmat;                     // [max_points] normal-map tv_min, tv_max (meshes of materials)
     uint64_t* keys;
@@ -238,6 +251,7 @@ cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_fetch_mat(const FrameArgs& a, cudaStream_t s);   // meshes of materials, after launch_fetch
+cudaError_t launch_near_work(const FrameArgs& a, cudaStream_t s);   // after launch_fetch
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s);
 
 // One scene of a batched splat: its display constants and the buffers the
@@ -256,7 +270,6 @@ constexpr int kMaxBatchViews = 4096;   // rendered views summed over a batch
 // per SM, slots view slots per lane (1, 2, 3, 4, 6 or 8).
 cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots, int grid_per_sm, int sm_count,
                                cudaStream_t s);
-cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
 // pos [nr] (views on the display-view axis) and samples [n_samples][3] are
 // read only for Gaussian reconstruction (recon 2, 3).
@@ -264,8 +277,9 @@ cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const f
                               int n_samples, uint8_t* panel, cudaStream_t s);
 cudaError_t launch_mip_level(const uint8_t* src, uint32_t sw, uint32_t sh, uint8_t* dst,
                              uint32_t dw, uint32_t dh, cudaStream_t s);
+// mode 0: random global, 1: shared memory, 2: warp-coherent global
 cudaError_t launch_probe_atomic(uint64_t* words, uint64_t n_words, const uint32_t* idx,
-                                const uint64_t* val, uint64_t n_ops, bool shared, int sm_count,
+                                const uint64_t* val, uint64_t n_ops, int mode, int sm_count,
                                 cudaStream_t s);
 
 }  // namespace lfdpr

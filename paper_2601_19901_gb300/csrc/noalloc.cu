@@ -39,6 +39,25 @@ struct NoAllocScratch {
 // a device address: the address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
+// What a call writes into the scratch besides the kernels' own outputs: the
+// eye positions and texture sizes, passed by value as one kernel parameter
+// (8.2 KB; kernel parameters are copied when the launch is issued, so no host
+// buffer has to outlive the call).
+struct FillParams {
+    float ex[kMaxRenderViews];
+    TexDesc tex[kNoAllocMaxTex];
+    int nr;
+    uint32_t n_tex;
+};
+static_assert(sizeof(FillParams) < 32000, "kernel parameter limit");
+
+// Clear the counters and store the eyes and texture sizes of one call.
+__global__ void k_noalloc_fill(const __grid_constant__ FillParams p, NoAllocScratch* scr) {
+    for (int k = threadIdx.x; k < p.nr; k += blockDim.x) scr->ex[k] = p.ex[k];
+    for (uint32_t k = threadIdx.x; k < p.n_tex; k += blockDim.x) scr->tex[k] = p.tex[k];
+    if (threadIdx.x == 0) scr->ctr = Counters{};
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
@@ -138,28 +157,24 @@ extern "C" lfdpr_status lfdpr_sample_points_noalloc(
     c.x0 = -0.5f * s.focal_w;
     c.y0 = 0.5f * s.focal_h;
 
-    float ex[kMaxRenderViews];
-    const double cone = s.cone_deg;
-    for (int k = 0; k < nr; k++) {
-        const double deg = ss ? -cone / 2.0 + cone * (k + 1) / (2.0 * s.n_views)
-                                        : -cone / 2.0 + cone * (k + 0.5) / s.n_views;
-        ex[k] = float(double(s.view_dist) * std::tan(deg * M_PI / 180.0));
-    }
-    TexDesc td[kNoAllocMaxTex];
+    FillParams fp{};
+    fp.nr = nr;
+    fp.n_tex = n_tex;
+    for (int k = 0; k < nr; k++)
+        fp.ex[k] = float(double(s.view_dist) * std::tan(eye_angle_deg(s, k, 0.5) * M_PI / 180.0));
     for (uint32_t k = 0; k < n_tex; k++) {
         const uint32_t w = tex_wh[2 * k], h = tex_wh[2 * k + 1];
         uint32_t m = w > h ? w : h, l = 0;
         while ((1u << l) < m) l++;
-        td[k].offset = 0;
-        td[k].w = w;
-        td[k].h = h;
-        td[k].levels = l + 1;
-        td[k].pad = 0;
+        fp.tex[k].offset = 0;
+        fp.tex[k].w = w;
+        fp.tex[k].h = h;
+        fp.tex[k].levels = l + 1;
+        fp.tex[k].pad = 0;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CKN(cudaMemcpyAsync(scr->ex, ex, sizeof(float) * nr, cudaMemcpyHostToDevice, st), "copy eyes");
-    CKN(cudaMemcpyAsync(scr->tex, td, sizeof(TexDesc) * n_tex, cudaMemcpyHostToDevice, st), "copy texture sizes");
-    CKN(cudaMemsetAsync(&scr->ctr, 0, sizeof(Counters), st), "clear counters");
+    k_noalloc_fill<<<1, 256, 0, st>>>(fp, scr);
+    CKN(cudaGetLastError(), "launch k_noalloc_fill");
 
     for (int k = 0; k < 12; k++) a.model[k] = model[k];
     a.ex = scr->ex;

@@ -28,7 +28,7 @@ struct lfdpr_display {
     uint4* points = nullptr;
     uint32_t max_points = 0;
     lfdpr::WorkRec* work = nullptr;
-    uint32_t* near = nullptr;
+    uint32_t* near = nullptr;     // points whose cell or triangle reaches within near_z of the eyes' plane
     lfdpr::ResolveRec* rrec = nullptr;
     uint2* rmat = nullptr;        // normal-map tv_min / tv_max per point (allocated with the first mesh of materials)
     uint64_t* keys = nullptr;
@@ -74,8 +74,8 @@ lfdpr_status cuda_fail(cudaError_t e, const char* what);
 // Kernel arguments of one frame of `mesh` on `disp` (model left unset).
 FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh);
 // The frame up to the splat on stream s: counters reset, set-up, scan,
-// emission, fetch, key clear, and (if near) the near-plane splat; stage
-// events 0-5 recorded if marks.
+// emission, fetch (with the near-limit records), key clear; stage events 0-5
+// recorded if marks.
 lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
-                                bool marks, bool near);
+                                bool marks);
 }  // namespace lfdpr

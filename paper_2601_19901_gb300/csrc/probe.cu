@@ -1,6 +1,7 @@
 // Roofline probe for the splat's depth test: throughput of 64-bit atomicMin
-// on global memory (resolved in L2) and on shared memory. Each thread takes
-// operations k = tid, tid + stride, ... of (idx[k], val[k]).
+// on global memory (resolved in L2) at random or warp-coherent addresses, and
+// on shared memory. Each thread takes operations k = tid, tid + stride, ... of
+// (idx[k], val[k]).
 #include "lfdpr_internal.cuh"
 
 namespace lfdpr {
@@ -15,6 +16,21 @@ __global__ void __launch_bounds__(256) k_probe_global(unsigned long long* words,
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_ops;
          k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t i = __ldg(idx + k);
+        if (i < n_words) atomicMin(words + i, __ldg(val + k));
+    }
+}
+
+// Coherent variant: the 32 operations of warp group q = k / 32 hit the 32
+// consecutive words from (idx[32 q] & ~31): one warp instruction covers 256
+// contiguous bytes. The grid stride is a multiple of 32, so a warp's lanes
+// always form one group.
+__global__ void __launch_bounds__(256) k_probe_coherent(unsigned long long* words, uint64_t n_words,
+                                                         const uint32_t* __restrict__ idx,
+                                                         const unsigned long long* __restrict__ val,
+                                                         uint64_t n_ops) {
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_ops;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = uint64_t(__ldg(idx + (k & ~uint64_t(31))) & ~31u) + (k & 31u);
         if (i < n_words) atomicMin(words + i, __ldg(val + k));
     }
 }
@@ -40,10 +56,12 @@ __global__ void __launch_bounds__(256) k_probe_shared(unsigned long long* words,
 }  // namespace
 
 cudaError_t launch_probe_atomic(uint64_t* words, uint64_t n_words, const uint32_t* idx, const uint64_t* val,
-                                uint64_t n_ops, bool shared, int sm_count, cudaStream_t s) {
+                                uint64_t n_ops, int mode, int sm_count, cudaStream_t s) {
     auto* w = reinterpret_cast<unsigned long long*>(words);
     auto* v = reinterpret_cast<const unsigned long long*>(val);
-    if (shared) {
+    if (mode == 2) {
+        k_probe_coherent<<<sm_count * 8, 256, 0, s>>>(w, n_words, idx, v, n_ops);
+    } else if (mode == 1) {
         const size_t smem = (size_t)n_words * 8u;
         cudaError_t e = cudaFuncSetAttribute(k_probe_shared, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -67,7 +67,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
 }
 
 lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
-                                bool marks, bool near) {
+                                bool marks) {
     auto mk = [&](int k) {
         if (marks) cudaEventRecord(disp->ev[k], s);
     };
@@ -87,7 +87,8 @@ lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const Fra
         CKF(launch_emit(a, s), "launch k_emit");
         mk(3);
         CKF(launch_fetch(a, s), "launch k_fetch");
-        disp->launches += 4;
+        CKF(launch_near_work(a, s), "launch k_near_work");
+        disp->launches += 5;
         if (a.mat_tex) {
             CKF(launch_fetch_mat(a, s), "launch k_fetch_mat");
             disp->launches += 1;
@@ -98,10 +99,6 @@ lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const Fra
     mk(4);
     CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
     mk(5);
-    if (near && mesh->n_tris) {
-        CKF(launch_splat_near(a, s), "launch k_splat_near");
-        disp->launches += 1;
-    }
 #undef CKF
     return LFDPR_OK;
 }
@@ -172,17 +169,6 @@ void free_mesh(lfdpr_mesh* m) {
     cudaFree(m->offsets);
     cudaFree(m->block_sums);
     delete m;
-}
-
-bool supersampled(const lfdpr_display_desc& d) { return d.recon == 1 || d.recon == 2; }
-
-// Eye angle of rendered view k at the fraction u of its interval: N equal
-// angular intervals, or 2N half-intervals with angular supersampling (u = 1/2
-// puts the even ones on the N view centres).
-double eye_angle_deg(const lfdpr_display_desc& d, int k, double u) {
-    const double cone = d.cone_deg;
-    return supersampled(d) ? -cone / 2.0 + cone * (k + 0.5 + u) / (2.0 * d.n_views)
-                           : -cone / 2.0 + cone * (k + u) / d.n_views;
 }
 
 // Eyes, their largest |x| and the views' positions on the display-view axis
@@ -653,12 +639,11 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FrameArgs a = frame_args(disp, mesh);
     for (int k = 0; k < 12; k++) a.model[k] = model[k];
-    const lfdpr_status st = record_frame_front(disp, mesh, a, s, disp->timing, false);
+    const lfdpr_status st = record_frame_front(disp, mesh, a, s, disp->timing);
     if (st != LFDPR_OK) return st;
     if (mesh->n_tris) {
         CK(launch_splat(a, s), "launch k_splat");
-        CK(launch_splat_near(a, s), "launch k_splat_near");
-        disp->launches += 2;
+        disp->launches += 1;
     }
     mark(disp, 6, s);
     CK(launch_resolve(a, s), "launch k_resolve");
@@ -765,14 +750,15 @@ lfdpr_status lfdpr_get_buffers(lfdpr_display* disp, lfdpr_mesh* mesh, lfdpr_buff
 }
 
 lfdpr_status lfdpr_probe_atomic_min(uint64_t* words, uint64_t n_words, const uint32_t* idx, const uint64_t* val,
-                                    uint64_t n_ops, int32_t shared, void* stream) {
+                                    uint64_t n_ops, int32_t mode, void* stream) {
     g_err[0] = 0;
     if (!words || !idx || !val || n_words == 0) return fail(LFDPR_EINVAL, "probe: null or empty argument");
-    if (shared && n_words > 8192) return fail(LFDPR_EINVAL, "probe: shared variant holds at most 8192 words");
+    if (mode < 0 || mode > 2) return fail(LFDPR_EINVAL, "probe: mode %d outside 0-2", mode);
+    if (mode == 1 && n_words > 8192) return fail(LFDPR_EINVAL, "probe: shared variant holds at most 8192 words");
     int dev = 0, sms = 1;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
-    CK(launch_probe_atomic(words, n_words, idx, val, n_ops, shared != 0, sms, static_cast<cudaStream_t>(stream)),
+    CK(launch_probe_atomic(words, n_words, idx, val, n_ops, mode, sms, static_cast<cudaStream_t>(stream)),
        "launch probe");
     return LFDPR_OK;
 }

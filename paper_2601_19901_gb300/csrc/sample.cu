@@ -11,9 +11,12 @@
 //            column walk writes (triangle, cell) for each of its points.
 //   k_fetch  one thread per point: texture coordinate of the cell centre and
 //            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7); then the
-//            point's splat record (its cell projected into the views) and,
-//            if some view can hold a candidate pixel of it, its place in the
+//            point's splat record (its cell projected into the views) and, if
+//            some view can hold a candidate pixel of it, its place in the
 //            splat's work list.
+//   k_near_work  one thread per point whose cell or triangle reaches within
+//            near_z of the eyes' plane: the splat record of its cell and
+//            triangle clipped to that limit.
 //
 // Every floating-point step here is bit-specified (binary32, explicit fmaf,
 // IEEE division and square root) so the point set is identical to the CPU
@@ -582,7 +585,7 @@ __device__ __forceinline__ void lattice_corner(const float4& q0, const float4& q
 constexpr float kCrossDy = 1e-3f;
 template <int N>
 __device__ __forceinline__ void band_bounds(const float* A, const float* B, const float* Y, float ya, float yb,
-                                            float E, float4& L) {
+                                            float E, float cross_dy, float4& L) {
     float xm[N], xp[N];   // x at eye -E and at eye +E
 #pragma unroll
     for (int k = 0; k < N; k++) {
@@ -610,7 +613,7 @@ __device__ __forceinline__ void band_bounds(const float* A, const float* B, cons
             const bool cross = row && ((Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]));
             const float dxm = xm[q] - xm[p], dxp = xp[q] - xp[p];
             const float rdy = __fdividef(1.0f, cross ? Y[q] - Y[p] : 1.0f);
-            const float f = (yc - Y[p]) * rdy, d = kCrossDy * fabsf(rdy);
+            const float f = (yc - Y[p]) * rdy, d = cross_dy * fabsf(rdy);
             const float f0 = fmaxf(f - d, 0.0f), f1 = fminf(f + d, 1.0f);
             fold(cross, fmaf(f0, dxm, xm[p]), fmaf(f0, dxp, xp[p]));
             fold(cross, fmaf(f1, dxm, xm[p]), fmaf(f1, dxp, xp[p]));
@@ -622,6 +625,138 @@ __device__ __forceinline__ void band_bounds(const float* A, const float* B, cons
     }
     const float hE = E > 0.0f ? __fdividef(0.5f, E) : 0.0f;
     L = make_float4(0.5f * (lm + lp), (lp - lm) * hE, 0.5f * (um + up), (up - um) * hE);
+}
+
+// Points whose cell or triangle reaches within near_z of the eyes' plane are
+// projected with up to D / near_z magnification and, past the plane, not at
+// all. Their cell and triangle are clipped to depth D - z >= near_z first (a
+// plane shared by every view: all eyes lie at z = D), which leaves bounded
+// polygons whose vertices project affinely in Ex like any other; candidate
+// bounds then come from band_bounds with a margin kNearPad (and crossing
+// uncertainty kNearCrossDy) sized for that magnification. Hits nearer than
+// near_z are rejected by the per-pixel test as everywhere.
+constexpr float kNearPad = 1.0f / 16.0f;
+constexpr float kNearCrossDy = 1.0f / 32.0f;
+
+// Clip the convex polygon V (N world vertices) to z <= zc (Sutherland-
+// Hodgman against one plane): at most N + 1 vertices, written to O and padded
+// to N + 1 by repeating the last one (repeated vertices add no area and cross
+// no row). Returns the vertex count (below 3: nothing left).
+template <int N>
+__device__ __forceinline__ int clip_below(const float (&V)[N][3], float zc, float (&O)[N + 1][3]) {
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        const float* p = V[k];
+        const float* q = V[k + 1 == N ? 0 : k + 1];
+        const bool pin = p[2] <= zc, qin = q[2] <= zc;
+        if (pin) {
+            O[m][0] = p[0];
+            O[m][1] = p[1];
+            O[m][2] = p[2];
+            m++;
+        }
+        if (pin != qin) {
+            const float f = __fdiv_rn(zc - p[2], q[2] - p[2]);
+            O[m][0] = fmaf(f, q[0] - p[0], p[0]);
+            O[m][1] = fmaf(f, q[1] - p[1], p[1]);
+            O[m][2] = zc;
+            m++;
+        }
+    }
+    for (int k = m; k < N + 1; k++) {
+        O[k][0] = m ? O[m - 1][0] : 0.0f;
+        O[k][1] = m ? O[m - 1][1] : 0.0f;
+        O[k][2] = m ? O[m - 1][2] : zc;
+    }
+    return m;
+}
+
+// The splat record of such a point: candidate rows and column bounds of the
+// clipped cell and triangle (L0, L1, not yet shifted to pixel columns), and
+// Eq. 8's area coefficients of the clipped cell (its drawable part).
+struct NearRec {
+    uint32_t y0, ny;
+    float4 L0, L1;
+    float alpha, beta;
+};
+__device__ __forceinline__ NearRec near_record(const DispConst& c, const float4& q0, const float4& q1,
+                                               const float4& q2, const float4& q3, const float4& q4, int i, int j,
+                                               bool interior) {
+    const float zc = c.D - c.near_z;
+    NearRec o;
+    o.y0 = 0;
+    o.ny = 0;
+    o.L0 = make_float4(-INFINITY, 0.0f, INFINITY, 0.0f);
+    o.L1 = o.L0;
+    o.alpha = 0.0f;
+    o.beta = 0.0f;
+    float Cw[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        lattice_corner(q0, q1, q2, q3, i + (k == 1 || k == 2), j + (k >= 2), Cw[k]);
+    float P[5][3];
+    const int m = clip_below<4>(Cw, zc, P);
+    if (m < 3) return o;
+    // the triangle's vertices from the lattice frame: P0 + a u-hat + b v-hat
+    float Tw[3][3];
+    Tw[0][0] = q0.x;
+    Tw[0][1] = q0.y;
+    Tw[0][2] = q0.z;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float aa = k ? q4.z : q4.x, bb = k ? q4.w : q4.y;
+        Tw[k + 1][0] = fmaf(aa, q1.x, fmaf(bb, q2.x, q0.x));
+        Tw[k + 1][1] = fmaf(aa, q1.y, fmaf(bb, q2.y, q0.y));
+        Tw[k + 1][2] = fmaf(aa, q1.z, fmaf(bb, q2.z, q0.z));
+    }
+    float Q[4][3];
+    const int mt = clip_below<3>(Tw, zc, Q);
+    float A[5], B[5], Y[5], s[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        s[k] = __fdiv_rn(c.D, c.D - P[k][2]);
+        project_point(c.D, c.x0, c.y0, c.ipw, c.iph, P[k][0], P[k][1], P[k][2], A[k], B[k], Y[k]);
+    }
+    // Eq. 8: the clipped cell's shoelace sum relative to its first vertex
+    const float cx0 = P[0][0] * s[0], cy0 = P[0][1] * s[0];
+    float da[4], db[4], dy[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        da[k] = fmaf(P[k + 1][0], s[k + 1], -cx0) * c.ipw;
+        db[k] = (s[0] - s[k + 1]) * c.ipw;
+        dy[k] = fmaf(-P[k + 1][1], s[k + 1], cy0) * c.iph;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        o.alpha = o.alpha + fmaf(da[k], dy[k + 1], -(da[k + 1] * dy[k]));
+        o.beta = o.beta + fmaf(db[k], dy[k + 1], -(db[k + 1] * dy[k]));
+    }
+    if (mt < 3) return o;   // no part of the triangle can be drawn
+    float tA[4], tB[4], tY[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        project_point(c.D, c.x0, c.y0, c.ipw, c.iph, Q[k][0], Q[k][1], Q[k][2], tA[k], tB[k], tY[k]);
+    float cymn = Y[0], cymx = Y[0], tymn = tY[0], tymx = tY[0];
+#pragma unroll
+    for (int k = 1; k < 5; k++) {
+        cymn = fminf(cymn, Y[k]);
+        cymx = fmaxf(cymx, Y[k]);
+    }
+#pragma unroll
+    for (int k = 1; k < 4; k++) {
+        tymn = fminf(tymn, tY[k]);
+        tymx = fmaxf(tymx, tY[k]);
+    }
+    const float fy0 = fmaxf(ceilf(fmaxf(cymn, tymn) - 0.5f - kNearPad), 0.0f);
+    const float fy1 = fminf(floorf(fminf(cymx, tymx) - 0.5f + kNearPad), float(c.H - 1));
+    if (!(fy0 <= fy1)) return o;
+    o.y0 = uint32_t(int(fy0));
+    o.ny = uint32_t(int(fy1) - int(fy0) + 1);
+    const float ya = float(o.y0) + 0.5f, yb = float(o.y0 + o.ny - 1u) + 0.5f;
+    band_bounds<5>(A, B, Y, ya, yb, c.ex_max, kNearCrossDy, o.L0);
+    if (!interior) band_bounds<4>(tA, tB, tY, ya, yb, c.ex_max, kNearCrossDy, o.L1);
+    return o;
 }
 
 // One thread per point: tv_min / tv_max (Sec. 3.3), then the point's splat
@@ -657,52 +792,78 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
 
         // splat work record
         const TriProj tp = a.tproj[pt.x];
-        float A[4], B[4], Y[4], Cx[4], Cy[4], Cs[4];
-        bool near = !((c.D - tp.b.w) > 1e-4f * c.D);
+        float Cw[4][3];
+        // the cell or its triangle reaches depth D - z < near_z: clipped path
+        bool near = !((c.D - tp.b.w) >= c.near_z);
         bool interior = true;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int ia = int(i) + (k == 1 || k == 2), jb = int(j) + (k >= 2);
-            float C[3];
-            lattice_corner(q0, q1, q2, q3, ia, jb, C);
-            Cx[k] = C[0];
-            Cy[k] = C[1];
-            Cs[k] = __fdiv_rn(c.D, c.D - C[2]);
-            near |= !((c.D - C[2]) > 1e-4f * c.D);
-            project_point(c.D, c.x0, c.y0, c.ipw, c.iph, C[0], C[1], C[2], A[k], B[k], Y[k]);
+            lattice_corner(q0, q1, q2, q3, ia, jb, Cw[k]);
+            near |= !((c.D - Cw[k][2]) >= c.near_z);
             const float uu = float(ia) * su + q2.w, vv = float(jb) * sv + q3.w;
             interior &= edge_fn(q4.x, q4.y, q4.z, q4.w, uu, vv) >= 0.0f &&
                         edge_fn(q4.z, q4.w, 0.0f, 0.0f, uu, vv) >= 0.0f &&
                         edge_fn(0.0f, 0.0f, q4.x, q4.y, uu, vv) >= 0.0f;
         }
-        const float cymn = fminf(fminf(Y[0], Y[1]), fminf(Y[2], Y[3]));
-        const float cymx = fmaxf(fmaxf(Y[0], Y[1]), fmaxf(Y[2], Y[3]));
-        const float tymn = fminf(fminf(tp.y.x, tp.y.y), tp.y.z), tymx = fmaxf(fmaxf(tp.y.x, tp.y.y), tp.y.z);
-        const float fy0 = fmaxf(ceilf(fmaxf(cymn, tymn) - 0.5f - kBoxPad), 0.0f);
-        const float fy1 = fminf(floorf(fminf(cymx, tymx) - 0.5f + kBoxPad), H1);
+        const bool depth_ok = !near && (c.D - tp.a.w) <= c.far_z;
+        const uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
         uint32_t y0 = 0, ny = 0;
-        if (!near && fy0 <= fy1) {
-            y0 = uint32_t(int(fy0));
-            ny = uint32_t(int(fy1) - int(fy0) + 1);
-        }
-        const bool depth_ok = (c.D - tp.b.w) >= c.near_z && (c.D - tp.a.w) <= c.far_z;
-        uint32_t flags = (interior ? kFlagInterior : 0u) | (depth_ok ? kFlagDepthOk : 0u);
+        float alpha, beta, pad;
         // candidate columns: lower and upper lines of the cell's and of the
         // triangle's x-extent within the band of candidate rows (none where
         // the triangle is one cell, or the cell lies inside its triangle)
         float4 L0 = make_float4(-INFINITY, 0.0f, INFINITY, 0.0f), L1 = L0;
+        if (!near) {
+            pad = kBoxPad;
+            float A[4], B[4], Y[4], Cs[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                Cs[k] = __fdiv_rn(c.D, c.D - Cw[k][2]);
+                project_point(c.D, c.x0, c.y0, c.ipw, c.iph, Cw[k][0], Cw[k][1], Cw[k][2], A[k], B[k], Y[k]);
+            }
+            const float cymn = fminf(fminf(Y[0], Y[1]), fminf(Y[2], Y[3]));
+            const float cymx = fmaxf(fmaxf(Y[0], Y[1]), fmaxf(Y[2], Y[3]));
+            const float tymn = fminf(fminf(tp.y.x, tp.y.y), tp.y.z), tymx = fmaxf(fmaxf(tp.y.x, tp.y.y), tp.y.z);
+            const float fy0 = fmaxf(ceilf(fmaxf(cymn, tymn) - 0.5f - kBoxPad), 0.0f);
+            const float fy1 = fminf(floorf(fminf(cymx, tymx) - 0.5f + kBoxPad), H1);
+            if (fy0 <= fy1) {
+                y0 = uint32_t(int(fy0));
+                ny = uint32_t(int(fy1) - int(fy0) + 1);
+                const float ya = float(y0) + 0.5f, yb = float(y0 + ny - 1u) + 0.5f;
+                const float tA3[3] = {tp.a.x, tp.a.y, tp.a.z}, tB3[3] = {tp.b.x, tp.b.y, tp.b.z};
+                const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
+                if (__ldg(a.counts + pt.x) != 1u) band_bounds<4>(A, B, Y, ya, yb, c.ex_max, kCrossDy, L0);
+                if (!interior) band_bounds<3>(tA3, tB3, tY3, ya, yb, c.ex_max, kCrossDy, L1);
+            }
+            // Eq. 8's projected cell area is |alpha + beta Ex| / 2: a corner's pixel
+            // x is (x s - x0) W/fw + (1 - s) W/fw Ex (s = D / (D - z)), its pixel y
+            // (y0 - y s) H/fh the same in every view, so the shoelace sum of the
+            // corners taken relative to the first one is affine in Ex; the
+            // differences are formed before scaling so that x0 and y0 cancel exactly
+            float da[3], db[3], dy[3];
+            const float cx0 = Cw[0][0] * Cs[0], cy0 = Cw[0][1] * Cs[0];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                da[k] = fmaf(Cw[k + 1][0], Cs[k + 1], -cx0) * c.ipw;
+                db[k] = (Cs[0] - Cs[k + 1]) * c.ipw;
+                dy[k] = fmaf(-Cw[k + 1][1], Cs[k + 1], cy0) * c.iph;
+            }
+            alpha = fmaf(da[0], dy[1], -(da[1] * dy[0])) + fmaf(da[1], dy[2], -(da[2] * dy[1]));
+            beta = fmaf(db[0], dy[1], -(db[1] * dy[0])) + fmaf(db[1], dy[2], -(db[2] * dy[1]));
+        } else {
+            // listed for k_near_work, which writes its record
+            pad = kNearPad;
+            alpha = 0.0f;
+            beta = 0.0f;
+        }
         if (ny > 0) {
-            const float ya = float(y0) + 0.5f, yb = float(y0 + ny - 1u) + 0.5f;
-            const float tA3[3] = {tp.a.x, tp.a.y, tp.a.z}, tB3[3] = {tp.b.x, tp.b.y, tp.b.z};
-            const float tY3[3] = {tp.y.x, tp.y.y, tp.y.z};
-            if (__ldg(a.counts + pt.x) != 1u) band_bounds<4>(A, B, Y, ya, yb, c.ex_max, L0);
-            if (!interior) band_bounds<3>(tA3, tB3, tY3, ya, yb, c.ex_max, L1);
             // shifted so the splat converts them straight to pixel columns:
-            // pixel centres at x + 1/2, candidate margin kBoxPad on each side
-            L0.x = L0.x - (0.5f + kBoxPad);
-            L1.x = L1.x - (0.5f + kBoxPad);
-            L0.z = L0.z - (0.5f - kBoxPad);
-            L1.z = L1.z - (0.5f - kBoxPad);
+            // pixel centres at x + 1/2, candidate margin `pad` on each side
+            L0.x = L0.x - (0.5f + pad);
+            L1.x = L1.x - (0.5f + pad);
+            L0.z = L0.z - (0.5f - pad);
+            L1.z = L1.z - (0.5f - pad);
             // No candidate column in any view: a correctly rounded fmaf is
             // monotone in Ex, so over eyes in [-E, E] the splat's lower
             // line stays above the larger of its two lines' smaller end
@@ -720,28 +881,12 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
             const float xhi = fminf(floorf(fminf(fmaxf(h0m, h0p), fmaxf(h1m, h1p))), float(c.W - 1));
             if (ordered && xlo > xhi) ny = 0;
         }
-
-        // Eq. 8's projected cell area is |alpha + beta Ex| / 2: a corner's pixel
-        // x is (x s - x0) W/fw + (1 - s) W/fw Ex (s = D / (D - z)), its pixel y
-        // (y0 - y s) H/fh the same in every view, so the shoelace sum of the
-        // corners taken relative to the first one is affine in Ex; the
-        // differences are formed before scaling so that x0 and y0 cancel exactly
-        float da[3], db[3], dy[3];
-        const float cx0 = Cx[0] * Cs[0], cy0 = Cy[0] * Cs[0];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            da[k] = fmaf(Cx[k + 1], Cs[k + 1], -cx0) * c.ipw;
-            db[k] = (Cs[0] - Cs[k + 1]) * c.ipw;
-            dy[k] = fmaf(-Cy[k + 1], Cs[k + 1], cy0) * c.iph;
-        }
-        const float alpha = fmaf(da[0], dy[1], -(da[1] * dy[0])) + fmaf(da[1], dy[2], -(da[2] * dy[1]));
-        const float beta = fmaf(db[0], dy[1], -(db[1] * dy[0])) + fmaf(db[1], dy[2], -(db[2] * dy[1]));
         ResolveRec* rr = a.rrec + p;
         rr->a = make_float4(alpha, beta, q5.x, q5.y);
         rr->b = make_uint4(__float_as_uint(q5.z), tmin, tmax, 0u);
 
         // warp-aggregated appends: points with candidate rows to the work
-        // list, points reaching the eyes' plane to the near list
+        // list, points reaching within near_z of the eyes' plane to the near list
         const unsigned mask = __activemask();
         const int leader = __ffs(mask) - 1;
         const unsigned below = (1u << lane) - 1u;
@@ -761,6 +906,55 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
             w->meta = make_uint4(y0 | (ny << 14) | (flags << 29), pt.y, pt.x, p);
         }
         if (near) a.near[nbase + __popc(bnear & below)] = p;
+    }
+}
+
+// The splat records of the near list (run after k_fetch): each point's cell
+// and triangle clipped to depth >= near_z (near_record), its work record
+// appended to the work list if some view can hold a candidate pixel, and
+// Eq. 8's coefficients of the clipped cell in its resolve record.
+__global__ void __launch_bounds__(256) k_near_work(FrameArgs a) {
+    if (a.ctr->overflow) return;
+    const DispConst& c = a.dc;
+    const uint32_t n = a.ctr->n_near;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t p = a.near[k];
+        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        const TriRec* r = a.rec + pt.x;
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+        const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
+        bool interior = true;
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const int ia = i + (m == 1 || m == 2), jb = j + (m >= 2);
+            const float uu = float(ia) * q0.w + q2.w, vv = float(jb) * q1.w + q3.w;
+            interior &= edge_fn(q4.x, q4.y, q4.z, q4.w, uu, vv) >= 0.0f &&
+                        edge_fn(q4.z, q4.w, 0.0f, 0.0f, uu, vv) >= 0.0f &&
+                        edge_fn(0.0f, 0.0f, q4.x, q4.y, uu, vv) >= 0.0f;
+        }
+        NearRec o = near_record(c, q0, q1, q2, q3, q4, i, j, interior);
+        a.rrec[p].a.x = o.alpha;
+        a.rrec[p].a.y = o.beta;
+        if (o.ny > 0) {
+            o.L0.x = o.L0.x - (0.5f + kNearPad);
+            o.L1.x = o.L1.x - (0.5f + kNearPad);
+            o.L0.z = o.L0.z - (0.5f - kNearPad);
+            o.L1.z = o.L1.z - (0.5f - kNearPad);
+        }
+        const unsigned mask = __activemask();
+        const int leader = __ffs(mask) - 1;
+        const unsigned bal = __ballot_sync(mask, o.ny > 0);
+        uint32_t base = 0;
+        if (lane == leader && bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
+        base = __shfl_sync(mask, base, leader);
+        if (o.ny > 0) {
+            WorkRec* w = a.work + base + __popc(bal & ((1u << lane) - 1u));
+            w->L0 = o.L0;
+            w->L1 = o.L1;
+            w->meta = make_uint4(o.y0 | (o.ny << 14) | ((interior ? kFlagInterior : 0u) << 29), pt.y, pt.x, p);
+        }
     }
 }
 
@@ -823,6 +1017,11 @@ cudaError_t launch_fetch_mat(const FrameArgs& a, cudaStream_t s) {
 
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s) {
     k_fetch<<<a.sm_count * 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_work(const FrameArgs& a, cudaStream_t s) {
+    k_near_work<<<a.sm_count, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

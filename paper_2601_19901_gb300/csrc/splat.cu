@@ -46,8 +46,9 @@ namespace {
 // test. The margin of the candidate ranges only admits extra candidates; the
 // test alone decides.
 //
-// Points whose cell or triangle reaches the eyes' plane (none in front-only
-// scenes) are listed apart and splatted by k_splat_near.
+// Points whose cell or triangle reaches within near_z of the eyes' plane come
+// with candidate bounds of their cell and triangle clipped to that limit
+// (k_fetch) and take the same passes and test.
 constexpr int kSplatWarps = 8;
 // Ask L2 for the line holding p (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -373,49 +374,6 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat_batch(const Splat
     splat_units<S>(src, s_unit0[n_scenes], reinterpret_cast<SplatWarpSmem<S>*>(s_dyn)[threadIdx.x >> 5]);
 }
 
-// Points whose cell or triangle reaches the eyes' plane: their projections
-// are unbounded, so every pixel of every view takes the plane-space test,
-// one (point, view) pair per thread. None occur in front-only scenes.
-__global__ void __launch_bounds__(256) k_splat_near(FrameArgs a) {
-    if (a.ctr->overflow) return;
-    const DispConst& c = a.dc;
-    const uint32_t n = a.ctr->n_near;
-    const uint64_t pairs = (uint64_t)n * c.nr;
-    const uint64_t npix = (uint64_t)c.W * c.H;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.keys);
-    uint32_t writes = 0;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < pairs;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = uint32_t(g / c.nr);
-        const int v = int(g - (uint64_t)k * c.nr);
-        const uint32_t p = a.near[k];
-        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
-        const TriRec* r = a.rec + pt.x;
-        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
-        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
-        const int i = int(pt.y & 0xffffu), j = int(pt.y >> 16);
-        const float ulo = float(i) * q0.w, uhi = float(i + 1) * q0.w;
-        const float vlo = float(j) * q1.w, vhi = float(j + 1) * q1.w;
-        const float Ex = __ldg(a.ex + v);
-        const float qEx = Ex - q0.x, qEy = 0.0f - q0.y, qEz = c.D - q0.z;
-        const float num = -dot3(q3.x, q3.y, q3.z, qEx, qEy, qEz);
-        for (int y = 0; y < c.H; y++) {
-            for (int x = 0; x < c.W; x++) {
-                float t;
-                if (!pixel_test(c, Ex, num, qEx, qEy, qEz, q1, q2, q3, q4, ulo, uhi, vlo, vhi, false, false, x, y,
-                                t))
-                    continue;
-                atomicMin(keys + (uint64_t)v * npix + (uint64_t)y * c.W + x,
-                          ((unsigned long long)__float_as_uint(t) << 32) | p);
-                writes++;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) writes += __shfl_xor_sync(0xffffffffu, writes, o);
-    if ((threadIdx.x & 31) == 0 && writes) atomicAdd(&a.ctr->n_writes, writes);
-}
-
 // Eq. 8's interpolation weight for one view pixel whose depth test kept the
 // point with resolve record (ra, rb): the splat's pixel area in view Ex is
 // the shoelace area of its cell corners projected from the eye,
@@ -652,11 +610,6 @@ cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots
         case 8: return splat_batch<8>(scenes, n_scenes, grid, s);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_splat_near(const FrameArgs& a, cudaStream_t s) {
-    k_splat_near<<<a.sm_count * 2, 256, 0, s>>>(a);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {

@@ -261,11 +261,13 @@ def lfdpr_view_eyes(disp: int, n: int) -> np.ndarray:
     return out
 
 
+PROBE_RANDOM, PROBE_SHARED, PROBE_COHERENT = 0, 1, 2
+
+
 def lfdpr_probe_atomic_min(words_ptr: int, n_words: int, idx_ptr: int, val_ptr: int, n_ops: int,
-                           shared: bool, stream=None):
+                           mode: int, stream=None):
     _check(lib().lfdpr_probe_atomic_min(C.c_void_p(words_ptr), n_words, C.c_void_p(idx_ptr),
-                                        C.c_void_p(val_ptr), n_ops, 1 if shared else 0,
-                                        _stream(stream)))
+                                        C.c_void_p(val_ptr), n_ops, int(mode), _stream(stream)))
 
 
 NOALLOC_MAX_TRIS = 32768

@@ -806,6 +806,47 @@ def test_eq8_area_of_cells_against_the_projection_matrix():
     assert areas.min() < 0.05 and areas.max() > 4.0
 
 
+def test_eq8_area_of_a_cell_reaching_the_eyes_plane_is_its_drawable_part():
+    """A cell that reaches past the eyes' plane has no bounded projection;
+    its Eq. 8 area is that of its part at depth >= near_z. Pinned against
+    rays through a dense grid of sub-pixel positions, each hit tested
+    against the cell and the near limit, in double."""
+    d = replace(unit_display(), n_views=3, cone_deg=30.0)
+    D, near = float(d.view_dist), float(d.near_z)
+    eu = np.array([1.0, 0.0, 0.0])
+    ev = np.array([0.0, 0.6, 0.8])          # tilted toward the eyes: z grows along v
+    su, sv = 0.1, 0.5                       # z runs from D - 0.3 to D + 0.1
+    nrm = np.cross(eu, ev)
+    h = 1.0 / 8.0
+    for Ex in O.eyes(d).astype(np.float64):
+        # the cell straight in front of this eye
+        P0 = np.array([float(np.float32(Ex)) - 0.05, -0.05, D - 0.3])
+        T = np.zeros(O.TRI_FLOATS, np.float32)
+        T[O.F["p0"]:O.F["p0"] + 3] = P0
+        T[O.F["eu"]:O.F["eu"] + 3] = eu
+        T[O.F["ev"]:O.F["ev"] + 3] = ev
+        T[O.F["s_u"]], T[O.F["s_v"]] = su, sv
+        P0 = T[O.F["p0"]:O.F["p0"] + 3].astype(np.float64)
+        E = np.array([Ex, 0.0, D])
+        xs = np.arange(-300.0, 300.0, h) + h / 2
+        X, Y = np.meshgrid(xs, xs)
+        F = np.stack([-0.5 * d.focal_w + X * d.focal_w / d.view_w, 0.5 * d.focal_h - Y * d.focal_h / d.view_h,
+                      np.zeros_like(X)], -1)
+        dirs = F - E
+        t = ((P0 - E) @ nrm) / (dirs @ nrm)
+        hit = E + t[..., None] * dirs
+        q = hit - P0
+        u, v = q @ eu, q @ ev
+        inside = (u >= 0) & (u < su) & (v >= 0) & (v < sv) & (t * D >= near) & (t > 0)
+        assert not inside[0].any() and not inside[-1].any() and not inside[:, 0].any() and not inside[:, -1].any()
+        want = inside.sum() * h * h
+        ys_, xs_ = np.nonzero(inside)
+        perim = 2 * (np.ptp(xs_) + np.ptp(ys_)) * h
+        got = O.splat_area_px(d, T, 0, 0, float(Ex))
+        assert want > 1000.0
+        assert abs(got - want) <= perim * h, (Ex, got, want)
+
+
 # ---------------------------------------------------------------------------
 # Sec. 4's supersampling at random angles and Gaussian reconstruction
 # ---------------------------------------------------------------------------

@@ -6,7 +6,8 @@ device memory - call lfdpr_sample_points_noalloc with buffers they already
 own; its scratch is a fixed array inside the library. Its output must equal
 the regular path's point generation with the tolerance every sampling test
 here uses (bit-exact counts and point set), on two calls in a row: the second
-call reuses the scratch the first one left behind.
+call reuses the scratch the first one left behind. The second call must not
+change the device's free memory.
 """
 import numpy as np
 import pytest
@@ -63,6 +64,51 @@ def test_noalloc_matches_the_regular_entry_point_on_two_calls(setup):
             assert np.array_equal(counts, ref_counts)
             assert np.array_equal(pts[:n, :2], ref_pts)
             assert np.all(pts[n:] == 0)             # nothing written past the point set
+
+
+def test_noalloc_second_call_leaves_free_device_memory_unchanged(setup):
+    import torch
+    d, sc, bufs, wh = setup
+    s = torch.cuda.current_stream()
+    cap = 1 << 16
+    pts = torch.zeros((cap, 4), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(sc.n_tris, dtype=torch.int32, device="cuda")
+    fc = torch.zeros(4, dtype=torch.int32, device="cuda")
+
+    def call(frame):
+        lfdpr.lfdpr_sample_points_noalloc(lfdpr.desc_of(d), S.model_matrix(frame), bufs["xyz"].data_ptr(),
+                                          bufs["uv"].data_ptr(), bufs["idx"].data_ptr(),
+                                          bufs["tri_tex"].data_ptr(), sc.n_tris, wh, pts.data_ptr(), cap,
+                                          counts.data_ptr(), fc.data_ptr(), s)
+        torch.cuda.synchronize()
+
+    call(1)                                   # loads the kernels and looks up the scratch address
+    free0, _ = torch.cuda.mem_get_info()
+    call(2)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert fc.cpu()[0] > 0
+
+
+def test_noalloc_with_angular_supersampling_matches_the_regular_entry_point(setup):
+    """2N rendered views (recon 1): the eyes at the half-interval steps."""
+    import torch
+    from dataclasses import replace
+    _, sc, bufs, wh = setup
+    d = replace(S.display_tiny(), n_views=5, recon=1)
+    s = torch.cuda.current_stream()
+    with lfdpr.Renderer(d, sc) as R:
+        m = S.model_matrix(6)
+        R.render(m, s)
+        st = R.stats(s)
+        b = R.buffers()
+        n = int(st.n_points)
+        ref_counts = lfdpr.device_to_numpy(b.counts, (sc.n_tris,), np.uint32)
+        ref_pts = lfdpr.device_to_numpy(b.points, (n, 4), np.uint32)[:, :2]
+        pts, counts, fc = _noalloc(d, sc, bufs, wh, m, n, s)
+        assert fc[0] == n and fc[1] == 0 and fc[3] == st.n_live_tris
+        assert np.array_equal(counts, ref_counts)
+        assert np.array_equal(pts[:n, :2], ref_pts)
 
 
 def test_noalloc_reports_overflow_without_writing(setup):
