@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--config", choices=["paper", "angular", "gauss", "gauss2x", "tiny", "pbr", "batch", "learned"],
                    default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--view-band", type=int, default=None,
+                   help="views per band of key clear, splat and resolve (0: all at once; default: the library's)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
     p.add_argument("--batch-tris", type=str, default="50000,2000000",
@@ -77,10 +79,11 @@ def workload(cfg):
                 WORKLOAD.replace("48 views", "96 views tent-reconstructed to 48 (+crosstalk 0.15)"))
     if cfg == "gauss2x":
         d = S.display_angular_ss()
-        return (replace(d, recon=2, view_w=2 * d.view_w, view_h=2 * d.view_h), S.scene_paper(),
+        return (replace(d, recon=2, view_w=2 * d.view_w, view_h=2 * d.view_h, ss_level=1), S.scene_paper(),
                 WORKLOAD.replace("48 views over 40 deg at 420x560", "96 views at 840x1120 (2x spatial and 2x "
-                                 "angular supersampling, random angles), Gaussian reconstruction (8 samples) to 48 "
-                                 "views over 40 deg at 420x560 (+crosstalk 0.15)"))
+                                 "angular supersampling, random angles), a mip level of each view at 420x560, "
+                                 "Gaussian reconstruction (8 samples) to 48 views over 40 deg at 420x560 "
+                                 "(+crosstalk 0.15)"))
     if cfg == "gauss":
         return (replace(S.display_angular_ss(), recon=2), S.scene_paper(),
                 WORKLOAD.replace("48 views", "96 views at random angles in their intervals, Gaussian "
@@ -427,13 +430,15 @@ def run_ours(args):
     R = lfdpr.Renderer(d, sc, max_points=(1 << 24) if args.config == "gauss2x" else 0, stream=stream,
                        shading=shading_of(args.config))
     R.set_stage_timing(True)
+    if args.view_band is not None:
+        lfdpr.lfdpr_set_view_band(R.disp, args.view_band)
     if d.recon in (2, 3):
         # Sec. 4's random angles and Gaussian samples (seeded; sigma = diameter / 4, in output
-        # pixels: view pixels times the spatial supersampling factor)
-        ss = 2.0 if args.config == "gauss2x" else 1.0
+        # pixels: with spatial supersampling the reconstruction reads the views' mip level
+        # whose texels are output pixels)
         rng = np.random.default_rng(2024)
         R.set_view_jitter(rng.random(d.n_render_views).astype(np.float32))
-        R.set_recon_samples((rng.normal(0.0, 1.0, (8, 3)) * [ss * 2.25 / 4, ss * 2.25 / 4, 0.5]).astype(np.float32))
+        R.set_recon_samples((rng.normal(0.0, 1.0, (8, 3)) * [2.25 / 4, 2.25 / 4, 0.5]).astype(np.float32))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
     frames = multigpu.rank_frames(rank, world, args.warmup + args.steps)
@@ -550,7 +555,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl, "l2": "flushed (512 MiB write) between timed steps",
-                       "points_per_frame": P, "rendered_views": d.n_render_views},
+                       "points_per_frame": P, "rendered_views": d.n_render_views,
+                       "view_band": args.view_band},
             "points_per_s": value * P,
             "point_view_splats_per_s": P * d.n_render_views / (splat_ms / 1000.0),
             "stage_ms": st_mean,
@@ -633,7 +639,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ms = []
+    ms, scene_ms = [], []
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(k & 255)
@@ -643,6 +649,7 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+        scene_ms.append(B.scene_ms())
     clk = clocks.stop()
     points = sum(B.stats(i, stream).n_points for i in range(n))
     total_ms = multigpu.max_over_ranks(sum(ms), device="cuda")
@@ -680,7 +687,13 @@ def run_batch(args):
                            "l2": "flushed (512 MiB write) between timed batches",
                            "rendered_views": sum(d.n_render_views for d in ds)},
                 "batch_ms_p50": pct(0.50), "batch_ms_p99": pct(0.99),
-                "scene_frame_latency_note": "every scene's frame completes with its batch",
+                "scene_latency_ms": {
+                    "p50": float(np.percentile(np.concatenate(scene_ms), 50)),
+                    "p99": float(np.percentile(np.concatenate(scene_ms), 99)),
+                    "per_scene_p50": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 50, axis=0)],
+                    "per_scene_p99": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 99, axis=0)],
+                    "what": "device time from the start of the batch's graph to the end of each scene's "
+                            "interleave (events inside the graph), over every scene and timed batch"},
                 "points_per_batch": points, "points_per_s": points * args.steps * world / (total_ms / 1000.0),
                 "sequential_frames_per_s": seq_rate, "speedup_vs_sequential": value / world / seq_rate,
                 "autotuned": {"branches": cfg.branches, "splat_blocks_per_sm": cfg.splat_blocks_per_sm,

@@ -189,6 +189,21 @@ lfdpr_status lfdpr_destroy_display(lfdpr_display *disp);
 lfdpr_status lfdpr_set_view_jitter(lfdpr_display *disp, const float *u, int32_t n);
 
 /*
+ * lfdpr_set_spatial_supersampling: 2x (level 1) or 4x (level 2) spatial
+ * supersampling (Sec. 4; Sec. 5.1 builds a mipmap of each light field view
+ * for it). The display's views are rendered at view_w x view_h, 2^level times
+ * the output resolution per axis; lfdpr_interleave first reduces every
+ * rendered view to mip level `level` (level times the 2 x 2 box
+ * (a + b + c + d + 2) >> 2 per channel, the textures' mip rounding) and
+ * interleaves those output-resolution views (with Gaussian reconstruction the
+ * sample offsets are then in output pixels). Level 0 (the default) turns it
+ * off. view_w and view_h must be multiples of 2^level; the level's views are
+ * allocated here (4 B per output pixel per rendered view). Errors: EINVAL,
+ * ENOMEM, ECUDA.
+ */
+lfdpr_status lfdpr_set_spatial_supersampling(lfdpr_display *disp, int32_t level);
+
+/*
  * lfdpr_set_recon_samples: the sample offsets of the Gaussian
  * reconstruction (recon 2, 3; Sec. 4 integrates its filters with a few
  * random samples; the caller draws them): samples f32 [n][3] (host, copied),
@@ -271,6 +286,17 @@ lfdpr_status lfdpr_set_stage_timing(lfdpr_display *disp, int32_t enable);
  * keys more slowly. Errors: EINVAL (null display, limit outside [1, 2^24]).
  */
 lfdpr_status lfdpr_set_splat_lane_limit(lfdpr_display *disp, uint32_t limit);
+
+/*
+ * lfdpr_set_view_band: order the depth test (Sec. 3.2, Sec. 5.1) by view
+ * band. With band = b > 0 and fewer than the rendered views, each frame
+ * clears, splats and resolves views [0, b), then [b, 2b), ..., so that a
+ * band's key buffers (8 B per pixel) can stay resident in L2 while they are
+ * hit, when all the views' keys would not fit; results are identical. 0 (the
+ * default) treats all views as one band. Errors: EINVAL (null display,
+ * band < 0).
+ */
+lfdpr_status lfdpr_set_view_band(lfdpr_display *disp, int32_t band);
 
 /* lfdpr_get_buffers: borrowed device pointers of the last frame (see lfdpr_buffers). */
 lfdpr_status lfdpr_get_buffers(lfdpr_display *disp, lfdpr_mesh *mesh, lfdpr_buffers *out);
@@ -466,6 +492,15 @@ lfdpr_status lfdpr_batch_autotune(lfdpr_batch *batch, const float *models, int32
  * NULL); *n is the number of candidates (0 before any autotune). */
 lfdpr_status lfdpr_batch_autotune_table(const lfdpr_batch *batch, lfdpr_batch_config *cfgs, float *ms,
                                         int32_t capacity, int32_t *n);
+
+/*
+ * lfdpr_batch_scene_ms: per-scene frame latency of the last replayed batch:
+ * ms[i] = device time from the start of the batch's graph to the end of
+ * scene i's interleave (events recorded inside the graph), for i < n
+ * (capacity >= n). Waits for the batch to finish. Errors: EINVAL (null, too
+ * small, no batch rendered yet), ECUDA.
+ */
+lfdpr_status lfdpr_batch_scene_ms(const lfdpr_batch *batch, float *ms, int32_t capacity);
 
 /* Device panel u8 [panel_h][panel_w][4] of scene i after lfdpr_render_batch
  * (borrowed; valid until the batch or its display is destroyed). */

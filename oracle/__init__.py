@@ -56,7 +56,8 @@ class OrcDisplay(C.Structure):
                 ("panel_w", C.c_int32), ("panel_h", C.c_int32),
                 ("lens_pitch_px", C.c_float), ("slant", C.c_float), ("phase_offset", C.c_float),
                 ("recon", C.c_int32), ("crosstalk", C.c_float),
-                ("jitter", C.c_void_p), ("samples", C.c_void_p), ("n_samples", C.c_int32)]
+                ("jitter", C.c_void_p), ("samples", C.c_void_p), ("n_samples", C.c_int32),
+                ("ss_level", C.c_int32)]
 
 
 def _disp(d, jitter=None, samples=None) -> OrcDisplay:
@@ -67,7 +68,7 @@ def _disp(d, jitter=None, samples=None) -> OrcDisplay:
     o = OrcDisplay(d.n_views, d.view_w, d.view_h, d.cone_deg, d.view_dist,
                    d.focal_w, d.focal_h, d.near_z, d.far_z, d.bias_h, d.bias_v,
                    d.panel_w, d.panel_h, d.lens_pitch_px, d.slant, d.phase_offset,
-                   d.recon, d.crosstalk, None, None, 0)
+                   d.recon, d.crosstalk, None, None, 0, getattr(d, "ss_level", 0))
     if jitter is not None:
         o._jitter = np.ascontiguousarray(jitter, np.float32)
         o.jitter = o._jitter.ctypes.data
@@ -108,6 +109,7 @@ def lib():
             L.orc_view_of_subpixel.restype = C.c_int
             L.orc_view_of_subpixel.argtypes = [P, C.c_int, C.c_int, C.c_int]
             L.orc_interleave.argtypes = [P, P, P]
+            L.orc_view_mip.argtypes = [P, C.c_int, C.c_int, C.c_int, P]
             L.orc_view_pos.restype = C.c_float
             L.orc_view_pos.argtypes = [P, C.c_int]
             L.orc_subpixel_phase.restype = C.c_float
@@ -400,6 +402,14 @@ def interleave(d, rendered: np.ndarray, jitter=None, samples=None) -> np.ndarray
     pan = np.zeros((d.panel_h, d.panel_w, 4), np.uint8)
     lib().orc_interleave(C.byref(dd), _p(np.ascontiguousarray(rendered, np.uint8)), _p(pan))
     return pan
+
+
+def view_mip(view: np.ndarray, level: int) -> np.ndarray:
+    """Mip level `level` of one RGBA8 view (h, w, 4)."""
+    h, w = view.shape[:2]
+    out = np.zeros((h >> level, w >> level, 4), np.uint8)
+    lib().orc_view_mip(_p(np.ascontiguousarray(view, np.uint8)), w, h, level, _p(out))
+    return out
 
 
 def display_views(d, rendered: np.ndarray) -> np.ndarray:

@@ -54,6 +54,7 @@ typedef struct {
     const float *jitter;    /* NULL, or per rendered view u in [0, 1]: its place in its interval */
     const float *samples;   /* recon 2, 3: n_samples x (dx, dy in view pixels, dphi in display views) */
     int32_t n_samples;
+    int32_t ss_level;       /* spatial supersampling: views rendered at 2^ss_level x the output size */
 } orc_display;
 
 /* Per-triangle record, written by orc_setup as ORC_TRI_FLOATS floats. */
@@ -1202,7 +1203,43 @@ float orc_gauss_value(const orc_display *d, const uint8_t *rendered, const float
 }
 
 /*
- * orc_interleave: the elemental image array. Panel subpixel (x, y, c) shows
+ * Mip level L of one rendered view (Sec. 5.1: with spatial supersampling a
+ * mipmap of each light field view is built): L times the 2 x 2 box of the
+ * level above, (a + b + c + d + 2) >> 2 per channel, as for the textures.
+ * W and H must be multiples of 2^L; out holds (W >> L) x (H >> L) RGBA8.
+ */
+void orc_view_mip(const uint8_t *view, int W, int H, int L, uint8_t *out) {
+    size_t n = (size_t)W * H * 4;
+    uint8_t *cur = (uint8_t *)malloc(n), *nxt = (uint8_t *)malloc(n);
+    memcpy(cur, view, n);
+    int w = W, h = H;
+    for (int l = 0; l < L; l++) {
+        int nw = w / 2, nh = h / 2;
+        for (int y = 0; y < nh; y++)
+            for (int x = 0; x < nw; x++)
+                for (int c = 0; c < 4; c++) {
+                    unsigned s = cur[((size_t)(2 * y) * w + 2 * x) * 4 + c] + cur[((size_t)(2 * y) * w + 2 * x + 1) * 4 + c] +
+                                 cur[((size_t)(2 * y + 1) * w + 2 * x) * 4 + c] +
+                                 cur[((size_t)(2 * y + 1) * w + 2 * x + 1) * 4 + c];
+                    nxt[((size_t)y * nw + x) * 4 + c] = (uint8_t)((s + 2) >> 2);
+                }
+        uint8_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        w = nw;
+        h = nh;
+    }
+    memcpy(out, cur, (size_t)w * h * 4);
+    free(cur);
+    free(nxt);
+}
+
+static void interleave_views(const orc_display *d, const uint8_t *rendered, uint8_t *panel);
+
+/*
+ * orc_interleave: the elemental image array. With spatial supersampling
+ * (ss_level L > 0) the views are first reduced to mip level L, whose texels
+ * are output pixels, and the interleave below reads those. Panel subpixel (x, y, c) shows
  * channel c of display view orc_view_of_subpixel(x, y, c) at the nearest view
  * texel (floor((x+1/2) W / W_p), floor((y+1/2) H / H_p)); alpha is 255. With
  * Gaussian reconstruction (recon 2 or 3) it shows orc_gauss_value at the
@@ -1210,6 +1247,24 @@ float orc_gauss_value(const orc_display *d, const uint8_t *rendered, const float
  * phi + 1 (wrapping over the N views) at weight x each.
  */
 void orc_interleave(const orc_display *d, const uint8_t *rendered, uint8_t *panel) {
+    if (d->ss_level > 0) {
+        int L = d->ss_level, nr = orc_n_render_views(d);
+        orc_display dl = *d;
+        dl.view_w = d->view_w >> L;
+        dl.view_h = d->view_h >> L;
+        dl.ss_level = 0;
+        size_t per = (size_t)dl.view_w * dl.view_h * 4;
+        uint8_t *lv = (uint8_t *)malloc(per * (size_t)nr);
+        for (int m = 0; m < nr; m++)
+            orc_view_mip(rendered + (size_t)m * d->view_w * d->view_h * 4, d->view_w, d->view_h, L, lv + per * m);
+        interleave_views(&dl, lv, panel);
+        free(lv);
+        return;
+    }
+    interleave_views(d, rendered, panel);
+}
+
+static void interleave_views(const orc_display *d, const uint8_t *rendered, uint8_t *panel) {
     int N = d->n_views, W = d->view_w, H = d->view_h, Wp = d->panel_w, Hp = d->panel_h;
     size_t npix = (size_t)W * H;
     if (d->recon == 2 || d->recon == 3) {

@@ -34,6 +34,8 @@ struct lfdpr_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool stale = true;               // capture again before the next replay
+    std::vector<cudaEvent_t> tev;    // timing: [0] the batch starts, [1 + i] scene i's panel is done
+    bool replayed = false;           // a graph with the timing events has been launched
     std::vector<lfdpr_batch_config> tried;   // the last autotune's candidates
     std::vector<float> tried_ms;             // and their mean ms per batch
 };
@@ -81,6 +83,8 @@ void free_batch(lfdpr_batch* b) {
     if (!b) return;
     drop_graph(b);
     drop_branches(b);
+    for (auto e : b->tev)
+        if (e) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->staged) cudaEventDestroy(b->staged);
     cudaFree(b->d_models);
@@ -94,6 +98,9 @@ lfdpr_status record_batch(lfdpr_batch* b) {
     const int K = b->cfg.branches;
     cudaStream_t s = b->cap;
     cudaEvent_t fork = b->ev[0], fork2 = b->ev[1];
+    // timing events as event-record nodes of the graph (a plain record during
+    // capture would only join streams)
+    CK(cudaEventRecordWithFlags(b->tev[0], s, cudaEventRecordExternal), "batch: start event");
     CK(cudaEventRecord(fork, s), "batch: fork");
     for (int j = 0; j < K; j++) CK(cudaStreamWaitEvent(b->br[j], fork, 0), "batch: branch wait");
     for (int i = 0; i < b->n; i++) {
@@ -113,11 +120,12 @@ lfdpr_status record_batch(lfdpr_batch* b) {
     for (int i = 0; i < b->n; i++) {
         const FrameArgs a = frame_args(b->disp[i], b->mesh[i]);
         CK(launch_resolve(a, b->br[i % K]), "launch k_resolve");
-        const lfdpr_display* d = b->disp[i];
+        lfdpr_display* d = b->disp[i];
         if ((d->desc.recon == 2 || d->desc.recon == 3) && d->n_samples == 0)
             return fail(LFDPR_EINVAL, "batch: scene %d needs lfdpr_set_recon_samples", i);
-        CK(launch_interleave(d->dc, d->views, d->d_pos, d->d_samples, d->n_samples, d->panel, b->br[i % K]),
-           "launch k_interleave");
+        const lfdpr_status sti = record_interleave(b->disp[i], d->panel, b->br[i % K]);
+        if (sti != LFDPR_OK) return sti;
+        CK(cudaEventRecordWithFlags(b->tev[1 + i], b->br[i % K], cudaEventRecordExternal), "batch: scene event");
     }
     for (int j = 0; j < K; j++) {
         CK(cudaEventRecord(b->ev[2 + K + j], b->br[j]), "batch: join");
@@ -213,6 +221,14 @@ lfdpr_status lfdpr_create_batch(lfdpr_display* const* displays, lfdpr_mesh* cons
         (e = cudaMalloc(&b->d_scenes, sizeof(SplatScene) * n)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_scenes, sc.data(), sizeof(SplatScene) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = [&] {
+            b->tev.assign(n + 1, nullptr);
+            for (auto& t : b->tev) {
+                const cudaError_t r = cudaEventCreate(&t);
+                if (r != cudaSuccess) return r;
+            }
+            return cudaSuccess;
+        }()) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "create_batch");
@@ -266,11 +282,12 @@ lfdpr_status lfdpr_render_batch(lfdpr_batch* b, const float* models, void* strea
         if (st != LFDPR_OK) return st;
     }
     CK(cudaGraphLaunch(b->exec, s), "render_batch: graph launch");
+    b->replayed = true;
     for (int i = 0; i < b->n; i++) {
         b->disp[i]->ev_frame = b->disp[i]->ev_interleave = false;
         // set-up, scan, emission, fetch, near-limit records (and the materials'
-        // fetch), resolve, interleave
-        b->disp[i]->launches += b->mesh[i]->n_tris ? (b->mesh[i]->mat_tex ? 8 : 7) : 2;
+        // fetch), resolve, (view mips,) interleave
+        b->disp[i]->launches += (b->mesh[i]->n_tris ? (b->mesh[i]->mat_tex ? 8 : 7) : 2) + (b->disp[i]->ss_level > 0);
     }
     b->disp[0]->launches += 1;
     return LFDPR_OK;
@@ -341,6 +358,18 @@ lfdpr_status lfdpr_batch_autotune_table(const lfdpr_batch* batch, lfdpr_batch_co
     for (int32_t k = 0; k < *n && k < capacity; k++) {
         if (cfgs) cfgs[k] = batch->tried[k];
         if (ms) ms[k] = batch->tried_ms[k];
+    }
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_batch_scene_ms(const lfdpr_batch* batch, float* ms, int32_t capacity) {
+    g_err[0] = 0;
+    if (!batch || !ms) return fail(LFDPR_EINVAL, "batch_scene_ms: null argument");
+    if (capacity < batch->n) return fail(LFDPR_EINVAL, "batch_scene_ms: capacity %d < %d scenes", capacity, batch->n);
+    if (!batch->replayed) return fail(LFDPR_EINVAL, "batch_scene_ms: no batch rendered yet");
+    for (int i = 0; i < batch->n; i++) {
+        CK(cudaEventSynchronize(batch->tev[1 + i]), "batch_scene_ms: synchronize");
+        CK(cudaEventElapsedTime(&ms[i], batch->tev[0], batch->tev[1 + i]), "batch_scene_ms: elapsed");
     }
     return LFDPR_OK;
 }

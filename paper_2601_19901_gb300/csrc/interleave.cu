@@ -269,6 +269,83 @@ __global__ void __launch_bounds__(256) k_interleave_gauss(DispConst c, const uin
 
 }  // namespace
 
+namespace {
+
+// One 2 x 2 box of RGBA8 texels: (a + b + c + d + 2) >> 2 per channel.
+__device__ __forceinline__ uint32_t box4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    uint32_t o = 0u;
+#pragma unroll
+    for (int ch = 0; ch < 4; ch++) {
+        const uint32_t s = ((a >> (8 * ch)) & 255u) + ((b >> (8 * ch)) & 255u) + ((c >> (8 * ch)) & 255u) +
+                           ((d >> (8 * ch)) & 255u);
+        o |= ((s + 2u) >> 2) << (8 * ch);
+    }
+    return o;
+}
+
+// Mip level L (1 or 2) of every rendered view (Sec. 5.1: with spatial
+// supersampling a mipmap of each view is built): L times the 2 x 2 box of the
+// level above, with the texture mips' rounding. One thread per level-L texel
+// reads its 2^L x 2^L block of level-0 texels with vector loads (W and H are
+// multiples of 2^L) and reduces it level by level.
+template <int L>
+__global__ void __launch_bounds__(256) k_view_mip(const uint8_t* __restrict__ src, uint32_t W, uint32_t H,
+                                                  uint32_t nr, uint8_t* __restrict__ dst) {
+    constexpr int K = 1 << L;
+    const uint32_t wl = W >> L, hl = H >> L;
+    const uint64_t total = (uint64_t)wl * hl * nr;
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = uint32_t(t % wl);
+        const uint64_t r = t / wl;
+        const uint32_t y = uint32_t(r % hl), v = uint32_t(r / hl);
+        const uint32_t* base = s32 + (uint64_t)v * W * H + (uint64_t)(y * K) * W + x * K;
+        uint32_t px[K][K];
+#pragma unroll
+        for (int dy = 0; dy < K; dy++) {
+            if constexpr (K == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2*>(base + (uint64_t)dy * W));
+                px[dy][0] = q.x;
+                px[dy][1] = q.y;
+            } else {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(base + (uint64_t)dy * W));
+                px[dy][0] = q.x;
+                px[dy][1] = q.y;
+                px[dy][2] = q.z;
+                px[dy][3] = q.w;
+            }
+        }
+        uint32_t out;
+        if constexpr (K == 2) {
+            out = box4(px[0][0], px[0][1], px[1][0], px[1][1]);
+        } else {
+            const uint32_t a = box4(px[0][0], px[0][1], px[1][0], px[1][1]);
+            const uint32_t b = box4(px[0][2], px[0][3], px[1][2], px[1][3]);
+            const uint32_t c = box4(px[2][0], px[2][1], px[3][0], px[3][1]);
+            const uint32_t e = box4(px[2][2], px[2][3], px[3][2], px[3][3]);
+            out = box4(a, b, c, e);
+        }
+        d32[(uint64_t)v * wl * hl + (uint64_t)y * wl + x] = out;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_view_mip(const uint8_t* views, int W, int H, int nr, int level, uint8_t* out, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (level == 1)
+        k_view_mip<1><<<sms * 8, 256, 0, s>>>(views, uint32_t(W), uint32_t(H), uint32_t(nr), out);
+    else if (level == 2)
+        k_view_mip<2><<<sms * 8, 256, 0, s>>>(views, uint32_t(W), uint32_t(H), uint32_t(nr), out);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const float* pos, const float* samples,
                               int n_samples, uint8_t* panel, cudaStream_t s) {
     int dev = 0, sms = 0, smem_max = 0;

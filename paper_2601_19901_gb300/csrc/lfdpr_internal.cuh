@@ -241,6 +241,7 @@ struct FrameArgs {
     Counters* ctr;
     int sm_count;
     uint32_t splat_lane_limit;       // candidates per lane above which a splat unit is walked lane by lane
+    int view_lo, view_hi;            // the rendered views [view_lo, view_hi) the splat and resolve cover
 };
 // The default splat_lane_limit: with every lane below 2^24 candidates a
 // unit's candidate numbers stay below 2^32.
@@ -275,6 +276,8 @@ cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s);
 // read only for Gaussian reconstruction (recon 2, 3).
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const float* pos, const float* samples,
                               int n_samples, uint8_t* panel, cudaStream_t s);
+// Mip level `level` (1 or 2) of nr views of W x H RGBA8 into out.
+cudaError_t launch_view_mip(const uint8_t* views, int W, int H, int nr, int level, uint8_t* out, cudaStream_t s);
 cudaError_t launch_mip_level(const uint8_t* src, uint32_t sw, uint32_t sh, uint8_t* dst,
                              uint32_t dw, uint32_t dh, cudaStream_t s);
 // mode 0: random global, 1: shared memory, 2: warp-coherent global

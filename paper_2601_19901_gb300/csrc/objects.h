@@ -34,6 +34,8 @@ struct lfdpr_display {
     uint64_t* keys = nullptr;
     uint8_t* views = nullptr;
     uint8_t* panel = nullptr;      // device scratch for host-memory panels
+    int ss_level = 0;              // spatial supersampling: the interleave reads this mip level of the views
+    uint8_t* views_mip = nullptr;  // that level of every rendered view
     lfdpr::Counters* ctr = nullptr;
     int n_meshes = 0;
     int64_t launches = 0;
@@ -43,6 +45,9 @@ struct lfdpr_display {
     bool ev_interleave = false;   // the interleave's events were recorded
     int shading = LFDPR_SHADING_UNLIT;
     uint32_t splat_lane_limit = lfdpr::kSplatLaneLimit;
+    int view_band = 0;            // views per band of key clear, splat and resolve (0: all at once)
+    std::vector<cudaEvent_t> band_ev;   // per band: before the clear, after it, after the splat, after the resolve
+    int bands_timed = 0;          // bands of the last frame whose events were recorded
     lfdpr::Shading sh{};          // light (unit direction), radiance, ambient
 };
 
@@ -71,11 +76,14 @@ namespace lfdpr {
 // Set the thread's last-error text and return s.
 lfdpr_status fail(lfdpr_status s, const char* fmt, ...);
 lfdpr_status cuda_fail(cudaError_t e, const char* what);
+// The interleave of the display's last views on stream s into `panel`:
+// with spatial supersampling, mip level ss_level of every view first.
+lfdpr_status record_interleave(lfdpr_display* disp, uint8_t* panel, cudaStream_t s);
 // Kernel arguments of one frame of `mesh` on `disp` (model left unset).
 FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh);
 // The frame up to the splat on stream s: counters reset, set-up, scan,
-// emission, fetch (with the near-limit records), key clear; stage events 0-5
-// recorded if marks.
+// emission, fetch (with the near-limit records), key clear (unless the
+// views are cleared band by band); stage events 0-5 recorded if marks.
 lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
-                                bool marks);
+                                bool marks, bool clear_keys = true);
 }  // namespace lfdpr

@@ -3,6 +3,7 @@
 // Host arithmetic that feeds the kernels' bit-exact steps (eye positions,
 // pixel footprints) is done in double and rounded once to binary32; this file
 // is compiled with -ffp-contract=off so no host multiply-add is fused.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,11 +64,13 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.ctr = disp->ctr;
     a.sm_count = disp->sm_count;
     a.splat_lane_limit = disp->splat_lane_limit;
+    a.view_lo = 0;
+    a.view_hi = disp->dc.nr;
     return a;
 }
 
 lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
-                                bool marks) {
+                                bool marks, bool clear_keys) {
     auto mk = [&](int k) {
         if (marks) cudaEventRecord(disp->ev[k], s);
     };
@@ -97,9 +100,26 @@ lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const Fra
         for (int k = 1; k <= 3; k++) mk(k);
     }
     mk(4);
-    CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
+    if (clear_keys) CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
     mk(5);
 #undef CKF
+    return LFDPR_OK;
+}
+
+lfdpr_status record_interleave(lfdpr_display* disp, uint8_t* panel, cudaStream_t s) {
+    DispConst dc = disp->dc;
+    const uint8_t* views = disp->views;
+    if (disp->ss_level > 0) {
+        const cudaError_t e = launch_view_mip(disp->views, dc.W, dc.H, dc.nr, disp->ss_level, disp->views_mip, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launch k_view_mip");
+        disp->launches += 1;
+        dc.W >>= disp->ss_level;
+        dc.H >>= disp->ss_level;
+        views = disp->views_mip;
+    }
+    const cudaError_t e = launch_interleave(dc, views, disp->d_pos, disp->d_samples, disp->n_samples, panel, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_interleave");
+    disp->launches += 1;
     return LFDPR_OK;
 }
 }  // namespace lfdpr
@@ -136,6 +156,8 @@ void free_display(lfdpr_display* d) {
     if (!d) return;
     for (auto& e : d->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : d->band_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(d->d_ex);
     cudaFree(d->d_pos);
     cudaFree(d->d_samples);
@@ -147,6 +169,7 @@ void free_display(lfdpr_display* d) {
     cudaFree(d->keys);
     cudaFree(d->views);
     cudaFree(d->panel);
+    cudaFree(d->views_mip);
     cudaFree(d->ctr);
     delete d;
 }
@@ -639,16 +662,54 @@ lfdpr_status lfdpr_render_frame(lfdpr_display* disp, lfdpr_mesh* mesh, const flo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FrameArgs a = frame_args(disp, mesh);
     for (int k = 0; k < 12; k++) a.model[k] = model[k];
-    const lfdpr_status st = record_frame_front(disp, mesh, a, s, disp->timing);
+    const int nr = disp->dc.nr;
+    const int band = disp->view_band > 0 && disp->view_band < nr ? disp->view_band : nr;
+    const lfdpr_status st = record_frame_front(disp, mesh, a, s, disp->timing, band == nr);
     if (st != LFDPR_OK) return st;
-    if (mesh->n_tris) {
-        CK(launch_splat(a, s), "launch k_splat");
+    disp->bands_timed = 0;
+    if (band == nr) {
+        if (mesh->n_tris) {
+            CK(launch_splat(a, s), "launch k_splat");
+            disp->launches += 1;
+        }
+        mark(disp, 6, s);
+        CK(launch_resolve(a, s), "launch k_resolve");
         disp->launches += 1;
+        mark(disp, 7, s);
+    } else {
+        // band by band: each band's keys are cleared, hit by the splat and
+        // read by the resolve while they can stay in L2
+        const int nb = (nr + band - 1) / band;
+        if (disp->timing && int(disp->band_ev.size()) < 4 * nb) {
+            const size_t have = disp->band_ev.size();
+            disp->band_ev.resize(4 * nb, nullptr);
+            for (size_t k = have; k < disp->band_ev.size(); k++)
+                CK(cudaEventCreate(&disp->band_ev[k]), "cudaEventCreate");
+        }
+        const uint64_t vpix = uint64_t(disp->dc.W) * disp->dc.H;
+        for (int b = 0; b < nb; b++) {
+            a.view_lo = b * band;
+            a.view_hi = std::min(nr, a.view_lo + band);
+            auto bm = [&](int k) {
+                if (disp->timing) cudaEventRecord(disp->band_ev[4 * b + k], s);
+            };
+            bm(0);
+            CK(cudaMemsetAsync(disp->keys + vpix * a.view_lo, 0xff, 8u * vpix * (a.view_hi - a.view_lo), s),
+               "clear keys");
+            bm(1);
+            if (mesh->n_tris) {
+                CK(launch_splat(a, s), "launch k_splat");
+                disp->launches += 1;
+            }
+            bm(2);
+            CK(launch_resolve(a, s), "launch k_resolve");
+            disp->launches += 1;
+            bm(3);
+        }
+        mark(disp, 6, s);
+        mark(disp, 7, s);
+        disp->bands_timed = disp->timing ? nb : 0;
     }
-    mark(disp, 6, s);
-    CK(launch_resolve(a, s), "launch k_resolve");
-    disp->launches += 1;
-    mark(disp, 7, s);
     disp->ev_frame = disp->timing;
     return LFDPR_OK;
 }
@@ -667,9 +728,8 @@ lfdpr_status lfdpr_interleave(lfdpr_display* disp, uint8_t* panel_rgba8, void* s
     mark(disp, LFDPR_N_STAGES, s);
     if ((disp->desc.recon == 2 || disp->desc.recon == 3) && disp->n_samples == 0)
         return fail(LFDPR_EINVAL, "interleave: Gaussian reconstruction needs lfdpr_set_recon_samples");
-    CK(launch_interleave(disp->dc, disp->views, disp->d_pos, disp->d_samples, disp->n_samples, dst, s),
-       "launch k_interleave");
-    disp->launches += 1;
+    const lfdpr_status st = record_interleave(disp, dst, s);
+    if (st != LFDPR_OK) return st;
     mark(disp, LFDPR_N_STAGES + 1, s);
     disp->ev_interleave = disp->timing;
     if (!on_device) {
@@ -699,6 +759,17 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display* disp, void* stream, lfdpr_stats* o
         if (disp->ev_frame)
             for (int k = 0; k < LFDPR_STAGE_INTERLEAVE; k++)
                 CK(cudaEventElapsedTime(&out->stage_ms[k], disp->ev[k], disp->ev[k + 1]), "stage time");
+        if (disp->ev_frame && disp->bands_timed > 0) {
+            // banded frame: clear, splat and resolve summed over the bands
+            for (int k = 0; k < 3; k++) out->stage_ms[LFDPR_STAGE_CLEAR + k] = 0.0f;
+            for (int b = 0; b < disp->bands_timed; b++)
+                for (int k = 0; k < 3; k++) {
+                    float ms = 0.0f;
+                    CK(cudaEventElapsedTime(&ms, disp->band_ev[4 * b + k], disp->band_ev[4 * b + k + 1]),
+                       "band stage time");
+                    out->stage_ms[LFDPR_STAGE_CLEAR + k] += ms;
+                }
+        }
         if (disp->ev_interleave)
             CK(cudaEventElapsedTime(&out->stage_ms[LFDPR_STAGE_INTERLEAVE], disp->ev[LFDPR_N_STAGES],
                                     disp->ev[LFDPR_N_STAGES + 1]),
@@ -707,6 +778,36 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display* disp, void* stream, lfdpr_stats* o
     if (c.overflow)
         return fail(LFDPR_EOVERFLOW, "frame needed %u points, capacity %u", c.n_points, disp->max_points);
     if (c.cell_overflow) return fail(LFDPR_EOVERFLOW, "a triangle needed more than 65535 lattice cells per axis");
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_spatial_supersampling(lfdpr_display* disp, int32_t level) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "set_spatial_supersampling: null display");
+    if (level < 0 || level > 2) return fail(LFDPR_EINVAL, "set_spatial_supersampling: level %d outside 0-2", level);
+    const int k = 1 << level;
+    if (disp->dc.W % k || disp->dc.H % k)
+        return fail(LFDPR_EINVAL, "set_spatial_supersampling: views %dx%d not divisible by %d", disp->dc.W, disp->dc.H,
+                    k);
+    if (level > 0) {
+        const uint64_t bytes = 4u * uint64_t(disp->dc.W >> level) * uint64_t(disp->dc.H >> level) * disp->dc.nr;
+        uint8_t* p = nullptr;
+        CK(cudaMalloc(&p, bytes), "set_spatial_supersampling: view mip buffer");
+        cudaFree(disp->views_mip);
+        disp->views_mip = p;
+    } else {
+        cudaFree(disp->views_mip);
+        disp->views_mip = nullptr;
+    }
+    disp->ss_level = level;
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_set_view_band(lfdpr_display* disp, int32_t band) {
+    g_err[0] = 0;
+    if (!disp) return fail(LFDPR_EINVAL, "set_view_band: null display");
+    if (band < 0) return fail(LFDPR_EINVAL, "set_view_band: band %d < 0", band);
+    disp->view_band = band;
     return LFDPR_OK;
 }
 

@@ -137,6 +137,8 @@ struct OneScene {
     }
     __device__ __forceinline__ Counters* ctr(int) const { return a.ctr; }
     __device__ __forceinline__ uint32_t lane_limit() const { return a.splat_lane_limit; }
+    __device__ __forceinline__ int view_lo(int) const { return a.view_lo; }
+    __device__ __forceinline__ int view_hi(int) const { return a.view_hi; }
 };
 
 struct ManyScenes {
@@ -167,6 +169,8 @@ struct ManyScenes {
     }
     __device__ __forceinline__ Counters* ctr(int q) const { return scenes[q].ctr; }
     __device__ __forceinline__ uint32_t lane_limit() const { return kSplatLaneLimit; }
+    __device__ __forceinline__ int view_lo(int) const { return 0; }
+    __device__ __forceinline__ int view_hi(int q) const { return s_dc[q].nr; }
 };
 
 // Candidate rr of segment e: its pixel, the test, and the depth-test atomic.
@@ -225,7 +229,8 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
             const uint32_t kn = k0 + 2u * P * n_warps + uint32_t(lane);   // the next unit's records
             if (lane < 2 * P && kn < n) prefetch_l2(work + kn);
         }
-        for (int g0 = 0; g0 < c.nr; g0 += 16 * S) {
+        const int vlo = src.view_lo(sc), vhi = src.view_hi(sc);
+        for (int g0 = vlo; g0 < vhi; g0 += 16 * S) {
             __syncwarp();   // the previous passes are done with sm
             uint32_t pk[P][S], ny[P];
             float ex[S];   // the lane's views' eyes, the same for every pair
@@ -238,7 +243,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                 const float4 l0 = __ldg(&wr->L0), l1 = __ldg(&wr->L1);
                 const uint4 meta = __ldg(&wr->meta);
                 ny[p] = k < n ? (meta.x >> 14) & 0x7fffu : 0u;
-                if (g0 == 0 && sub == 0) {   // the point's test constants
+                if (g0 == vlo && sub == 0) {   // the point's test constants
                     const TriRec* r = src.rec(sc) + meta.z;
                     const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
                     const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
@@ -254,9 +259,9 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) {
                     const int v = g0 + 16 * sl + sub;
-                    if (p == 0) ex[sl] = v < c.nr ? src.eye(sc, v) : 0.0f;
+                    if (p == 0) ex[sl] = v < vhi ? src.eye(sc, v) : 0.0f;
                     pk[p][sl] = 0u;
-                    if (v < c.nr) {
+                    if (v < vhi) {
                         const float Ex = ex[sl];
                         const float lo = fmaxf(fmaf(l0.y, Ex, l0.x), fmaf(l1.y, Ex, l1.x));
                         const float hi = fminf(fmaf(l0.w, Ex, l0.z), fmaf(l1.w, Ex, l1.z));
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
     const DispConst& c = a.dc;
     const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
     const uint32_t p0 = blockIdx.x * (256u * kResolvePix) + threadIdx.x;
-    const int v = blockIdx.y;
+    const int v = a.view_lo + int(blockIdx.y);
     const uint64_t o0 = (uint64_t)v * npix;
     unsigned long long key[kResolvePix];
 #pragma unroll
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
     const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
     const uint32_t px = blockIdx.x * blockDim.x + threadIdx.x;
     if (px >= npix) return;
-    const int v = blockIdx.y;
+    const int v = a.view_lo + int(blockIdx.y);
     const uint64_t o = (uint64_t)v * npix + px;
     const unsigned long long key = a.keys[o];
     uint32_t out = 0u;
@@ -586,9 +591,10 @@ cudaError_t splat_batch(const SplatScene* scenes, int n_scenes, int grid, cudaSt
 }  // namespace
 
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
-    // the fewest view slots per lane that hold every rendered view in one
-    // group (more than 128 views take several groups of 128)
-    const int nr = a.dc.nr, grid = a.sm_count * 16;
+    // the fewest view slots per lane that hold every view of the range
+    // [view_lo, view_hi) in one group (more than 128 views take several
+    // groups of 128)
+    const int nr = a.view_hi - a.view_lo, grid = a.sm_count * 16;
     if (nr <= 16) return splat_one<1>(a, grid, s);
     if (nr <= 32) return splat_one<2>(a, grid, s);
     if (nr <= 48) return splat_one<3>(a, grid, s);
@@ -614,11 +620,12 @@ cudaError_t launch_splat_batch(const SplatScene* scenes, int n_scenes, int slots
 
 cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {
     const uint32_t npix = uint32_t(a.dc.W) * uint32_t(a.dc.H);
-    const dim3 grid((npix + 255u) / 256u, uint32_t(a.dc.nr));
+    const uint32_t nv = uint32_t(a.view_hi - a.view_lo);
+    const dim3 grid((npix + 255u) / 256u, nv);
     if (a.pbr)
         k_resolve_pbr<<<grid, 256, 0, s>>>(a);
     else
-        k_resolve<<<dim3((npix + 256u * kResolvePix - 1u) / (256u * kResolvePix), uint32_t(a.dc.nr)), 256, 0, s>>>(a);
+        k_resolve<<<dim3((npix + 256u * kResolvePix - 1u) / (256u * kResolvePix), nv), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

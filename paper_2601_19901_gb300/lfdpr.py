@@ -34,7 +34,8 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_upload_mesh_materials", "lfdpr_set_shading",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
-           "lfdpr_batch_autotune_table",
+           "lfdpr_batch_autotune_table", "lfdpr_batch_scene_ms", "lfdpr_set_spatial_supersampling",
+           "lfdpr_set_view_band",
            "lfdpr_recon_weight_count", "lfdpr_recon_bias_count", "lfdpr_create_recon",
            "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_recon_status",
            "lfdpr_conv3x3_bf16"]
@@ -115,6 +116,8 @@ def lib() -> C.CDLL:
         L.lfdpr_set_splat_lane_limit.argtypes = [P, C.c_uint32]
         L.lfdpr_set_view_jitter.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_recon_samples.argtypes = [P, P, C.c_int32]
+        L.lfdpr_set_spatial_supersampling.argtypes = [P, C.c_int32]
+        L.lfdpr_set_view_band.argtypes = [P, C.c_int32]
         L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
                                                   P, C.c_uint32, P, C.c_uint32, P, P, P]
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
@@ -134,6 +137,7 @@ def lib() -> C.CDLL:
                                            C.POINTER(C.c_float)]
         L.lfdpr_batch_panel.argtypes = [P, C.c_int32, C.POINTER(C.c_void_p)]
         L.lfdpr_batch_autotune_table.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_int32)]
+        L.lfdpr_batch_scene_ms.argtypes = [P, P, C.c_int32]
         L.lfdpr_recon_weight_count.argtypes = [C.c_int32]
         L.lfdpr_recon_bias_count.argtypes = [C.c_int32]
         L.lfdpr_create_recon.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, C.c_int64, P, C.c_int64,
@@ -190,6 +194,28 @@ def lfdpr_create_display(desc: DisplayDesc) -> int:
     h = C.c_void_p()
     _check(lib().lfdpr_create_display(C.byref(desc), C.byref(h)))
     return h.value
+
+
+def lfdpr_set_spatial_supersampling(disp: int, level: int):
+    _check(lib().lfdpr_set_spatial_supersampling(disp, int(level)))
+
+
+def lfdpr_set_view_band(disp: int, band: int):
+    _check(lib().lfdpr_set_view_band(disp, int(band)))
+
+
+def create_display(display, max_points: int = 0) -> int:
+    """lfdpr_create_display from a scenes.Display, with its spatial
+    supersampling level set."""
+    h = lfdpr_create_display(desc_of(display, max_points))
+    level = getattr(display, "ss_level", 0)
+    if level:
+        try:
+            lfdpr_set_spatial_supersampling(h, level)
+        except Exception:
+            lfdpr_destroy_display(h)
+            raise
+    return h
 
 
 def lfdpr_destroy_display(disp: int):
@@ -397,6 +423,13 @@ def lfdpr_batch_autotune_table(batch: int):
     return [cfgs[k].as_tuple() + (ms[k],) for k in range(n.value)]
 
 
+def lfdpr_batch_scene_ms(batch: int, n: int) -> np.ndarray:
+    """Per-scene frame latency (ms) of the last replayed batch."""
+    out = np.zeros(n, np.float32)
+    _check(lib().lfdpr_batch_scene_ms(batch, _ptr(out), n))
+    return out
+
+
 def lfdpr_batch_panel(batch: int, i: int) -> int:
     h = C.c_void_p()
     _check(lib().lfdpr_batch_panel(batch, i, C.byref(h)))
@@ -456,7 +489,7 @@ class Renderer:
         textures as a texture set); `shading` (e.g. scenes.Shading) shades it
         physically."""
         self.display = display
-        self.disp = lfdpr_create_display(desc_of(display, max_points))
+        self.disp = create_display(display, max_points)
         self.mesh = None
         self.texset = None
         try:
@@ -556,7 +589,7 @@ class Batch:
         try:
             for k, (d, sc) in enumerate(zip(displays, scenes)):
                 mp = max_points[k] if max_points is not None else 0
-                self.disps.append(lfdpr_create_display(desc_of(d, mp)))
+                self.disps.append(create_display(d, mp))
                 self.meshes.append(lfdpr_upload_mesh_textured(self.disps[-1], sc.xyz, sc.uv, sc.idx,
                                                               sc.tri_tex, tex_set.handle, stream))
             self.batch = lfdpr_create_batch(self.disps, self.meshes)
@@ -581,6 +614,9 @@ class Batch:
 
     def panel(self, i: int) -> int:
         return lfdpr_batch_panel(self.batch, i)
+
+    def scene_ms(self) -> np.ndarray:
+        return lfdpr_batch_scene_ms(self.batch, len(self.disps))
 
     def stats(self, i: int, stream=None) -> Stats:
         return lfdpr_frame_stats(self.disps[i], stream)

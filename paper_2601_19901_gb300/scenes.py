@@ -51,6 +51,9 @@ class Display:
     # 2*n_views, Gaussian reconstruction; 3: render n_views, Gaussian reconstruction
     recon: int = 0
     crosstalk: float = 0.0  # weight of each +-1 neighbour view before interleave
+    # spatial supersampling: the views are rendered at 2^ss_level times the
+    # output resolution and the interleave reads mip level ss_level of each
+    ss_level: int = 0
 
     @property
     def n_render_views(self) -> int:

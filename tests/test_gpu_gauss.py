@@ -86,3 +86,48 @@ def test_gaussian_arguments_are_checked(env):
                 R.set_view_jitter(bad)
             assert e.value.status == lfdpr.EINVAL
         torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# 2x and 4x spatial supersampling: views at 2^L times the output size, the
+# interleave reading mip level L of each (Sec. 5.1 builds a mipmap of each view)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("recon,level,xtalk", [(0, 1, 0.0), (1, 1, 0.15), (2, 1, 0.15), (3, 2, 0.0), (0, 2, 0.15)])
+def test_spatial_supersampling_panel_matches_oracle(env, recon, level, xtalk):
+    sc = env
+    base = S.display_tiny()
+    k = 1 << level
+    d = replace(base, view_w=k * base.view_w, view_h=k * base.view_h, recon=recon, crosstalk=xtalk,
+                ss_level=level)
+    m = S.model_matrix(6)
+    jit = smp = None
+    with lfdpr.Renderer(d, sc) as R:
+        if recon in (2, 3):
+            jit = np.random.default_rng(level).random(d.n_render_views).astype(np.float32)
+            smp = (np.random.default_rng(level + 3).normal(0.0, 1.0, (8, 3)) * SIGMA).astype(np.float32)
+            R.set_view_jitter(jit)
+            R.set_recon_samples(smp)
+        g = gpu_frame(d, sc, m, renderer=R)
+    # the render at the supersampled size (two views against the oracle)
+    vl = [0, d.n_render_views - 1]
+    o = O.render(d, sc, m, views=vl, panel=False, jitter=jit)
+    check_sampling(g, o, "ss %d" % level)
+    check_views(g, o, views=vl, msg="ss %d" % level)
+    # the view mips and the interleave of the GPU's own views: bit-exact
+    assert np.array_equal(g.panel, O.interleave(d, g.views, jitter=jit, samples=smp))
+
+
+def test_spatial_supersampling_arguments_are_checked(env):
+    sc = env
+    d = replace(S.display_tiny(), view_w=130, view_h=128)
+    with lfdpr.Renderer(d, sc) as R:
+        for bad in (-1, 3):
+            with pytest.raises(lfdpr.LfdprError) as e:
+                lfdpr.lfdpr_set_spatial_supersampling(R.disp, bad)
+            assert e.value.status == lfdpr.EINVAL
+        lfdpr.lfdpr_set_spatial_supersampling(R.disp, 1)      # 130 x 128: divisible by 2
+        with pytest.raises(lfdpr.LfdprError) as e:
+            lfdpr.lfdpr_set_spatial_supersampling(R.disp, 2)  # 130 is not divisible by 4
+        assert e.value.status == lfdpr.EINVAL
+        lfdpr.lfdpr_set_spatial_supersampling(R.disp, 0)

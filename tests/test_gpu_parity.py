@@ -188,3 +188,23 @@ def test_nonfinite_model_rejected():
         with pytest.raises(lfdpr.LfdprError) as e:
             R.render(m)
         assert e.value.status == lfdpr.EINVAL
+
+
+@pytest.mark.parametrize("band", [5, 16])
+def test_view_bands_give_the_same_frame(band):
+    """Clearing, splatting and resolving the views band by band leaves every
+    key, view and the panel as rendering all views at once."""
+    d = mini_paper_display(ss=True)          # 96 rendered views: 20 bands of 5 (the last of 1), or 6 of 16
+    sc = mini_paper_scene(seed=7)
+    m = S.model_matrix(4)
+    g0 = gpu_frame(d, sc, m)
+    with lfdpr.Renderer(d, sc) as R:
+        lfdpr.lfdpr_set_view_band(R.disp, band)
+        R.set_stage_timing(True)
+        g1 = gpu_frame(d, sc, m, renderer=R)
+        st = R.stats()
+    assert np.array_equal(g0.keys, g1.keys)
+    assert np.array_equal(g0.views, g1.views)
+    assert np.array_equal(g0.panel, g1.panel)
+    assert g1.stats.n_splat_writes == g0.stats.n_splat_writes
+    assert st.stage_ms[lfdpr.STAGES.index("splat")] > 0.0 and st.stage_ms[lfdpr.STAGES.index("resolve")] > 0.0

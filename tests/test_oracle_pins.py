@@ -938,3 +938,44 @@ def test_gauss_takes_the_nearest_view_by_brute_force():
                     dist = np.abs(pos - a)
                     m = int(np.flatnonzero(dist == dist.min())[-1])
                     assert pan[y, x, c] == 11 * m, (dphi, x, y, c)
+
+
+# ---------------------------------------------------------------------------
+# Spatial supersampling (Sec. 4; Sec. 5.1 builds a mipmap of each view)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("recon,level", [(0, 1), (1, 1), (3, 1), (2, 1), (0, 2), (3, 2)])
+def test_spatial_ss_of_replicated_views_is_the_plain_interleave(recon, level):
+    """Views rendered at 2^L times the output size whose pixels are L-fold
+    replicas of an output-size view: their mip level L is that view, so the
+    panel equals the plain interleave of it (with the same Gaussian samples,
+    in output pixels, and crosstalk)."""
+    d0 = replace(_gauss_display(recon, crosstalk=0.15), panel_w=160, panel_h=96)
+    k = 1 << level
+    d1 = replace(d0, view_w=k * d0.view_w, view_h=k * d0.view_h, ss_level=level)
+    v = _random_views(d0, seed=9 + level)
+    vk = np.repeat(np.repeat(v, k, axis=1), k, axis=2)
+    samples = None
+    if recon in (2, 3):
+        samples = np.random.default_rng(5).normal(0.0, [0.5625, 0.5625, 0.5], (8, 3)).astype(np.float32)
+    assert np.array_equal(O.interleave(d1, vk, samples=samples), O.interleave(d0, v, samples=samples))
+
+
+def test_spatial_ss_of_checkerboard_views_is_mid_grey():
+    d0 = replace(_gauss_display(0), panel_w=128, panel_h=64)
+    d1 = replace(d0, view_w=2 * d0.view_w, view_h=2 * d0.view_h, ss_level=1)
+    yy, xx = np.mgrid[0:d1.view_h, 0:d1.view_w]
+    board = np.where(((xx + yy) & 1)[..., None] == 1, 255, 0).astype(np.uint8)
+    v = np.broadcast_to(board, (d1.n_render_views, d1.view_h, d1.view_w, 4)).copy()
+    pan = O.interleave(d1, v)
+    # (0 + 255 + 0 + 255 + 2) >> 2 = 128 in every channel
+    assert np.all(pan[..., :3] == 128) and np.all(pan[..., 3] == 255)
+    # level 2 of the same boards: the mid-grey of mid-greys
+    assert np.all(O.view_mip(v[0], 2) == 128)
+
+
+def test_view_mip_of_a_constant_view_is_constant():
+    v = np.full((64, 48, 4), 201, np.uint8)
+    for level in (1, 2, 3):
+        m = O.view_mip(v, level)
+        assert m.shape == (64 >> level, 48 >> level, 4) and np.all(m == 201)
