@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--view-band", type=int, default=None,
                    help="views per band of key clear, splat and resolve (0: all at once; default: the library's)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the 96-view and learned-path measurements after the main timed region")
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
     p.add_argument("--batch-tris", type=str, default="50000,2000000",
                    help="--config batch: triangle-count range per scene (log-uniform)")
@@ -585,6 +587,8 @@ def run_ours(args):
                                 "tiny_frame_seconds": t_tiny,
                                 "tiny_frame": "2,048 triangles, 8 views of 128x128, 512x512 panel",
                                 "host": info}
+    if world == 1 and args.config == "paper" and not args.no_secondary:
+        line["secondary"] = secondary_measurements(args, sc, stream)
     print(json.dumps(line), flush=True)
     R.close()
     if world > 1:
@@ -708,114 +712,183 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-def run_learned(args):
+def learned_measure(sc, steps, warmup, quality_frames, stream=None):
+    """The learned quarter-view path (12 views rendered, the U-Net's
+    tensor-core kernels predict the 48 reconstructed views, interleave) and
+    the plain renders it stands in for, on scene `sc`: frames/s of each with
+    L2 flushed between frames, the network alone, and per-frame PSNR / SSIM
+    of the prediction against both readings of its judge (the full render's
+    96-view tent reconstruction, and the plain 48-view render)."""
     import torch
     from dataclasses import replace
-    from paper_2601_19901_gb300 import build as B_, lfdpr, recon_net as RN, scenes as S
-
-    B_.build()
-    lfdpr.lib()
+    from paper_2601_19901_gb300 import lfdpr, recon_net as RN, scenes as S
     w, b, nin = RN.load_weights()
-    sc = S.scene_paper()
     d_in = replace(S.display_paper(), n_views=nin)
     d_full = S.display_angular_ss()
     d_out = replace(S.display_paper(), n_views=4 * nin, crosstalk=d_full.crosstalk)
+    d_plain = S.display_paper()
     H, W = d_in.view_h, d_in.view_w
-    stream = torch.cuda.Stream()
+    stream = stream or torch.cuda.Stream()
     ts = lfdpr.TextureSet(sc.textures, stream)
-    # input, full (2x angular), learned output, and the plain 4n-view render for context
-    dis = [lfdpr.lfdpr_create_display(lfdpr.desc_of(d)) for d in (d_in, d_full, d_out, S.display_paper())]
+    # input, full (2x angular), learned output, and the plain 4n-view render
+    dis = [lfdpr.lfdpr_create_display(lfdpr.desc_of(d)) for d in (d_in, d_full, d_out, d_plain)]
     me = [lfdpr.lfdpr_upload_mesh_textured(dis[k], sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle, stream)
           for k in (0, 1, 3)]
     R = lfdpr.Recon(W, H, nin, w, b)
     panel = torch.empty((d_out.panel_h, d_out.panel_w, 4), dtype=torch.uint8, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    try:
+        def learned(f):
+            lfdpr.lfdpr_render_frame(dis[0], me[0], S.model_matrix(f), stream)
+            R.run(dis[0], dis[2], stream)
+            lfdpr.lfdpr_interleave(dis[2], panel.data_ptr(), stream)
 
-    def learned(f):
-        lfdpr.lfdpr_render_frame(dis[0], me[0], S.model_matrix(f), stream)
-        R.run(dis[0], dis[2], stream)
-        lfdpr.lfdpr_interleave(dis[2], panel.data_ptr(), stream)
+        def full(f):
+            lfdpr.lfdpr_render_frame(dis[1], me[1], S.model_matrix(f), stream)
+            lfdpr.lfdpr_interleave(dis[1], panel.data_ptr(), stream)
 
-    def plain(f):
-        lfdpr.lfdpr_render_frame(dis[1], me[1], S.model_matrix(f), stream)
-        lfdpr.lfdpr_interleave(dis[1], panel.data_ptr(), stream)
+        def plain(f):
+            lfdpr.lfdpr_render_frame(dis[3], me[2], S.model_matrix(f), stream)
+            lfdpr.lfdpr_interleave(dis[3], panel.data_ptr(), stream)
 
-    def timed(fn, first):
-        for k in range(args.warmup):
-            fn(first + k)
-        ms = []
-        for k in range(args.steps):
+        def timed(fn, first):
+            for k in range(warmup):
+                fn(first + k)
+            ms = []
+            for k in range(steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(first + warmup + k)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return statistics.mean(ms)
+
+        # the network alone
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        learned(0)
+        e0.record(stream)
+        for _ in range(10):
+            R.run(dis[0], dis[2], stream)
+        e1.record(stream)
+        e1.synchronize()
+        net_ms = e0.elapsed_time(e1) / 10
+        ms_learned = timed(learned, 0)
+        ms_full = timed(full, 0)
+        ms_plain = timed(plain, 0)
+        q = []
+        for f in quality_frames:
+            learned(f)
+            full(f)
+            plain(f)
+            torch.cuda.synchronize()
+            bf = lfdpr.lfdpr_get_buffers(dis[1], me[1])
+            truth = RN.tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
+            bo = lfdpr.lfdpr_get_buffers(dis[2], me[0])
+            pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
+            b4 = lfdpr.lfdpr_get_buffers(dis[3], me[2])
+            plain48 = lfdpr.device_view(b4.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
+            q.append((RN.psnr(pred, truth), RN.ssim(pred, truth), RN.psnr(plain48, truth),
+                      RN.psnr(pred, plain48), RN.ssim(pred, plain48)))
+        # algorithmic FLOPs of one forward pass: the 3x3 layers over the padded
+        # views plus the output product over [features | inputs] (32 + 48) x 3 * 4n
+        flops = 0
+        hp, wp = RN.padded(H, W)
+        for ci, co, lev in RN.LAYERS:
+            flops += 2 * 9 * ci * co * (hp >> lev) * (wp >> lev)
+        flops += 2 * 80 * 3 * 4 * nin * hp * wp
+    finally:
+        R.close()
+        for m_ in me:
+            lfdpr.lfdpr_destroy_mesh(m_)
+        for d_ in dis:
+            lfdpr.lfdpr_destroy_display(d_)
+        ts.close()
+    return {"views_rendered": nin, "views_predicted": 4 * nin,
+            "frames_per_s": 1000.0 / ms_learned, "ms_per_frame": ms_learned,
+            "full_render_frames_per_s": 1000.0 / ms_full, "plain_48_view_frames_per_s": 1000.0 / ms_plain,
+            "network_ms": net_ms, "network_flops": flops, "network_tflops": flops / (net_ms / 1000.0) / 1e12,
+            "vs_full_render": {"what": "judge = the 96-view render's tent reconstruction (the display's "
+                                       "angularly supersampled views)",
+                               "psnr_db_mean": statistics.mean(x[0] for x in q),
+                               "psnr_db_min": min(x[0] for x in q),
+                               "ssim_mean": statistics.mean(x[1] for x in q),
+                               "speedup": ms_full / ms_learned},
+            "vs_plain_48_views": {"what": "judge = the plain 48-view render",
+                                  "psnr_db_mean": statistics.mean(x[3] for x in q),
+                                  "psnr_db_min": min(x[3] for x in q),
+                                  "ssim_mean": statistics.mean(x[4] for x in q),
+                                  "speedup": ms_plain / ms_learned},
+            "plain_48_views_vs_full_render_psnr_db": statistics.mean(x[2] for x in q),
+            "quality_frames": list(quality_frames)}
+
+
+def run_learned(args):
+    from paper_2601_19901_gb300 import build as B_, lfdpr, scenes as S
+    B_.build()
+    lfdpr.lib()
+    m = learned_measure(S.scene_paper(), args.steps, args.warmup, range(0, 120, 8))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    line = {"metric": "learned quarter-view path frames/s at PSNR vs the plain full render",
+            "value": m["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (network), f32 (render)", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("48 views", "%d views rendered, 48 predicted"
+                                                    % m["views_rendered"]),
+                       "l2": "flushed (512 MiB write) between timed steps"},
+            "learned": m,
+            "roofline": {"bound": "tensor", "achieved": m["network_tflops"], "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": m["network_tflops"] / peak_tf, "traffic": None,
+                         "kernel": "the network (k_conv_tc, tcgen05)",
+                         "peak_source": "measured bf16 dense GEMM, burst (MEASURED_PEAKS.json)"
+                         if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s bf16"}}
+    print(json.dumps(line), flush=True)
+
+
+def secondary_measurements(args, sc, stream):
+    """Frames/s of the 96-view (2x angular, tent, crosstalk) frame on the same
+    scene, and the learned quarter-view path with its quality against both
+    readings of its judge: measured after the main timed region, reported
+    beside it (not part of `value`)."""
+    import torch
+    from paper_2601_19901_gb300 import lfdpr, scenes as S
+    out = {}
+    d = S.display_angular_ss()
+    R = lfdpr.Renderer(d, sc, stream=stream)
+    try:
+        R.set_stage_timing(True)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
+        for k in range(3):
+            R.render(S.model_matrix(k), stream)
+            R.interleave(panel.data_ptr(), stream)
+        ms, splat = [], []
+        for k in range(10):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 255)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn(first + args.warmup + k)
+            R.render(S.model_matrix(3 + k), stream)
+            R.interleave(panel.data_ptr(), stream)
             e1.record(stream)
-            e1.synchronize()
+            st = R.stats(stream)
             ms.append(e0.elapsed_time(e1))
-        return statistics.mean(ms)
-
-    # the network alone
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    learned(0)
-    e0.record(stream)
-    for _ in range(10):
-        R.run(dis[0], dis[2], stream)
-    e1.record(stream)
-    e1.synchronize()
-    net_ms = e0.elapsed_time(e1) / 10
-    ms_learned = timed(learned, 0)
-    ms_plain = timed(plain, 0)
-    # quality over the 120-frame orbit (every 8th frame)
-    q = []
-    for f in range(0, 120, 8):
-        learned(f)
-        plain(f)
-        torch.cuda.synchronize()
-        bf = lfdpr.lfdpr_get_buffers(dis[1], me[1])
-        truth = RN.tent_views(lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8))
-        bo = lfdpr.lfdpr_get_buffers(dis[2], me[0])
-        pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
-        lfdpr.lfdpr_render_frame(dis[3], me[2], S.model_matrix(f), stream)
-        torch.cuda.synchronize()
-        b4 = lfdpr.lfdpr_get_buffers(dis[3], me[2])
-        plain48 = lfdpr.device_view(b4.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
-        q.append((RN.psnr(pred, truth), RN.ssim(pred, truth), RN.psnr(plain48, truth)))
-    # algorithmic FLOPs of one forward pass: the 3x3 layers over the padded
-    # views plus the output product over [features | inputs] (32 + 48) x 3 * 4n
-    flops = 0
-    hp, wp = RN.padded(H, W)
-    for ci, co, lev in RN.LAYERS:
-        flops += 2 * 9 * ci * co * (hp >> lev) * (wp >> lev)
-    flops += 2 * 80 * 3 * 4 * nin * hp * wp
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak_tf = peaks.get("bf16_tflops", 1900.0)
-    net_tf = flops / (net_ms / 1000.0) / 1e12
-    line = {"metric": "learned quarter-view path frames/s at PSNR vs the plain full render",
-            "value": 1000.0 / ms_learned, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16 (network), f32 (render)", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("48 views", "%d views rendered, 48 predicted" % nin),
-                       "l2": "flushed (512 MiB write) between timed steps"},
-            "plain_full_render_frames_per_s": 1000.0 / ms_plain,
-            "speedup_vs_plain": ms_plain / ms_learned,
-            "network_ms": net_ms, "network_tflops": net_tf,
-            "roofline": {"bound": "tensor", "achieved": net_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": net_tf / peak_tf, "traffic": None, "kernel": "the network (k_conv_tc, tcgen05)",
-                         "peak_source": "measured bf16 dense GEMM, burst" if "bf16_tflops" in peaks
-                         else "fallback 1.9 PFLOP/s bf16"},
-            "psnr_db": {"mean": statistics.mean(x[0] for x in q), "min": min(x[0] for x in q)},
-            "ssim": {"mean": statistics.mean(x[1] for x in q), "min": min(x[1] for x in q)},
-            "psnr_db_plain_48_views_without_angular_ss": statistics.mean(x[2] for x in q),
-            "quality_frames": len(q)}
-    print(json.dumps(line), flush=True)
-    R.close()
-    for m_ in me:
-        lfdpr.lfdpr_destroy_mesh(m_)
-    for d_ in dis:
-        lfdpr.lfdpr_destroy_display(d_)
-    ts.close()
+            splat.append(st.stage_ms[lfdpr.STAGES.index("splat")])
+        out["angular_96_views"] = {"what": "the same scene rendered at 2x angular rate (96 views of 420x560), "
+                                           "tent to 48, crosstalk 0.15, interleaved; 10 frames, L2 flushed",
+                                   "frames_per_s": 1000.0 / statistics.mean(ms),
+                                   "splat_ms": statistics.mean(splat)}
+    finally:
+        R.close()
+    try:
+        out["learned"] = learned_measure(sc, 10, 3, range(0, 120, 15), stream)
+    except Exception as e:   # the weights ship with the package; report rather than hide a failure
+        out["learned"] = {"error": repr(e)}
+    return out
 
 
 def main():
