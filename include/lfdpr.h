@@ -506,6 +506,35 @@ lfdpr_status lfdpr_batch_scene_ms(const lfdpr_batch *batch, float *ms, int32_t c
  * (borrowed; valid until the batch or its display is destroyed). */
 lfdpr_status lfdpr_batch_panel(const lfdpr_batch *batch, int32_t i, const uint8_t **panel);
 
+/*
+ * Fault injection and allocation accounting (test hooks; the paper has no
+ * counterpart). Every device and pinned-host allocation the library makes
+ * goes through one layer that counts what is live. lfdpr_fault_inject_alloc
+ * arms it: after `after` more successful allocations (0: the next one), one
+ * allocation fails as if memory had run out, so the call making it returns
+ * LFDPR_ENOMEM having freed what it had allocated; the hook then disarms.
+ * -1 disarms it. Process-wide, all threads and devices. Errors: EINVAL
+ * (after < -1).
+ */
+lfdpr_status lfdpr_fault_inject_alloc(int64_t after);
+
+/*
+ * lfdpr_checked_status: the checked build (liblfdpr_checked.so, compiled with
+ * LFDPR_CHECKED: the frame kernels' global indices are range-checked, and an
+ * out-of-range index skips its access and is recorded instead of faulting)
+ * reports the first failing check site (0: none; 1-3 set-up vertex, texture
+ * and material ids, 4 emitted point, 5 point triangle, 6-9 work and near
+ * lists, 10-11 splat key, 12 resolve record, 13 view, 20-23 interleave
+ * reads and panel writes, 24 view mip) and the number of failures since the
+ * last reset (reset != 0 clears them). Synchronises the device. The regular
+ * build returns EINVAL. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_checked_status(uint32_t *first_site, uint64_t *failures, int32_t reset);
+
+/* Allocations the library holds now (count and bytes) and has made in all
+ * since the process started; any pointer may be NULL. */
+lfdpr_status lfdpr_alloc_stats(int64_t *live_count, int64_t *live_bytes, int64_t *total_count);
+
 /* Description of the last error on this thread ("" if none). */
 const char *lfdpr_last_error(void);
 

@@ -87,9 +87,9 @@ void free_batch(lfdpr_batch* b) {
         if (e) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->staged) cudaEventDestroy(b->staged);
-    cudaFree(b->d_models);
-    cudaFreeHost(b->h_models);
-    cudaFree(b->d_scenes);
+    dev_free(b->d_models);
+    host_free(b->h_models);
+    dev_free(b->d_scenes);
     delete b;
 }
 
@@ -216,9 +216,9 @@ lfdpr_status lfdpr_create_batch(lfdpr_display* const* displays, lfdpr_mesh* cons
         sc[i].keys = displays[i]->keys;
     }
     cudaError_t e;
-    if ((e = cudaMalloc(&b->d_models, sizeof(float) * 12 * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&b->h_models, sizeof(float) * 12 * n)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_scenes, sizeof(SplatScene) * n)) != cudaSuccess ||
+    if ((e = dev_malloc(&b->d_models, sizeof(float) * 12 * n)) != cudaSuccess ||
+        (e = host_malloc(&b->h_models, sizeof(float) * 12 * n)) != cudaSuccess ||
+        (e = dev_malloc(&b->d_scenes, sizeof(SplatScene) * n)) != cudaSuccess ||
         (e = cudaMemcpy(b->d_scenes, sc.data(), sizeof(SplatScene) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
         (e = [&] {

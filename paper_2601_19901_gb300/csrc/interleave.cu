@@ -106,6 +106,7 @@ __device__ __forceinline__ int source_y(const DispConst& c, int y) {
 
 __device__ __forceinline__ void store4(const DispConst& c, uint8_t* __restrict__ panel, int xg, int y,
                                        const uint32_t* px) {
+    if (!LFDPR_IN_BOUNDS(uint32_t(y), uint32_t(c.Hp), 21) || !LFDPR_IN_BOUNDS(uint32_t(xg), uint32_t(c.Wp), 21)) return;
     uint8_t* dst = panel + ((uint64_t)y * c.Wp + xg) * 4u;
     if (xg + 4 <= c.Wp && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
         *reinterpret_cast<uint4*>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
@@ -135,7 +136,9 @@ __global__ void __launch_bounds__(kTileThreads) k_interleave_tile(DispConst c, c
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int m = warp; m < c.nr; m += kTileThreads / 32) {
         const uint32_t* src = v32 + (uint64_t)m * npix + (uint64_t)sy * c.W + sx_lo;
-        for (int i = lane; i < n; i += 32) s_row[m * stride + i] = __ldg(src + i);
+        for (int i = lane; i < n; i += 32)
+            if (LFDPR_IN_BOUNDS(uint32_t(sx_lo + i), uint32_t(c.W), 20) && LFDPR_IN_BOUNDS(i, stride, 20))
+                s_row[m * stride + i] = __ldg(src + i);
     }
     __syncthreads();
     const int xg = x0 + 4 * threadIdx.x;
@@ -165,7 +168,8 @@ __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* 
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const int x = min(xg + e, c.Wp - 1);
-            const uint64_t pix = (uint64_t)sy * c.W + source_x(c, x);
+            uint64_t pix = (uint64_t)sy * c.W + source_x(c, x);
+            if (!LFDPR_IN_BOUNDS(pix, npix, 22)) pix = 0;
             px[e] = panel_pixel(c, GlobalTexels{views, npix, pix}, x, y);
         }
         store4(c, panel, xg, y, px);
@@ -229,7 +233,8 @@ __device__ __forceinline__ uint32_t gauss_pixel(const DispConst& c, const uint32
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 if (k > 0 && !xt) continue;
-                const int m = nearest_view(pos, nr, r, phi[ch][k] + dphi);
+                int m = nearest_view(pos, nr, r, phi[ch][k] + dphi);
+                if (!LFDPR_IN_BOUNDS(uint32_t(m), uint32_t(nr), 23)) m = 0;
                 acc[ch][k] += float((__ldg(row + (uint64_t)m * npix) >> (8 * ch)) & 255u);
             }
     }
@@ -301,6 +306,7 @@ __global__ void __launch_bounds__(256) k_view_mip(const uint8_t* __restrict__ sr
         const uint32_t x = uint32_t(t % wl);
         const uint64_t r = t / wl;
         const uint32_t y = uint32_t(r % hl), v = uint32_t(r / hl);
+        if (!LFDPR_IN_BOUNDS((uint64_t)(y * K + K - 1) * W + x * K + K - 1, (uint64_t)W * H, 24)) continue;
         const uint32_t* base = s32 + (uint64_t)v * W * H + (uint64_t)(y * K) * W + x * K;
         uint32_t px[K][K];
 #pragma unroll
@@ -332,6 +338,8 @@ __global__ void __launch_bounds__(256) k_view_mip(const uint8_t* __restrict__ sr
 }
 
 }  // namespace
+
+LFDPR_CHECK_READER(checks_interleave)
 
 cudaError_t launch_view_mip(const uint8_t* views, int W, int H, int nr, int level, uint8_t* out, cudaStream_t s) {
     int dev = 0, sms = 0;

@@ -201,6 +201,65 @@ inline double eye_angle_deg(const lfdpr_display_desc& d, int k, double u) {
                            : -cone / 2.0 + cone * (k + u) / d.n_views;
 }
 
+// Index checks of the checked build (compiled with -DLFDPR_CHECKED=1 into
+// liblfdpr_checked.so): LFDPR_IN_BOUNDS(i, n, site) is false when i >= n, and
+// then records the first failing site (+1) and counts the failure in this
+// translation unit's record, so that the caller skips the access instead of
+// faulting. In the regular build it is `true` and costs nothing. Each .cu
+// file that uses it defines its reader with LFDPR_CHECK_READER(name).
+#ifdef LFDPR_CHECKED
+static __device__ unsigned int g_check[2];
+__device__ __forceinline__ bool check_index(uint64_t i, uint64_t n, unsigned site) {
+    if (i < n) return true;
+    atomicCAS(&g_check[0], 0u, site + 1u);
+    atomicAdd(&g_check[1], 1u);
+    return false;
+}
+#define LFDPR_IN_BOUNDS(i, n, site) (::lfdpr::check_index(uint64_t(i), uint64_t(n), (site)))
+#define LFDPR_CHECK_READER(name)                                                          \
+    cudaError_t name(unsigned out[2], bool reset) {                                       \
+        cudaError_t e = cudaMemcpyFromSymbol(out, g_check, 2 * sizeof(unsigned));         \
+        if (e == cudaSuccess && reset) {                                                   \
+            const unsigned zero[2] = {0u, 0u};                                             \
+            e = cudaMemcpyToSymbol(g_check, zero, sizeof zero);                            \
+        }                                                                                  \
+        return e;                                                                          \
+    }
+#else
+#define LFDPR_IN_BOUNDS(i, n, site) true
+#define LFDPR_CHECK_READER(name)                                                          \
+    cudaError_t name(unsigned out[2], bool) {                                             \
+        out[0] = out[1] = 0u;                                                              \
+        return cudaSuccess;                                                                \
+    }
+#endif
+// The checked build's records of sample.cu, splat.cu and interleave.cu.
+cudaError_t checks_sample(unsigned out[2], bool reset);
+cudaError_t checks_splat(unsigned out[2], bool reset);
+cudaError_t checks_interleave(unsigned out[2], bool reset);
+
+// Every device and pinned-host allocation of the library goes through these:
+// they keep count of what is live (lfdpr_alloc_stats) and can be made to
+// fail on purpose (lfdpr_fault_inject_alloc), as if memory had run out.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t s);
+cudaError_t host_malloc_raw(void** p, size_t bytes);
+void dev_free(void* p);
+void dev_free_async(void* p, cudaStream_t s);
+void host_free(void* p);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+    return dev_malloc_async_raw(reinterpret_cast<void**>(p), bytes, s);
+}
+template <class T>
+inline cudaError_t host_malloc(T** p, size_t bytes) {
+    return host_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
 // Per-thread description of the last error, read by lfdpr_last_error().
 __attribute__((visibility("hidden"))) extern thread_local char g_last_error[512];
 
@@ -216,6 +275,7 @@ struct FrameArgs {
     const float* xyz;
     const float* uv;
     const uint32_t* idx;
+    uint32_t n_verts;
     const uint32_t* tri_tex;         // texture per triangle, or material per triangle when mat_tex is set
     const uint4* mat_tex;            // null, or [materials] texture ids: albedo, normal, roughness, metallic
     int pbr;                         // shade physically (needs mat_tex)
@@ -224,6 +284,7 @@ struct FrameArgs {
     const uint8_t* pool;
     const uint64_t* lvl;             // [n_tex][kMaxLevels] byte offset of each mip level in the pool
     uint32_t n_tris, n_tex;
+    uint32_t n_mat;                  // materials of a mesh of materials (0 otherwise)
     TriRec* rec;
     uint32_t* counts;
     uint32_t* offsets;

@@ -179,6 +179,7 @@ extern "C" lfdpr_status lfdpr_sample_points_noalloc(
     for (int k = 0; k < 12; k++) a.model[k] = model[k];
     a.ex = scr->ex;
     a.xyz = xyz;
+    a.n_verts = 0xffffffffu;   // not known here: vertex indices are the caller's to keep in range
     a.uv = uv;
     a.idx = idx;
     a.tri_tex = tri_tex;

@@ -779,12 +779,12 @@ namespace {
 
 void free_recon(lfdpr_recon* r) {
     if (!r) return;
-    cudaFree(r->w);
-    cudaFree(r->b);
-    cudaFree(r->w_out);
-    cudaFree(r->b_out);
-    cudaFree(r->status);
-    cudaFree(r->act);
+    dev_free(r->w);
+    dev_free(r->b);
+    dev_free(r->w_out);
+    dev_free(r->b_out);
+    dev_free(r->status);
+    dev_free(r->act);
     delete r;
 }
 
@@ -855,16 +855,16 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     const int64_t nw3 = wo, nb3 = bo;
     uint16_t* w_raw = nullptr;   // device staging of the 3x3 blob before packing
     uint16_t* wout_raw = nullptr;
-    if ((e = cudaMalloc(&r->w, 2 * nw3)) != cudaSuccess || (e = cudaMalloc(&r->b, 4 * nb3)) != cudaSuccess ||
-        (e = cudaMalloc(&r->w_out, 2 * int64_t(ntout) * 80)) != cudaSuccess ||
-        (e = cudaMalloc(&r->b_out, 4 * int64_t(ntout))) != cudaSuccess ||
-        (e = cudaMalloc(&r->status, sizeof(int))) != cudaSuccess || (e = cudaMalloc(&r->act, 2 * total)) != cudaSuccess ||
-        (e = cudaMalloc(&w_raw, 2 * nw3)) != cudaSuccess ||
-        (e = cudaMalloc(&wout_raw, 2 * int64_t(no3) * 80)) != cudaSuccess) {
-        cudaFree(w_raw);
-        cudaFree(wout_raw);
+    if ((e = dev_malloc(&r->w, 2 * nw3)) != cudaSuccess || (e = dev_malloc(&r->b, 4 * nb3)) != cudaSuccess ||
+        (e = dev_malloc(&r->w_out, 2 * int64_t(ntout) * 80)) != cudaSuccess ||
+        (e = dev_malloc(&r->b_out, 4 * int64_t(ntout))) != cudaSuccess ||
+        (e = dev_malloc(&r->status, sizeof(int))) != cudaSuccess || (e = dev_malloc(&r->act, 2 * total)) != cudaSuccess ||
+        (e = dev_malloc(&w_raw, 2 * nw3)) != cudaSuccess ||
+        (e = dev_malloc(&wout_raw, 2 * int64_t(no3) * 80)) != cudaSuccess) {
+        dev_free(w_raw);
+        dev_free(wout_raw);
         free_recon(r);
-        return cuda_fail(e, "create_recon: cudaMalloc");
+        return cuda_fail(e, "create_recon: allocation");
     }
     __nv_bfloat16** bufs[kTensors] = {&r->x0,  &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1,  &r->p2,  &r->e2a, &r->e2,
                                       &r->p3,  &r->ba,  &r->U2, &r->d2a, &r->U1, &r->d1a, &r->U0, &r->d0a, &r->d0};
@@ -925,8 +925,8 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
               make_map(&r->out_d0, r->d0, 32, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess &&
               make_map(&r->out_x0, r->x0, 48, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess;
     if (!maps_ok) {
-        cudaFree(w_raw);
-        cudaFree(wout_raw);
+        dev_free(w_raw);
+        dev_free(wout_raw);
         free_recon(r);
         return fail(LFDPR_EINVAL, "create_recon: no tensor-core layout for %dx%d views", view_w, view_h);
     }
@@ -942,8 +942,8 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
             e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(wout_raw), no3, 1, 80, ntout, 1, r->w_out, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    cudaFree(w_raw);
-    cudaFree(wout_raw);
+    dev_free(w_raw);
+    dev_free(wout_raw);
     if (e != cudaSuccess) {
         free_recon(r);
         return cuda_fail(e, "create_recon: upload");
@@ -1045,9 +1045,9 @@ lfdpr_status lfdpr_conv3x3_bf16(const void* in, int32_t H, int32_t W, int32_t ci
     // chunked bordered copies of the input and output, and the packed weights
     const size_t qp = qpad(H, W);
     __nv_bfloat16 *ci = nullptr, *co = nullptr, *wpk = nullptr;
-    cudaError_t e = cudaMallocAsync(&ci, 2 * qp * cin, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&co, 2 * qp * cout, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&wpk, size_t(2) * cout * 9 * cin, s);
+    cudaError_t e = dev_malloc_async(&ci, 2 * qp * cin, s);
+    if (e == cudaSuccess) e = dev_malloc_async(&co, 2 * qp * cout, s);
+    if (e == cudaSuccess) e = dev_malloc_async(&wpk, size_t(2) * cout * 9 * cin, s);
     CUtensorMap m;
     if (e == cudaSuccess) e = cudaMemsetAsync(ci, 0, 2 * qp * cin, s);
     if (e == cudaSuccess) e = make_map(&m, ci, cin, qp, g.rows);
@@ -1061,9 +1061,9 @@ lfdpr_status lfdpr_conv3x3_bf16(const void* in, int32_t H, int32_t W, int32_t ci
         k_from_chunked<<<sms * 8, 256, 0, s>>>(co, H, W, cout, static_cast<__nv_bfloat16*>(out));
         e = cudaGetLastError();
     }
-    cudaFreeAsync(ci, s);
-    cudaFreeAsync(co, s);
-    cudaFreeAsync(wpk, s);
+    dev_free_async(ci, s);
+    dev_free_async(co, s);
+    dev_free_async(wpk, s);
     if (e != cudaSuccess) return cuda_fail(e, "conv3x3");
     return LFDPR_OK;
 }

@@ -4,7 +4,10 @@
 // pixel footprints) is done in double and rounded once to binary32; this file
 // is compiled with -ffp-contract=off so no host multiply-add is fused.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +20,75 @@ using namespace lfdpr;
 
 namespace lfdpr {
 thread_local char g_last_error[512] = "";
+
+namespace {
+std::mutex g_alloc_mu;
+std::unordered_map<void*, size_t> g_live;     // what the library holds: address -> bytes
+int64_t g_live_bytes = 0, g_allocs = 0;
+std::atomic<int64_t> g_fail_after{-1};        // the allocation this many from now fails (-1: none)
+
+// Whether this allocation is the one armed to fail (disarms once it fires).
+bool fail_now() {
+    int64_t v = g_fail_after.load();
+    while (v >= 0)
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
+void keep(void* p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_live[p] = bytes;
+    g_live_bytes += int64_t(bytes);
+    g_allocs++;
+}
+
+bool drop(void* p) {
+    if (!p) return false;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    auto it = g_live.find(p);
+    if (it == g_live.end()) return false;
+    g_live_bytes -= int64_t(it->second);
+    g_live.erase(it);
+    return true;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+    *p = nullptr;
+    if (fail_now()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) keep(*p, bytes);
+    return e;
+}
+
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (fail_now()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) keep(*p, bytes);
+    return e;
+}
+
+cudaError_t host_malloc_raw(void** p, size_t bytes) {
+    *p = nullptr;
+    if (fail_now()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) keep(*p, bytes);
+    return e;
+}
+
+void dev_free(void* p) {
+    if (drop(p)) cudaFree(p);
+}
+
+void dev_free_async(void* p, cudaStream_t s) {
+    if (drop(p)) cudaFreeAsync(p, s);
+}
+
+void host_free(void* p) {
+    if (drop(p)) cudaFreeHost(p);
+}
 
 lfdpr_status fail(lfdpr_status s, const char* fmt, ...) {
     va_list ap;
@@ -36,6 +108,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.dc = disp->dc;
     a.ex = disp->d_ex;
     a.xyz = mesh->xyz;
+    a.n_verts = mesh->n_verts;
     a.uv = mesh->uv;
     a.idx = mesh->idx;
     a.tri_tex = mesh->tri_tex;
@@ -47,6 +120,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.lvl = mesh->lvl;
     a.n_tris = mesh->n_tris;
     a.n_tex = mesh->n_tex;
+    a.n_mat = mesh->n_mat;
     a.rec = mesh->rec;
     a.counts = mesh->counts;
     a.offsets = mesh->offsets;
@@ -158,39 +232,39 @@ void free_display(lfdpr_display* d) {
         if (e) cudaEventDestroy(e);
     for (auto& e : d->band_ev)
         if (e) cudaEventDestroy(e);
-    cudaFree(d->d_ex);
-    cudaFree(d->d_pos);
-    cudaFree(d->d_samples);
-    cudaFree(d->points);
-    cudaFree(d->work);
-    cudaFree(d->near);
-    cudaFree(d->rrec);
-    cudaFree(d->rmat);
-    cudaFree(d->keys);
-    cudaFree(d->views);
-    cudaFree(d->panel);
-    cudaFree(d->views_mip);
-    cudaFree(d->ctr);
+    dev_free(d->d_ex);
+    dev_free(d->d_pos);
+    dev_free(d->d_samples);
+    dev_free(d->points);
+    dev_free(d->work);
+    dev_free(d->near);
+    dev_free(d->rrec);
+    dev_free(d->rmat);
+    dev_free(d->keys);
+    dev_free(d->views);
+    dev_free(d->panel);
+    dev_free(d->views_mip);
+    dev_free(d->ctr);
     delete d;
 }
 
 void free_mesh(lfdpr_mesh* m) {
     if (!m) return;
-    cudaFree(m->xyz);
-    cudaFree(m->uv);
-    cudaFree(m->idx);
-    cudaFree(m->tri_tex);
-    cudaFree(m->mat_tex);
+    dev_free(m->xyz);
+    dev_free(m->uv);
+    dev_free(m->idx);
+    dev_free(m->tri_tex);
+    dev_free(m->mat_tex);
     if (m->owns_textures) {
-        cudaFree(m->pool);
-        cudaFree(m->tex);
-        cudaFree(m->lvl);
+        dev_free(m->pool);
+        dev_free(m->tex);
+        dev_free(m->lvl);
     }
-    cudaFree(m->rec);
-    cudaFree(m->tproj);
-    cudaFree(m->counts);
-    cudaFree(m->offsets);
-    cudaFree(m->block_sums);
+    dev_free(m->rec);
+    dev_free(m->tproj);
+    dev_free(m->counts);
+    dev_free(m->offsets);
+    dev_free(m->block_sums);
     delete m;
 }
 
@@ -243,16 +317,16 @@ lfdpr_status upload_textures(const uint8_t* const* tex_rgba8, const uint32_t* te
     TexDesc* tex = nullptr;
     uint64_t* dl = nullptr;
     auto undo = [&]() {
-        cudaFree(pool);
-        cudaFree(tex);
-        cudaFree(dl);
+        dev_free(pool);
+        dev_free(tex);
+        dev_free(dl);
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&pool, pool_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
-        (e = cudaMalloc(&dl, sizeof(uint64_t) * kMaxLevels * n_tex)) != cudaSuccess) {
+    if ((e = dev_malloc(&pool, pool_bytes)) != cudaSuccess ||
+        (e = dev_malloc(&tex, sizeof(TexDesc) * n_tex)) != cudaSuccess ||
+        (e = dev_malloc(&dl, sizeof(uint64_t) * kMaxLevels * n_tex)) != cudaSuccess) {
         undo();
-        return cuda_fail(e, "textures: cudaMalloc");
+        return cuda_fail(e, "textures: allocation");
     }
 #define CKT(call, what)                 \
     do {                                \
@@ -311,14 +385,14 @@ lfdpr_status upload_geometry(lfdpr_display* disp, const float* xyz, const float*
     m->n_blocks = (n_tris + kSetupThreads - 1) / kSetupThreads;
     const uint64_t nt = n_tris ? n_tris : 1, nv = n_verts ? n_verts : 1;
     cudaError_t e;
-    if ((e = cudaMalloc(&m->xyz, 12u * nv)) != cudaSuccess || (e = cudaMalloc(&m->uv, 8u * nv)) != cudaSuccess ||
-        (e = cudaMalloc(&m->idx, 12u * nt)) != cudaSuccess || (e = cudaMalloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->counts, 4u * nt)) != cudaSuccess || (e = cudaMalloc(&m->offsets, 4u * nt)) != cudaSuccess ||
-        (e = cudaMalloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
+    if ((e = dev_malloc(&m->xyz, 12u * nv)) != cudaSuccess || (e = dev_malloc(&m->uv, 8u * nv)) != cudaSuccess ||
+        (e = dev_malloc(&m->idx, 12u * nt)) != cudaSuccess || (e = dev_malloc(&m->tri_tex, 4u * nt)) != cudaSuccess ||
+        (e = dev_malloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
+        (e = dev_malloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
+        (e = dev_malloc(&m->counts, 4u * nt)) != cudaSuccess || (e = dev_malloc(&m->offsets, 4u * nt)) != cudaSuccess ||
+        (e = dev_malloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
         free_mesh(m);
-        return cuda_fail(e, "upload_mesh: cudaMalloc");
+        return cuda_fail(e, "upload_mesh: allocation");
     }
 #define CKM(call, what)                 \
     do {                                \
@@ -351,6 +425,47 @@ void mark(lfdpr_display* d, int k, cudaStream_t s) {
 extern "C" {
 
 const char* lfdpr_last_error(void) { return g_err; }
+
+lfdpr_status lfdpr_fault_inject_alloc(int64_t after) {
+    g_err[0] = 0;
+    if (after < -1) return fail(LFDPR_EINVAL, "fault_inject_alloc: %lld < -1", (long long)after);
+    lfdpr::g_fail_after.store(after);
+    return LFDPR_OK;
+}
+
+lfdpr_status lfdpr_checked_status(uint32_t* first_site, uint64_t* failures, int32_t reset) {
+    g_err[0] = 0;
+#ifndef LFDPR_CHECKED
+    (void)first_site;
+    (void)failures;
+    (void)reset;
+    return fail(LFDPR_EINVAL, "checked_status: not the checked build (liblfdpr_checked.so)");
+#else
+    CK(cudaDeviceSynchronize(), "checked_status: synchronize");
+    cudaError_t (*readers[3])(unsigned[2], bool) = {lfdpr::checks_sample, lfdpr::checks_splat,
+                                                   lfdpr::checks_interleave};
+    uint32_t site = 0;
+    uint64_t n = 0;
+    for (auto rd : readers) {
+        unsigned r[2];
+        CK(rd(r, reset != 0), "checked_status: read");
+        if (!site && r[0]) site = r[0];
+        n += r[1];
+    }
+    if (first_site) *first_site = site;
+    if (failures) *failures = n;
+    return LFDPR_OK;
+#endif
+}
+
+lfdpr_status lfdpr_alloc_stats(int64_t* live_count, int64_t* live_bytes, int64_t* total_count) {
+    g_err[0] = 0;
+    std::lock_guard<std::mutex> lock(lfdpr::g_alloc_mu);
+    if (live_count) *live_count = int64_t(lfdpr::g_live.size());
+    if (live_bytes) *live_bytes = lfdpr::g_live_bytes;
+    if (total_count) *total_count = lfdpr::g_allocs;
+    return LFDPR_OK;
+}
 
 int32_t lfdpr_version(void) { return LFDPR_VERSION; }
 
@@ -427,19 +542,19 @@ lfdpr_status lfdpr_create_display(const lfdpr_display_desc* desc, lfdpr_display*
 
     const uint64_t npix = uint64_t(s.view_w) * s.view_h * nr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&d->d_pos, sizeof(float) * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&d->d_samples, sizeof(float) * 3 * 32)) != cudaSuccess ||
-        (e = cudaMalloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->work, sizeof(WorkRec) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->near, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->rrec, sizeof(ResolveRec) * (uint64_t)d->max_points)) != cudaSuccess ||
-        (e = cudaMalloc(&d->keys, 8u * npix)) != cudaSuccess ||
-        (e = cudaMalloc(&d->views, 4u * npix)) != cudaSuccess ||
-        (e = cudaMalloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
-        (e = cudaMalloc(&d->ctr, sizeof(Counters))) != cudaSuccess) {
+    if ((e = dev_malloc(&d->d_ex, sizeof(float) * nr)) != cudaSuccess ||
+        (e = dev_malloc(&d->d_pos, sizeof(float) * nr)) != cudaSuccess ||
+        (e = dev_malloc(&d->d_samples, sizeof(float) * 3 * 32)) != cudaSuccess ||
+        (e = dev_malloc(&d->points, sizeof(uint4) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = dev_malloc(&d->work, sizeof(WorkRec) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = dev_malloc(&d->near, sizeof(uint32_t) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = dev_malloc(&d->rrec, sizeof(ResolveRec) * (uint64_t)d->max_points)) != cudaSuccess ||
+        (e = dev_malloc(&d->keys, 8u * npix)) != cudaSuccess ||
+        (e = dev_malloc(&d->views, 4u * npix)) != cudaSuccess ||
+        (e = dev_malloc(&d->panel, 4u * uint64_t(s.panel_w) * s.panel_h)) != cudaSuccess ||
+        (e = dev_malloc(&d->ctr, sizeof(Counters))) != cudaSuccess) {
         free_display(d);
-        return cuda_fail(e, "create_display: cudaMalloc");
+        return cuda_fail(e, "create_display: allocation");
     }
     const std::vector<float> pos = view_positions(d);
     if ((e = cudaMemcpy(d->d_ex, d->h_ex.data(), sizeof(float) * nr, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -550,9 +665,9 @@ lfdpr_status lfdpr_destroy_texture_set(lfdpr_texture_set* set) {
     g_err[0] = 0;
     if (!set) return fail(LFDPR_EINVAL, "destroy_texture_set: null");
     if (set->n_meshes != 0) return fail(LFDPR_EINVAL, "destroy_texture_set: meshes still use it");
-    cudaFree(set->pool);
-    cudaFree(set->tex);
-    cudaFree(set->lvl);
+    dev_free(set->pool);
+    dev_free(set->tex);
+    dev_free(set->lvl);
     delete set;
     return LFDPR_OK;
 }
@@ -592,14 +707,14 @@ lfdpr_status lfdpr_upload_mesh_materials(lfdpr_display* disp, const float* xyz, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the display's per-point normal-map values, on its first mesh of materials
     if (!disp->rmat) {
-        const cudaError_t e = cudaMalloc(&disp->rmat, sizeof(uint2) * (uint64_t)disp->max_points);
+        const cudaError_t e = dev_malloc(&disp->rmat, sizeof(uint2) * (uint64_t)disp->max_points);
         if (e != cudaSuccess) return cuda_fail(e, "upload_mesh_materials: normal-map buffer");
     }
     lfdpr_mesh* m = nullptr;
     // the material ids are checked against n_mat like texture ids
     const lfdpr_status st = upload_geometry(disp, xyz, uv, idx, tri_mat, n_verts, n_tris, n_mat, s, &m);
     if (st != LFDPR_OK) return st;
-    cudaError_t e = cudaMalloc(&m->mat_tex, 16ull * n_mat);
+    cudaError_t e = dev_malloc(&m->mat_tex, 16ull * n_mat);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->mat_tex, mat_tex, 16ull * n_mat, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -792,11 +907,11 @@ lfdpr_status lfdpr_set_spatial_supersampling(lfdpr_display* disp, int32_t level)
     if (level > 0) {
         const uint64_t bytes = 4u * uint64_t(disp->dc.W >> level) * uint64_t(disp->dc.H >> level) * disp->dc.nr;
         uint8_t* p = nullptr;
-        CK(cudaMalloc(&p, bytes), "set_spatial_supersampling: view mip buffer");
-        cudaFree(disp->views_mip);
+        CK(dev_malloc(&p, bytes), "set_spatial_supersampling: view mip buffer");
+        dev_free(disp->views_mip);
         disp->views_mip = p;
     } else {
-        cudaFree(disp->views_mip);
+        dev_free(disp->views_mip);
         disp->views_mip = nullptr;
     }
     disp->ss_level = level;

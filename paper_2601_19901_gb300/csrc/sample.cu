@@ -147,7 +147,8 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     for (int k = 0; k < 12; k++) M[k] = a.model_dev ? __ldg(a.model_dev + k) : a.model[k];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const uint32_t vi = a.idx[3 * (size_t)t + k];
+        uint32_t vi = a.idx[3 * (size_t)t + k];
+        if (!LFDPR_IN_BOUNDS(vi, a.n_verts, 1)) vi = 0;
         transform(M, a.xyz[3 * (size_t)vi], a.xyz[3 * (size_t)vi + 1], a.xyz[3 * (size_t)vi + 2], P[k]);
         Q[k][0] = a.uv[2 * (size_t)vi];
         Q[k][1] = a.uv[2 * (size_t)vi + 1];
@@ -278,9 +279,14 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     uint32_t tex = a.tri_tex[t];
     uint4 mt = make_uint4(0u, 0u, 0u, 0u);
     if (a.mat_tex) {
+        if (!LFDPR_IN_BOUNDS(tex, a.n_mat, 3)) tex = 0;
         mt = a.mat_tex[tex];
         tex = mt.x;
+        if (!LFDPR_IN_BOUNDS(mt.y, a.n_tex, 2) || !LFDPR_IN_BOUNDS(mt.z, a.n_tex, 2) ||
+            !LFDPR_IN_BOUNDS(mt.w, a.n_tex, 2))
+            mt.y = mt.z = mt.w = 0;
     }
+    if (!LFDPR_IN_BOUNDS(tex, a.n_tex, 2)) tex = 0;
     const TexDesc td = a.tex[tex];
     const float X = float(td.w), Y = float(td.h);
     const float ds1 = Q[1][0] - Q[0][0], dt1 = Q[1][1] - Q[0][1];
@@ -484,7 +490,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
         int j0, j1;
         column_rows(U, V, su, sv, umax, i, &j0, &j1);
         for (int j = j0; j < j1; j++) {
-            *reinterpret_cast<uint2*>(a.points + p) = make_uint2(t, uint32_t(i) | (uint32_t(j) << 16));
+            if (LFDPR_IN_BOUNDS(p, a.max_points, 4))
+                *reinterpret_cast<uint2*>(a.points + p) = make_uint2(t, uint32_t(i) | (uint32_t(j) << 16));
             p++;
         }
     }
@@ -770,7 +777,8 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
     const float H1 = float(c.H - 1);
     const int lane = threadIdx.x & 31;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
+        if (!LFDPR_IN_BOUNDS(pt.x, a.n_tris, 5)) pt.x = 0;
         const TriRec* r = a.rec + pt.x;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
@@ -899,13 +907,14 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         }
         base = __shfl_sync(mask, base, leader);
         nbase = __shfl_sync(mask, nbase, leader);
-        if (ny > 0) {
+        if (ny > 0 && LFDPR_IN_BOUNDS(base + __popc(bal & below), a.max_points, 6)) {
             WorkRec* w = a.work + base + __popc(bal & below);
             w->L0 = L0;
             w->L1 = L1;
             w->meta = make_uint4(y0 | (ny << 14) | (flags << 29), pt.y, pt.x, p);
         }
-        if (near) a.near[nbase + __popc(bnear & below)] = p;
+        if (near && LFDPR_IN_BOUNDS(nbase + __popc(bnear & below), a.max_points, 7))
+            a.near[nbase + __popc(bnear & below)] = p;
     }
 }
 
@@ -920,6 +929,7 @@ __global__ void __launch_bounds__(256) k_near_work(FrameArgs a) {
     const int lane = threadIdx.x & 31;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t p = a.near[k];
+        if (!LFDPR_IN_BOUNDS(p, a.max_points, 8)) continue;
         const uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
         const TriRec* r = a.rec + pt.x;
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
@@ -949,7 +959,7 @@ __global__ void __launch_bounds__(256) k_near_work(FrameArgs a) {
         uint32_t base = 0;
         if (lane == leader && bal) base = atomicAdd(&a.ctr->n_work, uint32_t(__popc(bal)));
         base = __shfl_sync(mask, base, leader);
-        if (o.ny > 0) {
+        if (o.ny > 0 && LFDPR_IN_BOUNDS(base + __popc(bal & ((1u << lane) - 1u)), a.max_points, 9)) {
             WorkRec* w = a.work + base + __popc(bal & ((1u << lane) - 1u));
             w->L0 = o.L0;
             w->L1 = o.L1;
@@ -994,6 +1004,8 @@ __global__ void __launch_bounds__(256) k_fetch_mat(FrameArgs a) {
 }
 
 }  // namespace
+
+LFDPR_CHECK_READER(checks_sample)
 
 cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s) {
     k_setup<<<a.n_blocks, kSetupThreads, 0, s>>>(a);

@@ -192,6 +192,9 @@ __device__ __forceinline__ void test_candidate(const DispConst& c, const SplatWa
     if (!pixel_test(c, Ex, num, qEx, qEy, qEz, d1, q2, q3, q4, b.x, b.y, b.z, b.w, flags & kFlagInterior,
                     flags & kFlagDepthOk, x, y, t))
         return;
+    if (!LFDPR_IN_BOUNDS(vo, c.nr, 10) || !LFDPR_IN_BOUNDS(uint32_t(x), c.W, 11) ||
+        !LFDPR_IN_BOUNDS(uint32_t(y), c.H, 11))
+        return;
     // a view holds at most 2^26 pixels: 32-bit offset within it
     atomicMin(keys + ((uint64_t)vo * npix + (uint32_t(y) * uint32_t(c.W) + uint32_t(x))),
               ((unsigned long long)__float_as_uint(t) << 32) | __float_as_uint(d0.w));
@@ -422,6 +425,7 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
     uint4 rb[kResolvePix];
 #pragma unroll
     for (int k = 0; k < kResolvePix; k++) {
+        if (key[k] != ~0ull && !LFDPR_IN_BOUNDS(uint32_t(key[k]), a.max_points, 12)) key[k] = ~0ull;
         if (key[k] != ~0ull) {
             const ResolveRec* rp = a.rrec + uint32_t(key[k]);
             ra[k] = __ldg(&rp->a);
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
 #pragma unroll
     for (int k = 0; k < kResolvePix; k++) {
         const uint32_t p = p0 + 256u * k;
-        if (p < npix)
+        if (p < npix && LFDPR_IN_BOUNDS(uint32_t(v), uint32_t(c.nr), 13))
             reinterpret_cast<uint32_t*>(a.views)[o0 + p] = key[k] != ~0ull ? resolve_pixel(Ex, ra[k], rb[k]) : 0u;
     }
 }
@@ -503,7 +507,8 @@ __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
     if (px >= npix) return;
     const int v = a.view_lo + int(blockIdx.y);
     const uint64_t o = (uint64_t)v * npix + px;
-    const unsigned long long key = a.keys[o];
+    unsigned long long key = a.keys[o];
+    if (key != ~0ull && !LFDPR_IN_BOUNDS(uint32_t(key), a.max_points, 12)) key = ~0ull;
     uint32_t out = 0u;
     if (key != ~0ull) {
         const uint32_t p = uint32_t(key);
@@ -589,6 +594,8 @@ cudaError_t splat_batch(const SplatScene* scenes, int n_scenes, int grid, cudaSt
 }
 
 }  // namespace
+
+LFDPR_CHECK_READER(checks_splat)
 
 cudaError_t launch_splat(const FrameArgs& a, cudaStream_t s) {
     // the fewest view slots per lane that hold every view of the range

@@ -15,7 +15,10 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblfdpr.so")
+# LFDPR_CHECKED=1 loads the checked build (index checks that record instead of
+# faulting; see lfdpr_checked_status) in place of the regular one
+CHECKED = os.environ.get("LFDPR_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_HERE, "liblfdpr_checked.so" if CHECKED else "liblfdpr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, EDEVICE = range(6)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "EDEVICE"}
@@ -35,7 +38,8 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_create_batch", "lfdpr_destroy_batch", "lfdpr_batch_get_config",
            "lfdpr_batch_set_config", "lfdpr_render_batch", "lfdpr_batch_autotune", "lfdpr_batch_panel",
            "lfdpr_batch_autotune_table", "lfdpr_batch_scene_ms", "lfdpr_set_spatial_supersampling",
-           "lfdpr_set_view_band",
+           "lfdpr_set_view_band", "lfdpr_fault_inject_alloc", "lfdpr_alloc_stats",
+           "lfdpr_checked_status",
            "lfdpr_recon_weight_count", "lfdpr_recon_bias_count", "lfdpr_create_recon",
            "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_recon_status",
            "lfdpr_conv3x3_bf16"]
@@ -118,6 +122,9 @@ def lib() -> C.CDLL:
         L.lfdpr_set_recon_samples.argtypes = [P, P, C.c_int32]
         L.lfdpr_set_spatial_supersampling.argtypes = [P, C.c_int32]
         L.lfdpr_set_view_band.argtypes = [P, C.c_int32]
+        L.lfdpr_fault_inject_alloc.argtypes = [C.c_int64]
+        L.lfdpr_alloc_stats.argtypes = [P, P, P]
+        L.lfdpr_checked_status.argtypes = [P, P, C.c_int32]
         L.lfdpr_sample_points_noalloc.argtypes = [C.POINTER(DisplayDesc), P, P, P, P, P, C.c_uint32,
                                                   P, C.c_uint32, P, C.c_uint32, P, P, P]
         L.lfdpr_probe_atomic_min.argtypes = [P, C.c_uint64, P, P, C.c_uint64, C.c_int32, P]
@@ -202,6 +209,24 @@ def lfdpr_set_spatial_supersampling(disp: int, level: int):
 
 def lfdpr_set_view_band(disp: int, band: int):
     _check(lib().lfdpr_set_view_band(disp, int(band)))
+
+
+def lfdpr_fault_inject_alloc(after: int):
+    _check(lib().lfdpr_fault_inject_alloc(int(after)))
+
+
+def lfdpr_checked_status(reset: bool = False):
+    """(first failing check site, failures) of the checked build."""
+    site, n = C.c_uint32(0), C.c_uint64(0)
+    _check(lib().lfdpr_checked_status(C.byref(site), C.byref(n), 1 if reset else 0))
+    return site.value, n.value
+
+
+def lfdpr_alloc_stats():
+    """(live allocations, live bytes, allocations made since the process started)."""
+    out = [C.c_int64(0) for _ in range(3)]
+    _check(lib().lfdpr_alloc_stats(*[C.byref(o) for o in out]))
+    return tuple(o.value for o in out)
 
 
 def create_display(display, max_points: int = 0) -> int:

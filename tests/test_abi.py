@@ -81,3 +81,37 @@ def test_null_arguments_rejected(L):
     assert L.lfdpr_destroy_mesh(None) == lfdpr.EINVAL
     assert L.lfdpr_probe_atomic_min(None, 0, None, None, 0, 0, None) == lfdpr.EINVAL
     assert b"null" in L.lfdpr_last_error()
+
+
+def test_fault_injection_hook_on_the_host(L):
+    """The allocation-failure hook is armed and disarmed without a device;
+    arguments outside its range are rejected; the accounting reads back."""
+    live0, bytes0, total0 = lfdpr.lfdpr_alloc_stats()
+    assert live0 >= 0 and bytes0 >= 0 and total0 >= live0
+    lfdpr.lfdpr_fault_inject_alloc(0)
+    lfdpr.lfdpr_fault_inject_alloc(-1)
+    with pytest.raises(lfdpr.LfdprError) as e:
+        lfdpr.lfdpr_fault_inject_alloc(-2)
+    assert e.value.status == lfdpr.EINVAL
+    assert L.lfdpr_alloc_stats(None, None, None) == lfdpr.OK
+
+
+@pytest.mark.skipif(_torch_gpu(), reason="checks the no-device path")
+def test_armed_hook_without_a_device_allocates_nothing(L):
+    before = lfdpr.lfdpr_alloc_stats()
+    lfdpr.lfdpr_fault_inject_alloc(0)
+    try:
+        with pytest.raises(lfdpr.LfdprError) as e:
+            lfdpr.lfdpr_create_display(lfdpr.desc_of(scenes.display_tiny()))
+        assert e.value.status == lfdpr.EDEVICE
+        assert lfdpr.lfdpr_alloc_stats() == before
+    finally:
+        lfdpr.lfdpr_fault_inject_alloc(-1)
+
+
+def test_regular_build_reports_it_is_not_checked(L):
+    if lfdpr.CHECKED:
+        pytest.skip("this process loaded the checked build")
+    with pytest.raises(lfdpr.LfdprError) as e:
+        lfdpr.lfdpr_checked_status()
+    assert e.value.status == lfdpr.EINVAL
