@@ -285,8 +285,8 @@ lfdpr_status lfdpr_render_batch(lfdpr_batch* b, const float* models, void* strea
     b->replayed = true;
     for (int i = 0; i < b->n; i++) {
         b->disp[i]->ev_frame = b->disp[i]->ev_interleave = false;
-        // set-up, scan, emission, fetch, near-limit records (and the materials'
-        // fetch), resolve, (view mips,) interleave
+        // set-up, scan, emission, fetch, near-limit records (and the
+        // materials' fetch), resolve, (view mips,) interleave
         b->disp[i]->launches += (b->mesh[i]->n_tris ? (b->mesh[i]->mat_tex ? 8 : 7) : 2) + (b->disp[i]->ss_level > 0);
     }
     b->disp[0]->launches += 1;

@@ -15,6 +15,7 @@ constexpr int kMaxRenderViews = 512;
 constexpr int kMaxCell = 65535;          // lattice indices are stored as u16
 constexpr int kMaxLevels = 16;           // mip levels of a texture (16384 = 2^14 texels a side)
 constexpr int kSetupThreads = 256;       // triangles per set-up / emit block
+constexpr uint32_t kEmitBig = 128;       // points above which a triangle is emitted by a whole warp
 constexpr float kBoxPad = 1.0f / 256.0f; // margin (pixels) of candidate pixel ranges against rounding
                                          // (projection error is about 1e-4 pixel)
 

@@ -8,7 +8,8 @@
 //            total point count, overflow flag.
 //   k_emit   one thread per triangle: warp-shuffle block scan of the counts
 //            plus the block offset gives each triangle's first point id; the
-//            column walk writes (triangle, cell) for each of its points.
+//            column walk writes (triangle, cell) for each of its points (a
+//            warp per triangle of more than kEmitBig points).
 //   k_fetch  one thread per point: texture coordinate of the cell centre and
 //            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7); then the
 //            point's splat record (its cell projected into the views) and, if
@@ -447,11 +448,38 @@ __global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
     }
 }
 
+// The points of triangle t from point id p on, in (column, row) order: a
+// single thread (lanes = 1) or a warp's lanes side by side in each column.
+__device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint32_t p, int lane, int lanes) {
+    const TriRec* rp = a.rec + t;
+    TriRec r;
+    r.q[0] = rp->q[0]; r.q[1] = rp->q[1]; r.q[2] = rp->q[2]; r.q[3] = rp->q[3];
+    r.q[4] = rp->q[4]; r.q[5] = rp->q[5];
+    float U[3], V[3];
+    shifted_uv(r, U, V);
+    const float su = r.q[0].w, sv = r.q[1].w, umax = r.q[5].w;
+    const int cols = int(ceilf(__fdiv_rn(umax, su)));
+    for (int i = 0; i < cols; i++) {
+        int j0, j1;
+        column_rows(U, V, su, sv, umax, i, &j0, &j1);
+        for (int j = j0 + lane; j < j1; j += lanes) {
+            const uint32_t q = p + uint32_t(j - j0);
+            if (LFDPR_IN_BOUNDS(q, a.max_points, 4))
+                *reinterpret_cast<uint2*>(a.points + q) = make_uint2(t, uint32_t(i) | (uint32_t(j) << 16));
+        }
+        p += uint32_t(j1 - j0);
+    }
+}
+
 // Block-level exclusive scan of the counts (warp shuffles), plus the block's
 // offset: each triangle's first point id. Then emit its points in (column,
-// row) order.
+// row) order; the block's triangles of more than kEmitBig points are listed
+// in shared memory and emitted afterwards by the block's warps, a warp each,
+// so that one thread does not walk tens of thousands of points.
 __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
     __shared__ uint32_t s_warp[kSetupThreads / 32];
+    __shared__ uint32_t s_big[kSetupThreads], s_first[kSetupThreads];
+    __shared__ uint32_t s_nbig;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t cnt = t < a.n_tris ? a.counts[t] : 0u;
@@ -462,6 +490,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
         if (lane >= o) inc += n;
     }
     if (lane == 31) s_warp[warp] = inc;
+    if (threadIdx.x == 0) s_nbig = 0u;
     __syncthreads();
     if (warp == 0) {
         uint32_t w = lane < kSetupThreads / 32 ? s_warp[lane] : 0u;
@@ -473,28 +502,20 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
         if (lane < kSetupThreads / 32) s_warp[lane] = w;
     }
     __syncthreads();
-    if (t >= a.n_tris) return;
-    const uint32_t first = a.block_sums[blockIdx.x] + (warp > 0 ? s_warp[warp - 1] : 0u) + inc - cnt;
-    a.offsets[t] = first;
-    if (cnt == 0 || a.ctr->overflow) return;
-    const TriRec* rp = a.rec + t;
-    TriRec r;
-    r.q[0] = rp->q[0]; r.q[1] = rp->q[1]; r.q[2] = rp->q[2]; r.q[3] = rp->q[3];
-    r.q[4] = rp->q[4]; r.q[5] = rp->q[5];
-    float U[3], V[3];
-    shifted_uv(r, U, V);
-    const float su = r.q[0].w, sv = r.q[1].w, umax = r.q[5].w;
-    const int cols = int(ceilf(__fdiv_rn(umax, su)));
-    uint32_t p = first;
-    for (int i = 0; i < cols; i++) {
-        int j0, j1;
-        column_rows(U, V, su, sv, umax, i, &j0, &j1);
-        for (int j = j0; j < j1; j++) {
-            if (LFDPR_IN_BOUNDS(p, a.max_points, 4))
-                *reinterpret_cast<uint2*>(a.points + p) = make_uint2(t, uint32_t(i) | (uint32_t(j) << 16));
-            p++;
+    const bool overflow = a.ctr->overflow != 0u;
+    if (t < a.n_tris) {
+        const uint32_t first = a.block_sums[blockIdx.x] + (warp > 0 ? s_warp[warp - 1] : 0u) + inc - cnt;
+        a.offsets[t] = first;
+        if (cnt > kEmitBig && !overflow) {
+            const uint32_t b = atomicAdd(&s_nbig, 1u);
+            s_big[b] = t;
+            s_first[b] = first;
+        } else if (cnt > 0 && !overflow) {
+            emit_points(a, t, first, 0, 1);
         }
     }
+    __syncthreads();
+    for (uint32_t b = uint32_t(warp); b < s_nbig; b += kSetupThreads / 32) emit_points(a, s_big[b], s_first[b], lane, 32);
 }
 
 // The two trilinear fetches of a point (Sec. 3.3: tv_min at lod_a, tv_max at

@@ -208,3 +208,36 @@ def test_view_bands_give_the_same_frame(band):
     assert np.array_equal(g0.panel, g1.panel)
     assert g1.stats.n_splat_writes == g0.stats.n_splat_writes
     assert st.stage_ms[lfdpr.STAGES.index("splat")] > 0.0 and st.stage_ms[lfdpr.STAGES.index("resolve")] > 0.0
+
+
+def large_triangles_scene():
+    """Triangles of a few hundred to tens of thousands of points each on the
+    paper-shaped display (fine textures, so Eq. 3 keeps the cells at pixel
+    size), with slanted edges for ragged columns, and some small ones."""
+    rng = np.random.default_rng(12)
+    tris = [[[-0.9, -0.8, 0.2], [0.7, -0.9, -0.3], [-0.6, 0.9, 0.1]],
+            [[0.1, 0.1, 0.5], [0.5, 0.15, 0.4], [0.2, 0.6, 0.45]],
+            [[-0.3, -0.2, 0.8], [-0.1, -0.25, 0.7], [-0.2, 0.05, 0.75]],
+            [[0.3, -0.7, -0.5], [0.8, -0.2, -0.9], [0.35, -0.1, -0.4]]]
+    for _ in range(40):
+        c = rng.uniform(-0.8, 0.8, 3)
+        tris.append((c + rng.normal(0.0, 0.02, (3, 3))).tolist())
+    tris = np.asarray(tris, np.float32)
+    n = len(tris)
+    uv = rng.uniform(0.0, 4.0, (n * 3, 2)).astype(np.float32)
+    tex = rng.integers(0, 256, (1024, 1024, 4), dtype=np.uint8)
+    return S.Scene(xyz=tris.reshape(-1, 3), uv=uv, idx=np.arange(3 * n, dtype=np.uint32).reshape(n, 3),
+                   tri_tex=np.zeros(n, np.uint32), textures=[tex])
+
+
+def test_large_triangles_emit_the_oracle_point_set():
+    """Triangles of more than 128 points are emitted by a warp each
+    (k_emit_big): counts and the whole point set bit-exact, views as usual."""
+    d = S.display_paper()
+    sc = large_triangles_scene()
+    m = S.model_matrix(2)
+    o = O.render(d, sc, m, views=[0, 47], panel=False)
+    assert o.counts.max() > 10000 and (o.counts > 128).sum() >= 3 and (o.counts[o.counts > 0] <= 128).sum() >= 10
+    g = gpu_frame(d, sc, m, panel=False)
+    check_sampling(g, o, "large triangles")
+    check_views(g, o, views=[0, 47], msg="large triangles")

@@ -111,6 +111,37 @@ def test_noalloc_with_angular_supersampling_matches_the_regular_entry_point(setu
         assert np.array_equal(pts[:n, :2], ref_pts)
 
 
+def test_noalloc_with_large_triangles_matches_the_regular_entry_point():
+    """Triangles of more than 128 points (a warp writes each one's points,
+    its list held in the fixed scratch)."""
+    import sys
+    import os
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_gpu_parity import large_triangles_scene
+    d = S.display_paper()
+    sc = large_triangles_scene()
+    dev = torch.device("cuda")
+    bufs = dict(xyz=torch.from_numpy(sc.xyz).to(dev), uv=torch.from_numpy(sc.uv).to(dev),
+                idx=torch.from_numpy(sc.idx.astype(np.int32)).to(dev),
+                tri_tex=torch.from_numpy(sc.tri_tex.astype(np.int32)).to(dev))
+    wh = np.array([[t.shape[1], t.shape[0]] for t in sc.textures], np.uint32)
+    s = torch.cuda.current_stream()
+    with lfdpr.Renderer(d, sc) as R:
+        m = S.model_matrix(2)
+        R.render(m, s)
+        st = R.stats(s)
+        b = R.buffers()
+        n = int(st.n_points)
+        ref_counts = lfdpr.device_to_numpy(b.counts, (sc.n_tris,), np.uint32)
+        ref_pts = lfdpr.device_to_numpy(b.points, (n, 4), np.uint32)[:, :2]
+        assert ref_counts.max() > 10000
+        pts, counts, fc = _noalloc(d, sc, bufs, wh, m, n, s)
+        assert fc[0] == n and fc[1] == 0
+        assert np.array_equal(counts, ref_counts)
+        assert np.array_equal(pts[:n, :2], ref_pts)
+
+
 def test_noalloc_reports_overflow_without_writing(setup):
     import torch
     d, sc, bufs, wh = setup
