@@ -217,13 +217,16 @@ def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin
 # Offline training on view stacks the library renders
 # ---------------------------------------------------------------------------
 
-def train(out_path: str, iters: int = 20000, n_scenes: int = 12, seed: int = 0, lr: float = 1e-3,
-          log_every: int = 1000, eval_frames: int = 8):
-    """Train on `iters` stacks: each is a random training scene (procedural,
-    seeds disjoint from the evaluation scene) at a random rotation, rendered
-    by the library as the n-view input and the 2x-angular full display whose
-    tent reconstruction is the target. Writes the weights (npz) and returns
-    the evaluation PSNR/SSIM on the paper-shaped scene."""
+def train(out_path: str, iters: int = 20000, n_scenes: int = 200, seed: int = 0, lr: float = 1e-3,
+          log_every: int = 1000, eval_frames: int = 8, pool: int = 16):
+    """Train on `iters` stacks: each is a random training scene at a random
+    camera pose (a turn about the vertical, a tilt of up to 15 degrees and a
+    shift of up to 0.15), rendered by the library as the n-view input and the
+    2x-angular full display whose tent reconstruction is the target. The
+    scenes are n_scenes procedurally seeded ones (seeds disjoint from the
+    evaluation scene's): `pool` of them are uploaded at a time, and one is
+    replaced by the next new scene every iters / n_scenes stacks. Writes the
+    weights (npz) and returns the timing."""
     torch = _torch()
     from . import build, lfdpr, scenes as S
 
@@ -240,11 +243,30 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 12, seed: int = 0, 
     ts = lfdpr.TextureSet(S.textures_paper())
     disp_in = lfdpr.lfdpr_create_display(lfdpr.desc_of(d_in, 1 << 23))
     disp_full = lfdpr.lfdpr_create_display(lfdpr.desc_of(d_full, 1 << 23))
-    meshes = []
-    for k in range(n_scenes):
+    pool = min(pool, n_scenes)
+    scene_no = [0]
+
+    def new_scene():
+        k = scene_no[0]
+        scene_no[0] += 1
         sc = S.geometry_paper(n_instances=int(rng.integers(80, 320)), seed=1000 + 17 * k)
-        meshes.append((lfdpr.lfdpr_upload_mesh_textured(disp_in, sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle),
-                       lfdpr.lfdpr_upload_mesh_textured(disp_full, sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle)))
+        return (lfdpr.lfdpr_upload_mesh_textured(disp_in, sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle),
+                lfdpr.lfdpr_upload_mesh_textured(disp_full, sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle))
+
+    meshes = [new_scene() for _ in range(pool)]
+    replace_every = max(1, iters // max(1, n_scenes - pool))
+
+    def pose():
+        yaw = math.radians(float(rng.uniform(0.0, 360.0)))
+        tilt = math.radians(float(rng.uniform(-15.0, 15.0)))
+        cy, sy, ct, st = math.cos(yaw), math.sin(yaw), math.cos(tilt), math.sin(tilt)
+        ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+        rx = np.array([[1, 0, 0], [0, ct, -st], [0, st, ct]])
+        m = np.eye(4)
+        m[:3, :3] = rx @ ry
+        m[:3, 3] = rng.uniform(-0.15, 0.15, 3)
+        return m.astype(np.float32)
+
     model = make_unet(nin).to(dev)
     opt = torch.optim.Adam(model.parameters(), lr=lr)
     sched = torch.optim.lr_scheduler.OneCycleLR(opt, max_lr=lr, total_steps=iters, pct_start=0.05)
@@ -263,9 +285,14 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 12, seed: int = 0, 
         return v_in, v_full
 
     for it in range(iters):
-        k = int(rng.integers(n_scenes))
-        ang = float(rng.uniform(0.0, 360.0))
-        mm = S.model_matrix(1, deg_per_frame=ang)
+        if it > 0 and it % replace_every == 0 and scene_no[0] < n_scenes:
+            slot = (scene_no[0] - pool) % pool
+            torch.cuda.synchronize()
+            lfdpr.lfdpr_destroy_mesh(meshes[slot][0])
+            lfdpr.lfdpr_destroy_mesh(meshes[slot][1])
+            meshes[slot] = new_scene()
+        k = int(rng.integers(pool))
+        mm = pose()
         v_in, v_full = stack(meshes[k][0], meshes[k][1], mm)
         x = network_input(v_in, nin, hp, wp)
         tgt = tent_views(v_full).permute(0, 3, 1, 2).reshape(1, -1, H, W).float() / 255.0
@@ -284,14 +311,15 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 12, seed: int = 0, 
     train_s = time.time() - t0
     w, b = export(model)
     np.savez(out_path, weights=w, biases=b, in_views=np.int32(nin), view_w=np.int32(W), view_h=np.int32(H),
-             iters=np.int32(iters), seed=np.int32(seed), loss_history=np.array(hist, np.float64))
+             iters=np.int32(iters), seed=np.int32(seed), scenes=np.int32(scene_no[0]),
+             loss_history=np.array(hist, np.float64))
     for m_in, m_full in meshes:
         lfdpr.lfdpr_destroy_mesh(m_in)
         lfdpr.lfdpr_destroy_mesh(m_full)
     lfdpr.lfdpr_destroy_display(disp_in)
     lfdpr.lfdpr_destroy_display(disp_full)
     ts.close()
-    return {"setup_s": setup_s, "train_s": train_s, "iters": iters}
+    return {"setup_s": setup_s, "train_s": train_s, "iters": iters, "scenes": scene_no[0]}
 
 
 def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=range(0, 120, 15), stream=None):
@@ -350,7 +378,7 @@ if __name__ == "__main__":
     p = argparse.ArgumentParser(description="train the angular reconstruction network")
     p.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "recon_weights.npz"))
     p.add_argument("--iters", type=int, default=20000)
-    p.add_argument("--scenes", type=int, default=12)
+    p.add_argument("--scenes", type=int, default=200)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--eval", action="store_true", help="evaluate the written weights on the paper-shaped scene")
