@@ -207,13 +207,23 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
 
     // closest and farthest eye (Fig. 5): height over the plane plus the
     // in-plane distance to the 2-D triangle; min and max over every rendered
-    // view. exact_d2(v) is the defining formula for view v. Only views that
-    // can hold the minimum or the maximum are evaluated with it: cheap bounds
-    // h^2 + max(0, |q - c| - R)^2 <= d_v^2 <= h^2 + |q - c|^2 (c the 2-D
-    // centroid, R the largest vertex distance from it, both widened against
-    // rounding) rule the others out against the exact values of the view
-    // whose eye is nearest the triangle's centroid and of the two end views.
-    // The result equals the minimum and maximum over all views.
+    // view. exact_d2(v) is the defining formula for view v, and the result
+    // equals its minimum and maximum over all views; views that cannot hold
+    // either are ruled out without evaluating them:
+    // - f(x), the exact squared distance from the eye at x to the triangle of
+    //   this same binary32 frame, is convex in x: a squared distance to a
+    //   convex set, taken along a line. exact_d2(v) is within E of f(x_v),
+    //   E = 2^-18 (S + L)^2 = 64 u (S + L)^2 (u = 2^-24), S bounding |q|_1
+    //   over the eyes and L the 2-D extent |a1| + |b1| + |a2| + |b2|: the
+    //   rounding of the dot products, edge tests and segment distances stays
+    //   below 30 u (S + L)^2, and the rest covers the tests' own rounding.
+    // - Minimum: walking from a start view, once a view's value exceeds the
+    //   one before it by 2E, f does not decrease from there on, so every later
+    //   view computes at least that value - 2E, which is at least the value
+    //   before it: no later view can lower the minimum. The same walking back.
+    // - Maximum: between two evaluated views a < b, f lies under its chord,
+    //   so the views strictly between compute at most the chord + 2E; the
+    //   chord is largest at the view next to a or the one next to b.
     const float ie01 = seg_inv_len2(0.0f, 0.0f, a1, b1), ie12 = seg_inv_len2(a1, b1, a2, b2);
     const float ie20 = seg_inv_len2(a2, b2, 0.0f, 0.0f);
     const float qy = 0.0f - P[0][1], qz = c.D - P[0][2];
@@ -231,44 +241,56 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
                        seg_dist2(a2, b2, 0.0f, 0.0f, ie20, qu, qv));
         return fmaf(h, h, d2);
     };
-    const int vs = nearest_eye(a.ex, c.nr, (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f));
-    float d2min = exact_d2(vs), d2max = d2min;
-    {
-        const float e0 = exact_d2(0), e1 = exact_d2(c.nr - 1);
-        d2min = fminf(d2min, fminf(e0, e1));
-        d2max = fmaxf(d2max, fmaxf(e0, e1));
+    const int nr = c.nr;
+    const float x_first = a.ex[0], x_last = a.ex[nr - 1];
+    const float S = fmaxf(fabsf(x_first - P[0][0]), fabsf(x_last - P[0][0])) * 1.0001f + fabsf(qy) + fabsf(qz);
+    const float SL = S + ((fabsf(a1) + fabsf(b1)) + (fabsf(a2) + fabsf(b2)));
+    const float E2 = 0x1p-17f * (SL * SL);   // 2E
+    const int g = nearest_eye(a.ex, nr, (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f));
+    const float fg = exact_d2(g);
+    float d2min = fg, d2max = fg;
+    int hi = g, lo = g;
+    float f_at_hi = fg, f_at_lo = fg;   // the values of views hi and lo
+    while (hi + 1 < nr) {
+        const float f = exact_d2(++hi);
+        d2min = fminf(d2min, f);
+        d2max = fmaxf(d2max, f);
+        const bool rising = f - f_at_hi >= E2;
+        f_at_hi = f;
+        if (rising) break;
     }
-    {
-        const float cu = (a1 + a2) * (1.0f / 3.0f), cv = (b1 + b2) * (1.0f / 3.0f);
-        const float r0 = fmaf(cu, cu, cv * cv);
-        const float r1 = fmaf(a1 - cu, a1 - cu, (b1 - cv) * (b1 - cv));
-        const float r2 = fmaf(a2 - cu, a2 - cu, (b2 - cv) * (b2 - cv));
-        const float R = sqrtf(fmaxf(fmaxf(r0, r1), r2)) * 1.0001f + 1e-7f;
-        const float ku = fmaf(qy, uy, qz * uz), kv = fmaf(qy, vy, qz * vz), kh = fmaf(qy, ny, qz * nz);
-        for (int blk = 0; blk < c.nr; blk += 64) {
-            const int nb = c.nr - blk < 64 ? c.nr - blk : 64;
-            unsigned long long mask = 0ull;
-            for (int b = 0; b < nb; b++) {
-                const float qx = a.ex[blk + b] - P[0][0];
-                const float du = fmaf(qx, ux, ku) - cu, dv = fmaf(qx, vx, kv) - cv;
-                const float h = fmaf(qx, nx, kh);
-                const float hh = h * h;
-                const float rho2 = fmaf(du, du, dv * dv);
-                const float rho = rho2 * rsqrtf(fmaxf(rho2, 1e-30f));
-                const float g = fmaxf(fmaf(rho, 0.99999f, -R), 0.0f);
-                const float lo = fmaf(g, g, hh) * 0.9999f - 1e-12f;
-                const float hi = (hh + rho2) * 1.0001f + 1e-12f;
-                if (lo < d2min || hi > d2max) mask |= 1ull << b;
-            }
-            while (mask) {
-                const int b = __ffsll((long long)mask) - 1;
-                mask &= mask - 1ull;
-                const float e = exact_d2(blk + b);
-                d2min = fminf(d2min, e);
-                d2max = fmaxf(d2max, e);
-            }
-        }
+    while (lo > 0) {
+        const float f = exact_d2(--lo);
+        d2min = fminf(d2min, f);
+        d2max = fmaxf(d2max, f);
+        const bool rising = f - f_at_lo >= E2;
+        f_at_lo = f;
+        if (rising) break;
     }
+    float f_first = 0.0f, f_last = 0.0f;
+    if (lo > 0) {
+        f_first = exact_d2(0);
+        d2max = fmaxf(d2max, f_first);
+    }
+    if (hi < nr - 1) {
+        f_last = exact_d2(nr - 1);
+        d2max = fmaxf(d2max, f_last);
+    }
+    // the two gaps (0, lo) and (hi, nr - 1); d2max is final unless a gap
+    // fails its chord test, and then that gap is evaluated view by view
+    auto gap_clear = [&](int ga, int gb, float fa, float fb) -> bool {
+        const float xa = a.ex[ga], span = a.ex[gb] - xa;
+        if (!(span > 0.0f)) return false;
+        const float t1 = (a.ex[ga + 1] - xa) / span, t2 = (a.ex[gb - 1] - xa) / span;
+        const float cmax = fmaxf(fmaf(fb - fa, t1, fa), fmaf(fb - fa, t2, fa));
+        return cmax + E2 <= d2max;
+    };
+    const bool clear_lo = lo < 2 || gap_clear(0, lo, f_first, f_at_lo);
+    const bool clear_hi = hi > nr - 3 || gap_clear(hi, nr - 1, f_at_hi, f_last);
+    if (!clear_lo)
+        for (int v = 1; v < lo; v++) d2max = fmaxf(d2max, exact_d2(v));
+    if (!clear_hi)
+        for (int v = hi + 1; v < nr - 1; v++) d2max = fmaxf(d2max, exact_d2(v));
     const float dmin = fmaxf(__fsqrt_rn(d2min), c.near_z);
     const float dmax = fmaxf(__fsqrt_rn(d2max), c.near_z);
 
