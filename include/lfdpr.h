@@ -255,10 +255,12 @@ lfdpr_status lfdpr_render_frame(lfdpr_display *disp, lfdpr_mesh *mesh, const flo
  * lfdpr_interleave: build the elemental image array from the last frame's
  * views (Sec. 4): optional tent reconstruction of 2N supersampled views, then
  * optional crosstalk mixing, then the slanted-lens subpixel interleave.
- * `panel_rgba8` is u8 [panel_h][panel_w][4], caller-owned, in device memory or
- * in host memory (pinned or pageable); for host memory the panel is built in
- * device scratch and copied back on `stream`, and the call returns after the
- * copy has completed. Errors: EINVAL, ECUDA.
+ * `panel_rgba8` is u8 [panel_h][panel_w][4], caller-owned, in device memory
+ * (4-byte aligned) or in host memory (pinned or pageable). Pinned host memory
+ * is written by the interleave kernels through its device mapping; pageable
+ * memory gets the panel built in device scratch and copied back on `stream`.
+ * For host memory the call returns once the panel is complete there.
+ * Errors: EINVAL (also a device panel not 4-byte aligned), ECUDA.
  */
 lfdpr_status lfdpr_interleave(lfdpr_display *disp, uint8_t *panel_rgba8, void *stream);
 

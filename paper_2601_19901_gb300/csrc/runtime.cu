@@ -833,13 +833,23 @@ lfdpr_status lfdpr_interleave(lfdpr_display* disp, uint8_t* panel_rgba8, void* s
     g_err[0] = 0;
     if (!disp || !panel_rgba8) return fail(LFDPR_EINVAL, "interleave: null argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // device memory is written in place; pinned host memory through its
+    // device mapping (the kernels' stores cross the host link, and no copy
+    // follows); pageable memory by a copy of the device scratch panel
     cudaPointerAttributes at;
     bool on_device = false;
-    if (cudaPointerGetAttributes(&at, panel_rgba8) == cudaSuccess)
+    uint8_t* mapped = nullptr;
+    if (cudaPointerGetAttributes(&at, panel_rgba8) == cudaSuccess) {
         on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-    else
+        if (at.type == cudaMemoryTypeHost && at.devicePointer &&
+            (reinterpret_cast<uintptr_t>(at.devicePointer) & 3u) == 0)
+            mapped = static_cast<uint8_t*>(at.devicePointer);
+    } else {
         cudaGetLastError();
-    uint8_t* dst = on_device ? panel_rgba8 : disp->panel;
+    }
+    if (on_device && (reinterpret_cast<uintptr_t>(panel_rgba8) & 3u) != 0)
+        return fail(LFDPR_EINVAL, "interleave: a device panel must be 4-byte aligned");
+    uint8_t* dst = on_device ? panel_rgba8 : mapped ? mapped : disp->panel;
     mark(disp, LFDPR_N_STAGES, s);
     if ((disp->desc.recon == 2 || disp->desc.recon == 3) && disp->n_samples == 0)
         return fail(LFDPR_EINVAL, "interleave: Gaussian reconstruction needs lfdpr_set_recon_samples");
@@ -847,7 +857,9 @@ lfdpr_status lfdpr_interleave(lfdpr_display* disp, uint8_t* panel_rgba8, void* s
     if (st != LFDPR_OK) return st;
     mark(disp, LFDPR_N_STAGES + 1, s);
     disp->ev_interleave = disp->timing;
-    if (!on_device) {
+    if (mapped) {
+        CK(cudaStreamSynchronize(s), "interleave: synchronize");
+    } else if (!on_device) {
         const uint64_t bytes = 4u * uint64_t(disp->dc.Wp) * disp->dc.Hp;
         CK(cudaMemcpyAsync(panel_rgba8, disp->panel, bytes, cudaMemcpyDeviceToHost, s), "interleave: copy to host");
         CK(cudaStreamSynchronize(s), "interleave: synchronize");

@@ -82,11 +82,23 @@ def test_several_frames_on_one_renderer_match_fresh_frames():
             check_views(g, o)
 
 
-def test_host_panel_equals_device_panel():
+@pytest.mark.parametrize("variant", ["tent", "supersampled", "gauss", "view_mips", "odd_width"])
+def test_host_panel_equals_device_panel(variant):
+    """Device, pinned host (written through its device mapping) and pageable
+    host panels (a copy of the device scratch) hold the same bytes, for every
+    interleave kernel; pinned memory at a 4-byte offset too."""
     import torch
-    d = S.display_tiny()
+    base = S.display_tiny()
+    d = {"tent": base,
+         "supersampled": replace(base, recon=1, crosstalk=0.15),
+         "gauss": replace(base, recon=2, crosstalk=0.15),
+         "view_mips": replace(base, view_w=256, view_h=256, ss_level=1),
+         "odd_width": replace(base, panel_w=509, panel_h=131)}[variant]
     sc = S.scene_tiny()
     with lfdpr.Renderer(d, sc) as R:
+        if variant == "gauss":
+            R.set_view_jitter(np.random.default_rng(1).random(d.n_render_views).astype(np.float32))
+            R.set_recon_samples((np.random.default_rng(2).normal(0.0, 0.3, (8, 3))).astype(np.float32))
         s = torch.cuda.current_stream()
         R.render(S.model_matrix(3), s)
         dev = torch.zeros((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
@@ -95,9 +107,28 @@ def test_host_panel_equals_device_panel():
         R.interleave(host.data_ptr(), s)
         pageable = np.zeros((d.panel_h, d.panel_w, 4), np.uint8)
         R.interleave(pageable.ctypes.data, s)
+        nb = d.panel_h * d.panel_w * 4
+        shifted = torch.zeros(nb + 16, dtype=torch.uint8).pin_memory()
+        R.interleave(shifted.data_ptr() + 4, s)
         torch.cuda.synchronize()
-        assert np.array_equal(dev.cpu().numpy(), host.numpy())
-        assert np.array_equal(host.numpy(), pageable)
+        ref = dev.cpu().numpy()
+        assert ref.any()
+        assert np.array_equal(ref, host.numpy())
+        assert np.array_equal(ref, pageable)
+        assert np.array_equal(ref.reshape(-1), shifted.numpy()[4:4 + nb])
+
+
+def test_device_panel_must_be_4_byte_aligned():
+    import torch
+    d = S.display_tiny()
+    with lfdpr.Renderer(d, S.scene_tiny()) as R:
+        s = torch.cuda.current_stream()
+        R.render(S.model_matrix(3), s)
+        buf = torch.zeros(d.panel_h * d.panel_w * 4 + 16, dtype=torch.uint8, device="cuda")
+        with pytest.raises(lfdpr.LfdprError, match="4-byte aligned"):
+            R.interleave(buf.data_ptr() + 2, s)
+        R.interleave(buf.data_ptr() + 4, s)   # 4-byte aligned, not 16: the narrow stores
+        torch.cuda.synchronize()
 
 
 # ---------------------------------------------------------------------------
