@@ -92,41 +92,59 @@ __device__ bool culled(const DispConst& c, const float* __restrict__ ex, const f
     return true;
 }
 
-// Rows [j0, j1) of lattice column i overlapping the triangle (conservative
-// rule): the triangle's v range over the column slab [i s_u, (i+1) s_u]
-// from the vertices inside the slab and the edge crossings of its borders.
-__device__ __forceinline__ int column_rows(const float U[3], const float V[3], float su, float sv,
-                                           float umax, int i, int* j0, int* j1) {
-    const float a = float(i) * su;
-    const float b = fminf(float(i + 1) * su, umax);
-    float lo = INFINITY, hi = -INFINITY;
+// The lattice columns of a triangle, in order: rows [j0, j1) of column i
+// overlapping it (conservative rule) span its v range over the column slab
+// [i s_u, min((i+1) s_u, u_max)], from the vertices inside the slab and the
+// edge crossings of the slab's two borders. For every column i < ceil(u_max /
+// s_u), i s_u <= u_max, so a column's left border is exactly the right border
+// of the one before: its crossings are carried over, not recomputed.
+struct ColumnWalk {
+    float U[3], V[3], su, sv, umax;
+    float lo_b, hi_b;   // v range of the edge crossings of the last right border
+
+    __device__ __forceinline__ void crossings(float x, float& lo, float& hi) const {
+        lo = INFINITY;
+        hi = -INFINITY;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        if (U[k] >= a && U[k] <= b) { lo = fminf(lo, V[k]); hi = fmaxf(hi, V[k]); }
-    }
-#pragma unroll
-    for (int e = 0; e < 3; e++) {
-        const int p = e, r = e == 2 ? 0 : e + 1;
-        if (U[p] == U[r]) continue;
-        const float umn = fminf(U[p], U[r]), umx = fmaxf(U[p], U[r]);
-        const float du = U[r] - U[p], dv = V[r] - V[p];
-        if (a >= umn && a <= umx) {
-            const float vx = fmaf(__fdiv_rn(a - U[p], du), dv, V[p]);
-            lo = fminf(lo, vx);
-            hi = fmaxf(hi, vx);
-        }
-        if (b >= umn && b <= umx) {
-            const float vx = fmaf(__fdiv_rn(b - U[p], du), dv, V[p]);
-            lo = fminf(lo, vx);
-            hi = fmaxf(hi, vx);
+        for (int e = 0; e < 3; e++) {
+            const int p = e, r = e == 2 ? 0 : e + 1;
+            if (U[p] == U[r]) continue;
+            const float umn = fminf(U[p], U[r]), umx = fmaxf(U[p], U[r]);
+            if (x >= umn && x <= umx) {
+                const float vx = fmaf(__fdiv_rn(x - U[p], U[r] - U[p]), V[r] - V[p], V[p]);
+                lo = fminf(lo, vx);
+                hi = fmaxf(hi, vx);
+            }
         }
     }
-    if (lo > hi) { *j0 = 0; *j1 = 0; return 0; }
-    *j0 = int(floorf(__fdiv_rn(lo, sv)));
-    *j1 = int(ceilf(__fdiv_rn(hi, sv)));
-    if (*j1 < *j0) *j1 = *j0;
-    return *j1 - *j0;
-}
+    __device__ __forceinline__ ColumnWalk(const float U_[3], const float V_[3], float su_, float sv_, float umax_)
+        : su(su_), sv(sv_), umax(umax_) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            U[k] = U_[k];
+            V[k] = V_[k];
+        }
+        crossings(float(0) * su, lo_b, hi_b);
+    }
+    // column i: call for i = 0, 1, 2, ... in turn
+    __device__ __forceinline__ int rows(int i, int* j0, int* j1) {
+        const float a = float(i) * su;
+        const float b = fminf(float(i + 1) * su, umax);
+        float lo = lo_b, hi = hi_b;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (U[k] >= a && U[k] <= b) { lo = fminf(lo, V[k]); hi = fmaxf(hi, V[k]); }
+        }
+        crossings(b, lo_b, hi_b);
+        lo = fminf(lo, lo_b);
+        hi = fmaxf(hi, hi_b);
+        if (lo > hi) { *j0 = 0; *j1 = 0; return 0; }
+        *j0 = int(floorf(__fdiv_rn(lo, sv)));
+        *j1 = int(ceilf(__fdiv_rn(hi, sv)));
+        if (*j1 < *j0) *j1 = *j0;
+        return *j1 - *j0;
+    }
+};
 
 __device__ __forceinline__ void shifted_uv(const TriRec& r, float U[3], float V[3]) {
     const float umin = r.q[2].w, vmin = r.q[3].w;
@@ -140,7 +158,8 @@ struct SetupOut {
     bool cell_overflow;
 };
 
-__device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, TriProj& tp) {
+// ex: the rendered views' eye x, ascending (a copy in shared memory)
+__device__ SetupOut setup_triangle(const FrameArgs& a, const float* ex, uint32_t t, TriRec& r, TriProj& tp) {
     const DispConst& c = a.dc;
     SetupOut res{0u, false, false};
     float P[3][3], Q[3][2], M[12];
@@ -157,7 +176,7 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
 #pragma unroll
     for (int k = 0; k < 8; k++) r.q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     r.q[0] = make_float4(P[0][0], P[0][1], P[0][2], 0.0f);
-    if (culled(c, a.ex, P)) return res;
+    if (culled(c, ex, P)) return res;
 
     // area and unit normal
     float e1[3], e2[3];
@@ -228,7 +247,7 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     const float ie20 = seg_inv_len2(a2, b2, 0.0f, 0.0f);
     const float qy = 0.0f - P[0][1], qz = c.D - P[0][2];
     auto exact_d2 = [&](int v) -> float {
-        const float qx = a.ex[v] - P[0][0];
+        const float qx = ex[v] - P[0][0];
         const float qu = dot3(qx, qy, qz, ux, uy, uz);
         const float qv = dot3(qx, qy, qz, vx, vy, vz);
         const float h = dot3(qx, qy, qz, nx, ny, nz);
@@ -242,11 +261,11 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
         return fmaf(h, h, d2);
     };
     const int nr = c.nr;
-    const float x_first = a.ex[0], x_last = a.ex[nr - 1];
+    const float x_first = ex[0], x_last = ex[nr - 1];
     const float S = fmaxf(fabsf(x_first - P[0][0]), fabsf(x_last - P[0][0])) * 1.0001f + fabsf(qy) + fabsf(qz);
     const float SL = S + ((fabsf(a1) + fabsf(b1)) + (fabsf(a2) + fabsf(b2)));
     const float E2 = 0x1p-17f * (SL * SL);   // 2E
-    const int g = nearest_eye(a.ex, nr, (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f));
+    const int g = nearest_eye(ex, nr, (P[0][0] + P[1][0] + P[2][0]) * (1.0f / 3.0f));
     const float fg = exact_d2(g);
     float d2min = fg, d2max = fg;
     int hi = g, lo = g;
@@ -279,9 +298,9 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     // the two gaps (0, lo) and (hi, nr - 1); d2max is final unless a gap
     // fails its chord test, and then that gap is evaluated view by view
     auto gap_clear = [&](int ga, int gb, float fa, float fb) -> bool {
-        const float xa = a.ex[ga], span = a.ex[gb] - xa;
+        const float xa = ex[ga], span = ex[gb] - xa;
         if (!(span > 0.0f)) return false;
-        const float t1 = (a.ex[ga + 1] - xa) / span, t2 = (a.ex[gb - 1] - xa) / span;
+        const float t1 = (ex[ga + 1] - xa) / span, t2 = (ex[gb - 1] - xa) / span;
         const float cmax = fmaxf(fmaf(fb - fa, t1, fa), fmaf(fb - fa, t2, fa));
         return cmax + E2 <= d2max;
     };
@@ -367,9 +386,10 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, uint32_t t, TriRec& r, Tr
     if (!(ncol <= float(kMaxCell))) { res.cell_overflow = true; return res; }
     const int cols = int(ncol);
     uint32_t cnt = 0;
+    ColumnWalk walk(U, V, su, sv, umax);
     for (int i = 0; i < cols; i++) {
         int j0, j1;
-        const int rows = column_rows(U, V, su, sv, umax, i, &j0, &j1);
+        const int rows = walk.rows(i, &j0, &j1);
         if (j1 > kMaxCell + 1) { res.cell_overflow = true; return res; }
         cnt += uint32_t(rows);
     }
@@ -405,12 +425,15 @@ __device__ __forceinline__ T block_sum(T v, T* smem) {
 __global__ void __launch_bounds__(kSetupThreads, 4) k_setup(FrameArgs a) {
     __shared__ uint32_t s_cnt[kSetupThreads / 32];
     __shared__ uint32_t s_live[kSetupThreads / 32];
+    __shared__ float s_ex[kMaxRenderViews];
+    for (int v = threadIdx.x; v < a.dc.nr; v += blockDim.x) s_ex[v] = a.ex[v];
+    __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t count = 0, live = 0;
     if (t < a.n_tris) {
         TriRec r;
         TriProj tp;
-        const SetupOut o = setup_triangle(a, t, r, tp);
+        const SetupOut o = setup_triangle(a, s_ex, t, r, tp);
         TriRec* dst = a.rec + t;
 #pragma unroll
         for (int k = 0; k < 8; k++) dst->q[k] = r.q[k];
@@ -481,9 +504,10 @@ __device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint
     shifted_uv(r, U, V);
     const float su = r.q[0].w, sv = r.q[1].w, umax = r.q[5].w;
     const int cols = int(ceilf(__fdiv_rn(umax, su)));
+    ColumnWalk walk(U, V, su, sv, umax);
     for (int i = 0; i < cols; i++) {
         int j0, j1;
-        column_rows(U, V, su, sv, umax, i, &j0, &j1);
+        walk.rows(i, &j0, &j1);
         for (int j = j0 + lane; j < j1; j += lanes) {
             const uint32_t q = p + uint32_t(j - j0);
             if (LFDPR_IN_BOUNDS(q, a.max_points, 4))
