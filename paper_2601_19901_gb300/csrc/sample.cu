@@ -564,13 +564,45 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
     for (uint32_t b = uint32_t(warp); b < s_nbig; b += kSetupThreads / 32) emit_points(a, s_big[b], s_first[b], lane, 32);
 }
 
+// One mip level's bilinear sample at texture coordinates (fs, ft) in [0, 1):
+// wrap addressing, texel centres at (k+1/2)/w. Loading the four texels and
+// blending them are separate steps, so that every load of a point can be in
+// flight before the first blend.
+struct BilinearTap {
+    uint32_t tex[4];
+    float fx, fy;
+};
+__device__ __forceinline__ void bilinear_load(const uint8_t* __restrict__ pool, const uint64_t* __restrict__ loff,
+                                              uint32_t w, uint32_t h, int l, float fs, float ft, BilinearTap& b) {
+    const uint32_t lw = (w >> l) ? (w >> l) : 1u, lh = (h >> l) ? (h >> l) : 1u;
+    const float x = fmaf(fs, float(lw), -0.5f), y = fmaf(ft, float(lh), -0.5f);
+    const float xf = floorf(x), yf = floorf(y);
+    b.fx = x - xf;
+    b.fy = y - yf;
+    const uint32_t ix0 = uint32_t(int(xf)) & (lw - 1), iy0 = uint32_t(int(yf)) & (lh - 1);
+    const uint32_t ix1 = (ix0 + 1) & (lw - 1), iy1 = (iy0 + 1) & (lh - 1);
+    const uint32_t* T = reinterpret_cast<const uint32_t*>(pool + __ldg(loff + l));
+    b.tex[0] = __ldg(T + (size_t)iy0 * lw + ix0);
+    b.tex[1] = __ldg(T + (size_t)iy0 * lw + ix1);
+    b.tex[2] = __ldg(T + (size_t)iy1 * lw + ix0);
+    b.tex[3] = __ldg(T + (size_t)iy1 * lw + ix1);
+}
+__device__ __forceinline__ float bilinear_channel(const BilinearTap& b, int ch) {
+    const float va = float((b.tex[0] >> (8 * ch)) & 255u), vb = float((b.tex[1] >> (8 * ch)) & 255u);
+    const float vc = float((b.tex[2] >> (8 * ch)) & 255u), vd = float((b.tex[3] >> (8 * ch)) & 255u);
+    const float top = fmaf(b.fx, vb - va, va);
+    const float bot = fmaf(b.fx, vd - vc, vc);
+    return fmaf(b.fy, bot - top, top);
+}
+
 // The two trilinear fetches of a point (Sec. 3.3: tv_min at lod_a, tv_max at
 // lod_b). Each: LOD clamped to [0, L_max], level floor(LOD) blended to the
-// next by the fraction (FP32 weights), bilinear with wrap addressing and
-// texel centres at (k+1/2)/w, rounded half-even to RGBA8. All sixteen texel
-// loads are issued before any blending: per LOD, level floor(LOD) and the
-// next level (clamped to the last; unused when the fraction is 0). loff[l] is
-// the byte offset of level l in the pool.
+// next by the fraction (FP32 weights), bilinear, rounded half-even to RGBA8.
+// The levels are A = floor(lod_a), B = min(A + 1, L) and C = floor(lod_b),
+// D = min(C + 1, L) with C >= A; when C is A (then D is B) or C is B, those
+// levels' samples are shared instead of loaded and blended twice (the LOD
+// pair of a triangle mostly lies within one level). loff[l] is the byte
+// offset of level l in the pool.
 __device__ __forceinline__ void trilinear_pair(const uint8_t* __restrict__ pool, const uint64_t* __restrict__ loff,
                                                uint32_t w, uint32_t h, int L, float s, float t, float lod_a,
                                                float lod_b, uint32_t& out_a, uint32_t& out_b) {
@@ -579,50 +611,42 @@ __device__ __forceinline__ void trilinear_pair(const uint8_t* __restrict__ pool,
     const float fs = s - floorf(s), ft = t - floorf(t);
     float lods[2] = {lod_a, lod_b}, frac[2];
     int lev[2];
-    uint32_t tex[2][2][4];
-    float fx[2][2], fy[2][2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
         const float lod = fminf(fmaxf(lods[q], 0.0f), float(L));
         lev[q] = int(floorf(lod));
         frac[q] = lod - float(lev[q]);
+    }
+    const int A = lev[0], B = A + 1 > L ? L : A + 1, C = lev[1], D = C + 1 > L ? L : C + 1;
+    // C is A (then D is B) or B for almost every triangle: three taps, the
+    // third at D; C beyond B takes its own tap in place of A's for the
+    // second fetch
+    const bool far_c = C != A && C != B;
+    BilinearTap ta, tb, te;
+    bilinear_load(pool, loff, w, h, A, fs, ft, ta);
+    bilinear_load(pool, loff, w, h, B, fs, ft, tb);
+    bilinear_load(pool, loff, w, h, D, fs, ft, te);
+    uint32_t out[2] = {0u, 0u};
+    const bool blend0 = frac[0] > 0.0f && lev[0] < L, blend1 = frac[1] > 0.0f && lev[1] < L;
 #pragma unroll
-        for (int m = 0; m < 2; m++) {
-            const int l = lev[q] + m > L ? L : lev[q] + m;
-            const uint32_t lw = (w >> l) ? (w >> l) : 1u, lh = (h >> l) ? (h >> l) : 1u;
-            const float x = fmaf(fs, float(lw), -0.5f), y = fmaf(ft, float(lh), -0.5f);
-            const float xf = floorf(x), yf = floorf(y);
-            fx[q][m] = x - xf;
-            fy[q][m] = y - yf;
-            const uint32_t ix0 = uint32_t(int(xf)) & (lw - 1), iy0 = uint32_t(int(yf)) & (lh - 1);
-            const uint32_t ix1 = (ix0 + 1) & (lw - 1), iy1 = (iy0 + 1) & (lh - 1);
-            const uint32_t* T = reinterpret_cast<const uint32_t*>(pool + __ldg(loff + l));
-            tex[q][m][0] = __ldg(T + (size_t)iy0 * lw + ix0);
-            tex[q][m][1] = __ldg(T + (size_t)iy0 * lw + ix1);
-            tex[q][m][2] = __ldg(T + (size_t)iy1 * lw + ix0);
-            tex[q][m][3] = __ldg(T + (size_t)iy1 * lw + ix1);
+    for (int ch = 0; ch < 4; ch++) {
+        const float va = bilinear_channel(ta, ch), vb = bilinear_channel(tb, ch);
+        const float v0 = blend0 ? fmaf(frac[0], vb - va, va) : va;
+        out[0] |= uint32_t(round_u8(v0)) << (8 * ch);
+        if (!far_c) {
+            const float vc = C == A ? va : vb;
+            const float vd = C == A ? vb : bilinear_channel(te, ch);
+            const float v1 = blend1 ? fmaf(frac[1], vd - vc, vc) : vc;
+            out[1] |= uint32_t(round_u8(v1)) << (8 * ch);
         }
     }
-    uint32_t out[2] = {0u, 0u};
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        float cv[2][4];
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-#pragma unroll
-            for (int ch = 0; ch < 4; ch++) {
-                const float va = float((tex[q][m][0] >> (8 * ch)) & 255u), vb = float((tex[q][m][1] >> (8 * ch)) & 255u);
-                const float vc = float((tex[q][m][2] >> (8 * ch)) & 255u), vd = float((tex[q][m][3] >> (8 * ch)) & 255u);
-                const float top = fmaf(fx[q][m], vb - va, va);
-                const float bot = fmaf(fx[q][m], vd - vc, vc);
-                cv[m][ch] = fmaf(fy[q][m], bot - top, top);
-            }
-        }
-        const bool blend = frac[q] > 0.0f && lev[q] < L;
+    if (far_c) {
+        bilinear_load(pool, loff, w, h, C, fs, ft, ta);
 #pragma unroll
         for (int ch = 0; ch < 4; ch++) {
-            const float v = blend ? fmaf(frac[q], cv[1][ch] - cv[0][ch], cv[0][ch]) : cv[0][ch];
-            out[q] |= uint32_t(round_u8(v)) << (8 * ch);
+            const float vc = bilinear_channel(ta, ch), vd = bilinear_channel(te, ch);
+            const float v1 = blend1 ? fmaf(frac[1], vd - vc, vc) : vc;
+            out[1] |= uint32_t(round_u8(v1)) << (8 * ch);
         }
     }
     out_a = out[0];
@@ -847,11 +871,11 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
         if (!LFDPR_IN_BOUNDS(pt.x, a.n_tris, 5)) pt.x = 0;
         const TriRec* r = a.rec + pt.x;
-        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
-        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
+        // the texture map and spacings first; the frame (the same 128-byte
+        // line) after the fetch, so it does not stay live across the gathers
+        const float su = __ldg(&r->q[0].w), sv = __ldg(&r->q[1].w);
         const float4 q6 = __ldg(&r->q[6]), q7 = __ldg(&r->q[7]);
         const uint32_t i = pt.y & 0xffffu, j = pt.y >> 16;
-        const float su = q0.w, sv = q1.w;
         const float uc = (float(i) + 0.5f) * su;
         const float vc = (float(j) + 0.5f) * sv;
         const float s = fmaf(q6.y, uc, fmaf(q6.z, vc, q6.x));
@@ -863,7 +887,8 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         trilinear_pair(a.pool, a.lvl + (size_t)texid * kMaxLevels, td.w, td.h, int(td.levels) - 1, s, t, q7.z,
                        q7.w, tmin, tmax);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
-        const float4 q5 = __ldg(&r->q[5]);
+        const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
+        const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]), q5 = __ldg(&r->q[5]);
 
         // splat work record
         const TriProj tp = a.tproj[pt.x];
