@@ -272,3 +272,24 @@ def test_large_triangles_emit_the_oracle_point_set():
     g = gpu_frame(d, sc, m, panel=False)
     check_sampling(g, o, "large triangles")
     check_views(g, o, views=[0, 47], msg="large triangles")
+
+
+def test_consecutive_frames_scan_and_emit_like_the_oracle():
+    """Set-up, scan and emit over several frames in a row on one renderer,
+    each with its own model (one with nothing live): every count,
+    first-point offset and point bit-exact."""
+    d = S.display_paper()
+    sc = S.scene_paper(n_instances=24, res=24, n_textures=4, max_tex=256, min_tex=16, seed=9)
+    assert sc.n_tris > 40 * 256
+    with lfdpr.Renderer(d, sc) as R:
+        for k, f in enumerate((0, 17, 40, 17, 91)):
+            m = S.model_matrix(f)
+            if k == 3:
+                m = m.copy()
+                m[0, 3] += 5.0   # the whole mesh out of every view: nothing live
+            o = O.render(d, sc, m, splat=False)
+            g = gpu_frame(d, sc, m, panel=False, renderer=R)
+            assert g.stats.overflow == 0 and g.stats.n_points == len(o.points), (k, g.stats.n_points)
+            check_sampling(g, o, "frame %d" % k)
+            if k == 3:
+                assert g.stats.n_points == 0 and g.stats.n_live_tris == 0
