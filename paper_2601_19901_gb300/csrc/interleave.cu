@@ -26,18 +26,20 @@ namespace {
 struct GlobalTexels {
     const uint8_t* __restrict__ views;
     uint64_t npix, pix;
-    __device__ __forceinline__ float operator()(int view, int ch) const {
-        return float(__ldg(views + ((uint64_t)view * npix + pix) * 4u + ch));
+    __device__ __forceinline__ uint32_t byte(int view, int ch) const {
+        return __ldg(views + ((uint64_t)view * npix + pix) * 4u + ch);
     }
+    __device__ __forceinline__ float operator()(int view, int ch) const { return float(byte(view, ch)); }
 };
 
 // The same from a staged row segment: s[view * stride + i], RGBA8 words.
 struct SharedTexels {
     const uint32_t* s;
     int stride, i;
-    __device__ __forceinline__ float operator()(int view, int ch) const {
-        return float((s[view * stride + i] >> (8 * ch)) & 255u);
+    __device__ __forceinline__ uint32_t byte(int view, int ch) const {
+        return (s[view * stride + i] >> (8 * ch)) & 255u;
     }
+    __device__ __forceinline__ float operator()(int view, int ch) const { return float(byte(view, ch)); }
 };
 
 // Display view k, channel ch, as binary32 before rounding.
@@ -76,6 +78,13 @@ __device__ __forceinline__ int view_of_subpixel(const DispConst& c, int x, int y
 template <class T>
 __device__ __forceinline__ uint32_t panel_pixel(const DispConst& c, const T& tex, int x, int y) {
     uint32_t o = 0xff000000u;
+    if (c.recon != 1 && !(c.xtalk > 0.0f)) {
+        // each subpixel shows its view's byte as it is (a byte converted to
+        // binary32 and rounded back is the byte)
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) o |= tex.byte(view_of_subpixel(c, x, y, ch), ch) << (8 * ch);
+        return o;
+    }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
         const int k = view_of_subpixel(c, x, y, ch);
