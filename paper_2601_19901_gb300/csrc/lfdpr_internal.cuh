@@ -304,6 +304,7 @@ struct FrameArgs {
     int sm_count;
     uint32_t splat_lane_limit;       // candidates per lane above which a splat unit is walked lane by lane
     int view_lo, view_hi;            // the rendered views [view_lo, view_hi) the splat and resolve cover
+    int clear_keys;                  // k_fetch resets every view's keys after its points (else a memset does)
 };
 // The default splat_lane_limit: with every lane below 2^24 candidates a
 // unit's candidate numbers stay below 2^32.

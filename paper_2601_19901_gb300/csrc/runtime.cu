@@ -143,8 +143,12 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     return a;
 }
 
-lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a, cudaStream_t s,
+lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const FrameArgs& a_in, cudaStream_t s,
                                 bool marks, bool clear_keys) {
+    // with triangles to sample, k_fetch clears the keys after its points;
+    // without, a memset does
+    FrameArgs a = a_in;
+    a.clear_keys = clear_keys && mesh->n_tris ? 1 : 0;
     auto mk = [&](int k) {
         if (marks) cudaEventRecord(disp->ev[k], s);
     };
@@ -174,7 +178,7 @@ lfdpr_status record_frame_front(lfdpr_display* disp, lfdpr_mesh* mesh, const Fra
         for (int k = 1; k <= 3; k++) mk(k);
     }
     mk(4);
-    if (clear_keys) CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
+    if (clear_keys && !a.clear_keys) CKF(cudaMemsetAsync(disp->keys, 0xff, 8u * npix, s), "clear keys");
     mk(5);
 #undef CKF
     return LFDPR_OK;

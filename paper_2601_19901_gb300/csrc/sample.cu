@@ -862,9 +862,8 @@ __device__ __forceinline__ NearRec near_record(const DispConst& c, const float4&
 // the point joins the splat's work list if some view can hold a candidate
 // pixel of it.
 __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
-    if (a.ctr->overflow) return;
     const DispConst& c = a.dc;
-    const uint32_t n = a.ctr->n_points;
+    const uint32_t n = a.ctr->overflow ? 0u : a.ctr->n_points;
     const float H1 = float(c.H - 1);
     const int lane = threadIdx.x & 31;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -1007,6 +1006,17 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         }
         if (near && LFDPR_IN_BOUNDS(nbase + __popc(bnear & below), a.max_points, 7))
             a.near[nbase + __popc(bnear & below)] = p;
+    }
+    // the splat's depth keys reset to empty (all ones) at the end of the
+    // pass, so that they are still in L2 when the splat starts (the frame's
+    // key clear, when clear_keys is set)
+    if (a.clear_keys) {
+        const uint64_t n8 = uint64_t(c.W) * uint64_t(c.H) * uint64_t(c.nr), n16 = n8 / 2u;
+        uint4* k16 = reinterpret_cast<uint4*>(a.keys);
+        const uint4 ones = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+        const uint64_t first = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+        for (uint64_t i = first; i < n16; i += uint64_t(gridDim.x) * blockDim.x) k16[i] = ones;
+        if (first == 0 && (n8 & 1u)) a.keys[n8 - 1] = ~0ull;
     }
 }
 
