@@ -88,7 +88,8 @@ enum {
     LFDPR_STAGE_SCAN = 1,       /* exclusive scan of the counts */
     LFDPR_STAGE_EMIT = 2,       /* point emission */
     LFDPR_STAGE_FETCH = 3,      /* tv_min / tv_max fetch (Sec. 3.3) */
-    LFDPR_STAGE_CLEAR = 4,      /* view key buffers reset */
+    LFDPR_STAGE_CLEAR = 4,      /* view key buffers reset (done by the fetch pass, and timed
+                                   there, when the mesh has triangles) */
     LFDPR_STAGE_SPLAT = 5,      /* splatting with the depth test (Sec. 3.2) */
     LFDPR_STAGE_RESOLVE = 6,    /* Eq. 8-9 per view pixel */
     LFDPR_STAGE_INTERLEAVE = 7, /* reconstruction, crosstalk, interleave (Sec. 4) */
