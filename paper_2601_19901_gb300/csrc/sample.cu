@@ -451,43 +451,43 @@ __global__ void __launch_bounds__(kSetupThreads, 4) k_setup(FrameArgs a) {
     }
 }
 
-// Exclusive scan of the per-block point counts (one block of 1024 threads,
-// chunks of 1024 with a running carry); the total decides overflow.
+// Exclusive scan of the per-block point counts in one block of 1024 threads:
+// each thread sums a contiguous run of ceil(n / 1024) block sums, the block
+// scans those 1024 sums, and each thread writes its run's prefixes; the
+// total decides overflow. Prefixes saturate at 2^32 - 1.
 __global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
     __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0ull;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t base = 0; base < a.n_blocks; base += 1024) {
-        const uint32_t k = base + threadIdx.x;
-        const unsigned long long v = k < a.n_blocks ? a.block_sums[k] : 0ull;
-        unsigned long long inc = v;
+    const uint32_t n = a.n_blocks, per = (n + 1023u) / 1024u;
+    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+    unsigned long long run = 0ull;
+    for (uint32_t k = lo; k < hi; k++) run += a.block_sums[k];
+    unsigned long long inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = s_warp[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
         }
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long n = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += n;
-            }
-            s_warp[lane] = w;   // inclusive over warps
-        }
-        __syncthreads();
-        const unsigned long long excl = s_carry + (warp > 0 ? s_warp[warp - 1] : 0ull) + inc - v;
-        if (k < a.n_blocks) a.block_sums[k] = uint32_t(excl > 0xffffffffull ? 0xffffffffull : excl);
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += s_warp[31];
-        __syncthreads();
+        s_warp[lane] = w;   // inclusive over warps
     }
-    if (threadIdx.x == 0) {
-        const unsigned long long total = s_carry;
+    __syncthreads();
+    unsigned long long excl = (warp > 0 ? s_warp[warp - 1] : 0ull) + inc - run;
+    for (uint32_t k = lo; k < hi; k++) {
+        const uint32_t v = a.block_sums[k];
+        a.block_sums[k] = uint32_t(excl > 0xffffffffull ? 0xffffffffull : excl);
+        excl += v;
+    }
+    if (threadIdx.x == 1023) {
+        const unsigned long long total = s_warp[31];
         a.ctr->n_points = uint32_t(total > 0xffffffffull ? 0xffffffffull : total);
         a.ctr->overflow = total > (unsigned long long)a.max_points ? 1u : 0u;
     }
