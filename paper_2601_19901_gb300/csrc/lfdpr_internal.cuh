@@ -87,13 +87,12 @@ struct TriProj {
 // Splat work record of a point with at least one candidate pixel row.
 // Candidate rows are the pixel-centre rows inside both the cell's and the
 // triangle's projected y-extent (the same in every view, since every eye lies
-// on y = 0, z = D). With a single candidate row, L0 and L1 hold the lines
-// x = alpha + beta Ex along which the projected cell's two boundary crossings
-// (L0) and the projected triangle's two crossings (L1) of that row move with
-// the eye position, so a view's candidate columns lie between them. Otherwise
-// (flag kFlagBox) L0 and L1 hold the cell corners' A and B of
-// project_point() and candidates come from the x-extents. Written compacted
-// by the fetch pass, in no particular order.
+// on y = 0, z = D). L0 and L1 bound the x-extent, within that band of rows,
+// of the projected cell (L0) and of the projected triangle (L1), each by a
+// lower and an upper line x = a + b Ex valid for every eye, so a view's
+// candidate columns lie between the larger lower and the smaller upper line
+// (k_fetch's band_bounds). Written compacted by the fetch pass, in no
+// particular order.
 struct WorkRec {
     // lower a, b, upper a, b of the cell's (L0) and triangle's (L1) x-extent,
     // x = a + b Ex, less 1/2 + kBoxPad (lower) and 1/2 - kBoxPad (upper): the
