@@ -81,6 +81,36 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon *recon, const uint8_t *in_views, ui
 lfdpr_status lfdpr_recon_status(lfdpr_recon *recon, int32_t *flags);
 
 /*
+ * lfdpr_warp_views: the depth-guided warp of rendered views to other eyes on
+ * the same eye line. Every eye lies on y = 0, z = D and every view shares the
+ * focal rectangle at z = 0, so a surface point keeps its pixel row in every
+ * view: seen at pixel centre x + 1/2 with ray parameter t from eye E_a (the
+ * depth key's high word), it is at x + 1/2 + (1 - 1/t) pixels_per_unit (E -
+ * E_a) from eye E (Sec. 3.2's projection through the shared focal plane).
+ * For each output eye, the two input views bracketing it (weight s towards
+ * the second, clamped to [0, 1]) are moved there: each input pixel with a
+ * key lands at pixel floor(x'), the smallest t winning (then the first input,
+ * then the leftmost source); a pixel with a winner blends the two inputs,
+ * each interpolated linearly along the row at the winner's position in it
+ * and counted only where its own key there is within 1 % of the winner's t,
+ * with weights (1 - s, s) renormalised (neither agreeing: the winner's own
+ * source pixel); a pixel with no winner takes (1 - s) c_0 + s c_1 of the
+ * inputs at the same pixel. Rounded half to even to RGBA8, alpha 255.
+ *  in_views   device u8 [in_count][view_h][view_w][4]
+ *  in_keys    device u64 [in_count][view_h][view_w]: the views' depth keys
+ *             (lfdpr_get_buffers), all ones where a pixel is empty
+ *  in_eyes    device f32 [in_count]: the input eyes' x, ascending
+ *  out_eyes   device f32 [out_count]: the output eyes' x
+ *  pixels_per_unit  view_w / focal_w of the display
+ *  out_views  device u8 [out_count][view_h][view_w][4], caller-owned
+ * Limits: 2 <= in_count, 1 <= out_count, both <= 512; view_w <= 4096,
+ * view_h <= 16384. Asynchronous on `stream`. Errors: EINVAL, ECUDA.
+ */
+lfdpr_status lfdpr_warp_views(const uint8_t *in_views, const uint64_t *in_keys, const float *in_eyes, int32_t in_count,
+                              const float *out_eyes, int32_t out_count, int32_t view_w, int32_t view_h,
+                              float pixels_per_unit, uint8_t *out_views, void *stream);
+
+/*
  * lfdpr_conv3x3_bf16: one 3x3 layer of the network (test hook): in bf16
  * [H][W][cin], wgt bf16 [cout][3][3][cin], bias f32 [cout], out bf16
  * [H][W][cout]: zero padding 1, + bias, ReLU, on the network's tensor-core

@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "liblfdpr.so")
 LIB_CHECKED = os.path.join(HERE, "liblfdpr_checked.so")
 BUILD = os.path.join(HERE, "_build")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
-SOURCES = ["runtime.cu", "sample.cu", "splat.cu", "interleave.cu", "mip.cu", "probe.cu", "noalloc.cu", "batch.cu", "recon.cu"]
+SOURCES = ["runtime.cu", "sample.cu", "splat.cu", "interleave.cu", "mip.cu", "probe.cu", "noalloc.cu", "batch.cu", "recon.cu",
+           "warp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]

@@ -42,7 +42,7 @@ EXPORTS = ["lfdpr_create_display", "lfdpr_destroy_display", "lfdpr_upload_mesh",
            "lfdpr_checked_status",
            "lfdpr_recon_weight_count", "lfdpr_recon_bias_count", "lfdpr_create_recon",
            "lfdpr_destroy_recon", "lfdpr_recon_run", "lfdpr_recon_forward", "lfdpr_recon_status",
-           "lfdpr_conv3x3_bf16"]
+           "lfdpr_conv3x3_bf16", "lfdpr_warp_views"]
 
 
 class LfdprError(RuntimeError):
@@ -154,6 +154,7 @@ def lib() -> C.CDLL:
         L.lfdpr_recon_forward.argtypes = [P, P, P, P]
         L.lfdpr_recon_status.argtypes = [P, P]
         L.lfdpr_conv3x3_bf16.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int32, P, P]
+        L.lfdpr_warp_views.argtypes = [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, C.c_float, P, P]
         for name in EXPORTS:
             fn = getattr(L, name)
             if name == "lfdpr_last_error":
@@ -488,6 +489,14 @@ def lfdpr_recon_run(recon: int, src_disp: int, dst_disp: int, stream=None):
 
 def lfdpr_recon_forward(recon: int, in_ptr: int, out_ptr: int, stream=None):
     _check(lib().lfdpr_recon_forward(recon, C.c_void_p(in_ptr), C.c_void_p(out_ptr), _stream(stream)))
+
+
+def lfdpr_warp_views(in_views_ptr: int, in_keys_ptr: int, in_eyes_ptr: int, in_count: int, out_eyes_ptr: int,
+                     out_count: int, view_w: int, view_h: int, pixels_per_unit: float, out_ptr: int, stream=None):
+    """Device pointers: RGBA8 views, u64 depth keys, f32 eye x arrays; see lfdpr_recon.h."""
+    _check(lib().lfdpr_warp_views(C.c_void_p(in_views_ptr), C.c_void_p(in_keys_ptr), C.c_void_p(in_eyes_ptr),
+                                  in_count, C.c_void_p(out_eyes_ptr), out_count, view_w, view_h,
+                                  float(pixels_per_unit), C.c_void_p(out_ptr), _stream(stream)))
 
 
 def lfdpr_recon_status(recon: int) -> int:
