@@ -735,6 +735,8 @@ def learned_measure(sc, steps, warmup, quality_frames, stream=None):
     me = [lfdpr.lfdpr_upload_mesh_textured(dis[k], sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle, stream)
           for k in (0, 1, 3)]
     R = lfdpr.Recon(W, H, nin, w, b)
+    in_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(dis[0], nin)).cuda()
+    out_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(dis[2], 4 * nin)).cuda()
     panel = torch.empty((d_out.panel_h, d_out.panel_w, 4), dtype=torch.uint8, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     try:
@@ -790,15 +792,19 @@ def learned_measure(sc, steps, warmup, quality_frames, stream=None):
             pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
             b4 = lfdpr.lfdpr_get_buffers(dis[3], me[2])
             plain48 = lfdpr.device_view(b4.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
+            bi = lfdpr.lfdpr_get_buffers(dis[0], me[0])
+            warp = RN.warped_base(lfdpr.device_view(bi.views, (nin, H, W, 4), np.uint8),
+                                  lfdpr.device_view(bi.keys, (nin, H, W), np.uint64), in_eyes, out_eyes,
+                                  RN.pixels_per_unit(d_in))[..., :3]
             q.append((RN.psnr(pred, truth), RN.ssim(pred, truth), RN.psnr(plain48, truth),
-                      RN.psnr(pred, plain48), RN.ssim(pred, plain48)))
+                      RN.psnr(pred, plain48), RN.ssim(pred, plain48), RN.psnr(warp, truth), RN.psnr(warp, plain48)))
         # algorithmic FLOPs of one forward pass: the 3x3 layers over the padded
-        # views plus the output product over [features | inputs] (32 + 48) x 3 * 4n
+        # views plus the 1x1 output layer (32 x 3 * 4n); the warp is not counted
         flops = 0
         hp, wp = RN.padded(H, W)
         for ci, co, lev in RN.LAYERS:
             flops += 2 * 9 * ci * co * (hp >> lev) * (wp >> lev)
-        flops += 2 * 80 * 3 * 4 * nin * hp * wp
+        flops += 2 * 32 * 3 * 4 * nin * hp * wp
     finally:
         R.close()
         for m_ in me:
@@ -822,6 +828,8 @@ def learned_measure(sc, steps, warmup, quality_frames, stream=None):
                                   "ssim_mean": statistics.mean(x[4] for x in q),
                                   "speedup": ms_plain / ms_learned},
             "plain_48_views_vs_full_render_psnr_db": statistics.mean(x[2] for x in q),
+            "warped_base_alone_psnr_db": {"vs_full_render": statistics.mean(x[5] for x in q),
+                                          "vs_plain_48_views": statistics.mean(x[6] for x in q)},
             "quality_frames": list(quality_frames)}
 
 

@@ -14,15 +14,14 @@
  * to multiples of 8 pixels; four levels of two 3x3 convolutions + bias + ReLU
  * (channels 32, 64, 128, 256), 2x2 average pooling down, nearest 2x
  * upsampling concatenated with the level's features (upsampled first) up;
- * then a 1x1 convolution to 3 * 4n channels added to the linear angular
- * interpolation of the input views (input j at output index 4j + 3/2,
- * clamped at the ends), clamped to [0, 1], times 255, rounded half to even.
- * Activations and weights are bf16 with fp32 accumulation on the tensor
- * cores (tcgen05.mma, accumulators in tensor memory, operands staged by TMA);
- * the 1x1 layer and the angular interpolation run as one product over
- * [features (32), input channels (48)] (the interpolation weights 0, 1/8,
- * 3/8, 5/8, 7/8, 1 are exact in bf16). Activations are held as images with
- * a one-pixel ring of zeros (the 3x3 padding), channels in chunks of eight.
+ * then a 1x1 convolution to 3 * 4n channels added to the base, clamped to
+ * [0, 1], times 255, rounded half to even. The base is the input views
+ * warped to the output eyes by their depth keys (lfdpr_warp_views below),
+ * RGB / 255 as bf16. Activations and weights are bf16 with fp32
+ * accumulation on the tensor cores (tcgen05.mma, accumulators in tensor
+ * memory, operands staged by TMA); the 1x1 layer's epilogue adds the base.
+ * Activations are held as images with a one-pixel ring of zeros (the 3x3
+ * padding), channels in chunks of eight.
  *
  * 3x3 layers in order, (input channels, output channels):
  *   (48,32) (32,32) | (32,64) (64,64) | (64,128) (128,128) | (128,256) (256,256)
@@ -60,16 +59,21 @@ lfdpr_status lfdpr_destroy_recon(lfdpr_recon *recon);
 
 /*
  * lfdpr_recon_run: predict the views of display `dst` (4 in_views rendered
- * views, no angular supersampling, same view size) from the rendered views of
- * display `src` (in_views rendered views), asynchronously on `stream`. The
+ * views, no angular supersampling, same view size) from the rendered views
+ * and depth keys of display `src` (in_views rendered views, the last frame
+ * rendered), asynchronously on `stream`. The
  * result is in dst's view buffer (lfdpr_get_buffers), so lfdpr_interleave(dst,
  * ...) builds its panel. One network runs one forward pass at a time.
  */
 lfdpr_status lfdpr_recon_run(lfdpr_recon *recon, const lfdpr_display *src, lfdpr_display *dst, void *stream);
 
-/* The same on raw device buffers: in_views u8 [in_views][H][W][4],
- * out_views u8 [4 in_views][H][W][4]. */
-lfdpr_status lfdpr_recon_forward(lfdpr_recon *recon, const uint8_t *in_views, uint8_t *out_views, void *stream);
+/* The same on raw device buffers: in_views u8 [in_views][H][W][4], their
+ * depth keys in_keys u64 [in_views][H][W], the input and output eyes' x
+ * (f32 [in_views], ascending, and [4 in_views]), pixels_per_unit = view_w /
+ * focal_w, out_views u8 [4 in_views][H][W][4]. */
+lfdpr_status lfdpr_recon_forward(lfdpr_recon *recon, const uint8_t *in_views, const uint64_t *in_keys,
+                                 const float *in_eyes, const float *out_eyes, float pixels_per_unit,
+                                 uint8_t *out_views, void *stream);
 
 /*
  * lfdpr_recon_status: the failed-wait flags the network's kernels recorded
@@ -93,8 +97,8 @@ lfdpr_status lfdpr_recon_status(lfdpr_recon *recon, int32_t *flags);
  * then the leftmost source); a pixel with a winner blends the two inputs,
  * each interpolated linearly along the row at the winner's position in it
  * and counted only where its own key there is within 1 % of the winner's t,
- * with weights (1 - s, s) renormalised (neither agreeing: the winner's own
- * source pixel); a pixel with no winner takes (1 - s) c_0 + s c_1 of the
+ * with weights (1 - s, s) renormalised by the reciprocal of their sum
+ * (neither agreeing: the winner's own source pixel); a pixel with no winner takes (1 - s) c_0 + s c_1 of the
  * inputs at the same pixel. Rounded half to even to RGBA8, alpha 255.
  *  in_views   device u8 [in_count][view_h][view_w][4]
  *  in_keys    device u64 [in_count][view_h][view_w]: the views' depth keys

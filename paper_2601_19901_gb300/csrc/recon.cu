@@ -27,11 +27,11 @@
 //                 done. The four warps then read the accumulators back
 //                 (tcgen05.ld), add the bias, apply ReLU and store bf16, with
 //                 zeros on the border ring, one 16-byte store per chunk.
-//   k_conv_tc<1>  the output layer: a 1x1 product over [d0 (32 channels) |
-//                 x0 (48 input channels)] that gives the 1x1 convolution
-//                 plus the fixed angular interpolation of the input views,
-//                 clamped, scaled to 255, rounded half to even, written as
-//                 RGBA8 output views.
+//   k_conv_tc<1>  the output layer: the 1x1 convolution of d0 (32
+//                 channels), plus the base (the input views warped to the
+//                 output eyes by warp.cu's k_warp_views, RGB / 255 as bf16)
+//                 and the bias, clamped, scaled to 255, rounded half to even,
+//                 written as RGBA8 output views.
 //   k_pack_w      weights [cout][taps][cin] -> the per-K-step stage images
 //                 [n tile][K step][tap][2][NT][8] the MMAs read.
 //   k_avgpool2, k_recon_in   pooling and the input packing, between chunked
@@ -224,6 +224,7 @@ struct TcGeom {
     int Wbo, Qpo;             // that tensor's bordered width and positions per chunk
     int nout, H, W;           // output layer: views written, view size
     int bias_n;               // biases staged in shared memory (<= 256)
+    const uint32_t* base;     // output layer: the residual's base, RGBA8 views laid out as the output
 };
 
 // A wait that also gives up as soon as another role of the block has given
@@ -450,14 +451,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                         for (int i = 0; i < 12; i++)
                             *reinterpret_cast<float4*>(bv + 4 * i) = reinterpret_cast<const float4*>(s_bias + j)[i];
 #pragma unroll
+                        // the base's 16 views at this position, all loads in flight first
+                        uint32_t bws[16];
+#pragma unroll
                         for (int k = 0; k < 16; k++) {
                             const int view = j / 3 + k;
-                            // round(clamp(x + b, 0, 1) 255), half to even: saturating add, scale, convert
-                            const uint32_t r0 = __float2uint_rn(__saturatef(v[3 * k] + bv[3 * k]) * 255.0f);
-                            const uint32_t g0 = __float2uint_rn(__saturatef(v[3 * k + 1] + bv[3 * k + 1]) * 255.0f);
-                            const uint32_t b0 = __float2uint_rn(__saturatef(v[3 * k + 2] + bv[3 * k + 2]) * 255.0f);
-                            if (inside && view < g.nout)
-                                views[size_t(view) * npix + pix] = 0xff000000u | r0 | (g0 << 8) | (b0 << 16);
+                            bws[k] = inside && view < g.nout ? __ldg(g.base + size_t(view) * npix + pix) : 0u;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            const int view = j / 3 + k;
+                            if (!(inside && view < g.nout)) continue;
+                            // the base's RGB / 255 as bf16 values, added to the product
+                            const uint32_t bw = bws[k];
+                            float base[3];
+#pragma unroll
+                            for (int c = 0; c < 3; c++)
+                                base[c] = __bfloat162float(
+                                    __float2bfloat16_rn(float((bw >> (8 * c)) & 255u) * (1.0f / 255.0f)));
+                            // round(clamp(x + base + b, 0, 1) 255), half to even: saturating add, scale, convert
+                            const uint32_t r0 = __float2uint_rn(__saturatef((v[3 * k] + base[0]) + bv[3 * k]) * 255.0f);
+                            const uint32_t g0 =
+                                __float2uint_rn(__saturatef((v[3 * k + 1] + base[1]) + bv[3 * k + 1]) * 255.0f);
+                            const uint32_t b0 =
+                                __float2uint_rn(__saturatef((v[3 * k + 2] + base[2]) + bv[3 * k + 2]) * 255.0f);
+                            views[size_t(view) * npix + pix] = 0xff000000u | r0 | (g0 << 8) | (b0 << 16);
                         }
                     }
                 }
@@ -797,12 +815,13 @@ struct lfdpr_recon {
     int W = 0, H = 0, Wp = 0, Hp = 0, nin = 0, nout = 0, sm_count = 1;
     __nv_bfloat16* w = nullptr;       // packed 3x3 weights, layer by layer
     float* b = nullptr;               // all 3x3 biases
-    __nv_bfloat16* w_out = nullptr;   // packed output layer: [32 (1x1 weights) | 48 (angular base)] x NT_out
+    __nv_bfloat16* w_out = nullptr;   // packed output layer: 32 (1x1 weights) x NT_out
     float* b_out = nullptr;           // [NT_out] (zero past 3 nout)
     int* status = nullptr;            // device: failed waits (bit 0 copies, 1 MMA, 2 epilogue)
     int64_t w_off[14] = {}, b_off[14] = {};
     TcGeom geom[14] = {}, geom_out = {};
-    CUtensorMap in_map[14], in_map_b[14], out_d0, out_x0;
+    CUtensorMap in_map[14], in_map_b[14], out_d0;
+    uint8_t* warp = nullptr;          // [nout][H][W][4] the input views warped to the output eyes (RGBA8)
     __nv_bfloat16* act = nullptr;     // activation arena (chunked bordered tensors)
     // encoder e*, pooled p*, bottleneck ba, upsampled U* (written by layers 7, 9, 11), decoder d*
     __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *U2, *d2a, *U1, *d1a, *U0, *d0a, *d0;
@@ -817,6 +836,7 @@ void free_recon(lfdpr_recon* r) {
     dev_free(r->w_out);
     dev_free(r->b_out);
     dev_free(r->status);
+    dev_free(r->warp);
     dev_free(r->act);
     delete r;
 }
@@ -883,17 +903,18 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         offs[k] = total;
         total += (sizes[k] + 127) / 128 * 128;
     }
-    const int ntout = out_nt(r->nout), no3 = 3 * r->nout;
+    const int ntout = out_nt(r->nout), no3 = 3 * r->nout, ko = 32;
     cudaError_t e;
     const int64_t nw3 = wo, nb3 = bo;
     uint16_t* w_raw = nullptr;   // device staging of the 3x3 blob before packing
     uint16_t* wout_raw = nullptr;
     if ((e = dev_malloc(&r->w, 2 * nw3)) != cudaSuccess || (e = dev_malloc(&r->b, 4 * nb3)) != cudaSuccess ||
-        (e = dev_malloc(&r->w_out, 2 * int64_t(ntout) * 80)) != cudaSuccess ||
+        (e = dev_malloc(&r->w_out, 2 * int64_t(ntout) * ko)) != cudaSuccess ||
+        (e = dev_malloc(&r->warp, 4 * int64_t(r->nout) * r->W * r->H)) != cudaSuccess ||
         (e = dev_malloc(&r->b_out, 4 * int64_t(ntout))) != cudaSuccess ||
         (e = dev_malloc(&r->status, sizeof(int))) != cudaSuccess || (e = dev_malloc(&r->act, 2 * total)) != cudaSuccess ||
         (e = dev_malloc(&w_raw, 2 * nw3)) != cudaSuccess ||
-        (e = dev_malloc(&wout_raw, 2 * int64_t(no3) * 80)) != cudaSuccess) {
+        (e = dev_malloc(&wout_raw, 2 * int64_t(no3) * ko)) != cudaSuccess) {
         dev_free(w_raw);
         dev_free(wout_raw);
         free_recon(r);
@@ -902,23 +923,11 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     __nv_bfloat16** bufs[kTensors] = {&r->x0,  &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1,  &r->p2,  &r->e2a, &r->e2,
                                       &r->p3,  &r->ba,  &r->U2, &r->d2a, &r->U1, &r->d1a, &r->U0, &r->d0a, &r->d0};
     for (int k = 0; k < kTensors; k++) *bufs[k] = r->act + offs[k];
-    // the output layer: its 32 weights, then the angular base over the 48
-    // input channels (bf16 bit patterns: 1/8, 3/8, 5/8, 7/8 and 1 are exact)
-    std::vector<uint16_t> wout(size_t(no3) * 80, 0);
-    auto bf16_bits = [](float f) {
-        uint32_t u;
-        std::memcpy(&u, &f, 4);
-        return uint16_t(u >> 16);   // exact for the base weights
-    };
-    for (int o = 0; o < no3; o++) {
-        for (int k = 0; k < 32; k++) wout[size_t(o) * 80 + k] = weights_bf16[nw3 + int64_t(o) * 32 + k];
-        const int kv = o / 3, c = o - 3 * kv;
-        const float pos = (float(kv) - 1.5f) * 0.25f;
-        const int j0 = std::min(std::max(int(std::floor(pos)), 0), r->nin - 2);
-        const float t = std::min(std::max(pos - float(j0), 0.0f), 1.0f);
-        wout[size_t(o) * 80 + 32 + 3 * j0 + c] = bf16_bits(1.0f - t);
-        wout[size_t(o) * 80 + 32 + 3 * (j0 + 1) + c] = bf16_bits(t);
-    }
+    // the output layer's 32 weights per output channel (the base is added in
+    // its epilogue)
+    std::vector<uint16_t> wout(size_t(no3) * ko, 0);
+    for (int o = 0; o < no3; o++)
+        for (int k = 0; k < 32; k++) wout[size_t(o) * ko + k] = weights_bf16[nw3 + int64_t(o) * 32 + k];
     std::vector<float> bout(ntout, 0.0f);
     for (int o = 0; o < no3; o++) bout[o] = biases[nb3 + o];
     // layer geometry and packed weights
@@ -936,7 +945,8 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
             r->geom[l].Qpo = int(qpad(2 * Hl, 2 * Wl));
         }
     }
-    r->geom_out = tc_geom(r->Hp, r->Wp, 32, 48, 1, ntout, 1, 1, 0);
+    r->geom_out = tc_geom(r->Hp, r->Wp, 32, 0, 1, ntout, 1, 1, 0);
+    r->geom_out.base = reinterpret_cast<const uint32_t*>(r->warp);
     r->geom_out.nout = r->nout;
     r->geom_out.H = r->H;
     r->geom_out.W = r->W;
@@ -955,8 +965,7 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
             r->in_map_b[l] = r->in_map[l];
     }
     maps_ok = maps_ok && tc_valid(r->geom_out) &&
-              make_map(&r->out_d0, r->d0, 32, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess &&
-              make_map(&r->out_x0, r->x0, 48, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess;
+              make_map(&r->out_d0, r->d0, 32, r->geom_out.Qp, r->geom_out.rows) == cudaSuccess;
     if (!maps_ok) {
         dev_free(w_raw);
         dev_free(wout_raw);
@@ -972,7 +981,7 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
             e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(w_raw) + r->w_off[l], kLayers[l].cout, 9,
                             kLayers[l].cin, r->geom[l].NT, r->geom[l].n_tiles, r->w + r->w_off[l], 0);
         if (e == cudaSuccess)
-            e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(wout_raw), no3, 1, 80, ntout, 1, r->w_out, 0);
+            e = launch_pack(reinterpret_cast<const __nv_bfloat16*>(wout_raw), no3, 1, ko, ntout, 1, r->w_out, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     dev_free(w_raw);
@@ -992,9 +1001,14 @@ lfdpr_status lfdpr_destroy_recon(lfdpr_recon* r) {
     return LFDPR_OK;
 }
 
-lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_t* out_views, void* stream) {
+lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, const uint64_t* in_keys,
+                                 const float* in_eyes, const float* out_eyes, float pixels_per_unit,
+                                 uint8_t* out_views, void* stream) {
     lfdpr::g_last_error[0] = 0;
-    if (!r || !in_views || !out_views) return fail(LFDPR_EINVAL, "recon_forward: null argument");
+    if (!r || !in_views || !in_keys || !in_eyes || !out_eyes || !out_views)
+        return fail(LFDPR_EINVAL, "recon_forward: null argument");
+    if (!(pixels_per_unit > 0.0f) || !std::isfinite(pixels_per_unit))
+        return fail(LFDPR_EINVAL, "recon_forward: pixels_per_unit must be positive and finite");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H0 = r->Hp, W0 = r->Wp, sm = r->sm_count;
     __nv_bfloat16* conv_out[14] = {r->e0a, r->e0, r->e1a, r->e1, r->e2a, r->e2, r->ba,
@@ -1013,6 +1027,11 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     } while (0)
     k_recon_in<<<sm * 8, 256, 0, s>>>(in_views, r->nin, r->H, r->W, H0, W0, r->x0);
     CKR(cudaGetLastError(), "launch k_recon_in");
+    // the residual's base: the input views warped to the output eyes
+    CKR(launch_warp_views(in_views, in_keys, in_eyes, r->nin, out_eyes, r->nout, r->W, r->H, pixels_per_unit,
+                          r->warp, s),
+        "launch k_warp_views");
+
     CKR(conv(0), "conv 0");
     CKR(conv(1), "conv 1");
     CKR(pool(r->e0, H0, W0, 32, r->p1), "pool 1");
@@ -1030,7 +1049,7 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, uint8_
     CKR(conv(11), "conv 11");
     CKR(conv(12), "conv 12");
     CKR(conv(13), "conv 13");
-    CKR(launch_tc(1, r->geom_out, r->out_d0, r->out_x0, r->w_out, r->b_out, out_views, r->status, s),
+    CKR(launch_tc(1, r->geom_out, r->out_d0, r->out_d0, r->w_out, r->b_out, out_views, r->status, s),
         "output layer");
 #undef CKR
     return LFDPR_OK;
@@ -1043,7 +1062,7 @@ lfdpr_status lfdpr_recon_run(lfdpr_recon* r, const lfdpr_display* src, lfdpr_dis
         return fail(LFDPR_EINVAL, "recon_run: source display must render %d views of %dx%d", r->nin, r->W, r->H);
     if (dst->dc.nr != r->nout || dst->dc.W != r->W || dst->dc.H != r->H)
         return fail(LFDPR_EINVAL, "recon_run: target display must hold %d views of %dx%d", r->nout, r->W, r->H);
-    return lfdpr_recon_forward(r, src->views, dst->views, stream);
+    return lfdpr_recon_forward(r, src->views, src->keys, src->d_ex, dst->d_ex, src->dc.ipw, dst->views, stream);
 }
 
 lfdpr_status lfdpr_recon_status(lfdpr_recon* r, int32_t* flags) {

@@ -17,7 +17,8 @@
 //     the two inputs and interpolates that input's row linearly there. An
 //     input agrees if its own key at the pixel holding that position has a
 //     t within 1 % of the winner's. The agreeing inputs are blended with
-//     weights (1 - s, s), renormalised; with none agreeing, the winner's own
+//     weights (1 - s, s), renormalised (times the reciprocal of their sum);
+//     with none agreeing, the winner's own
 //     source pixel is taken. A pixel with no winner (disoccluded, or beyond
 //     every input's reach) takes the unshifted blend (1 - s) c_0 + s c_1.
 // Colours are rounded half to even to 8 bits; alpha is 255. All arithmetic is
@@ -31,7 +32,7 @@
 namespace lfdpr {
 namespace {
 
-constexpr int kWarpThreads = 128;
+constexpr int kWarpThreads = 256;
 constexpr uint64_t kNoKey = ~0ull;
 
 struct WarpArgs {
@@ -51,92 +52,140 @@ __device__ __forceinline__ bool key_depth(uint64_t key, float& t) {
 
 __device__ __forceinline__ float channel(uint32_t rgba, int c) { return float((rgba >> (8 * c)) & 255u); }
 
-// Block (row y, output view k).
-__global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
-    extern __shared__ unsigned long long s_win[];   // [W] forward-splat winners
-    const int y = blockIdx.x, k = blockIdx.y, W = a.W;
-    if (y >= a.H || k >= a.nout) return;
-    const float E = a.out_eyes[k];
+// The input bracket of output eye E: j0 the last input eye at or before E
+// (clamped to [0, nin - 2]), s the weight towards input j0 + 1.
+__device__ __forceinline__ int bracket(const WarpArgs& a, float E, float& s) {
     int j0 = 0;
     for (int j = 0; j < a.nin; j++)
         if (a.in_eyes[j] <= E) j0 = j;
     j0 = min(j0, a.nin - 2);
     const float e0 = a.in_eyes[j0], e1 = a.in_eyes[j0 + 1];
-    float s = e1 > e0 ? (E - e0) / (e1 - e0) : 0.0f;
+    s = e1 > e0 ? (E - e0) / (e1 - e0) : 0.0f;
     s = fminf(fmaxf(s, 0.0f), 1.0f);
-    const size_t npix = size_t(W) * a.H, row = size_t(y) * W;
-    const uint64_t* key[2] = {a.keys + size_t(j0) * npix + row, a.keys + size_t(j0 + 1) * npix + row};
-    const uint32_t* col[2] = {reinterpret_cast<const uint32_t*>(a.views) + size_t(j0) * npix + row,
-                              reinterpret_cast<const uint32_t*>(a.views) + size_t(j0 + 1) * npix + row};
-    const float eye[2] = {e0, e1};
+    return j0;
+}
 
-    for (int i = threadIdx.x; i < W; i += blockDim.x) s_win[i] = kNoKey;
+// Views an interval block takes at a time, for view width W.
+__host__ __device__ __forceinline__ int views_per_pass(int W) {
+    const int v = 32768 / (8 * W);
+    return v < 1 ? 1 : (v > 8 ? 8 : v);
+}
+
+// Block (row y, input interval j): every output view whose bracket is
+// (j, j + 1), up to views_per_pass(W) of them at a time. The two input rows
+// are staged once in shared memory with each pixel's t and disparity factor
+// g = (1 - 1/t) W / fw (NaN where it has no key). The nearest point per
+// output pixel is the 64-bit minimum of (t bits, input, source pixel).
+__global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
+    extern __shared__ __align__(16) uint8_t s_raw[];
+    const int y = blockIdx.x, j = blockIdx.y, W = a.W, V = views_per_pass(W);
+    if (y >= a.H || j > a.nin - 2) return;
+    float* s_t = reinterpret_cast<float*>(s_raw);               // [2][W]
+    float* s_g = s_t + 2 * W;                                   // [2][W]
+    uint32_t* s_c = reinterpret_cast<uint32_t*>(s_g + 2 * W);   // [2][W]
+    unsigned long long* s_win = reinterpret_cast<unsigned long long*>(s_c + 2 * W);   // [V][W] nearest point
+    __shared__ int s_views[kMaxRenderViews];
+    __shared__ float s_w[kMaxRenderViews], s_E[kMaxRenderViews];
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    const size_t npix = size_t(W) * a.H, row = size_t(y) * W;
+    for (int q = threadIdx.x; q < 2 * W; q += blockDim.x) {
+        const int src = q >= W, i = q - src * W;
+        const size_t o = size_t(j + src) * npix + row + i;
+        float t;
+        const bool ok = key_depth(a.keys[o], t);
+        s_t[q] = ok ? t : __int_as_float(0x7fc00000);   // NaN: no key
+        s_g[q] = ok ? (1.0f - 1.0f / t) * a.ipw : __int_as_float(0x7fc00000);
+        s_c[q] = reinterpret_cast<const uint32_t*>(a.views)[o];
+    }
     __syncthreads();
-    // 1. forward
-#pragma unroll
-    for (int src = 0; src < 2; src++) {
-        const float dE = E - eye[src];
-        for (int i = threadIdx.x; i < W; i += blockDim.x) {
-            const uint64_t kk = key[src][i];
-            float t;
-            if (!key_depth(kk, t)) continue;
-            const float f = 1.0f - 1.0f / t;
-            const float X = (float(i) + 0.5f) + (f * a.ipw) * dE;
-            if (!isfinite(X)) continue;
-            const float px = floorf(X);
-            if (px < 0.0f || px >= float(W)) continue;
-            atomicMin(&s_win[int(px)], (kk & 0xffffffff00000000ull) | (uint64_t(src) << 16) | uint64_t(i));
+    // the output views of this interval with their weights
+    for (int k = threadIdx.x; k < a.nout; k += blockDim.x) {
+        float s;
+        const float E = a.out_eyes[k];
+        if (bracket(a, E, s) == j) {
+            const int m = atomicAdd(&s_n, 1);
+            s_views[m] = k;
+            s_w[m] = s;
+            s_E[m] = E;
         }
     }
     __syncthreads();
-    // 2. backward
-    uint32_t* out = reinterpret_cast<uint32_t*>(a.out) + size_t(k) * npix + row;
-    for (int p = threadIdx.x; p < W; p += blockDim.x) {
-        const uint64_t w = s_win[p];
-        float v[3];
-        if (w == kNoKey) {
-            const uint32_t c0 = col[0][p], c1 = col[1][p];
-#pragma unroll
-            for (int c = 0; c < 3; c++) v[c] = (1.0f - s) * channel(c0, c) + s * channel(c1, c);
-        } else {
-            const float t = __uint_as_float(uint32_t(w >> 32));
-            const float f = 1.0f - 1.0f / t;
-            float vs[2][3], wt[2];
-#pragma unroll
-            for (int src = 0; src < 2; src++) {
-                const float X = (float(p) + 0.5f) + (f * a.ipw) * (eye[src] - E);
-                const float xa = X - 0.5f;
-                const float fl = floorf(xa), fr = xa - fl;
-                const float fn = floorf(X);
-                // indices clamped to the row (X is finite: the winner came from this row)
-                const int i0 = int(fminf(fmaxf(fl, 0.0f), float(W - 1)));
-                const int i1 = int(fminf(fmaxf(fl + 1.0f, 0.0f), float(W - 1)));
-                const int n = int(fminf(fmaxf(fn, 0.0f), float(W - 1)));
-                const uint32_t ca = col[src][i0], cb = col[src][i1];
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const float va = channel(ca, c), vb = channel(cb, c);
-                    vs[src][c] = va + fr * (vb - va);
-                }
-                float tn;
-                const bool agree = key_depth(key[src][n], tn) && fabsf(tn - t) <= 0.01f * t;
-                wt[src] = agree ? (src == 0 ? 1.0f - s : s) : 0.0f;
-            }
-            const float ws = wt[0] + wt[1];
-            if (ws > 0.0f) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = (wt[0] * vs[0][c] + wt[1] * vs[1][c]) / ws;
-            } else {
-                const int src = int((w >> 16) & 1u), i = int(w & 0xffffu);
-                const uint32_t cs = col[src][i];
-#pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = channel(cs, c);
+    const int n_views = s_n;
+    const float eye[2] = {a.in_eyes[j], a.in_eyes[j + 1]};
+    for (int m0 = 0; m0 < n_views; m0 += V) {
+        const int nv = min(V, n_views - m0);
+        for (int q = threadIdx.x; q < nv * W; q += blockDim.x) s_win[q] = kNoKey;
+        __syncthreads();
+        // 1. forward: the nearest point landing on each pixel (t, then input,
+        // then source pixel)
+        for (int m = 0; m < nv; m++) {
+            const float d0 = s_E[m0 + m] - eye[0], d1 = s_E[m0 + m] - eye[1];
+            for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) {
+                const int src = r >= W, i = r - src * W;
+                const float g = s_g[r];
+                if (isnan(g)) continue;
+                const float X = (float(i) + 0.5f) + g * (src ? d1 : d0);
+                if (!isfinite(X)) continue;
+                const float px = floorf(X);
+                if (px < 0.0f || px >= float(W)) continue;
+                atomicMin(&s_win[m * W + int(px)],
+                          (uint64_t(__float_as_uint(s_t[r])) << 32) | (uint64_t(src) << 16) | uint64_t(i));
             }
         }
-        uint32_t o = 0xff000000u;
+        __syncthreads();
+        // 2. backward
+        for (int m = 0; m < nv; m++)
+        for (int p = threadIdx.x; p < W; p += blockDim.x) {
+            const int q = m * W + p, k = s_views[m0 + m];
+            const float E = s_E[m0 + m], s = s_w[m0 + m];
+            const uint64_t w = s_win[q];
+            float v[3];
+            if (w == kNoKey) {
+                const uint32_t c0 = s_c[p], c1 = s_c[W + p];
 #pragma unroll
-        for (int c = 0; c < 3; c++) o |= uint32_t(rintf(fminf(fmaxf(v[c], 0.0f), 255.0f))) << (8 * c);
-        out[p] = o;
+                for (int c = 0; c < 3; c++) v[c] = (1.0f - s) * channel(c0, c) + s * channel(c1, c);
+            } else {
+                const int ws_ = int((w >> 16) & 1u), wi = int(w & 0xffffu);
+                const float t = s_t[ws_ * W + wi], g = s_g[ws_ * W + wi];
+                float vs[2][3], wt[2];
+#pragma unroll
+                for (int src = 0; src < 2; src++) {
+                    const float X = (float(p) + 0.5f) + g * (eye[src] - E);
+                    const float xa = X - 0.5f;
+                    const float fl = floorf(xa), fr = xa - fl;
+                    const float fn = floorf(X);
+                    // indices clamped to the row (X is finite: the winner came from this row)
+                    const int i0 = int(fminf(fmaxf(fl, 0.0f), float(W - 1)));
+                    const int i1 = int(fminf(fmaxf(fl + 1.0f, 0.0f), float(W - 1)));
+                    const int n = int(fminf(fmaxf(fn, 0.0f), float(W - 1)));
+                    const uint32_t ca = s_c[src * W + i0], cb = s_c[src * W + i1];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float va = channel(ca, c), vb = channel(cb, c);
+                        vs[src][c] = va + fr * (vb - va);
+                    }
+                    const float tn = s_t[src * W + n];
+                    const bool agree = !isnan(tn) && fabsf(tn - t) <= 0.01f * t;
+                    wt[src] = agree ? (src == 0 ? 1.0f - s : s) : 0.0f;
+                }
+                const float ws = wt[0] + wt[1];
+                if (ws > 0.0f) {
+                    const float rw = 1.0f / ws;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) v[c] = (wt[0] * vs[0][c] + wt[1] * vs[1][c]) * rw;
+                } else {
+                    const uint32_t cs = s_c[ws_ * W + wi];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) v[c] = channel(cs, c);
+                }
+            }
+            uint32_t o = 0xff000000u;
+#pragma unroll
+            for (int c = 0; c < 3; c++) o |= uint32_t(rintf(fminf(fmaxf(v[c], 0.0f), 255.0f))) << (8 * c);
+            reinterpret_cast<uint32_t*>(a.out)[size_t(k) * npix + row + p] = o;
+        }
+        __syncthreads();   // this pass's views are done with the minima
     }
 }
 
@@ -145,11 +194,17 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
 cudaError_t launch_warp_views(const uint8_t* views, const uint64_t* keys, const float* in_eyes, int nin,
                               const float* out_eyes, int nout, int W, int H, float ipw, uint8_t* out,
                               cudaStream_t s) {
-    if (nin < 2 || nout < 1 || W < 1 || H < 1 || W > kMaxWarpWidth || H > 65535 || nout > 65535 || !(ipw > 0.0f))
+    if (nin < 2 || nout < 1 || W < 1 || H < 1 || W > kMaxWarpWidth || H > 65535 || nout > kMaxRenderViews || !(ipw > 0.0f))
         return cudaErrorInvalidValue;
-    // the winners' row: at most 32 KB of shared memory
+    // shared memory: the two input rows (t, g, colour) and the pass's minima:
+    // (24 + 8 V) bytes a pixel, at most 128 KB
+    const size_t smem = (24u + 8u * size_t(views_per_pass(W))) * size_t(W);
+    if (smem > 48u * 1024u) {
+        const cudaError_t e = cudaFuncSetAttribute(k_warp_views, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
     WarpArgs a{views, keys, in_eyes, out_eyes, nin, nout, W, H, ipw, out};
-    k_warp_views<<<dim3(unsigned(H), unsigned(nout)), kWarpThreads, sizeof(unsigned long long) * size_t(W), s>>>(a);
+    k_warp_views<<<dim3(unsigned(H), unsigned(nin - 1)), kWarpThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

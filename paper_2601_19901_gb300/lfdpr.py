@@ -151,7 +151,7 @@ def lib() -> C.CDLL:
                                          C.POINTER(C.c_void_p)]
         L.lfdpr_destroy_recon.argtypes = [P]
         L.lfdpr_recon_run.argtypes = [P, P, P, P]
-        L.lfdpr_recon_forward.argtypes = [P, P, P, P]
+        L.lfdpr_recon_forward.argtypes = [P, P, P, P, P, C.c_float, P, P]
         L.lfdpr_recon_status.argtypes = [P, P]
         L.lfdpr_conv3x3_bf16.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int32, P, P]
         L.lfdpr_warp_views.argtypes = [P, P, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, C.c_float, P, P]
@@ -487,8 +487,11 @@ def lfdpr_recon_run(recon: int, src_disp: int, dst_disp: int, stream=None):
     _check(lib().lfdpr_recon_run(recon, src_disp, dst_disp, _stream(stream)))
 
 
-def lfdpr_recon_forward(recon: int, in_ptr: int, out_ptr: int, stream=None):
-    _check(lib().lfdpr_recon_forward(recon, C.c_void_p(in_ptr), C.c_void_p(out_ptr), _stream(stream)))
+def lfdpr_recon_forward(recon: int, in_ptr: int, keys_ptr: int, in_eyes_ptr: int, out_eyes_ptr: int,
+                        pixels_per_unit: float, out_ptr: int, stream=None):
+    _check(lib().lfdpr_recon_forward(recon, C.c_void_p(in_ptr), C.c_void_p(keys_ptr), C.c_void_p(in_eyes_ptr),
+                                     C.c_void_p(out_eyes_ptr), float(pixels_per_unit), C.c_void_p(out_ptr),
+                                     _stream(stream)))
 
 
 def lfdpr_warp_views(in_views_ptr: int, in_keys_ptr: int, in_eyes_ptr: int, in_count: int, out_eyes_ptr: int,
@@ -686,8 +689,10 @@ class Recon:
     def run(self, src_disp: int, dst_disp: int, stream=None):
         lfdpr_recon_run(self.handle, src_disp, dst_disp, stream)
 
-    def forward(self, in_ptr: int, out_ptr: int, stream=None):
-        lfdpr_recon_forward(self.handle, in_ptr, out_ptr, stream)
+    def forward(self, in_ptr: int, keys_ptr: int, in_eyes_ptr: int, out_eyes_ptr: int, pixels_per_unit: float,
+                out_ptr: int, stream=None):
+        lfdpr_recon_forward(self.handle, in_ptr, keys_ptr, in_eyes_ptr, out_eyes_ptr, pixels_per_unit, out_ptr,
+                            stream)
 
     def status(self) -> int:
         return lfdpr_recon_status(self.handle)

@@ -3,7 +3,8 @@
 The architecture is the one include/lfdpr_recon.h fixes: n rendered views in,
 the 4n views of the full display after angular supersampling and the
 [1/4, 1/2, 1/4] tent reconstruction (Sec. 4) out, as a residual over the
-linear angular interpolation of the input views. This module holds
+input views warped to the output eyes by their depth keys (the library's
+lfdpr_warp_views). This module holds
 
   * the architecture (UNet) and its export to the library's weight layout;
   * reference_forward: the same forward pass in fp32 that rounds to bf16
@@ -35,21 +36,33 @@ def padded(h: int, w: int):
     return (h + 7) // 8 * 8, (w + 7) // 8 * 8
 
 
-def base_matrix(nin: int) -> np.ndarray:
-    """[3 * 4 nin, 48]: output view k, channel c = (1 - t) input j0 + t input
-    j1 with input j at output index 4 j + 3/2 (clamped at the ends), in the
-    binary32 arithmetic of the library's output kernel."""
-    nout = 4 * nin
-    m = np.zeros((3 * nout, IN_CHANNELS), np.float32)
-    for k in range(nout):
-        pos = np.float32((np.float32(k) - np.float32(1.5)) * np.float32(0.25))
-        j0 = min(max(int(math.floor(pos)), 0), max(nin - 2, 0))
-        t = float(np.float32(min(max(pos - np.float32(j0), np.float32(0.0)), np.float32(1.0)))) if nin > 1 else 0.0
-        j1 = j0 + 1 if nin > 1 else j0
-        for c in range(3):
-            m[3 * k + c, 3 * j0 + c] += 1.0 - t
-            m[3 * k + c, 3 * j1 + c] += t
-    return m
+def pixels_per_unit(d) -> float:
+    """view_w / focal_w as the library's display constants hold it."""
+    return float(np.float32(float(d.view_w) / float(d.focal_w)))
+
+
+def warped_base(views_u8, keys, in_eyes, out_eyes, ppu: float):
+    """The residual's base: the library's depth-guided warp of the input views
+    [nin][H][W][4] (u8 torch, device) with their depth keys (int64 torch,
+    device) from input eyes to output eyes (f32 torch, device) -> u8
+    [nout][H][W][4] (torch, device)."""
+    torch = _torch()
+    from . import lfdpr
+    nin, h, w, _ = views_u8.shape
+    out = torch.empty((len(out_eyes), h, w, 4), dtype=torch.uint8, device=views_u8.device)
+    lfdpr.lfdpr_warp_views(views_u8.data_ptr(), keys.data_ptr(), in_eyes.data_ptr(), nin, out_eyes.data_ptr(),
+                           len(out_eyes), w, h, ppu, out.data_ptr(), torch.cuda.current_stream())
+    return out
+
+
+def base_input(warp_u8, hp: int, wp: int):
+    """[1, 3 nout, hp, wp] float: the warped views' RGB times 1/255 (the
+    library's conversion into the base channels), zero outside the views."""
+    torch = _torch()
+    n, h, w, _ = warp_u8.shape
+    x = torch.zeros((1, 3 * n, hp, wp), dtype=torch.float32, device=warp_u8.device)
+    x[0, :, :h, :w] = warp_u8[..., :3].permute(0, 3, 1, 2).reshape(3 * n, h, w).float() * np.float32(1.0 / 255.0)
+    return x
 
 
 def _torch():
@@ -67,7 +80,6 @@ def make_unet(nin: int = 12):
             self.nin = nin
             self.convs = nn.ModuleList([nn.Conv2d(ci, co, 3, padding=1) for ci, co, _ in LAYERS])
             self.out = nn.Conv2d(32, 3 * 4 * nin, 1)
-            self.register_buffer("M", torch.from_numpy(base_matrix(nin)))
 
         def features(self, x):
             c, r = self.convs, F.relu
@@ -83,8 +95,7 @@ def make_unet(nin: int = 12):
             d1 = r(c[11](r(c[10](torch.cat([up(d2), e1], 1)))))
             return r(c[13](r(c[12](torch.cat([up(d1), e0], 1)))))
 
-        def forward(self, x):
-            base = torch.einsum("oc,bchw->bohw", self.M.to(x.dtype), x)
+        def forward(self, x, base):
             return self.out(self.features(x)) + base
 
     return UNet()
@@ -166,9 +177,10 @@ def _bf16(t):
     return t.to(torch.bfloat16).float()
 
 
-def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin: int):
+def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin: int, warp_u8):
     """The library's forward pass in fp32, rounding to bf16 where its kernels
-    store bf16: views [nin][H][W][4] u8 (torch) -> [4 nin][H][W][4] u8."""
+    store bf16: views [nin][H][W][4] u8 and their warp to the output eyes
+    warp_u8 [4 nin][H][W][4] u8 (torch) -> [4 nin][H][W][4] u8."""
     torch = _torch()
     F = torch.nn.functional
     dev = views_u8.device
@@ -203,9 +215,10 @@ def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin
     d2 = conv(9, conv(8, torch.cat([up(b), e2], 1)))
     d1 = conv(11, conv(10, torch.cat([up(d2), e1], 1)))
     d0 = conv(13, conv(12, torch.cat([up(d1), e0], 1)))
-    # the library's output layer: one product over [d0 (32) | x0 (48)]
-    w_all = torch.cat([w_out, torch.from_numpy(base_matrix(nin)).to(dev)], 1)
-    out = torch.einsum("ok,bkhw->bohw", w_all, torch.cat([d0, x0], 1)) + b_out[None, :, None, None]
+    # the library's output layer: the 1x1 product of d0, plus the base (RGB /
+    # 255 rounded to bf16), plus the bias
+    base = _bf16(base_input(warp_u8, hp, wp))
+    out = (torch.einsum("ok,bkhw->bohw", w_out, d0) + base) + b_out[None, :, None, None]
     v = torch.round(out.clamp(0.0, 1.0) * 255.0)[0, :, :h, :w]
     rgb = v.reshape(4 * nin, 3, h, w).permute(0, 2, 3, 1).to(torch.uint8)
     res = torch.full((4 * nin, h, w, 4), 255, dtype=torch.uint8, device=dev)
@@ -243,6 +256,13 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 200, seed: int = 0,
     ts = lfdpr.TextureSet(S.textures_paper())
     disp_in = lfdpr.lfdpr_create_display(lfdpr.desc_of(d_in, 1 << 23))
     disp_full = lfdpr.lfdpr_create_display(lfdpr.desc_of(d_full, 1 << 23))
+    # the base: the input views warped to the 4n output eyes
+    d_out = replace(S.display_paper(), n_views=4 * nin)
+    disp_out = lfdpr.lfdpr_create_display(lfdpr.desc_of(d_out))
+    in_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(disp_in, nin)).to(dev)
+    out_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(disp_out, 4 * nin)).to(dev)
+    lfdpr.lfdpr_destroy_display(disp_out)
+    ppu = pixels_per_unit(d_in)
     pool = min(pool, n_scenes)
     scene_no = [0]
 
@@ -281,8 +301,9 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 200, seed: int = 0,
         bi = lfdpr.lfdpr_get_buffers(disp_in, m_in)
         bf = lfdpr.lfdpr_get_buffers(disp_full, m_full)
         v_in = lfdpr.device_view(bi.views, (nin, H, W, 4), np.uint8)
+        k_in = lfdpr.device_view(bi.keys, (nin, H, W), np.uint64)
         v_full = lfdpr.device_view(bf.views, (2 * d_full.n_views, H, W, 4), np.uint8)
-        return v_in, v_full
+        return v_in, k_in, v_full
 
     for it in range(iters):
         if it > 0 and it % replace_every == 0 and scene_no[0] < n_scenes:
@@ -293,11 +314,12 @@ def train(out_path: str, iters: int = 20000, n_scenes: int = 200, seed: int = 0,
             meshes[slot] = new_scene()
         k = int(rng.integers(pool))
         mm = pose()
-        v_in, v_full = stack(meshes[k][0], meshes[k][1], mm)
+        v_in, k_in, v_full = stack(meshes[k][0], meshes[k][1], mm)
         x = network_input(v_in, nin, hp, wp)
+        base = base_input(warped_base(v_in, k_in, in_eyes, out_eyes, ppu), hp, wp)
         tgt = tent_views(v_full).permute(0, 3, 1, 2).reshape(1, -1, H, W).float() / 255.0
         with torch.autocast("cuda", dtype=torch.bfloat16):
-            pred = model(x)
+            pred = model(x, base)
         loss = torch.mean((pred.float()[:, :, :H, :W] - tgt) ** 2)
         opt.zero_grad(set_to_none=True)
         loss.backward()
@@ -327,7 +349,8 @@ def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=rang
     render on the paper-shaped scene (orbit frames, 3 degrees each): the
     library renders the n-view display and the 2x-angular full display, its
     kernels run the network into the 4n-view display, and the prediction is
-    compared with the full render's tent reconstruction."""
+    compared with the full render's tent reconstruction; the warped base
+    alone is scored too."""
     torch = _torch()
     from . import lfdpr, scenes as S
     sc = S.scene_paper()
@@ -339,6 +362,8 @@ def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=rang
     disps = [lfdpr.lfdpr_create_display(lfdpr.desc_of(d)) for d in (d_in, d_full, d_out)]
     meshes = [lfdpr.lfdpr_upload_mesh_textured(disps[k], sc.xyz, sc.uv, sc.idx, sc.tri_tex, ts.handle)
               for k in range(2)]
+    in_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(disps[0], nin)).cuda()
+    out_eyes = torch.from_numpy(lfdpr.lfdpr_view_eyes(disps[2], 4 * nin)).cuda()
     res = []
     with lfdpr.Recon(W, H, nin, weights, biases) as R:
         for f in frames:
@@ -352,12 +377,10 @@ def evaluate(weights: np.ndarray, biases: np.ndarray, nin: int = 12, frames=rang
             pred = lfdpr.device_view(bo.views, (4 * nin, H, W, 4), np.uint8)[..., :3]
             bi = lfdpr.lfdpr_get_buffers(disps[0], meshes[0])
             inp = lfdpr.device_view(bi.views, (nin, H, W, 4), np.uint8)
-            x = network_input(inp, nin, *padded(H, W))
-            base = torch.einsum("oc,bchw->bohw", torch.from_numpy(base_matrix(nin)).to(x.device), x)
-            base = torch.round(base.clamp(0, 1) * 255.0)[0, :, :H, :W].reshape(4 * nin, 3, H, W)
-            base = base.permute(0, 2, 3, 1).to(torch.uint8)
+            keys = lfdpr.device_view(bi.keys, (nin, H, W), np.uint64)
+            base = warped_base(inp, keys, in_eyes, out_eyes, pixels_per_unit(d_in))[..., :3]
             res.append({"frame": int(f), "psnr": psnr(pred, truth), "ssim": ssim(pred, truth),
-                        "psnr_interp": psnr(base, truth)})
+                        "psnr_warp": psnr(base, truth)})
     for m_ in meshes:
         lfdpr.lfdpr_destroy_mesh(m_)
     for d_ in disps:

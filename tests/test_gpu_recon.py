@@ -69,6 +69,9 @@ def _random_net(torch, seed):
 
 @pytest.mark.parametrize("h,w", [(40, 44), (64, 56), (560, 420)])
 def test_forward_matches_reference(torch, h, w):
+    """The whole forward pass, with its warped base (the warp itself is held
+    byte-exact to its own restatement in test_gpu_warp.py), against the fp32
+    reference that rounds where the kernels store bf16."""
     wts, bs = _random_net(torch, 7)
     g = torch.Generator(device="cpu").manual_seed(h * w)
     # smooth-ish random views so the network sees image-like inputs
@@ -76,12 +79,21 @@ def test_forward_matches_reference(torch, h, w):
     views = torch.nn.functional.interpolate(base.permute(0, 3, 1, 2), size=(h, w), mode="bilinear",
                                             align_corners=False).permute(0, 2, 3, 1)
     views = (views * 255).round().to(torch.uint8).contiguous().cuda()
+    # depth keys: ray parameters around the focal plane, a fifth of the pixels empty
+    t = (0.6 + 0.8 * torch.rand((12, h, w), generator=g)).numpy().astype(np.float32)
+    keys = (t.view(np.uint32).astype(np.uint64) << np.uint64(32))
+    keys[np.random.default_rng(h).random((12, h, w)) < 0.2] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    keys = torch.from_numpy(keys.view(np.int64)).cuda()
+    in_eyes = torch.linspace(-1.4, 1.4, 12, dtype=torch.float32).cuda()
+    out_eyes = torch.linspace(-1.45, 1.45, 48, dtype=torch.float32).cuda()
+    ppu = 100.0
     out = torch.zeros((48, h, w, 4), dtype=torch.uint8, device="cuda")
     with lfdpr.Recon(w, h, 12, wts, bs) as R:
-        R.forward(views.data_ptr(), out.data_ptr())
+        R.forward(views.data_ptr(), keys.data_ptr(), in_eyes.data_ptr(), out_eyes.data_ptr(), ppu, out.data_ptr())
         torch.cuda.synchronize()
         assert R.status() == 0
-    ref = RN.reference_forward(wts, bs, views, 12)
+    warp = RN.warped_base(views, keys, in_eyes, out_eyes, ppu)
+    ref = RN.reference_forward(wts, bs, views, 12, warp)
     d = (out.int() - ref.int()).abs()
     assert torch.all(out[..., 3] == 255)
     assert int(d.max()) <= 3

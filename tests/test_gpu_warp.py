@@ -93,7 +93,7 @@ def warp_reference(views, keys, in_eyes, out_eyes, ipw):
                 agree = okn & (np.abs(tn - t) <= F32(0.01) * t)
                 wt.append(np.where(agree, (F32(1) - s) if src == 0 else s, F32(0)).astype(F32))
             ws = wt[0] + wt[1]
-            blend = (wt[0][..., None] * vs[0] + wt[1][..., None] * vs[1]) / ws[..., None]
+            blend = (wt[0][..., None] * vs[0] + wt[1][..., None] * vs[1]) * (F32(1) / ws)[..., None]
             ssrc = ((win >> np.uint64(16)) & np.uint64(1)).astype(np.int64)
             sidx = (win & np.uint64(0xFFFF)).astype(np.int64)
             own = np.where((ssrc == 0)[..., None], src_col[0][rows, np.minimum(sidx, W - 1)],
