@@ -29,7 +29,7 @@
 //                 zeros on the border ring, one 16-byte store per chunk.
 //   k_conv_tc<1>  the output layer: the 1x1 convolution of d0 (32
 //                 channels), plus the base (the input views warped to the
-//                 output eyes by warp.cu's k_warp_views, RGB / 255 as bf16)
+//                 output eyes by warp.cu's k_warp_views, RGB / 255)
 //                 and the bias, clamped, scaled to 255, rounded half to even,
 //                 written as RGBA8 output views.
 //   k_pack_w      weights [cout][taps][cin] -> the per-K-step stage images
@@ -462,13 +462,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                         for (int k = 0; k < 16; k++) {
                             const int view = j / 3 + k;
                             if (!(inside && view < g.nout)) continue;
-                            // the base's RGB / 255 as bf16 values, added to the product
+                            // the base's RGB / 255, added to the product
                             const uint32_t bw = bws[k];
                             float base[3];
 #pragma unroll
-                            for (int c = 0; c < 3; c++)
-                                base[c] = __bfloat162float(
-                                    __float2bfloat16_rn(float((bw >> (8 * c)) & 255u) * (1.0f / 255.0f)));
+                            for (int c = 0; c < 3; c++) base[c] = float((bw >> (8 * c)) & 255u) * (1.0f / 255.0f);
                             // round(clamp(x + base + b, 0, 1) 255), half to even: saturating add, scale, convert
                             const uint32_t r0 = __float2uint_rn(__saturatef((v[3 * k] + base[0]) + bv[3 * k]) * 255.0f);
                             const uint32_t g0 =

@@ -216,8 +216,8 @@ def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin
     d1 = conv(11, conv(10, torch.cat([up(d2), e1], 1)))
     d0 = conv(13, conv(12, torch.cat([up(d1), e0], 1)))
     # the library's output layer: the 1x1 product of d0, plus the base (RGB /
-    # 255 rounded to bf16), plus the bias
-    base = _bf16(base_input(warp_u8, hp, wp))
+    # 255 in binary32), plus the bias
+    base = base_input(warp_u8, hp, wp)
     out = (torch.einsum("ok,bkhw->bohw", w_out, d0) + base) + b_out[None, :, None, None]
     v = torch.round(out.clamp(0.0, 1.0) * 255.0)[0, :, :h, :w]
     rgb = v.reshape(4 * nin, 3, h, w).permute(0, 2, 3, 1).to(torch.uint8)
