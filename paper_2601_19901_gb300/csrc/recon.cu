@@ -820,6 +820,8 @@ struct lfdpr_recon {
     TcGeom geom[14] = {}, geom_out = {};
     CUtensorMap in_map[14], in_map_b[14], out_d0;
     uint8_t* warp = nullptr;          // [nout][H][W][4] the input views warped to the output eyes (RGBA8)
+    cudaStream_t side = nullptr;      // the warp runs here, beside the network's layers
+    cudaEvent_t fork = nullptr, join = nullptr;
     __nv_bfloat16* act = nullptr;     // activation arena (chunked bordered tensors)
     // encoder e*, pooled p*, bottleneck ba, upsampled U* (written by layers 7, 9, 11), decoder d*
     __nv_bfloat16 *x0, *e0a, *e0, *p1, *e1a, *e1, *p2, *e2a, *e2, *p3, *ba, *U2, *d2a, *U1, *d1a, *U0, *d0a, *d0;
@@ -836,6 +838,9 @@ void free_recon(lfdpr_recon* r) {
     dev_free(r->status);
     dev_free(r->warp);
     dev_free(r->act);
+    if (r->fork) cudaEventDestroy(r->fork);
+    if (r->join) cudaEventDestroy(r->join);
+    if (r->side) cudaStreamDestroy(r->side);
     delete r;
 }
 
@@ -917,6 +922,14 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
         dev_free(wout_raw);
         free_recon(r);
         return cuda_fail(e, "create_recon: allocation");
+    }
+    if ((e = cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming)) != cudaSuccess) {
+        dev_free(w_raw);
+        dev_free(wout_raw);
+        free_recon(r);
+        return cuda_fail(e, "create_recon: stream");
     }
     __nv_bfloat16** bufs[kTensors] = {&r->x0,  &r->e0a, &r->e0, &r->p1, &r->e1a, &r->e1,  &r->p2,  &r->e2a, &r->e2,
                                       &r->p3,  &r->ba,  &r->U2, &r->d2a, &r->U1, &r->d1a, &r->U0, &r->d0a, &r->d0};
@@ -1025,10 +1038,14 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, const 
     } while (0)
     k_recon_in<<<sm * 8, 256, 0, s>>>(in_views, r->nin, r->H, r->W, H0, W0, r->x0);
     CKR(cudaGetLastError(), "launch k_recon_in");
-    // the residual's base: the input views warped to the output eyes
+    // the residual's base: the input views warped to the output eyes, on the
+    // side stream while the layers run (SMs the layers leave idle take it)
+    CKR(cudaEventRecord(r->fork, s), "recon_forward: fork");
+    CKR(cudaStreamWaitEvent(r->side, r->fork, 0), "recon_forward: fork");
     CKR(launch_warp_views(in_views, in_keys, in_eyes, r->nin, out_eyes, r->nout, r->W, r->H, pixels_per_unit,
-                          r->warp, s),
+                          r->warp, r->side),
         "launch k_warp_views");
+    CKR(cudaEventRecord(r->join, r->side), "recon_forward: join");
 
     CKR(conv(0), "conv 0");
     CKR(conv(1), "conv 1");
@@ -1047,6 +1064,7 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, const 
     CKR(conv(11), "conv 11");
     CKR(conv(12), "conv 12");
     CKR(conv(13), "conv 13");
+    CKR(cudaStreamWaitEvent(s, r->join, 0), "recon_forward: join");
     CKR(launch_tc(1, r->geom_out, r->out_d0, r->out_d0, r->w_out, r->b_out, out_views, r->status, s),
         "output layer");
 #undef CKR
