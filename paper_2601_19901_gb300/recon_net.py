@@ -230,7 +230,7 @@ def reference_forward(weights_u16: np.ndarray, biases: np.ndarray, views_u8, nin
 # Offline training on view stacks the library renders
 # ---------------------------------------------------------------------------
 
-def train(out_path: str, iters: int = 20000, n_scenes: int = 200, seed: int = 0, lr: float = 1e-3,
+def train(out_path: str, iters: int = 60000, n_scenes: int = 200, seed: int = 0, lr: float = 1e-3,
           log_every: int = 1000, eval_frames: int = 8, pool: int = 16):
     """Train on `iters` stacks: each is a random training scene at a random
     camera pose (a turn about the vertical, a tilt of up to 15 degrees and a
@@ -400,7 +400,7 @@ if __name__ == "__main__":
     import argparse
     p = argparse.ArgumentParser(description="train the angular reconstruction network")
     p.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "recon_weights.npz"))
-    p.add_argument("--iters", type=int, default=20000)
+    p.add_argument("--iters", type=int, default=60000)
     p.add_argument("--scenes", type=int, default=200)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lr", type=float, default=1e-3)
