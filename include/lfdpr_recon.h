@@ -49,7 +49,7 @@ int64_t lfdpr_recon_bias_count(int32_t in_views);
 
 /*
  * lfdpr_create_recon: a network for in_views (even, 2..16) input views of
- * view_w x view_h pixels (8..4096 a side); weights_bf16 and biases (host)
+ * view_w x view_h pixels (8..4032 wide, 8..4096 high); weights_bf16 and biases (host)
  * are copied; the activation buffers are allocated once here.
  * Errors: EINVAL (counts not as above), ENOMEM, ECUDA.
  */
@@ -107,7 +107,7 @@ lfdpr_status lfdpr_recon_status(lfdpr_recon *recon, int32_t *flags);
  *  out_eyes   device f32 [out_count]: the output eyes' x
  *  pixels_per_unit  view_w / focal_w of the display
  *  out_views  device u8 [out_count][view_h][view_w][4], caller-owned
- * Limits: 2 <= in_count, 1 <= out_count, both <= 512; view_w <= 4096,
+ * Limits: 2 <= in_count, 1 <= out_count, both <= 512; view_w <= 4032,
  * view_h <= 16384. Asynchronous on `stream`. Errors: EINVAL, ECUDA.
  */
 lfdpr_status lfdpr_warp_views(const uint8_t *in_views, const uint64_t *in_keys, const float *in_eyes, int32_t in_count,

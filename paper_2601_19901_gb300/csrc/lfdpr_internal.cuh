@@ -312,7 +312,7 @@ constexpr uint32_t kSplatLaneLimit = 1u << 24;
 cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s);
 // The depth-guided warp of nin rendered views (RGBA8 and depth keys) to nout
 // eyes on the same eye line (warp.cu); views at most kMaxWarpWidth wide.
-constexpr int kMaxWarpWidth = 4096;
+constexpr int kMaxWarpWidth = 4032;   // the warp block's shared memory: 56 bytes a pixel at the widest
 cudaError_t launch_warp_views(const uint8_t* views, const uint64_t* keys, const float* in_eyes, int nin,
                               const float* out_eyes, int nout, int W, int H, float ipw, uint8_t* out,
                               cudaStream_t s);

@@ -870,8 +870,8 @@ lfdpr_status lfdpr_create_recon(int32_t view_w, int32_t view_h, int32_t in_views
     *out = nullptr;
     if (in_views < 2 || in_views > 16 || (in_views & 1))
         return fail(LFDPR_EINVAL, "create_recon: in_views must be even, in [2, 16]");
-    if (view_w < 8 || view_h < 8 || view_w > 4096 || view_h > 4096)
-        return fail(LFDPR_EINVAL, "create_recon: views must be 8..4096 pixels a side");
+    if (view_w < 8 || view_h < 8 || view_w > kMaxWarpWidth || view_h > 4096)
+        return fail(LFDPR_EINVAL, "create_recon: views must be 8..%d pixels wide, 8..4096 high", kMaxWarpWidth);
     if (n_weights != lfdpr_recon_weight_count(in_views) || n_biases != lfdpr_recon_bias_count(in_views))
         return fail(LFDPR_EINVAL, "create_recon: expected %lld weights and %lld biases",
                     (long long)lfdpr_recon_weight_count(in_views), (long long)lfdpr_recon_bias_count(in_views));

@@ -68,22 +68,32 @@ __device__ __forceinline__ int bracket(const WarpArgs& a, float E, float& s) {
 // Views an interval block takes at a time, for view width W.
 __host__ __device__ __forceinline__ int views_per_pass(int W) {
     const int v = 32768 / (8 * W);
-    return v < 1 ? 1 : (v > 8 ? 8 : v);
+    return v < 1 ? 1 : (v > 4 ? 4 : v);
+}
+
+// (m, r) -> (m, r + step) over rows of length L, for step and r < L.
+__device__ __forceinline__ void advance(int& m, int& r, int step, int L) {
+    r += step;
+    while (r >= L) {
+        r -= L;
+        m++;
+    }
 }
 
 // Block (row y, input interval j): every output view whose bracket is
 // (j, j + 1), up to views_per_pass(W) of them at a time. The two input rows
-// are staged once in shared memory with each pixel's t and disparity factor
-// g = (1 - 1/t) W / fw (NaN where it has no key). The nearest point per
-// output pixel is the 64-bit minimum of (t bits, input, source pixel).
+// are staged once in shared memory with each pixel's t, disparity factor
+// g = (1 - 1/t) W / fw (both NaN where it has no key) and colour as binary32.
+// The nearest point per output pixel is the 64-bit minimum of (t bits,
+// input, source pixel).
 __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
     extern __shared__ __align__(16) uint8_t s_raw[];
     const int y = blockIdx.x, j = blockIdx.y, W = a.W, V = views_per_pass(W);
     if (y >= a.H || j > a.nin - 2) return;
-    float* s_t = reinterpret_cast<float*>(s_raw);               // [2][W]
-    float* s_g = s_t + 2 * W;                                   // [2][W]
-    uint32_t* s_c = reinterpret_cast<uint32_t*>(s_g + 2 * W);   // [2][W]
-    unsigned long long* s_win = reinterpret_cast<unsigned long long*>(s_c + 2 * W);   // [V][W] nearest point
+    float4* s_rgb = reinterpret_cast<float4*>(s_raw);                       // [2][W] colour
+    float* s_t = reinterpret_cast<float*>(s_rgb + 2 * W);                   // [2][W]
+    float* s_g = s_t + 2 * W;                                               // [2][W]
+    unsigned long long* s_win = reinterpret_cast<unsigned long long*>(s_g + 2 * W);   // [V][W] nearest point
     __shared__ int s_views[kMaxRenderViews];
     __shared__ float s_w[kMaxRenderViews], s_E[kMaxRenderViews];
     __shared__ int s_n;
@@ -96,7 +106,8 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
         const bool ok = key_depth(a.keys[o], t);
         s_t[q] = ok ? t : __int_as_float(0x7fc00000);   // NaN: no key
         s_g[q] = ok ? (1.0f - 1.0f / t) * a.ipw : __int_as_float(0x7fc00000);
-        s_c[q] = reinterpret_cast<const uint32_t*>(a.views)[o];
+        const uint32_t c = reinterpret_cast<const uint32_t*>(a.views)[o];
+        s_rgb[q] = make_float4(channel(c, 0), channel(c, 1), channel(c, 2), 0.0f);
     }
     __syncthreads();
     // the output views of this interval with their weights
@@ -113,19 +124,21 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
     __syncthreads();
     const int n_views = s_n;
     const float eye[2] = {a.in_eyes[j], a.in_eyes[j + 1]};
+    const int step = blockDim.x;
     for (int m0 = 0; m0 < n_views; m0 += V) {
         const int nv = min(V, n_views - m0);
-        for (int q = threadIdx.x; q < nv * W; q += blockDim.x) s_win[q] = kNoKey;
+        for (int q = threadIdx.x; q < nv * W; q += step) s_win[q] = kNoKey;
         __syncthreads();
         // 1. forward: the nearest point landing on each pixel (t, then input,
-        // then source pixel)
-        for (int m = 0; m < nv; m++) {
-            const float d0 = s_E[m0 + m] - eye[0], d1 = s_E[m0 + m] - eye[1];
-            for (int r = threadIdx.x; r < 2 * W; r += blockDim.x) {
-                const int src = r >= W, i = r - src * W;
+        // then source pixel); candidates (view m, input pixel r) in one sweep
+        {
+            int m = 0, r = threadIdx.x;
+            advance(m, r, 0, 2 * W);
+            for (; m < nv; advance(m, r, step, 2 * W)) {
                 const float g = s_g[r];
                 if (isnan(g)) continue;
-                const float X = (float(i) + 0.5f) + g * (src ? d1 : d0);
+                const int src = r >= W, i = r - src * W;
+                const float X = (float(i) + 0.5f) + g * (s_E[m0 + m] - eye[src]);
                 if (!isfinite(X)) continue;
                 const float px = floorf(X);
                 if (px < 0.0f || px >= float(W)) continue;
@@ -134,21 +147,24 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
             }
         }
         __syncthreads();
-        // 2. backward
-        for (int m = 0; m < nv; m++)
-        for (int p = threadIdx.x; p < W; p += blockDim.x) {
-            const int q = m * W + p, k = s_views[m0 + m];
+        // 2. backward: output pixels (view m, pixel p) in one sweep
+        int m = 0, p = threadIdx.x;
+        advance(m, p, 0, W);
+        for (; m < nv; advance(m, p, step, W)) {
+            const int k = s_views[m0 + m];
             const float E = s_E[m0 + m], s = s_w[m0 + m];
-            const uint64_t w = s_win[q];
+            const uint64_t w = s_win[m * W + p];
             float v[3];
             if (w == kNoKey) {
-                const uint32_t c0 = s_c[p], c1 = s_c[W + p];
-#pragma unroll
-                for (int c = 0; c < 3; c++) v[c] = (1.0f - s) * channel(c0, c) + s * channel(c1, c);
+                const float4 c0 = s_rgb[p], c1 = s_rgb[W + p];
+                v[0] = (1.0f - s) * c0.x + s * c1.x;
+                v[1] = (1.0f - s) * c0.y + s * c1.y;
+                v[2] = (1.0f - s) * c0.z + s * c1.z;
             } else {
                 const int ws_ = int((w >> 16) & 1u), wi = int(w & 0xffffu);
                 const float t = s_t[ws_ * W + wi], g = s_g[ws_ * W + wi];
-                float vs[2][3], wt[2];
+                float4 vs[2];
+                float wt[2];
 #pragma unroll
                 for (int src = 0; src < 2; src++) {
                     const float X = (float(p) + 0.5f) + g * (eye[src] - E);
@@ -159,12 +175,9 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
                     const int i0 = int(fminf(fmaxf(fl, 0.0f), float(W - 1)));
                     const int i1 = int(fminf(fmaxf(fl + 1.0f, 0.0f), float(W - 1)));
                     const int n = int(fminf(fmaxf(fn, 0.0f), float(W - 1)));
-                    const uint32_t ca = s_c[src * W + i0], cb = s_c[src * W + i1];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const float va = channel(ca, c), vb = channel(cb, c);
-                        vs[src][c] = va + fr * (vb - va);
-                    }
+                    const float4 ca = s_rgb[src * W + i0], cb = s_rgb[src * W + i1];
+                    vs[src] = make_float4(ca.x + fr * (cb.x - ca.x), ca.y + fr * (cb.y - ca.y),
+                                          ca.z + fr * (cb.z - ca.z), 0.0f);
                     const float tn = s_t[src * W + n];
                     const bool agree = !isnan(tn) && fabsf(tn - t) <= 0.01f * t;
                     wt[src] = agree ? (src == 0 ? 1.0f - s : s) : 0.0f;
@@ -172,12 +185,14 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp_views(WarpArgs a) {
                 const float ws = wt[0] + wt[1];
                 if (ws > 0.0f) {
                     const float rw = 1.0f / ws;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) v[c] = (wt[0] * vs[0][c] + wt[1] * vs[1][c]) * rw;
+                    v[0] = (wt[0] * vs[0].x + wt[1] * vs[1].x) * rw;
+                    v[1] = (wt[0] * vs[0].y + wt[1] * vs[1].y) * rw;
+                    v[2] = (wt[0] * vs[0].z + wt[1] * vs[1].z) * rw;
                 } else {
-                    const uint32_t cs = s_c[ws_ * W + wi];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) v[c] = channel(cs, c);
+                    const float4 cs = s_rgb[ws_ * W + wi];
+                    v[0] = cs.x;
+                    v[1] = cs.y;
+                    v[2] = cs.z;
                 }
             }
             uint32_t o = 0xff000000u;
@@ -196,9 +211,9 @@ cudaError_t launch_warp_views(const uint8_t* views, const uint64_t* keys, const 
                               cudaStream_t s) {
     if (nin < 2 || nout < 1 || W < 1 || H < 1 || W > kMaxWarpWidth || H > 65535 || nout > kMaxRenderViews || !(ipw > 0.0f))
         return cudaErrorInvalidValue;
-    // shared memory: the two input rows (t, g, colour) and the pass's minima:
-    // (24 + 8 V) bytes a pixel, at most 128 KB
-    const size_t smem = (24u + 8u * size_t(views_per_pass(W))) * size_t(W);
+    // shared memory: the two input rows (colour, t, g) and the pass's minima:
+    // (48 + 8 V) bytes a pixel, at most 224 KB
+    const size_t smem = (48u + 8u * size_t(views_per_pass(W))) * size_t(W);
     if (smem > 48u * 1024u) {
         const cudaError_t e = cudaFuncSetAttribute(k_warp_views, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;

@@ -143,10 +143,11 @@ def _eyes(d):
         return R.eyes()
 
 
-@pytest.mark.parametrize("case", ["random", "coincident_eyes", "outside_span", "far_and_near"])
+@pytest.mark.parametrize("case", ["random", "coincident_eyes", "outside_span", "far_and_near", "widest"])
 def test_warp_of_synthetic_keys_matches_the_reference(case):
-    rng = np.random.default_rng({"random": 1, "coincident_eyes": 2, "outside_span": 3, "far_and_near": 4}[case])
-    nin, H, W = 5, 7, 173
+    rng = np.random.default_rng({"random": 1, "coincident_eyes": 2, "outside_span": 3, "far_and_near": 4,
+                                 "widest": 5}[case])
+    nin, H, W = (5, 7, 173) if case != "widest" else (3, 3, 4032)
     in_eyes = np.sort(rng.uniform(-1.0, 1.0, nin)).astype(F32)
     out_eyes = rng.uniform(-1.0, 1.0, 9).astype(F32)
     if case == "coincident_eyes":
