@@ -108,7 +108,9 @@ lfdpr_status lfdpr_recon_status(lfdpr_recon *recon, int32_t *flags);
  *  pixels_per_unit  view_w / focal_w of the display
  *  out_views  device u8 [out_count][view_h][view_w][4], caller-owned
  * Limits: 2 <= in_count, 1 <= out_count, both <= 512; view_w <= 4032,
- * view_h <= 16384. Asynchronous on `stream`. Errors: EINVAL, ECUDA.
+ * view_h <= 16384; views and eyes 4-byte aligned, keys 8-byte aligned.
+ * Asynchronous on `stream`. Errors: EINVAL (also a limit or alignment not
+ * met), ECUDA.
  */
 lfdpr_status lfdpr_warp_views(const uint8_t *in_views, const uint64_t *in_keys, const float *in_eyes, int32_t in_count,
                               const float *out_eyes, int32_t out_count, int32_t view_w, int32_t view_h,

@@ -1020,6 +1020,10 @@ lfdpr_status lfdpr_recon_forward(lfdpr_recon* r, const uint8_t* in_views, const 
         return fail(LFDPR_EINVAL, "recon_forward: null argument");
     if (!(pixels_per_unit > 0.0f) || !std::isfinite(pixels_per_unit))
         return fail(LFDPR_EINVAL, "recon_forward: pixels_per_unit must be positive and finite");
+    if ((reinterpret_cast<uintptr_t>(in_views) & 3u) || (reinterpret_cast<uintptr_t>(out_views) & 3u) ||
+        (reinterpret_cast<uintptr_t>(in_keys) & 7u) || (reinterpret_cast<uintptr_t>(in_eyes) & 3u) ||
+        (reinterpret_cast<uintptr_t>(out_eyes) & 3u))
+        return fail(LFDPR_EINVAL, "recon_forward: views and eyes must be 4-byte aligned, keys 8-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H0 = r->Hp, W0 = r->Wp, sm = r->sm_count;
     __nv_bfloat16* conv_out[14] = {r->e0a, r->e0, r->e1a, r->e1, r->e2a, r->e2, r->ba,

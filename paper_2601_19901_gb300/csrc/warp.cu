@@ -239,6 +239,10 @@ extern "C" lfdpr_status lfdpr_warp_views(const uint8_t* in_views, const uint64_t
                            lfdpr::kMaxWarpWidth);
     if (!(pixels_per_unit > 0.0f) || !std::isfinite(pixels_per_unit))
         return lfdpr::fail(LFDPR_EINVAL, "warp_views: pixels_per_unit must be positive and finite");
+    if ((reinterpret_cast<uintptr_t>(in_views) & 3u) || (reinterpret_cast<uintptr_t>(out_views) & 3u) ||
+        (reinterpret_cast<uintptr_t>(in_keys) & 7u) || (reinterpret_cast<uintptr_t>(in_eyes) & 3u) ||
+        (reinterpret_cast<uintptr_t>(out_eyes) & 3u))
+        return lfdpr::fail(LFDPR_EINVAL, "warp_views: views and eyes must be 4-byte aligned, keys 8-byte aligned");
     const cudaError_t e = lfdpr::launch_warp_views(in_views, in_keys, in_eyes, in_count, out_eyes, out_count, view_w,
                                                    view_h, pixels_per_unit, out_views, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return lfdpr::cuda_fail(e, "launch k_warp_views");

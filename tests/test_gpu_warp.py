@@ -194,3 +194,22 @@ def test_warp_moves_a_plane_by_its_disparity():
         return np.mean(np.abs(a[:, :, margin:-margin, :3].astype(np.int16) -
                               vout[:, :, margin:-margin, :3].astype(np.int16)))
     assert err(got) < 0.3 * err(naive), (err(got), err(naive))
+
+
+def test_warp_arguments_are_checked():
+    import torch
+    views = torch.zeros((2, 4, 8, 4), dtype=torch.uint8, device="cuda")
+    keys = torch.zeros((2 * 4 * 8 + 1,), dtype=torch.int64, device="cuda")
+    eyes = torch.zeros(4, dtype=torch.float32, device="cuda")
+    out = torch.zeros((3, 4, 8, 4), dtype=torch.uint8, device="cuda")
+    ok = dict(in_views_ptr=views.data_ptr(), in_keys_ptr=keys.data_ptr(), in_eyes_ptr=eyes.data_ptr(), in_count=2,
+              out_eyes_ptr=eyes.data_ptr(), out_count=3, view_w=8, view_h=4, pixels_per_unit=50.0,
+              out_ptr=out.data_ptr())
+    lfdpr.lfdpr_warp_views(**ok)
+    torch.cuda.synchronize()
+    for bad in (dict(in_count=1), dict(out_count=0), dict(view_w=4033), dict(pixels_per_unit=0.0),
+                dict(pixels_per_unit=float("nan")), dict(in_keys_ptr=keys.data_ptr() + 4),
+                dict(out_ptr=out.data_ptr() + 2), dict(in_views_ptr=0)):
+        with pytest.raises(lfdpr.LfdprError) as e:
+            lfdpr.lfdpr_warp_views(**{**ok, **bad})
+        assert e.value.status == lfdpr.EINVAL, bad
