@@ -467,6 +467,9 @@ def run_ours(args):
     step_ms, stage = [], {n: [] for n in lfdpr.STAGES}
     n_points = []
     n_writes = []
+    # the timed frames carry no per-stage events (about 20 us a frame on the
+    # device); the stages are timed in as many instrumented frames right after
+    R.set_stage_timing(False)
     launches0 = R.stats(stream).kernel_launches
     if world > 1:
         dist.barrier()
@@ -483,13 +486,21 @@ def run_ours(args):
         e1.record(stream)
         st = R.stats(stream)
         step_ms.append(e0.elapsed_time(e1))
-        for i, n in enumerate(lfdpr.STAGES):
-            stage[n].append(st.stage_ms[i])
         n_points.append(st.n_points)
         n_writes.append(getattr(st, "n_splat_writes", 0))
     torch.cuda.synchronize()
     launches = R.stats(stream).kernel_launches - launches0
     clk = clocks.stop()
+    R.set_stage_timing(True)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        R.render(frame_model(args.warmup + k), stream)
+        R.interleave(panel.data_ptr(), stream)
+        st = R.stats(stream)
+        for i, n in enumerate(lfdpr.STAGES):
+            stage[n].append(st.stage_ms[i])
+    R.set_stage_timing(False)
     total_ms = multigpu.max_over_ranks(sum(step_ms), device="cuda")
     if world > 1:
         dist.barrier()
@@ -516,6 +527,22 @@ def run_ours(args):
         e2e_s = multigpu.max_over_ranks(e2e_s, device="cuda")
         e2e = {"value": multigpu.job_rate(world, n_e2e, e2e_s), "unit": "frames/s", "h2d_bytes_per_step": 64,
                "d2h_bytes_per_step": 4 * d.panel_w * d.panel_h}
+        # what the host link allows: the panel's bytes copied device -> pinned host
+        # by the copy engine (the interleave's own stores into pinned memory cross
+        # the same link)
+        link = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                host_panel.copy_(panel, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            link.append(e0.elapsed_time(e1))
+        link_ms = statistics.median(link)
+        e2e["host_link"] = {"d2h_gbs": 4 * d.panel_w * d.panel_h / (link_ms / 1000.0) / 1e9,
+                            "panel_copy_ms": link_ms,
+                            "what": "the panel copied device -> pinned host by the copy engine, median of 10"}
 
     if rank != 0:
         R.close()
@@ -562,6 +589,9 @@ def run_ours(args):
             "points_per_s": value * P,
             "point_view_splats_per_s": P * d.n_render_views / (splat_ms / 1000.0),
             "stage_ms": st_mean,
+            "stage_ms_note": "CUDA events between the stages of %d instrumented frames run right after the timed "
+                             "ones (the same frames, L2 flushed); the events add about 20 us a frame, so the "
+                             "timed frames carry none" % args.steps,
             "roofline": roofline,
             "roofline_other": roofline_other,
             "splat_writes_per_frame": writes,
@@ -868,24 +898,27 @@ def secondary_measurements(args, sc, stream):
     d = S.display_angular_ss()
     R = lfdpr.Renderer(d, sc, stream=stream)
     try:
-        R.set_stage_timing(True)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
         panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
         for k in range(3):
             R.render(S.model_matrix(k), stream)
             R.interleave(panel.data_ptr(), stream)
         ms, splat = [], []
-        for k in range(10):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 255)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            R.render(S.model_matrix(3 + k), stream)
-            R.interleave(panel.data_ptr(), stream)
-            e1.record(stream)
-            st = R.stats(stream)
-            ms.append(e0.elapsed_time(e1))
-            splat.append(st.stage_ms[lfdpr.STAGES.index("splat")])
+        for timing in (False, True):   # whole frames uninstrumented, then the splat's stage time
+            R.set_stage_timing(timing)
+            for k in range(10):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                R.render(S.model_matrix(3 + k), stream)
+                R.interleave(panel.data_ptr(), stream)
+                e1.record(stream)
+                st = R.stats(stream)
+                if timing:
+                    splat.append(st.stage_ms[lfdpr.STAGES.index("splat")])
+                else:
+                    ms.append(e0.elapsed_time(e1))
         out["angular_96_views"] = {"what": "the same scene rendered at 2x angular rate (96 views of 420x560), "
                                            "tent to 48, crosstalk 0.15, interleaved; 10 frames, L2 flushed",
                                    "frames_per_s": 1000.0 / statistics.mean(ms),

@@ -131,6 +131,8 @@ constexpr int kTileCols = 4 * kTileThreads;   // panel columns per tile
 // for every rendered view, then the panel rows whose source row is sy.
 __global__ void __launch_bounds__(kTileThreads) k_interleave_tile(DispConst c, const uint8_t* __restrict__ views,
                                                                   uint8_t* __restrict__ panel, int stride) {
+    wait_previous_kernel();
+    allow_next_kernel();
     extern __shared__ uint32_t s_row[];
     const int sy = blockIdx.y;
     const int x0 = blockIdx.x * kTileCols;
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(kTileThreads) k_interleave_tile(DispConst c, c
 
 __global__ void __launch_bounds__(256) k_interleave(DispConst c, const uint8_t* __restrict__ views,
                                                      uint8_t* __restrict__ panel) {
+    wait_previous_kernel();
+    allow_next_kernel();
     const uint64_t npix = (uint64_t)c.W * c.H;
     const int groups_x = (c.Wp + 3) >> 2;
     const uint64_t total = (uint64_t)groups_x * c.Hp;
@@ -266,6 +270,8 @@ __global__ void __launch_bounds__(256) k_interleave_gauss(DispConst c, const uin
                                                           const float* __restrict__ pos,
                                                           const float* __restrict__ samples, int ns,
                                                           uint8_t* __restrict__ panel) {
+    wait_previous_kernel();
+    allow_next_kernel();
     __shared__ float s_pos[kMaxRenderViews];
     __shared__ float s_smp[3 * 32];
     for (int i = threadIdx.x; i < c.nr; i += blockDim.x) s_pos[i] = pos[i];
@@ -305,6 +311,8 @@ __device__ __forceinline__ uint32_t box4(uint32_t a, uint32_t b, uint32_t c, uin
 template <int L>
 __global__ void __launch_bounds__(256) k_view_mip(const uint8_t* __restrict__ src, uint32_t W, uint32_t H,
                                                   uint32_t nr, uint8_t* __restrict__ dst) {
+    wait_previous_kernel();
+    allow_next_kernel();
     constexpr int K = 1 << L;
     const uint32_t wl = W >> L, hl = H >> L;
     const uint64_t total = (uint64_t)wl * hl * nr;
@@ -355,12 +363,12 @@ cudaError_t launch_view_mip(const uint8_t* views, int W, int H, int nr, int leve
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (level == 1)
-        k_view_mip<1><<<sms * 8, 256, 0, s>>>(views, uint32_t(W), uint32_t(H), uint32_t(nr), out);
-    else if (level == 2)
-        k_view_mip<2><<<sms * 8, 256, 0, s>>>(views, uint32_t(W), uint32_t(H), uint32_t(nr), out);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_after_previous(k_view_mip<1>, dim3(sms * 8), dim3(256), 0, s, views, uint32_t(W), uint32_t(H),
+                                     uint32_t(nr), out);
+    if (level == 2)
+        return launch_after_previous(k_view_mip<2>, dim3(sms * 8), dim3(256), 0, s, views, uint32_t(W), uint32_t(H),
+                                     uint32_t(nr), out);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const float* pos, const float* samples,
@@ -371,8 +379,8 @@ cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const f
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (dc.recon == 2 || dc.recon == 3) {
         if (n_samples < 1 || n_samples > 32) return cudaErrorInvalidValue;
-        k_interleave_gauss<<<sms * 16, 256, 0, s>>>(dc, views, pos, samples, n_samples, panel);
-        return cudaGetLastError();
+        return launch_after_previous(k_interleave_gauss, dim3(sms * 16), dim3(256), 0, s, dc, views, pos, samples,
+                                     n_samples, panel);
     }
     // widest source segment of a tile: (kTileCols - 1) W / Wp + 2 pixels
     const int64_t seg = ((int64_t)(kTileCols - 1) * dc.W) / dc.Wp + 2;
@@ -382,11 +390,10 @@ cudaError_t launch_interleave(const DispConst& dc, const uint8_t* views, const f
                                              int(bytes));
         if (e != cudaSuccess) return e;
         const dim3 grid((dc.Wp + kTileCols - 1) / kTileCols, dc.H);
-        k_interleave_tile<<<grid, kTileThreads, size_t(bytes), s>>>(dc, views, panel, int(seg));
-    } else {
-        k_interleave<<<sms * 8, 256, 0, s>>>(dc, views, panel);
+        return launch_after_previous(k_interleave_tile, grid, dim3(kTileThreads), size_t(bytes), s, dc, views, panel,
+                                     int(seg));
     }
-    return cudaGetLastError();
+    return launch_after_previous(k_interleave, dim3(sms * 8), dim3(256), 0, s, dc, views, panel);
 }
 
 }  // namespace lfdpr

@@ -309,6 +309,32 @@ struct FrameArgs {
 // unit's candidate numbers stay below 2^32.
 constexpr uint32_t kSplatLaneLimit = 1u << 24;
 
+// Programmatic dependent launch. A kernel launched by launch_after_previous
+// may be placed on the SMs while the kernel before it on the stream is still
+// running, so its launch overlaps that kernel's last blocks. Each such kernel
+// calls wait_previous_kernel() before it reads or writes anything: the wait
+// returns once the previous kernel has finished and its writes are visible
+// (at once after any other stream operation, or for a plain launch), so the
+// stream's order holds as for a plain launch. allow_next_kernel() lets the
+// kernel after it be placed early in turn.
+__device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... P, typename... A>
+cudaError_t launch_after_previous(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s);
 // The depth-guided warp of nin rendered views (RGBA8 and depth keys) to nout
 // eyes on the same eye line (warp.cu); views at most kMaxWarpWidth wide.

@@ -72,16 +72,6 @@ constexpr long long kWaitCycles = 2000000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
-// Programmatic dependent launch: a layer's kernel is launched while the one
-// before it is still running; its blocks do their set-up (barriers, tensor
-// memory, biases), then wait here until the previous kernel has finished
-// and its writes are visible, before touching its output. Without a
-// preceding kernel (or launched plainly) the wait returns at once.
-__device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-// Let the next kernel in the stream be launched now (its blocks still wait
-// for this kernel to finish before they read what it writes).
-__device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t par) {
     uint32_t ok;
     asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -298,8 +288,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     tc::fence_after();
     uint32_t tmem;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(slot));
-    tc::wait_previous_kernel();
-    tc::allow_next_kernel();
+    wait_previous_kernel();
+    allow_next_kernel();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -541,8 +531,8 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
 // out (level H/2 x W/2) = mean of 2x2 blocks of in (level H x W); C % 8 == 0.
 // One thread per (chunk, output pixel), pixels fastest.
 __global__ void k_avgpool2(const __nv_bfloat16* __restrict__ in, int H, int W, int C, __nv_bfloat16* __restrict__ out) {
-    tc::wait_previous_kernel();
-    tc::allow_next_kernel();
+    wait_previous_kernel();
+    allow_next_kernel();
     const int Ho = H / 2, Wo = W / 2;
     const size_t npx = size_t(Ho) * Wo, total = npx * (C / 8), qi = qpad(H, W), qo = qpad(Ho, Wo);
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
@@ -569,7 +559,7 @@ __global__ void k_avgpool2(const __nv_bfloat16* __restrict__ in, int H, int W, i
 // One thread per pixel: its nin RGBA8 words, six 16-byte chunk stores.
 __global__ void k_recon_in(const uint8_t* __restrict__ views, int nin, int H, int W, int Hp, int Wp,
                            __nv_bfloat16* __restrict__ x0) {
-    tc::allow_next_kernel();   // launched plainly: it waits for everything before it
+    allow_next_kernel();   // launched plainly: it waits for everything before it
     const size_t total = size_t(Hp) * Wp, npix = size_t(H) * W, qp = qpad(Hp, Wp);
     for (size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x; p < total; p += size_t(gridDim.x) * blockDim.x) {
         const int x = int(p % Wp), y = int(p / Wp);
@@ -715,25 +705,9 @@ bool tc_valid(const TcGeom& g) {
            g.bias_n >= 1 && g.bias_n <= 256 && (g.taps == 1 || (g.NT / 2) % 16 == 0) && tc_smem(g) <= kTcSmemMax;
 }
 
-// A kernel launched with programmatic stream serialization: it may start
-// before the previous kernel on the stream has finished, and waits for it in
-// the kernel (tc::wait_previous_kernel).
-template <typename... P, typename... A>
-cudaError_t launch_after_previous(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t s,
-                                  A&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(unsigned(block));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
+// Each layer is launched as a programmatic dependent of the kernel before it
+// (launch_after_previous): its blocks set up their barriers, tensor memory
+// and biases, then wait for that kernel in wait_previous_kernel().
 cudaError_t launch_tc(int epi, const TcGeom& g, const CUtensorMap& ma, const CUtensorMap& mb, const void* wpk,
                       const float* bias, void* out, int* status, cudaStream_t s) {
     if (!tc_valid(g)) return cudaErrorInvalidValue;

@@ -423,6 +423,8 @@ __device__ __forceinline__ T block_sum(T v, T* smem) {
 }
 
 __global__ void __launch_bounds__(kSetupThreads, 4) k_setup(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     __shared__ uint32_t s_cnt[kSetupThreads / 32];
     __shared__ uint32_t s_live[kSetupThreads / 32];
     __shared__ float s_ex[kMaxRenderViews];
@@ -456,6 +458,8 @@ __global__ void __launch_bounds__(kSetupThreads, 4) k_setup(FrameArgs a) {
 // scans those 1024 sums, and each thread writes its run's prefixes; the
 // total decides overflow. Prefixes saturate at 2^32 - 1.
 __global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     __shared__ unsigned long long s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n = a.n_blocks, per = (n + 1023u) / 1024u;
@@ -523,6 +527,8 @@ __device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint
 // in shared memory and emitted afterwards by the block's warps, a warp each,
 // so that one thread does not walk tens of thousands of points.
 __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     __shared__ uint32_t s_warp[kSetupThreads / 32];
     __shared__ uint32_t s_big[kSetupThreads], s_first[kSetupThreads];
     __shared__ uint32_t s_nbig;
@@ -862,6 +868,8 @@ __device__ __forceinline__ NearRec near_record(const DispConst& c, const float4&
 // the point joins the splat's work list if some view can hold a candidate
 // pixel of it.
 __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     const DispConst& c = a.dc;
     const uint32_t n = a.ctr->overflow ? 0u : a.ctr->n_points;
     const float H1 = float(c.H - 1);
@@ -1025,6 +1033,8 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
 // appended to the work list if some view can hold a candidate pixel, and
 // Eq. 8's coefficients of the clipped cell in its resolve record.
 __global__ void __launch_bounds__(256) k_near_work(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     if (a.ctr->overflow) return;
     const DispConst& c = a.dc;
     const uint32_t n = a.ctr->n_near;
@@ -1077,6 +1087,8 @@ __global__ void __launch_bounds__(256) k_near_work(FrameArgs a) {
 // rmat, the roughness and metallic R channels to the resolve record's b.w as
 // bytes (min, max, min, max).
 __global__ void __launch_bounds__(256) k_fetch_mat(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     if (a.ctr->overflow) return;
     const uint32_t n = a.ctr->n_points;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -1115,28 +1127,23 @@ cudaError_t launch_setup(const FrameArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_scan(const FrameArgs& a, cudaStream_t s) {
-    k_scan<<<1, 1024, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_scan, dim3(1), dim3(1024), 0, s, a);
 }
 
 cudaError_t launch_emit(const FrameArgs& a, cudaStream_t s) {
-    k_emit<<<a.n_blocks, kSetupThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_emit, dim3(a.n_blocks), dim3(kSetupThreads), 0, s, a);
 }
 
 cudaError_t launch_fetch_mat(const FrameArgs& a, cudaStream_t s) {
-    k_fetch_mat<<<a.sm_count * 8, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_fetch_mat, dim3(a.sm_count * 8), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_fetch(const FrameArgs& a, cudaStream_t s) {
-    k_fetch<<<a.sm_count * 8, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_fetch, dim3(a.sm_count * 8), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_near_work(const FrameArgs& a, cudaStream_t s) {
-    k_near_work<<<a.sm_count, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_near_work, dim3(a.sm_count), dim3(256), 0, s, a);
 }
 
 }  // namespace lfdpr

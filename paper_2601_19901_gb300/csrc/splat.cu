@@ -341,6 +341,8 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
 
 template <int S>
 __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     extern __shared__ __align__(16) uint8_t s_dyn[];
     __shared__ float s_ex[kMaxRenderViews];
     for (int v = threadIdx.x; v < a.dc.nr; v += blockDim.x) s_ex[v] = a.ex[v];
@@ -410,6 +412,8 @@ __device__ __forceinline__ uint32_t resolve_pixel(float Ex, const float4& ra, co
 // keeps that many dependent gathers in flight.
 constexpr int kResolvePix = 2;
 __global__ void __launch_bounds__(256) k_resolve(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     const DispConst& c = a.dc;
     const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
     const uint32_t p0 = blockIdx.x * (256u * kResolvePix) + threadIdx.x;
@@ -501,6 +505,8 @@ __device__ __forceinline__ float3 pbr_shade(const float3& albedo, float rough, f
 // the triangle faces away from the eye; RGB = pbr_shade clamped, times 255,
 // rounded half to even, alpha 255.
 __global__ void __launch_bounds__(256) k_resolve_pbr(FrameArgs a) {
+    wait_previous_kernel();
+    allow_next_kernel();
     const DispConst& c = a.dc;
     const uint32_t npix = uint32_t(c.W) * uint32_t(c.H);
     const uint32_t px = blockIdx.x * blockDim.x + threadIdx.x;
@@ -579,8 +585,7 @@ cudaError_t splat_one(const FrameArgs& a, int grid, cudaStream_t s) {
     static const cudaError_t attr =
         cudaFuncSetAttribute(k_splat<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (attr != cudaSuccess) return attr;
-    k_splat<S><<<grid, kSplatWarps * 32, bytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_after_previous(k_splat<S>, dim3(grid), dim3(kSplatWarps * 32), bytes, s, a);
 }
 
 template <int S>
@@ -629,11 +634,9 @@ cudaError_t launch_resolve(const FrameArgs& a, cudaStream_t s) {
     const uint32_t npix = uint32_t(a.dc.W) * uint32_t(a.dc.H);
     const uint32_t nv = uint32_t(a.view_hi - a.view_lo);
     const dim3 grid((npix + 255u) / 256u, nv);
-    if (a.pbr)
-        k_resolve_pbr<<<grid, 256, 0, s>>>(a);
-    else
-        k_resolve<<<dim3((npix + 256u * kResolvePix - 1u) / (256u * kResolvePix), nv), 256, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.pbr) return launch_after_previous(k_resolve_pbr, grid, dim3(256), 0, s, a);
+    return launch_after_previous(k_resolve, dim3((npix + 256u * kResolvePix - 1u) / (256u * kResolvePix), nv),
+                                 dim3(256), 0, s, a);
 }
 
 }  // namespace lfdpr
