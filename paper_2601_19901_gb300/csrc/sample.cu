@@ -707,22 +707,27 @@ __device__ __forceinline__ void band_bounds(const float* A, const float* B, cons
     };
 #pragma unroll
     for (int k = 0; k < N; k++) fold(Y[k] >= ya && Y[k] <= yb, xm[k], xp[k]);
+    // an edge's reciprocal height is used only where a row crosses it (so
+    // its height is not zero)
+    float rdy[N];
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const float yc = r ? yb : ya;
-        const bool row = r == 0 || yb > ya;
+    for (int e = 0; e < N; e++) rdy[e] = __fdividef(1.0f, Y[e + 1 == N ? 0 : e + 1] - Y[e]);
+    auto row_crossings = [&](float yc) {
 #pragma unroll
         for (int e = 0; e < N; e++) {
             const int p = e, q = e + 1 == N ? 0 : e + 1;
-            const bool cross = row && ((Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]));
+            const bool cross = (Y[p] <= yc && yc < Y[q]) || (Y[q] <= yc && yc < Y[p]);
             const float dxm = xm[q] - xm[p], dxp = xp[q] - xp[p];
-            const float rdy = __fdividef(1.0f, cross ? Y[q] - Y[p] : 1.0f);
-            const float f = (yc - Y[p]) * rdy, d = cross_dy * fabsf(rdy);
+            const float f = (yc - Y[p]) * rdy[e], d = cross_dy * fabsf(rdy[e]);
             const float f0 = fmaxf(f - d, 0.0f), f1 = fminf(f + d, 1.0f);
             fold(cross, fmaf(f0, dxm, xm[p]), fmaf(f0, dxp, xp[p]));
             fold(cross, fmaf(f1, dxm, xm[p]), fmaf(f1, dxp, xp[p]));
         }
-    }
+    };
+    row_crossings(ya);
+    // a band of one row (most cells are at most a pixel high) has no second
+    // boundary row
+    if (yb > ya) row_crossings(yb);
     if (!(lm <= um)) {
 #pragma unroll
         for (int k = 0; k < N; k++) fold(true, xm[k], xp[k]);
