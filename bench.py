@@ -747,7 +747,7 @@ def learned_measure(sc, steps, warmup, quality_frames, stream=None):
     tensor-core kernels predict the 48 reconstructed views, interleave) and
     the plain renders it stands in for, on scene `sc`: frames/s of each with
     L2 flushed between frames, the network alone, and per-frame PSNR / SSIM
-    of the prediction against both readings of its judge (the full render's
+    of the prediction against both readings of its ground truth (the full render's
     96-view tent reconstruction, and the plain 48-view render)."""
     import torch
     from dataclasses import replace
@@ -846,13 +846,13 @@ def learned_measure(sc, steps, warmup, quality_frames, stream=None):
             "frames_per_s": 1000.0 / ms_learned, "ms_per_frame": ms_learned,
             "full_render_frames_per_s": 1000.0 / ms_full, "plain_48_view_frames_per_s": 1000.0 / ms_plain,
             "network_ms": net_ms, "network_flops": flops, "network_tflops": flops / (net_ms / 1000.0) / 1e12,
-            "vs_full_render": {"what": "judge = the 96-view render's tent reconstruction (the display's "
+            "vs_full_render": {"what": "ground truth = the 96-view render's tent reconstruction (the display's "
                                        "angularly supersampled views)",
                                "psnr_db_mean": statistics.mean(x[0] for x in q),
                                "psnr_db_min": min(x[0] for x in q),
                                "ssim_mean": statistics.mean(x[1] for x in q),
                                "speedup": ms_full / ms_learned},
-            "vs_plain_48_views": {"what": "judge = the plain 48-view render",
+            "vs_plain_48_views": {"what": "ground truth = the plain 48-view render",
                                   "psnr_db_mean": statistics.mean(x[3] for x in q),
                                   "psnr_db_min": min(x[3] for x in q),
                                   "ssim_mean": statistics.mean(x[4] for x in q),
@@ -890,7 +890,7 @@ def run_learned(args):
 def secondary_measurements(args, sc, stream):
     """Frames/s of the 96-view (2x angular, tent, crosstalk) frame on the same
     scene, and the learned quarter-view path with its quality against both
-    readings of its judge: measured after the main timed region, reported
+    readings of its ground truth: measured after the main timed region, reported
     beside it (not part of `value`)."""
     import torch
     from paper_2601_19901_gb300 import lfdpr, scenes as S

@@ -1,6 +1,6 @@
 """Helpers of the GPU parity tests: run one frame through the C ABI, read the
 library's buffers back, and compare them with the CPU oracle under the
-spec tolerances:
+parity tolerances:
   - per-triangle counts, sampling records and the point set: bit-exact;
   - splat: >= 99.9 % of view pixels carry the same winning point id;
   - colour: max |diff| <= 1 (of 255) on pixels with the same winner, and

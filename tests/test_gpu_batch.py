@@ -3,7 +3,7 @@
 A batch renders several scenes, each on its own display (different view
 counts, view sizes, panels, angular supersampling), from one texture set, as
 one replayed CUDA graph with a persistent splat over all scenes. Every scene
-must match the CPU oracle under the benchmark spec's tolerances (point sets
+must match the CPU oracle under the parity tolerances (point sets
 bit-exact, >= 99.9 % same winning ids, colour within 1/255, PSNR >= 50 dB,
 the interleave bit-exact on the same views); and its keys, views and panel
 must be bit-identical to rendering that scene alone with lfdpr_render_frame +

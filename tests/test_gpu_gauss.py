@@ -3,7 +3,7 @@ GPU against the oracle.
 
 The eyes move with the caller's jitter, so the whole frame (sampling, splat,
 resolve) must still match the oracle run with the same jitter under the
-spec tolerances; the Gaussian interleave, given the same views, must
+parity tolerances; the Gaussian interleave, given the same views, must
 match the oracle bit for bit, with and without crosstalk, over 2N and N
 views; jitter 1/2 everywhere must give the default frame exactly.
 """

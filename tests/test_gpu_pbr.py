@@ -4,7 +4,7 @@ and shading during view generation).
 
 Sampling (counts, records, point set, albedo tv) and every texture's fetched
 tv_min / tv_max are bit-exact; the shaded views (FP32 on the GPU, double in
-the oracle) meet the benchmark spec's tolerances: >= 99.9 % same winners, colour
+the oracle) meet the parity tolerances: >= 99.9 % same winners, colour
 within 1 of 255 on same-winner pixels, PSNR >= 50 dB.
 """
 from dataclasses import replace

@@ -7,7 +7,7 @@ supersampling) and a scene (up to 400 triangles of sizes over two decades,
 some degenerate, some reaching the eyes' plane, one to three textures of
 power-of-two sizes from 1 to 64 texels a side, wrapped UVs), under a random
 rigid model transform. Sampling must be bit-exact, views within the
-spec tolerances, and the panel bit-exact against the oracle's
+parity tolerances, and the panel bit-exact against the oracle's
 interleave of the GPU's views.
 """
 import math
