@@ -235,6 +235,30 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
         const int vlo = src.view_lo(sc), vhi = src.view_hi(sc);
         for (int g0 = vlo; g0 < vhi; g0 += 16 * S) {
             __syncwarp();   // the previous passes are done with sm
+            if (g0 == vlo) {
+                // the unit's test constants, one float4 a lane: lane 6 q + f
+                // stages float4 f of point k0 + q (a point past the end takes
+                // the unit's first record; it has no rows)
+                const int q = lane / 6, f = lane - 6 * q;
+                if (q < 2 * P) {
+                    const uint32_t k = k0 + uint32_t(q);
+                    const uint4 meta = __ldg(&work[k < n ? k : k0].meta);
+                    const TriRec* r = src.rec(sc) + meta.z;
+                    float4 v = __ldg(&r->q[f < 5 ? f : 0]);
+                    if (f == 0) {
+                        v.y = 0.0f - v.y;
+                        v.z = c.D - v.z;
+                        v.w = __uint_as_float(meta.w);
+                    } else if (f == 1) {
+                        v.w = __uint_as_float(meta.x);
+                    } else if (f == 5) {
+                        const float sv = __ldg(&r->q[1].w);
+                        const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
+                        v = make_float4(float(i) * v.w, float(i + 1) * v.w, float(j) * sv, float(j + 1) * sv);
+                    }
+                    sm.pt[q][f] = v;
+                }
+            }
             uint32_t pk[P][S], ny[P];
             float ex[S];   // the lane's views' eyes, the same for every pair
             uint32_t cnt = 0;
@@ -246,19 +270,6 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                 const float4 l0 = __ldg(&wr->L0), l1 = __ldg(&wr->L1);
                 const uint4 meta = __ldg(&wr->meta);
                 ny[p] = k < n ? (meta.x >> 14) & 0x7fffu : 0u;
-                if (g0 == vlo && sub == 0) {   // the point's test constants
-                    const TriRec* r = src.rec(sc) + meta.z;
-                    const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
-                    const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]);
-                    const int i = int(meta.y & 0xffffu), j = int(meta.y >> 16);
-                    float4* d = sm.pt[2 * p + half];
-                    d[0] = make_float4(q0.x, 0.0f - q0.y, c.D - q0.z, __uint_as_float(meta.w));
-                    d[1] = make_float4(q1.x, q1.y, q1.z, __uint_as_float(meta.x));
-                    d[2] = q2;
-                    d[3] = q3;
-                    d[4] = q4;
-                    d[5] = make_float4(float(i) * q0.w, float(i + 1) * q0.w, float(j) * q1.w, float(j + 1) * q1.w);
-                }
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) {
                     const int v = g0 + 16 * sl + sub;
