@@ -173,6 +173,15 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, const float* ex, uint32_t
         Q[k][0] = a.uv[2 * (size_t)vi];
         Q[k][1] = a.uv[2 * (size_t)vi + 1];
     }
+    // the texture's size (of a mesh of materials, the albedo's): loaded
+    // before the cull so that its dependent loads overlap the frame arithmetic
+    uint32_t tex = a.tri_tex[t];
+    if (a.mat_tex) {
+        if (!LFDPR_IN_BOUNDS(tex, a.n_mat, 3)) tex = 0;
+        tex = a.mat_tex[tex].x;
+    }
+    if (!LFDPR_IN_BOUNDS(tex, a.n_tex, 2)) tex = 0;
+    const uint32_t tex_w = a.tex[tex].w, tex_h = a.tex[tex].h;
 #pragma unroll
     for (int k = 0; k < 8; k++) r.q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     r.q[0] = make_float4(P[0][0], P[0][1], P[0][2], 0.0f);
@@ -318,24 +327,18 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, const float* ex, uint32_t
     const float size_xy = su0 * sv0;
     // a mesh of materials: the albedo sets the record's LOD pair, Eq. 1 takes
     // the largest texel count of the material's four textures
-    uint32_t tex = a.tri_tex[t];
-    uint4 mt = make_uint4(0u, 0u, 0u, 0u);
-    if (a.mat_tex) {
-        if (!LFDPR_IN_BOUNDS(tex, a.n_mat, 3)) tex = 0;
-        mt = a.mat_tex[tex];
-        tex = mt.x;
-        if (!LFDPR_IN_BOUNDS(mt.y, a.n_tex, 2) || !LFDPR_IN_BOUNDS(mt.z, a.n_tex, 2) ||
-            !LFDPR_IN_BOUNDS(mt.w, a.n_tex, 2))
-            mt.y = mt.z = mt.w = 0;
-    }
-    if (!LFDPR_IN_BOUNDS(tex, a.n_tex, 2)) tex = 0;
-    const TexDesc td = a.tex[tex];
-    const float X = float(td.w), Y = float(td.h);
+    const float X = float(tex_w), Y = float(tex_h);
     const float ds1 = Q[1][0] - Q[0][0], dt1 = Q[1][1] - Q[0][1];
     const float ds2 = Q[2][0] - Q[0][0], dt2 = Q[2][1] - Q[0][1];
     const float A_ts = 0.5f * fabsf(fmaf(ds1, dt2, -(dt1 * ds2)));
     float n_tex = (A_ts * X) * Y;
     if (a.mat_tex) {
+        uint32_t m = a.tri_tex[t];
+        if (!LFDPR_IN_BOUNDS(m, a.n_mat, 3)) m = 0;
+        uint4 mt = a.mat_tex[m];
+        if (!LFDPR_IN_BOUNDS(mt.y, a.n_tex, 2) || !LFDPR_IN_BOUNDS(mt.z, a.n_tex, 2) ||
+            !LFDPR_IN_BOUNDS(mt.w, a.n_tex, 2))
+            mt.y = mt.z = mt.w = 0;
         const uint32_t ids[3] = {mt.y, mt.z, mt.w};
 #pragma unroll
         for (int k = 0; k < 3; k++) {
