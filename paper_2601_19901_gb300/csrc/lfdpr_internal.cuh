@@ -117,6 +117,12 @@ struct Shading {
     float l[3], rgb[3], amb[3];
 };
 
+// A live triangle's column summary: for a triangle of at most four lattice
+// columns, word i holds column i's first row j0 | its row count << 16 (zero
+// for the columns past the last); a wider one holds kColSumWalk in word 0
+// (no column has j0 = rows = 65535, since j0 + rows <= kMaxCell + 1), and
+// its points are found by walking the columns again.
+constexpr uint32_t kColSumWalk = 0xffffffffu;
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]
 
@@ -288,6 +294,7 @@ struct FrameArgs {
     TriRec* rec;
     uint32_t* counts;
     uint32_t* offsets;
+    uint4* colsum;                   // [n_tris] column summaries (k_setup -> k_emit); null: k_emit walks
     uint32_t* block_sums;            // [n_blocks]
     uint32_t n_blocks;
     uint4* points;

@@ -69,6 +69,7 @@ struct lfdpr_mesh {
     lfdpr::TriProj* tproj = nullptr;
     uint32_t* counts = nullptr;
     uint32_t* offsets = nullptr;
+    uint4* colsum = nullptr;
     uint32_t* block_sums = nullptr;
 };
 

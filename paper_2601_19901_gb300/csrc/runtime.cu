@@ -124,6 +124,7 @@ FrameArgs frame_args(const lfdpr_display* disp, const lfdpr_mesh* mesh) {
     a.rec = mesh->rec;
     a.counts = mesh->counts;
     a.offsets = mesh->offsets;
+    a.colsum = mesh->colsum;
     a.block_sums = mesh->block_sums;
     a.n_blocks = mesh->n_blocks;
     a.points = disp->points;
@@ -268,6 +269,7 @@ void free_mesh(lfdpr_mesh* m) {
     dev_free(m->tproj);
     dev_free(m->counts);
     dev_free(m->offsets);
+    dev_free(m->colsum);
     dev_free(m->block_sums);
     delete m;
 }
@@ -394,6 +396,7 @@ lfdpr_status upload_geometry(lfdpr_display* disp, const float* xyz, const float*
         (e = dev_malloc(&m->rec, sizeof(TriRec) * nt)) != cudaSuccess ||
         (e = dev_malloc(&m->tproj, sizeof(TriProj) * nt)) != cudaSuccess ||
         (e = dev_malloc(&m->counts, 4u * nt)) != cudaSuccess || (e = dev_malloc(&m->offsets, 4u * nt)) != cudaSuccess ||
+        (e = dev_malloc(&m->colsum, sizeof(uint4) * nt)) != cudaSuccess ||
         (e = dev_malloc(&m->block_sums, 4u * (m->n_blocks ? m->n_blocks : 1))) != cudaSuccess) {
         free_mesh(m);
         return cuda_fail(e, "upload_mesh: allocation");

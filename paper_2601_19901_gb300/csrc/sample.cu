@@ -389,12 +389,23 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, const float* ex, uint32_t
     if (!(ncol <= float(kMaxCell))) { res.cell_overflow = true; return res; }
     const int cols = int(ncol);
     uint32_t cnt = 0;
+    // the column summary for k_emit, stored word by word as the columns are
+    // found (a wider triangle, or a column of 2^16 rows, is marked for a walk)
+    uint32_t* cs = a.colsum ? reinterpret_cast<uint32_t*>(a.colsum + t) : nullptr;
+    bool summary = cols <= 4;
     ColumnWalk walk(U, V, su, sv, umax);
     for (int i = 0; i < cols; i++) {
         int j0, j1;
         const int rows = walk.rows(i, &j0, &j1);
         if (j1 > kMaxCell + 1) { res.cell_overflow = true; return res; }
         cnt += uint32_t(rows);
+        summary &= rows <= 0xffff;
+        if (cs && summary) cs[i] = uint32_t(j0) | (uint32_t(rows) << 16);
+    }
+    if (cs) {
+        if (!summary) cs[0] = kColSumWalk;
+        else
+            for (int i = cols; i < 4; i++) cs[i] = 0u;
     }
     res.count = cnt;
     res.live = true;
@@ -503,6 +514,24 @@ __global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
 // The points of triangle t from point id p on, in (column, row) order: a
 // single thread (lanes = 1) or a warp's lanes side by side in each column.
 __device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint32_t p, int lane, int lanes) {
+    if (a.colsum) {
+        // the columns k_setup found, without walking them again
+        const uint4 cs = a.colsum[t];
+        if (cs.x != kColSumWalk) {
+            const uint32_t w[4] = {cs.x, cs.y, cs.z, cs.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t j0 = w[i] & 0xffffu, rows = w[i] >> 16;
+                for (uint32_t r = uint32_t(lane); r < rows; r += uint32_t(lanes)) {
+                    const uint32_t q = p + r;
+                    if (LFDPR_IN_BOUNDS(q, a.max_points, 4))
+                        *reinterpret_cast<uint2*>(a.points + q) = make_uint2(t, uint32_t(i) | ((j0 + r) << 16));
+                }
+                p += rows;
+            }
+            return;
+        }
+    }
     const TriRec* rp = a.rec + t;
     TriRec r;
     r.q[0] = rp->q[0]; r.q[1] = rp->q[1]; r.q[2] = rp->q[2]; r.q[3] = rp->q[3];
