@@ -118,10 +118,10 @@ struct Shading {
 };
 
 // A live triangle's column summary: for a triangle of at most four lattice
-// columns, word i holds column i's first row j0 | its row count << 16 (zero
-// for the columns past the last); a wider one holds kColSumWalk in word 0
-// (no column has j0 = rows = 65535, since j0 + rows <= kMaxCell + 1), and
-// its points are found by walking the columns again.
+// columns, word i holds column i's first row j0 | its row count << 16 (the
+// words past the last column are left unwritten); a wider one holds
+// kColSumWalk in word 0 (no column has j0 = rows = 65535, since j0 + rows <=
+// kMaxCell + 1), and its points are found by walking the columns again.
 constexpr uint32_t kColSumWalk = 0xffffffffu;
 constexpr uint32_t kFlagInterior = 1u;  // the cell lies inside its triangle
 constexpr uint32_t kFlagDepthOk = 2u;   // every hit on the triangle is within [near, far]

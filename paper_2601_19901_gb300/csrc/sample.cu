@@ -402,11 +402,7 @@ __device__ SetupOut setup_triangle(const FrameArgs& a, const float* ex, uint32_t
         summary &= rows <= 0xffff;
         if (cs && summary) cs[i] = uint32_t(j0) | (uint32_t(rows) << 16);
     }
-    if (cs) {
-        if (!summary) cs[0] = kColSumWalk;
-        else
-            for (int i = cols; i < 4; i++) cs[i] = 0u;
-    }
+    if (cs && !summary) cs[0] = kColSumWalk;
     res.count = cnt;
     res.live = true;
     // the splat's per-triangle projection constants
@@ -511,16 +507,21 @@ __global__ void __launch_bounds__(1024) k_scan(FrameArgs a) {
     }
 }
 
-// The points of triangle t from point id p on, in (column, row) order: a
+// The n points of triangle t from point id p on, in (column, row) order: a
 // single thread (lanes = 1) or a warp's lanes side by side in each column.
-__device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint32_t p, int lane, int lanes) {
+__device__ __forceinline__ void emit_points(const FrameArgs& a, uint32_t t, uint32_t p, uint32_t n, int lane,
+                                            int lanes) {
     if (a.colsum) {
-        // the columns k_setup found, without walking them again
+        // the columns k_setup found, without walking them again; the words
+        // past the last column are not written, and are not read: the
+        // columns before them hold all n points
         const uint4 cs = a.colsum[t];
         if (cs.x != kColSumWalk) {
             const uint32_t w[4] = {cs.x, cs.y, cs.z, cs.w};
+            const uint32_t end = p + n;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
+                if (p == end) break;
                 const uint32_t j0 = w[i] & 0xffffu, rows = w[i] >> 16;
                 for (uint32_t r = uint32_t(lane); r < rows; r += uint32_t(lanes)) {
                     const uint32_t q = p + r;
@@ -595,11 +596,12 @@ __global__ void __launch_bounds__(kSetupThreads) k_emit(FrameArgs a) {
             s_big[b] = t;
             s_first[b] = first;
         } else if (cnt > 0 && !overflow) {
-            emit_points(a, t, first, 0, 1);
+            emit_points(a, t, first, cnt, 0, 1);
         }
     }
     __syncthreads();
-    for (uint32_t b = uint32_t(warp); b < s_nbig; b += kSetupThreads / 32) emit_points(a, s_big[b], s_first[b], lane, 32);
+    for (uint32_t b = uint32_t(warp); b < s_nbig; b += kSetupThreads / 32)
+        emit_points(a, s_big[b], s_first[b], a.counts[s_big[b]], lane, 32);
 }
 
 // One mip level's bilinear sample at texture coordinates (fs, ft) in [0, 1):
