@@ -182,7 +182,8 @@ __device__ __forceinline__ void test_candidate(const DispConst& c, const SplatWa
     const float4 d0 = d[0], d1 = d[1], q2 = d[2], q3 = d[3], q4 = d[4], b = d[5];
     const uint32_t meta = __float_as_uint(d1.w), flags = meta >> 29;
     const uint32_t nx = e.y >> 14;
-    const uint32_t ry = div_floor(rr, nx);
+    // one row (most segments): no division
+    const uint32_t ry = rr < nx ? 0u : div_floor(rr, nx);
     const int x = int(e.y & 0x3fffu) + int(rr - ry * nx), y = int(meta & 0x3fffu) + int(ry);
     const uint32_t vo = e.z & 0xffffu;
     const float Ex = __uint_as_float(e.w);
