@@ -555,7 +555,9 @@ def run_ours(args):
     npix = d.n_render_views * d.view_w * d.view_h
     b = R.buffers()
     n_live = R.stats(stream).n_live_tris
-    splat_bytes = 8 * P + 80 * n_live + 16 * npix
+    # the splat's algorithmic bytes: each point's 16 B and its triangle's 80 B
+    # read once, each view pixel's 8-B key written once
+    splat_bytes = 16 * P + 80 * n_live + 8 * npix
     achieved = splat_bytes / (splat_ms / 1000.0) / 1e9
     traffic = profiled_traffic("k_splat_paper_frame.md", ["splat.cu", "lfdpr_internal.cuh"]) \
         if args.config == "paper" else None
