@@ -68,12 +68,25 @@ def parse():
     p.add_argument("--batch-scenes", type=int, default=32, help="--config batch: scenes per batch")
     p.add_argument("--batch-tris", type=str, default="50000,2000000",
                    help="--config batch: triangle-count range per scene (log-uniform)")
+    p.add_argument("--scene-instances", type=int, default=200,
+                   help="meshes of the paper-shaped scene (200: 10^6 triangles); fewer make the small "
+                        "case of the same kernels for ncu captures, never a bench line")
     return p.parse_args()
 
 
-def workload(cfg):
+def workload(cfg, instances=200):
     from dataclasses import replace
     from paper_2601_19901_gb300 import scenes as S
+    if instances != 200:
+        # the same display and scene recipe with fewer meshes (profiling only)
+        wl = WORKLOAD.replace("1,000,000 triangles (200 displaced meshes",
+                              "%d triangles (%d displaced meshes: a reduced case for profiling, not the workload"
+                              % (5000 * instances, instances))
+        if cfg == "angular":
+            return S.display_angular_ss(), S.scene_paper(n_instances=instances), wl
+        if cfg == "paper":
+            return S.display_paper(), S.scene_paper(n_instances=instances), wl
+        raise SystemExit("--scene-instances applies to --config paper and angular")
     if cfg == "tiny":
         return S.display_tiny(), S.scene_tiny(), "tiny: 2,048 triangles, 8 views 128x128, 512x512 panel"
     if cfg == "angular":
@@ -307,7 +320,7 @@ def run_reference(args):
     import oracle as O
     from paper_2601_19901_gb300 import scenes as S
     O.build()
-    d, sc, wl = workload(args.config)
+    d, sc, wl = workload(args.config, args.scene_instances)
     tx = O.Textures(sc.textures)
     info = cpu_info()
     frames = OracleFrames(args.config, d, sc, info["usable_cores"])
@@ -427,7 +440,7 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    d, sc, wl = workload(args.config)
+    d, sc, wl = workload(args.config, args.scene_instances)
     stream = torch.cuda.Stream()
     R = lfdpr.Renderer(d, sc, max_points=(1 << 24) if args.config == "gauss2x" else 0, stream=stream,
                        shading=shading_of(args.config))

@@ -262,7 +262,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
             }
             uint32_t pk[P][S], ny[P];
             float ex[S];   // the lane's views' eyes, the same for every pair
-            uint32_t cnt = 0;
+            uint32_t cnt = 0, nz = 0;   // the lane's candidates and non-empty (point, view) segments
 #pragma unroll
             for (int p = 0; p < P; p++) {
                 // a half past the end takes the unit's first record, with no rows
@@ -286,6 +286,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                             const uint32_t nx = uint32_t(ix1 - ix0) + 1u;
                             pk[p][sl] = uint32_t(ix0) | (nx << 14);
                             cnt += nx * ny[p];
+                            nz++;
                         }
                     }
                 }
@@ -293,23 +294,19 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
             // a segment holds at most 2^26 candidates (one view), so lanes
             // below the limit (at most 2^24) keep the unit's numbering below 2^32
             const bool big = __any_sync(0xffffffffu, cnt >= src.lane_limit());
-            // the unit's candidates numbered in (lane, pair, slot) order
-            uint32_t incl = cnt;
+            // the unit's candidates and segments numbered in (lane, pair, slot)
+            // order: one scan of both counts, the candidates in the high word
+            // (wrapping as 32-bit sums would, only when the unit is walked)
+            // and the segments (at most 32 S P) in the low one
+            unsigned long long incl = ((unsigned long long)cnt << 32) | nz;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            uint32_t first = incl - cnt, rank = 0, nseg = 0;
-#pragma unroll
-            for (int p = 0; p < P; p++)
-#pragma unroll
-                for (int sl = 0; sl < S; sl++) {
-                    const uint32_t bal = __ballot_sync(0xffffffffu, pk[p][sl] != 0u);
-                    rank += __popc(bal & lanes_below);
-                    nseg += __popc(bal);
-                }
+            const unsigned long long all = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t total = uint32_t(all >> 32), nseg = uint32_t(all);
+            uint32_t first = uint32_t(incl >> 32) - cnt, rank = uint32_t(incl) - nz;
 #pragma unroll
             for (int p = 0; p < P; p++)
 #pragma unroll
