@@ -573,7 +573,7 @@ def run_ours(args):
     splat_bytes = 16 * P + 80 * n_live + 8 * npix
     achieved = splat_bytes / (splat_ms / 1000.0) / 1e9
     traffic = profiled_traffic("k_splat_paper_frame.md", ["splat.cu", "lfdpr_internal.cuh"]) \
-        if args.config == "paper" else None
+        if args.config == "paper" and args.scene_instances == 200 else None
     roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "kernel": "k_splat",
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
