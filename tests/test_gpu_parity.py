@@ -293,3 +293,45 @@ def test_consecutive_frames_scan_and_emit_like_the_oracle():
             check_sampling(g, o, "frame %d" % k)
             if k == 3:
                 assert g.stats.n_points == 0 and g.stats.n_live_tris == 0
+
+
+def _column_cases_scene(h: float):
+    """A sliver of two lattice columns whose first holds exactly 2^16 rows
+    (the most a column may hold), two triangles of many columns, and small
+    ones of one to four columns, all facing the eyes at z = 0."""
+    rng = np.random.default_rng(21)
+    tris = [[[-0.003, -h / 2, 0.0], [0.003, -h / 2, 0.0], [0.0, h / 2, 0.0]],
+            [[-0.6, -0.5, 0.0], [-0.45, -0.52, 0.0], [-0.55, -0.47, 0.0]],
+            [[0.3, 0.3, 0.0], [0.5, 0.32, 0.0], [0.33, 0.36, 0.0]]]
+    for _ in range(60):
+        c = np.array([rng.uniform(-0.7, 0.7), rng.uniform(-0.9, 0.9), 0.0])
+        tris.append((c + np.concatenate([rng.normal(0.0, 0.006, (3, 2)), np.zeros((3, 1))], 1)).tolist())
+    tris = np.asarray(tris, np.float32)
+    n = len(tris)
+    uv = np.tile(np.asarray([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0]], np.float32), (n, 1))
+    tex = np.random.default_rng(22).integers(0, 256, (1024, 1024, 4), dtype=np.uint8)
+    return S.Scene(xyz=tris.reshape(-1, 3), uv=uv, idx=np.arange(3 * n, dtype=np.uint32).reshape(n, 3),
+                   tri_tex=np.zeros(n, np.uint32), textures=[tex])
+
+
+def test_column_summaries_and_column_walks_emit_the_oracle_point_set():
+    """k_emit writes a triangle of at most four lattice columns from the
+    column summary k_setup keeps, and walks the columns again for a wider
+    one or for a column of 2^16 rows (which the summary's 16-bit row count
+    cannot hold): counts, records and the point set bit-exact either way."""
+    d = S.display_paper()
+    m = np.eye(4, dtype=np.float32)
+    probe = O.render(d, _column_cases_scene(1.0), m, splat=False, panel=False)
+    sv = float(probe.tri[0, O.F["s_v"]])
+    sc = _column_cases_scene(65535.5 * sv)
+    o = O.render(d, sc, m, splat=False, panel=False)
+    assert o.status == 0
+    tri_of = o.points[:, 0].astype(np.int64)
+    col = (o.points[:, 1] & 0xffff).astype(np.int64)
+    ncols = np.array([len(np.unique(col[tri_of == t])) for t in range(sc.n_tris)])
+    assert ((tri_of == 0) & (col == 0)).sum() == 65536 and ncols[0] == 2
+    assert ncols[1] > 4 and ncols[2] > 4
+    assert ((ncols >= 1) & (ncols <= 4)).sum() >= 20
+    g = gpu_frame(d, sc, m, panel=False)
+    assert g.stats.overflow == 0 and g.stats.n_points == len(o.points)
+    check_sampling(g, o, "column cases")
