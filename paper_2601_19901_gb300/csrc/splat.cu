@@ -396,13 +396,17 @@ __global__ void __launch_bounds__(kSplatWarps * 32, 4) k_splat_batch(const Splat
 // Eq. 8's interpolation weight for one view pixel whose depth test kept the
 // point with resolve record (ra, rb): the splat's pixel area in view Ex is
 // the shoelace area of its cell corners projected from the eye,
-// |alpha + beta Ex| / 2.
+// |alpha + beta Ex| / 2. The colour it weights is held to the oracle within
+// one level of 255, so both quotients take the hardware's approximate
+// division (relative error near 1e-7: a colour moves by far less than a
+// level, and changes level only where it lies within that of a rounding
+// boundary); the divisors are at most 1 and a ratio of texture areas.
 __device__ __forceinline__ float eq8_weight(float Ex, const float4& ra, const uint4& rb) {
     const float area_px = 0.5f * fabsf(fmaf(ra.y, Ex, ra.x));
     const float vmin = ra.w, vmax = __uint_as_float(rb.x);
-    const float size_vse = __fdiv_rn(ra.z, fminf(1.0f, area_px));
+    const float size_vse = __fdividef(ra.z, fminf(1.0f, area_px));
     const float size_vs = fminf(fmaxf(size_vse, vmin), vmax);
-    return vmax > vmin ? __fdiv_rn(size_vs - vmin, vmax - vmin) : 0.0f;
+    return vmax > vmin ? __fdividef(size_vs - vmin, vmax - vmin) : 0.0f;
 }
 
 __device__ __forceinline__ uint32_t resolve_pixel(float Ex, const float4& ra, const uint4& rb) {
