@@ -271,24 +271,22 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                 const float4 l0 = __ldg(&wr->L0), l1 = __ldg(&wr->L1);
                 const uint4 meta = __ldg(&wr->meta);
                 ny[p] = k < n ? (meta.x >> 14) & 0x7fffu : 0u;
+                // branch-free: every slot computes its range, an empty or
+                // absent one is masked to zero
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) {
                     const int v = g0 + 16 * sl + sub;
-                    if (p == 0) ex[sl] = v < vhi ? src.eye(sc, v) : 0.0f;
-                    pk[p][sl] = 0u;
-                    if (v < vhi) {
-                        const float Ex = ex[sl];
-                        const float lo = fmaxf(fmaf(l0.y, Ex, l0.x), fmaf(l1.y, Ex, l1.x));
-                        const float hi = fminf(fmaf(l0.w, Ex, l0.z), fmaf(l1.w, Ex, l1.z));
-                        const int ix0 = max(__float2int_ru(lo), 0);
-                        const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
-                        if (ix0 <= ix1 && ny[p] > 0u) {
-                            const uint32_t nx = uint32_t(ix1 - ix0) + 1u;
-                            pk[p][sl] = uint32_t(ix0) | (nx << 14);
-                            cnt += nx * ny[p];
-                            nz++;
-                        }
-                    }
+                    if (p == 0) ex[sl] = src.eye(sc, v < vhi ? v : vlo);
+                    const float Ex = ex[sl];
+                    const float lo = fmaxf(fmaf(l0.y, Ex, l0.x), fmaf(l1.y, Ex, l1.x));
+                    const float hi = fminf(fmaf(l0.w, Ex, l0.z), fmaf(l1.w, Ex, l1.z));
+                    const int ix0 = max(__float2int_ru(lo), 0);
+                    const int ix1 = min(__float2int_rd(hi), int(c.W) - 1);
+                    const bool ok = v < vhi && ix0 <= ix1 && ny[p] > 0u;
+                    const uint32_t nx = ok ? uint32_t(ix1 - ix0) + 1u : 0u;
+                    pk[p][sl] = ok ? uint32_t(ix0) | (nx << 14) : 0u;
+                    cnt += nx * ny[p];
+                    nz += ok ? 1u : 0u;
                 }
             }
             // a segment holds at most 2^26 candidates (one view), so lanes
@@ -311,12 +309,12 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
             for (int p = 0; p < P; p++)
 #pragma unroll
                 for (int sl = 0; sl < S; sl++) {
-                    if (pk[p][sl] != 0u) {
+                    const bool ok = pk[p][sl] != 0u;
+                    if (ok)
                         sm.seg[rank] = make_uint4(first, pk[p][sl], uint32_t(g0 + 16 * sl + sub) | uint32_t(2 * p + half) << 16,
                                                   __float_as_uint(ex[sl]));
-                        rank++;
-                        first += (pk[p][sl] >> 14) * ny[p];
-                    }
+                    rank += ok ? 1u : 0u;
+                    first += (pk[p][sl] >> 14) * ny[p];
                 }
             __syncwarp();
             if (big) {
