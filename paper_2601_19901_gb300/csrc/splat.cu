@@ -50,8 +50,9 @@ namespace {
 // with candidate bounds of their cell and triangle clipped to that limit
 // (k_fetch) and take the same passes and test.
 constexpr int kSplatWarps = 8;
-// Ask L2 for the line holding p (no register result).
+// Ask L2 (L1) for the line holding p (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // The per-pixel test; every condition is evaluated (no early exits), so the
 // lanes' different candidates do not diverge.
@@ -233,6 +234,15 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
             const uint32_t kn = k0 + 2u * P * n_warps + uint32_t(lane);   // the next unit's records
             if (lane < 2 * P && kn < n) prefetch_l2(work + kn);
         }
+        // the next unit's triangles (of one scene): read their ids now (the
+        // work records were asked for a unit ago), ask L1 for their records'
+        // 128-byte lines once this unit's candidates are formed, so that the
+        // next unit's staging finds them there
+        uint32_t next_tri = 0xffffffffu;
+        if constexpr (!Src::kMany) {
+            const uint32_t kn = k0 + 2u * P * n_warps + uint32_t(lane);
+            if (lane < 2 * P && kn < n) next_tri = __ldg(&work[kn].meta.z);
+        }
         const int vlo = src.view_lo(sc), vhi = src.view_hi(sc);
         for (int g0 = vlo; g0 < vhi; g0 += 16 * S) {
             __syncwarp();   // the previous passes are done with sm
@@ -316,6 +326,7 @@ __device__ __forceinline__ void splat_units(const Src& src, uint32_t total_units
                     rank += ok ? 1u : 0u;
                     first += (pk[p][sl] >> 14) * ny[p];
                 }
+            if (next_tri != 0xffffffffu && g0 == vlo) prefetch_l1(src.rec(sc) + next_tri);
             __syncwarp();
             if (big) {
                 // huge cells: each lane walks whole segments
