@@ -325,6 +325,9 @@ constexpr uint32_t kSplatLaneLimit = 1u << 24;
 // stream's order holds as for a plain launch. allow_next_kernel() lets the
 // kernel after it be placed early in turn.
 __device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Ask L2 (L1) for the line holding p (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 template <typename... P, typename... A>
 cudaError_t launch_after_previous(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

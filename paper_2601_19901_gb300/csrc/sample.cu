@@ -917,6 +917,10 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         uint2 pt = *reinterpret_cast<const uint2*>(a.points + p);
         if (!LFDPR_IN_BOUNDS(pt.x, a.n_tris, 5)) pt.x = 0;
         const TriRec* r = a.rec + pt.x;
+        // the thread's next point's triangle, read now: its record and
+        // projection lines are asked of L1 while this point's texels load
+        const uint32_t pnext = p + gridDim.x * blockDim.x;
+        const uint32_t tnext = pnext < n ? a.points[pnext].x : 0xffffffffu;
         // the texture map and spacings first; the frame (the same 128-byte
         // line) after the fetch, so it does not stay live across the gathers
         const float su = __ldg(&r->q[0].w), sv = __ldg(&r->q[1].w);
@@ -933,6 +937,10 @@ __global__ void __launch_bounds__(256, 4) k_fetch(FrameArgs a) {
         trilinear_pair(a.pool, a.lvl + (size_t)texid * kMaxLevels, td.w, td.h, int(td.levels) - 1, s, t, q7.z,
                        q7.w, tmin, tmax);
         *(reinterpret_cast<uint2*>(a.points + p) + 1) = make_uint2(tmin, tmax);
+        if (tnext < a.n_tris) {
+            prefetch_l1(a.rec + tnext);
+            prefetch_l1(a.tproj + tnext);
+        }
         const float4 q0 = __ldg(&r->q[0]), q1 = __ldg(&r->q[1]), q2 = __ldg(&r->q[2]);
         const float4 q3 = __ldg(&r->q[3]), q4 = __ldg(&r->q[4]), q5 = __ldg(&r->q[5]);
 

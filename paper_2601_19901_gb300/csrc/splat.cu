@@ -50,9 +50,6 @@ namespace {
 // with candidate bounds of their cell and triangle clipped to that limit
 // (k_fetch) and take the same passes and test.
 constexpr int kSplatWarps = 8;
-// Ask L2 (L1) for the line holding p (no register result).
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // The per-pixel test; every condition is evaluated (no early exits), so the
 // lanes' different candidates do not diverge.
