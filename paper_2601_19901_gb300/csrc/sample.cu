@@ -3,18 +3,23 @@
 //   k_setup  one thread per triangle: model transform, visibility against every
 //            view (Sec. 3), T_align frame, LFD-biased spacings from the closest
 //            eye, Eq. 1-3 texture limit, Eq. 4-7 mip set-up, point count by the
-//            lattice column walk; block sums for the scan.
+//            lattice column walk (each column's first row and row count kept
+//            for k_emit when there are at most four); block sums for the scan.
 //   k_scan   one block: exclusive scan of the block sums -> block offsets,
 //            total point count, overflow flag.
 //   k_emit   one thread per triangle: warp-shuffle block scan of the counts
 //            plus the block offset gives each triangle's first point id; the
-//            column walk writes (triangle, cell) for each of its points (a
-//            warp per triangle of more than kEmitBig points).
+//            column summary (or, for a wider triangle, the column walk again)
+//            writes (triangle, cell) for each of its points (a warp per
+//            triangle of more than kEmitBig points).
 //   k_fetch  one thread per point: texture coordinate of the cell centre and
 //            two trilinear fetches at LOD_min and LOD_max (Eq. 6-7); then the
 //            point's splat record (its cell projected into the views) and, if
 //            some view can hold a candidate pixel of it, its place in the
-//            splat's work list.
+//            splat's work list; the pass ends with the frame's key reset.
+//
+// Every kernel after k_setup is launched as a programmatic dependent of the
+// one before it and waits for it at its top (wait_previous_kernel).
 //   k_near_work  one thread per point whose cell or triangle reaches within
 //            near_z of the eyes' plane: the splat record of its cell and
 //            triangle clipped to that limit.
