@@ -17,6 +17,10 @@
  *  - Output buffers are owned by the caller.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
  *    launch work are asynchronous with respect to the host on that stream.
+ *    A frame's kernels after the first are launched as programmatic
+ *    dependents of the kernel before them (their launch overlaps its last
+ *    blocks) and wait for it before touching memory, so stream order holds
+ *    for the caller's own work as for plain launches.
  *  - Every call returns an lfdpr_status and never aborts the process. On error
  *    lfdpr_last_error() (per thread) holds a one-line description. Errors of
  *    asynchronous device work (point-buffer overflow, a launch failure) are
@@ -275,7 +279,9 @@ lfdpr_status lfdpr_frame_stats(lfdpr_display *disp, void *stream, lfdpr_stats *o
  * lfdpr_set_stage_timing: enable (1) or disable (0) CUDA events between the
  * stages of lfdpr_render_frame and around lfdpr_interleave, recorded on the
  * caller's stream; lfdpr_frame_stats then reports each stage's device time.
- * Off by default. Errors: EINVAL.
+ * The events separate the stages' kernels (no launch overlaps the kernel
+ * before it), so a timed frame runs a little longer (about 20 us for the
+ * paper-shaped frame). Off by default. Errors: EINVAL.
  */
 lfdpr_status lfdpr_set_stage_timing(lfdpr_display *disp, int32_t enable);
 
