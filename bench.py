@@ -640,10 +640,91 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batch_measure(n_scenes, tris_range, steps, warmup, stream, world=1, rank=0, clocks=None):
+    """Batched multi-scene frames (one CUDA graph per batch, autotuned): the
+    batch's frames/s with L2 flushed between batches, per-scene latency, and
+    the same frames one scene after another for comparison."""
+    import torch
+    from paper_2601_19901_gb300 import lfdpr, multigpu, scenes as S
+    ds, scs = S.batch_paper(n_scenes=n_scenes, tris_range=tris_range)
+    n = len(ds)
+    ts = lfdpr.TextureSet(S.textures_paper(), stream)
+    B = lfdpr.Batch(ds, scs, ts, [max(1 << 20, 6 * sc.n_tris) for sc in scs], stream)
+    try:
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        base = multigpu.rank_frames(rank, world, 1)[0]
+
+        def models(f):
+            return np.stack([S.model_matrix(base + f + 7 * k) for k in range(n)]).astype(np.float32)
+
+        cfg, tuned_ms = B.autotune(models(0), reps=2, stream=stream)
+        table = B.autotune_table()
+        for w in range(warmup):
+            B.render(models(1 + w), stream)
+        for i in range(n):
+            st = B.stats(i, stream)
+            if st.overflow or st.cell_overflow:
+                raise RuntimeError("scene %d overflowed its point buffer" % i)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.start()
+            time.sleep(0.3)
+        ms, scene_ms = [], []
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.render(models(1 + warmup + k), stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            scene_ms.append(B.scene_ms())
+        clk = clocks.stop() if clocks is not None else None
+        points = sum(B.stats(i, stream).n_points for i in range(n))
+        # the same frames one scene after another through lfdpr_render_frame + lfdpr_interleave
+        seq = []
+        for k in range(max(2, min(steps, 5))):
+            m = models(1 + warmup + k)
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(n):
+                lfdpr.lfdpr_render_frame(B.disps[i], B.meshes[i], m[i], stream)
+                lfdpr.lfdpr_interleave(B.disps[i], B.panel(i), stream)
+            e1.record(stream)
+            e1.synchronize()
+            seq.append(e0.elapsed_time(e1))
+        ms_sorted = sorted(ms)
+        pct = lambda q: ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(q * len(ms_sorted))) - 1)]
+        seq_rate = n / (statistics.mean(seq) / 1000.0)
+        return {"ms": ms, "n": n, "clk": clk, "points": points,
+                "workload": "%d paper-shaped scenes, %d triangles in all (%d-%d per scene), 24/48/96 views at "
+                            "420x560 or 640x360, 2560x1600 panels, 64 shared textures 64^2-4096^2"
+                            % (n, sum(s.n_tris for s in scs), min(s.n_tris for s in scs), max(s.n_tris for s in scs)),
+                "rendered_views": sum(d.n_render_views for d in ds),
+                "batch_ms_p50": pct(0.50), "batch_ms_p99": pct(0.99),
+                "scene_latency_ms": {
+                    "p50": float(np.percentile(np.concatenate(scene_ms), 50)),
+                    "p99": float(np.percentile(np.concatenate(scene_ms), 99)),
+                    "per_scene_p50": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 50, axis=0)],
+                    "per_scene_p99": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 99, axis=0)],
+                    "what": "device time from the start of the batch's graph to the end of each scene's "
+                            "interleave (events inside the graph), over every scene and timed batch"},
+                "sequential_frames_per_s": seq_rate,
+                "autotuned": {"branches": cfg.branches, "splat_blocks_per_sm": cfg.splat_blocks_per_sm,
+                              "splat_slots": cfg.splat_slots, "ms_per_batch_while_tuning": tuned_ms,
+                              "candidates_ms": {"%d/%d/%d" % t[:3]: round(t[3], 3) for t in table}}}
+    finally:
+        B.close()
+        ts.close()
+
+
 def run_batch(args):
     import torch
     import torch.distributed as dist
-    from paper_2601_19901_gb300 import build as B_, lfdpr, multigpu, scenes as S
+    from paper_2601_19901_gb300 import build as B_, lfdpr, multigpu
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -657,104 +738,80 @@ def run_batch(args):
         dist.barrier()
     lfdpr.lib()
     lo, hi = (float(x) for x in args.batch_tris.split(","))
-    ds, scs = S.batch_paper(n_scenes=args.batch_scenes, tris_range=(lo, hi))
-    n = len(ds)
     stream = torch.cuda.Stream()
-    ts = lfdpr.TextureSet(S.textures_paper(), stream)
-    B = lfdpr.Batch(ds, scs, ts, [max(1 << 20, 6 * sc.n_tris) for sc in scs], stream)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    base = multigpu.rank_frames(rank, world, 1)[0]
-
-    def models(f):
-        return np.stack([S.model_matrix(base + f + 7 * k) for k in range(n)]).astype(np.float32)
-
-    cfg, tuned_ms = B.autotune(models(0), reps=2, stream=stream)
-    table = B.autotune_table()
-    for w in range(args.warmup):
-        B.render(models(1 + w), stream)
-    for i in range(n):
-        st = B.stats(i, stream)
-        if st.overflow or st.cell_overflow:
-            raise RuntimeError("scene %d overflowed its point buffer" % i)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         pass
-    clocks = ClockSampler(uuid)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    ms, scene_ms = [], []
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        B.render(models(1 + args.warmup + k), stream)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        scene_ms.append(B.scene_ms())
-    clk = clocks.stop()
-    points = sum(B.stats(i, stream).n_points for i in range(n))
+    r = batch_measure(args.batch_scenes, (lo, hi), args.steps, args.warmup, stream, world, rank, ClockSampler(uuid))
+    n, ms = r["n"], r["ms"]
     total_ms = multigpu.max_over_ranks(sum(ms), device="cuda")
     value = multigpu.job_rate(world, n * args.steps, total_ms / 1000.0)
-    # the same frames one scene after another through lfdpr_render_frame + lfdpr_interleave
-    seq = []
-    for k in range(max(2, min(args.steps, 5))):
-        m = models(1 + args.warmup + k)
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(n):
-            lfdpr.lfdpr_render_frame(B.disps[i], B.meshes[i], m[i], stream)
-            lfdpr.lfdpr_interleave(B.disps[i], B.panel(i), stream)
-        e1.record(stream)
-        e1.synchronize()
-        seq.append(e0.elapsed_time(e1))
     if world > 1:
         dist.barrier()
     if rank == 0:
-        ms_sorted = sorted(ms)
-        pct = lambda q: ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(q * len(ms_sorted))) - 1)]
-        seq_rate = n / (statistics.mean(seq) / 1000.0)
         line = {"metric": "batched multi-scene display frames/s (every scene of the batch rendered and "
                           "interleaved)",
                 "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "%d paper-shaped scenes, %d triangles in all (%d-%d per scene), "
-                                       "24/48/96 views at 420x560 or 640x360, 2560x1600 panels, 64 shared "
-                                       "textures 64^2-4096^2" % (n, sum(s.n_tris for s in scs),
-                                                                 min(s.n_tris for s in scs),
-                                                                 max(s.n_tris for s in scs)),
-                           "l2": "flushed (512 MiB write) between timed batches",
-                           "rendered_views": sum(d.n_render_views for d in ds)},
-                "batch_ms_p50": pct(0.50), "batch_ms_p99": pct(0.99),
-                "scene_latency_ms": {
-                    "p50": float(np.percentile(np.concatenate(scene_ms), 50)),
-                    "p99": float(np.percentile(np.concatenate(scene_ms), 99)),
-                    "per_scene_p50": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 50, axis=0)],
-                    "per_scene_p99": [round(float(x), 3) for x in np.percentile(np.stack(scene_ms), 99, axis=0)],
-                    "what": "device time from the start of the batch's graph to the end of each scene's "
-                            "interleave (events inside the graph), over every scene and timed batch"},
-                "points_per_batch": points, "points_per_s": points * args.steps * world / (total_ms / 1000.0),
-                "sequential_frames_per_s": seq_rate, "speedup_vs_sequential": value / world / seq_rate,
-                "autotuned": {"branches": cfg.branches, "splat_blocks_per_sm": cfg.splat_blocks_per_sm,
-                              "splat_slots": cfg.splat_slots, "ms_per_batch_while_tuning": tuned_ms,
-                              "candidates_ms": {"%d/%d/%d" % t[:3]: round(t[3], 3) for t in table}},
+                "config": {"workload": r["workload"], "l2": "flushed (512 MiB write) between timed batches",
+                           "rendered_views": r["rendered_views"]},
+                "batch_ms_p50": r["batch_ms_p50"], "batch_ms_p99": r["batch_ms_p99"],
+                "scene_latency_ms": r["scene_latency_ms"],
+                "points_per_batch": r["points"], "points_per_s": r["points"] * args.steps * world / (total_ms / 1000.0),
+                "sequential_frames_per_s": r["sequential_frames_per_s"],
+                "speedup_vs_sequential": value / world / r["sequential_frames_per_s"],
+                "autotuned": r["autotuned"],
                 "gpu_launches": int(args.steps * (7 * n + 1)),
-                "clocks": clk}
+                "clocks": r["clk"]}
         print(json.dumps(line), flush=True)
-    B.close()
-    ts.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def pbr_measure(stream, steps=10, warmup=3):
+    """Meshes of materials with physically based shading on the paper-shaped
+    geometry: frames/s with L2 flushed between frames, then the stages of as
+    many instrumented frames."""
+    import torch
+    from paper_2601_19901_gb300 import lfdpr, scenes as S
+    d, sc = S.display_paper(), S.scene_pbr_paper()
+    R = lfdpr.Renderer(d, sc, stream=stream, shading=S.Shading())
+    try:
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        panel = torch.empty((d.panel_h, d.panel_w, 4), dtype=torch.uint8, device="cuda")
+        for k in range(warmup):
+            R.render(S.model_matrix(k), stream)
+            R.interleave(panel.data_ptr(), stream)
+        ms, stage = [], {n: [] for n in lfdpr.STAGES}
+        for timing in (False, True):
+            R.set_stage_timing(timing)
+            for k in range(steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                R.render(S.model_matrix(warmup + k), stream)
+                R.interleave(panel.data_ptr(), stream)
+                e1.record(stream)
+                st = R.stats(stream)
+                if timing:
+                    for i, n in enumerate(lfdpr.STAGES):
+                        stage[n].append(st.stage_ms[i])
+                else:
+                    ms.append(e0.elapsed_time(e1))
+        return {"what": "the paper-shaped geometry with 16 materials of four textures (albedo, normal, roughness, "
+                        "metallic) 64^2-4096^2, physically based shading, 48 views, interleaved; %d frames, L2 "
+                        "flushed" % steps,
+                "frames_per_s": 1000.0 / statistics.mean(ms),
+                "stage_ms": {n: statistics.mean(v) for n, v in stage.items()}}
+    finally:
+        R.close()
 
 
 def learned_measure(sc, steps, warmup, quality_frames, stream=None):
@@ -904,9 +961,10 @@ def run_learned(args):
 
 def secondary_measurements(args, sc, stream):
     """Frames/s of the 96-view (2x angular, tent, crosstalk) frame on the same
-    scene, and the learned quarter-view path with its quality against both
-    readings of its ground truth: measured after the main timed region, reported
-    beside it (not part of `value`)."""
+    scene, the learned quarter-view path with its quality against both
+    readings of its ground truth, a batch of 32 paper-shaped scenes, and the
+    meshes of materials with physically based shading: measured after the
+    main timed region, reported beside it (not part of `value`)."""
     import torch
     from paper_2601_19901_gb300 import lfdpr, scenes as S
     out = {}
@@ -944,6 +1002,21 @@ def secondary_measurements(args, sc, stream):
         out["learned"] = learned_measure(sc, 10, 3, range(0, 120, 15), stream)
     except Exception as e:   # the weights ship with the package; report rather than hide a failure
         out["learned"] = {"error": repr(e)}
+    try:
+        r = batch_measure(32, (5.0e4, 2.0e6), 5, 2, stream)
+        out["batch_32_scenes"] = {
+            "what": r["workload"] + "; one CUDA graph per batch, autotuned; 5 batches, L2 flushed",
+            "frames_per_s": r["n"] * len(r["ms"]) / (sum(r["ms"]) / 1000.0),
+            "batch_ms_p50": r["batch_ms_p50"], "scene_latency_ms_p50": r["scene_latency_ms"]["p50"],
+            "scene_latency_ms_p99": r["scene_latency_ms"]["p99"],
+            "sequential_frames_per_s": r["sequential_frames_per_s"], "autotuned": {
+                k: r["autotuned"][k] for k in ("branches", "splat_blocks_per_sm", "splat_slots")}}
+    except Exception as e:
+        out["batch_32_scenes"] = {"error": repr(e)}
+    try:
+        out["pbr_materials"] = pbr_measure(stream)
+    except Exception as e:
+        out["pbr_materials"] = {"error": repr(e)}
     return out
 
 
