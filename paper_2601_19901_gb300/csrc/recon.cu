@@ -440,7 +440,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 #pragma unroll
                         for (int i = 0; i < 12; i++)
                             *reinterpret_cast<float4*>(bv + 4 * i) = reinterpret_cast<const float4*>(s_bias + j)[i];
-#pragma unroll
                         // the base's 16 views at this position, all loads in flight first
                         uint32_t bws[16];
 #pragma unroll
