@@ -20,7 +20,11 @@
  *    A frame's kernels after the first are launched as programmatic
  *    dependents of the kernel before them (their launch overlaps its last
  *    blocks) and wait for it before touching memory, so stream order holds
- *    for the caller's own work as for plain launches.
+ *    for the caller's own work as for plain launches. Each of them lets the
+ *    next kernel start early, so a kernel of the caller's that is itself
+ *    launched with programmatic stream serialization right after a call must
+ *    wait for its predecessor (griddepcontrol.wait) before reading the
+ *    call's results, as programmatic dependent launch requires.
  *  - Every call returns an lfdpr_status and never aborts the process. On error
  *    lfdpr_last_error() (per thread) holds a one-line description. Errors of
  *    asynchronous device work (point-buffer overflow, a launch failure) are
